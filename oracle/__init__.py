@@ -1,0 +1,221 @@
+"""Plain serial FP64 CPU oracle for the Paraexp direct-adjoint loop (arXiv 2004.00546).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. It shares no code with
+the CUDA library in ``paper_2004_00546_gb300``; the two meet only through the
+seeded input generators, which hold none of the method's arithmetic.
+
+Every function here is a thin ctypes marshaller over ``pxo.c``; the arithmetic
+lives in C (see the comments there for the passage each function follows).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pxo.c")
+_LIB_PATH = os.path.join(_HERE, "libpxo.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_p = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile ``pxo.c`` into ``libpxo.so`` with plain gcc (no vendor libraries)."""
+    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], cwd=_HERE
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            sigs = {
+                "pxo_ad1_apply": [_i, _d, _d, _d, _p, _p],
+                "pxo_ad1_apply_T": [_i, _d, _d, _d, _p, _p],
+                "pxo_ad1_cn_step": [_i, _d, _d, _d, _d, _p, _p, _p],
+                "pxo_ad1_cn_step_T": [_i, _d, _d, _d, _d, _p, _p],
+                "pxo_ad1_phi_dft": [_i, _d, _d, _d, _i, _d, _d, _i64, _i, _p, _p],
+                "pxo_ad1_cn_gradient_serial": [_i, _d, _d, _d, _d, _i64, _p, _p, _p, _p],
+                "pxo_ad1_cn_gradient_paraexp": [_i, _d, _d, _d, _d, _i64, _i, _i, _p, _p, _p, _p],
+                "pxo_bu1_rhs": [_i, _d, _d, _p, _p],
+                "pxo_bu1_jac": [_i, _d, _d, _p, _p, _p],
+                "pxo_bu1_jac_T": [_i, _d, _d, _p, _p, _p],
+                "pxo_bu1_rk4_step": [_i, _d, _d, _d, _d, _d, _p, _p, _p],
+                "pxo_bu1_gradient_serial": [_i, _d, _d, _d, _i64, _d, _p, _p, _p, _p, _p, _p],
+                "pxo_bu1_gradient_hybrid": [_i, _d, _d, _d, _i64, _d, _i, _i, _i, _i, _p, _p, _p,
+                                            _p, _p],
+                "pxo_expm": [_i, _p, _p],
+                "pxo_ad1_krylov_expv": [_i, _d, _d, _d, _d, _i, _p, _p, _p],
+                "pxo_partition_nonequi": [_d, _i, _d, _p],
+            }
+            for name, argt in sigs.items():
+                fn = getattr(L, name)
+                fn.argtypes = argt
+                fn.restype = _i
+            _lib = L
+    return _lib
+
+
+def _in(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_p)
+
+
+def _check(rc: int, name: str):
+    if rc != 0:
+        raise ValueError(f"{name}: invalid arguments (rc={rc})")
+
+
+TWO_PI = 2.0 * np.pi
+
+
+# ---- 1D advection-diffusion ------------------------------------------------
+def ad1_apply(q, c, nu, L=TWO_PI, transpose=False):
+    q = _in(q)
+    out = np.empty_like(q)
+    fn = lib().pxo_ad1_apply_T if transpose else lib().pxo_ad1_apply
+    _check(fn(q.size, L, c, nu, _ptr(q), _ptr(out)), "ad1_apply")
+    return out
+
+
+def ad1_cn_step(q, c, nu, dt, src=None, L=TWO_PI):
+    q = _in(q)
+    s = None if src is None else _in(src)
+    out = np.empty_like(q)
+    _check(lib().pxo_ad1_cn_step(q.size, L, c, nu, dt, _ptr(q), _ptr(s), _ptr(out)), "cn_step")
+    return out
+
+
+def ad1_cn_step_T(q, c, nu, dt, L=TWO_PI):
+    q = _in(q)
+    out = np.empty_like(q)
+    _check(lib().pxo_ad1_cn_step_T(q.size, L, c, nu, dt, _ptr(q), _ptr(out)), "cn_step_T")
+    return out
+
+
+PHI_EXP, PHI_CN, PHI_RK4 = 0, 1, 2
+
+
+def ad1_phi_dft(v, c, nu, mode, t=0.0, dt=0.0, steps=0, transpose=False, L=TWO_PI):
+    v = _in(v)
+    out = np.empty_like(v)
+    _check(lib().pxo_ad1_phi_dft(v.size, L, c, nu, mode, t, dt, int(steps), int(transpose),
+                                 _ptr(v), _ptr(out)), "phi_dft")
+    return out
+
+
+def ad1_cn_gradient_serial(q0, c, nu, T, K, L=TWO_PI):
+    q0 = _in(q0)
+    J = ctypes.c_double()
+    g = np.empty_like(q0)
+    qT = np.empty_like(q0)
+    _check(lib().pxo_ad1_cn_gradient_serial(q0.size, L, c, nu, T, int(K), _ptr(q0),
+                                            ctypes.byref(J), _ptr(g), _ptr(qT)), "cn_serial")
+    return J.value, g, qT
+
+
+def ad1_cn_gradient_paraexp(q0, c, nu, T, K, P, phi_mode, L=TWO_PI):
+    q0 = _in(q0)
+    J = ctypes.c_double()
+    g = np.empty_like(q0)
+    qT = np.empty_like(q0)
+    _check(lib().pxo_ad1_cn_gradient_paraexp(q0.size, L, c, nu, T, int(K), int(P), int(phi_mode),
+                                             _ptr(q0), ctypes.byref(J), _ptr(g), _ptr(qT)),
+           "cn_paraexp")
+    return J.value, g, qT
+
+
+def ad1_krylov_expv(v, c, nu, t, m, L=TWO_PI):
+    v = _in(v)
+    e = np.empty_like(v)
+    p1 = np.empty_like(v)
+    _check(lib().pxo_ad1_krylov_expv(v.size, L, c, nu, t, m, _ptr(v), _ptr(e), _ptr(p1)),
+           "krylov_expv")
+    return e, p1
+
+
+# ---- 1D Burgers -------------------------------------------------------------
+def bu1_rhs(u, nu, L=TWO_PI):
+    u = _in(u)
+    out = np.empty_like(u)
+    _check(lib().pxo_bu1_rhs(u.size, L, nu, _ptr(u), _ptr(out)), "bu1_rhs")
+    return out
+
+
+def bu1_jac(u, w, nu, L=TWO_PI, transpose=False):
+    u, w = _in(u), _in(w)
+    out = np.empty_like(u)
+    fn = lib().pxo_bu1_jac_T if transpose else lib().pxo_bu1_jac
+    _check(fn(u.size, L, nu, _ptr(u), _ptr(w), _ptr(out)), "bu1_jac")
+    return out
+
+
+def bu1_rk4_step(u, f, nu, dt, t=0.0, omega=0.0, L=TWO_PI):
+    u, f = _in(u), _in(f)
+    out = np.empty_like(u)
+    _check(lib().pxo_bu1_rk4_step(u.size, L, nu, dt, t, omega, _ptr(f), _ptr(u), _ptr(out)),
+           "bu1_rk4_step")
+    return out
+
+
+def bu1_gradient_serial(f, g, nu, T, K, omega=0.0, u0=None, L=TWO_PI, want_traj=False):
+    f, g = _in(f), _in(g)
+    u0a = None if u0 is None else _in(u0)
+    J = ctypes.c_double()
+    grad = np.empty_like(f)
+    traj = np.empty((int(K) + 1, f.size)) if want_traj else None
+    _check(lib().pxo_bu1_gradient_serial(f.size, L, nu, T, int(K), omega, _ptr(u0a), _ptr(f),
+                                         _ptr(g), ctypes.byref(J), _ptr(grad), _ptr(traj)),
+           "bu1_serial")
+    return (J.value, grad, traj) if want_traj else (J.value, grad)
+
+
+HOM_MAGNUS, HOM_STEPPER = 0, 1
+
+
+def bu1_gradient_hybrid(f, g, nu, T, K, P, hom_mode=HOM_MAGNUS, M_mag=25, m_kry=30, omega=0.0,
+                        u0=None, L=TWO_PI):
+    f, g = _in(f), _in(g)
+    u0a = None if u0 is None else _in(u0)
+    J = ctypes.c_double()
+    grad = np.empty_like(f)
+    _check(lib().pxo_bu1_gradient_hybrid(f.size, L, nu, T, int(K), omega, int(P), int(hom_mode),
+                                         int(M_mag), int(m_kry), _ptr(u0a), _ptr(f), _ptr(g),
+                                         ctypes.byref(J), _ptr(grad)), "bu1_hybrid")
+    return J.value, grad
+
+
+# ---- small helpers -----------------------------------------------------------
+def expm(A):
+    A = _in(A)
+    d = A.shape[0]
+    E = np.empty_like(A)
+    _check(lib().pxo_expm(d, _ptr(A), _ptr(E)), "expm")
+    return E
+
+
+def partition_nonequi(T, N, k):
+    out = np.empty(N + 1)
+    _check(lib().pxo_partition_nonequi(T, N, k, _ptr(out)), "partition_nonequi")
+    return out

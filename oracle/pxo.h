@@ -1,0 +1,108 @@
+/*
+ * pxo — plain, serial, FP64 CPU oracle for the Paraexp direct-adjoint loop
+ * (Skene, Eggl & Schmid, "A parallel-in-time approach for accelerating
+ * direct-adjoint studies", arXiv 2004.00546).
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is the independent reference that the
+ * CUDA path is checked against. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * Conventions (all functions):
+ *   - host pointers, FP64, caller-owned; nothing is retained after return;
+ *   - periodic grid x_i = i*h, h = L/n, n >= 3 (periodic central differences need
+ *     three distinct neighbours); functions return 0 on success, -1 on invalid
+ *     arguments (null pointer, n < 3, K < 1, P < 1, K % P != 0, ...).
+ *   - "transpose" means the plain matrix transpose (discrete adjoint, Sec. 2:
+ *     the discrete adjoint operator is the conjugate transpose; everything is real).
+ */
+#ifndef PXO_H
+#define PXO_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- 1D linear advection-diffusion, Sec. 4.2 (1D restriction) -------------
+ * (A q)_i = -c (q_{i+1}-q_{i-1})/(2h) + nu (q_{i+1}-2 q_i+q_{i-1})/h^2.      */
+int pxo_ad1_apply(int n, double L, double c, double nu, const double* q, double* out);
+int pxo_ad1_apply_T(int n, double L, double c, double nu, const double* q, double* out);
+
+/* Crank–Nicolson step (I - dt/2 A) out = (I + dt/2 A) q + dt*src (src may be NULL),
+ * solved as a periodic tridiagonal system by Sherman–Morrison + Thomas.          */
+int pxo_ad1_cn_step(int n, double L, double c, double nu, double dt, const double* q,
+                    const double* src, double* out);
+/* Transposed CN map: out = (I + dt/2 A^T)(I - dt/2 A^T)^{-1} q.                  */
+int pxo_ad1_cn_step_T(int n, double L, double c, double nu, double dt, const double* q,
+                      double* out);
+
+/* Exact homogeneous propagator of the circulant A by a naive O(n^2) DFT.
+ * mode 0 (EXP):     out = exp(t A) v                (t = time span)
+ * mode 1 (STEPPER): out = R_CN(dt A)^steps v,  R_CN(z) = (1+z/2)/(1-z/2)
+ * mode 2 (STEPPER): out = R_RK4(dt A)^steps v, R_RK4(z) = 1+z+z^2/2+z^3/6+z^4/24
+ * transpose != 0 uses A^T.                                                     */
+int pxo_ad1_phi_dft(int n, double L, double c, double nu, int mode, double t, double dt,
+                    int64_t steps, int transpose, const double* v, double* out);
+
+/* Serial direct-adjoint loop, IC control, J = 0.5 ||q(T)||^2, CN with K steps.
+ * Returns J in *J, dJ/dq0 in grad (n), q(T) in qT (may be NULL).                 */
+int pxo_ad1_cn_gradient_serial(int n, double L, double c, double nu, double T, int64_t K,
+                               const double* q0, double* J, double* grad, double* qT);
+
+/* Paraexp direct-adjoint loop (Alg. 1; Eqs. linzero, linInhomEqus, hom, fullsol0,
+ * adjInhom, adjHomNormal, fulladjsol) for the same problem, equal partition into P
+ * parts; inhomogeneous parts stepped with CN, homogeneous parts with the exact DFT
+ * propagator of mode phi_mode (0 = exp, 1 = CN stepper).                          */
+int pxo_ad1_cn_gradient_paraexp(int n, double L, double c, double nu, double T, int64_t K,
+                                int P, int phi_mode, const double* q0, double* J,
+                                double* grad, double* qT);
+
+/* ---- 1D viscous Burgers, Sec. 4.3 (1D restriction) -------------------------
+ * N(u)_i = -u_i (u_{i+1}-u_{i-1})/(2h) + nu (u_{i+1}-2u_i+u_{i-1})/h^2          */
+int pxo_bu1_rhs(int n, double L, double nu, const double* u, double* out);
+/* Jacobian dN/du at u applied to w, and its transpose.                          */
+int pxo_bu1_jac(int n, double L, double nu, const double* u, const double* w, double* out);
+int pxo_bu1_jac_T(int n, double L, double nu, const double* u, const double* w, double* out);
+
+/* One classical RK4 step of du/dt = N(u) + s(t) f at time t; s(t) = sin(omega t),
+ * or s = 1 when omega == 0.                                                      */
+int pxo_bu1_rk4_step(int n, double L, double nu, double dt, double t, double omega,
+                     const double* f, const double* u, double* out);
+
+/* Serial direct-adjoint loop for forcing control f, u(0) = u0 (NULL = 0),
+ * J = (1/T) sum_{j=1..K} dt ||u_j - g||^2 (rectangle rule of Eq. cost).
+ * Exact discrete adjoint of the RK4 map (reverse sweep of the four stages).
+ * traj (optional, (K+1)*n) receives u_0..u_K.                                    */
+int pxo_bu1_gradient_serial(int n, double L, double nu, double T, int64_t K, double omega,
+                            const double* u0, const double* f, const double* g, double* J,
+                            double* grad, double* traj);
+
+/* Hybrid serial-direct / parallel-adjoint loop (Sec. 3.3; Eqs. seriesDirect,
+ * hybadjinhom, adjHomNormal, fullAdjSolHyb) with the equal partition into P parts.
+ * Adjoint inhomogeneous parts: exact discrete RK4 adjoint per subinterval.
+ * Adjoint homogeneous parts (chained through the subintervals):
+ *   hom_mode 0: 4th-order Magnus steps of M_mag RK4 steps each (two Gauss nodes,
+ *               U interpolated by 4-point Lagrange in time), exp and phi_1 by a
+ *               Krylov space of dimension m_kry (Saad 1992) and a dense exponential;
+ *   hom_mode 1: exact transposed RK4 stepping (consistency reference).           */
+int pxo_bu1_gradient_hybrid(int n, double L, double nu, double T, int64_t K, double omega,
+                            int P, int hom_mode, int M_mag, int m_kry, const double* u0,
+                            const double* f, const double* g, double* J, double* grad);
+
+/* ---- small dense and Krylov building blocks ------------------------------- */
+/* Dense matrix exponential (row-major d x d), scaling and squaring of a Taylor
+ * series evaluated in long double.                                              */
+int pxo_expm(int d, const double* A, double* E);
+/* Krylov approximation (Saad 1992) of exp(t A) v and, optionally, t*phi_1(t A) v
+ * for the 1D advection-diffusion operator (m = Krylov dimension).                */
+int pxo_ad1_krylov_expv(int n, double L, double c, double nu, double t, int m,
+                        const double* v, double* out_exp, double* out_phi1);
+
+/* Non-equidistant partition of Eq. nonEquiP: T_j = T (1 - r^j)/(1 - r^N),
+ * r = k/(k+1); out has N+1 entries.                                              */
+int pxo_partition_nonequi(double T, int N, double k, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
