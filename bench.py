@@ -1,0 +1,352 @@
+"""Benchmark: gradient evaluations per second of the Paraexp direct-adjoint loop on GB300.
+
+One step = one full direct-adjoint loop (direct solve, adjoint solve, objective and
+gradient) through the C ABI of libpxa, inputs resident in HBM.
+
+Default workload (the 1D viscous Burgers configuration): n = 1024, nu = 0.005,
+T = 2, classical RK4 with dt = 1e-4 (K = 20000 steps), FP64, forcing control with
+random Fourier coefficients (k <= 16), tracking objective against a seeded target,
+P = 32 subintervals; the direct problem is serial, the adjoint is Paraexp (hybrid
+scheme). ``--workload advdiff1d`` runs the 1D advection-diffusion configuration
+(n = 256, CN with K = 4096, P = 8, Krylov m = 30).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s: batched Paraexp vs serial stepping, same GPU, rel.err<=1e-8"
+FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of GB300 (1.25 TFLOP/s)
+SMS = 152
+
+WORKLOADS = {
+    "burgers1d": dict(kind="burgers1d", n=1024, nu=0.005, T=2.0, K=20000, P=32, M=25, m=20,
+                      tol=1e-9, label="1D viscous Burgers n=1024 nu=0.005 T=2 RK4 dt=1e-4 FP64 P=32"),
+    "advdiff1d": dict(kind="advdiff1d", n=256, c=1.0, nu=0.01, T=1.0, K=4096, P=8, m=30, sub=1,
+                      tol=1e-11, label="1D advection-diffusion n=256 nu=0.01 T=1 CN 4096 steps FP64 P=8 m=30"),
+}
+
+# Algorithmic FP64 operations per grid point per step of each kernel.
+FLOPS_RK4_DIRECT = 62.0       # four stages of N(u) + s f, stage updates, J accumulation
+FLOPS_RK4_ADJOINT = 150.0     # stage recompute (3 x 14) + four J^T applies and updates
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="burgers1d", choices=sorted(WORKLOADS))
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 2 + i and r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs(w):
+    from paper_2004_00546_gb300 import inputs as I
+
+    if w["kind"] == "burgers1d":
+        p = I.burgers1d_problem(n=w["n"])
+        return {"control": p["f"], "target": p["g"]}
+    p = I.advdiff1d_problem(n=w["n"])
+    return {"control": p["q0"]}
+
+
+def make_ctx(X, w, phi):
+    ctx = X.Context()
+    if w["kind"] == "burgers1d":
+        ctx.set_operator(X.BURGERS_1D, w["n"], nu=w["nu"])
+        ctx.set_time(w["T"], w["K"], X.RK4, w["P"])
+        ctx.set_krylov(w["m"], w["tol"], phi, 1)
+        ctx.set_magnus(w["M"])
+    else:
+        ctx.set_operator(X.ADVDIFF_1D, w["n"], c=w["c"], nu=w["nu"])
+        ctx.set_time(w["T"], w["K"], X.CN, w["P"])
+        ctx.set_krylov(w["m"], w["tol"], phi, w["sub"])
+    return ctx
+
+
+def oracle_gradient(w, inp, K=None):
+    """Serial FP64 oracle (the plain definition of the discrete gradient)."""
+    import oracle as O
+
+    K = w["K"] if K is None else K
+    T = w["T"] * K / w["K"]
+    if w["kind"] == "burgers1d":
+        J, g = O.bu1_gradient_serial(inp["control"], inp["target"], w["nu"], T, K)
+    else:
+        J, g, _ = O.ad1_cn_gradient_serial(inp["control"], w["c"], w["nu"], T, K)
+    return J, g
+
+
+def time_mode(X, torch, ctx, mode, steps, warmup, flush, timing=False):
+    """Per-step CUDA-event times (ms) on the context's stream, L2 flushed between steps."""
+    n = ctx.n
+    grad = torch.empty(n, dtype=torch.float64, device="cuda")
+    Jd = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx.set_timing(timing)
+    ctx.set_graph(not timing)
+    for _ in range(warmup):
+        ctx.gradient(mode, grad)
+    times, phases = [], []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if timing:
+            ctx.gradient(mode, grad)
+        else:
+            ctx.gradient_async(mode, Jd, grad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        times.append(e0.elapsed_time(e1))
+        if timing:
+            phases.append(ctx.stats())
+    return times, phases, grad
+
+
+def run_ours(args, w, rank, world):
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    X.load()
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    inp = make_inputs(w)
+    ctl = torch.as_tensor(inp["control"], device="cuda")
+    tgt = torch.as_tensor(inp["target"], device="cuda") if "target" in inp else None
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    variants = {}
+    phis = [("paraexp_stepper", X.PARAEXP, X.PHI_STEPPER), ("paraexp_exp", X.PARAEXP, X.PHI_EXP),
+            ("serial", X.SERIAL, X.PHI_STEPPER)]
+    grads = {}
+    for name, mode, phi in phis:
+        ctx = make_ctx(X, w, phi)
+        ctx.set_control(ctl)
+        if tgt is not None:
+            ctx.set_target(tgt)
+        times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
+        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name}
+        grads[name] = g.detach().cpu().numpy()
+        ctx.close()
+
+    # accuracy of each variant against the serial FP64 oracle (one full gradient)
+    cpu = {}
+    if rank == 0:
+        t0 = time.perf_counter()
+        J_ref, g_ref = oracle_gradient(w, inp)
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt_cpu, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full serial FP64 gradient of the {w['kind']} workload ({dt_cpu:.2f} s)"}
+        for name in variants:
+            variants[name]["rel_err"] = float(np.linalg.norm(grads[name] - g_ref) / np.linalg.norm(g_ref))
+
+    # the headline: fastest Paraexp variant whose gradient meets rel.err <= 1e-8
+    ok = [k for k in ("paraexp_exp", "paraexp_stepper")
+          if variants[k].get("rel_err", 0.0) <= 1e-8]
+    head = min(ok, key=lambda k: variants[k]["ms_per_step"]) if ok else "paraexp_stepper"
+    phi = X.PHI_EXP if head == "paraexp_exp" else X.PHI_STEPPER
+    ctx = make_ctx(X, w, phi)
+    ctx.set_control(ctl)
+    if tgt is not None:
+        ctx.set_target(tgt)
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_index) as clk:
+        times, phases, _ = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush,
+                                     timing=True)
+    total_ms = float(sum(times))
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point: H2D of the control, D2H of the gradient
+    ctx.set_timing(False)
+    ctx.set_graph(True)
+    gh = np.empty(w["n"])
+    ch = np.ascontiguousarray(inp["control"])
+    ctx.gradient_host(X.PARAEXP, ch, gh)
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.gradient_host(X.PARAEXP, ch, gh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world / float(np.mean(e2e_t)), "unit": "gradient evals/s",
+           "h2d_bytes_per_step": 8 * w["n"], "d2h_bytes_per_step": 8 * w["n"] + 8}
+
+    # roofline of the dominant kernel, from the per-phase CUDA events of the timed steps
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in
+          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom")}
+    n, K, P = w["n"], w["K"], w["P"]
+    if w["kind"] == "burgers1d":
+        kernels = {
+            "bu1_direct_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K),
+            "bu1_adjoint_lanes_kernel": (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K),
+            "homogeneous_chain": (ph["ms_adjoint_hom"],
+                                  FLOPS_RK4_ADJOINT * n * K * (P - 1) / P if head == "paraexp_stepper" else None),
+        }
+    else:
+        kernels = {
+            "cn_lanes_kernel": (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"], None),
+            "ad1_chain_kernel": (ph["ms_direct_hom"] + ph["ms_adjoint_hom"], None),
+        }
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    ms_dom, flops = kernels[dom]
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": FP64_PEAK_GFLOPS / 1e3,
+            "peak_kind": "nominal FP64 (1.25 TFLOP/s, 152 SMs x 2 DFMA/clk x 2.07 GHz ~ 1.26)",
+            "traffic": None, "ms_per_launch": ms_dom}
+    if flops is not None and ms_dom > 0:
+        ach = flops / (ms_dom * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / (FP64_PEAK_GFLOPS / 1e3)})
+    else:
+        roof.update({"achieved": None, "frac": None})
+
+    launches_per_step = {"burgers1d": 4, "advdiff1d": 7}[w["kind"]]
+    line = {
+        "metric": METRIC, "value": value, "unit": "gradient evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 fields shaped like the paper's workloads)",
+        "config": {"workload": w["label"], "homogeneous": head, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "variants": variants, "phases_ms": ph, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+    }
+    ctx.close()
+    return line
+
+
+def run_reference(args, w, rank, world):
+    """The reference arm: the serial FP64 CPU oracle, timed on this host's cores."""
+    if rank != 0:
+        return None
+    inp = make_inputs(w)
+    # bounded sample per step: the first K_s steps of the window (direct + adjoint);
+    # the cost is linear in the number of steps, so throughput scales by K_s / K
+    K_s = max(w["P"], min(w["K"], 2000))
+    while w["K"] % K_s:
+        K_s -= 1
+    for _ in range(args.warmup):
+        oracle_gradient(w, inp, K_s)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_gradient(w, inp, K_s)
+        t.append(time.perf_counter() - t0)
+    per_full = float(np.mean(t)) * w["K"] / K_s
+    value = 1.0 / per_full
+    sample = f"first {K_s} of {w['K']} time steps (direct + adjoint), scaled by {K_s}/{w['K']}"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "gradient evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["label"]},
+            "cpu_baseline": {"value": value, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "gradient evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        line = run_reference(args, w, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = run_ours(args, w, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

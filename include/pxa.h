@@ -1,0 +1,173 @@
+/*
+ * pxa.h — C ABI of libpxa, Paraexp direct-adjoint gradients on one GB300 (sm_103a).
+ *
+ * Method: Skene, Eggl & Schmid, "A parallel-in-time approach for accelerating
+ * direct-adjoint studies" (arXiv 2004.00546). The time window [0, T] is split into
+ * P subintervals (Alg. 1, equal partition T_p = p T / P). The zero-initial-value
+ * inhomogeneous subproblems of every subinterval (Eq. linInhomEqus, Eq. adjInhom,
+ * Eq. hybadjinhom) are time-stepped concurrently, one CUDA thread block per
+ * subinterval ("lane"). The homogeneous problems (Eq. hom, Eq. adjHomNormal) are
+ * propagated by Krylov matrix-exponential actions (Sec. 4.1, Saad 1992); by
+ * linearity the problems active on one subinterval are carried as their sum. The
+ * full solution is the superposition of Eq. fullsol0 / Eq. fulladjsol, and the
+ * gradient follows from Eq. initupdate (initial-condition control) or
+ * Eq. paramupdate (forcing control).
+ *
+ * Problems (Sec. 4.2, 4.3, restricted to what this library implements):
+ *   PXA_ADVDIFF_1D: dq/dt = A q,  (A q)_i = -c (q_{i+1}-q_{i-1})/(2h)
+ *                                  + nu (q_{i+1}-2 q_i+q_{i-1})/h^2,  periodic,
+ *                   x_i = i h, h = L/n; Crank–Nicolson stepping; control = q(0);
+ *                   objective J = 0.5 ||q(T)||^2.
+ *   PXA_BURGERS_1D: du/dt = -u du/dx + nu d2u/dx2 + s(t) f(x), u(0) = 0, central
+ *                   differences, periodic; classical RK4; control = f;
+ *                   s(t) = sin(omega t) (omega != 0) or 1; objective
+ *                   J = (1/T) sum_{j=1..K} dt ||u_j - g||^2 (rectangle rule of
+ *                   Eq. cost). The direct problem is solved in series and the
+ *                   adjoint in parallel (hybrid scheme, Sec. 3.3); its homogeneous
+ *                   parts use 4th-order Magnus steps with Krylov exponentials.
+ *
+ * Conventions:
+ *   - Every call returns a pxa_status (0 = PXA_OK). No call aborts, traps or
+ *     throws. Errors raised inside kernels are written to a device status word and
+ *     reported by the next call that synchronises (pxa_gradient, pxa_sync).
+ *   - Device pointers ("_dev") are caller-owned, borrowed for the duration of the
+ *     call (or, for pxa_set_control / pxa_set_objective, until the next set_* call
+ *     or pxa_destroy) and never freed by the library. Host pointers ("_host") are
+ *     read or written before the call returns.
+ *   - All vectors are FP64, contiguous, n elements (the grid points in order).
+ *   - The library owns its workspace. It is (re)allocated by the first solve after
+ *     a set_* call; later solves allocate nothing.
+ *   - All work is enqueued on the stream given to pxa_create (a cudaStream_t,
+ *     borrowed; NULL = the legacy default stream).
+ *   - Not thread-safe per context: one host thread at a time per pxa_ctx.
+ */
+#ifndef PXA_H
+#define PXA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pxa_ctx pxa_ctx;
+
+typedef enum {
+  PXA_OK = 0,
+  PXA_ERR_INVALID = -1,        /* bad argument or unsupported combination */
+  PXA_ERR_CUDA = -2,           /* a CUDA runtime call failed (see pxa_last_error) */
+  PXA_ERR_OOM = -3,            /* workspace allocation failed */
+  PXA_ERR_NOT_CONVERGED = -4,  /* a Krylov error estimate exceeded the tolerance */
+  PXA_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
+  PXA_ERR_NONFINITE = -6,      /* J or the gradient is not finite */
+  PXA_ERR_STATE = -7           /* call made before the context was configured */
+} pxa_status;
+
+typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2 } pxa_problem;
+typedef enum { PXA_CN = 1, PXA_RK4 = 2 } pxa_stepper;
+/* Homogeneous propagator. EXP: exp(t A) (the paper's choice). STEPPER: the stepper's
+ * own amplification R(dt A)^k (R_CN(z) = (1+z/2)/(1-z/2)), which makes Paraexp
+ * reproduce serial stepping up to the Krylov tolerance. */
+typedef enum { PXA_PHI_EXP = 0, PXA_PHI_STEPPER = 1 } pxa_phi;
+/* SERIAL: one lane over [0, T] (plain serial stepping, same kernels).
+ * PARAEXP: P lanes + homogeneous propagation + superposition. */
+typedef enum { PXA_SERIAL = 0, PXA_PARAEXP = 1 } pxa_mode;
+/* Direct-state storage for the time-varying adjoint (Sec. 3.5): FULL keeps every
+ * step in HBM; CHECKPOINTS keeps the P+1 subinterval boundaries and recomputes each
+ * subinterval inside its adjoint lane. */
+typedef enum { PXA_STORE_FULL = 0, PXA_STORE_CHECKPOINTS = 1 } pxa_memory;
+
+typedef struct {
+  int kind;   /* pxa_problem */
+  int n;      /* grid points, 3 <= n <= 4096 */
+  double L;   /* domain length (> 0), h = L / n */
+  double c;   /* advection speed (PXA_ADVDIFF_1D) */
+  double nu;  /* diffusion coefficient (>= 0) */
+} pxa_operator_desc;
+
+typedef struct {
+  double J;                 /* objective of the last gradient */
+  double krylov_err_max;    /* largest a-posteriori Krylov error estimate (relative) */
+  int krylov_m;             /* Krylov dimension in use */
+  int krylov_substeps;      /* Krylov substeps per subinterval in use */
+  int magnus_steps;         /* RK4 steps per Magnus step (Burgers) */
+  int lanes;                /* lanes of the last solve */
+  int64_t workspace_bytes;  /* device workspace owned by the context */
+  float ms_direct_inhom;    /* phase times of the last pxa_gradient with timing on */
+  float ms_direct_hom;
+  float ms_adjoint_inhom;
+  float ms_adjoint_hom;
+  float ms_total;
+} pxa_stats;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (borrowed; NULL = default stream). *out receives the context. */
+int pxa_create(pxa_ctx** out, int device, void* cuda_stream);
+/* Release the context and its workspace. NULL is ignored. */
+void pxa_destroy(pxa_ctx* ctx);
+/* Text of the last error raised on this context ("" if none). Never NULL. */
+const char* pxa_last_error(const pxa_ctx* ctx);
+
+/* Operator and grid (Sec. 4.2 / 4.3). Invalidates the workspace. */
+int pxa_set_operator(pxa_ctx* ctx, const pxa_operator_desc* op);
+/* Time window [0, T], K steps of `stepper` (PXA_CN for ADVDIFF_1D, PXA_RK4 for
+ * BURGERS_1D), P equal subintervals (Alg. 1). K % P == 0 is required. */
+int pxa_set_time(pxa_ctx* ctx, double T, int64_t K, int stepper, int P);
+/* Krylov dimension m (2 <= m <= 48), tolerance on the a-posteriori estimate
+ * (relative to ||v||), homogeneous propagator (pxa_phi) and the number of Krylov
+ * substeps per subinterval (>= 1; each substep spans K/(P*substeps) steps, which
+ * must be an integer). */
+int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
+/* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
+int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);
+/* Control (Eq. initupdate / paramupdate): ADVDIFF_1D: q0_dev = initial condition.
+ * BURGERS_1D: f_dev = forcing, s(t) = sin(omega t) or 1 when omega == 0. */
+int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
+/* Tracking target g (BURGERS_1D). */
+int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
+/* Direct-state storage policy (pxa_memory). */
+int pxa_set_memory(pxa_ctx* ctx, int policy);
+/* Capture the whole gradient into a CUDA graph and replay it (1) or launch kernels
+ * one by one (0, default). */
+int pxa_set_graph(pxa_ctx* ctx, int enable);
+
+/* One direct-adjoint loop: J into *J_host (may be NULL), dJ/d(control) into
+ * grad_dev (n doubles, caller-owned). Synchronises the stream; returns device-side
+ * errors (NOT_CONVERGED, NONFINITE). */
+int pxa_gradient(pxa_ctx* ctx, int mode, double* J_host, double* grad_dev);
+/* Same, asynchronous: J is written to J_dev (one double, device). Errors raised
+ * inside kernels surface at the next pxa_sync. Graph-capturable once the workspace
+ * exists (after one pxa_gradient). */
+int pxa_gradient_async(pxa_ctx* ctx, int mode, double* J_dev, double* grad_dev);
+/* Wait for the stream and report device-side errors. */
+int pxa_sync(pxa_ctx* ctx);
+/* End-to-end call with host buffers: copies control_host (n doubles) to the device,
+ * runs pxa_gradient and copies the gradient back into grad_host (n doubles). */
+int pxa_gradient_host(pxa_ctx* ctx, int mode, const double* control_host, double* J_host,
+                      double* grad_host);
+/* Statistics of the last solve. */
+int pxa_get_stats(const pxa_ctx* ctx, pxa_stats* out);
+/* Per-phase CUDA-event timing inside pxa_gradient (0 = off, default). */
+int pxa_set_timing(pxa_ctx* ctx, int enable);
+
+/* ---- building blocks, exposed for kernel-level tests --------------------------
+ * y = A x (transpose = 0) or A^T x (transpose = 1) for ADVDIFF_1D. */
+int pxa_apply_operator(pxa_ctx* ctx, int transpose, const double* x_dev, double* y_dev);
+/* y = M^steps x for the configured stepper (ADVDIFF_1D: the CN map
+ * M = (I - dt/2 A)^{-1} (I + dt/2 A), dt = T/K), or (M^T)^steps x. One thread block. */
+int pxa_step(pxa_ctx* ctx, int transpose, int64_t steps, const double* x_dev, double* y_dev);
+/* y = phi(A) x over `substeps` Krylov substeps spanning `span_steps` time steps
+ * (ADVDIFF_1D; phi from pxa_set_krylov). err_host (may be NULL) receives the
+ * largest relative error estimate. */
+int pxa_expv(pxa_ctx* ctx, int transpose, int64_t span_steps, int substeps,
+             const double* x_dev, double* y_dev, double* err_host);
+/* Burgers building blocks on the configured grid: y = N(u) (rhs, no forcing),
+ * y = J(u)^T x (transposed Jacobian). */
+int pxa_burgers_rhs(pxa_ctx* ctx, const double* u_dev, double* y_dev);
+int pxa_burgers_jac_T(pxa_ctx* ctx, const double* u_dev, const double* x_dev, double* y_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PXA_H */

@@ -1,0 +1,61 @@
+// kernels_1d.cuh — host-side launch wrappers of the 1D kernels (kernels_1d.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pxa {
+
+struct Bu1Grid {
+  int n;
+  double inv2h, invh2, nu;
+};
+
+size_t krylov_smem_bytes(int n, int m, int extra_vecs, bool v_in_smem);
+
+cudaError_t launch_cn_lanes(cudaStream_t st, int lanes, int threads, int n, int r,
+                            const double* taps, int transpose, int64_t steps, const double* x0,
+                            const double* src, double* out);
+cudaError_t launch_band_minus_identity(cudaStream_t st, int n, int r, const double* taps,
+                                       int transpose, const double* x, double* y);
+cudaError_t launch_ad1_apply(cudaStream_t st, int n, double am, double a0, double ap,
+                             int transpose, const double* x, double* y);
+cudaError_t launch_ad1_chain(cudaStream_t st, int threads, int n, double am, double a0, double ap,
+                             int transpose, const double* E, int first, int stride, int count,
+                             double* hout, double* Vglob, int m, int phi_mode, double hscale,
+                             int64_t steps_per_sub, int nsub, double tol, int v_in_smem,
+                             int* status, double* errmax);
+cudaError_t launch_ad1_expv(cudaStream_t st, int threads, int n, double am, double a0, double ap,
+                            int transpose, const double* x, double* y, double* Vglob, int m,
+                            int phi_mode, double hscale, int64_t steps_per_sub, int nsub,
+                            double tol, int v_in_smem, int* status, double* errmax);
+cudaError_t launch_ad1_superpose_direct(cudaStream_t st, int threads, int n, int r,
+                                        const double* taps, const double* q0, const double* elast,
+                                        const double* hsum, double* qT, double* srcT, double* J,
+                                        int* status);
+cudaError_t launch_ad1_superpose_adjoint(cudaStream_t st, int n, const double* lamK,
+                                         const double* e0, const double* hsum, double* grad,
+                                         int* status);
+cudaError_t launch_bu1_direct(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
+                              int64_t K, double omega, const double* f, const double* gt,
+                              const double* u0, double* traj, double* ckpt, int64_t ck_every,
+                              double* J, int* status);
+cudaError_t launch_bu1_adjoint_lanes(cudaStream_t st, int lanes, int threads, Bu1Grid g,
+                                     double dt, double T, int64_t k, double omega,
+                                     const double* f, const double* gt, const double* traj,
+                                     const double* ckpt, double* scratch, double* wout,
+                                     double* gout, int* status);
+cudaError_t launch_bu1_magnus_chain(cudaStream_t st, int threads, Bu1Grid g, double dt, int64_t K,
+                                    int P, int64_t k, int M, double omega, const double* traj,
+                                    int64_t lane_k, const double* W, double* gH, double* Vglob, int m, double tol,
+                                    int v_in_smem, int* status, double* errmax);
+cudaError_t launch_bu1_stepper_chain(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
+                                     int64_t k, int P, double omega, const double* f,
+                                     const double* gt, const double* rows, int64_t lane_k,
+                                     const double* W, double* gH);
+cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
+                             double* grad, int* status);
+cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);
+cudaError_t launch_bu1_jacT(cudaStream_t st, Bu1Grid g, const double* U, const double* x, double* y);
+
+}  // namespace pxa

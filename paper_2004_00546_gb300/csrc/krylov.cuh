@@ -1,0 +1,154 @@
+// krylov.cuh — one-thread-block Arnoldi process and Krylov matrix functions
+// (Sec. 4.1: exp(B) v ~ V_m exp(H_m) V_m^T v, Saad 1992).
+//
+// The Krylov basis V (m+1 vectors of length n, leading dimension ldv) lives in
+// shared memory when it fits, otherwise in global memory (L2-resident); the code
+// is the same through generic pointers. Orthogonalisation is classical
+// Gram–Schmidt applied twice (CGS2): the j+1 dot products of one pass are
+// independent, so each warp takes a subset of them and reduces with shuffles.
+#pragma once
+#include "common.cuh"
+
+namespace pxa {
+
+// Shared scratch that one Krylov solve needs (all in shared memory).
+struct KrylovScratch {
+  double* H;     // (kMaxM+1) x kLD Hessenberg
+  double* D0;    // kLD x kLD dense scratch
+  double* D1;
+  double* D2;
+  double* D3;
+  double* hcol;  // kDMax doubles
+  double* red;   // 40 doubles
+  int* ipiv;
+  int* flag;
+};
+
+// All threads: dots[i] = <V_i, w> for i = 0..cnt-1 (warp-per-dot). Ends with a barrier.
+__device__ __forceinline__ void multi_dot(const double* V, int ldv, int cnt, const double* w,
+                                          int n, double* dots) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < cnt; i += nw) {
+    const double* vi = V + (size_t)i * ldv;
+    double s = 0.0;
+    for (int p = lane; p < n; p += 32) s = fma(vi[p], w[p], s);
+    s = warp_sum(s);
+    if (lane == 0) dots[i] = s;
+  }
+  __syncthreads();
+}
+
+// w -= sum_i c[i] V_i (threads over points). Ends with a barrier.
+__device__ __forceinline__ void multi_axpy(const double* V, int ldv, int cnt, const double* c,
+                                           double* w, int n) {
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    double acc = w[p];
+    for (int i = 0; i < cnt; ++i) acc = fma(-c[i], V[(size_t)i * ldv + p], acc);
+    w[p] = acc;
+  }
+  __syncthreads();
+}
+
+// Arnoldi with CGS2 on the block-cooperative operator `op` (op.apply(x, y) writes
+// y = Op x and ends with a barrier). V_0 = v / ||v||. Returns beta = ||v||; *mm_out
+// receives the dimension reached (< m after a happy breakdown, when the Krylov
+// space is invariant), H(0..mm, 0..mm-1) is filled. If beta == 0, mm = 0.
+template <class Op>
+__device__ double arnoldi(Op& op, const double* v, int n, int m, double* V, int ldv,
+                          KrylovScratch& ks, int* mm_out) {
+  double ss = 0.0;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) ss = fma(v[p], v[p], ss);
+  double beta = sqrt(block_sum(ss, ks.red));
+  for (int e = threadIdx.x; e < (kMaxM + 1) * kLD; e += blockDim.x) ks.H[e] = 0.0;
+  if (beta == 0.0) {
+    __syncthreads();
+    *mm_out = 0;
+    return 0.0;
+  }
+  const double inv = 1.0 / beta;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) V[p] = v[p] * inv;
+  __syncthreads();
+  int mm = m;
+  for (int j = 0; j < m; ++j) {
+    double* w = V + (size_t)(j + 1) * ldv;
+    op.apply(V + (size_t)j * ldv, w);
+    // first Gram–Schmidt pass
+    multi_dot(V, ldv, j + 1, w, n, ks.hcol);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) ks.H[i * kLD + j] = ks.hcol[i];
+    multi_axpy(V, ldv, j + 1, ks.hcol, w, n);
+    // second pass (re-orthogonalisation)
+    multi_dot(V, ldv, j + 1, w, n, ks.hcol);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) ks.H[i * kLD + j] += ks.hcol[i];
+    multi_axpy(V, ldv, j + 1, ks.hcol, w, n);
+    double s2 = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) s2 = fma(w[p], w[p], s2);
+    double hn = sqrt(block_sum(s2, ks.red));
+    if (threadIdx.x == 0) ks.H[(j + 1) * kLD + j] = hn;
+    if (hn <= 1e-14 * beta) {  // happy breakdown: exact in the space built so far
+      mm = j + 1;
+      __syncthreads();
+      break;
+    }
+    const double ih = 1.0 / hn;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) w[p] *= ih;
+    __syncthreads();
+  }
+  *mm_out = mm;
+  return beta;
+}
+
+// y = beta * V_mm * c (c in shared memory, mm entries). Ends with a barrier.
+__device__ __forceinline__ void krylov_combine(const double* V, int ldv, int mm, const double* c,
+                                               double beta, double* y, int n) {
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < mm; ++i) acc = fma(c[i], V[(size_t)i * ldv + p], acc);
+    y[p] = beta * acc;
+  }
+  __syncthreads();
+}
+
+// Homogeneous propagator on the Krylov space.
+//   phi_mode 0 (EXP):      F = exp(H)            (H already carries the time span)
+//   phi_mode 1 (CN power): F = [(I - H/2)^{-1} (I + H/2)]^steps
+// with H = dt * H_m for the stepper modes. Writes the first column of F to c[0..mm)
+// and returns |F[mm-1][0]| for Saad's a-posteriori estimate beta*h_{mm+1,mm}*|F[mm-1][0]|.
+// `want_phi1`: also writes phi_1(H) e_1 to c1 (EXP only), through the augmented
+// matrix [[H, e_1], [0, 0]] whose exponential holds phi_1(H) e_1 in its last column.
+__device__ inline double hessenberg_phi(KrylovScratch& ks, int mm, int phi_mode, double hscale,
+                                        int64_t steps, bool want_phi1, double* c, double* c1) {
+  const int d = (phi_mode == 0 && want_phi1) ? mm + 1 : mm;
+  // D0 = hscale * H_mm (padded)
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    int i = e / d, j = e % d;
+    double v = 0.0;
+    if (i < mm && j < mm) v = hscale * ks.H[i * kLD + j];
+    if (want_phi1 && phi_mode == 0 && j == mm && i == 0) v = 1.0;
+    ks.D0[i * kLD + j] = v;
+  }
+  __syncthreads();
+  if (phi_mode == 0) {
+    dense_expm(ks.D1, ks.D0, ks.D2, ks.D3, d, ks.red);  // D1 = exp(D0)
+  } else {
+    // R = (I - Z/2)^{-1} (I + Z/2): A = I - Z/2 in D2, B = I + Z/2 in D1
+    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+      int i = e / d, j = e % d;
+      double z = 0.5 * ks.D0[i * kLD + j];
+      ks.D2[i * kLD + j] = (i == j ? 1.0 : 0.0) - z;
+      ks.D1[i * kLD + j] = (i == j ? 1.0 : 0.0) + z;
+    }
+    __syncthreads();
+    dense_solve(ks.D2, ks.D1, d, ks.hcol, ks.ipiv);  // D1 = R
+    dense_copy(ks.D0, ks.D1, d);
+    __syncthreads();
+    dense_pow(ks.D1, ks.D0, ks.D2, d, steps);  // D1 = R^steps
+  }
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+    c[i] = ks.D1[i * kLD + 0];
+    if (want_phi1 && phi_mode == 0) c1[i] = ks.D1[i * kLD + mm];
+  }
+  __syncthreads();
+  return fabs(ks.D1[(mm - 1) * kLD + 0]);
+}
+
+}  // namespace pxa

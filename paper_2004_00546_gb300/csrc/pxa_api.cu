@@ -1,0 +1,666 @@
+// pxa_api.cu — the C ABI of libpxa (declared in include/pxa.h): context, workspace,
+// orchestration of the Paraexp direct-adjoint loop on one stream, CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pxa.h"
+#include "kernels_1d.cuh"
+
+using namespace pxa;
+
+struct pxa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;       // the caller's stream (borrowed)
+  cudaStream_t cap_stream = nullptr;   // library-owned stream used to capture graphs
+  std::string err;
+
+  // configuration
+  bool have_op = false, have_time = false;
+  pxa_operator_desc op{};
+  double T = 0.0;
+  int64_t K = 0;
+  int stepper = 0, P = 1;
+  int kry_m = 30, kry_phi = PXA_PHI_STEPPER, kry_sub = 1;
+  double kry_tol = 1e-11;
+  int magnus_M = 25;
+  const double* control = nullptr;
+  double omega = 0.0;
+  const double* target = nullptr;
+  int memory = PXA_STORE_FULL;
+  bool use_graph = false, timing = false;
+
+  // derived
+  double am = 0, a0 = 0, ap = 0;  // advection-diffusion stencil
+  int band_r = 0;
+  std::vector<double> band_host;
+
+  // workspace (device)
+  bool ready = false;
+  std::vector<void*> allocs;
+  int64_t ws_bytes = 0;
+  double* taps = nullptr;     // 2r+1
+  double* E = nullptr;        // [P][n] lane outputs (direct / Burgers W)
+  double* EA = nullptr;       // [P][n] adjoint lane outputs (Burgers G)
+  double* src = nullptr;      // n
+  double* srcA = nullptr;     // n
+  double* hsum = nullptr;     // n
+  double* hsumA = nullptr;    // n
+  double* qT = nullptr;       // n
+  double* tmp = nullptr;      // n
+  double* V = nullptr;        // Krylov basis (global fallback)
+  double* traj = nullptr;     // Burgers direct trajectory (K+1)*n or checkpoints
+  double* scratch = nullptr;  // Burgers recompute rows
+  double* Jdev = nullptr;     // 1
+  double* errmax = nullptr;   // 1
+  int* status = nullptr;      // 1
+  double* ctl_buf = nullptr;  // n (pxa_gradient_host)
+  double* grad_buf = nullptr; // n (pxa_gradient_host)
+  bool v_in_smem = false;
+
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  int g_mode = -1;
+  const double* g_grad = nullptr;
+  const double* g_J = nullptr;
+
+  // statistics
+  pxa_stats stats{};
+  cudaEvent_t ev[6] = {};
+  bool ev_ready = false;
+};
+
+namespace {
+
+int fail(pxa_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(pxa_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PXA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PXA_CUDA(c, expr, where)               \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+  } while (0)
+
+void release_workspace(pxa_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->ws_bytes = 0;
+  c->ready = false;
+  c->taps = c->E = c->EA = c->src = c->srcA = c->hsum = c->hsumA = c->qT = c->tmp = nullptr;
+  c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
+  c->status = nullptr;
+}
+
+void invalidate(pxa_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->g_mode = -1;
+}
+
+template <typename T>
+int alloc(pxa_ctx* c, T** out, size_t count) {
+  void* p = nullptr;
+  size_t bytes = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PXA_ERR_OOM, std::string("workspace allocation of ") + std::to_string(bytes) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(p);
+  c->ws_bytes += (int64_t)bytes;
+  *out = static_cast<T*>(p);
+  return PXA_OK;
+}
+
+// Taps m_j (|j| <= r) of the circulant Crank–Nicolson map
+//   M = (I - dt/2 A)^{-1} (I + dt/2 A),  (M x)_i = sum_j m_j x_{i+j},
+// from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
+// by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj} in long double. The taps decay
+// geometrically (the implicit matrix is diagonally dominant); the band stops where
+// both |m_r| and |m_-r| fall below 2^-72 |m_0|, far under FP64 rounding of the step.
+int cn_band(pxa_ctx* c, int n, double am, double a0, double ap, double dt,
+            std::vector<double>& taps, int& r) {
+  typedef std::complex<long double> C;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<C> R(n), w(n);
+  for (int k = 0; k < n; ++k) {
+    long double ph = 2.0L * pi * (long double)k / (long double)n;
+    w[k] = C(cosl(ph), sinl(ph));
+  }
+  const long double th = 0.5L * (long double)dt;
+  for (int k = 0; k < n; ++k) {
+    C lam = (long double)a0 + (long double)am * std::conj(w[k]) + (long double)ap * w[k];
+    R[k] = (1.0L + th * lam) / (1.0L - th * lam);
+  }
+  auto tap = [&](int j) {
+    C s = 0.0L;
+    for (int k = 0; k < n; ++k) {
+      long long idx = ((long long)k * (long long)(((j % n) + n) % n)) % n;
+      s += R[k] * std::conj(w[idx]);
+    }
+    return (double)(s.real() / (long double)n);
+  };
+  std::vector<double> pos, neg;  // pos[j] = m_j, neg[j] = m_-j
+  double m0 = tap(0);
+  pos.push_back(m0);
+  neg.push_back(m0);
+  const double thr = std::ldexp(std::fabs(m0), -72);
+  int rmax = (n - 1) / 2;
+  r = 0;
+  for (int j = 1; j <= rmax; ++j) {
+    double mp = tap(j), mn = tap(-j);
+    pos.push_back(mp);
+    neg.push_back(mn);
+    r = j;
+    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;
+    if (j == rmax)
+      return fail(c, PXA_ERR_INVALID,
+                  "Crank-Nicolson map is not banded at this dt/h (taps do not decay within n/2)");
+  }
+  taps.assign(2 * r + 1, 0.0);
+  for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
+  return PXA_OK;
+}
+
+int threads_for(int n) {
+  int t = ((n + 31) / 32) * 32;
+  return t > 1024 ? 1024 : (t < 64 ? 64 : t);
+}
+
+int prepare(pxa_ctx* c) {
+  if (c->ready) return PXA_OK;
+  if (!c->have_op || !c->have_time) return fail(c, PXA_ERR_STATE, "set_operator and set_time first");
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  release_workspace(c);
+  const int n = c->op.n, P = c->P;
+  int rc;
+  if ((rc = alloc(c, &c->Jdev, 1))) return rc;
+  if ((rc = alloc(c, &c->errmax, 1))) return rc;
+  if ((rc = alloc(c, &c->status, 1))) return rc;
+  if ((rc = alloc(c, &c->E, (size_t)P * n))) return rc;
+  if ((rc = alloc(c, &c->EA, (size_t)P * n))) return rc;
+  if ((rc = alloc(c, &c->src, n))) return rc;
+  if ((rc = alloc(c, &c->srcA, n))) return rc;
+  if ((rc = alloc(c, &c->hsum, n))) return rc;
+  if ((rc = alloc(c, &c->hsumA, n))) return rc;
+  if ((rc = alloc(c, &c->qT, n))) return rc;
+  if ((rc = alloc(c, &c->tmp, n))) return rc;
+  if ((rc = alloc(c, &c->ctl_buf, n))) return rc;
+  if ((rc = alloc(c, &c->grad_buf, n))) return rc;
+  // Krylov basis: in shared memory when it fits beside the dense scratch
+  int extra = c->op.kind == PXA_ADVDIFF_1D ? n : 5 * (n + 2) + n;
+  size_t with_v = krylov_smem_bytes(n, c->kry_m, extra, true);
+  c->v_in_smem = with_v <= 200 * 1024;
+  if ((rc = alloc(c, &c->V, (size_t)(c->kry_m + 1) * n))) return rc;
+  if (c->op.kind == PXA_ADVDIFF_1D) {
+    double dt = c->T / (double)c->K;
+    if ((rc = cn_band(c, n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r))) return rc;
+    if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
+    PXA_CUDA(c, cudaMemcpy(c->taps, c->band_host.data(), sizeof(double) * c->band_host.size(),
+                           cudaMemcpyHostToDevice), "copy taps");
+  } else {
+    int64_t k = c->K / P;
+    if (c->memory == PXA_STORE_FULL) {
+      if ((rc = alloc(c, &c->traj, (size_t)(c->K + 1) * n))) return rc;
+    } else {
+      if ((rc = alloc(c, &c->traj, (size_t)(P + 1) * n))) return rc;
+      if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
+    }
+  }
+  PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "memset status");
+  c->stats.workspace_bytes = c->ws_bytes;
+  c->ready = true;
+  return PXA_OK;
+}
+
+void ev_record(pxa_ctx* c, int i) {
+  if (c->timing && c->ev_ready) cudaEventRecord(c->ev[i], c->stream);
+}
+
+// ---- 1D advection-diffusion (IC control, terminal objective) ----------------
+int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+  cudaStream_t st = c->stream;
+  const int n = c->op.n, P = c->P, r = c->band_r, th = threads_for(n);
+  const int64_t K = c->K;
+  const double dt = c->T / (double)K;
+  const double* q0 = c->control;
+  if (mode == PXA_SERIAL) {
+    ev_record(c, 0);
+    PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 0, K, q0, nullptr, c->E), "cn serial");
+    ev_record(c, 1);
+    ev_record(c, 2);
+    PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, nullptr, c->E, nullptr, c->qT,
+                                            nullptr, Jdev, c->status), "superpose");
+    PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 1, K, c->qT, nullptr, c->EA), "cn serial T");
+    ev_record(c, 3);
+    ev_record(c, 4);
+    PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, nullptr, c->EA, nullptr, grad, c->status), "grad");
+    ev_record(c, 5);
+    return PXA_OK;
+  }
+  const int64_t k = K / P;
+  const int nsub = c->kry_sub;
+  const int64_t steps_sub = k / nsub;
+  const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)steps_sub : dt;
+  const int kth = 256;
+  PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
+  ev_record(c, 0);
+  // Eq. linzero: the shifted problem has zero IC and source A q0; in CN form the
+  // lane recursion is q~' = M q~ + (M - I) q0.
+  PXA_CUDA(c, launch_band_minus_identity(st, n, r, c->taps, 0, q0, c->src), "src");
+  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 0, k, nullptr, c->src, c->E), "lanes");
+  ev_record(c, 1);
+  if (P > 1) {
+    PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
+                                 c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub, c->kry_tol,
+                                 c->v_in_smem, c->status, c->errmax), "chain");
+  }
+  ev_record(c, 2);
+  PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, q0, c->E + (size_t)(P - 1) * n,
+                                          P > 1 ? c->hsum : nullptr, c->qT, c->srcA, Jdev,
+                                          c->status), "superpose");
+  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 1, k, nullptr, c->srcA, c->EA), "adj lanes");
+  ev_record(c, 3);
+  if (P > 1) {
+    PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1,
+                                 c->hsumA, c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub,
+                                 c->kry_tol, c->v_in_smem, c->status, c->errmax), "adj chain");
+  }
+  ev_record(c, 4);
+  PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, c->qT, c->EA, P > 1 ? c->hsumA : nullptr, grad,
+                                           c->status), "grad");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
+// ---- 1D Burgers (forcing control, tracking objective), hybrid scheme ----------
+int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+  cudaStream_t st = c->stream;
+  const int n = c->op.n, th = threads_for(n);
+  const int64_t K = c->K;
+  const double dt = c->T / (double)K;
+  const double h = c->op.L / n;
+  Bu1Grid g{n, 1.0 / (2.0 * h), 1.0 / (h * h), c->op.nu};
+  const int P = mode == PXA_SERIAL ? 1 : c->P;
+  const int64_t k = K / P;
+  const bool full = c->memory == PXA_STORE_FULL;
+  PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
+  ev_record(c, 0);
+  if (full) {
+    PXA_CUDA(c, launch_bu1_direct(st, th, g, dt, c->T, K, c->omega, c->control, c->target, nullptr,
+                                  c->traj, nullptr, 1, Jdev, c->status), "direct");
+  } else {
+    // checkpoints at the boundaries of the lanes of this mode (P+1 rows; 2 rows serial)
+    PXA_CUDA(c, launch_bu1_direct(st, th, g, dt, c->T, K, c->omega, c->control, c->target, nullptr,
+                                  nullptr, c->traj, k, Jdev, c->status), "direct");
+  }
+  ev_record(c, 1);
+  ev_record(c, 2);
+  const int ath = n > 2048 ? 1024 : (threads_for(n) > 512 ? 512 : threads_for(n));
+  PXA_CUDA(c, launch_bu1_adjoint_lanes(st, P, ath, g, dt, c->T, k, c->omega, c->control, c->target,
+                                       full ? c->traj : nullptr, full ? nullptr : c->traj,
+                                       c->scratch, c->E, c->EA, c->status), "adjoint lanes");
+  ev_record(c, 3);
+  if (P > 1 && c->kry_phi == PXA_PHI_STEPPER) {
+    PXA_CUDA(c, launch_bu1_stepper_chain(st, ath, g, dt, c->T, k, P, c->omega, c->control, c->target,
+                                         full ? c->traj : c->scratch, full ? 0 : k, c->E, c->hsum),
+             "stepper chain");
+  } else if (P > 1) {
+    PXA_CUDA(c, launch_bu1_magnus_chain(st, n > 2048 ? 1024 : 512, g, dt, K, P, k, c->magnus_M, c->omega,
+                                        full ? c->traj : c->scratch, full ? 0 : k, c->E, c->hsum, c->V, c->kry_m, c->kry_tol, c->v_in_smem,
+                                        c->status, c->errmax), "magnus chain");
+  }
+  ev_record(c, 4);
+  PXA_CUDA(c, launch_sum_lanes(st, n, P, c->EA, P > 1 ? c->hsum : nullptr, grad, c->status), "sum");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
+int enqueue(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+  if (mode != PXA_SERIAL && mode != PXA_PARAEXP) return fail(c, PXA_ERR_INVALID, "mode");
+  if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first");
+  if (c->op.kind == PXA_BURGERS_1D && !c->target) return fail(c, PXA_ERR_STATE, "set_target first");
+  if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, Jdev, grad);
+  return enqueue_bu1(c, mode, Jdev, grad);
+}
+
+int read_status(pxa_ctx* c) {
+  int st = 0;
+  double em = 0.0;
+  PXA_CUDA(c, cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  PXA_CUDA(c, cudaMemcpy(&em, c->errmax, sizeof(double), cudaMemcpyDeviceToHost), "read errmax");
+  c->stats.krylov_err_max = em;
+  if (st != 0) {
+    PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "reset status");
+    if (st == PXA_ERR_NOT_CONVERGED)
+      return fail(c, st, "Krylov error estimate above tolerance (increase m or substeps)");
+    if (st == PXA_ERR_NONFINITE) return fail(c, st, "objective or gradient is not finite");
+    return fail(c, st, "device error status " + std::to_string(st));
+  }
+  return PXA_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int pxa_create(pxa_ctx** out, int device, void* cuda_stream) {
+  if (!out) return PXA_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return PXA_ERR_CUDA;
+  }
+  pxa_ctx* c = new pxa_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return PXA_OK;
+}
+
+void pxa_destroy(pxa_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  release_workspace(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_ready)
+    for (auto& e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* pxa_last_error(const pxa_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pxa_set_operator(pxa_ctx* c, const pxa_operator_desc* op) {
+  if (!c || !op) return PXA_ERR_INVALID;
+  if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D)
+    return fail(c, PXA_ERR_INVALID, "operator kind");
+  if (op->n < 3 || op->n > 4096 || !(op->L > 0.0) || !(op->nu >= 0.0))
+    return fail(c, PXA_ERR_INVALID, "operator parameters (3 <= n <= 4096, L > 0, nu >= 0)");
+  c->op = *op;
+  double h = op->L / op->n;
+  c->am = op->c / (2.0 * h) + op->nu / (h * h);
+  c->a0 = -2.0 * op->nu / (h * h);
+  c->ap = -op->c / (2.0 * h) + op->nu / (h * h);
+  c->have_op = true;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_time(pxa_ctx* c, double T, int64_t K, int stepper, int P) {
+  if (!c) return PXA_ERR_INVALID;
+  if (!(T > 0.0) || K < 1 || P < 1 || K % P != 0) return fail(c, PXA_ERR_INVALID, "T > 0, K >= 1, P >= 1, K % P == 0");
+  if (!c->have_op) return fail(c, PXA_ERR_STATE, "set_operator first");
+  if (c->op.kind == PXA_ADVDIFF_1D && stepper != PXA_CN) return fail(c, PXA_ERR_INVALID, "ADVDIFF_1D uses PXA_CN");
+  if (c->op.kind == PXA_BURGERS_1D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "BURGERS_1D uses PXA_RK4");
+  if (c->op.kind == PXA_BURGERS_1D && K < 4) return fail(c, PXA_ERR_INVALID, "K >= 4 for time interpolation");
+  c->T = T;
+  c->K = K;
+  c->stepper = stepper;
+  c->P = P;
+  c->have_time = true;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_krylov(pxa_ctx* c, int m, double tol, int phi, int substeps) {
+  if (!c) return PXA_ERR_INVALID;
+  if (m < 2 || m > 48 || !(tol > 0.0) || (phi != PXA_PHI_EXP && phi != PXA_PHI_STEPPER) || substeps < 1)
+    return fail(c, PXA_ERR_INVALID, "krylov parameters (2 <= m <= 48, tol > 0, substeps >= 1)");
+  if (c->have_time && (c->K / c->P) % substeps != 0)
+    return fail(c, PXA_ERR_INVALID, "substeps must divide the steps of one subinterval");
+  c->kry_m = m;
+  c->kry_tol = tol;
+  c->kry_phi = phi;
+  c->kry_sub = substeps;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_magnus(pxa_ctx* c, int steps_per_magnus) {
+  if (!c) return PXA_ERR_INVALID;
+  if (steps_per_magnus < 1 || (c->have_time && (c->K / c->P) % steps_per_magnus != 0))
+    return fail(c, PXA_ERR_INVALID, "steps_per_magnus must divide the steps of one subinterval");
+  c->magnus_M = steps_per_magnus;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_control(pxa_ctx* c, const double* control_dev, double omega) {
+  if (!c || !control_dev) return PXA_ERR_INVALID;
+  c->control = control_dev;
+  c->omega = omega;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_target(pxa_ctx* c, const double* target_dev) {
+  if (!c || !target_dev) return PXA_ERR_INVALID;
+  c->target = target_dev;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_memory(pxa_ctx* c, int policy) {
+  if (!c || (policy != PXA_STORE_FULL && policy != PXA_STORE_CHECKPOINTS)) return PXA_ERR_INVALID;
+  c->memory = policy;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_graph(pxa_ctx* c, int enable) {
+  if (!c) return PXA_ERR_INVALID;
+  c->use_graph = enable != 0;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_timing(pxa_ctx* c, int enable) {
+  if (!c) return PXA_ERR_INVALID;
+  if (enable && !c->ev_ready) {
+    cudaSetDevice(c->device);
+    for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
+    c->ev_ready = true;
+  }
+  c->timing = enable != 0;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
+  if (!c || !grad_dev) return PXA_ERR_INVALID;
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  double* Jd = J_dev ? J_dev : c->Jdev;
+  c->stats.lanes = mode == PXA_SERIAL ? 1 : c->P;
+  c->stats.krylov_m = c->kry_m;
+  c->stats.krylov_substeps = c->kry_sub;
+  c->stats.magnus_steps = c->magnus_M;
+  if (c->use_graph && !c->timing) {
+    if (!c->gexec || c->g_mode != mode || c->g_grad != grad_dev || c->g_J != Jd) {
+      invalidate(c);
+      // Capture on a library-owned stream (the caller's may be the legacy default
+      // stream, which cannot be captured); the graph is then launched on the caller's.
+      if (!c->cap_stream)
+        PXA_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+      cudaGraph_t graph;
+      cudaStream_t user = c->stream;
+      c->stream = c->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) {
+        c->stream = user;
+        return cuda_fail(c, e, "begin capture");
+      }
+      int erc = enqueue(c, mode, Jd, grad_dev);
+      e = cudaStreamEndCapture(c->stream, &graph);
+      c->stream = user;
+      if (erc) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        return erc;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      c->g_mode = mode;
+      c->g_grad = grad_dev;
+      c->g_J = Jd;
+    }
+    PXA_CUDA(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    return PXA_OK;
+  }
+  return enqueue(c, mode, Jd, grad_dev);
+}
+
+int pxa_sync(pxa_ctx* c) {
+  if (!c) return PXA_ERR_INVALID;
+  if (!c->ready) return PXA_OK;
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  return read_status(c);
+}
+
+int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
+  if (!c || !grad_dev) return PXA_ERR_INVALID;
+  int rc = pxa_gradient_async(c, mode, nullptr, grad_dev);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  double J = 0.0;
+  PXA_CUDA(c, cudaMemcpy(&J, c->Jdev, sizeof(double), cudaMemcpyDeviceToHost), "read J");
+  c->stats.J = J;
+  if (J_host) *J_host = J;
+  if (c->timing && c->ev_ready) {
+    float a = 0, b = 0, d = 0, e = 0, t = 0;
+    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&e, c->ev[3], c->ev[4]);
+    cudaEventElapsedTime(&t, c->ev[0], c->ev[5]);
+    c->stats.ms_direct_inhom = a;
+    c->stats.ms_direct_hom = b;
+    c->stats.ms_adjoint_inhom = d;
+    c->stats.ms_adjoint_hom = e;
+    c->stats.ms_total = t;
+  }
+  return read_status(c);
+}
+
+int pxa_gradient_host(pxa_ctx* c, int mode, const double* control_host, double* J_host,
+                      double* grad_host) {
+  if (!c || !control_host || !grad_host) return PXA_ERR_INVALID;
+  int rc = prepare(c);
+  if (rc) return rc;
+  const int n = c->op.n;
+  const double* saved = c->control;
+  PXA_CUDA(c, cudaMemcpyAsync(c->ctl_buf, control_host, sizeof(double) * n, cudaMemcpyHostToDevice,
+                              c->stream), "H2D control");
+  if (saved != c->ctl_buf) {
+    c->control = c->ctl_buf;
+    invalidate(c);
+  }
+  rc = pxa_gradient(c, mode, J_host, c->grad_buf);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaMemcpyAsync(grad_host, c->grad_buf, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                              c->stream), "D2H grad");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  return PXA_OK;
+}
+
+int pxa_get_stats(const pxa_ctx* c, pxa_stats* out) {
+  if (!c || !out) return PXA_ERR_INVALID;
+  *out = c->stats;
+  return PXA_OK;
+}
+
+// ---- building blocks ----------------------------------------------------------
+int pxa_apply_operator(pxa_ctx* c, int transpose, const double* x_dev, double* y_dev) {
+  if (!c || !x_dev || !y_dev) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  PXA_CUDA(c, launch_ad1_apply(c->stream, c->op.n, c->am, c->a0, c->ap, transpose, x_dev, y_dev), "apply");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  return PXA_OK;
+}
+
+int pxa_step(pxa_ctx* c, int transpose, int64_t steps, const double* x_dev, double* y_dev) {
+  if (!c || !x_dev || !y_dev || steps < 0) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  int rc = prepare(c);
+  if (rc) return rc;
+  const int n = c->op.n;
+  PXA_CUDA(c, launch_cn_lanes(c->stream, 1, threads_for(n), n, c->band_r, c->taps, transpose, steps,
+                              x_dev, nullptr, y_dev), "step");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  return PXA_OK;
+}
+
+int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const double* x_dev,
+             double* y_dev, double* err_host) {
+  if (!c || !x_dev || !y_dev || span_steps < 1 || substeps < 1 || span_steps % substeps != 0)
+    return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  int rc = prepare(c);
+  if (rc) return rc;
+  const int n = c->op.n;
+  const double dt = c->T / (double)c->K;
+  const int64_t sps = span_steps / substeps;
+  const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)sps : dt;
+  PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), c->stream), "reset errmax");
+  PXA_CUDA(c, launch_ad1_expv(c->stream, 256, n, c->am, c->a0, c->ap, transpose, x_dev, y_dev, c->V,
+                              c->kry_m, c->kry_phi, hscale, sps, substeps, c->kry_tol, c->v_in_smem,
+                              c->status, c->errmax), "expv");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  rc = read_status(c);
+  if (err_host) *err_host = c->stats.krylov_err_max;
+  return rc;
+}
+
+int pxa_burgers_rhs(pxa_ctx* c, const double* u_dev, double* y_dev) {
+  if (!c || !u_dev || !y_dev) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_BURGERS_1D) return fail(c, PXA_ERR_STATE, "BURGERS_1D operator required");
+  const int n = c->op.n;
+  const double h = c->op.L / n;
+  Bu1Grid g{n, 1.0 / (2.0 * h), 1.0 / (h * h), c->op.nu};
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  PXA_CUDA(c, launch_bu1_rhs(c->stream, g, u_dev, y_dev), "rhs");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  return PXA_OK;
+}
+
+int pxa_burgers_jac_T(pxa_ctx* c, const double* u_dev, const double* x_dev, double* y_dev) {
+  if (!c || !u_dev || !x_dev || !y_dev) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_BURGERS_1D) return fail(c, PXA_ERR_STATE, "BURGERS_1D operator required");
+  const int n = c->op.n;
+  const double h = c->op.L / n;
+  Bu1Grid g{n, 1.0 / (2.0 * h), 1.0 / (h * h), c->op.nu};
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  PXA_CUDA(c, launch_bu1_jacT(c->stream, g, u_dev, x_dev, y_dev), "jacT");
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  return PXA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+"""ctypes binding of libpxa (include/pxa.h): argument marshalling only.
+
+Every numerical step runs inside libpxa's CUDA kernels; this module converts torch
+tensors to device pointers, numpy arrays to host pointers, and pxa_status codes to
+exceptions. It never computes anything itself and has no CPU fallback: if the
+library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpxa.so")
+
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+ADVDIFF_1D, BURGERS_1D = 1, 2
+CN, RK4 = 1, 2
+PHI_EXP, PHI_STEPPER = 0, 1
+SERIAL, PARAEXP = 0, 1
+STORE_FULL, STORE_CHECKPOINTS = 0, 1
+
+_STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
+                 ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_TIMEOUT: "TIMEOUT",
+                 ERR_NONFINITE: "NONFINITE", ERR_STATE: "STATE"}
+
+EXPORTS = [
+    "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory",
+    "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
+    "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
+    "pxa_burgers_rhs", "pxa_burgers_jac_T",
+]
+
+
+class PxaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pxa status {_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class OperatorDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("L", ctypes.c_double),
+                ("c", ctypes.c_double), ("nu", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("krylov_err_max", ctypes.c_double),
+                ("krylov_m", ctypes.c_int), ("krylov_substeps", ctypes.c_int),
+                ("magnus_steps", ctypes.c_int), ("lanes", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_int64), ("ms_direct_inhom", ctypes.c_float),
+                ("ms_direct_hom", ctypes.c_float), ("ms_adjoint_inhom", ctypes.c_float),
+                ("ms_adjoint_hom", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpxa.so (built by ``paper_2004_00546_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpxa.so not found at {path}: run paper_2004_00546_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    p, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "pxa_create": [ctypes.POINTER(p), i, p],
+        "pxa_destroy": [p],
+        "pxa_last_error": [p],
+        "pxa_set_operator": [p, ctypes.POINTER(OperatorDesc)],
+        "pxa_set_time": [p, d, i64, i, i],
+        "pxa_set_krylov": [p, i, d, i, i],
+        "pxa_set_magnus": [p, i],
+        "pxa_set_control": [p, p, d],
+        "pxa_set_target": [p, p],
+        "pxa_set_memory": [p, i],
+        "pxa_set_graph": [p, i],
+        "pxa_set_timing": [p, i],
+        "pxa_gradient": [p, i, p, p],
+        "pxa_gradient_async": [p, i, p, p],
+        "pxa_sync": [p],
+        "pxa_gradient_host": [p, i, p, p, p],
+        "pxa_get_stats": [p, ctypes.POINTER(Stats)],
+        "pxa_apply_operator": [p, i, p, p],
+        "pxa_step": [p, i, i64, p, p],
+        "pxa_expv": [p, i, i64, i, p, p, p],
+        "pxa_burgers_rhs": [p, p, p],
+        "pxa_burgers_jac_T": [p, p, p, p],
+    }
+    for name, argt in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = argt
+        fn.restype = None if name == "pxa_destroy" else (ctypes.c_char_p if name == "pxa_last_error" else i)
+    _lib = L
+    return L
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    """Device pointer of a CUDA float64 contiguous torch tensor."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a) -> ctypes.c_void_p:
+    import numpy as np
+
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """One pxa_ctx on one device, bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self._L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        self._check(self._L.pxa_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)),
+                    ctx=None)
+        self._h = h
+        self._keep = {}
+
+    # -- plumbing --------------------------------------------------------------------
+    def _check(self, rc, ctx="self"):
+        if rc != OK:
+            msg = ""
+            if ctx is not None and getattr(self, "_h", None):
+                msg = self._L.pxa_last_error(self._h).decode()
+            raise PxaError(rc, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pxa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ---------------------------------------------------------------
+    def set_operator(self, kind, n, L=6.283185307179586, c=0.0, nu=0.0):
+        desc = OperatorDesc(kind, n, L, c, nu)
+        self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
+        self.n = n
+
+    def set_time(self, T, K, stepper, P):
+        self._check(self._L.pxa_set_time(self._h, T, int(K), stepper, int(P)))
+
+    def set_krylov(self, m, tol, phi, substeps=1):
+        self._check(self._L.pxa_set_krylov(self._h, int(m), tol, phi, int(substeps)))
+
+    def set_magnus(self, steps_per_magnus):
+        self._check(self._L.pxa_set_magnus(self._h, int(steps_per_magnus)))
+
+    def set_control(self, control, omega=0.0):
+        self._keep["control"] = control
+        self._check(self._L.pxa_set_control(self._h, _dptr(control), omega))
+
+    def set_target(self, target):
+        self._keep["target"] = target
+        self._check(self._L.pxa_set_target(self._h, _dptr(target)))
+
+    def set_memory(self, policy):
+        self._check(self._L.pxa_set_memory(self._h, policy))
+
+    def set_graph(self, enable):
+        self._check(self._L.pxa_set_graph(self._h, int(bool(enable))))
+
+    def set_timing(self, enable):
+        self._check(self._L.pxa_set_timing(self._h, int(bool(enable))))
+
+    # -- solves ------------------------------------------------------------------------
+    def gradient(self, mode, grad) -> float:
+        J = ctypes.c_double()
+        self._check(self._L.pxa_gradient(self._h, mode, ctypes.byref(J), _dptr(grad)))
+        return J.value
+
+    def gradient_async(self, mode, J_dev, grad):
+        self._check(self._L.pxa_gradient_async(self._h, mode, _dptr(J_dev), _dptr(grad)))
+
+    def sync(self):
+        self._check(self._L.pxa_sync(self._h))
+
+    def gradient_host(self, mode, control_host, grad_host) -> float:
+        J = ctypes.c_double()
+        self._check(self._L.pxa_gradient_host(self._h, mode, _hptr(control_host), ctypes.byref(J),
+                                              _hptr(grad_host)))
+        return J.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.pxa_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    # -- building blocks -----------------------------------------------------------------
+    def apply_operator(self, x, y, transpose=False):
+        self._check(self._L.pxa_apply_operator(self._h, int(transpose), _dptr(x), _dptr(y)))
+
+    def step(self, x, y, steps, transpose=False):
+        self._check(self._L.pxa_step(self._h, int(transpose), int(steps), _dptr(x), _dptr(y)))
+
+    def expv(self, x, y, span_steps, substeps=1, transpose=False) -> float:
+        err = ctypes.c_double()
+        self._check(self._L.pxa_expv(self._h, int(transpose), int(span_steps), int(substeps),
+                                     _dptr(x), _dptr(y), ctypes.byref(err)))
+        return err.value
+
+    def burgers_rhs(self, u, y):
+        self._check(self._L.pxa_burgers_rhs(self._h, _dptr(u), _dptr(y)))
+
+    def burgers_jac_T(self, u, x, y):
+        self._check(self._L.pxa_burgers_jac_T(self._h, _dptr(u), _dptr(x), _dptr(y)))

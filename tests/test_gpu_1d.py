@@ -1,0 +1,316 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, 1D problems.
+
+Tolerances: FP64 throughout; the CUDA path must match the oracle within 1e-10
+relative (the gradient, J and building blocks), and Paraexp with the stepper's own
+propagator must match serial stepping within 1e-8 (the accuracy gate of the
+benchmark). Building blocks that involve no long recursions are held to 1e-13.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_00546_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def X(cuda_ok):
+    from paper_2004_00546_gb300 import pxa
+
+    return pxa
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    return t
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def ad1_ctx(X, n, c, nu, T, K, P, m=30, tol=1e-11, phi=None, sub=1):
+    ctx = X.Context()
+    ctx.set_operator(X.ADVDIFF_1D, n, c=c, nu=nu)
+    ctx.set_time(T, K, X.CN, P)
+    ctx.set_krylov(m, tol, X.PHI_STEPPER if phi is None else phi, sub)
+    return ctx
+
+
+# ---- building blocks ----------------------------------------------------------------
+@pytest.mark.parametrize("n", [3, 31, 256, 1000, 4096])
+def test_apply_operator_matches_oracle(X, torch, n):
+    ctx = ad1_ctx(X, n, 1.0, 0.01, 1.0, 16, 1)
+    x = I.grf_k2(max(n, 4), 3)[:n] if n >= 4 else np.array([0.3, -1.0, 2.0])
+    xd = dev(torch, x)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        ctx.apply_operator(xd, y, transpose=tr)
+        ref = O.ad1_apply(x, 1.0, 0.01, transpose=tr)
+        assert rel(host(y), ref) < 1e-13
+
+
+@pytest.mark.parametrize("n,steps", [(31, 7), (256, 100), (1000, 33)])
+def test_cn_step_matches_oracle(X, torch, n, steps):
+    T, K = 1.0, 4096
+    ctx = ad1_ctx(X, n, 1.0, 0.01, T, K, 1)
+    x = I.grf_k2(n if n % 2 == 0 else n + 1, 5)[:n]
+    xd = dev(torch, x)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        ctx.step(xd, y, steps, transpose=tr)
+        ref = x.copy()
+        for _ in range(steps):
+            ref = O.ad1_cn_step_T(ref, 1.0, 0.01, T / K) if tr else O.ad1_cn_step(ref, 1.0, 0.01, T / K)
+        assert rel(host(y), ref) < 1e-12
+
+
+@pytest.mark.parametrize("phi", ["exp", "stepper"])
+@pytest.mark.parametrize("sub", [1, 4])
+def test_krylov_expv_matches_exact_propagator(X, torch, phi, sub):
+    n, c, nu, T, K = 256, 1.0, 0.01, 1.0, 4096
+    ctx = ad1_ctx(X, n, c, nu, T, K, 8, m=30, tol=1e-10,
+                  phi=X.PHI_EXP if phi == "exp" else X.PHI_STEPPER)
+    v = I.grf_k2(n, 9)
+    span = 512
+    xd = dev(torch, v)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        err = ctx.expv(xd, y, span, substeps=sub, transpose=tr)
+        if phi == "exp":
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=span * T / K, transpose=tr)
+        else:
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_CN, dt=T / K, steps=span, transpose=tr)
+        assert rel(host(y), ref) < 1e-10
+        assert err < 1e-10
+
+
+def test_krylov_not_converged_is_reported(X, torch):
+    """A Krylov space far too small for the span must come back as NOT_CONVERGED,
+    raised on the host from the device status word (no fault, context stays usable)."""
+    n = 256
+    ctx = ad1_ctx(X, n, 1.0, 0.01, 1.0, 4096, 1, m=3, tol=1e-12, phi=X.PHI_EXP)
+    xd = dev(torch, I.grf_k2(n, 1))
+    y = torch.empty_like(xd)
+    with pytest.raises(X.PxaError) as ei:
+        ctx.expv(xd, y, 4096)
+    assert ei.value.code == X.ERR_NOT_CONVERGED
+    ctx.set_krylov(30, 1e-10, X.PHI_EXP, 1)
+    ctx.expv(xd, y, 64)  # the same context keeps working
+
+
+# ---- full direct-adjoint loops, 1D advection-diffusion --------------------------------
+C1 = dict(n=256, c=1.0, nu=0.01, T=1.0, K=4096, P=8, m=30)
+
+
+@pytest.fixture(scope="module")
+def c1_oracle():
+    p = I.advdiff1d_problem()
+    J, g, qT = O.ad1_cn_gradient_serial(p["q0"], p["c"], p["nu"], p["T"], C1["K"])
+    return p, J, g
+
+
+def test_c1_serial_matches_oracle(X, torch, c1_oracle):
+    p, J, g = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"])
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    gd = torch.empty_like(q0)
+    Jg = ctx.gradient(X.SERIAL, gd)
+    assert abs(Jg - J) / J < 1e-10
+    assert rel(host(gd), g) < 1e-10
+
+
+@pytest.mark.parametrize("sub", [1, 2])
+def test_c1_paraexp_stepper_matches_serial_and_oracle(X, torch, c1_oracle, sub):
+    p, J, g = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"], m=C1["m"], sub=sub)
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    gd = torch.empty_like(q0)
+    Jg = ctx.gradient(X.PARAEXP, gd)
+    # accuracy gate against serial stepping
+    assert abs(Jg - J) / J < 1e-8
+    assert rel(host(gd), g) < 1e-8
+    # against the oracle's Paraexp with the exact stepper propagator
+    Jo, go, _ = O.ad1_cn_gradient_paraexp(p["q0"], p["c"], p["nu"], p["T"], C1["K"], C1["P"], O.PHI_CN)
+    assert abs(Jg - Jo) / Jo < 1e-10
+    assert rel(host(gd), go) < 1e-10
+
+
+def test_c1_paraexp_exp_matches_oracle(X, torch, c1_oracle):
+    p, _, _ = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"], m=30, phi=X.PHI_EXP)
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    gd = torch.empty_like(q0)
+    Jg = ctx.gradient(X.PARAEXP, gd)
+    Jo, go, _ = O.ad1_cn_gradient_paraexp(p["q0"], p["c"], p["nu"], p["T"], C1["K"], C1["P"], O.PHI_EXP)
+    assert abs(Jg - Jo) / Jo < 1e-10
+    assert rel(host(gd), go) < 1e-10
+
+
+@pytest.mark.parametrize("n,K,P,nu,sub", [(1000, 1000, 5, 0.002, 4), (37, 60, 3, 0.02, 1),
+                                          (256, 512, 1, 0.01, 1), (2048, 256, 16, 1e-4, 1)])
+def test_c1_ragged_sizes(X, torch, n, K, P, nu, sub):
+    c, T = 0.8, 0.5
+    q0 = I.grf_k2(n + (n % 2), 77)[:n]
+    J, g, _ = O.ad1_cn_gradient_serial(q0, c, nu, T, K)
+    ctx = ad1_ctx(X, n, c, nu, T, K, P, m=40, tol=1e-10, sub=sub)
+    qd = dev(torch, q0)
+    ctx.set_control(qd)
+    gd = torch.empty_like(qd)
+    Js = ctx.gradient(X.SERIAL, gd)
+    assert abs(Js - J) / J < 1e-10 and rel(host(gd), g) < 1e-10
+    Jp = ctx.gradient(X.PARAEXP, gd)
+    assert abs(Jp - J) / J < 1e-8 and rel(host(gd), g) < 1e-8
+
+
+def test_c1_graph_replay_and_host_entry(X, torch, c1_oracle):
+    p, J, g = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"])
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    g1 = torch.empty_like(q0)
+    J1 = ctx.gradient(X.PARAEXP, g1)
+    ctx.set_graph(True)
+    g2 = torch.empty_like(q0)
+    J2 = ctx.gradient(X.PARAEXP, g2)
+    J3 = ctx.gradient(X.PARAEXP, g2)  # replay of the captured graph
+    assert J1 == J2 == J3
+    assert torch.equal(g1, g2)
+    gh = np.empty(C1["n"])
+    Jh = ctx.gradient_host(X.PARAEXP, np.ascontiguousarray(p["q0"]), gh)
+    assert Jh == J1
+    assert np.array_equal(gh, host(g1))
+
+
+# ---- 1D viscous Burgers ------------------------------------------------------------------
+def bu1_ctx(X, n, nu, T, K, P, M=25, m=30, tol=1e-10, phi=None, memory=None):
+    ctx = X.Context()
+    ctx.set_operator(X.BURGERS_1D, n, nu=nu)
+    ctx.set_time(T, K, X.RK4, P)
+    ctx.set_krylov(m, tol, X.PHI_EXP if phi is None else phi, 1)
+    if phi is None or phi == X.PHI_EXP:
+        ctx.set_magnus(M)
+    if memory is not None:
+        ctx.set_memory(memory)
+    return ctx
+
+
+@pytest.mark.parametrize("n", [3, 64, 1000])
+def test_burgers_building_blocks(X, torch, n):
+    ctx = bu1_ctx(X, n, 0.01, 1.0, 100, 1)
+    rng = np.random.default_rng(n)
+    u, x = rng.standard_normal(n), rng.standard_normal(n)
+    ud, xd = dev(torch, u), dev(torch, x)
+    y = torch.empty_like(ud)
+    ctx.burgers_rhs(ud, y)
+    assert rel(host(y), O.bu1_rhs(u, 0.01)) < 1e-13
+    ctx.burgers_jac_T(ud, xd, y)
+    assert rel(host(y), O.bu1_jac(u, x, 0.01, transpose=True)) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def bu_small():
+    n, nu, T, K = 200, 0.01, 0.3, 600
+    f = 3.0 * I.fourier1d(n, 8, 61)
+    g = I.fourier1d(n, 8, 62)
+    J, grad = O.bu1_gradient_serial(f, g, nu, T, K)
+    return dict(n=n, nu=nu, T=T, K=K, f=f, g=g, J=J, grad=grad)
+
+
+@pytest.mark.parametrize("memory", ["full", "checkpoints"])
+def test_burgers_serial_matches_oracle(X, torch, bu_small, memory):
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6,
+                  memory=X.STORE_FULL if memory == "full" else X.STORE_CHECKPOINTS)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.SERIAL, out)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out), b["grad"]) < 1e-10
+
+
+@pytest.mark.parametrize("memory", ["full", "checkpoints"])
+@pytest.mark.parametrize("P", [1, 6, 20])
+def test_burgers_paraexp_stepper_chain_is_exact(X, torch, bu_small, memory, P):
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, phi=X.PHI_STEPPER,
+                  memory=X.STORE_FULL if memory == "full" else X.STORE_CHECKPOINTS)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out), b["grad"]) < 1e-10
+
+
+@pytest.mark.parametrize("memory", ["full", "checkpoints"])
+def test_burgers_paraexp_magnus_matches_oracle(X, torch, bu_small, memory):
+    b = bu_small
+    P, M, m = 6, 10, 30
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, M=M, m=m,
+                  memory=X.STORE_FULL if memory == "full" else X.STORE_CHECKPOINTS)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.PARAEXP, out)
+    Jo, go = O.bu1_gradient_hybrid(b["f"], b["g"], b["nu"], b["T"], b["K"], P, O.HOM_MAGNUS, M, m)
+    assert abs(J - Jo) / Jo < 1e-10
+    assert rel(host(out), go) < 1e-10
+    # the Magnus approximation itself stays close to serial stepping at this step size
+    assert rel(host(out), b["grad"]) < 1e-6
+
+
+# ---- full size 1D Burgers (n = 1024, K = 20000, P = 32) ---------------------------------
+@pytest.fixture(scope="module")
+def bu_full():
+    p = I.burgers1d_problem()
+    J, grad = O.bu1_gradient_serial(p["f"], p["g"], p["nu"], p["T"], 20000)
+    return dict(p=p, J=J, grad=grad)
+
+
+def test_burgers_full_size_serial_and_stepper_paraexp(X, torch, bu_full):
+    p = bu_full["p"]
+    ctx = bu1_ctx(X, 1024, p["nu"], p["T"], 20000, 32, phi=X.PHI_STEPPER)
+    fd, gd_ = dev(torch, p["f"]), dev(torch, p["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.SERIAL, out)
+    assert abs(J - bu_full["J"]) / bu_full["J"] < 1e-10
+    assert rel(host(out), bu_full["grad"]) < 1e-10
+    J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - bu_full["J"]) / bu_full["J"] < 1e-10
+    assert rel(host(out), bu_full["grad"]) < 1e-10
+
+
+def test_burgers_full_size_magnus_matches_oracle(X, torch, bu_full):
+    p = bu_full["p"]
+    M, m = 25, 20
+    ctx = bu1_ctx(X, 1024, p["nu"], p["T"], 20000, 32, M=M, m=m, tol=1e-9)
+    fd, gd_ = dev(torch, p["f"]), dev(torch, p["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.PARAEXP, out)
+    Jo, go = O.bu1_gradient_hybrid(p["f"], p["g"], p["nu"], p["T"], 20000, 32, O.HOM_MAGNUS, M, 30)
+    assert abs(J - Jo) / Jo < 1e-10
+    assert rel(host(out), go) < 1e-9
