@@ -61,7 +61,8 @@ typedef enum {
   PXA_ERR_NOT_CONVERGED = -4,  /* a Krylov error estimate exceeded the tolerance */
   PXA_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
   PXA_ERR_NONFINITE = -6,      /* J or the gradient is not finite */
-  PXA_ERR_STATE = -7           /* call made before the context was configured */
+  PXA_ERR_STATE = -7,          /* call made before the context was configured */
+  PXA_ERR_TOO_LARGE = -8       /* request exceeds the fixed buffer of pxa_expv_static */
 } pxa_status;
 
 typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2 } pxa_problem;
@@ -166,6 +167,41 @@ int pxa_expv(pxa_ctx* ctx, int transpose, int64_t span_steps, int substeps,
  * y = J(u)^T x (transposed Jacobian). */
 int pxa_burgers_rhs(pxa_ctx* ctx, const double* u_dev, double* y_dev);
 int pxa_burgers_jac_T(pxa_ctx* ctx, const double* u_dev, const double* x_dev, double* y_dev);
+
+/* ---- allocation-free Krylov propagation ----------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that must
+ * not allocate device memory: a plugin inside an application that owns every byte
+ * of device memory, or a real-time loop that fixes its memory footprint at start-up
+ * and cannot handle an allocation failure later. The context-based calls above
+ * allocate their workspace on the first solve, so such callers cannot use them.
+ *
+ * Computes what pxa_expv computes for PXA_ADVDIFF_1D (stencil of pxa_operator_desc
+ * with kind PXA_ADVDIFF_1D, time step dt = T/K): y = phi(A) x (or phi(A^T) x) over
+ * `substeps` Krylov substeps spanning `span_steps` time steps, phi = exp (PXA_PHI_EXP)
+ * or the Crank–Nicolson power (PXA_PHI_STEPPER); Krylov dimension m, tolerance tol
+ * on the a-posteriori estimate. x_dev, y_dev: caller-owned device vectors of n doubles.
+ * err_host (may be NULL) receives the largest relative error estimate.
+ *
+ * Memory: the Krylov basis, the status word and the error estimate live in one
+ * fixed array of PXA_EXPV_STATIC_MAX_DOUBLES doubles (1 MiB) defined inside the
+ * library; every GPU that loads the library holds it until the process exits. The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Requests with n * (m + 1) > PXA_EXPV_STATIC_MAX_DOUBLES - 64 return
+ * PXA_ERR_TOO_LARGE before touching the device.
+ *
+ * Set-up: the first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream capture.
+ * The call runs on `cuda_stream` of device `device` and synchronises that stream
+ * before returning. Every call shares the one array, which keeps the last call's
+ * contents: the status word and the error estimate are cleared by each call, the
+ * basis is overwritten. Calls that overlap on the GPU (other streams, other host
+ * threads) race on the array and must be serialised by the caller.
+ * Returns PXA_OK, PXA_ERR_INVALID (bad arguments), PXA_ERR_TOO_LARGE,
+ * PXA_ERR_NOT_CONVERGED (estimate above tol) or PXA_ERR_CUDA. */
+#define PXA_EXPV_STATIC_MAX_DOUBLES 131072
+int pxa_expv_static(int device, void* cuda_stream, const pxa_operator_desc* op, double T,
+                    int64_t K, int m, double tol, int phi, int transpose, int64_t span_steps,
+                    int substeps, const double* x_dev, double* y_dev, double* err_host);
 
 #ifdef __cplusplus
 }

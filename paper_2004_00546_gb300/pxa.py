@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libpxa.so")
 
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6, -7)
+ERR_TOO_LARGE = -8
+EXPV_STATIC_MAX_DOUBLES = 131072
 ADVDIFF_1D, BURGERS_1D = 1, 2
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
@@ -23,14 +25,14 @@ STORE_FULL, STORE_CHECKPOINTS = 0, 1
 
 _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
                  ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_TIMEOUT: "TIMEOUT",
-                 ERR_NONFINITE: "NONFINITE", ERR_STATE: "STATE"}
+                 ERR_NONFINITE: "NONFINITE", ERR_STATE: "STATE", ERR_TOO_LARGE: "TOO_LARGE"}
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
     "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
-    "pxa_burgers_rhs", "pxa_burgers_jac_T",
+    "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static",
 ]
 
 
@@ -89,6 +91,7 @@ def load(path: str = LIB_PATH):
         "pxa_expv": [p, i, i64, i, p, p, p],
         "pxa_burgers_rhs": [p, p, p],
         "pxa_burgers_jac_T": [p, p, p, p],
+        "pxa_expv_static": [i, p, ctypes.POINTER(OperatorDesc), d, i64, i, d, i, i, i64, i, p, p, p],
     }
     for name, argt in sig.items():
         fn = getattr(L, name)
@@ -223,3 +226,22 @@ class Context:
 
     def burgers_jac_T(self, u, x, y):
         self._check(self._L.pxa_burgers_jac_T(self._h, _dptr(u), _dptr(x), _dptr(y)))
+
+
+def expv_static(x, y, n, c, nu, T, K, m, tol, phi, span_steps, substeps=1, transpose=False,
+                L=6.283185307179586, device=0, stream=None) -> float:
+    """pxa_expv_static: the Krylov propagation of Context.expv with the library's fixed
+    device scratch array instead of an allocated workspace (see include/pxa.h)."""
+    import torch
+
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    desc = OperatorDesc(ADVDIFF_1D, n, L, c, nu)
+    err = ctypes.c_double()
+    rc = lib.pxa_expv_static(device, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(desc), T,
+                             int(K), int(m), tol, phi, int(transpose), int(span_steps), int(substeps),
+                             _dptr(x), _dptr(y), ctypes.byref(err))
+    if rc != OK:
+        raise PxaError(rc, "pxa_expv_static")
+    return err.value
