@@ -129,6 +129,12 @@ int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
 int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
 /* Direct-state storage policy (pxa_memory). */
 int pxa_set_memory(pxa_ctx* ctx, int policy);
+/* CTAs per thread-block cluster of the BURGERS_1D RK4 kernels: the serial direct
+ * lane, each of the P concurrent adjoint lanes, and the homogeneous chain (1..16;
+ * 0 = automatic: 16 for the serial lanes, SMs/P for the concurrent lanes, both capped
+ * so that each CTA keeps >= 32 grid points). One lane is split into contiguous
+ * chunks, one per CTA, exchanging halos through distributed shared memory. */
+int pxa_set_cluster(pxa_ctx* ctx, int direct, int lanes, int chain);
 /* Capture the whole gradient into a CUDA graph and replay it (1) or launch kernels
  * one by one (0, default). */
 int pxa_set_graph(pxa_ctx* ctx, int enable);

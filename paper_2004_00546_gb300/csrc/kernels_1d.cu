@@ -11,8 +11,8 @@
 //   ad1_superpose_*          Eq. fullsol0 and Eq. fulladjsol at the end points,
 //                            J, the adjoint terminal value (Eq. adjFinalTime) and the
 //                            initial-condition gradient (Eq. initupdate).
-//   bu1_direct_kernel        Eq. seriesDirect: serial RK4 of the nonlinear problem.
-//   bu1_adjoint_lanes_kernel Eq. hybadjinhom: exact discrete adjoint of RK4 per lane.
+//   (the RK4 direct, adjoint lanes and stepper chain run on thread-block clusters,
+//    see kernels_bu1_cluster.cu)
 //   bu1_magnus_chain_kernel  Eq. adjHomNormal for the linear time-varying adjoint:
 //                            4th-order Magnus steps, Krylov exp and phi_1.
 //   sum_lanes_kernel         Eq. fullAdjSolHyb integrated against s(t): the forcing
@@ -315,74 +315,6 @@ __device__ __forceinline__ double forcing_s(double omega, double t) {
   return omega == 0.0 ? 1.0 : sin(omega * t);
 }
 
-// Serial RK4 of the nonlinear direct problem (Eq. seriesDirect), one block.
-// Stores every state (traj != null) and/or the states at multiples of ck_every
-// (ckpt != null), and J = (1/T) sum_{j>=1} dt ||u_j - g||^2.
-__global__ void bu1_direct_kernel(Bu1Grid g, double dt, double T, int64_t K, double omega,
-                                  const double* __restrict__ f, const double* __restrict__ gt,
-                                  const double* __restrict__ u0, double* __restrict__ traj,
-                                  double* __restrict__ ckpt, int64_t ck_every,
-                                  double* __restrict__ Jdev, int* status) {
-  extern __shared__ double sm[];
-  const int n = g.n;
-  double* red = sm;
-  double* u = red + 40;
-  double* ya = u + n + 2;
-  double* yb = ya + n + 2;
-  double* acc = yb + n + 2;
-  double* ff = acc + n;
-  double* gg = ff + n;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    double v = u0 ? u0[p] : 0.0;
-    put1(u, n, p, v);
-    ff[p] = f[p];
-    gg[p] = gt[p];
-    if (traj) traj[p] = v;
-    if (ckpt) ckpt[p] = v;
-  }
-  __syncthreads();
-  double jp = 0.0;
-  for (int64_t s = 0; s < K; ++s) {
-    const double t = (double)s * dt;
-    const double s1 = forcing_s(omega, t), s2 = forcing_s(omega, t + 0.5 * dt),
-                 s4 = forcing_s(omega, t + dt);
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double k = bu1_rhs_at(g, u, p) + s1 * ff[p];
-      acc[p] = k;
-      put1(ya, n, p, u[p + 1] + 0.5 * dt * k);
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double k = bu1_rhs_at(g, ya, p) + s2 * ff[p];
-      acc[p] += 2.0 * k;
-      put1(yb, n, p, u[p + 1] + 0.5 * dt * k);
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double k = bu1_rhs_at(g, yb, p) + s2 * ff[p];
-      acc[p] += 2.0 * k;
-      put1(ya, n, p, u[p + 1] + dt * k);
-    }
-    __syncthreads();
-    const bool write_ck = ckpt && ((s + 1) % ck_every == 0);
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double k = bu1_rhs_at(g, ya, p) + s4 * ff[p];
-      double un = u[p + 1] + dt / 6.0 * (acc[p] + k);
-      put1(u, n, p, un);
-      double d = un - gg[p];
-      jp = fma(d, d, jp);
-      if (traj) traj[(size_t)(s + 1) * n + p] = un;
-      if (write_ck) ckpt[(size_t)((s + 1) / ck_every) * n + p] = un;
-    }
-    __syncthreads();
-  }
-  double J = dt / T * block_sum(jp, red);
-  if (threadIdx.x == 0) {
-    *Jdev = J;
-    if (!isfinite(J)) set_status(status, PXA_ERR_NONFINITE);
-  }
-}
-
 // Address of direct state row s: contiguous rows (lane_k == 0) or the per-lane
 // recompute layout, where lane l holds rows l*k .. l*k+k in a block of k+1 rows.
 __device__ __forceinline__ const double* row_ptr(const double* base, int n, int64_t s,
@@ -391,253 +323,6 @@ __device__ __forceinline__ const double* row_ptr(const double* base, int n, int6
   int64_t l = s / lane_k;
   if (l > lanes - 1) l = lanes - 1;
   return base + ((size_t)l * (size_t)(lane_k + 1) + (size_t)(s - l * lane_k)) * n;
-}
-
-// Shared buffers of a reverse RK4 sweep (all halo-1 except ff, gg).
-struct SweepBufs {
-  double *u, *Y2, *Y3, *Y4, *ma, *mb;
-  const double *ff, *gg;
-};
-
-// Reverse sweep of the RK4 map from step s_top down to s_bot (exclusive of the source
-// of u_{s_bot}): lambda_s = M_s^T lambda_{s+1} (+ (2dt/T)(u_s - g) for s > s_bot when
-// with_source), and gacc += G_s^T lambda_{s+1} where G_s = du_{s+1}/df. The stage
-// states Y2..Y4 are recomputed from u_s. lam/gacc: the thread's points
-// p = threadIdx.x + q*blockDim.x.
-template <int PPT>
-__device__ void bu1_reverse_sweep(const Bu1Grid& g, double dt, double T, double omega,
-                                  const double* rows, int64_t lane_k, int lanes, int64_t s_top,
-                                  int64_t s_bot, const SweepBufs& b, double (&lam)[PPT],
-                                  double (&gacc)[PPT], bool with_source) {
-  const int n = g.n;
-  const double src = 2.0 * dt / T;
-  double lamn[PPT];
-  for (int64_t s = s_top - 1; s >= s_bot; --s) {
-    const double t = (double)s * dt;
-    const double c1 = forcing_s(omega, t), c2 = forcing_s(omega, t + 0.5 * dt),
-                 c4 = forcing_s(omega, t + dt);
-    const double* us = row_ptr(rows, n, s, lane_k, lanes);
-    __syncthreads();  // the previous step finished reading u and the stage buffers
-    for (int p = threadIdx.x; p < n; p += blockDim.x) put1(b.u, n, p, us[p]);
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x)
-      put1(b.Y2, n, p, b.u[p + 1] + 0.5 * dt * (bu1_rhs_at(g, b.u, p) + c1 * b.ff[p]));
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x)
-      put1(b.Y3, n, p, b.u[p + 1] + 0.5 * dt * (bu1_rhs_at(g, b.Y2, p) + c2 * b.ff[p]));
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x)
-      put1(b.Y4, n, p, b.u[p + 1] + dt * (bu1_rhs_at(g, b.Y3, p) + c2 * b.ff[p]));
-    // stage 4: kbar4 = dt/6 lam
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) {
-        double m4 = dt / 6.0 * lam[q];
-        gacc[q] = fma(c4, m4, gacc[q]);
-        put1(b.ma, n, p, m4);
-      }
-    }
-    __syncthreads();
-    // Ybar4 = J(Y4)^T kbar4 ; kbar3 = dt/3 lam + dt Ybar4
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) {
-        double nv = bu1_jacT_at(g, b.Y4, b.ma, p);
-        lamn[q] = lam[q] + nv;
-        double m3 = dt / 3.0 * lam[q] + dt * nv;
-        gacc[q] = fma(c2, m3, gacc[q]);
-        put1(b.mb, n, p, m3);
-      }
-    }
-    __syncthreads();
-    // Ybar3 = J(Y3)^T kbar3 ; kbar2 = dt/3 lam + dt/2 Ybar3
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) {
-        double nv = bu1_jacT_at(g, b.Y3, b.mb, p);
-        lamn[q] += nv;
-        double m2 = dt / 3.0 * lam[q] + 0.5 * dt * nv;
-        gacc[q] = fma(c2, m2, gacc[q]);
-        put1(b.ma, n, p, m2);
-      }
-    }
-    __syncthreads();
-    // Ybar2 = J(Y2)^T kbar2 ; kbar1 = dt/6 lam + dt/2 Ybar2
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) {
-        double nv = bu1_jacT_at(g, b.Y2, b.ma, p);
-        lamn[q] += nv;
-        double m1 = dt / 6.0 * lam[q] + 0.5 * dt * nv;
-        gacc[q] = fma(c1, m1, gacc[q]);
-        put1(b.mb, n, p, m1);
-      }
-    }
-    __syncthreads();
-    // Ybar1 = J(u_s)^T kbar1 ; lambda_s = lambda_{s+1} + sum Ybar (+ source of u_s)
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) {
-        double nv = bu1_jacT_at(g, b.u, b.mb, p);
-        double l = lamn[q] + nv;
-        if (with_source && s > s_bot) l = fma(src, b.u[p + 1] - b.gg[p], l);
-        lam[q] = l;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ SweepBufs carve_sweep(double* sm, int n, const double* f,
-                                                 const double* gt) {
-  SweepBufs b;
-  b.u = sm;
-  b.Y2 = b.u + n + 2;
-  b.Y3 = b.Y2 + n + 2;
-  b.Y4 = b.Y3 + n + 2;
-  b.ma = b.Y4 + n + 2;
-  b.mb = b.ma + n + 2;
-  double* ff = b.mb + n + 2;
-  double* gg = ff + n;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    ff[p] = f[p];
-    gg[p] = gt[p];
-  }
-  b.ff = ff;
-  b.gg = gg;
-  __syncthreads();
-  return b;
-}
-
-// Recompute the direct states of rows s0..s1 from row s0 (already in `my` row 0) with
-// the same RK4 as bu1_direct_kernel; rows written to my[(s - s0) * n].
-__device__ void bu1_recompute(const Bu1Grid& g, double dt, double omega, int64_t s0, int64_t s1,
-                              double* my, const SweepBufs& b) {
-  const int n = g.n;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) put1(b.u, n, p, my[p]);
-  __syncthreads();
-  for (int64_t s = s0; s < s1; ++s) {
-    const double t = (double)s * dt;
-    const double c1 = forcing_s(omega, t), c2 = forcing_s(omega, t + 0.5 * dt),
-                 c4 = forcing_s(omega, t + dt);
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double kk = bu1_rhs_at(g, b.u, p) + c1 * b.ff[p];
-      b.ma[p + 1] = kk;
-      put1(b.Y2, n, p, b.u[p + 1] + 0.5 * dt * kk);
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double kk = bu1_rhs_at(g, b.Y2, p) + c2 * b.ff[p];
-      b.ma[p + 1] += 2.0 * kk;
-      put1(b.Y3, n, p, b.u[p + 1] + 0.5 * dt * kk);
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double kk = bu1_rhs_at(g, b.Y3, p) + c2 * b.ff[p];
-      b.ma[p + 1] += 2.0 * kk;
-      put1(b.Y4, n, p, b.u[p + 1] + dt * kk);
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      double kk = bu1_rhs_at(g, b.Y4, p) + c4 * b.ff[p];
-      double un = b.u[p + 1] + dt / 6.0 * (b.ma[p + 1] + kk);
-      put1(b.u, n, p, un);
-      my[(size_t)(s + 1 - s0) * n + p] = un;
-    }
-    __syncthreads();
-  }
-}
-
-// Exact discrete adjoint of RK4 over one lane [s0, s0+k) per block (Eq. hybadjinhom
-// with the objective's source; zero value above the lane's top). Reads direct state
-// rows from `traj` (full storage) or, in checkpoint mode, first recomputes the lane's
-// rows from checkpoint row `lane` of `ckpt` into the lane's block of `scratch`.
-// Outputs: wout[lane] = lambda at s0 (without the source of u_{s0}),
-//          gout[lane] = sum over the lane of G_s^T lambda_{s+1} (forcing gradient).
-template <int PPT>
-__global__ void bu1_adjoint_lanes_kernel(Bu1Grid g, double dt, double T, int64_t k,
-                                         double omega, const double* __restrict__ f,
-                                         const double* __restrict__ gt,
-                                         const double* __restrict__ traj,
-                                         const double* __restrict__ ckpt, double* scratch,
-                                         double* __restrict__ wout, double* __restrict__ gout,
-                                         int* status) {
-  extern __shared__ double sm[];
-  const int n = g.n;
-  const int lane = blockIdx.x;
-  const int64_t s0 = (int64_t)lane * k, s1 = s0 + k;
-  SweepBufs b = carve_sweep(sm, n, f, gt);
-  const double* rows = traj;
-  int64_t lane_k = 0;
-  if (ckpt) {
-    double* my = scratch + (size_t)lane * (size_t)(k + 1) * n;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) my[p] = ckpt[(size_t)lane * n + p];
-    __syncthreads();
-    bu1_recompute(g, dt, omega, s0, s1, my, b);
-    rows = scratch;
-    lane_k = k;
-  }
-  double lam[PPT], gacc[PPT];
-  const double src = 2.0 * dt / T;
-  const double* top = row_ptr(rows, n, s1, lane_k, (int)gridDim.x);
-  // the top row of a lane lives in that lane's own block (row k), not in the next one
-  if (lane_k) top = rows + ((size_t)lane * (size_t)(k + 1) + (size_t)k) * n;
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    int p = threadIdx.x + q * blockDim.x;
-    gacc[q] = 0.0;
-    lam[q] = (p < n) ? src * (top[p] - b.gg[p]) : 0.0;
-  }
-  bu1_reverse_sweep<PPT>(g, dt, T, omega, rows, lane_k, (int)gridDim.x, s1, s0, b, lam, gacc, true);
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    int p = threadIdx.x + q * blockDim.x;
-    if (p < n) {
-      wout[(size_t)lane * n + p] = lam[q];
-      gout[(size_t)lane * n + p] = gacc[q];
-    }
-  }
-  (void)status;
-}
-
-// Homogeneous adjoint chain with the stepper's own propagator (exact transposed RK4
-// maps, no source): h = 0; for lane = P-2 .. 0: h += W[lane+1]; sweep h through the
-// lane, accumulating its forcing-gradient integral into gH. One block.
-template <int PPT>
-__global__ void bu1_stepper_chain_kernel(Bu1Grid g, double dt, double T, int64_t k, int P,
-                                         double omega, const double* __restrict__ f,
-                                         const double* __restrict__ gt,
-                                         const double* __restrict__ rows, int64_t lane_k,
-                                         const double* __restrict__ W,
-                                         double* __restrict__ gH) {
-  extern __shared__ double sm[];
-  const int n = g.n;
-  SweepBufs b = carve_sweep(sm, n, f, gt);
-  double lam[PPT], gacc[PPT];
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    lam[q] = 0.0;
-    gacc[q] = 0.0;
-  }
-  for (int lane = P - 2; lane >= 0; --lane) {
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      int p = threadIdx.x + q * blockDim.x;
-      if (p < n) lam[q] += W[(size_t)(lane + 1) * n + p];
-    }
-    const int64_t s0 = (int64_t)lane * k;
-    bu1_reverse_sweep<PPT>(g, dt, T, omega, rows, lane_k, P, s0 + k, s0, b, lam, gacc, false);
-  }
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    int p = threadIdx.x + q * blockDim.x;
-    if (p < n) gH[p] = gacc[q];
-  }
 }
 
 // Magnus operator of one backward step of the adjoint (time reversed, tau = t_top - t):
@@ -906,43 +591,6 @@ cudaError_t launch_ad1_superpose_adjoint(cudaStream_t st, int n, const double* l
   return cudaGetLastError();
 }
 
-cudaError_t launch_bu1_direct(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
-                              int64_t K, double omega, const double* f, const double* gt,
-                              const double* u0, double* traj, double* ckpt, int64_t ck_every,
-                              double* J, int* status) {
-  size_t sh = sizeof(double) * (40 + 3 * (size_t)(g.n + 2) + 3 * (size_t)g.n);
-  cudaError_t e = cudaFuncSetAttribute(bu1_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  if (e != cudaSuccess) return e;
-  bu1_direct_kernel<<<1, threads, sh, st>>>(g, dt, T, K, omega, f, gt, u0, traj, ckpt, ck_every,
-                                             J, status);
-  return cudaGetLastError();
-}
-
-template <int PPT>
-static cudaError_t launch_adj_t(cudaStream_t st, int lanes, int threads, size_t sh, Bu1Grid g,
-                                double dt, double T, int64_t k, double omega, const double* f,
-                                const double* gt, const double* traj, const double* ckpt,
-                                double* scratch, double* wout, double* gout, int* status) {
-  cudaError_t e = cudaFuncSetAttribute(bu1_adjoint_lanes_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  if (e != cudaSuccess) return e;
-  bu1_adjoint_lanes_kernel<PPT><<<lanes, threads, sh, st>>>(g, dt, T, k, omega, f, gt, traj, ckpt,
-                                                            scratch, wout, gout, status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bu1_adjoint_lanes(cudaStream_t st, int lanes, int threads, Bu1Grid g,
-                                     double dt, double T, int64_t k, double omega,
-                                     const double* f, const double* gt, const double* traj,
-                                     const double* ckpt, double* scratch, double* wout,
-                                     double* gout, int* status) {
-  size_t sh = sizeof(double) * (6 * (size_t)(g.n + 2) + 2 * (size_t)g.n);
-  int ppt = (g.n + threads - 1) / threads;
-  if (ppt <= 1) return launch_adj_t<1>(st, lanes, threads, sh, g, dt, T, k, omega, f, gt, traj, ckpt, scratch, wout, gout, status);
-  if (ppt <= 2) return launch_adj_t<2>(st, lanes, threads, sh, g, dt, T, k, omega, f, gt, traj, ckpt, scratch, wout, gout, status);
-  if (ppt <= 4) return launch_adj_t<4>(st, lanes, threads, sh, g, dt, T, k, omega, f, gt, traj, ckpt, scratch, wout, gout, status);
-  return cudaErrorInvalidValue;
-}
-
 template <int PPT>
 static cudaError_t launch_mag_t(cudaStream_t st, int threads, size_t sh, Bu1Grid g, double dt,
                                 int64_t K, int P, int64_t k, int M, double omega,
@@ -964,29 +612,6 @@ cudaError_t launch_bu1_magnus_chain(cudaStream_t st, int threads, Bu1Grid g, dou
   if (ppt <= 1) return launch_mag_t<1>(st, threads, sh, g, dt, K, P, k, M, omega, traj, lane_k, W, gH, Vglob, m, tol, v_in_smem, status, errmax);
   if (ppt <= 2) return launch_mag_t<2>(st, threads, sh, g, dt, K, P, k, M, omega, traj, lane_k, W, gH, Vglob, m, tol, v_in_smem, status, errmax);
   if (ppt <= 4) return launch_mag_t<4>(st, threads, sh, g, dt, K, P, k, M, omega, traj, lane_k, W, gH, Vglob, m, tol, v_in_smem, status, errmax);
-  return cudaErrorInvalidValue;
-}
-
-template <int PPT>
-static cudaError_t launch_stc_t(cudaStream_t st, int threads, size_t sh, Bu1Grid g, double dt,
-                                double T, int64_t k, int P, double omega, const double* f,
-                                const double* gt, const double* rows, int64_t lane_k,
-                                const double* W, double* gH) {
-  cudaError_t e = cudaFuncSetAttribute(bu1_stepper_chain_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  if (e != cudaSuccess) return e;
-  bu1_stepper_chain_kernel<PPT><<<1, threads, sh, st>>>(g, dt, T, k, P, omega, f, gt, rows, lane_k, W, gH);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bu1_stepper_chain(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
-                                     int64_t k, int P, double omega, const double* f,
-                                     const double* gt, const double* rows, int64_t lane_k,
-                                     const double* W, double* gH) {
-  size_t sh = sizeof(double) * (6 * (size_t)(g.n + 2) + 2 * (size_t)g.n);
-  int ppt = (g.n + threads - 1) / threads;
-  if (ppt <= 1) return launch_stc_t<1>(st, threads, sh, g, dt, T, k, P, omega, f, gt, rows, lane_k, W, gH);
-  if (ppt <= 2) return launch_stc_t<2>(st, threads, sh, g, dt, T, k, P, omega, f, gt, rows, lane_k, W, gH);
-  if (ppt <= 4) return launch_stc_t<4>(st, threads, sh, g, dt, T, k, P, omega, f, gt, rows, lane_k, W, gH);
   return cudaErrorInvalidValue;
 }
 

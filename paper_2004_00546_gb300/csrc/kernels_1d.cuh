@@ -36,23 +36,22 @@ cudaError_t launch_ad1_superpose_direct(cudaStream_t st, int threads, int n, int
 cudaError_t launch_ad1_superpose_adjoint(cudaStream_t st, int n, const double* lamK,
                                          const double* e0, const double* hsum, double* grad,
                                          int* status);
-cudaError_t launch_bu1_direct(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
-                              int64_t K, double omega, const double* f, const double* gt,
-                              const double* u0, double* traj, double* ckpt, int64_t ck_every,
-                              double* J, int* status);
-cudaError_t launch_bu1_adjoint_lanes(cudaStream_t st, int lanes, int threads, Bu1Grid g,
-                                     double dt, double T, int64_t k, double omega,
-                                     const double* f, const double* gt, const double* traj,
-                                     const double* ckpt, double* scratch, double* wout,
-                                     double* gout, int* status);
 cudaError_t launch_bu1_magnus_chain(cudaStream_t st, int threads, Bu1Grid g, double dt, int64_t K,
                                     int P, int64_t k, int M, double omega, const double* traj,
                                     int64_t lane_k, const double* W, double* gH, double* Vglob, int m, double tol,
                                     int v_in_smem, int* status, double* errmax);
-cudaError_t launch_bu1_stepper_chain(cudaStream_t st, int threads, Bu1Grid g, double dt, double T,
-                                     int64_t k, int P, double omega, const double* f,
-                                     const double* gt, const double* rows, int64_t lane_k,
-                                     const double* W, double* gH);
+bool bu1c_valid_cluster(int n, int C);
+cudaError_t launch_bu1c_direct(cudaStream_t st, int C, int n, double L, double nu, double dt,
+                               double T, int64_t K, double omega, const double* f, const double* gt,
+                               double* traj, double* ckpt, int64_t ck_every, double* J, int* status);
+cudaError_t launch_bu1c_adjoint_lanes(cudaStream_t st, int C, int lanes, int n, double L, double nu,
+                                      double dt, double T, int64_t k, double omega, const double* f,
+                                      const double* gt, const double* traj, const double* ckpt,
+                                      double* scratch, double* wout, double* gout);
+cudaError_t launch_bu1c_stepper_chain(cudaStream_t st, int C, int n, double L, double nu, double dt,
+                                      double T, int64_t k, int P, double omega, const double* f,
+                                      const double* gt, const double* rows, int64_t lane_k,
+                                      const double* W, double* gH);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);
 cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);

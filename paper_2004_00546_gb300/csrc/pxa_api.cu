@@ -34,6 +34,9 @@ struct pxa_ctx {
   const double* target = nullptr;
   int memory = PXA_STORE_FULL;
   bool use_graph = false, timing = false;
+  // CTAs per thread-block cluster for the Burgers RK4 kernels (0 = choose automatically)
+  int cl_req_direct = 0, cl_req_lanes = 0, cl_req_chain = 0;
+  int cl_direct = 1, cl_lanes = 1, cl_chain = 1;
 
   // derived
   double am = 0, a0 = 0, ap = 0;  // advection-diffusion stencil
@@ -225,6 +228,22 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
     }
   }
+  if (c->op.kind == PXA_BURGERS_1D) {
+    // A serial lane gets the widest cluster that keeps >= 32 points per CTA; the P
+    // concurrent adjoint lanes share the SMs (P * C <= number of SMs).
+    int sms = 0;
+    PXA_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "SM count");
+    auto widest = [&](int limit) {
+      int C = 16;
+      while (C > 1 && (C > limit || n / C < 32 || !bu1c_valid_cluster(n, C))) C /= 2;
+      return C;
+    };
+    c->cl_direct = c->cl_req_direct > 0 ? c->cl_req_direct : widest(16);
+    c->cl_chain = c->cl_req_chain > 0 ? c->cl_req_chain : widest(16);
+    c->cl_lanes = c->cl_req_lanes > 0 ? c->cl_req_lanes : widest(P > 0 ? sms / P : 1);
+    for (int C : {c->cl_direct, c->cl_chain, c->cl_lanes})
+      if (!bu1c_valid_cluster(n, C)) return fail(c, PXA_ERR_INVALID, "cluster size does not fit the grid");
+  }
   PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "memset status");
   c->stats.workspace_bytes = c->ws_bytes;
   c->ready = true;
@@ -294,7 +313,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
 // ---- 1D Burgers (forcing control, tracking objective), hybrid scheme ----------
 int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
-  const int n = c->op.n, th = threads_for(n);
+  const int n = c->op.n;
   const int64_t K = c->K;
   const double dt = c->T / (double)K;
   const double h = c->op.L / n;
@@ -304,24 +323,22 @@ int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   const bool full = c->memory == PXA_STORE_FULL;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
   ev_record(c, 0);
-  if (full) {
-    PXA_CUDA(c, launch_bu1_direct(st, th, g, dt, c->T, K, c->omega, c->control, c->target, nullptr,
-                                  c->traj, nullptr, 1, Jdev, c->status), "direct");
-  } else {
-    // checkpoints at the boundaries of the lanes of this mode (P+1 rows; 2 rows serial)
-    PXA_CUDA(c, launch_bu1_direct(st, th, g, dt, c->T, K, c->omega, c->control, c->target, nullptr,
-                                  nullptr, c->traj, k, Jdev, c->status), "direct");
-  }
+  // direct (Eq. seriesDirect) on one cluster of cl_direct CTAs
+  PXA_CUDA(c, launch_bu1c_direct(st, c->cl_direct, n, c->op.L, c->op.nu, dt, c->T, K, c->omega,
+                                 c->control, c->target, full ? c->traj : nullptr,
+                                 full ? nullptr : c->traj, k, Jdev, c->status), "direct");
   ev_record(c, 1);
   ev_record(c, 2);
-  const int ath = n > 2048 ? 1024 : (threads_for(n) > 512 ? 512 : threads_for(n));
-  PXA_CUDA(c, launch_bu1_adjoint_lanes(st, P, ath, g, dt, c->T, k, c->omega, c->control, c->target,
-                                       full ? c->traj : nullptr, full ? nullptr : c->traj,
-                                       c->scratch, c->E, c->EA, c->status), "adjoint lanes");
+  const int cl_lane = P == 1 ? c->cl_direct : c->cl_lanes;
+  PXA_CUDA(c, launch_bu1c_adjoint_lanes(st, cl_lane, P, n, c->op.L, c->op.nu, dt, c->T, k, c->omega,
+                                        c->control, c->target, full ? c->traj : nullptr,
+                                        full ? nullptr : c->traj, c->scratch, c->E, c->EA),
+           "adjoint lanes");
   ev_record(c, 3);
   if (P > 1 && c->kry_phi == PXA_PHI_STEPPER) {
-    PXA_CUDA(c, launch_bu1_stepper_chain(st, ath, g, dt, c->T, k, P, c->omega, c->control, c->target,
-                                         full ? c->traj : c->scratch, full ? 0 : k, c->E, c->hsum),
+    PXA_CUDA(c, launch_bu1c_stepper_chain(st, c->cl_chain, n, c->op.L, c->op.nu, dt, c->T, k, P,
+                                          c->omega, c->control, c->target,
+                                          full ? c->traj : c->scratch, full ? 0 : k, c->E, c->hsum),
              "stepper chain");
   } else if (P > 1) {
     PXA_CUDA(c, launch_bu1_magnus_chain(st, n > 2048 ? 1024 : 512, g, dt, K, P, k, c->magnus_M, c->omega,
@@ -467,6 +484,18 @@ int pxa_set_target(pxa_ctx* c, const double* target_dev) {
 int pxa_set_memory(pxa_ctx* c, int policy) {
   if (!c || (policy != PXA_STORE_FULL && policy != PXA_STORE_CHECKPOINTS)) return PXA_ERR_INVALID;
   c->memory = policy;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_cluster(pxa_ctx* c, int direct, int lanes, int chain) {
+  if (!c) return PXA_ERR_INVALID;
+  for (int C : {direct, lanes, chain})
+    if (C < 0 || C > 16) return fail(c, PXA_ERR_INVALID, "cluster sizes must be 0 (auto) or 1..16");
+  c->cl_req_direct = direct;
+  c->cl_req_lanes = lanes;
+  c->cl_req_chain = chain;
   release_workspace(c);
   invalidate(c);
   return PXA_OK;

@@ -32,7 +32,7 @@ EXPORTS = [
     "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
-    "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static",
+    "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster",
 ]
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "pxa_set_target": [p, p],
         "pxa_set_memory": [p, i],
         "pxa_set_graph": [p, i],
+        "pxa_set_cluster": [p, i, i, i],
         "pxa_set_timing": [p, i],
         "pxa_gradient": [p, i, p, p],
         "pxa_gradient_async": [p, i, p, p],
@@ -178,6 +179,9 @@ class Context:
 
     def set_memory(self, policy):
         self._check(self._L.pxa_set_memory(self._h, policy))
+
+    def set_cluster(self, direct=0, lanes=0, chain=0):
+        self._check(self._L.pxa_set_cluster(self._h, int(direct), int(lanes), int(chain)))
 
     def set_graph(self, enable):
         self._check(self._L.pxa_set_graph(self._h, int(bool(enable))))

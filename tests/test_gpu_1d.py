@@ -279,6 +279,36 @@ def test_burgers_paraexp_magnus_matches_oracle(X, torch, bu_small, memory):
     assert rel(host(out), b["grad"]) < 1e-6
 
 
+@pytest.mark.parametrize("C", [1, 2, 3, 8, 16])
+def test_burgers_cluster_sizes(X, torch, bu_small, C):
+    """Every cluster size gives the same gradient; n = 200 with C = 16 leaves a last
+    chunk (5 points) smaller than the reverse step's halo, so halos span two CTAs."""
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    ctx.set_cluster(C, C, C)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    for mode in (X.SERIAL, X.PARAEXP):
+        J = ctx.gradient(mode, out)
+        assert abs(J - b["J"]) / b["J"] < 1e-10
+        assert rel(host(out), b["grad"]) < 1e-10
+
+
+def test_burgers_cluster_checkpoint_recompute(X, torch, bu_small):
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER, memory=X.STORE_CHECKPOINTS)
+    ctx.set_cluster(4, 3, 4)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out), b["grad"]) < 1e-10
+
+
 # ---- full size 1D Burgers (n = 1024, K = 20000, P = 32) ---------------------------------
 @pytest.fixture(scope="module")
 def bu_full():
