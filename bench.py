@@ -41,8 +41,19 @@ WORKLOADS = {
 }
 
 # Algorithmic FP64 operations per grid point per step of each kernel.
-FLOPS_RK4_DIRECT = 62.0       # four stages of N(u) + s f, stage updates, J accumulation
-FLOPS_RK4_ADJOINT = 150.0     # stage recompute (3 x 14) + four J^T applies and updates
+FLOPS_RK4_DIRECT = 62.0       # four stages of N(u) + s f (14 each), final update 3, J 3
+FLOPS_RK4_ADJOINT = 109.0     # stage recompute 36, four transposed-Jacobian stages 70, source 3
+FLOPS_RK4_ADJOINT_HOM = 106.0  # the same without the objective's source
+FLOPS_CN_BAND_TAP = 2.0       # one FMA per tap of the circulant CN band per point per step
+
+# DRAM bytes per launch from the committed ncu captures (profiles/*.md); None when the
+# kernel changed after the capture.
+TRAFFIC = {
+    "bu1c_stepper_chain_kernel": 159.98e6 + 2.99e6,
+    "bu1c_direct_kernel": 1.50e6 + 103.94e6,
+    "ad1_chain_kernel": 91.4e3,
+    "cn_lanes_kernel": 12.0e3,
+}
 
 
 def parse():
@@ -253,27 +264,46 @@ def run_ours(args, w, rank, world):
     # roofline of the dominant kernel, from the per-phase CUDA events of the timed steps
     ph = {k: float(np.mean([p[k] for p in phases])) for k in
           ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom")}
+    st = ctx.stats()
     n, K, P = w["n"], w["K"], w["P"]
+    k = K // P
     if w["kind"] == "burgers1d":
+        cl = ctx.cluster_sizes()
         kernels = {
-            "bu1_direct_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K),
-            "bu1_adjoint_lanes_kernel": (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K),
-            "homogeneous_chain": (ph["ms_adjoint_hom"],
-                                  FLOPS_RK4_ADJOINT * n * K * (P - 1) / P if head == "paraexp_stepper" else None),
+            # name: (ms per launch, algorithmic FP64 flop per launch, SMs used, DRAM bytes per launch)
+            "bu1c_direct_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K, cl[0],
+                                   TRAFFIC.get("bu1c_direct_kernel")),
+            "bu1c_adjoint_lanes_kernel": (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K, P * cl[1],
+                                          TRAFFIC.get("bu1c_adjoint_lanes_kernel")),
         }
+        if head == "paraexp_stepper":
+            kernels["bu1c_stepper_chain_kernel"] = (ph["ms_adjoint_hom"],
+                                                    FLOPS_RK4_ADJOINT_HOM * n * k * (P - 1), cl[2],
+                                                    TRAFFIC.get("bu1c_stepper_chain_kernel"))
+        else:
+            kernels["bu1_magnus_chain_kernel"] = (ph["ms_adjoint_hom"], None, 1, None)
     else:
+        m = w["m"]
+        arnoldi = (8 * m + 4 * m * (m + 1) + 2 * m) * n  # operator, CGS2, norms, combine
+        dense = 2 * (m ** 3) * (1 + int(np.log2(k // w["sub"])))  # solve + squarings
         kernels = {
-            "cn_lanes_kernel": (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"], None),
-            "ad1_chain_kernel": (ph["ms_direct_hom"] + ph["ms_adjoint_hom"], None),
+            "ad1_chain_kernel": (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]),
+                                 (P - 1) * w["sub"] * (arnoldi + dense), 1, TRAFFIC.get("ad1_chain_kernel")),
+            "cn_lanes_kernel": (0.5 * (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"]),
+                                FLOPS_CN_BAND_TAP * st["band_taps"] * n * k * P, P,
+                                TRAFFIC.get("cn_lanes_kernel")),
         }
-    dom = max(kernels, key=lambda k: kernels[k][0])
-    ms_dom, flops = kernels[dom]
-    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": FP64_PEAK_GFLOPS / 1e3,
-            "peak_kind": "nominal FP64 (1.25 TFLOP/s, 152 SMs x 2 DFMA/clk x 2.07 GHz ~ 1.26)",
-            "traffic": None, "ms_per_launch": ms_dom}
+    dom = max(kernels, key=lambda kk: kernels[kk][0])
+    ms_dom, flops, sms_used, traffic = kernels[dom]
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak_tf,
+            "peak_kind": "nominal FP64 of GB300 (1.25 TFLOP/s; 152 SMs x 2 FP64 FMA/clk)",
+            "traffic": traffic, "ms_per_launch": ms_dom, "sms_used": sms_used}
     if flops is not None and ms_dom > 0:
         ach = flops / (ms_dom * 1e-3) / 1e12
-        roof.update({"achieved": ach, "frac": ach / (FP64_PEAK_GFLOPS / 1e3)})
+        roof.update({"achieved": ach, "frac": ach / peak_tf,
+                     "frac_of_used_sms": ach / (peak_tf * sms_used / SMS),
+                     "flop_per_launch": flops})
     else:
         roof.update({"achieved": None, "frac": None})
 

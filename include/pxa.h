@@ -100,6 +100,10 @@ typedef struct {
   float ms_adjoint_inhom;
   float ms_adjoint_hom;
   float ms_total;
+  int band_taps;            /* taps of the circulant CN band (ADVDIFF_1D) */
+  int cluster_direct;       /* CTAs per cluster in use (BURGERS_1D) */
+  int cluster_lanes;
+  int cluster_chain;
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t

@@ -246,6 +246,10 @@ int prepare(pxa_ctx* c) {
   }
   PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "memset status");
   c->stats.workspace_bytes = c->ws_bytes;
+  c->stats.band_taps = c->op.kind == PXA_ADVDIFF_1D ? 2 * c->band_r + 1 : 0;
+  c->stats.cluster_direct = c->cl_direct;
+  c->stats.cluster_lanes = c->cl_lanes;
+  c->stats.cluster_chain = c->cl_chain;
   c->ready = true;
   return PXA_OK;
 }

@@ -53,7 +53,9 @@ class Stats(ctypes.Structure):
                 ("magnus_steps", ctypes.c_int), ("lanes", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_int64), ("ms_direct_inhom", ctypes.c_float),
                 ("ms_direct_hom", ctypes.c_float), ("ms_adjoint_inhom", ctypes.c_float),
-                ("ms_adjoint_hom", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_adjoint_hom", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("band_taps", ctypes.c_int), ("cluster_direct", ctypes.c_int),
+                ("cluster_lanes", ctypes.c_int), ("cluster_chain", ctypes.c_int)]
 
 
 _lib = None
@@ -211,6 +213,10 @@ class Context:
         s = Stats()
         self._check(self._L.pxa_get_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def cluster_sizes(self):
+        s = self.stats()
+        return s["cluster_direct"], s["cluster_lanes"], s["cluster_chain"]
 
     # -- building blocks -----------------------------------------------------------------
     def apply_operator(self, x, y, transpose=False):
