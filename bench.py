@@ -197,13 +197,22 @@ def run_ours(args, w, rank, world):
     phis = [("paraexp_stepper", X.PARAEXP, X.PHI_STEPPER), ("paraexp_exp", X.PARAEXP, X.PHI_EXP),
             ("serial", X.SERIAL, X.PHI_STEPPER)]
     grads = {}
+    tuned = {}
     for name, mode, phi in phis:
         ctx = make_ctx(X, w, phi)
         ctx.set_control(ctl)
         if tgt is not None:
             ctx.set_target(tgt)
+        best_ms = None
+        if not (w["kind"] == "burgers1d" and phi == X.PHI_EXP):
+            # autotuner (outside any timed region): Krylov m / substeps, or cluster sizes
+            best_ms = ctx.autotune(mode, torch.empty(w["n"], dtype=torch.float64, device="cuda"))
+        st = ctx.stats()
+        tuned[name] = {"krylov_m": st["krylov_m"], "krylov_substeps": st["krylov_substeps"],
+                       "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]],
+                       "autotune_best_ms": best_ms}
         times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
-        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name}
+        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name, "tuned": tuned[name]}
         grads[name] = g.detach().cpu().numpy()
         ctx.close()
 
@@ -227,6 +236,11 @@ def run_ours(args, w, rank, world):
     ctx.set_control(ctl)
     if tgt is not None:
         ctx.set_target(tgt)
+    tv = tuned[head]
+    if w["kind"] == "advdiff1d":
+        ctx.set_krylov(tv["krylov_m"], w["tol"], phi, tv["krylov_substeps"])
+    else:
+        ctx.set_cluster(*tv["clusters"])
 
     if world > 1:
         import torch.distributed as dist
@@ -283,12 +297,12 @@ def run_ours(args, w, rank, world):
         else:
             kernels["bu1_magnus_chain_kernel"] = (ph["ms_adjoint_hom"], None, 1, None)
     else:
-        m = w["m"]
+        m, sub = st["krylov_m"], st["krylov_substeps"]
         arnoldi = (8 * m + 4 * m * (m + 1) + 2 * m) * n  # operator, CGS2, norms, combine
-        dense = 2 * (m ** 3) * (1 + int(np.log2(k // w["sub"])))  # solve + squarings
+        dense = 2 * (m ** 3) * (1 + int(np.log2(k // sub)))  # solve + squarings
         kernels = {
             "ad1_chain_kernel": (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]),
-                                 (P - 1) * w["sub"] * (arnoldi + dense), 1, TRAFFIC.get("ad1_chain_kernel")),
+                                 (P - 1) * sub * (arnoldi + dense), 1, TRAFFIC.get("ad1_chain_kernel")),
             "cn_lanes_kernel": (0.5 * (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"]),
                                 FLOPS_CN_BAND_TAP * st["band_taps"] * n * k * P, P,
                                 TRAFFIC.get("cn_lanes_kernel")),

@@ -151,6 +151,15 @@ int pxa_gradient(pxa_ctx* ctx, int mode, double* J_host, double* grad_dev);
  * inside kernels surface at the next pxa_sync. Graph-capturable once the workspace
  * exists (after one pxa_gradient). */
 int pxa_gradient_async(pxa_ctx* ctx, int mode, double* J_dev, double* grad_dev);
+/* The two halves of pxa_gradient, for a caller that differentiates through the
+ * direct solve (e.g. an autograd function): pxa_solve_direct runs the direct problem
+ * and stores what the adjoint needs (q(T) and the adjoint source, or the Burgers
+ * trajectory / checkpoints) in the context, returning J; pxa_solve_adjoint then runs
+ * the adjoint problem of the same mode and writes dJ/d(control) to grad_dev. Any
+ * set_* call in between invalidates the stored state (PXA_ERR_STATE). Both
+ * synchronise the stream. */
+int pxa_solve_direct(pxa_ctx* ctx, int mode, double* J_host);
+int pxa_solve_adjoint(pxa_ctx* ctx, int mode, double* grad_dev);
 /* Wait for the stream and report device-side errors. */
 int pxa_sync(pxa_ctx* ctx);
 /* End-to-end call with host buffers: copies control_host (n doubles) to the device,
@@ -161,6 +170,15 @@ int pxa_gradient_host(pxa_ctx* ctx, int mode, const double* control_host, double
 int pxa_get_stats(const pxa_ctx* ctx, pxa_stats* out);
 /* Per-phase CUDA-event timing inside pxa_gradient (0 = off, default). */
 int pxa_set_timing(pxa_ctx* ctx, int enable);
+/* Autotuner: times one gradient of `mode` for each candidate configuration on the
+ * configured problem (control and target must be set) and keeps the fastest whose
+ * Krylov error estimates stay within the tolerance. ADVDIFF_1D candidates: Krylov
+ * dimension m and substeps per subinterval (m in {16, 20, 24, 30, 36, 40}, substeps in
+ * {1, 2, 4, 8} dividing K/P). BURGERS_1D candidates: cluster sizes of the direct,
+ * lane and chain kernels. grad_dev: n doubles of scratch for the trial gradients.
+ * *best_ms_host (may be NULL) receives the best time. Allocates workspace while
+ * tuning; returns PXA_ERR_NOT_CONVERGED if no candidate meets the tolerance. */
+int pxa_autotune(pxa_ctx* ctx, int mode, double* grad_dev, double* best_ms_host);
 
 /* ---- building blocks, exposed for kernel-level tests --------------------------
  * y = A x (transpose = 0) or A^T x (transpose = 1) for ADVDIFF_1D. */

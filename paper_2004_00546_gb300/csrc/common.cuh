@@ -61,6 +61,8 @@ __device__ __forceinline__ void dense_copy(double* dst, const double* src, int d
 }
 
 // C = alpha * A * B + beta_diag * I (C must not alias A or B). Ends with a barrier.
+// One entry per thread and pass: the kernels that use it are bound by the SM's FP64
+// issue rate, so extra partial sums (more FP64 adds) cost more than they hide.
 __device__ __forceinline__ void dense_gemm(double* C, const double* A, const double* B, int d,
                                            double alpha, double beta_diag) {
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
@@ -199,23 +201,37 @@ __device__ inline void dense_solve(double* A, double* B, int d, double* col, int
   }
 }
 
-// E = R^e for a d x d matrix R by binary powering. R is overwritten; T is scratch.
-__device__ inline void dense_pow(double* E, double* R, double* T, int d, int64_t e) {
-  dense_identity(E, d);
-  __syncthreads();
+// R^e for a d x d matrix by binary powering with pointer rotation over four buffers
+// (R holds the base on entry; E, T1, T2 are scratch; no copies). Returns the buffer
+// that holds the result (the identity is written into E when e == 0).
+__device__ inline double* dense_pow(double* R, double* E, double* T1, double* T2, int d, int64_t e) {
+  double* pool[4] = {R, E, T1, T2};
+  int ib = 0, ir = -1;
+  if (e <= 0) {
+    dense_identity(E, d);
+    __syncthreads();
+    return E;
+  }
   while (e > 0) {
     if (e & 1) {
-      dense_gemm(T, E, R, d, 1.0, 0.0);
-      dense_copy(E, T, d);
-      __syncthreads();
+      if (ir < 0) {
+        ir = ib;
+      } else {
+        int f = 0;
+        while (f == ib || f == ir) ++f;
+        dense_gemm(pool[f], pool[ir], pool[ib], d, 1.0, 0.0);
+        ir = f;
+      }
     }
     e >>= 1;
     if (e > 0) {
-      dense_gemm(T, R, R, d, 1.0, 0.0);
-      dense_copy(R, T, d);
-      __syncthreads();
+      int f = 0;
+      while (f == ib || f == ir) ++f;
+      dense_gemm(pool[f], pool[ib], pool[ib], d, 1.0, 0.0);
+      ib = f;
     }
   }
+  return pool[ir];
 }
 
 }  // namespace pxa

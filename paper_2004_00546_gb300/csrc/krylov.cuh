@@ -127,6 +127,7 @@ __device__ inline double hessenberg_phi(KrylovScratch& ks, int mm, int phi_mode,
     ks.D0[i * kLD + j] = v;
   }
   __syncthreads();
+  double* F = ks.D1;
   if (phi_mode == 0) {
     dense_expm(ks.D1, ks.D0, ks.D2, ks.D3, d, ks.red);  // D1 = exp(D0)
   } else {
@@ -139,16 +140,14 @@ __device__ inline double hessenberg_phi(KrylovScratch& ks, int mm, int phi_mode,
     }
     __syncthreads();
     dense_solve(ks.D2, ks.D1, d, ks.hcol, ks.ipiv);  // D1 = R
-    dense_copy(ks.D0, ks.D1, d);
-    __syncthreads();
-    dense_pow(ks.D1, ks.D0, ks.D2, d, steps);  // D1 = R^steps
+    F = dense_pow(ks.D1, ks.D0, ks.D2, ks.D3, d, steps);  // F = R^steps
   }
   for (int i = threadIdx.x; i < mm; i += blockDim.x) {
-    c[i] = ks.D1[i * kLD + 0];
-    if (want_phi1 && phi_mode == 0) c1[i] = ks.D1[i * kLD + mm];
+    c[i] = F[i * kLD + 0];
+    if (want_phi1 && phi_mode == 0) c1[i] = F[i * kLD + mm];
   }
   __syncthreads();
-  return fabs(ks.D1[(mm - 1) * kLD + 0]);
+  return fabs(F[(mm - 1) * kLD + 0]);
 }
 
 }  // namespace pxa

@@ -66,6 +66,8 @@ struct pxa_ctx {
   double* grad_buf = nullptr; // n (pxa_gradient_host)
   bool v_in_smem = false;
 
+  int direct_mode = -1;  // mode of the last pxa_solve_direct whose state is still valid
+
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   int g_mode = -1;
@@ -115,6 +117,7 @@ void invalidate(pxa_ctx* c) {
     c->gexec = nullptr;
   }
   c->g_mode = -1;
+  c->direct_mode = -1;
 }
 
 template <typename T>
@@ -138,7 +141,8 @@ int alloc(pxa_ctx* c, T** out, size_t count) {
 // from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
 // by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj} in long double. The taps decay
 // geometrically (the implicit matrix is diagonally dominant); the band stops where
-// both |m_r| and |m_-r| fall below 2^-72 |m_0|, far under FP64 rounding of the step.
+// both |m_r| and |m_-r| fall below 2^-64 |m_0|, far under FP64 rounding of the step;
+// when they do not decay within n/2 the full circulant is used.
 int cn_band(pxa_ctx* c, int n, double am, double a0, double ap, double dt,
             std::vector<double>& taps, int& r) {
   typedef std::complex<long double> C;
@@ -165,18 +169,18 @@ int cn_band(pxa_ctx* c, int n, double am, double a0, double ap, double dt,
   double m0 = tap(0);
   pos.push_back(m0);
   neg.push_back(m0);
-  const double thr = std::ldexp(std::fabs(m0), -72);
-  int rmax = (n - 1) / 2;
+  const double thr = std::ldexp(std::fabs(m0), -64);
+  // widest band: every offset once; for even n the offset n/2 equals -n/2 and is
+  // stored once (on the negative side)
+  const int rmax = n / 2;
   r = 0;
   for (int j = 1; j <= rmax; ++j) {
-    double mp = tap(j), mn = tap(-j);
+    double mn = tap(-j);
+    double mp = (2 * j == n) ? 0.0 : tap(j);
     pos.push_back(mp);
     neg.push_back(mn);
     r = j;
-    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;
-    if (j == rmax)
-      return fail(c, PXA_ERR_INVALID,
-                  "Crank-Nicolson map is not banded at this dt/h (taps do not decay within n/2)");
+    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;  // the tail is below FP64 rounding
   }
   taps.assign(2 * r + 1, 0.0);
   for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
@@ -259,24 +263,30 @@ void ev_record(pxa_ctx* c, int i) {
 }
 
 // ---- 1D advection-diffusion (IC control, terminal objective) ----------------
-int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+// parts: bit 0 = direct solve (J, q(T), adjoint source), bit 1 = adjoint solve (gradient)
+int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
+  const bool do_d = parts & 1, do_a = parts & 2;
   const int n = c->op.n, P = c->P, r = c->band_r, th = threads_for(n);
   const int64_t K = c->K;
   const double dt = c->T / (double)K;
   const double* q0 = c->control;
   if (mode == PXA_SERIAL) {
-    ev_record(c, 0);
-    PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 0, K, q0, nullptr, c->E), "cn serial");
-    ev_record(c, 1);
-    ev_record(c, 2);
-    PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, nullptr, c->E, nullptr, c->qT,
-                                            nullptr, Jdev, c->status), "superpose");
-    PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 1, K, c->qT, nullptr, c->EA), "cn serial T");
-    ev_record(c, 3);
-    ev_record(c, 4);
-    PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, nullptr, c->EA, nullptr, grad, c->status), "grad");
-    ev_record(c, 5);
+    if (do_d) {
+      ev_record(c, 0);
+      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 0, K, q0, nullptr, c->E), "cn serial");
+      ev_record(c, 1);
+      ev_record(c, 2);
+      PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, nullptr, c->E, nullptr, c->qT,
+                                              nullptr, Jdev, c->status), "superpose");
+    }
+    if (do_a) {
+      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 1, K, c->qT, nullptr, c->EA), "cn serial T");
+      ev_record(c, 3);
+      ev_record(c, 4);
+      PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, nullptr, c->EA, nullptr, grad, c->status), "grad");
+      ev_record(c, 5);
+    }
     return PXA_OK;
   }
   const int64_t k = K / P;
@@ -284,6 +294,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   const int64_t steps_sub = k / nsub;
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)steps_sub : dt;
   const int kth = 256;
+  if (do_d) {
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
   ev_record(c, 0);
   // Eq. linzero: the shifted problem has zero IC and source A q0; in CN form the
@@ -300,6 +311,8 @@ int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, q0, c->E + (size_t)(P - 1) * n,
                                           P > 1 ? c->hsum : nullptr, c->qT, c->srcA, Jdev,
                                           c->status), "superpose");
+  }
+  if (!do_a) return PXA_OK;
   PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 1, k, nullptr, c->srcA, c->EA), "adj lanes");
   ev_record(c, 3);
   if (P > 1) {
@@ -315,8 +328,9 @@ int enqueue_ad1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
 }
 
 // ---- 1D Burgers (forcing control, tracking objective), hybrid scheme ----------
-int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
+  const bool do_d = parts & 1, do_a = parts & 2;
   const int n = c->op.n;
   const int64_t K = c->K;
   const double dt = c->T / (double)K;
@@ -326,12 +340,15 @@ int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   const int64_t k = K / P;
   const bool full = c->memory == PXA_STORE_FULL;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
-  ev_record(c, 0);
-  // direct (Eq. seriesDirect) on one cluster of cl_direct CTAs
-  PXA_CUDA(c, launch_bu1c_direct(st, c->cl_direct, n, c->op.L, c->op.nu, dt, c->T, K, c->omega,
-                                 c->control, c->target, full ? c->traj : nullptr,
-                                 full ? nullptr : c->traj, k, Jdev, c->status), "direct");
-  ev_record(c, 1);
+  if (do_d) {
+    ev_record(c, 0);
+    // direct (Eq. seriesDirect) on one cluster of cl_direct CTAs
+    PXA_CUDA(c, launch_bu1c_direct(st, c->cl_direct, n, c->op.L, c->op.nu, dt, c->T, K, c->omega,
+                                   c->control, c->target, full ? c->traj : nullptr,
+                                   full ? nullptr : c->traj, k, Jdev, c->status), "direct");
+    ev_record(c, 1);
+  }
+  if (!do_a) return PXA_OK;
   ev_record(c, 2);
   const int cl_lane = P == 1 ? c->cl_direct : c->cl_lanes;
   PXA_CUDA(c, launch_bu1c_adjoint_lanes(st, cl_lane, P, n, c->op.L, c->op.nu, dt, c->T, k, c->omega,
@@ -355,12 +372,16 @@ int enqueue_bu1(pxa_ctx* c, int mode, double* Jdev, double* grad) {
   return PXA_OK;
 }
 
-int enqueue(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+int enqueue_parts(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (mode != PXA_SERIAL && mode != PXA_PARAEXP) return fail(c, PXA_ERR_INVALID, "mode");
   if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first");
   if (c->op.kind == PXA_BURGERS_1D && !c->target) return fail(c, PXA_ERR_STATE, "set_target first");
-  if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, Jdev, grad);
-  return enqueue_bu1(c, mode, Jdev, grad);
+  if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, parts, Jdev, grad);
+  return enqueue_bu1(c, mode, parts, Jdev, grad);
+}
+
+int enqueue(pxa_ctx* c, int mode, double* Jdev, double* grad) {
+  return enqueue_parts(c, mode, 3, Jdev, grad);
 }
 
 int read_status(pxa_ctx* c) {
@@ -602,6 +623,34 @@ int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
   return read_status(c);
 }
 
+int pxa_solve_direct(pxa_ctx* c, int mode, double* J_host) {
+  if (!c) return PXA_ERR_INVALID;
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  rc = enqueue_parts(c, mode, 1, c->Jdev, nullptr);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  double J = 0.0;
+  PXA_CUDA(c, cudaMemcpy(&J, c->Jdev, sizeof(double), cudaMemcpyDeviceToHost), "read J");
+  c->stats.J = J;
+  if (J_host) *J_host = J;
+  rc = read_status(c);
+  c->direct_mode = rc == PXA_OK ? mode : -1;
+  return rc;
+}
+
+int pxa_solve_adjoint(pxa_ctx* c, int mode, double* grad_dev) {
+  if (!c || !grad_dev) return PXA_ERR_INVALID;
+  if (!c->ready || c->direct_mode != mode)
+    return fail(c, PXA_ERR_STATE, "pxa_solve_adjoint needs a pxa_solve_direct of the same mode first");
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  int rc = enqueue_parts(c, mode, 2, c->Jdev, grad_dev);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  return read_status(c);
+}
+
 int pxa_gradient_host(pxa_ctx* c, int mode, const double* control_host, double* J_host,
                       double* grad_host) {
   if (!c || !control_host || !grad_host) return PXA_ERR_INVALID;
@@ -620,6 +669,95 @@ int pxa_gradient_host(pxa_ctx* c, int mode, const double* control_host, double* 
   PXA_CUDA(c, cudaMemcpyAsync(grad_host, c->grad_buf, sizeof(double) * n, cudaMemcpyDeviceToHost,
                               c->stream), "D2H grad");
   PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  return PXA_OK;
+}
+
+int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
+  if (!c || !grad_dev) return PXA_ERR_INVALID;
+  if (!c->have_op || !c->have_time || !c->control) return fail(c, PXA_ERR_STATE, "configure the problem first");
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const bool graph = c->use_graph, timing = c->timing;
+  c->use_graph = false;
+  c->timing = false;
+  cudaEvent_t e0, e1;
+  PXA_CUDA(c, cudaEventCreate(&e0), "event");
+  PXA_CUDA(c, cudaEventCreate(&e1), "event");
+  struct Cand { int a, b, cc; };
+  std::vector<Cand> cands;
+  const int64_t k = c->K / c->P;
+  if (c->op.kind == PXA_ADVDIFF_1D) {
+    for (int m : {16, 20, 24, 30, 36, 40})
+      for (int sub : {1, 2, 4, 8})
+        if (k % sub == 0 && m < c->op.n) cands.push_back({m, sub, 0});
+  } else {
+    int sms = 0;
+    PXA_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "SM count");
+    auto ok = [&](int C) { return bu1c_valid_cluster(c->op.n, C) && (C == 1 || c->op.n / C >= 24); };
+    for (int cd : {1, 2, 4, 8, 12, 16})
+      for (int cl : {1, 2, 3, 4})
+        if (ok(cd) && ok(cl) && cl * c->P <= (sms > 0 ? sms : 152)) cands.push_back({cd, cl, cd});
+  }
+  const int m0 = c->kry_m, s0 = c->kry_sub, rd = c->cl_req_direct, rl = c->cl_req_lanes, rc0 = c->cl_req_chain;
+  double best = 1e300;
+  Cand bestc{-1, -1, -1};
+  for (const Cand& cd : cands) {
+    if (c->op.kind == PXA_ADVDIFF_1D) {
+      c->kry_m = cd.a;
+      c->kry_sub = cd.b;
+    } else {
+      c->cl_req_direct = cd.a;
+      c->cl_req_lanes = cd.b;
+      c->cl_req_chain = cd.cc;
+    }
+    release_workspace(c);
+    invalidate(c);
+    int rc = prepare(c);
+    if (rc) continue;
+    double J;
+    rc = pxa_gradient(c, mode, &J, grad_dev);  // warm-up (and convergence check)
+    if (rc == PXA_ERR_NOT_CONVERGED) continue;
+    if (rc) break;
+    PXA_CUDA(c, cudaEventRecord(e0, c->stream), "record");
+    rc = enqueue(c, mode, c->Jdev, grad_dev);
+    PXA_CUDA(c, cudaEventRecord(e1, c->stream), "record");
+    PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
+    if (rc || read_status(c) != PXA_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestc = cd;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->use_graph = graph;
+  c->timing = timing;
+  if (bestc.a < 0) {
+    c->kry_m = m0;
+    c->kry_sub = s0;
+    c->cl_req_direct = rd;
+    c->cl_req_lanes = rl;
+    c->cl_req_chain = rc0;
+    release_workspace(c);
+    invalidate(c);
+    return fail(c, PXA_ERR_NOT_CONVERGED, "no autotuner candidate met the Krylov tolerance");
+  }
+  if (c->op.kind == PXA_ADVDIFF_1D) {
+    c->kry_m = bestc.a;
+    c->kry_sub = bestc.b;
+  } else {
+    c->cl_req_direct = bestc.a;
+    c->cl_req_lanes = bestc.b;
+    c->cl_req_chain = bestc.cc;
+  }
+  release_workspace(c);
+  invalidate(c);
+  int rc = prepare(c);
+  if (rc) return rc;
+  c->stats.krylov_m = c->kry_m;
+  c->stats.krylov_substeps = c->kry_sub;
+  if (best_ms_host) *best_ms_host = best;
   return PXA_OK;
 }
 

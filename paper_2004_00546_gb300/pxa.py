@@ -32,7 +32,7 @@ EXPORTS = [
     "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
-    "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster",
+    "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
 ]
 
 
@@ -83,6 +83,9 @@ def load(path: str = LIB_PATH):
         "pxa_set_memory": [p, i],
         "pxa_set_graph": [p, i],
         "pxa_set_cluster": [p, i, i, i],
+        "pxa_autotune": [p, i, p, p],
+        "pxa_solve_direct": [p, i, p],
+        "pxa_solve_adjoint": [p, i, p],
         "pxa_set_timing": [p, i],
         "pxa_gradient": [p, i, p, p],
         "pxa_gradient_async": [p, i, p, p],
@@ -197,6 +200,14 @@ class Context:
         self._check(self._L.pxa_gradient(self._h, mode, ctypes.byref(J), _dptr(grad)))
         return J.value
 
+    def solve_direct(self, mode) -> float:
+        J = ctypes.c_double()
+        self._check(self._L.pxa_solve_direct(self._h, mode, ctypes.byref(J)))
+        return J.value
+
+    def solve_adjoint(self, mode, grad):
+        self._check(self._L.pxa_solve_adjoint(self._h, mode, _dptr(grad)))
+
     def gradient_async(self, mode, J_dev, grad):
         self._check(self._L.pxa_gradient_async(self._h, mode, _dptr(J_dev), _dptr(grad)))
 
@@ -208,6 +219,11 @@ class Context:
         self._check(self._L.pxa_gradient_host(self._h, mode, _hptr(control_host), ctypes.byref(J),
                                               _hptr(grad_host)))
         return J.value
+
+    def autotune(self, mode, grad) -> float:
+        ms = ctypes.c_double()
+        self._check(self._L.pxa_autotune(self._h, mode, _dptr(grad), ctypes.byref(ms)))
+        return ms.value
 
     def stats(self) -> dict:
         s = Stats()

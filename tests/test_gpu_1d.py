@@ -197,6 +197,40 @@ def test_c1_graph_replay_and_host_entry(X, torch, c1_oracle):
     assert np.array_equal(gh, host(g1))
 
 
+def test_c1_autotune_keeps_parity(X, torch, c1_oracle):
+    p, J, g = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"])
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    gd = torch.empty_like(q0)
+    ms = ctx.autotune(X.PARAEXP, gd)
+    assert ms > 0
+    st = ctx.stats()
+    assert st["krylov_m"] in (16, 20, 24, 30, 36, 40) and st["krylov_substeps"] in (1, 2, 4, 8)
+    Jg = ctx.gradient(X.PARAEXP, gd)
+    assert abs(Jg - J) / J < 1e-8 and rel(host(gd), g) < 1e-8
+
+
+def test_split_solves_match_gradient_and_check_order(X, torch, c1_oracle):
+    p, J, g = c1_oracle
+    ctx = ad1_ctx(X, C1["n"], C1["c"], C1["nu"], C1["T"], C1["K"], C1["P"])
+    q0 = dev(torch, p["q0"])
+    ctx.set_control(q0)
+    gd = torch.empty_like(q0)
+    with pytest.raises(X.PxaError) as ei:
+        ctx.solve_adjoint(X.PARAEXP, gd)
+    assert ei.value.code == X.ERR_STATE
+    for mode in (X.SERIAL, X.PARAEXP):
+        Jd = ctx.solve_direct(mode)
+        ctx.solve_adjoint(mode, gd)
+        g2 = torch.empty_like(q0)
+        Jf = ctx.gradient(mode, g2)
+        assert Jd == Jf and torch.equal(gd, g2)
+    ctx.solve_direct(X.SERIAL)
+    with pytest.raises(X.PxaError):
+        ctx.solve_adjoint(X.PARAEXP, gd)  # mode mismatch
+
+
 # ---- 1D viscous Burgers ------------------------------------------------------------------
 def bu1_ctx(X, n, nu, T, K, P, M=25, m=30, tol=1e-10, phi=None, memory=None):
     ctx = X.Context()
@@ -305,6 +339,20 @@ def test_burgers_cluster_checkpoint_recompute(X, torch, bu_small):
     ctx.set_target(gd_)
     out = torch.empty_like(fd)
     J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out), b["grad"]) < 1e-10
+
+
+def test_burgers_autotune_and_split_solves(X, torch, bu_small):
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    assert ctx.autotune(X.PARAEXP, out) > 0
+    J = ctx.solve_direct(X.PARAEXP)
+    ctx.solve_adjoint(X.PARAEXP, out)
     assert abs(J - b["J"]) / b["J"] < 1e-10
     assert rel(host(out), b["grad"]) < 1e-10
 
