@@ -38,6 +38,10 @@ WORKLOADS = {
                       tol=1e-9, label="1D viscous Burgers n=1024 nu=0.005 T=2 RK4 dt=1e-4 FP64 P=32"),
     "advdiff1d": dict(kind="advdiff1d", n=256, c=1.0, nu=0.01, T=1.0, K=4096, P=8, m=30, sub=1,
                       tol=1e-11, label="1D advection-diffusion n=256 nu=0.01 T=1 CN 4096 steps FP64 P=8 m=30"),
+    "advdiff2d": dict(kind="advdiff2d", n=512, nu=1e-3, T=1.0, K=1024, P=64,
+                      label="2D advection-diffusion 512x512 nu=1e-3 T=1 RK4 1024 steps FP32 stepping P=64"),
+    "advdiff2d_lanes": dict(kind="lanes2d", n=2048, lanes=64, steps=10,
+                            label="2D RK4 FP32 lanes kernel, 64 lanes x 2048^2 (1 GiB per state array)"),
 }
 
 # Algorithmic FP64 operations per grid point per step of each kernel.
@@ -63,6 +67,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="burgers1d", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="grid size override for the 2D workloads")
     return ap.parse_args()
 
 
@@ -367,6 +372,104 @@ def run_reference(args, w, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def inputs_2d(n):
+    from paper_2004_00546_gb300 import inputs as I
+
+    u, v = I.streamfunction_velocity(n, n, 8, 2006)
+    x = I.grid1d(n)
+    X, Y = np.meshgrid(x, x)
+    return u, v, np.ones((n, n)), np.sin(X) * np.sin(Y)
+
+
+def ctx_2d(X, torch, w, n, P, K):
+    u, v, f, ft = inputs_2d(n)
+    keep = [torch.as_tensor(a.reshape(-1), device="cuda") for a in (u, v, f, ft)]
+    ctx = X.Context()
+    ctx.set_operator_2d(n, n, keep[0], keep[1], w.get("nu", 1e-3))
+    ctx.set_time(w.get("T", 1.0), K, X.RK4, P)
+    ctx.set_krylov(20, 1e-10, X.PHI_STEPPER, 1)
+    ctx.set_control(keep[2], 1.0)
+    ctx.set_target(keep[3])
+    return ctx, keep
+
+
+def run_lanes2d(args, w):
+    """HBM roofline of the 2D FP32 RK4 lanes kernel (TMA halo tiles) at a size far
+    above L2: algorithmic bytes = lanes * n^2 * (4 read + 4 write) per step."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    n = args.n or w["n"]
+    lanes, steps = w["lanes"], max(args.steps, 2)
+    ctx, keep = ctx_2d(X, torch, {"nu": 1e-3, "T": 1.0}, n, 1, 1024)
+    for _ in range(max(args.warmup, 1)):
+        ctx.rk4_lanes_2d(lanes, 2)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms = ctx.rk4_lanes_2d(lanes, steps)
+    alg = lanes * n * n * 8.0 * steps
+    peak = measured_hbm_peak()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"metric": "HBM GB/s of the 2D FP32 RK4 lanes kernel", "value": gbs, "unit": "GB/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": w["label"].replace("2048", str(n)), "lanes": lanes},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "peak_kind": "measured copy bandwidth"},
+            "clocks": clk.summary(), "gpu_launches": steps}
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def run_2d(args, w, rank, world):
+    """2D advection-diffusion: serial FP32 stepping vs the hybrid Paraexp adjoint."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    n = args.n or w["n"]
+    ctx, keep = ctx_2d(X, torch, w, n, w["P"], w["K"])
+    grad = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    variants, grads = {}, {}
+    for name, mode in (("paraexp_stepper", X.PARAEXP), ("serial", X.SERIAL)):
+        times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
+        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name}
+        grads[name] = g.detach().cpu().numpy()
+    variants["paraexp_stepper"]["rel_diff_vs_gpu_serial"] = float(
+        np.linalg.norm(grads["paraexp_stepper"] - grads["serial"]) / np.linalg.norm(grads["serial"]))
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        times, phases, _ = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush, timing=True)
+    total_ms = float(sum(times))
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in
+          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom")}
+    cpu = {}
+    if rank == 0:
+        import oracle as O
+
+        u, v, f, ft = inputs_2d(n)
+        Ks = 16
+        t0 = time.perf_counter()
+        O.ad2_gradient_serial(f, ft, u, v, w["nu"], w["T"] * Ks / w["K"], Ks, omega=1.0)
+        dt_cpu = (time.perf_counter() - t0) * w["K"] / Ks
+        cpu = {"value": 1.0 / dt_cpu, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {Ks} of {w['K']} steps (direct + adjoint), scaled by {Ks}/{w['K']}"}
+    return {"metric": METRIC, "value": args.steps / (total_ms / 1e3), "unit": "gradient evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 stepping, f64 accumulation", "data": "synthetic",
+            "config": {"workload": w["label"].replace("512x512", f"{n}x{n}"), "l2": "flushed between steps"},
+            "variants": variants, "phases_ms": ph, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": None}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -383,7 +486,12 @@ def main():
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    line = run_ours(args, w, rank, world)
+    if w["kind"] == "lanes2d":
+        line = run_lanes2d(args, w)
+    elif w["kind"] == "advdiff2d":
+        line = run_2d(args, w, rank, world)
+    else:
+        line = run_ours(args, w, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

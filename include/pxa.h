@@ -18,6 +18,14 @@
  *                                  + nu (q_{i+1}-2 q_i+q_{i-1})/h^2,  periodic,
  *                   x_i = i h, h = L/n; Crank–Nicolson stepping; control = q(0);
  *                   objective J = 0.5 ||q(T)||^2.
+ *   PXA_ADVDIFF_2D: dq/dt = A q + s(t) f, (A q) = -u q_x - v q_y + nu (q_xx + q_yy) by
+ *                   central differences on a periodic nx x ny grid with a frozen
+ *                   velocity (u, v); q(0) = 0; control = f; the target is the
+ *                   trajectory driven by f_true (pxa_set_target), J = (1/T) sum_{j=1..K}
+ *                   dt ||q_j(f) - q_j(f_true)||^2 (Eq. cost). RK4 stepping in FP32 on
+ *                   TMA-staged halo tiles; J and the gradient accumulate in FP64.
+ *                   Serial direct + Paraexp adjoint (hybrid scheme, Sec. 3.3) with the
+ *                   stepper's own propagator for the homogeneous parts.
  *   PXA_BURGERS_1D: du/dt = -u du/dx + nu d2u/dx2 + s(t) f(x), u(0) = 0, central
  *                   differences, periodic; classical RK4; control = f;
  *                   s(t) = sin(omega t) (omega != 0) or 1; objective
@@ -65,7 +73,7 @@ typedef enum {
   PXA_ERR_TOO_LARGE = -8       /* request exceeds the fixed buffer of pxa_expv_static */
 } pxa_status;
 
-typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2 } pxa_problem;
+typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2, PXA_ADVDIFF_2D = 3 } pxa_problem;
 typedef enum { PXA_CN = 1, PXA_RK4 = 2 } pxa_stepper;
 /* Homogeneous propagator. EXP: exp(t A) (the paper's choice). STEPPER: the stepper's
  * own amplification R(dt A)^k (R_CN(z) = (1+z/2)/(1-z/2)), which makes Paraexp
@@ -81,10 +89,13 @@ typedef enum { PXA_STORE_FULL = 0, PXA_STORE_CHECKPOINTS = 1 } pxa_memory;
 
 typedef struct {
   int kind;   /* pxa_problem */
-  int n;      /* grid points, 3 <= n <= 4096 */
-  double L;   /* domain length (> 0), h = L / n */
+  int n;      /* 1D: grid points, 3 <= n <= 4096; 2D: ignored (set to nx * ny) */
+  double L;   /* domain length (> 0), h = L / n (2D: L / nx on both axes) */
   double c;   /* advection speed (PXA_ADVDIFF_1D) */
   double nu;  /* diffusion coefficient (>= 0) */
+  int nx, ny; /* PXA_ADVDIFF_2D: grid, nx == ny, nx % 4 == 0, 8 <= nx <= 8192 */
+  const double* u_dev; /* PXA_ADVDIFF_2D: velocity components (device, [ny][nx] row-major, */
+  const double* v_dev; /*   x fastest), borrowed until the next set_operator */
 } pxa_operator_desc;
 
 typedef struct {
@@ -129,7 +140,7 @@ int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);
 /* Control (Eq. initupdate / paramupdate): ADVDIFF_1D: q0_dev = initial condition.
  * BURGERS_1D: f_dev = forcing, s(t) = sin(omega t) or 1 when omega == 0. */
 int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
-/* Tracking target g (BURGERS_1D). */
+/* Tracking target g (BURGERS_1D), or the true forcing f_true (ADVDIFF_2D). */
 int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
 /* Direct-state storage policy (pxa_memory). */
 int pxa_set_memory(pxa_ctx* ctx, int policy);
@@ -195,6 +206,14 @@ int pxa_expv(pxa_ctx* ctx, int transpose, int64_t span_steps, int substeps,
  * y = J(u)^T x (transposed Jacobian). */
 int pxa_burgers_rhs(pxa_ctx* ctx, const double* u_dev, double* y_dev);
 int pxa_burgers_jac_T(pxa_ctx* ctx, const double* u_dev, const double* x_dev, double* y_dev);
+
+/* ADVDIFF_2D: `steps` FP32 RK4 steps of `lanes` zero-initial-value inhomogeneous
+ * lanes (Eq. linInhomEqus with the forcing s(t) f of the configured control; lane l
+ * starts at step l * steps) on the TMA halo-tile kernel, timed with CUDA events on the
+ * context's stream. Allocates its own lane states (2 * lanes padded FP32 arrays) on the
+ * first call for a given lane count. *ms_host receives the elapsed time; out_dev
+ * (optional, lanes * nx * ny doubles) receives the final lane states. */
+int pxa_rk4_lanes_2d(pxa_ctx* ctx, int lanes, int64_t steps, double* out_dev, double* ms_host);
 
 /* ---- allocation-free Krylov propagation ----------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that must

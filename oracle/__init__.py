@@ -65,6 +65,10 @@ def lib():
                 "pxo_expm": [_i, _p, _p],
                 "pxo_ad1_krylov_expv": [_i, _d, _d, _d, _d, _i, _p, _p, _p],
                 "pxo_partition_nonequi": [_d, _i, _d, _p],
+                "pxo_ad2_apply": [_i, _i, _d, _d, _p, _p, _p, _p],
+                "pxo_ad2_apply_T": [_i, _i, _d, _d, _p, _p, _p, _p],
+                "pxo_ad2_rk4_step": [_i, _i, _d, _d, _p, _p, _d, _d, _d, _p, _p, _p],
+                "pxo_ad2_gradient_serial": [_i, _i, _d, _d, _p, _p, _d, _i64, _d, _p, _p, _p, _p],
             }
             for name, argt in sigs.items():
                 fn = getattr(L, name)
@@ -219,3 +223,32 @@ def partition_nonequi(T, N, k):
     out = np.empty(N + 1)
     _check(lib().pxo_partition_nonequi(T, N, k, _ptr(out)), "partition_nonequi")
     return out
+
+
+# ---- 2D advection-diffusion (arrays shaped (ny, nx)) -------------------------------------
+def ad2_apply(q, u, v, nu, L=TWO_PI, transpose=False):
+    q, u, v = _in(q), _in(u), _in(v)
+    ny, nx = q.shape
+    out = np.empty_like(q)
+    fn = lib().pxo_ad2_apply_T if transpose else lib().pxo_ad2_apply
+    _check(fn(nx, ny, L, nu, _ptr(u), _ptr(v), _ptr(q), _ptr(out)), "ad2_apply")
+    return out
+
+
+def ad2_rk4_step(q, u, v, nu, dt, f, t=0.0, omega=0.0, L=TWO_PI):
+    q, u, v, f = _in(q), _in(u), _in(v), _in(f)
+    ny, nx = q.shape
+    out = np.empty_like(q)
+    _check(lib().pxo_ad2_rk4_step(nx, ny, L, nu, _ptr(u), _ptr(v), dt, t, omega, _ptr(f), _ptr(q),
+                                  _ptr(out)), "ad2_rk4_step")
+    return out
+
+
+def ad2_gradient_serial(f, f_true, u, v, nu, T, K, omega=1.0, L=TWO_PI):
+    f, ft, u, v = _in(f), _in(f_true), _in(u), _in(v)
+    ny, nx = f.shape
+    J = ctypes.c_double()
+    g = np.empty_like(f)
+    _check(lib().pxo_ad2_gradient_serial(nx, ny, L, nu, _ptr(u), _ptr(v), T, int(K), omega, _ptr(f),
+                                         _ptr(ft), ctypes.byref(J), _ptr(g)), "ad2_serial")
+    return J.value, g

@@ -782,3 +782,125 @@ int pxo_partition_nonequi(double T, int N, double k, double* out) {
   for (int j = 0; j <= N; ++j) out[j] = T * (1.0 - pow(r, j)) / den;
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* 2D linear advection-diffusion with a frozen velocity field (Sec. 4.2).     */
+/* ------------------------------------------------------------------------- */
+static int bad_grid2(int nx, int ny, double L) { return nx < 3 || ny < 3 || nx != ny || !(L > 0.0); }
+
+int pxo_ad2_apply(int nx, int ny, double L, double nu, const double* u, const double* v,
+                  const double* q, double* out) {
+  if (bad_grid2(nx, ny, L) || !u || !v || !q || !out) return -1;
+  double h = L / nx;
+  for (int j = 0; j < ny; ++j) {
+    int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
+    for (int i = 0; i < nx; ++i) {
+      int im = (i - 1 + nx) % nx, ip = (i + 1) % nx;
+      size_t c = (size_t)j * nx + i;
+      double qx = (q[(size_t)j * nx + ip] - q[(size_t)j * nx + im]) / (2.0 * h);
+      double qy = (q[(size_t)jp * nx + i] - q[(size_t)jm * nx + i]) / (2.0 * h);
+      double lap = (q[(size_t)j * nx + ip] + q[(size_t)j * nx + im] + q[(size_t)jp * nx + i] +
+                    q[(size_t)jm * nx + i] - 4.0 * q[c]) / (h * h);
+      out[c] = -u[c] * qx - v[c] * qy + nu * lap;
+    }
+  }
+  return 0;
+}
+
+/* Transpose, entry by entry: A[(j,i),(j,i+1)] = -u_{j,i}/(2h) + nu/h^2,
+ * A[(j,i),(j,i-1)] = +u_{j,i}/(2h) + nu/h^2, likewise in y with v, and
+ * A[(j,i),(j,i)] = -4 nu/h^2. So (A^T l)_{j,i} = sum over the four neighbours r of
+ * A[r,(j,i)] l_r: the west neighbour's row holds (j,i) as its east entry, etc. */
+int pxo_ad2_apply_T(int nx, int ny, double L, double nu, const double* u, const double* v,
+                    const double* q, double* out) {
+  if (bad_grid2(nx, ny, L) || !u || !v || !q || !out) return -1;
+  double h = L / nx;
+  for (int j = 0; j < ny; ++j) {
+    int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
+    for (int i = 0; i < nx; ++i) {
+      int im = (i - 1 + nx) % nx, ip = (i + 1) % nx;
+      size_t c = (size_t)j * nx + i;
+      size_t w = (size_t)j * nx + im, e = (size_t)j * nx + ip;
+      size_t s = (size_t)jm * nx + i, n = (size_t)jp * nx + i;
+      /* neighbour west (j,i-1): its row has (j,i) as its east neighbour */
+      double a_w = -u[w] / (2.0 * h) + nu / (h * h);
+      /* neighbour east (j,i+1): (j,i) is its west neighbour */
+      double a_e = u[e] / (2.0 * h) + nu / (h * h);
+      double a_s = -v[s] / (2.0 * h) + nu / (h * h);
+      double a_n = v[n] / (2.0 * h) + nu / (h * h);
+      out[c] = a_w * q[w] + a_e * q[e] + a_s * q[s] + a_n * q[n] - 4.0 * nu / (h * h) * q[c];
+    }
+  }
+  return 0;
+}
+
+int pxo_ad2_rk4_step(int nx, int ny, double L, double nu, const double* u, const double* v,
+                     double dt, double t, double omega, const double* f, const double* q,
+                     double* out) {
+  if (bad_grid2(nx, ny, L) || !u || !v || !f || !q || !out) return -1;
+  size_t N = (size_t)nx * ny, nb = sizeof(double) * N;
+  double *k1 = malloc(nb), *k2 = malloc(nb), *k3 = malloc(nb), *k4 = malloc(nb), *y = malloc(nb);
+  double s1 = forcing_s(omega, t), s2 = forcing_s(omega, t + 0.5 * dt), s4 = forcing_s(omega, t + dt);
+  pxo_ad2_apply(nx, ny, L, nu, u, v, q, k1);
+  for (size_t i = 0; i < N; ++i) k1[i] += s1 * f[i];
+  for (size_t i = 0; i < N; ++i) y[i] = q[i] + 0.5 * dt * k1[i];
+  pxo_ad2_apply(nx, ny, L, nu, u, v, y, k2);
+  for (size_t i = 0; i < N; ++i) k2[i] += s2 * f[i];
+  for (size_t i = 0; i < N; ++i) y[i] = q[i] + 0.5 * dt * k2[i];
+  pxo_ad2_apply(nx, ny, L, nu, u, v, y, k3);
+  for (size_t i = 0; i < N; ++i) k3[i] += s2 * f[i];
+  for (size_t i = 0; i < N; ++i) y[i] = q[i] + dt * k3[i];
+  pxo_ad2_apply(nx, ny, L, nu, u, v, y, k4);
+  for (size_t i = 0; i < N; ++i) k4[i] += s4 * f[i];
+  for (size_t i = 0; i < N; ++i) out[i] = q[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  free(k1); free(k2); free(k3); free(k4); free(y);
+  return 0;
+}
+
+int pxo_ad2_gradient_serial(int nx, int ny, double L, double nu, const double* u,
+                            const double* v, double T, int64_t K, double omega,
+                            const double* f, const double* f_true, double* J, double* grad) {
+  if (bad_grid2(nx, ny, L) || K < 1 || !u || !v || !f || !f_true || !J || !grad) return -1;
+  size_t N = (size_t)nx * ny, nb = sizeof(double) * N;
+  double dt = T / (double)K;
+  double* d = malloc(nb);
+  double* traj = malloc(nb * (size_t)(K + 1));
+  if (!d || !traj) return -1;
+  for (size_t i = 0; i < N; ++i) d[i] = f[i] - f_true[i];
+  /* direct: the response e to the forcing f - f_true from e(0) = 0 */
+  memset(traj, 0, nb);
+  double Jacc = 0.0;
+  for (int64_t s = 0; s < K; ++s) {
+    pxo_ad2_rk4_step(nx, ny, L, nu, u, v, dt, s * dt, omega, d, traj + (size_t)s * N,
+                     traj + (size_t)(s + 1) * N);
+    double acc = 0.0;
+    for (size_t i = 0; i < N; ++i) acc += traj[(size_t)(s + 1) * N + i] * traj[(size_t)(s + 1) * N + i];
+    Jacc += dt / T * acc;
+  }
+  *J = Jacc;
+  /* adjoint: reverse of the four stages of the linear RK4 map */
+  double *lam = malloc(nb), *mu = malloc(nb), *nv = malloc(nb), *acc = malloc(nb);
+  memset(grad, 0, nb);
+  for (size_t i = 0; i < N; ++i) lam[i] = 2.0 * dt / T * traj[(size_t)K * N + i];
+  for (int64_t s = K - 1; s >= 0; --s) {
+    double t = s * dt;
+    double s1 = forcing_s(omega, t), s2 = forcing_s(omega, t + 0.5 * dt), s4 = forcing_s(omega, t + dt);
+    for (size_t i = 0; i < N; ++i) acc[i] = lam[i];
+    for (size_t i = 0; i < N; ++i) mu[i] = dt / 6.0 * lam[i];            /* kbar4 */
+    for (size_t i = 0; i < N; ++i) grad[i] += s4 * mu[i];
+    pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);                        /* Ybar4 */
+    for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 3.0 * lam[i] + dt * nv[i]; }
+    for (size_t i = 0; i < N; ++i) grad[i] += s2 * mu[i];
+    pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);                        /* Ybar3 */
+    for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 3.0 * lam[i] + 0.5 * dt * nv[i]; }
+    for (size_t i = 0; i < N; ++i) grad[i] += s2 * mu[i];
+    pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);                        /* Ybar2 */
+    for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 6.0 * lam[i] + 0.5 * dt * nv[i]; }
+    for (size_t i = 0; i < N; ++i) grad[i] += s1 * mu[i];
+    pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);                        /* Ybar1 */
+    for (size_t i = 0; i < N; ++i)
+      lam[i] = acc[i] + nv[i] + (s >= 1 ? 2.0 * dt / T * traj[(size_t)s * N + i] : 0.0);
+  }
+  free(d); free(traj); free(lam); free(mu); free(nv); free(acc);
+  return 0;
+}

@@ -89,6 +89,26 @@ int pxo_bu1_gradient_hybrid(int n, double L, double nu, double T, int64_t K, dou
                             int P, int hom_mode, int M_mag, int m_kry, const double* u0,
                             const double* f, const double* g, double* J, double* grad);
 
+/* ---- 2D linear advection-diffusion with a frozen velocity field (Sec. 4.2) ----
+ * Grid [ny][nx] row-major (x fastest), h = L/nx = L/ny (nx == ny required), periodic:
+ * (A q)_{j,i} = -u_{j,i} (q_{j,i+1}-q_{j,i-1})/(2h) - v_{j,i} (q_{j+1,i}-q_{j-1,i})/(2h)
+ *              + nu (q_{j,i+1}+q_{j,i-1}+q_{j+1,i}+q_{j-1,i}-4 q_{j,i})/h^2.          */
+int pxo_ad2_apply(int nx, int ny, double L, double nu, const double* u, const double* v,
+                  const double* q, double* out);
+int pxo_ad2_apply_T(int nx, int ny, double L, double nu, const double* u, const double* v,
+                    const double* q, double* out);
+/* One RK4 step of dq/dt = A q + s(t) f at time t, s(t) = sin(omega t) (1 if omega == 0). */
+int pxo_ad2_rk4_step(int nx, int ny, double L, double nu, const double* u, const double* v,
+                     double dt, double t, double omega, const double* f, const double* q,
+                     double* out);
+/* Serial direct-adjoint loop, forcing control f, zero initial value, tracking of the
+ * trajectory driven by f_true: J = (1/T) sum_{j=1..K} dt ||q_j(f) - q_j(f_true)||^2.
+ * By linearity q(f) - q(f_true) is the response to the forcing f - f_true, which is
+ * what is stepped. Exact discrete adjoint of the RK4 map. */
+int pxo_ad2_gradient_serial(int nx, int ny, double L, double nu, const double* u,
+                            const double* v, double T, int64_t K, double omega,
+                            const double* f, const double* f_true, double* J, double* grad);
+
 /* ---- small dense and Krylov building blocks ------------------------------- */
 /* Dense matrix exponential (row-major d x d), scaling and squaring of a Taylor
  * series evaluated in long double.                                              */

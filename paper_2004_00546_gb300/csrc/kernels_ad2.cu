@@ -1,0 +1,605 @@
+// kernels_ad2.cu — 2D advection-diffusion with a frozen velocity field (Sec. 4.2),
+// FP32 RK4 stepping on halo tiles staged in shared memory by TMA.
+//
+// State layout (per lane, FP32): a padded array [ny + 2G][nx + 2G], G = 4 ghost
+// layers holding periodic copies, so that every tile's halo is a plain rectangle of
+// global memory. One CTA owns a TX x TY tile; its (TX+2G) x (TY+2G) halo tile and the
+// coefficient tiles (u, v, forcing) arrive by cp.async.bulk.tensor (TMA) completing on
+// an mbarrier. The four RK4 stages are fused in shared memory on shrinking regions
+// (halo 3, 2, 1, 0), so one time step reads the state once and writes it once: the
+// kernel is bound by HBM (FP32: 8 bytes and ~60 flop per point per step). Edge tiles
+// also write the periodic ghost copies of their points.
+//
+// The transposed kernel runs one reverse step of the exact discrete adjoint of the
+// linear RK4 map (four applications of A^T fused on halo 3..0 from a halo-4 tile),
+// adds the objective's source read from the stored direct trajectory, and
+// accumulates the forcing gradient (FP32 per step, FP64 across steps).
+//
+// Paper mapping: Eq. seriesDirect (serial direct of the hybrid scheme),
+// Eq. hybadjinhom (adjoint lanes), Eq. adjHomNormal with the stepper's own
+// propagator (homogeneous chain), Eq. paramupdate / Eq. update (forcing gradient).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels_ad2.cuh"
+
+namespace pxa {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ double forcing_s(double omega, double t) {
+  return omega == 0.0 ? 1.0 : sin(omega * t);
+}
+
+// (A x)_c on a tile (row pitch BX2): advective central differences + 5-point Laplacian.
+__device__ __forceinline__ float A_at(const Ad2Params& p, const float* x, const float* u,
+                                      const float* v, int c) {
+  float xe = x[c + 1], xw = x[c - 1], xn = x[c + BX2], xs = x[c - BX2], x0 = x[c];
+  float qx = (xe - xw) * p.inv2h, qy = (xn - xs) * p.inv2h;
+  float lap = (xe + xw + xn + xs - 4.0f * x0) * p.invh2;
+  return -u[c] * qx - v[c] * qy + p.nu * lap;
+}
+
+// (A^T x)_c: the west neighbour's row holds c as its east entry, and so on.
+__device__ __forceinline__ float AT_at(const Ad2Params& p, const float* x, const float* u,
+                                       const float* v, int c) {
+  const float d = p.nu * p.invh2;
+  float aw = -u[c - 1] * p.inv2h + d, ae = u[c + 1] * p.inv2h + d;
+  float as = -v[c - BX2] * p.inv2h + d, an = v[c + BX2] * p.inv2h + d;
+  return aw * x[c - 1] + ae * x[c + 1] + as * x[c - BX2] + an * x[c + BX2] - 4.0f * d * x[c];
+}
+
+// Store value `val` of domain point (x, y) into a padded array and into its periodic
+// ghost copies. With nx, ny >= 2G a point has at most one alias per axis.
+__device__ __forceinline__ void store_with_ghosts(float* dst, const Ad2Params& p, int x, int y,
+                                                  float val) {
+  const int X = x + G2, Y = y + G2;
+  dst[(size_t)Y * p.Wp + X] = val;
+  const bool xl = x < G2, xh = x >= p.nx - G2, yl = y < G2, yh = y >= p.ny - G2;
+  if (!(xl | xh | yl | yh)) return;
+  const int Xa = xl ? X + p.nx : X - p.nx;
+  const int Ya = yl ? Y + p.ny : Y - p.ny;
+  const bool hx = xl | xh, hy = yl | yh;
+  if (hx) dst[(size_t)Y * p.Wp + Xa] = val;
+  if (hy) dst[(size_t)Ya * p.Wp + X] = val;
+  if (hx && hy) dst[(size_t)Ya * p.Wp + Xa] = val;
+}
+
+struct TileSmem {
+  float* coef;  // [3][TILE2] u, v, forcing
+  float* q[2];  // double-buffered state tiles
+  float* ya;
+  float* yb;
+  float* acc;
+  uint64_t* bar;  // [3]: coef, q[0], q[1]
+  double* red;    // 40
+  float* sc;      // 8: s(t) at the three stage times, double-buffered by lane parity
+};
+
+__device__ __forceinline__ TileSmem carve(unsigned char* raw) {
+  TileSmem t;
+  float* f = reinterpret_cast<float*>(raw);
+  t.coef = f;
+  t.q[0] = f + 3 * TILE2;
+  t.q[1] = f + 4 * TILE2;
+  t.ya = f + 5 * TILE2;
+  t.yb = f + 6 * TILE2;
+  t.acc = f + 7 * TILE2;
+  t.bar = reinterpret_cast<uint64_t*>(f + 8 * TILE2);
+  t.red = reinterpret_cast<double*>(t.bar + 4);
+  t.sc = reinterpret_cast<float*>(t.red + 40);
+  return t;
+}
+
+}  // namespace
+
+size_t ad2_smem_bytes() {
+  return (size_t)8 * TILE2 * sizeof(float) + 4 * sizeof(uint64_t) + 40 * sizeof(double) + 8 * sizeof(float);
+}
+
+// One RK4 time step of dq/dt = A q + s(t) f for a group of lanes on one tile.
+//
+// Thread layout: 64 columns x 4 row groups. Thread (tx, ty) owns tile column tx + 1
+// and RG consecutive rows of the halo-3 region, for every lane and every stage, so
+// that the stencil coefficients of its points (cE, cW, cN, cS from u, v; the forcing)
+// are computed once per CTA and kept in registers, vertical neighbours come from its
+// own registers, and only horizontal neighbours and the two strip ends go through
+// shared memory (stage values ping-pong between two tile buffers, one barrier per
+// stage). Lane l (global index) is at absolute step l * lane_k + s_local.
+// in/out: padded state arrays of the ping-pong pair, tensor-map z = buf * map_lanes + l.
+// traj (optional): interior of lane 0's new state as row traj_row. Jpart (WITH_J):
+// tile partial of (dt/T) ||q_new||^2 at Jpart[jrow * tiles + tile].
+template <bool WITH_J>
+__global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__ CUtensorMap qmap,
+                                                         const __grid_constant__ CUtensorMap cmap,
+                                                         Ad2Params p, float* __restrict__ states,
+                                                         int lanes, int map_lanes, int lanes_per_cta,
+                                                         int buf_in, int64_t lane_k, int64_t s_local,
+                                                         float* __restrict__ traj, int64_t traj_row,
+                                                         double* __restrict__ Jpart, int64_t jrow,
+                                                         double dt_over_T, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem t = carve(smem_raw);
+  const int tile = blockIdx.x;
+  const int tbx = tile % p.tiles_x, tby = tile / p.tiles_x;
+  const int x0 = tbx * TX2, y0 = tby * TY2;  // padded coordinates of the halo corner
+  const int l_begin = blockIdx.y * lanes_per_cta;
+  const int l_end = min(lanes, l_begin + lanes_per_cta);
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int col = tx + 1;                       // tile column
+  const bool colact = col <= BX2 - 2;           // inside the halo-3 region [1, BX2-1)
+  const int row0 = 1 + ty * RG2;                // first owned row
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&t.bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
+    tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in * map_lanes + l_begin, &t.bar[1]);
+  }
+  float* outbase = states + (size_t)(1 - buf_in) * map_lanes * p.Hp * p.Wp;
+  bool ok = mbar_wait(&t.bar[0], 0);
+  if (!ok) {
+    if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    return;
+  }
+  // per-point stencil coefficients: (A x)_c = cE x_e + cW x_w + cN x_n + cS x_s + cC x_c
+  const float d = p.nu * p.invh2, cC = -4.0f * d;
+  float cE[RG2], cW[RG2], cN[RG2], cS[RG2], fr[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int c = (row0 + i) * BX2 + col;
+    const float uu = t.coef[c], vv = t.coef[TILE2 + c];
+    cE[i] = -uu * p.inv2h + d;
+    cW[i] = uu * p.inv2h + d;
+    cN[i] = -vv * p.inv2h + d;
+    cS[i] = vv * p.inv2h + d;
+    fr[i] = t.coef[2 * TILE2 + c];
+  }
+  const float dt = p.dt, hdt = 0.5f * p.dt, sdt = p.dt / 6.0f;
+  float* Y0 = t.ya;
+  float* Y1 = t.yb;
+  // s(t) at the three stage times, evaluated once per lane by one thread (FP64 sin is
+  // 64x slower than FP32 arithmetic) into a double-buffered slot of 4 floats per lane
+  if (threadIdx.x == 0) {
+    const double tabs = (double)((int64_t)l_begin * lane_k + s_local) * p.dtd;
+    t.sc[0] = (float)forcing_s(p.omega, tabs);
+    t.sc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
+    t.sc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
+  }
+  __syncthreads();
+  for (int l = l_begin; l < l_end; ++l) {
+    const int li = l - l_begin;
+    if (threadIdx.x == 0 && l + 1 < l_end) {  // prefetch the next lane's tile
+      // order the generic-proxy reads of this buffer (previous lane) before the TMA write
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&t.bar[1 + ((li + 1) & 1)], TILE2 * sizeof(float));
+      tma_load_3d(t.q[0] + ((li + 1) & 1) * TILE2, &qmap, x0, y0, buf_in * map_lanes + l + 1, &t.bar[1 + ((li + 1) & 1)]);
+    }
+    ok = mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1);
+    if (!ok) {
+      if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+      return;
+    }
+    const float* Q = t.q[0] + (li & 1) * TILE2;
+    const float c1 = t.sc[4 * (li & 1) + 0], c2 = t.sc[4 * (li & 1) + 1], c4 = t.sc[4 * (li & 1) + 2];
+    float qv[RG2], acc[RG2], yv[RG2];
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) qv[i] = Q[(row0 + i) * BX2 + col];
+    // stage 1 on the halo-3 region (every owned point): neighbours from the q tile
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) {
+      const int c = (row0 + i) * BX2 + col;
+      const float xs = i > 0 ? qv[i - 1] : Q[c - BX2];
+      const float xn = i + 1 < RG2 ? qv[i + 1] : Q[c + BX2];
+      float k = cE[i] * Q[c + 1] + cW[i] * Q[c - 1] + cN[i] * xn + cS[i] * xs + cC * qv[i] + c1 * fr[i];
+      acc[i] = k;
+      yv[i] = qv[i] + hdt * k;
+      if (colact) Y0[c] = yv[i];
+    }
+    __syncthreads();
+    // stages 2 and 3: every owned point is updated (uniform work, no divergence at the
+    // barriers); values on the outer rings that read not-yet-valid neighbours are never
+    // used, because the valid region shrinks by one ring per stage and stage 4 stores
+    // only the interior. Vertical neighbours come from registers, horizontal ones and
+    // the strip ends from the previous stage's buffer.
+#pragma unroll
+    for (int stg = 2; stg <= 3; ++stg) {
+      const float* Xp = stg == 2 ? Y0 : Y1;
+      float* Xn = stg == 2 ? Y1 : Y0;
+      const float a = stg == 2 ? hdt : dt;
+      float prev = 0.0f;
+#pragma unroll
+      for (int i = 0; i < RG2; ++i) {
+        const int c = (row0 + i) * BX2 + col;
+        const float cur = yv[i];
+        const float xs = i > 0 ? prev : Xp[c - BX2];
+        const float xn = i + 1 < RG2 ? yv[i + 1] : Xp[c + BX2];
+        prev = cur;
+        float k = cE[i] * Xp[c + 1] + cW[i] * Xp[c - 1] + cN[i] * xn + cS[i] * xs + cC * cur + c2 * fr[i];
+        acc[i] += 2.0f * k;
+        yv[i] = qv[i] + a * k;
+        if (colact) Xn[c] = yv[i];
+      }
+      __syncthreads();
+    }
+    // stage 4 on the interior: q_new = q + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    float* out = outbase + (size_t)l * p.Hp * p.Wp;
+    double jl = 0.0;
+    {
+      const float* Xp = Y0;
+      const bool cin = col >= G2 && col < G2 + TX2;
+      const int x = x0 + col - G2;  // domain column (x0 is the halo corner in padded coordinates)
+      float prev = 0.0f;
+#pragma unroll
+      for (int i = 0; i < RG2; ++i) {
+        const int row = row0 + i;
+        const int c = row * BX2 + col;
+        const float cur = yv[i];
+        const float xs = i > 0 ? prev : Xp[c - BX2];
+        const float xn = i + 1 < RG2 ? yv[i + 1] : Xp[c + BX2];
+        prev = cur;
+        const int y = y0 + row - G2;
+        if (cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny) {
+          float k = cE[i] * Xp[c + 1] + cW[i] * Xp[c - 1] + cN[i] * xn + cS[i] * xs + cC * cur + c4 * fr[i];
+          float qn = qv[i] + sdt * (acc[i] + k);
+          store_with_ghosts(out, p, x, y, qn);
+          if (traj && l == 0) traj[(size_t)traj_row * p.nx * p.ny + (size_t)y * p.nx + x] = qn;
+          if (WITH_J) jl += (double)(qn * qn);
+        }
+      }
+    }
+    if (WITH_J) {
+      double s = block_sum(jl, t.red);
+      if (threadIdx.x == 0) Jpart[(size_t)jrow * gridDim.x + tile] = dt_over_T * s;
+    }
+    if (threadIdx.x == 0 && l + 1 < l_end) {
+      const double tabs = (double)((int64_t)(l + 1) * lane_k + s_local) * p.dtd;
+      float* nsc = t.sc + 4 * ((li + 1) & 1);
+      nsc[0] = (float)forcing_s(p.omega, tabs);
+      nsc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
+      nsc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
+    }
+    __syncthreads();  // all reads of q[li & 1] and the stage buffers done before reuse
+  }
+}
+
+// One reverse step of the exact discrete adjoint of the RK4 map for a group of lanes:
+// lambda_s = M^T lambda_{s+1} (+ (2dt/T) e_s when with_source and s_local > 0), and
+// G += sum of the stage terms s_i kbar_i (the forcing gradient, FP64 accumulator).
+// Lane l is at absolute step l * lane_k + s_local (its time lane_base + ...).
+__global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ CUtensorMap qmap,
+                                                       const __grid_constant__ CUtensorMap cmap,
+                                                       Ad2Params p, float* __restrict__ states,
+                                                       int lanes, int map_lanes, int lanes_per_cta,
+                                                       int buf_in, int64_t lane_k, int64_t lane_off,
+                                                       int64_t s_local, int with_source,
+                                                       const float* __restrict__ traj,
+                                                       double src_scale, double* __restrict__ G,
+                                                       int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem t = carve(smem_raw);
+  const int tile = blockIdx.x;
+  const int tbx = tile % p.tiles_x, tby = tile / p.tiles_x;
+  const int x0 = tbx * TX2, y0 = tby * TY2;
+  const int l_begin = blockIdx.y * lanes_per_cta;
+  const int l_end = min(lanes, l_begin + lanes_per_cta);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&t.bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
+    tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in * map_lanes + l_begin, &t.bar[1]);
+  }
+  const float* u = t.coef;
+  const float* v = t.coef + TILE2;
+  float* outbase = states + (size_t)(1 - buf_in) * map_lanes * p.Hp * p.Wp;
+  bool ok = mbar_wait(&t.bar[0], 0);
+  const float dt = p.dt;
+  float* ma = t.ya;
+  float* mb = t.yb;
+  float* Ln = t.acc;
+  for (int l = l_begin; l < l_end; ++l) {
+    const int li = l - l_begin;
+    if (threadIdx.x == 0 && l + 1 < l_end) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&t.bar[1 + ((li + 1) & 1)], TILE2 * sizeof(float));
+      tma_load_3d(t.q[0] + ((li + 1) & 1) * TILE2, &qmap, x0, y0, buf_in * map_lanes + l + 1, &t.bar[1 + ((li + 1) & 1)]);
+    }
+    ok = mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1) && ok;
+    if (!ok) {
+      if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+      return;
+    }
+    const float* L = t.q[0] + (li & 1) * TILE2;
+    const int64_t s_abs = lane_off + (int64_t)l * lane_k + s_local;
+    if (threadIdx.x == 0) {
+      const double tabs = (double)s_abs * p.dtd;
+      t.sc[0] = (float)forcing_s(p.omega, tabs);
+      t.sc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
+      t.sc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
+    }
+    __syncthreads();
+    const float c1 = t.sc[0], c2 = t.sc[1], c4 = t.sc[2];
+    // kbar4 = dt/6 lambda on the whole halo-4 tile
+    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) ma[e] = dt / 6.0f * L[e];
+    __syncthreads();
+    // halo 3: Ybar4 = A^T kbar4; kbar3 = dt/3 lambda + dt Ybar4; Ln = lambda + Ybar4
+    for (int e = threadIdx.x; e < (TX2 + 6) * (TY2 + 6); e += blockDim.x) {
+      int c = (G2 - 3 + e / (TX2 + 6)) * BX2 + (G2 - 3 + e % (TX2 + 6));
+      float nv = AT_at(p, ma, u, v, c);
+      mb[c] = dt / 3.0f * L[c] + dt * nv;
+      Ln[c] = L[c] + nv;
+    }
+    __syncthreads();
+    // the gradient terms in FP32 per step, kept in registers per interior point below;
+    // halo 2: Ybar3 = A^T kbar3; kbar2 = dt/3 lambda + dt/2 Ybar3
+    // (kbar4 is still in ma on the interior: read it before ma is overwritten)
+    float g4[ (TX2 * TY2 + 255) / 256 ];
+#pragma unroll
+    for (int q = 0; q < (TX2 * TY2 + 255) / 256; ++q) {
+      int e = threadIdx.x + q * 256;
+      int c = (G2 + e / TX2) * BX2 + (G2 + e % TX2);
+      g4[q] = c4 * ma[c] + c2 * mb[c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (TX2 + 4) * (TY2 + 4); e += blockDim.x) {
+      int c = (G2 - 2 + e / (TX2 + 4)) * BX2 + (G2 - 2 + e % (TX2 + 4));
+      float nv = AT_at(p, mb, u, v, c);
+      Ln[c] += nv;
+      ma[c] = dt / 3.0f * L[c] + 0.5f * dt * nv;
+    }
+    __syncthreads();
+    // halo 1: Ybar2 = A^T kbar2; kbar1 = dt/6 lambda + dt/2 Ybar2
+    for (int e = threadIdx.x; e < (TX2 + 2) * (TY2 + 2); e += blockDim.x) {
+      int c = (G2 - 1 + e / (TX2 + 2)) * BX2 + (G2 - 1 + e % (TX2 + 2));
+      float nv = AT_at(p, ma, u, v, c);
+      Ln[c] += nv;
+      mb[c] = dt / 6.0f * L[c] + 0.5f * dt * nv;
+    }
+    __syncthreads();
+    // interior: Ybar1 = A^T kbar1; lambda_s = Ln + Ybar1 (+ source); gradient terms
+    float* out = outbase + (size_t)l * p.Hp * p.Wp;
+    double* Gl = G + (size_t)l * p.nx * p.ny;
+    const float* es = traj ? traj + (size_t)s_abs * p.nx * p.ny : nullptr;
+#pragma unroll
+    for (int q = 0; q < (TX2 * TY2 + 255) / 256; ++q) {
+      int e = threadIdx.x + q * 256;
+      const int xx = e % TX2, yy = e / TX2;
+      const int c = (G2 + yy) * BX2 + (G2 + xx);
+      const int x = x0 + xx, y = y0 + yy;
+      if (e >= TX2 * TY2 || x >= p.nx || y >= p.ny) continue;
+      float nv = AT_at(p, mb, u, v, c);
+      float lam = Ln[c] + nv;
+      const size_t gi = (size_t)y * p.nx + x;
+      if (with_source && s_local > 0) lam += (float)src_scale * es[gi];
+      store_with_ghosts(out, p, x, y, lam);
+      float gstep = g4[q] + c2 * ma[c] + c1 * mb[c];
+      Gl[gi] += (double)gstep;
+    }
+    __syncthreads();
+  }
+}
+
+// Pack u, v (FP64, [ny][nx]) and the forcing f - f_true into the padded FP32
+// coefficient array [3][Hp][Wp] with periodic ghosts.
+__global__ void ad2_pack_coef_kernel(Ad2Params p, const double* __restrict__ u,
+                                     const double* __restrict__ v, const double* __restrict__ f,
+                                     const double* __restrict__ ft, float* __restrict__ coef) {
+  const size_t plane = (size_t)p.Hp * p.Wp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.nx * p.ny; i += gridDim.x * blockDim.x) {
+    int x = i % p.nx, y = i / p.nx;
+    store_with_ghosts(coef, p, x, y, (float)u[i]);
+    store_with_ghosts(coef + plane, p, x, y, (float)v[i]);
+    store_with_ghosts(coef + 2 * plane, p, x, y, (float)(f[i] - (ft ? ft[i] : 0.0)));
+  }
+}
+
+// Fill lanes' padded states: zero (src == nullptr), or scale * row(row0 + l*row_step)
+// of the FP32 trajectory (the adjoint's terminal source of each lane), or, when `add`
+// is set, state += padded vector `addv` (FP32 padded, per call one lane).
+__global__ void ad2_fill_kernel(Ad2Params p, float* __restrict__ states, int lanes,
+                                const float* __restrict__ traj, int64_t row0, int64_t row_step,
+                                double scale) {
+  const size_t plane = (size_t)p.Hp * p.Wp;
+  const size_t N = (size_t)p.nx * p.ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N * lanes;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int l = (int)(i / N);
+    size_t r = i % N;
+    int x = (int)(r % p.nx), y = (int)(r / p.nx);
+    float val = traj ? (float)(scale * traj[(size_t)(row0 + (int64_t)l * row_step) * N + r]) : 0.0f;
+    store_with_ghosts(states + (size_t)l * plane, p, x, y, val);
+  }
+}
+
+// dst (padded, one lane) += src (padded, one lane), ghosts included.
+__global__ void ad2_add_padded_kernel(size_t count, float* __restrict__ dst, const float* __restrict__ src) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
+// J = sum of the per-(step, tile) partials, in a fixed order (one block).
+__global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t count, double* J, int* status) {
+  extern __shared__ double red[];
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < count; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    *J = s;
+    if (!isfinite(s)) set_status(status, PXA_ERR_NONFINITE);
+  }
+}
+
+// grad = sum over lanes of G[l] (+ extra), FP64.
+__global__ void ad2_sum_grad_kernel(size_t N, int lanes, const double* __restrict__ G,
+                                    const double* __restrict__ extra, double* __restrict__ grad,
+                                    int* status) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    double acc = extra ? extra[i] : 0.0;
+    for (int l = 0; l < lanes; ++l) acc += G[(size_t)l * N + i];
+    grad[i] = acc;
+    if (!isfinite(acc)) set_status(status, PXA_ERR_NONFINITE);
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3D tiled map over `depth` padded planes [Hp][Wp] of FP32 with box (BX2, BY2, box_depth).
+bool ad2_make_map(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_depth) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)p.Wp, (cuuint64_t)p.Hp, (cuuint64_t)depth};
+  cuuint64_t strides[2] = {(cuuint64_t)p.Wp * sizeof(float), (cuuint64_t)p.Wp * p.Hp * sizeof(float)};
+  cuuint32_t box[3] = {(cuuint32_t)BX2, (cuuint32_t)BY2, (cuuint32_t)box_depth};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static cudaError_t set_smem(const void* fn) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ad2_smem_bytes());
+}
+
+cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
+                           const Ad2Params& p, float* states, int lanes, int map_lanes,
+                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, float* traj,
+                           int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
+                           int* status) {
+  dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
+  if (Jpart) {
+    cudaError_t e = set_smem((const void*)ad2_rk4_kernel<true>);
+    if (e != cudaSuccess) return e;
+    ad2_rk4_kernel<true><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
+                                                              lanes_per_cta, buf_in, lane_k, s_local,
+                                                              traj, traj_row, Jpart, jrow, dt_over_T,
+                                                              status);
+  } else {
+    cudaError_t e = set_smem((const void*)ad2_rk4_kernel<false>);
+    if (e != cudaSuccess) return e;
+    ad2_rk4_kernel<false><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
+                                                               lanes_per_cta, buf_in, lane_k, s_local,
+                                                               traj, traj_row, Jpart, jrow, dt_over_T,
+                                                               status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
+                            const Ad2Params& p, float* states, int lanes, int map_lanes,
+                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
+                            int with_source, const float* traj, double src_scale, double* G,
+                            int* status) {
+  cudaError_t e = set_smem((const void*)ad2_rk4T_kernel);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
+  ad2_rk4T_kernel<<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
+                                                       lanes_per_cta, buf_in, lane_k, lane_off, s_local,
+                                                       with_source, traj, src_scale, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const double* u,
+                                 const double* v, const double* f, const double* ft, float* coef) {
+  int threads = 256, blocks = (p.nx * p.ny + threads - 1) / threads;
+  ad2_pack_coef_kernel<<<blocks, threads, 0, st>>>(p, u, v, f, ft, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
+                            const float* traj, int64_t row0, int64_t row_step, double scale) {
+  size_t total = (size_t)p.nx * p.ny * lanes;
+  int threads = 256;
+  int blocks = (int)((total + threads - 1) / threads);
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  ad2_fill_kernel<<<blocks, threads, 0, st>>>(p, states, lanes, traj, row0, row_step, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, const float* src) {
+  int threads = 256;
+  int blocks = (int)((count + threads - 1) / threads);
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  ad2_add_padded_kernel<<<blocks, threads, 0, st>>>(count, dst, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* J, int* status) {
+  ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(part, count, J, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
+                                const double* extra, double* grad, int* status) {
+  int threads = 256;
+  int blocks = (int)((N + threads - 1) / threads);
+  ad2_sum_grad_kernel<<<blocks, threads, 0, st>>>(N, lanes, G, extra, grad, status);
+  return cudaGetLastError();
+}
+
+}  // namespace pxa

@@ -1,0 +1,46 @@
+// kernels_ad2.cuh — constants, parameters and launch wrappers of the 2D kernels.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pxa {
+
+constexpr int G2 = 4;                // ghost layers of the padded 2D arrays
+constexpr int TX2 = 56, TY2 = 34;    // tile interior (TX2 % 4 == 0 for 16-byte TMA x offsets)
+constexpr int BX2 = TX2 + 2 * G2;    // 64 floats = 256 bytes (a multiple of 16 for TMA)
+constexpr int BY2 = TY2 + 2 * G2;    // 42 rows
+constexpr int TILE2 = BX2 * BY2;     // 2688 floats = 10752 bytes (a multiple of 128)
+constexpr int RG2 = (BY2 - 2) / 4;   // rows of the halo-3 region owned by one thread (10)
+static_assert((BY2 - 2) % 4 == 0, "the halo-3 rows split evenly over the 4 row groups");
+static_assert(BX2 - 2 <= 64, "one thread per halo-3 column");
+
+struct Ad2Params {
+  int nx, ny, Wp, Hp, tiles_x, tiles_y;
+  float inv2h, invh2, nu, dt;
+  double dtd, omega;
+};
+
+size_t ad2_smem_bytes();
+bool ad2_make_map(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_depth);
+cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
+                           const Ad2Params& p, float* states, int lanes, int map_lanes,
+                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, float* traj,
+                           int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
+                           int* status);
+cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
+                            const Ad2Params& p, float* states, int lanes, int map_lanes,
+                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
+                            int with_source, const float* traj, double src_scale, double* G,
+                            int* status);
+cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const double* u,
+                                 const double* v, const double* f, const double* ft, float* coef);
+cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
+                            const float* traj, int64_t row0, int64_t row_step, double scale);
+cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, const float* src);
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* J, int* status);
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
+                                const double* extra, double* grad, int* status);
+
+}  // namespace pxa

@@ -11,6 +11,7 @@
 
 #include "../../include/pxa.h"
 #include "kernels_1d.cuh"
+#include "kernels_ad2.cuh"
 
 using namespace pxa;
 
@@ -68,6 +69,21 @@ struct pxa_ctx {
 
   int direct_mode = -1;  // mode of the last pxa_solve_direct whose state is still valid
 
+  // 2D advection-diffusion workspace (FP32 padded states, TMA maps)
+  Ad2Params p2{};
+  float* coef2 = nullptr;   // [3][Hp][Wp]
+  float* stD = nullptr;     // direct ping-pong [2][1][Hp][Wp]
+  float* stA = nullptr;     // adjoint lanes ping-pong [2][P][Hp][Wp]
+  float* stC = nullptr;     // homogeneous chain ping-pong [2][1][Hp][Wp]
+  float* traj2 = nullptr;   // [(K+1)][ny*nx] FP32 direct trajectory
+  double* Jpart = nullptr;  // [K][tiles]
+  double* G2buf = nullptr;  // [P][ny*nx] FP64 lane gradients
+  double* GC = nullptr;     // [ny*nx] FP64 chain gradient
+  CUtensorMap mapD, mapA, mapC, mapCoef;
+  float* stL = nullptr;     // pxa_rk4_lanes_2d states [2][lanesL][Hp][Wp]
+  int lanesL = 0;
+  CUtensorMap mapL;
+
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   int g_mode = -1;
@@ -109,6 +125,9 @@ void release_workspace(pxa_ctx* c) {
   c->taps = c->E = c->EA = c->src = c->srcA = c->hsum = c->hsumA = c->qT = c->tmp = nullptr;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
   c->status = nullptr;
+  c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
+  c->lanesL = 0;
+  c->Jpart = c->G2buf = c->GC = nullptr;
 }
 
 void invalidate(pxa_ctx* c) {
@@ -202,22 +221,55 @@ int prepare(pxa_ctx* c) {
   if ((rc = alloc(c, &c->Jdev, 1))) return rc;
   if ((rc = alloc(c, &c->errmax, 1))) return rc;
   if ((rc = alloc(c, &c->status, 1))) return rc;
-  if ((rc = alloc(c, &c->E, (size_t)P * n))) return rc;
-  if ((rc = alloc(c, &c->EA, (size_t)P * n))) return rc;
-  if ((rc = alloc(c, &c->src, n))) return rc;
-  if ((rc = alloc(c, &c->srcA, n))) return rc;
-  if ((rc = alloc(c, &c->hsum, n))) return rc;
-  if ((rc = alloc(c, &c->hsumA, n))) return rc;
-  if ((rc = alloc(c, &c->qT, n))) return rc;
-  if ((rc = alloc(c, &c->tmp, n))) return rc;
   if ((rc = alloc(c, &c->ctl_buf, n))) return rc;
   if ((rc = alloc(c, &c->grad_buf, n))) return rc;
-  // Krylov basis: in shared memory when it fits beside the dense scratch
-  int extra = c->op.kind == PXA_ADVDIFF_1D ? n : 5 * (n + 2) + n;
-  size_t with_v = krylov_smem_bytes(n, c->kry_m, extra, true);
-  c->v_in_smem = with_v <= 200 * 1024;
-  if ((rc = alloc(c, &c->V, (size_t)(c->kry_m + 1) * n))) return rc;
-  if (c->op.kind == PXA_ADVDIFF_1D) {
+  if (c->op.kind != PXA_ADVDIFF_2D) {
+    if ((rc = alloc(c, &c->E, (size_t)P * n))) return rc;
+    if ((rc = alloc(c, &c->EA, (size_t)P * n))) return rc;
+    if ((rc = alloc(c, &c->src, n))) return rc;
+    if ((rc = alloc(c, &c->srcA, n))) return rc;
+    if ((rc = alloc(c, &c->hsum, n))) return rc;
+    if ((rc = alloc(c, &c->hsumA, n))) return rc;
+    if ((rc = alloc(c, &c->qT, n))) return rc;
+    if ((rc = alloc(c, &c->tmp, n))) return rc;
+    // Krylov basis: in shared memory when it fits beside the dense scratch
+    int extra = c->op.kind == PXA_ADVDIFF_1D ? n : 5 * (n + 2) + n;
+    size_t with_v = krylov_smem_bytes(n, c->kry_m, extra, true);
+    c->v_in_smem = with_v <= 200 * 1024;
+    if ((rc = alloc(c, &c->V, (size_t)(c->kry_m + 1) * n))) return rc;
+  }
+  if (c->op.kind == PXA_ADVDIFF_2D) {
+    Ad2Params& a = c->p2;
+    a.nx = c->op.nx;
+    a.ny = c->op.ny;
+    a.Wp = a.nx + 2 * G2;
+    a.Hp = a.ny + 2 * G2;
+    a.tiles_x = (a.nx + TX2 - 1) / TX2;
+    a.tiles_y = (a.ny + TY2 - 1) / TY2;
+    const double h = c->op.L / a.nx;
+    a.inv2h = (float)(1.0 / (2.0 * h));
+    a.invh2 = (float)(1.0 / (h * h));
+    a.nu = (float)c->op.nu;
+    a.dtd = c->T / (double)c->K;
+    a.dt = (float)a.dtd;
+    a.omega = 0.0;
+    const size_t plane = (size_t)a.Hp * a.Wp, N = (size_t)a.nx * a.ny;
+    if ((rc = alloc(c, &c->coef2, 3 * plane))) return rc;
+    if ((rc = alloc(c, &c->stD, 2 * plane))) return rc;
+    if ((rc = alloc(c, &c->stA, 2 * (size_t)P * plane))) return rc;
+    if ((rc = alloc(c, &c->stC, 2 * plane))) return rc;
+    if ((rc = alloc(c, &c->traj2, (size_t)(c->K + 1) * N))) return rc;
+    if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y))) return rc;
+    if ((rc = alloc(c, &c->G2buf, (size_t)P * N))) return rc;
+    if ((rc = alloc(c, &c->GC, N))) return rc;
+    PXA_CUDA(c, cudaMemset(c->coef2, 0, sizeof(float) * 3 * plane), "memset coef");
+    PXA_CUDA(c, cudaMemset(c->stD, 0, sizeof(float) * 2 * plane), "memset");
+    PXA_CUDA(c, cudaMemset(c->stA, 0, sizeof(float) * 2 * (size_t)P * plane), "memset");
+    PXA_CUDA(c, cudaMemset(c->stC, 0, sizeof(float) * 2 * plane), "memset");
+    if (!ad2_make_map(&c->mapD, c->stD, a, 2, 1) || !ad2_make_map(&c->mapA, c->stA, a, 2 * P, 1) ||
+        !ad2_make_map(&c->mapC, c->stC, a, 2, 1) || !ad2_make_map(&c->mapCoef, c->coef2, a, 3, 3))
+      return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D state arrays");
+  } else if (c->op.kind == PXA_ADVDIFF_1D) {
     double dt = c->T / (double)c->K;
     if ((rc = cn_band(c, n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r))) return rc;
     if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
@@ -372,11 +424,78 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   return PXA_OK;
 }
 
+// ---- 2D advection-diffusion (forcing control, tracking of the f_true trajectory) ----
+int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
+  cudaStream_t st = c->stream;
+  Ad2Params a = c->p2;
+  a.omega = c->omega;
+  const bool do_d = parts & 1, do_a = parts & 2;
+  const int64_t K = c->K;
+  const int P = mode == PXA_SERIAL ? 1 : c->P;
+  const int64_t k = K / P;
+  const size_t N = (size_t)a.nx * a.ny, plane = (size_t)a.Hp * a.Wp;
+  const int tiles = a.tiles_x * a.tiles_y;
+  const double src = 2.0 * a.dtd / c->T;
+  if (mode == PXA_PARAEXP && c->kry_phi != PXA_PHI_STEPPER)
+    return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D Paraexp uses the stepper propagator (PXA_PHI_STEPPER)");
+  PXA_CUDA(c, launch_ad2_pack_coef(st, a, c->op.u_dev, c->op.v_dev, c->control, c->target, c->coef2),
+           "pack coefficients");
+  if (do_d) {
+    ev_record(c, 0);
+    // Eq. seriesDirect: serial FP32 RK4 of the response to f - f_true, storing every state
+    PXA_CUDA(c, cudaMemsetAsync(c->stD, 0, sizeof(float) * plane, st), "zero state");
+    PXA_CUDA(c, cudaMemsetAsync(c->traj2, 0, sizeof(float) * N, st), "zero row 0");
+    for (int64_t s = 0; s < K; ++s) {
+      PXA_CUDA(c, launch_ad2_rk4(st, c->mapD, c->mapCoef, a, c->stD, 1, 1, 1, (int)(s & 1), 0, s,
+                                 c->traj2, s + 1, c->Jpart, s, a.dtd / c->T, c->status),
+               "2d direct step");
+    }
+    PXA_CUDA(c, launch_ad2_reduce_J(st, c->Jpart, (size_t)K * tiles, Jdev, c->status), "reduce J");
+    ev_record(c, 1);
+  }
+  if (!do_a) return PXA_OK;
+  ev_record(c, 2);
+  PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(double) * (size_t)P * N, st), "zero G");
+  PXA_CUDA(c, cudaMemsetAsync(c->GC, 0, sizeof(double) * N, st), "zero GC");
+  // Eq. hybadjinhom: lane l starts from the objective's source at its top row (l+1) k
+  PXA_CUDA(c, launch_ad2_fill(st, a, c->stA, P, c->traj2, k, k, src), "lane init");
+  const int lpc = P >= 16 ? 16 : P;
+  for (int64_t j = 0; j < k; ++j) {
+    PXA_CUDA(c, launch_ad2_rk4T(st, c->mapA, c->mapCoef, a, c->stA, P, P, lpc, (int)(j & 1), k, 0,
+                                k - 1 - j, 1, c->traj2, src, c->G2buf, c->status),
+             "2d adjoint lanes");
+  }
+  ev_record(c, 3);
+  if (P > 1) {
+    // Eq. adjHomNormal with the stepper's own propagator: h = sum of the lane values
+    // W_{l+1} carried down subinterval by subinterval, no source
+    const float* Wbuf = c->stA + (size_t)(k & 1) * P * plane;
+    PXA_CUDA(c, cudaMemsetAsync(c->stC, 0, sizeof(float) * plane, st), "zero chain");
+    int bufc = 0;
+    for (int lane = P - 2; lane >= 0; --lane) {
+      PXA_CUDA(c, launch_ad2_add_padded(st, plane, c->stC + (size_t)bufc * plane,
+                                        Wbuf + (size_t)(lane + 1) * plane), "chain add");
+      for (int64_t j = 0; j < k; ++j) {
+        PXA_CUDA(c, launch_ad2_rk4T(st, c->mapC, c->mapCoef, a, c->stC, 1, 1, 1, bufc, 0,
+                                    (int64_t)lane * k, k - 1 - j, 0, nullptr, 0.0, c->GC, c->status),
+                 "2d chain step");
+        bufc ^= 1;
+      }
+    }
+  }
+  ev_record(c, 4);
+  PXA_CUDA(c, launch_ad2_sum_grad(st, N, P, c->G2buf, P > 1 ? c->GC : nullptr, grad, c->status), "sum grad");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
 int enqueue_parts(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (mode != PXA_SERIAL && mode != PXA_PARAEXP) return fail(c, PXA_ERR_INVALID, "mode");
   if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first");
   if (c->op.kind == PXA_BURGERS_1D && !c->target) return fail(c, PXA_ERR_STATE, "set_target first");
+  if (c->op.kind == PXA_ADVDIFF_2D && !c->target) return fail(c, PXA_ERR_STATE, "set_target (f_true) first");
   if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, parts, Jdev, grad);
+  if (c->op.kind == PXA_ADVDIFF_2D) return enqueue_ad2(c, mode, parts, Jdev, grad);
   return enqueue_bu1(c, mode, parts, Jdev, grad);
 }
 
@@ -435,8 +554,19 @@ const char* pxa_last_error(const pxa_ctx* c) { return c ? c->err.c_str() : "null
 
 int pxa_set_operator(pxa_ctx* c, const pxa_operator_desc* op) {
   if (!c || !op) return PXA_ERR_INVALID;
-  if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D)
+  if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D && op->kind != PXA_ADVDIFF_2D)
     return fail(c, PXA_ERR_INVALID, "operator kind");
+  if (op->kind == PXA_ADVDIFF_2D) {
+    if (op->nx != op->ny || op->nx % 4 != 0 || op->nx < 8 || op->nx > 8192 || !(op->L > 0.0) ||
+        !(op->nu >= 0.0) || !op->u_dev || !op->v_dev)
+      return fail(c, PXA_ERR_INVALID, "2D operator (nx == ny, nx % 4 == 0, 8 <= nx <= 8192, velocity)");
+    c->op = *op;
+    c->op.n = op->nx * op->ny;
+    c->have_op = true;
+    release_workspace(c);
+    invalidate(c);
+    return PXA_OK;
+  }
   if (op->n < 3 || op->n > 4096 || !(op->L > 0.0) || !(op->nu >= 0.0))
     return fail(c, PXA_ERR_INVALID, "operator parameters (3 <= n <= 4096, L > 0, nu >= 0)");
   c->op = *op;
@@ -456,6 +586,7 @@ int pxa_set_time(pxa_ctx* c, double T, int64_t K, int stepper, int P) {
   if (!c->have_op) return fail(c, PXA_ERR_STATE, "set_operator first");
   if (c->op.kind == PXA_ADVDIFF_1D && stepper != PXA_CN) return fail(c, PXA_ERR_INVALID, "ADVDIFF_1D uses PXA_CN");
   if (c->op.kind == PXA_BURGERS_1D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "BURGERS_1D uses PXA_RK4");
+  if (c->op.kind == PXA_ADVDIFF_2D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D uses PXA_RK4");
   if (c->op.kind == PXA_BURGERS_1D && K < 4) return fail(c, PXA_ERR_INVALID, "K >= 4 for time interpolation");
   c->T = T;
   c->K = K;
@@ -808,6 +939,54 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   rc = read_status(c);
   if (err_host) *err_host = c->stats.krylov_err_max;
   return rc;
+}
+
+int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, double* ms_host) {
+  if (!c || lanes < 1 || steps < 1) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_ADVDIFF_2D) return fail(c, PXA_ERR_STATE, "ADVDIFF_2D operator required");
+  if (!c->control || !c->target) return fail(c, PXA_ERR_STATE, "set_control and set_target first");
+  int rc = prepare(c);
+  if (rc) return rc;
+  Ad2Params a = c->p2;
+  a.omega = c->omega;
+  const size_t plane = (size_t)a.Hp * a.Wp, N = (size_t)a.nx * a.ny;
+  if (c->lanesL != lanes) {
+    if ((rc = alloc(c, &c->stL, 2 * (size_t)lanes * plane))) return rc;
+    if (!ad2_make_map(&c->mapL, c->stL, a, 2 * lanes, 1))
+      return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the lane states");
+    c->lanesL = lanes;
+  }
+  cudaStream_t st = c->stream;
+  PXA_CUDA(c, launch_ad2_pack_coef(st, a, c->op.u_dev, c->op.v_dev, c->control, c->target, c->coef2), "pack");
+  PXA_CUDA(c, cudaMemsetAsync(c->stL, 0, sizeof(float) * (size_t)lanes * plane, st), "zero lanes");
+  cudaEvent_t e0, e1;
+  PXA_CUDA(c, cudaEventCreate(&e0), "event");
+  PXA_CUDA(c, cudaEventCreate(&e1), "event");
+  const int lpc = lanes >= 16 ? 16 : lanes;
+  PXA_CUDA(c, cudaEventRecord(e0, st), "record");
+  for (int64_t s = 0; s < steps; ++s)
+    PXA_CUDA(c, launch_ad2_rk4(st, c->mapL, c->mapCoef, a, c->stL, lanes, lanes, lpc, (int)(s & 1),
+                               steps, s, nullptr, 0, nullptr, 0, 0.0, c->status), "lanes step");
+  PXA_CUDA(c, cudaEventRecord(e1, st), "record");
+  PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_host) *ms_host = ms;
+  if (out_dev) {
+    // copy the interiors of the final states (buffer steps & 1) out as FP64
+    std::vector<float> tmp(plane);
+    std::vector<double> row(N);
+    const float* fin = c->stL + (size_t)(steps & 1) * lanes * plane;
+    for (int l = 0; l < lanes; ++l) {
+      PXA_CUDA(c, cudaMemcpy(tmp.data(), fin + (size_t)l * plane, sizeof(float) * plane, cudaMemcpyDeviceToHost), "copy");
+      for (int y = 0; y < a.ny; ++y)
+        for (int x = 0; x < a.nx; ++x) row[(size_t)y * a.nx + x] = tmp[(size_t)(y + G2) * a.Wp + x + G2];
+      PXA_CUDA(c, cudaMemcpy(out_dev + (size_t)l * N, row.data(), sizeof(double) * N, cudaMemcpyHostToDevice), "copy");
+    }
+  }
+  return read_status(c);
 }
 
 int pxa_burgers_rhs(pxa_ctx* c, const double* u_dev, double* y_dev) {

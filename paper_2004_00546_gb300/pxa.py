@@ -17,7 +17,7 @@ OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINIT
     0, -1, -2, -3, -4, -5, -6, -7)
 ERR_TOO_LARGE = -8
 EXPV_STATIC_MAX_DOUBLES = 131072
-ADVDIFF_1D, BURGERS_1D = 1, 2
+ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D = 1, 2, 3
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
 SERIAL, PARAEXP = 0, 1
@@ -33,6 +33,7 @@ EXPORTS = [
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
+    "pxa_rk4_lanes_2d",
 ]
 
 
@@ -44,7 +45,8 @@ class PxaError(RuntimeError):
 
 class OperatorDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("L", ctypes.c_double),
-                ("c", ctypes.c_double), ("nu", ctypes.c_double)]
+                ("c", ctypes.c_double), ("nu", ctypes.c_double), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("u_dev", ctypes.c_void_p), ("v_dev", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -85,6 +87,7 @@ def load(path: str = LIB_PATH):
         "pxa_set_cluster": [p, i, i, i],
         "pxa_autotune": [p, i, p, p],
         "pxa_solve_direct": [p, i, p],
+        "pxa_rk4_lanes_2d": [p, i, i64, p, p],
         "pxa_solve_adjoint": [p, i, p],
         "pxa_set_timing": [p, i],
         "pxa_gradient": [p, i, p, p],
@@ -161,9 +164,16 @@ class Context:
 
     # -- configuration ---------------------------------------------------------------
     def set_operator(self, kind, n, L=6.283185307179586, c=0.0, nu=0.0):
-        desc = OperatorDesc(kind, n, L, c, nu)
+        desc = OperatorDesc(kind, n, L, c, nu, 0, 0, None, None)
         self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
         self.n = n
+
+    def set_operator_2d(self, nx, ny, u, v, nu, L=6.283185307179586):
+        """2D advection-diffusion with a frozen velocity (u, v: CUDA float64 (ny, nx))."""
+        self._keep["u"], self._keep["v"] = u, v
+        desc = OperatorDesc(ADVDIFF_2D, nx * ny, L, 0.0, nu, nx, ny, _dptr(u).value, _dptr(v).value)
+        self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
+        self.n = nx * ny
 
     def set_time(self, T, K, stepper, P):
         self._check(self._L.pxa_set_time(self._h, T, int(K), stepper, int(P)))
@@ -246,6 +256,12 @@ class Context:
         self._check(self._L.pxa_expv(self._h, int(transpose), int(span_steps), int(substeps),
                                      _dptr(x), _dptr(y), ctypes.byref(err)))
         return err.value
+
+    def rk4_lanes_2d(self, lanes, steps, out=None) -> float:
+        ms = ctypes.c_double()
+        self._check(self._L.pxa_rk4_lanes_2d(self._h, int(lanes), int(steps),
+                                             None if out is None else _dptr(out), ctypes.byref(ms)))
+        return ms.value
 
     def burgers_rhs(self, u, y):
         self._check(self._L.pxa_burgers_rhs(self._h, _dptr(u), _dptr(y)))
