@@ -117,6 +117,26 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_max(x: float) -> float:
+    """Max over the ranks of the process group (identity without one); NCCL reduces on
+    the GPU, gloo on the host."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Replicas: every rank processes units_per_rank units; the job takes the slowest
+    rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def make_inputs(w):
     from paper_2004_00546_gb300 import inputs as I
 
@@ -255,14 +275,8 @@ def run_ours(args, w, rank, world):
     with ClockSampler(dev_index) as clk:
         times, phases, _ = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush,
                                      timing=True)
-    total_ms = float(sum(times))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = reduce_max(float(sum(times)))
+    value = whole_job_rate(args.steps, world, total_ms)
 
     # end to end through the host-buffer entry point: H2D of the control, D2H of the gradient
     ctx.set_timing(False)

@@ -42,7 +42,7 @@ def test_autograd_matches_fused_gradient_and_oracle(env):
     assert float(J.detach()) == J2
     assert torch.equal(g_auto, g_fused)
     Jo, go, _ = O.ad1_cn_gradient_serial(q0, 1.0, 0.02, 0.5, K)
-    assert abs(float(J) - Jo) / Jo < 1e-10
+    assert abs(float(J.detach()) - Jo) / Jo < 1e-10
     assert np.linalg.norm(g_auto.cpu().numpy() - go) / np.linalg.norm(go) < 1e-10
 
 
