@@ -37,7 +37,7 @@ WORKLOADS = {
     "burgers1d": dict(kind="burgers1d", n=1024, nu=0.005, T=2.0, K=20000, P=32, M=25, m=20,
                       tol=1e-9, label="1D viscous Burgers n=1024 nu=0.005 T=2 RK4 dt=1e-4 FP64 P=32"),
     "advdiff1d": dict(kind="advdiff1d", n=256, c=1.0, nu=0.01, T=1.0, K=4096, P=8, m=30, sub=1,
-                      tol=1e-11, label="1D advection-diffusion n=256 nu=0.01 T=1 CN 4096 steps FP64 P=8 m=30"),
+                      tol=1e-11, label="1D advection-diffusion n=256 nu=0.01 T=1 CN 4096 steps FP64 P=8 (Krylov m autotuned)"),
     "advdiff2d": dict(kind="advdiff2d", n=512, nu=1e-3, T=1.0, K=1024, P=64,
                       label="2D advection-diffusion 512x512 nu=1e-3 T=1 RK4 1024 steps FP32 stepping P=64"),
     "advdiff2d_lanes": dict(kind="lanes2d", n=2048, lanes=64, steps=10,
@@ -45,16 +45,22 @@ WORKLOADS = {
 }
 
 # Algorithmic FP64 operations per grid point per step of each kernel.
-FLOPS_RK4_DIRECT = 62.0       # four stages of N(u) + s f (14 each), final update 3, J 3
-FLOPS_RK4_ADJOINT = 109.0     # stage recompute 36, four transposed-Jacobian stages 70, source 3
+FLOPS_RK4_DIRECT = 48.0       # four stages of N(u) + s f (8 each), stage states and weights 13, J 3
+FLOPS_BAND_PREPASS = 190.0    # stage states 36, Jacobian rows 28, tangent column of M_s 124, source 2
+FLOPS_BAND_SWEEP = 18.0       # nine FMAs of a row of M_s^T
+FLOPS_BAND_GRAD = 32.0        # transposed stage recursion kbar4..kbar1 and the weighted sum
+FLOPS_RK4_ADJOINT = 109.0     # stage re-stepping adjoint: recompute 36, four transposed stages 70, source 3
 FLOPS_RK4_ADJOINT_HOM = 106.0  # the same without the objective's source
 FLOPS_CN_BAND_TAP = 2.0       # one FMA per tap of the circulant CN band per point per step
+# FP64 warp instructions on one warp's path per step (the step-time floor is this count
+# x 64 cycles: one FP64 warp instruction per 64 cycles per SM sub-partition on GB300)
+FP64_INSTR_RK4_STEP = 27
+FP64_INSTR_BAND_STEP = 9
+SM_CLOCK_HZ = 2.07e9
 
 # DRAM bytes per launch from the committed ncu captures (profiles/*.md); None when the
 # kernel changed after the capture.
 TRAFFIC = {
-    "bu1c_stepper_chain_kernel": 159.98e6 + 2.99e6,
-    "bu1c_direct_kernel": 1.50e6 + 103.94e6,
     "ad1_chain_kernel": 91.4e3,
     "cn_lanes_kernel": 12.0e3,
 }
@@ -296,24 +302,38 @@ def run_ours(args, w, rank, world):
 
     # roofline of the dominant kernel, from the per-phase CUDA events of the timed steps
     ph = {k: float(np.mean([p[k] for p in phases])) for k in
-          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom")}
+          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_prep", "ms_adjoint_inhom",
+           "ms_adjoint_hom", "ms_total")}
     st = ctx.stats()
     n, K, P = w["n"], w["K"], w["P"]
     k = K // P
+    floors = {}
     if w["kind"] == "burgers1d":
         cl = ctx.cluster_sizes()
         kernels = {
             # name: (ms per launch, algorithmic FP64 flop per launch, SMs used, DRAM bytes per launch)
-            "bu1c_direct_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K, cl[0],
-                                   TRAFFIC.get("bu1c_direct_kernel")),
-            "bu1c_adjoint_lanes_kernel": (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K, P * cl[1],
-                                          TRAFFIC.get("bu1c_adjoint_lanes_kernel")),
+            "bu1_rk4_sweep_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K, cl[0],
+                                     TRAFFIC.get("bu1_rk4_sweep_kernel")),
         }
-        if head == "paraexp_stepper":
-            kernels["bu1c_stepper_chain_kernel"] = (ph["ms_adjoint_hom"],
-                                                    FLOPS_RK4_ADJOINT_HOM * n * k * (P - 1), cl[2],
-                                                    TRAFFIC.get("bu1c_stepper_chain_kernel"))
+        floors["bu1_rk4_sweep_kernel"] = K * FP64_INSTR_RK4_STEP * 64 / SM_CLOCK_HZ * 1e3
+        if st["adjoint_band"]:
+            kernels["bu1_band_prepass_kernel"] = (ph["ms_adjoint_prep"], FLOPS_BAND_PREPASS * n * (K + 1),
+                                                  SMS, TRAFFIC.get("bu1_band_prepass_kernel"))
+            kernels["bu1_band_sweep_kernel (lanes)"] = (ph["ms_adjoint_inhom"], FLOPS_BAND_SWEEP * n * K,
+                                                        P * cl[1], None)
+            if head == "paraexp_stepper":
+                kernels["bu1_band_sweep_kernel (chain)"] = (ph["ms_adjoint_hom"],
+                                                            FLOPS_BAND_SWEEP * n * k * (P - 1), cl[2],
+                                                            TRAFFIC.get("bu1_band_sweep_kernel"))
+                floors["bu1_band_sweep_kernel (chain)"] = (k * (P - 1) * FP64_INSTR_BAND_STEP * 64
+                                                           / SM_CLOCK_HZ * 1e3)
         else:
+            kernels["bu1c_adjoint_lanes_kernel"] = (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K,
+                                                    P * cl[1], None)
+            if head == "paraexp_stepper":
+                kernels["bu1c_stepper_chain_kernel"] = (ph["ms_adjoint_hom"],
+                                                        FLOPS_RK4_ADJOINT_HOM * n * k * (P - 1), cl[2], None)
+        if head != "paraexp_stepper":
             kernels["bu1_magnus_chain_kernel"] = (ph["ms_adjoint_hom"], None, 1, None)
     else:
         m, sub = st["krylov_m"], st["krylov_substeps"]
@@ -339,8 +359,15 @@ def run_ours(args, w, rank, world):
                      "flop_per_launch": flops})
     else:
         roof.update({"achieved": None, "frac": None})
+    if dom in floors:
+        # serial-chain floor: FP64 instructions per step on one warp's path x 64 cycles
+        roof.update({"issue_floor_ms": floors[dom], "frac_of_issue_floor": floors[dom] / ms_dom})
+    roof["kernels_ms"] = {kk: v[0] for kk, v in kernels.items()}
 
-    launches_per_step = {"burgers1d": 4, "advdiff1d": 7}[w["kind"]]
+    if w["kind"] == "burgers1d":
+        launches_per_step = (6 if st["adjoint_band"] else 4) + (1 if w.get("omega", 0.0) else 0)
+    else:
+        launches_per_step = 7
     line = {
         "metric": METRIC, "value": value, "unit": "gradient evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -86,6 +86,14 @@ typedef enum { PXA_SERIAL = 0, PXA_PARAEXP = 1 } pxa_mode;
  * step in HBM; CHECKPOINTS keeps the P+1 subinterval boundaries and recomputes each
  * subinterval inside its adjoint lane. */
 typedef enum { PXA_STORE_FULL = 0, PXA_STORE_CHECKPOINTS = 1 } pxa_memory;
+/* How the BURGERS_1D discrete adjoint (the transpose of the RK4 step map, Sec. 3.3) is
+ * evaluated. BANDED (default): every step's exact transposed Jacobian M_s^T is formed
+ * once as a 9-diagonal band by a parallel pass over the stored (or recomputed) states,
+ * and the adjoint lanes and the homogeneous chain become 9-tap recursions; used when
+ * its records (about 21 doubles per step and grid point) fit in half of the free
+ * device memory. RESTEP: every reverse step re-evaluates the four stages and applies
+ * their transposed Jacobians in turn (no per-step storage beyond the states). */
+typedef enum { PXA_ADJ_BANDED = 0, PXA_ADJ_RESTEP = 1 } pxa_adjoint;
 
 typedef struct {
   int kind;   /* pxa_problem */
@@ -115,6 +123,8 @@ typedef struct {
   int cluster_direct;       /* CTAs per cluster in use (BURGERS_1D) */
   int cluster_lanes;
   int cluster_chain;
+  float ms_adjoint_prep;    /* BURGERS_1D banded adjoint: recompute + band records */
+  int adjoint_band;         /* 1 when the banded adjoint is in use */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -144,6 +154,9 @@ int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
 int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
 /* Direct-state storage policy (pxa_memory). */
 int pxa_set_memory(pxa_ctx* ctx, int policy);
+/* BURGERS_1D adjoint evaluation (pxa_adjoint). BANDED falls back to RESTEP when its
+ * records do not fit; pxa_get_stats reports which one is in use. */
+int pxa_set_adjoint(pxa_ctx* ctx, int impl);
 /* CTAs per thread-block cluster of the BURGERS_1D RK4 kernels: the serial direct
  * lane, each of the P concurrent adjoint lanes, and the homogeneous chain (1..16;
  * 0 = automatic: 16 for the serial lanes, SMs/P for the concurrent lanes, both capped

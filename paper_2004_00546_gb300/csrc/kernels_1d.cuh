@@ -41,9 +41,6 @@ cudaError_t launch_bu1_magnus_chain(cudaStream_t st, int threads, Bu1Grid g, dou
                                     int64_t lane_k, const double* W, double* gH, double* Vglob, int m, double tol,
                                     int v_in_smem, int* status, double* errmax);
 bool bu1c_valid_cluster(int n, int C);
-cudaError_t launch_bu1c_direct(cudaStream_t st, int C, int n, double L, double nu, double dt,
-                               double T, int64_t K, double omega, const double* f, const double* gt,
-                               double* traj, double* ckpt, int64_t ck_every, double* J, int* status);
 cudaError_t launch_bu1c_adjoint_lanes(cudaStream_t st, int C, int lanes, int n, double L, double nu,
                                       double dt, double T, int64_t k, double omega, const double* f,
                                       const double* gt, const double* traj, const double* ckpt,
@@ -52,6 +49,31 @@ cudaError_t launch_bu1c_stepper_chain(cudaStream_t st, int C, int n, double L, d
                                       double T, int64_t k, int P, double omega, const double* f,
                                       const double* gt, const double* rows, int64_t lane_k,
                                       const double* W, double* gH);
+// Serial RK4 sweeps of the Burgers direct problem on clusters (kernels_bu1_rk4.cu).
+bool bu1_rk4_valid_cluster(int n, int C);
+cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, double omega, double* sc);
+cudaError_t launch_bu1_rk4_sweep(cudaStream_t st, int C, int lanes, int n, double L, double nu,
+                                 double dt, int64_t k, const double* f, const double* sc,
+                                 const double* x0, double* out, int64_t lane_rows, const double* gt,
+                                 double T, double* Jdev, double* ckpt, int64_t ck_every,
+                                 int* status);
+
+// Banded discrete adjoint of the Burgers RK4 map (kernels_bu1_band.cu). A record holds
+// the 9 taps of row i of M_s^T and the objective's source dJ/du_s[i].
+constexpr int BU1_BAND_RECORD = 10;
+constexpr int BU1_BAND_MAX_CHUNK = 1024;  // points per CTA of the banded sweep
+bool bu1_band_valid_cluster(int n, int C);
+int bu1_band_grad_blocks(int64_t K, int n);
+cudaError_t launch_bu1_band_prepass(cudaStream_t st, int n, double L, double nu, double dt, double T,
+                                    double omega, const double* f, const double* gt,
+                                    const double* rows, int64_t lane_k, int lanes, int64_t s_begin,
+                                    int64_t s_end, int64_t K, double* rec, double* jt);
+cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int n, const double* rec,
+                                  int64_t k, int P, int chain, const double* W, double* out_rows,
+                                  double* wout, int* status);
+cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
+                                 int64_t h_top, const double* LI, const double* H, const double* jt,
+                                 double* partial, const double* extra, double* grad, int* status);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);
 cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);

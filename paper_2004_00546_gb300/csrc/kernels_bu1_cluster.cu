@@ -128,69 +128,6 @@ __device__ __forceinline__ void rk4_chunk(const Bu1Coef& c, double dt, double c1
 
 }  // namespace
 
-// Serial RK4 of the nonlinear direct problem on one cluster (Eq. seriesDirect).
-// Stores every state (traj) and/or every ck_every-th state (ckpt) and
-// J = (1/T) sum_{j>=1} dt ||u_j - g||^2.
-__global__ void bu1c_direct_kernel(int n, Bu1Coef cf, double dt, double T, int64_t K,
-                                   double omega, const double* __restrict__ f,
-                                   const double* __restrict__ gt, double* __restrict__ traj,
-                                   double* __restrict__ ckpt, int64_t ck_every,
-                                   double* __restrict__ Jdev, int* status) {
-  cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ double sm[];
-  Chunk ch;
-  ch.init(n, (int)cl.num_blocks(), (int)cl.block_rank());
-  const int W = ch.nc + 2 * HD;
-  double* ub[2] = {sm, sm + W};
-  double* ya = sm + 2 * W;
-  double* yb = ya + W;
-  double* acc = yb + W;
-  double* ff = acc + W;
-  double* gg = ff + W;
-  double* red = gg + W;  // 64 doubles: red[0..16) partial sums on rank 0, red[16..) scratch
-  for (int p = -HD + (int)threadIdx.x; p < ch.cnt + HD; p += blockDim.x) {
-    int g = ch.gidx(p);
-    ub[0][HD + p] = 0.0;  // u(0) = 0
-    ff[HD + p] = f[g];
-    gg[HD + p] = gt[g];
-  }
-  for (int p = threadIdx.x; p < ch.cnt; p += blockDim.x) {
-    if (traj) traj[ch.start + p] = 0.0;
-    if (ckpt) ckpt[ch.start + p] = 0.0;
-  }
-  __syncthreads();
-  double jp = 0.0;
-  for (int64_t s = 0; s < K; ++s) {
-    double* u = ub[s & 1];
-    double* un = ub[(s + 1) & 1];
-    const double t = (double)s * dt;
-    rk4_chunk(cf, dt, forcing_s(omega, t), forcing_s(omega, t + 0.5 * dt),
-              forcing_s(omega, t + dt), u, ya, yb, acc, ff, ch.cnt, un);
-    const bool wck = ckpt && ((s + 1) % ck_every == 0);
-    for (int p = threadIdx.x; p < ch.cnt; p += blockDim.x) {
-      double v = un[HD + p];
-      double d = v - gg[HD + p];
-      jp = fma(d, d, jp);
-      if (traj) traj[(size_t)(s + 1) * n + ch.start + p] = v;
-      if (wck) ckpt[(size_t)((s + 1) / ck_every) * n + ch.start + p] = v;
-    }
-    __syncthreads();
-    push_halo<HD>(cl, un, ch);
-    cl.sync();
-  }
-  double part = block_sum(jp, red + 16);
-  double* r0 = cl.map_shared_rank(red, 0);
-  if (threadIdx.x == 0) r0[ch.rank] = part;
-  cl.sync();
-  if (ch.rank == 0 && threadIdx.x == 0) {
-    double J = 0.0;
-    for (int r = 0; r < ch.C; ++r) J += red[r];
-    J *= dt / T;
-    *Jdev = J;
-    if (!isfinite(J)) set_status(status, PXA_ERR_NONFINITE);
-  }
-}
-
 // Address of direct-state row s: contiguous rows (lane_k == 0) or the per-lane
 // recompute layout (lane l holds rows l*k .. l*k+k in a block of k+1 rows).
 __device__ __forceinline__ const double* crow(const double* base, int n, int64_t s, int64_t lane_k,
@@ -456,17 +393,6 @@ bool bu1c_valid_cluster(int n, int C) {
   int nc = (n + C - 1) / C;
   // every CTA owns at least one point (so each is a halo source for its neighbours)
   return (C - 1) * nc < n;
-}
-
-cudaError_t launch_bu1c_direct(cudaStream_t st, int C, int n, double L, double nu, double dt,
-                               double T, int64_t K, double omega, const double* f, const double* gt,
-                               double* traj, double* ckpt, int64_t ck_every, double* J, int* status) {
-  double h = L / n;
-  Bu1Coef cf{1.0 / (2.0 * h), 1.0 / (h * h), nu};
-  int nc = (n + C - 1) / C;
-  size_t sh = sizeof(double) * (7 * (size_t)(nc + 2 * HD) + 64);
-  void* args[] = {&n, &cf, &dt, &T, &K, &omega, &f, &gt, &traj, &ckpt, &ck_every, &J, &status};
-  return launch_cluster((const void*)bu1c_direct_kernel, C, C, cluster_threads(n, C), sh, st, args);
 }
 
 cudaError_t launch_bu1c_adjoint_lanes(cudaStream_t st, int C, int lanes, int n, double L, double nu,

@@ -34,6 +34,7 @@ struct pxa_ctx {
   double omega = 0.0;
   const double* target = nullptr;
   int memory = PXA_STORE_FULL;
+  int band_req = 1;  // pxa_set_adjoint: 1 = banded adjoint when it fits, 0 = stage re-stepping
   bool use_graph = false, timing = false;
   // CTAs per thread-block cluster for the Burgers RK4 kernels (0 = choose automatically)
   int cl_req_direct = 0, cl_req_lanes = 0, cl_req_chain = 0;
@@ -60,6 +61,16 @@ struct pxa_ctx {
   double* V = nullptr;        // Krylov basis (global fallback)
   double* traj = nullptr;     // Burgers direct trajectory (K+1)*n or checkpoints
   double* scratch = nullptr;  // Burgers recompute rows
+  // banded discrete adjoint of the Burgers RK4 map (used when it fits in memory)
+  bool band = false;
+  int cl_band_lanes = 1, cl_band_chain = 1;
+  int cl_rk4_direct = 1, cl_rk4_lanes = 1;  // cluster sizes of the RK4 sweeps (direct, recompute)
+  double* sc = nullptr;       // [K][3] forcing factors s(t) at the stage times (omega != 0)
+  double* rec = nullptr;      // [(K+1)][n][BU1_BAND_RECORD] rows of M_s^T and sources
+  double* jt = nullptr;       // [K][n][BU1_BAND_RECORD] transposed stage rows (gradient)
+  double* LI = nullptr;       // [(K+1)][n] adjoint lane rows
+  double* Hrows = nullptr;    // [(K+1)][n] homogeneous chain rows
+  double* gpart = nullptr;    // [blocks][n] gradient partial sums
   double* Jdev = nullptr;     // 1
   double* errmax = nullptr;   // 1
   int* status = nullptr;      // 1
@@ -92,8 +103,9 @@ struct pxa_ctx {
 
   // statistics
   pxa_stats stats{};
-  cudaEvent_t ev[6] = {};
+  cudaEvent_t ev[7] = {};
   bool ev_ready = false;
+  bool prep_marked = false;  // ev[6] marks the end of the adjoint preparation
 };
 
 namespace {
@@ -128,6 +140,8 @@ void release_workspace(pxa_ctx* c) {
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
   c->lanesL = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
+  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = nullptr;
+  c->band = false;
 }
 
 void invalidate(pxa_ctx* c) {
@@ -283,6 +297,23 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->traj, (size_t)(P + 1) * n))) return rc;
       if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
     }
+    // The banded adjoint keeps two records per step and point plus two lambda
+    // trajectories; it is used when that takes at most half of the free memory,
+    // otherwise the adjoint re-steps the stages (kernels_bu1_cluster.cu).
+    if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
+    const size_t rows1 = (size_t)(c->K + 1) * n;
+    const size_t band_doubles = rows1 * BU1_BAND_RECORD + (size_t)c->K * n * BU1_BAND_RECORD +
+                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n;
+    size_t free_b = 0, total_b = 0;
+    PXA_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    if (c->band_req != 0 && band_doubles * sizeof(double) <= free_b / 2) {
+      if ((rc = alloc(c, &c->rec, rows1 * BU1_BAND_RECORD))) return rc;
+      if ((rc = alloc(c, &c->jt, (size_t)c->K * n * BU1_BAND_RECORD))) return rc;
+      if ((rc = alloc(c, &c->LI, rows1))) return rc;
+      if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
+      if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
+      c->band = true;
+    }
   }
   if (c->op.kind == PXA_BURGERS_1D) {
     // A serial lane gets the widest cluster that keeps >= 32 points per CTA; the P
@@ -299,13 +330,38 @@ int prepare(pxa_ctx* c) {
     c->cl_lanes = c->cl_req_lanes > 0 ? c->cl_req_lanes : widest(P > 0 ? sms / P : 1);
     for (int C : {c->cl_direct, c->cl_chain, c->cl_lanes})
       if (!bu1c_valid_cluster(n, C)) return fail(c, PXA_ERR_INVALID, "cluster size does not fit the grid");
+    // the banded sweep needs >= 4 points per CTA (its halo) and <= 1024: the largest
+    // size not above the requested one that satisfies both, else the smallest that does
+    auto band_size = [&](int want) {
+      for (int C = want; C >= 1; --C)
+        if (bu1_band_valid_cluster(n, C)) return C;
+      for (int C = want + 1; C <= 16; ++C)
+        if (bu1_band_valid_cluster(n, C)) return C;
+      return 0;
+    };
+    c->cl_band_lanes = band_size(c->cl_lanes);
+    c->cl_band_chain = band_size(c->cl_chain);
+    auto rk4_size = [&](int want) {
+      for (int C = want; C >= 1; --C)
+        if (bu1_rk4_valid_cluster(n, C)) return C;
+      for (int C = want + 1; C <= 16; ++C)
+        if (bu1_rk4_valid_cluster(n, C)) return C;
+      return 0;
+    };
+    c->cl_rk4_direct = rk4_size(c->cl_direct);
+    c->cl_rk4_lanes = rk4_size(c->cl_lanes);
+    if (c->cl_rk4_direct == 0 || c->cl_rk4_lanes == 0)
+      return fail(c, PXA_ERR_INVALID, "no cluster size fits the RK4 sweep");
+    if (c->band && (c->cl_band_lanes == 0 || c->cl_band_chain == 0))
+      return fail(c, PXA_ERR_INVALID, "no cluster size fits the banded adjoint sweep");
   }
   PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "memset status");
   c->stats.workspace_bytes = c->ws_bytes;
   c->stats.band_taps = c->op.kind == PXA_ADVDIFF_1D ? 2 * c->band_r + 1 : 0;
-  c->stats.cluster_direct = c->cl_direct;
-  c->stats.cluster_lanes = c->cl_lanes;
-  c->stats.cluster_chain = c->cl_chain;
+  c->stats.cluster_direct = c->op.kind == PXA_BURGERS_1D ? c->cl_rk4_direct : c->cl_direct;
+  c->stats.cluster_lanes = c->band ? c->cl_band_lanes : c->cl_lanes;
+  c->stats.cluster_chain = c->band ? c->cl_band_chain : c->cl_chain;
+  c->stats.adjoint_band = c->band ? 1 : 0;
   c->ready = true;
   return PXA_OK;
 }
@@ -392,16 +448,64 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   const int64_t k = K / P;
   const bool full = c->memory == PXA_STORE_FULL;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
+  const double* sc = nullptr;
+  if (c->omega != 0.0) {
+    PXA_CUDA(c, launch_bu1_forcing_table(st, K, dt, c->omega, c->sc), "forcing table");
+    sc = c->sc;
+  }
   if (do_d) {
     ev_record(c, 0);
-    // direct (Eq. seriesDirect) on one cluster of cl_direct CTAs
-    PXA_CUDA(c, launch_bu1c_direct(st, c->cl_direct, n, c->op.L, c->op.nu, dt, c->T, K, c->omega,
-                                   c->control, c->target, full ? c->traj : nullptr,
-                                   full ? nullptr : c->traj, k, Jdev, c->status), "direct");
+    // direct (Eq. seriesDirect) on one cluster; every state (full storage) or the P+1
+    // subinterval boundaries (checkpoints) are kept
+    PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, K, c->control,
+                                     sc, nullptr, full ? c->traj : nullptr, 0, c->target, c->T, Jdev,
+                                     full ? nullptr : c->traj, k, c->status), "direct");
     ev_record(c, 1);
   }
   if (!do_a) return PXA_OK;
   ev_record(c, 2);
+  if (c->band) {
+    // Banded discrete adjoint: stored (or recomputed) states -> rows of M_s^T (parallel),
+    // P adjoint lanes + the homogeneous chain as 9-tap recursions, then the forcing
+    // gradient over all steps (parallel).
+    const double* rows = c->traj;
+    int64_t lane_k = 0;
+    if (!full) {
+      PXA_CUDA(c, launch_bu1_rk4_sweep(st, P == 1 ? c->cl_rk4_direct : c->cl_rk4_lanes, P, n,
+                                       c->op.L, c->op.nu, dt, k, c->control, sc, c->traj, c->scratch,
+                                       k + 1, nullptr, c->T, nullptr, nullptr, 1, c->status),
+               "recompute");
+      rows = c->scratch;
+      lane_k = k;
+    }
+    PXA_CUDA(c, launch_bu1_band_prepass(st, n, c->op.L, c->op.nu, dt, c->T, c->omega, c->control,
+                                        c->target, rows, lane_k, P, 0, K + 1, K, c->rec, c->jt),
+             "band prepass");
+    if (c->timing && c->ev_ready) {
+      cudaEventRecord(c->ev[6], st);
+      c->prep_marked = true;
+    }
+    PXA_CUDA(c, launch_bu1_band_sweep(st, P == 1 ? c->cl_band_chain : c->cl_band_lanes, P, n, c->rec,
+                                      k, P, 0, nullptr, c->LI, c->E, c->status), "band lanes");
+    ev_record(c, 3);
+    const bool chain = P > 1 && c->kry_phi == PXA_PHI_STEPPER;
+    if (chain) {
+      PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, n, c->rec, k, P, 1, c->E, c->Hrows,
+                                        nullptr, c->status), "band chain");
+    } else if (P > 1) {
+      PXA_CUDA(c, launch_bu1_magnus_chain(st, n > 2048 ? 1024 : 512, g, dt, K, P, k, c->magnus_M,
+                                          c->omega, rows, lane_k, c->E, c->hsum, c->V, c->kry_m,
+                                          c->kry_tol, c->v_in_smem, c->status, c->errmax),
+               "magnus chain");
+    }
+    ev_record(c, 4);
+    PXA_CUDA(c, launch_bu1_band_grad(st, n, dt, c->omega, K, chain ? (int64_t)(P - 1) * k : 0, c->LI,
+                                     chain ? c->Hrows : nullptr, c->jt, c->gpart,
+                                     (P > 1 && !chain) ? c->hsum : nullptr, grad, c->status),
+             "band gradient");
+    ev_record(c, 5);
+    return PXA_OK;
+  }
   const int cl_lane = P == 1 ? c->cl_direct : c->cl_lanes;
   PXA_CUDA(c, launch_bu1c_adjoint_lanes(st, cl_lane, P, n, c->op.L, c->op.nu, dt, c->T, k, c->omega,
                                         c->control, c->target, full ? c->traj : nullptr,
@@ -645,6 +749,14 @@ int pxa_set_memory(pxa_ctx* c, int policy) {
   return PXA_OK;
 }
 
+int pxa_set_adjoint(pxa_ctx* c, int impl) {
+  if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP)) return PXA_ERR_INVALID;
+  c->band_req = impl == PXA_ADJ_BANDED ? 1 : 0;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
 int pxa_set_cluster(pxa_ctx* c, int direct, int lanes, int chain) {
   if (!c) return PXA_ERR_INVALID;
   for (int C : {direct, lanes, chain})
@@ -682,6 +794,7 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
   if (rc) return rc;
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   double* Jd = J_dev ? J_dev : c->Jdev;
+  c->prep_marked = false;
   c->stats.lanes = mode == PXA_SERIAL ? 1 : c->P;
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;
@@ -742,11 +855,18 @@ int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
     float a = 0, b = 0, d = 0, e = 0, t = 0;
     cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
-    cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+    float pr = 0;
+    if (c->prep_marked) {
+      cudaEventElapsedTime(&pr, c->ev[2], c->ev[6]);
+      cudaEventElapsedTime(&d, c->ev[6], c->ev[3]);
+    } else {
+      cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+    }
     cudaEventElapsedTime(&e, c->ev[3], c->ev[4]);
     cudaEventElapsedTime(&t, c->ev[0], c->ev[5]);
     c->stats.ms_direct_inhom = a;
     c->stats.ms_direct_hom = b;
+    c->stats.ms_adjoint_prep = pr;
     c->stats.ms_adjoint_inhom = d;
     c->stats.ms_adjoint_hom = e;
     c->stats.ms_total = t;
@@ -823,7 +943,10 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   } else {
     int sms = 0;
     PXA_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device), "SM count");
-    auto ok = [&](int C) { return bu1c_valid_cluster(c->op.n, C) && (C == 1 || c->op.n / C >= 24); };
+    auto ok = [&](int C) {
+      return bu1c_valid_cluster(c->op.n, C) && bu1_rk4_valid_cluster(c->op.n, C) &&
+             (C == 1 || c->op.n / C >= 24);
+    };
     for (int cd : {1, 2, 4, 8, 12, 16})
       for (int cl : {1, 2, 3, 4})
         if (ok(cd) && ok(cl) && cl * c->P <= (sms > 0 ? sms : 152)) cands.push_back({cd, cl, cd});

@@ -22,6 +22,7 @@ CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
 SERIAL, PARAEXP = 0, 1
 STORE_FULL, STORE_CHECKPOINTS = 0, 1
+ADJ_BANDED, ADJ_RESTEP = 0, 1
 
 _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
                  ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_TIMEOUT: "TIMEOUT",
@@ -29,7 +30,7 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
@@ -57,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("ms_direct_hom", ctypes.c_float), ("ms_adjoint_inhom", ctypes.c_float),
                 ("ms_adjoint_hom", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("band_taps", ctypes.c_int), ("cluster_direct", ctypes.c_int),
-                ("cluster_lanes", ctypes.c_int), ("cluster_chain", ctypes.c_int)]
+                ("cluster_lanes", ctypes.c_int), ("cluster_chain", ctypes.c_int),
+                ("ms_adjoint_prep", ctypes.c_float), ("adjoint_band", ctypes.c_int)]
 
 
 _lib = None
@@ -83,6 +85,7 @@ def load(path: str = LIB_PATH):
         "pxa_set_control": [p, p, d],
         "pxa_set_target": [p, p],
         "pxa_set_memory": [p, i],
+        "pxa_set_adjoint": [p, i],
         "pxa_set_graph": [p, i],
         "pxa_set_cluster": [p, i, i, i],
         "pxa_autotune": [p, i, p, p],
@@ -194,6 +197,9 @@ class Context:
 
     def set_memory(self, policy):
         self._check(self._L.pxa_set_memory(self._h, policy))
+
+    def set_adjoint(self, impl):
+        self._check(self._L.pxa_set_adjoint(self._h, impl))
 
     def set_cluster(self, direct=0, lanes=0, chain=0):
         self._check(self._L.pxa_set_cluster(self._h, int(direct), int(lanes), int(chain)))
