@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="burgers1d", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=0, help="grid size override for the 2D workloads")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling run: W warm-up gradients then one more of the headline "
+                         "configuration (1D workloads), default cluster sizes, no autotuning")
     return ap.parse_args()
 
 
@@ -241,6 +244,7 @@ def run_ours(args, w, rank, world):
         st = ctx.stats()
         tuned[name] = {"krylov_m": st["krylov_m"], "krylov_substeps": st["krylov_substeps"],
                        "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]],
+                       "groups": [st["group_direct"], st["group_sweep"]],
                        "autotune_best_ms": best_ms}
         times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
         variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name, "tuned": tuned[name]}
@@ -272,6 +276,7 @@ def run_ours(args, w, rank, world):
         ctx.set_krylov(tv["krylov_m"], w["tol"], phi, tv["krylov_substeps"])
     else:
         ctx.set_cluster(*tv["clusters"])
+        ctx.set_groups(*tv["groups"])
 
     if world > 1:
         import torch.distributed as dist
@@ -380,6 +385,34 @@ def run_ours(args, w, rank, world):
     }
     ctx.close()
     return line
+
+
+def run_once(args, w):
+    """W warm-up gradients and one more (Paraexp, stepper propagator), for ncu: the
+    kernels of gradient W+1 are the launches after the first W of each name."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    X.load()
+    inp = make_inputs(w)
+    ctl = torch.as_tensor(inp["control"], device="cuda")
+    ctx = make_ctx(X, w, X.PHI_STEPPER)
+    ctx.set_control(ctl)
+    if "target" in inp:
+        ctx.set_target(torch.as_tensor(inp["target"], device="cuda"))
+    ctx.set_timing(True)
+    grad = torch.empty(w["n"], dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.gradient(X.PARAEXP, grad)
+    J = ctx.gradient(X.PARAEXP, grad)
+    st = ctx.stats()
+    ctx.close()
+    return {"once": w["label"], "J": J, "warmup": args.warmup,
+            "phases_ms": {k: st[k] for k in ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_prep",
+                                             "ms_adjoint_inhom", "ms_adjoint_hom", "ms_total")},
+            "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]]}
 
 
 def run_reference(args, w, rank, world):
@@ -527,7 +560,9 @@ def main():
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if w["kind"] == "lanes2d":
+    if args.once and w["kind"] in ("burgers1d", "advdiff1d"):
+        line = run_once(args, w)
+    elif w["kind"] == "lanes2d":
         line = run_lanes2d(args, w)
     elif w["kind"] == "advdiff2d":
         line = run_2d(args, w, rank, world)

@@ -125,6 +125,8 @@ typedef struct {
   int cluster_chain;
   float ms_adjoint_prep;    /* BURGERS_1D banded adjoint: recompute + band records */
   int adjoint_band;         /* 1 when the banded adjoint is in use */
+  int group_direct;         /* requested steps per halo exchange (0 = cost model) */
+  int group_sweep;
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -157,6 +159,17 @@ int pxa_set_memory(pxa_ctx* ctx, int policy);
 /* BURGERS_1D adjoint evaluation (pxa_adjoint). BANDED falls back to RESTEP when its
  * records do not fit; pxa_get_stats reports which one is in use. */
 int pxa_set_adjoint(pxa_ctx* ctx, int impl);
+/* BURGERS_1D with the banded adjoint and full storage: run the serial direct solve in
+ * chunks of whole subintervals and, on a library-owned low-priority stream, build the
+ * band records and run the adjoint lanes of each finished chunk while the next one is
+ * stepped (1, default), or run the phases one after another (0). Results are the same
+ * up to the summation order of J. */
+int pxa_set_overlap(pxa_ctx* ctx, int enable);
+/* BURGERS_1D: steps per halo exchange of the serial RK4 sweep (q_direct) and of the
+ * banded adjoint sweeps (q_sweep): 1, 2 or 4 (a CTA then also steps 4(q-1) of its
+ * neighbours' points on each side, and needs at least 4q points of its own); 0 = chosen
+ * by a cost model (default). The autotuner searches them. */
+int pxa_set_groups(pxa_ctx* ctx, int q_direct, int q_sweep);
 /* CTAs per thread-block cluster of the BURGERS_1D RK4 kernels: the serial direct
  * lane, each of the P concurrent adjoint lanes, and the homogeneous chain (1..16;
  * 0 = automatic: 16 for the serial lanes, SMs/P for the concurrent lanes, both capped

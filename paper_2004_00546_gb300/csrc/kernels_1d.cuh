@@ -52,11 +52,16 @@ cudaError_t launch_bu1c_stepper_chain(cudaStream_t st, int C, int n, double L, d
 // Serial RK4 sweeps of the Burgers direct problem on clusters (kernels_bu1_rk4.cu).
 bool bu1_rk4_valid_cluster(int n, int C);
 cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, double omega, double* sc);
+// reserve_smem > 0 requests that much dynamic shared memory per CTA, so that no other
+// kernel's CTA fits beside the sweep on its SMs while it runs concurrently with them.
+// group: steps per halo exchange (1, 2 or 4; 0 = chosen by a cost model; an invalid
+// request falls back to the largest valid smaller one). The banded sweep takes the same.
 cudaError_t launch_bu1_rk4_sweep(cudaStream_t st, int C, int lanes, int n, double L, double nu,
                                  double dt, int64_t k, const double* f, const double* sc,
                                  const double* x0, double* out, int64_t lane_rows, const double* gt,
                                  double T, double* Jdev, double* ckpt, int64_t ck_every,
-                                 int* status);
+                                 int* status, int priority, size_t reserve_smem, int group);
+cudaError_t launch_sum_parts(cudaStream_t st, int count, const double* parts, double* out, int* status);
 
 // Banded discrete adjoint of the Burgers RK4 map (kernels_bu1_band.cu). A record holds
 // the 9 taps of row i of M_s^T and the objective's source dJ/du_s[i].
@@ -67,12 +72,13 @@ int bu1_band_grad_blocks(int64_t K, int n);
 cudaError_t launch_bu1_band_prepass(cudaStream_t st, int n, double L, double nu, double dt, double T,
                                     double omega, const double* f, const double* gt,
                                     const double* rows, int64_t lane_k, int lanes, int64_t s_begin,
-                                    int64_t s_end, int64_t K, double* rec, double* jt);
-cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int n, const double* rec,
-                                  int64_t k, int P, int chain, const double* W, double* out_rows,
-                                  double* wout, int* status);
+                                    int64_t s_end, int64_t K, double* rec, double* jt, int priority);
+cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int lane0, int n,
+                                  const double* rec, int64_t k, int P, int chain, const double* W,
+                                  double* out_rows, double* wout, int* status, int priority,
+                                  int group);
 cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
-                                 int64_t h_top, const double* LI, const double* H, const double* jt,
+                                 int64_t li_top, const double* LI, const double* H, const double* jt,
                                  double* partial, const double* extra, double* grad, int* status);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);

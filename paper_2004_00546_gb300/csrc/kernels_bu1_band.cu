@@ -215,31 +215,126 @@ __global__ void __launch_bounds__(PT) bu1_band_prepass_kernel(
 }
 
 // ---- 2. banded reverse sweep --------------------------------------------------------
-// Lane mode (chain == 0): cluster l sweeps rows s_hi = (l+1)k down to s_lo = lk from
-// lambda_{s_hi} = source(s_hi), adding the source for s > s_lo; it writes rows
-// (s_lo, s_hi] to out_rows and lambda_{s_lo} to wout[l].
-// Chain mode (chain == 1, one cluster): h_{(P-1)k} = W[P-1], swept down to row 0 without
-// source, adding W[j] at rows jk (0 < j < P-1); rows (0, (P-1)k] go to out_rows.
-template <int DEPTH>
-__global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int64_t k, int P,
-                                      int chain, const double* __restrict__ W,
+// Lane mode (chain == 0): cluster c sweeps lane l = lane0 + c, rows s_hi = (l+1)k down to
+// s_lo = lk, from lambda_{s_hi} = source(s_hi), adding the source for s > s_lo; it writes
+// rows (s_lo, s_hi] to out_rows and lambda_{s_lo} to wout[l] (Eq. hybadjinhom).
+// Chain mode (chain == 1, one cluster): rows Pk down to 0. On the top subinterval
+// ((P-1)k, Pk] it is the top lane itself (source included, nothing above it); below,
+// it carries the sum of the homogeneous problems without source, adding the lane value
+// W[j] at row jk for j = P-2 .. 1 (Eq. adjHomNormal with the stepper's propagator).
+// Rows (0, Pk] go to out_rows. With P = 1 this is the plain serial adjoint.
+//
+// Steps are taken in groups of Q: a CTA also updates the 4(Q-1) points on each side of
+// its chunk (the neighbours' points, redundantly: an FP64 warp instruction costs the
+// same with idle lanes), so one exchange of 4Q boundary values per side serves Q steps.
+// A group with parity x starts from buffer A_x (halo received from the neighbours),
+// alternates through B_x, and writes its last step into A_{x^1}, which the neighbours
+// fill next: a neighbour may run up to one group ahead, and only ever writes the halo
+// of the buffer that the receiver reads in its next group.
+// Per-thread state of the banded sweep (one point per thread).
+struct SweepThread {
+  int p, cnt, lane, n;
+  int steps;         // s_hi - s_lo
+  int src_steps;     // the first src_steps steps add the objective's source
+  int inj_it;        // step index of the next lane-value injection (chain), else -1
+  int inj_j;
+  bool own, act, to_left, to_right;
+  uint32_t rl0, rl1, rr0, rr1, bl0, bl1, br0, br1;
+  const double* pf;  // record of the next prefetch
+  double* orow;      // output row of the current step (own points)
+  double* my_ring;
+  size_t row_stride;
+  int slot_stride, inj_stride;
+  const double* wrow;  // W[inj_j][g]
+  double* wout;
+};
+
+// One step (index it, position m within its group of Q) of the banded sweep.
+template <int Q, int DEPTH>
+__device__ __forceinline__ void band_step(SweepThread& t, int it, int m, int m0, int x,
+                                          const double*& in, double* A_x, double* B_x,
+                                          double* A_next, bool exchange_after) {
+  if (t.act && it + DEPTH - 1 < t.steps) {
+    double* d = t.my_ring + ((it + DEPTH - 1) & (DEPTH - 1)) * t.slot_stride;
+#pragma unroll
+    for (int q = 0; q < RW / 2; ++q) cp_async16(d + 2 * q, t.pf + 2 * q);
+  }
+  t.pf -= t.row_stride;
+  cp_async_commit();
+  cp_async_wait<DEPTH - 1>();
+  double* const out = m == Q - 1 ? A_next : (((m - m0) & 1) ? A_x : B_x);
+  const int w = 4 * (Q - 1 - m);
+  const bool inject = it == t.inj_it;
+  if (t.p >= -w && t.p < t.cnt + w) {
+    const double2* r2 = reinterpret_cast<const double2*>(t.my_ring + (it & (DEPTH - 1)) * t.slot_stride);
+    const double2 q0 = r2[0], q1 = r2[1], q2 = r2[2], q3 = r2[3], q4 = r2[4];
+    const double* L = in + t.p;
+    double acc = it < t.src_steps ? q4.y : 0.0;
+    acc = fma(q0.x, L[-4], acc);
+    acc = fma(q0.y, L[-3], acc);
+    acc = fma(q1.x, L[-2], acc);
+    acc = fma(q1.y, L[-1], acc);
+    acc = fma(q2.x, L[0], acc);
+    acc = fma(q2.y, L[1], acc);
+    acc = fma(q3.x, L[2], acc);
+    acc = fma(q3.y, L[3], acc);
+    acc = fma(q4.x, L[4], acc);
+    if (inject) acc += *t.wrow;
+    out[t.p] = acc;
+    if (m == Q - 1 && exchange_after) {
+      if (t.to_left) st_async_f64(x ? t.rl0 : t.rl1, acc, x ? t.bl0 : t.bl1);
+      if (t.to_right) st_async_f64(x ? t.rr0 : t.rr1, acc, x ? t.br0 : t.br1);
+    }
+    if (t.own) {
+      if (it < t.steps - 1) {
+        if (t.orow) *t.orow = acc;
+      } else if (t.wout) {
+        *t.wout = acc;
+      }
+    }
+  }
+  if (t.orow) t.orow -= t.n;
+  if (inject) {
+    --t.inj_j;
+    t.inj_it = t.inj_j >= 1 ? t.inj_it + t.inj_stride : -1;
+    t.wrow -= t.n;
+  }
+  in = out;
+  if (m < Q - 1) __syncthreads();
+}
+
+template <int Q, int DEPTH>
+__global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int k, int P,
+                                      int chain, int lane0, const double* __restrict__ W,
                                       double* __restrict__ out_rows, double* __restrict__ wout,
                                       int* status) {
+  constexpr int HQ = 4 * Q;      // halo of a group
+  constexpr int EX = 4 * Q - 4;  // points computed on each side beyond the chunk
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) double smb[];
   __shared__ __align__(8) uint64_t bar[2];
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int nc = (n + C - 1) / C, start = rank * nc, cnt = min(nc, n - start);
-  const int lane = chain ? 0 : (int)(blockIdx.x / C);
-  const int64_t s_hi = chain ? (int64_t)(P - 1) * k : (int64_t)(lane + 1) * k;
-  const int64_t s_lo = chain ? 0 : (int64_t)lane * k;
-  const int Wd = nc + 2 * SH;
-  double* const lam0 = smb;
-  double* const lam1 = smb + Wd;
-  double* ring = smb + 2 * Wd;  // [DEPTH][nc][RW]
+  const int lane = chain ? 0 : lane0 + (int)(blockIdx.x / C);
+  const int s_hi = chain ? P * k : (lane + 1) * k;
+  const int s_lo = chain ? 0 : lane * k;
+  const int Wd = nc + 2 * HQ;
+  double* const A0 = smb + HQ;
+  double* const A1 = smb + Wd + HQ;
+  double* const B0 = smb + 2 * Wd + HQ;
+  double* const B1 = smb + 3 * Wd + HQ;
+  const int npts = nc + 2 * EX;       // points handled by the threads
+  double* const ring = smb + 4 * Wd;  // [DEPTH][npts][RW]
   const int tid = threadIdx.x, nt = blockDim.x;
+  SweepThread t;
+  t.p = tid - EX;
+  t.cnt = cnt;
+  t.lane = lane;
+  t.n = n;
+  t.act = t.p >= -EX && t.p < cnt + EX;
+  t.own = t.p >= 0 && t.p < cnt;
+  const int g = wrapi(start + t.p, n);
   const bool multi = C > 1;
-  // the neighbours' chunk sizes, and where my boundary values land in their halos
   const int left = (rank + C - 1) % C, right = (rank + 1) % C;
   const int cnt_left = min(nc, n - left * nc);
   if (multi && tid == 0) {
@@ -247,95 +342,94 @@ __global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // lambda_{s_hi} on own points and halo
-  for (int p = tid - SH; p < cnt + SH; p += nt) {
-    const int g = wrapi(start + p, n);
-    const double v = chain ? W[(size_t)(P - 1) * n + g] : rec[((size_t)s_hi * n + g) * RW + (RW - 1)];
-    ((s_hi & 1) ? lam1 : lam0)[SH + p] = v;
-    if (p >= 0 && p < cnt && out_rows) out_rows[(size_t)s_hi * n + start + p] = v;
+  // lambda_{s_hi} on own points and halo, into A0 (group 0 starts there)
+  for (int q = tid - HQ; q < cnt + HQ; q += nt) {
+    const int gq = wrapi(start + q, n);
+    const double v = rec[((size_t)s_hi * n + gq) * RW + (RW - 1)];
+    A0[q] = v;
+    if (q >= 0 && q < cnt && out_rows) out_rows[(size_t)s_hi * n + start + q] = v;
   }
-  // Prefetch of the records of step s into ring slot `slot`, one commit group per step.
-  // Each thread copies the records of exactly the points it consumes, so its own
-  // cp.async.wait_group is the only wait the data needs.
-  auto prefetch = [&](int64_t s, int slot) {
-    if (s >= s_lo) {
-      const double* srcp = rec + ((size_t)s * n + start) * RW;
-      double* dst = ring + (size_t)slot * nc * RW;
-      for (int p = tid; p < cnt; p += nt) {
+  // remote halo slots (in A0 / A1) of my boundary points
+  t.to_left = multi && t.own && t.p < HQ;
+  t.to_right = multi && t.own && t.p >= cnt - HQ;
+  t.rl0 = t.rl1 = t.rr0 = t.rr1 = t.bl0 = t.bl1 = t.br0 = t.br1 = 0;
+  if (t.to_left) {
+    t.rl0 = map_rank(smem_u32(A0 + cnt_left + t.p), left);
+    t.rl1 = map_rank(smem_u32(A1 + cnt_left + t.p), left);
+    t.bl0 = map_rank(smem_u32(&bar[0]), left);
+    t.bl1 = map_rank(smem_u32(&bar[1]), left);
+  }
+  if (t.to_right) {
+    t.rr0 = map_rank(smem_u32(A0 + (t.p - cnt)), right);
+    t.rr1 = map_rank(smem_u32(A1 + (t.p - cnt)), right);
+    t.br0 = map_rank(smem_u32(&bar[0]), right);
+    t.br1 = map_rank(smem_u32(&bar[1]), right);
+  }
+  const int steps = s_hi - s_lo;
+  t.steps = steps;
+  t.src_steps = chain ? k - 1 : steps - 1;
+  // chain: W[j] is added at row j*k for j = P-2 .. 1, i.e. at step index s_hi-1-j*k
+  t.inj_j = chain ? P - 2 : 0;
+  t.inj_it = (chain && P >= 3) ? 2 * k - 1 : -1;  // row (P-2)k
+  t.inj_stride = k;
+  t.wrow = (chain && P >= 3) ? W + (size_t)(P - 2) * n + g : nullptr;
+  t.wout = (wout && t.own) ? wout + (size_t)lane * n + start + t.p : nullptr;
+  t.orow = (out_rows && t.own) ? out_rows + (size_t)(s_hi - 1) * n + start + t.p : nullptr;
+  t.row_stride = (size_t)n * RW;
+  t.pf = rec + ((size_t)(s_hi - 1) * n + g) * RW;
+  t.my_ring = ring + (size_t)(tid < npts ? tid : 0) * RW;
+  t.slot_stride = npts * RW;
 #pragma unroll
-        for (int j = 0; j < RW / 2; ++j) cp_async16(dst + (size_t)p * RW + 2 * j, srcp + (size_t)p * RW + 2 * j);
-      }
+  for (int j = 0; j < DEPTH - 1; ++j) {
+    if (t.act && j < steps) {
+      double* d = t.my_ring + j * t.slot_stride;
+#pragma unroll
+      for (int q = 0; q < RW / 2; ++q) cp_async16(d + 2 * q, t.pf + 2 * q);
     }
+    t.pf -= t.row_stride;
     cp_async_commit();
-  };
-#pragma unroll
-  for (int j = 0; j < DEPTH - 1; ++j) prefetch(s_hi - 1 - j, j);
+  }
+  const int groups = (steps + Q - 1) / Q;
+  const int rem = steps - (groups - 1) * Q;  // steps of the last group
   if (multi) {
-    if (tid == 0 && s_hi - 1 >= s_lo) mbar_arm(&bar[(s_hi - 1) & 1], 2 * SH * (int)sizeof(double));
+    if (tid == 0 && groups > 1) mbar_arm(&bar[1], 2 * HQ * (int)sizeof(double));
     cl.sync();  // barriers initialised and armed, initial lambda in place cluster-wide
   } else {
     __syncthreads();
   }
   uint32_t ph0 = 0u, ph1 = 0u;
-  const int64_t steps = s_hi - s_lo;
-  // chain: the next row that receives a lane value, W[inj_j] at row inj_j * k
-  int inj_j = chain ? P - 2 : 0;
-  int64_t inj_row = (int64_t)inj_j * k;
-  for (int64_t it = 0; it < steps; ++it) {
-    const int64_t s = s_hi - 1 - it;
-    prefetch(s - (DEPTH - 1), (int)((uint64_t)(it + DEPTH - 1) % DEPTH));
-    cp_async_wait<DEPTH - 1>();
-    const int b = (int)(s & 1);
-    double* const lb = b ? lam1 : lam0;
-    const double* Lp = (b ? lam0 : lam1) + SH;
-    double* Ln = lb + SH;
-    uint64_t* const bar_b = b ? &bar[1] : &bar[0];
-    const double* rs = ring + (size_t)((uint64_t)it % DEPTH) * nc * RW;
-    const bool add_src = !chain && s > s_lo;
-    const bool inject = chain && inj_j >= 1 && s == inj_row;
-    for (int p = tid; p < cnt; p += nt) {
-      const double2* r2 = reinterpret_cast<const double2*>(rs + (size_t)p * RW);
-      const double2 q0 = r2[0], q1 = r2[1], q2 = r2[2], q3 = r2[3], q4 = r2[4];
-      double acc = add_src ? q4.y : 0.0;
-      acc = fma(q0.x, Lp[p - 4], acc);
-      acc = fma(q0.y, Lp[p - 3], acc);
-      acc = fma(q1.x, Lp[p - 2], acc);
-      acc = fma(q1.y, Lp[p - 1], acc);
-      acc = fma(q2.x, Lp[p], acc);
-      acc = fma(q2.y, Lp[p + 1], acc);
-      acc = fma(q3.x, Lp[p + 2], acc);
-      acc = fma(q3.y, Lp[p + 3], acc);
-      acc = fma(q4.x, Lp[p + 4], acc);
-      if (inject) acc += W[(size_t)inj_j * n + start + p];
-      Ln[p] = acc;
-      if (multi) {
-        if (p < SH)  // my first points are the left neighbour's right halo
-          st_async_f64(map_rank(smem_u32(lb + SH + cnt_left + p), left), acc,
-                       map_rank(smem_u32(bar_b), left));
-        if (p >= cnt - SH)  // my last points are the right neighbour's left halo
-          st_async_f64(map_rank(smem_u32(lb + SH + (p - cnt)), right), acc,
-                       map_rank(smem_u32(bar_b), right));
-      }
-      if (s > s_lo && out_rows) out_rows[(size_t)s * n + start + p] = acc;
-      if (s == s_lo && wout) wout[(size_t)lane * n + start + p] = acc;
-    }
-    if (inject) {
-      --inj_j;
-      inj_row -= k;
-    }
-    if (multi) {
-      if (tid == 0 && s - 1 >= s_lo) mbar_arm(b ? &bar[0] : &bar[1], 2 * SH * (int)sizeof(double));
-      mbar_wait_bounded(bar_b, b ? ph1 : ph0, status);
-      if (b) ph1 ^= 1u; else ph0 ^= 1u;
-      __syncthreads();
+  int it = 0;
+  for (int grp = 0; grp < groups; ++grp) {
+    const int x = grp & 1;
+    double* const Ax = x ? A1 : A0;
+    double* const Bx = x ? B1 : B0;
+    double* const An = x ? A0 : A1;
+    const bool more = grp + 1 < groups;
+    const double* in = Ax;
+    if (grp + 1 < groups || rem == Q) {
+#pragma unroll
+      for (int m = 0; m < Q; ++m) band_step<Q, DEPTH>(t, it + m, m, 0, x, in, Ax, Bx, An, more);
+      it += Q;
     } else {
-      __syncthreads();
-      // one CTA holds the whole periodic grid: fill the halo from its own values
-      for (int j = tid; j < 2 * SH; j += nt) {
-        const int p = j < SH ? j - SH : cnt + (j - SH);
-        Ln[p] = Ln[wrapi(p, n)];
+      for (int m = Q - rem; m < Q; ++m, ++it) band_step<Q, DEPTH>(t, it, m, Q - rem, x, in, Ax, Bx, An, more);
+    }
+    if (more) {
+      if (multi) {
+        // A_{x^1} is complete once the neighbours' 4Q values per side arrived; arm the
+        // barrier of the exchange after the next group first
+        if (tid == 0 && grp + 2 < groups) mbar_arm(x ? &bar[1] : &bar[0], 2 * HQ * (int)sizeof(double));
+        mbar_wait_bounded(x ? &bar[0] : &bar[1], x ? ph0 : ph1, status);
+        if (x) ph0 ^= 1u; else ph1 ^= 1u;
+        __syncthreads();
+      } else {
+        __syncthreads();
+        // one CTA holds the whole periodic grid: fill the halo from its own values
+        for (int j = tid; j < 2 * HQ; j += nt) {
+          const int q = j < HQ ? j - HQ : cnt + (j - HQ);
+          An[q] = An[wrapi(q, n)];
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   cp_async_wait<0>();
@@ -344,9 +438,9 @@ __global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int
 
 // ---- 3. forcing gradient --------------------------------------------------------------
 // Grid (tiles, step blocks); partial[block_y][n] = sum over the block's steps s of
-// (G_s^T lambda_{s+1}), lambda = LI (+ H for rows <= h_top when H is given).
+// (G_s^T lambda_{s+1}), lambda = H (every row, when given) + LI (rows <= li_top).
 __global__ void __launch_bounds__(PT) bu1_band_grad_kernel(
-    int n, double dt, double omega, int64_t K, int64_t h_top, const double* __restrict__ LI,
+    int n, double dt, double omega, int64_t K, int64_t li_top, const double* __restrict__ LI,
     const double* __restrict__ H, const double* __restrict__ jt, int steps_per_block,
     double* __restrict__ partial) {
   __shared__ double lam[PT + 6], kb4[PT + 6], kb3[PT + 6], kb2[PT + 6];
@@ -363,11 +457,11 @@ __global__ void __launch_bounds__(PT) bu1_band_grad_kernel(
     const double c1 = forcing_s(omega, t), c2 = forcing_s(omega, t + 0.5 * dt),
                  c4 = forcing_s(omega, t + dt);
     const size_t row = (size_t)(s + 1) * n;
-    const bool withH = H != nullptr && s + 1 <= h_top;
+    const bool withLI = LI != nullptr && s + 1 <= li_top;
     for (int p = tid - O; p < PT + O; p += PT) {
       const int g = wrapi(i0 + p, n);
-      double v = LI[row + g];
-      if (withH) v += H[row + g];
+      double v = H ? H[row + g] : 0.0;
+      if (withLI) v += LI[row + g];
       lam[O + p] = v;
       kb4[O + p] = dt6 * v;
     }
@@ -435,15 +529,22 @@ int bu1_band_steps_per_block(int64_t K, int n) {
 cudaError_t launch_bu1_band_prepass(cudaStream_t st, int n, double L, double nu, double dt, double T,
                                     double omega, const double* f, const double* gt,
                                     const double* rows, int64_t lane_k, int lanes, int64_t s_begin,
-                                    int64_t s_end, int64_t K, double* rec, double* jt) {
+                                    int64_t s_end, int64_t K, double* rec, double* jt, int priority) {
   if (s_end <= s_begin) return cudaSuccess;
   const double h = L / n;
-  const int spb = bu1_band_steps_per_block(s_end - s_begin, n);
-  dim3 grid((n + PT - 1) / PT, (unsigned)((s_end - s_begin + spb - 1) / spb));
-  bu1_band_prepass_kernel<<<grid, PT, 0, st>>>(n, 1.0 / (2.0 * h), 1.0 / (h * h), nu, dt, T, omega,
-                                               f, gt, rows, lane_k, lanes, s_begin, s_end, K, spb,
-                                               rec, jt);
-  return cudaGetLastError();
+  int spb = bu1_band_steps_per_block(s_end - s_begin, n);
+  double inv2h = 1.0 / (2.0 * h), invh2 = 1.0 / (h * h);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((n + PT - 1) / PT, (unsigned)((s_end - s_begin + spb - 1) / spb));
+  cfg.blockDim = dim3(PT);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bu1_band_prepass_kernel, n, inv2h, invh2, nu, dt, T, omega, f, gt,
+                            rows, lane_k, lanes, s_begin, s_end, K, spb, rec, jt);
 }
 
 bool bu1_band_valid_cluster(int n, int C) {
@@ -455,42 +556,87 @@ bool bu1_band_valid_cluster(int n, int C) {
   return n - (C - 1) * nc >= SH;
 }
 
-static int sweep_threads(int nc) {
-  int t = ((nc + 31) / 32) * 32;
-  return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+static size_t sweep_smem(int nc, int q, int depth) {
+  const int npts = nc + 2 * (4 * q - 4);
+  return sizeof(double) * (4 * (size_t)(nc + 8 * q) + (size_t)depth * npts * RW);
 }
 
-static size_t sweep_smem(int nc, int depth) {
-  return sizeof(double) * (2 * (size_t)(nc + 2 * SH) + (size_t)depth * nc * RW);
+// Steps per exchange Q in {1, 2, 4}: every CTA must own the 4Q-point halo its neighbours
+// need, and the threads (chunk + 2 (4Q - 4) points) must fit in one CTA. Among those, the
+// Q with the least estimated time per step: one FP64 warp instruction per 64 cycles on
+// each of the 4 SM sub-partitions, 9 per point and step, and ~600 cycles per exchange.
+static bool sweep_group_ok(int n, int C, int q) {
+  const int nc = (n + C - 1) / C, last = n - (C - 1) * nc;
+  if (nc + 2 * (4 * q - 4) > 1024) return false;
+  if (q > 1 && C > 1 && last < 4 * q) return false;
+  if (q > 1 && C == 1 && n < 4 * q) return false;
+  return true;
 }
 
-cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int n, const double* rec,
-                                  int64_t k, int P, int chain, const double* W, double* out_rows,
-                                  double* wout, int* status) {
+static int sweep_group(int n, int C, int want) {
+  if (want == 4 || want == 2 || want == 1)
+    for (int q = want; q >= 1; q /= 2)
+      if (sweep_group_ok(n, C, q)) return q;
   const int nc = (n + C - 1) / C;
-  const int depth = sweep_smem(nc, 4) <= 200 * 1024 ? 4 : 2;
-  const size_t sh = sweep_smem(nc, depth);
-  const void* fn = depth == 4 ? (const void*)bu1_band_sweep_kernel<4> : (const void*)bu1_band_sweep_kernel<2>;
+  int best = 1;
+  double best_cost = 1e30;
+  for (int q : {1, 2, 4}) {
+    const int npts = nc + 2 * (4 * q - 4);
+    if (!sweep_group_ok(n, C, q)) continue;
+    const int warps = (npts + 31) / 32;
+    const double cost = (double)((warps + 3) / 4) * 9 * 64 + 600.0 / q;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = q;
+    }
+  }
+  return best;
+}
+
+template <int Q>
+static cudaError_t launch_sweep_q(cudaStream_t st, int C, int clusters, int nc, void** args,
+                                  int priority) {
+  const int depth = sweep_smem(nc, Q, 4) <= 200 * 1024 ? 4 : 2;
+  const size_t sh = sweep_smem(nc, Q, depth);
+  const void* fn = depth == 4 ? (const void*)bu1_band_sweep_kernel<Q, 4>
+                              : (const void*)bu1_band_sweep_kernel<Q, 2>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   if (C > 8) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  void* args[] = {&n, &rec, &k, &P, &chain, &W, &out_rows, &wout, &status};
+  const int npts = nc + 2 * (4 * Q - 4);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * clusters);
-  cfg.blockDim = dim3(sweep_threads(nc));
+  cfg.blockDim = dim3(((npts + 31) / 32) * 32);
   cfg.dynamicSmemBytes = sh;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = priority;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int lane0, int n,
+                                  const double* rec, int64_t k, int P, int chain, const double* W,
+                                  double* out_rows, double* wout, int* status, int priority,
+                                  int group) {
+  if (clusters <= 0) return cudaSuccess;
+  const int nc = (n + C - 1) / C;
+  int ki = (int)k;  // steps fit in int: K * n records are addressed with size_t
+  void* args[] = {&n, &rec, &ki, &P, &chain, &lane0, &W, &out_rows, &wout, &status};
+  switch (sweep_group(n, C, group)) {
+    case 4: return launch_sweep_q<4>(st, C, clusters, nc, args, priority);
+    case 2: return launch_sweep_q<2>(st, C, clusters, nc, args, priority);
+    default: return launch_sweep_q<1>(st, C, clusters, nc, args, priority);
+  }
 }
 
 int bu1_band_grad_blocks(int64_t K, int n) {
@@ -499,12 +645,12 @@ int bu1_band_grad_blocks(int64_t K, int n) {
 }
 
 cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
-                                 int64_t h_top, const double* LI, const double* H, const double* jt,
+                                 int64_t li_top, const double* LI, const double* H, const double* jt,
                                  double* partial, const double* extra, double* grad, int* status) {
   const int spb = bu1_band_steps_per_block(K, n);
   const int blocks = (int)((K + spb - 1) / spb);
   dim3 grid((n + PT - 1) / PT, blocks);
-  bu1_band_grad_kernel<<<grid, PT, 0, st>>>(n, dt, omega, K, h_top, LI, H, jt, spb, partial);
+  bu1_band_grad_kernel<<<grid, PT, 0, st>>>(n, dt, omega, K, li_top, LI, H, jt, spb, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bu1_band_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, blocks, partial, extra, grad, status);

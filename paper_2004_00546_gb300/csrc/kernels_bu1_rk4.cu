@@ -55,135 +55,256 @@ __global__ void bu1_forcing_table_kernel(int64_t K, double dt, double omega, dou
 // Cluster l steps s = l*k .. l*k+k-1 from x0[l] (x0 == NULL: zero state). State rows
 // go to out + (l*lane_rows + j)*n, j = 0..k (out may be NULL). With Jdev, J = (dt/T)
 // sum_{j>=1} ||u_j - g||^2 (one lane only); with ckpt, every ck_every-th state goes to
-// ckpt row s / ck_every. sc == NULL means s(t) = 1.
-__global__ void bu1_rk4_sweep_kernel(int n, double b, double a, double dt, int64_t k,
+// ckpt row s / ck_every. FORCED == false: s(t) = 1 (sc unused).
+//
+// Steps are taken in groups of Q: each CTA also steps the 4(Q-1) points on each side of
+// its chunk (its neighbours' points, redundantly), so one exchange of 4Q boundary values
+// per side serves Q steps. A group with parity x starts from state buffer A_x (halo
+// received), alternates through B_x and writes its last step into A_{x^1}, whose halo the
+// neighbours fill: a neighbour can run at most one group ahead and only ever writes the
+// halo of the buffer the receiver reads next.
+// Per-thread state of the RK4 sweep (one point per thread).
+struct Rk4Thread {
+  int p, cnt, n;
+  int k;              // steps of this lane
+  bool own;
+  double fp, gp;      // forcing and target at the point
+  double b, a, a2, h2, dt, dt6;
+  double c1, c2, c4;  // s(t) at the stage times of the current step
+  const double* scp;  // s(t) of the next step
+  double* yap;
+  double* ybp;
+  double* orow;       // output row of the next state (own points)
+  size_t n_stride;
+  double* ckpt;
+  int ck_left, ck_row, ck_every, start;
+  double jp;
+  bool with_j;
+  bool to_left, to_right;
+  uint32_t rl0, rl1, rr0, rr1, bl0, bl1, br0, br1;
+};
+
+// One RK4 step (index j, position m within its group of Q) on the points within
+// 4(Q-1-m) + 3 of the chunk.
+template <bool FORCED, int Q>
+__device__ __forceinline__ void rk4_step(Rk4Thread& t, int j, int m, int m0, int x,
+                                         const double*& in, double* A_x, double* B_x,
+                                         double* A_next, bool exchange_after) {
+  double* const outb = m == Q - 1 ? A_next : (((m - m0) & 1) ? A_x : B_x);
+  const int w = 4 * (Q - 1 - m);  // the new state is valid on [-w, cnt + w)
+  const int p = t.p;
+  double n1 = 1.0, n2 = 1.0, n4 = 1.0;
+  if (FORCED && j + 1 < t.k) {  // forcing factors of the next step, loaded a step ahead
+    n1 = t.scp[0];
+    n2 = t.scp[1];
+    n4 = t.scp[2];
+    t.scp += 3;
+  }
+  double cf1 = t.fp, cf2 = t.fp, cf4 = t.fp;
+  if (FORCED) {
+    cf1 = t.c1 * t.fp;
+    cf2 = t.c2 * t.fp;
+    cf4 = t.c4 * t.fp;
+  }
+  const double* Up = in + p;
+  double u0 = 0.0, acc = 0.0;
+  if (p >= -(w + 3) && p < t.cnt + w + 3) {
+    u0 = Up[0];
+    const double kk = stage_k(t.b, t.a, t.a2, Up[-1], u0, Up[1], cf1);
+    t.yap[0] = fma(t.h2, kk, u0);
+    acc = kk;
+  }
+  __syncthreads();
+  if (p >= -(w + 2) && p < t.cnt + w + 2) {
+    const double kk = stage_k(t.b, t.a, t.a2, t.yap[-1], t.yap[0], t.yap[1], cf2);
+    t.ybp[0] = fma(t.h2, kk, u0);
+    acc = fma(2.0, kk, acc);
+  }
+  __syncthreads();
+  if (p >= -(w + 1) && p < t.cnt + w + 1) {
+    const double kk = stage_k(t.b, t.a, t.a2, t.ybp[-1], t.ybp[0], t.ybp[1], cf2);
+    t.yap[0] = fma(t.dt, kk, u0);
+    acc = fma(2.0, kk, acc);
+  }
+  __syncthreads();
+  if (p >= -w && p < t.cnt + w) {
+    const double kk = stage_k(t.b, t.a, t.a2, t.yap[-1], t.yap[0], t.yap[1], cf4);
+    const double un = fma(t.dt6, acc + kk, u0);
+    outb[p] = un;
+    if (m == Q - 1 && exchange_after) {
+      if (t.to_left) st_async_f64(x ? t.rl0 : t.rl1, un, x ? t.bl0 : t.bl1);
+      if (t.to_right) st_async_f64(x ? t.rr0 : t.rr1, un, x ? t.br0 : t.br1);
+    }
+    if (t.own) {
+      if (t.with_j) {
+        const double d = un - t.gp;
+        t.jp = fma(d, d, t.jp);
+      }
+      if (t.orow) *t.orow = un;
+      if (t.ckpt && t.ck_left == 1) t.ckpt[(size_t)t.ck_row * t.n + t.start + p] = un;
+    }
+  }
+  if (t.orow) t.orow += t.n_stride;
+  if (t.ckpt) {
+    if (t.ck_left == 1) {
+      t.ck_left = t.ck_every;
+      ++t.ck_row;
+    } else {
+      --t.ck_left;
+    }
+  }
+  if (FORCED) {
+    t.c1 = n1;
+    t.c2 = n2;
+    t.c4 = n4;
+  }
+  in = outb;
+  if (m < Q - 1) __syncthreads();
+}
+
+// Cluster l steps s = l*k .. l*k+k-1 from x0[l] (x0 == NULL: zero state). State rows
+// go to out + (l*lane_rows + j)*n, j = 0..k (out may be NULL). With Jdev, J = (dt/T)
+// sum_{j>=1} ||u_j - g||^2 (one lane only); with ckpt, every ck_every-th state goes to
+// ckpt row s / ck_every. FORCED == false: s(t) = 1 (sc unused).
+//
+// Steps are taken in groups of Q: each CTA also steps the 4(Q-1) points on each side of
+// its chunk (its neighbours' points, redundantly), so one exchange of 4Q boundary values
+// per side serves Q steps. A group with parity x starts from state buffer A_x (halo
+// received), alternates through B_x and writes its last step into A_{x^1}, whose halo the
+// neighbours fill: a neighbour can run at most one group ahead and only ever writes the
+// halo of the buffer the receiver reads next.
+template <bool FORCED, int Q>
+__global__ void bu1_rk4_sweep_kernel(int n, double b, double a, double dt, int k,
                                      const double* __restrict__ f, const double* __restrict__ sc,
                                      const double* __restrict__ x0, double* __restrict__ out,
-                                     int64_t lane_rows, const double* __restrict__ gt, double T,
+                                     int lane_rows, const double* __restrict__ gt, double T,
                                      double* __restrict__ Jdev, double* __restrict__ ckpt,
-                                     int64_t ck_every, int* status) {
+                                     int ck_every, int* status) {
+  constexpr int HQ = 4 * Q;      // halo of a group
+  constexpr int EX = 4 * Q - 1;  // points stepped on each side beyond the chunk (stage 1)
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) uint64_t bar[2];
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int nc = (n + C - 1) / C, start = rank * nc, cnt = min(nc, n - start);
   const int lane = (int)(blockIdx.x / C);
-  const int64_t s0 = (int64_t)lane * k;
-  const int Wd = nc + 2 * HX;
-  double* const U0 = sm + HX;
-  double* const U1 = sm + Wd + HX;
-  double* const ya = sm + 2 * Wd + HX;
-  double* const yb = sm + 3 * Wd + HX;
-  double* const red = sm + 4 * Wd;  // 64 doubles
-  const int tid = threadIdx.x, p = tid - 3;
+  const int s0 = lane * k;
+  const int Wd = nc + 2 * HQ;
+  double* const A0 = sm + HQ;
+  double* const A1 = sm + Wd + HQ;
+  double* const B0 = sm + 2 * Wd + HQ;
+  double* const B1 = sm + 3 * Wd + HQ;
+  double* const ya = sm + 4 * Wd + HQ;
+  double* const yb = sm + 5 * Wd + HQ;
+  double* const red = sm + 6 * Wd;  // 64 doubles
+  const int tid = threadIdx.x;
   const bool multi = C > 1;
   const int left = (rank + C - 1) % C, right = (rank + 1) % C;
   const int cnt_left = min(nc, n - left * nc);
-  const double a2 = 2.0 * a, h2 = 0.5 * dt, dt6 = dt / 6.0;
-  const bool in1 = p >= -3 && p < cnt + 3, in2 = p >= -2 && p < cnt + 2, in3 = p >= -1 && p < cnt + 1,
-             own = p >= 0 && p < cnt;
-  const double fp = in1 ? f[((start + p) % n + n) % n] : 0.0;
-  const double gp = own && gt ? gt[start + p] : 0.0;
+  Rk4Thread t;
+  t.p = tid - EX;
+  t.cnt = cnt;
+  t.n = n;
+  t.k = k;
+  t.start = start;
+  t.own = t.p >= 0 && t.p < cnt;
+  const bool act = t.p >= -EX && t.p < cnt + EX;
+  t.fp = act ? f[((start + t.p) % n + n) % n] : 0.0;
+  t.gp = t.own && gt ? gt[start + t.p] : 0.0;
+  t.b = b;
+  t.a = a;
+  t.a2 = 2.0 * a;
+  t.h2 = 0.5 * dt;
+  t.dt = dt;
+  t.dt6 = dt / 6.0;
+  t.with_j = Jdev != nullptr;
+  t.jp = 0.0;
   if (multi && tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int q = tid - HX; q < cnt + HX; q += blockDim.x) {
+  for (int q = tid - HQ; q < cnt + HQ; q += blockDim.x) {
     const int g = ((start + q) % n + n) % n;
-    U0[q] = x0 ? x0[(size_t)lane * n + g] : 0.0;
+    A0[q] = x0 ? x0[(size_t)lane * n + g] : 0.0;
   }
   __syncthreads();
-  if (own) {
-    if (out) out[((size_t)lane * lane_rows) * n + start + p] = U0[p];
-    if (ckpt && s0 % ck_every == 0) ckpt[(size_t)(s0 / ck_every) * n + start + p] = U0[p];
+  if (t.own) {
+    if (out) out[((size_t)lane * lane_rows) * n + start + t.p] = A0[t.p];
+    if (ckpt && s0 % ck_every == 0) ckpt[(size_t)(s0 / ck_every) * n + start + t.p] = A0[t.p];
   }
-  int64_t ck_left = ckpt ? ck_every - (s0 % ck_every) : 0;  // steps until the next checkpoint
-  double c1 = 1.0, c2 = 1.0, c4 = 1.0;
-  if (sc) {
-    c1 = sc[3 * s0];
-    c2 = sc[3 * s0 + 1];
-    c4 = sc[3 * s0 + 2];
+  t.ckpt = ckpt;
+  t.ck_every = ck_every;
+  t.ck_left = ckpt ? ck_every - (s0 % ck_every) : 0;  // steps until the next checkpoint
+  t.ck_row = ckpt ? s0 / ck_every + 1 : 0;             // row of the next checkpoint
+  t.c1 = t.c2 = t.c4 = 1.0;
+  if (FORCED) {
+    t.c1 = sc[3 * (size_t)s0];
+    t.c2 = sc[3 * (size_t)s0 + 1];
+    t.c4 = sc[3 * (size_t)s0 + 2];
   }
+  t.scp = FORCED ? sc + 3 * ((size_t)s0 + 1) : nullptr;
+  // remote halo slots (in A0 / A1) of my boundary points and their barriers
+  t.to_left = multi && t.own && t.p < HQ;
+  t.to_right = multi && t.own && t.p >= cnt - HQ;
+  t.rl0 = t.rl1 = t.rr0 = t.rr1 = t.bl0 = t.bl1 = t.br0 = t.br1 = 0;
+  if (t.to_left) {
+    t.rl0 = map_rank(smem_u32(A0 + cnt_left + t.p), left);
+    t.rl1 = map_rank(smem_u32(A1 + cnt_left + t.p), left);
+    t.bl0 = map_rank(smem_u32(&bar[0]), left);
+    t.bl1 = map_rank(smem_u32(&bar[1]), left);
+  }
+  if (t.to_right) {
+    t.rr0 = map_rank(smem_u32(A0 + (t.p - cnt)), right);
+    t.rr1 = map_rank(smem_u32(A1 + (t.p - cnt)), right);
+    t.br0 = map_rank(smem_u32(&bar[0]), right);
+    t.br1 = map_rank(smem_u32(&bar[1]), right);
+  }
+  t.yap = ya + t.p;
+  t.ybp = yb + t.p;
+  t.n_stride = (size_t)n;
+  t.orow = (out && t.own) ? out + ((size_t)lane * lane_rows + 1) * n + start + t.p : nullptr;
+  const int groups = (k + Q - 1) / Q;
+  const int rem = k - (groups - 1) * Q;  // steps of the last group
   if (multi) {
-    if (tid == 0 && k >= 1) mbar_arm(&bar[1], 2 * HX * (int)sizeof(double));
+    if (tid == 0 && groups > 1) mbar_arm(&bar[1], 2 * HQ * (int)sizeof(double));
     cl.sync();
   }
   uint32_t ph0 = 0u, ph1 = 0u;
-  double jp = 0.0;
-  for (int64_t j = 0; j < k; ++j) {
-    const int bb = (int)(j & 1);
-    const double* U = bb ? U1 : U0;
-    double* Un = bb ? U0 : U1;
-    // forcing factors of the next step, loaded a step ahead
-    double n1 = 1.0, n2 = 1.0, n4 = 1.0;
-    if (sc && j + 1 < k) {
-      const double* q = sc + 3 * (s0 + j + 1);
-      n1 = q[0];
-      n2 = q[1];
-      n4 = q[2];
-    }
-    const double cf1 = sc ? c1 * fp : fp, cf2 = sc ? c2 * fp : fp, cf4 = sc ? c4 * fp : fp;
-    double u0 = 0.0, acc = 0.0;
-    if (in1) {
-      u0 = U[p];
-      const double kk = stage_k(b, a, a2, U[p - 1], u0, U[p + 1], cf1);
-      ya[p] = fma(h2, kk, u0);
-      acc = kk;
-    }
-    __syncthreads();
-    if (in2) {
-      const double kk = stage_k(b, a, a2, ya[p - 1], ya[p], ya[p + 1], cf2);
-      yb[p] = fma(h2, kk, u0);
-      acc = fma(2.0, kk, acc);
-    }
-    __syncthreads();
-    if (in3) {
-      const double kk = stage_k(b, a, a2, yb[p - 1], yb[p], yb[p + 1], cf2);
-      ya[p] = fma(dt, kk, u0);
-      acc = fma(2.0, kk, acc);
-    }
-    __syncthreads();
-    if (own) {
-      const double kk = stage_k(b, a, a2, ya[p - 1], ya[p], ya[p + 1], cf4);
-      const double un = fma(dt6, acc + kk, u0);
-      Un[p] = un;
-      if (multi) {
-        if (p < HX)  // my first points are the left neighbour's right halo
-          st_async_f64(map_rank(smem_u32(Un + cnt_left + p), left), un,
-                       map_rank(smem_u32(bb ? &bar[0] : &bar[1]), left));
-        if (p >= cnt - HX)  // my last points are the right neighbour's left halo
-          st_async_f64(map_rank(smem_u32(Un + (p - cnt)), right), un,
-                       map_rank(smem_u32(bb ? &bar[0] : &bar[1]), right));
-      }
-      if (Jdev) {
-        const double d = un - gp;
-        jp = fma(d, d, jp);
-      }
-      if (out) out[((size_t)lane * lane_rows + (size_t)(j + 1)) * n + start + p] = un;
-      if (ckpt && ck_left == 1) ckpt[(size_t)((s0 + j + 1) / ck_every) * n + start + p] = un;
-    }
-    if (ckpt) ck_left = ck_left == 1 ? ck_every : ck_left - 1;
-    c1 = n1;
-    c2 = n2;
-    c4 = n4;
-    if (multi) {
-      // arm the barrier of state j+2 (its previous phase, state j, completed a step ago)
-      if (tid == 0 && j + 2 <= k) mbar_arm(bb ? &bar[1] : &bar[0], 2 * HX * (int)sizeof(double));
-      mbar_wait_bounded(bb ? &bar[0] : &bar[1], bb ? ph0 : ph1, status);
-      if (bb) ph0 ^= 1u; else ph1 ^= 1u;
-      __syncthreads();
+  int j = 0;  // steps done
+  for (int grp = 0; grp < groups; ++grp) {
+    const int x = grp & 1;
+    double* const Ax = x ? A1 : A0;
+    double* const Bx = x ? B1 : B0;
+    double* const An = x ? A0 : A1;
+    const bool more = grp + 1 < groups;
+    const double* in = Ax;
+    if (more || rem == Q) {
+#pragma unroll
+      for (int m = 0; m < Q; ++m) rk4_step<FORCED, Q>(t, j + m, m, 0, x, in, Ax, Bx, An, more);
+      j += Q;
     } else {
-      __syncthreads();
-      for (int q = tid; q < 2 * HX; q += blockDim.x) {
-        const int pp = q < HX ? q - HX : cnt + (q - HX);
-        Un[pp] = Un[((pp % n) + n) % n];
+      for (int m = Q - rem; m < Q; ++m, ++j) rk4_step<FORCED, Q>(t, j, m, Q - rem, x, in, Ax, Bx, An, more);
+    }
+    if (more) {
+      if (multi) {
+        // arm the barrier of the exchange after the next group, then wait for this one
+        if (tid == 0 && grp + 2 < groups) mbar_arm(x ? &bar[1] : &bar[0], 2 * HQ * (int)sizeof(double));
+        mbar_wait_bounded(x ? &bar[0] : &bar[1], x ? ph0 : ph1, status);
+        if (x) ph0 ^= 1u; else ph1 ^= 1u;
+        __syncthreads();
+      } else {
+        __syncthreads();
+        for (int q = tid; q < 2 * HQ; q += blockDim.x) {
+          const int pp = q < HQ ? q - HQ : cnt + (q - HQ);
+          An[pp] = An[((pp % n) + n) % n];
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   if (Jdev) {
-    const double part = block_sum(jp, red + 16);
+    const double part = block_sum(t.jp, red + 16);
     if (multi) {
       double* r0 = cl.map_shared_rank(red, 0);
       if (tid == 0) r0[rank] = part;
@@ -202,6 +323,38 @@ __global__ void bu1_rk4_sweep_kernel(int n, double b, double a, double dt, int64
   if (multi) cl.sync();  // no CTA leaves while a neighbour could still address it
 }
 
+// Steps per exchange Q in {1, 2, 4}: every CTA must own the 4Q-point halo its neighbours
+// need and the threads (chunk + 2 (4Q - 1) points) must fit in one CTA; among those, the
+// Q with the least estimated time per step (27 FP64 warp instructions per step at 64
+// cycles on each of the 4 SM sub-partitions, ~600 cycles per exchange).
+static bool rk4_group_ok(int n, int C, int q) {
+  const int nc = (n + C - 1) / C, last = n - (C - 1) * nc;
+  if (nc + 2 * (4 * q - 1) > 1024) return false;
+  if (q > 1 && C > 1 && last < 4 * q) return false;
+  if (q > 1 && C == 1 && n < 4 * q) return false;
+  return true;
+}
+
+static int rk4_group(int n, int C, int want) {
+  if (want == 4 || want == 2 || want == 1)
+    for (int q = want; q >= 1; q /= 2)
+      if (rk4_group_ok(n, C, q)) return q;
+  const int nc = (n + C - 1) / C;
+  int best = 1;
+  double best_cost = 1e30;
+  for (int q : {1, 2, 4}) {
+    const int npts = nc + 2 * (4 * q - 1);
+    if (!rk4_group_ok(n, C, q)) continue;
+    const int warps = (npts + 31) / 32;
+    const double cost = (double)((warps + 3) / 4) * 27 * 64 + (C > 1 ? 600.0 : 100.0) / q;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = q;
+    }
+  }
+  return best;
+}
+
 bool bu1_rk4_valid_cluster(int n, int C) {
   if (C < 1 || C > 16) return false;
   const int nc = (n + C - 1) / C;
@@ -210,44 +363,77 @@ bool bu1_rk4_valid_cluster(int n, int C) {
   return n - (C - 1) * nc >= HX;  // every CTA owns the 4 points a neighbour needs
 }
 
+// out = sum of parts[0..count) in order (one thread); NONFINITE status if not finite.
+__global__ void sum_parts_kernel(int count, const double* __restrict__ parts, double* __restrict__ out,
+                                 int* status) {
+  double s = 0.0;
+  for (int i = 0; i < count; ++i) s += parts[i];
+  *out = s;
+  if (!isfinite(s)) set_status(status, PXA_ERR_NONFINITE);
+}
+
+cudaError_t launch_sum_parts(cudaStream_t st, int count, const double* parts, double* out, int* status) {
+  sum_parts_kernel<<<1, 1, 0, st>>>(count, parts, out, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, double omega, double* sc) {
   const unsigned blocks = (unsigned)((K + 255) / 256);
   bu1_forcing_table_kernel<<<blocks, 256, 0, st>>>(K, dt, omega, sc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bu1_rk4_sweep(cudaStream_t st, int C, int lanes, int n, double L, double nu,
-                                 double dt, int64_t k, const double* f, const double* sc,
-                                 const double* x0, double* out, int64_t lane_rows, const double* gt,
-                                 double T, double* Jdev, double* ckpt, int64_t ck_every,
-                                 int* status) {
-  const double h = L / n;
-  const double b = 1.0 / (2.0 * h), a = nu / (h * h);
-  const int nc = (n + C - 1) / C;
-  const size_t sh = sizeof(double) * (4 * (size_t)(nc + 2 * HX) + 64);
-  const void* fn = (const void*)bu1_rk4_sweep_kernel;
+template <bool FORCED, int Q>
+static cudaError_t launch_rk4_q(cudaStream_t st, int C, int lanes, int nc, void** args,
+                                int priority, size_t reserve) {
+  size_t sh = sizeof(double) * (6 * (size_t)(nc + 8 * Q) + 64);
+  if (reserve > sh) sh = reserve;
+  const void* fn = (const void*)bu1_rk4_sweep_kernel<FORCED, Q>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   if (C > 8) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  int threads = ((nc + 6 + 31) / 32) * 32;
-  void* args[] = {&n, (void*)&b, (void*)&a, &dt, &k, &f, &sc, &x0, &out, &lane_rows, &gt, &T, &Jdev,
-                  &ckpt, &ck_every, &status};
+  const int npts = nc + 2 * (4 * Q - 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * lanes);
-  cfg.blockDim = dim3(threads);
+  cfg.blockDim = dim3(((npts + 31) / 32) * 32);
   cfg.dynamicSmemBytes = sh;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = priority;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_bu1_rk4_sweep(cudaStream_t st, int C, int lanes, int n, double L, double nu,
+                                 double dt, int64_t k, const double* f, const double* sc,
+                                 const double* x0, double* out, int64_t lane_rows, const double* gt,
+                                 double T, double* Jdev, double* ckpt, int64_t ck_every,
+                                 int* status, int priority, size_t reserve_smem, int group) {
+  const double h = L / n;
+  double b = 1.0 / (2.0 * h), a = nu / (h * h);
+  const int nc = (n + C - 1) / C;
+  // step counts and row indices fit in int (K < 2^31); element offsets use size_t
+  int ki = (int)k, lr = (int)lane_rows, ce = (int)ck_every;
+  void* args[] = {&n, &b, &a, &dt, &ki, &f, &sc, &x0, &out, &lr, &gt, &T, &Jdev,
+                  &ckpt, &ce, &status};
+  const int q = rk4_group(n, C, group);
+  if (sc) {
+    if (q == 4) return launch_rk4_q<true, 4>(st, C, lanes, nc, args, priority, reserve_smem);
+    if (q == 2) return launch_rk4_q<true, 2>(st, C, lanes, nc, args, priority, reserve_smem);
+    return launch_rk4_q<true, 1>(st, C, lanes, nc, args, priority, reserve_smem);
+  }
+  if (q == 4) return launch_rk4_q<false, 4>(st, C, lanes, nc, args, priority, reserve_smem);
+  if (q == 2) return launch_rk4_q<false, 2>(st, C, lanes, nc, args, priority, reserve_smem);
+  return launch_rk4_q<false, 1>(st, C, lanes, nc, args, priority, reserve_smem);
 }
 
 }  // namespace pxa

@@ -66,6 +66,17 @@ struct pxa_ctx {
   int cl_band_lanes = 1, cl_band_chain = 1;
   int cl_rk4_direct = 1, cl_rk4_lanes = 1;  // cluster sizes of the RK4 sweeps (direct, recompute)
   double* sc = nullptr;       // [K][3] forcing factors s(t) at the stage times (omega != 0)
+  // hybrid overlap: the direct runs in chunks on the caller's stream while a library-owned
+  // low-priority stream builds the band records and runs the adjoint lanes of finished chunks
+  bool overlap = true;
+  int q_direct = 0, q_sweep = 0;  // steps per halo exchange of the RK4 / banded sweeps (0 = auto)
+  cudaStream_t side = nullptr;
+  static constexpr int kMaxChunks = 8;
+  cudaEvent_t ev_fork[kMaxChunks] = {};
+  cudaEvent_t ev_join = nullptr;
+  double* Jparts = nullptr;   // [kMaxChunks] objective of each direct chunk
+  int prio_hi = 0, prio_lo = 0;
+  size_t reserve_smem = 0;    // dynamic shared memory that makes a direct CTA own its SM
   double* rec = nullptr;      // [(K+1)][n][BU1_BAND_RECORD] rows of M_s^T and sources
   double* jt = nullptr;       // [K][n][BU1_BAND_RECORD] transposed stage rows (gradient)
   double* LI = nullptr;       // [(K+1)][n] adjoint lane rows
@@ -140,7 +151,20 @@ void release_workspace(pxa_ctx* c) {
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
   c->lanesL = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
-  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = nullptr;
+  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = nullptr;
+  if (c->side) {
+    cudaStreamDestroy(c->side);
+    c->side = nullptr;
+  }
+  for (auto& e : c->ev_fork)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  if (c->ev_join) {
+    cudaEventDestroy(c->ev_join);
+    c->ev_join = nullptr;
+  }
   c->band = false;
 }
 
@@ -312,7 +336,20 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->LI, rows1))) return rc;
       if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
       if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
+      if ((rc = alloc(c, &c->Jparts, pxa_ctx::kMaxChunks))) return rc;
       c->band = true;
+      int least = 0, greatest = 0;
+      PXA_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
+      c->prio_lo = least;
+      c->prio_hi = greatest;
+      PXA_CUDA(c, cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, least), "side stream");
+      for (auto& e : c->ev_fork) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+      PXA_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+      int optin = 0;
+      PXA_CUDA(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device),
+               "smem opt-in");
+      // leave room for the kernel's static shared memory within the per-CTA limit
+      c->reserve_smem = optin > 4096 ? (size_t)(optin - 2048) : 0;
     }
   }
   if (c->op.kind == PXA_BURGERS_1D) {
@@ -362,6 +399,8 @@ int prepare(pxa_ctx* c) {
   c->stats.cluster_lanes = c->band ? c->cl_band_lanes : c->cl_lanes;
   c->stats.cluster_chain = c->band ? c->cl_band_chain : c->cl_chain;
   c->stats.adjoint_band = c->band ? 1 : 0;
+  c->stats.group_direct = c->q_direct;
+  c->stats.group_sweep = c->q_sweep;
   c->ready = true;
   return PXA_OK;
 }
@@ -453,18 +492,71 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     PXA_CUDA(c, launch_bu1_forcing_table(st, K, dt, c->omega, c->sc), "forcing table");
     sc = c->sc;
   }
-  if (do_d) {
+  // Banded adjoint layout: the stepper chain covers the top subinterval itself (so lanes
+  // 0..P-2 run separately); with exp(tA) (Magnus) all P lanes run and the chain uses W[P-1].
+  const bool chain_top = c->band && (P == 1 || c->kry_phi == PXA_PHI_STEPPER);
+  const int side_lanes = chain_top ? P - 1 : P;
+  // With the overlap enabled the direct always runs in the same chunks (also for a direct
+  // solve alone), so that J is summed in the same order whichever call computed it.
+  const bool chunked = c->band && c->overlap && full && c->side;
+  const bool overlap = chunked && do_d && do_a;
+  if (do_d && chunked) {
+    // Hybrid overlap (Sec. 3.3): the serial direct runs in chunks of whole subintervals on
+    // this stream (high priority, each CTA owning its SM); after each chunk the side
+    // stream builds the band records of its rows and runs the adjoint lanes whose
+    // subintervals it completed, while the next chunk steps on.
+    ev_record(c, 0);
+    const int NC = P > 1 ? (P < pxa_ctx::kMaxChunks ? P : pxa_ctx::kMaxChunks) : pxa_ctx::kMaxChunks;
+    const int64_t kc = P > 1 ? ((int64_t)((P + NC - 1) / NC)) * k : (K + NC - 1) / NC;
+    int nch = 0;
+    for (int ci = 0; ci < NC; ++ci) {
+      const int64_t b0 = ci * kc, b1 = (ci + 1) * kc < K ? (ci + 1) * kc : K;
+      if (b0 >= K) break;
+      PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, b1 - b0,
+                                       c->control, sc ? sc + 3 * b0 : nullptr,
+                                       ci == 0 ? nullptr : c->traj + (size_t)b0 * n,
+                                       c->traj + (size_t)b0 * n, 0, c->target, c->T, c->Jparts + ci,
+                                       nullptr, 1, c->status, c->prio_hi, c->reserve_smem,
+                                       c->q_direct),
+               "direct chunk");
+      if (overlap) {
+        PXA_CUDA(c, cudaEventRecord(c->ev_fork[ci], st), "fork");
+        PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork[ci], 0), "fork wait");
+        PXA_CUDA(c, launch_bu1_band_prepass(c->side, n, c->op.L, c->op.nu, dt, c->T, c->omega,
+                                            c->control, c->target, c->traj, 0, P, ci == 0 ? 0 : b0 + 1,
+                                            b1 + 1, K, c->rec, c->jt, c->prio_lo), "band prepass");
+        const int l0 = (int)(b0 / k), l1 = (int)(b1 / k) < side_lanes ? (int)(b1 / k) : side_lanes;
+        if (l1 > l0)
+          PXA_CUDA(c, launch_bu1_band_sweep(c->side, c->cl_band_lanes, l1 - l0, l0, n, c->rec, k, P, 0,
+                                            nullptr, c->LI, c->E, c->status, c->prio_lo, c->q_sweep),
+                                            "band lanes");
+      }
+      ++nch;
+    }
+    PXA_CUDA(c, launch_sum_parts(st, nch, c->Jparts, Jdev, c->status), "J");
+    ev_record(c, 1);
+    if (overlap) {
+      ev_record(c, 2);
+      PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
+      PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
+      if (c->timing && c->ev_ready) {
+        cudaEventRecord(c->ev[6], st);
+        c->prep_marked = true;
+      }
+      ev_record(c, 3);
+    }
+  } else if (do_d) {
     ev_record(c, 0);
     // direct (Eq. seriesDirect) on one cluster; every state (full storage) or the P+1
     // subinterval boundaries (checkpoints) are kept
     PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, K, c->control,
                                      sc, nullptr, full ? c->traj : nullptr, 0, c->target, c->T, Jdev,
-                                     full ? nullptr : c->traj, k, c->status), "direct");
+                                     full ? nullptr : c->traj, k, c->status, 0, 0, c->q_direct), "direct");
     ev_record(c, 1);
   }
   if (!do_a) return PXA_OK;
-  ev_record(c, 2);
-  if (c->band) {
+  if (!overlap) ev_record(c, 2);
+  if (c->band && !overlap) {
     // Banded discrete adjoint: stored (or recomputed) states -> rows of M_s^T (parallel),
     // P adjoint lanes + the homogeneous chain as 9-tap recursions, then the forcing
     // gradient over all steps (parallel).
@@ -473,35 +565,40 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     if (!full) {
       PXA_CUDA(c, launch_bu1_rk4_sweep(st, P == 1 ? c->cl_rk4_direct : c->cl_rk4_lanes, P, n,
                                        c->op.L, c->op.nu, dt, k, c->control, sc, c->traj, c->scratch,
-                                       k + 1, nullptr, c->T, nullptr, nullptr, 1, c->status),
+                                       k + 1, nullptr, c->T, nullptr, nullptr, 1, c->status, 0, 0,
+                                       c->q_direct),
                "recompute");
       rows = c->scratch;
       lane_k = k;
     }
     PXA_CUDA(c, launch_bu1_band_prepass(st, n, c->op.L, c->op.nu, dt, c->T, c->omega, c->control,
-                                        c->target, rows, lane_k, P, 0, K + 1, K, c->rec, c->jt),
+                                        c->target, rows, lane_k, P, 0, K + 1, K, c->rec, c->jt, 0),
              "band prepass");
     if (c->timing && c->ev_ready) {
       cudaEventRecord(c->ev[6], st);
       c->prep_marked = true;
     }
-    PXA_CUDA(c, launch_bu1_band_sweep(st, P == 1 ? c->cl_band_chain : c->cl_band_lanes, P, n, c->rec,
-                                      k, P, 0, nullptr, c->LI, c->E, c->status), "band lanes");
+    PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_lanes, side_lanes, 0, n, c->rec, k, P, 0, nullptr,
+                                      c->LI, c->E, c->status, 0, c->q_sweep), "band lanes");
     ev_record(c, 3);
-    const bool chain = P > 1 && c->kry_phi == PXA_PHI_STEPPER;
-    if (chain) {
-      PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, n, c->rec, k, P, 1, c->E, c->Hrows,
-                                        nullptr, c->status), "band chain");
-    } else if (P > 1) {
+  }
+  if (c->band) {
+    const double* rows = full ? c->traj : c->scratch;
+    const int64_t lane_k = full ? 0 : k;
+    if (chain_top) {
+      // the top subinterval with its source, then the summed homogeneous problems
+      PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, 0, n, c->rec, k, P, 1, c->E, c->Hrows,
+                                        nullptr, c->status, 0, c->q_sweep), "band chain");
+    } else {
       PXA_CUDA(c, launch_bu1_magnus_chain(st, n > 2048 ? 1024 : 512, g, dt, K, P, k, c->magnus_M,
                                           c->omega, rows, lane_k, c->E, c->hsum, c->V, c->kry_m,
                                           c->kry_tol, c->v_in_smem, c->status, c->errmax),
                "magnus chain");
     }
     ev_record(c, 4);
-    PXA_CUDA(c, launch_bu1_band_grad(st, n, dt, c->omega, K, chain ? (int64_t)(P - 1) * k : 0, c->LI,
-                                     chain ? c->Hrows : nullptr, c->jt, c->gpart,
-                                     (P > 1 && !chain) ? c->hsum : nullptr, grad, c->status),
+    PXA_CUDA(c, launch_bu1_band_grad(st, n, dt, c->omega, K, chain_top ? (int64_t)(P - 1) * k : K,
+                                     side_lanes > 0 ? c->LI : nullptr, chain_top ? c->Hrows : nullptr,
+                                     c->jt, c->gpart, chain_top ? nullptr : c->hsum, grad, c->status),
              "band gradient");
     ev_record(c, 5);
     return PXA_OK;
@@ -757,6 +854,25 @@ int pxa_set_adjoint(pxa_ctx* c, int impl) {
   return PXA_OK;
 }
 
+int pxa_set_groups(pxa_ctx* c, int q_direct, int q_sweep) {
+  if (!c) return PXA_ERR_INVALID;
+  for (int q : {q_direct, q_sweep})
+    if (q != 0 && q != 1 && q != 2 && q != 4) return fail(c, PXA_ERR_INVALID, "group sizes are 0, 1, 2 or 4");
+  c->q_direct = q_direct;
+  c->q_sweep = q_sweep;
+  c->stats.group_direct = q_direct;
+  c->stats.group_sweep = q_sweep;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_overlap(pxa_ctx* c, int enable) {
+  if (!c) return PXA_ERR_INVALID;
+  c->overlap = enable != 0;
+  invalidate(c);
+  return PXA_OK;
+}
+
 int pxa_set_cluster(pxa_ctx* c, int direct, int lanes, int chain) {
   if (!c) return PXA_ERR_INVALID;
   for (int C : {direct, lanes, chain})
@@ -822,7 +938,8 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
         return erc;
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      // kernel nodes keep their own priorities (the direct above the overlapped side work)
+      e = cudaGraphInstantiateWithFlags(&c->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
       c->g_mode = mode;
@@ -1009,8 +1126,47 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   invalidate(c);
   int rc = prepare(c);
   if (rc) return rc;
+  if (c->op.kind == PXA_BURGERS_1D && c->band) {
+    // second pass at the chosen cluster sizes: steps per halo exchange of the direct
+    // sweep and of the banded sweeps (no reallocation needed)
+    const int qd0 = c->q_direct, qs0 = c->q_sweep;
+    int bqd = qd0, bqs = qs0;
+    cudaEvent_t f0, f1;
+    PXA_CUDA(c, cudaEventCreate(&f0), "event");
+    PXA_CUDA(c, cudaEventCreate(&f1), "event");
+    const bool graph2 = c->use_graph, timing2 = c->timing;
+    c->use_graph = false;
+    c->timing = false;
+    for (int qd : {1, 2, 4})
+      for (int qs : {1, 2, 4}) {
+        c->q_direct = qd;
+        c->q_sweep = qs;
+        if (enqueue(c, mode, c->Jdev, grad_dev) != PXA_OK) continue;  // warm-up
+        PXA_CUDA(c, cudaEventRecord(f0, c->stream), "record");
+        int erc = enqueue(c, mode, c->Jdev, grad_dev);
+        PXA_CUDA(c, cudaEventRecord(f1, c->stream), "record");
+        PXA_CUDA(c, cudaEventSynchronize(f1), "sync");
+        if (erc || read_status(c) != PXA_OK) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, f0, f1);
+        if (ms < best) {
+          best = ms;
+          bqd = qd;
+          bqs = qs;
+        }
+      }
+    cudaEventDestroy(f0);
+    cudaEventDestroy(f1);
+    c->use_graph = graph2;
+    c->timing = timing2;
+    c->q_direct = bqd;
+    c->q_sweep = bqs;
+    invalidate(c);
+  }
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;
+  c->stats.group_direct = c->q_direct;
+  c->stats.group_sweep = c->q_sweep;
   if (best_ms_host) *best_ms_host = best;
   return PXA_OK;
 }

@@ -30,7 +30,7 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("ms_adjoint_hom", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("band_taps", ctypes.c_int), ("cluster_direct", ctypes.c_int),
                 ("cluster_lanes", ctypes.c_int), ("cluster_chain", ctypes.c_int),
-                ("ms_adjoint_prep", ctypes.c_float), ("adjoint_band", ctypes.c_int)]
+                ("ms_adjoint_prep", ctypes.c_float), ("adjoint_band", ctypes.c_int),
+                ("group_direct", ctypes.c_int), ("group_sweep", ctypes.c_int)]
 
 
 _lib = None
@@ -86,6 +87,8 @@ def load(path: str = LIB_PATH):
         "pxa_set_target": [p, p],
         "pxa_set_memory": [p, i],
         "pxa_set_adjoint": [p, i],
+        "pxa_set_overlap": [p, i],
+        "pxa_set_groups": [p, i, i],
         "pxa_set_graph": [p, i],
         "pxa_set_cluster": [p, i, i, i],
         "pxa_autotune": [p, i, p, p],
@@ -200,6 +203,12 @@ class Context:
 
     def set_adjoint(self, impl):
         self._check(self._L.pxa_set_adjoint(self._h, impl))
+
+    def set_overlap(self, enable):
+        self._check(self._L.pxa_set_overlap(self._h, 1 if enable else 0))
+
+    def set_groups(self, q_direct=0, q_sweep=0):
+        self._check(self._L.pxa_set_groups(self._h, q_direct, q_sweep))
 
     def set_cluster(self, direct=0, lanes=0, chain=0):
         self._check(self._L.pxa_set_cluster(self._h, int(direct), int(lanes), int(chain)))

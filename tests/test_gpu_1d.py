@@ -436,3 +436,50 @@ def test_burgers_banded_small_grids_and_chunks(X, torch, n, C):
         assert rel(host(out), g0) < 1e-10
     st = ctx.stats()
     assert st["adjoint_band"] == 1
+
+
+@pytest.mark.parametrize("P,phi", [(6, "stepper"), (1, "stepper"), (6, "exp")])
+def test_burgers_overlapped_phases_match_sequential(X, torch, bu_small, P, phi):
+    """The chunked direct with the band records and adjoint lanes on a second stream
+    (hybrid overlap) gives the gradient of the sequential schedule: the same trajectory
+    bit for bit, J up to the summation order of its chunk partials."""
+    b = bu_small
+    ph = X.PHI_STEPPER if phi == "stepper" else X.PHI_EXP
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    res = {}
+    for ov in (True, False):
+        ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, M=10, phi=ph)
+        ctx.set_overlap(ov)
+        ctx.set_control(fd)
+        ctx.set_target(gd_)
+        out = torch.empty_like(fd)
+        mode = X.SERIAL if P == 1 else X.PARAEXP
+        J = ctx.gradient(mode, out)
+        res[ov] = (J, host(out))
+        if phi == "stepper":
+            assert abs(J - b["J"]) / b["J"] < 1e-10
+            assert rel(host(out), b["grad"]) < 1e-10
+        ctx.close()
+    assert abs(res[True][0] - res[False][0]) <= 1e-14 * abs(res[False][0])
+    assert np.array_equal(res[True][1], res[False][1])
+
+
+@pytest.mark.parametrize("qd,qs", [(1, 1), (2, 4), (4, 2)])
+@pytest.mark.parametrize("C", [4, 16])
+def test_burgers_exchange_groups(X, torch, bu_small, qd, qs, C):
+    """Every number of steps per halo exchange (1, 2, 4) of the direct and of the banded
+    sweeps gives the oracle's gradient; the grid of 200 points over 16 CTAs leaves chunks
+    of 13 and 5 points, so the group size falls back where the 4q halo does not fit."""
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    ctx.set_cluster(C, C, C)
+    ctx.set_groups(qd, qs)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd, 1.5)
+    ctx.set_target(gd_)
+    J0, g0 = O.bu1_gradient_serial(b["f"], b["g"], b["nu"], b["T"], b["K"], omega=1.5)
+    out = torch.empty_like(fd)
+    for mode in (X.SERIAL, X.PARAEXP):
+        J = ctx.gradient(mode, out)
+        assert abs(J - J0) / J0 < 1e-10
+        assert rel(host(out), g0) < 1e-10
