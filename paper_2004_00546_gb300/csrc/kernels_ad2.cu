@@ -510,11 +510,16 @@ static EncodeTiledFn encode_fn() {
 
 // 3D tiled map over `depth` padded planes [Hp][Wp] of FP32 with box (BX2, BY2, box_depth).
 bool ad2_make_map(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_depth) {
+  return ad2_make_map_box(map, base, p, depth, BX2, BY2, box_depth);
+}
+
+bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_x,
+                      int box_y, int box_depth) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)p.Wp, (cuuint64_t)p.Hp, (cuuint64_t)depth};
   cuuint64_t strides[2] = {(cuuint64_t)p.Wp * sizeof(float), (cuuint64_t)p.Wp * p.Hp * sizeof(float)};
-  cuuint32_t box[3] = {(cuuint32_t)BX2, (cuuint32_t)BY2, (cuuint32_t)box_depth};
+  cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_depth};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

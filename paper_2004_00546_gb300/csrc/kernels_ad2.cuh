@@ -24,6 +24,9 @@ struct Ad2Params {
 
 size_t ad2_smem_bytes();
 bool ad2_make_map(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_depth);
+// 3D map over [depth][Hp][Wp] FP32 with a box of box_x x box_y x box_depth elements.
+bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_x,
+                      int box_y, int box_depth);
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, float* traj,
@@ -40,6 +43,17 @@ cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, 
                             const float* traj, int64_t row0, int64_t row_step, double scale);
 cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, const float* src);
 cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* J, int* status);
+// Register-wavefront RK4 step for many lanes (kernels_ad2_roll.cu); needs ad2_roll_ok.
+bool ad2_roll_ok(const Ad2Params& p);
+cudaError_t launch_ad2_forcing_table(cudaStream_t st, int64_t s0, int64_t count, double dt,
+                                     double omega, float* sc);
+// qmap: ad2_make_map_box over the state buffers (depth 2*lanes: z = buf*lanes + lane) with
+// box {64, AD2_ROLL_BR, 1}; cmap: over the coefficient array (depth 3) with box
+// {64, AD2_ROLL_BR, 3}. buf_in selects the input buffer; the output is the other one.
+constexpr int AD2_ROLL_BR = 4;
+cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
+                                const Ad2Params& p, float* states, int lanes, int buf_in,
+                                const float* sc, int sc_stride, int* status);
 cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
                                 const double* extra, double* grad, int* status);
 

@@ -562,9 +562,7 @@ static size_t sweep_smem(int nc, int q, int depth) {
 }
 
 // Steps per exchange Q in {1, 2, 4}: every CTA must own the 4Q-point halo its neighbours
-// need, and the threads (chunk + 2 (4Q - 4) points) must fit in one CTA. Among those, the
-// Q with the least estimated time per step: one FP64 warp instruction per 64 cycles on
-// each of the 4 SM sub-partitions, 9 per point and step, and ~600 cycles per exchange.
+// need, and the threads (chunk + 2 (4Q - 4) points) must fit in one CTA.
 static bool sweep_group_ok(int n, int C, int q) {
   const int nc = (n + C - 1) / C, last = n - (C - 1) * nc;
   if (nc + 2 * (4 * q - 4) > 1024) return false;
@@ -573,24 +571,15 @@ static bool sweep_group_ok(int n, int C, int q) {
   return true;
 }
 
+// The requested Q, or the largest valid smaller one. Without a request: Q = 1. Measured
+// on GB300 at n = 1024 over 16 CTAs, grouping the 9-tap steps (Q = 4: 88 points on 3
+// warps) was slower than one exchange per step (64 points on 2 warps), unlike the RK4
+// sweep; the autotuner still tries 2 and 4.
 static int sweep_group(int n, int C, int want) {
   if (want == 4 || want == 2 || want == 1)
     for (int q = want; q >= 1; q /= 2)
       if (sweep_group_ok(n, C, q)) return q;
-  const int nc = (n + C - 1) / C;
-  int best = 1;
-  double best_cost = 1e30;
-  for (int q : {1, 2, 4}) {
-    const int npts = nc + 2 * (4 * q - 4);
-    if (!sweep_group_ok(n, C, q)) continue;
-    const int warps = (npts + 31) / 32;
-    const double cost = (double)((warps + 3) / 4) * 9 * 64 + 600.0 / q;
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = q;
-    }
-  }
-  return best;
+  return 1;
 }
 
 template <int Q>

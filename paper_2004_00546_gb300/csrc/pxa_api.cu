@@ -104,6 +104,9 @@ struct pxa_ctx {
   CUtensorMap mapD, mapA, mapC, mapCoef;
   float* stL = nullptr;     // pxa_rk4_lanes_2d states [2][lanesL][Hp][Wp]
   int lanesL = 0;
+  float* scL = nullptr;     // pxa_rk4_lanes_2d forcing factors [lanes * steps][3]
+  int64_t scL_count = 0;
+  CUtensorMap mapL4, mapC4; // row-block maps of the lane states and coefficients (wavefront)
   CUtensorMap mapL;
 
   // graph cache
@@ -150,6 +153,8 @@ void release_workspace(pxa_ctx* c) {
   c->status = nullptr;
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
   c->lanesL = 0;
+  c->scL = nullptr;
+  c->scL_count = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = nullptr;
   if (c->side) {
@@ -1231,7 +1236,9 @@ int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, doub
   const size_t plane = (size_t)a.Hp * a.Wp, N = (size_t)a.nx * a.ny;
   if (c->lanesL != lanes) {
     if ((rc = alloc(c, &c->stL, 2 * (size_t)lanes * plane))) return rc;
-    if (!ad2_make_map(&c->mapL, c->stL, a, 2 * lanes, 1))
+    if (!ad2_make_map(&c->mapL, c->stL, a, 2 * lanes, 1) ||
+        !ad2_make_map_box(&c->mapL4, c->stL, a, 2 * lanes, 64, AD2_ROLL_BR, 1) ||
+        !ad2_make_map_box(&c->mapC4, c->coef2, a, 3, 64, AD2_ROLL_BR, 3))
       return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the lane states");
     c->lanesL = lanes;
   }
@@ -1242,10 +1249,24 @@ int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, doub
   PXA_CUDA(c, cudaEventCreate(&e0), "event");
   PXA_CUDA(c, cudaEventCreate(&e1), "event");
   const int lpc = lanes >= 16 ? 16 : lanes;
+  // lane l takes steps l*steps .. l*steps+steps-1 of one time axis
+  const bool roll = ad2_roll_ok(a);
+  if (roll && c->scL_count < (int64_t)lanes * steps) {
+    if ((rc = alloc(c, &c->scL, 3 * (size_t)lanes * steps))) return rc;
+    c->scL_count = (int64_t)lanes * steps;
+  }
+  if (roll)
+    PXA_CUDA(c, launch_ad2_forcing_table(st, 0, (int64_t)lanes * steps, a.dtd, a.omega, c->scL), "table");
   PXA_CUDA(c, cudaEventRecord(e0, st), "record");
-  for (int64_t s = 0; s < steps; ++s)
-    PXA_CUDA(c, launch_ad2_rk4(st, c->mapL, c->mapCoef, a, c->stL, lanes, lanes, lpc, (int)(s & 1),
-                               steps, s, nullptr, 0, nullptr, 0, 0.0, c->status), "lanes step");
+  for (int64_t s = 0; s < steps; ++s) {
+    if (roll) {
+      PXA_CUDA(c, launch_ad2_rk4_roll(st, c->mapL4, c->mapC4, a, c->stL, lanes, (int)(s & 1),
+                                      c->scL + 3 * s, (int)steps, c->status), "lanes step");
+    } else {
+      PXA_CUDA(c, launch_ad2_rk4(st, c->mapL, c->mapCoef, a, c->stL, lanes, lanes, lpc, (int)(s & 1),
+                                 steps, s, nullptr, 0, nullptr, 0, 0.0, c->status), "lanes step");
+    }
+  }
   PXA_CUDA(c, cudaEventRecord(e1, st), "record");
   PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
   float ms = 0.f;
