@@ -61,8 +61,13 @@ SM_CLOCK_HZ = 2.07e9
 # DRAM bytes per launch from the committed ncu captures (profiles/*.md); None when the
 # kernel changed after the capture.
 TRAFFIC = {
-    "ad1_chain_kernel": 91.4e3,
+    "ad1_chain_kernel": 82.7e3,
     "cn_lanes_kernel": 12.0e3,
+    # the direct solve is 8 chunk launches of 61.95 KB DRAM reads each (the trajectory
+    # rows stay in L2 during the launch)
+    "bu1_rk4_sweep_kernel": 8 * 61.95e3,
+    "bu1_band_sweep_kernel": 1.6407e9 + 0.1587e9,
+    "bu1_band_prepass_kernel": 8 * (30.49e6 + 357.0e6),
 }
 
 
