@@ -91,9 +91,12 @@ typedef enum { PXA_STORE_FULL = 0, PXA_STORE_CHECKPOINTS = 1 } pxa_memory;
  * once as a 9-diagonal band by a parallel pass over the stored (or recomputed) states,
  * and the adjoint lanes and the homogeneous chain become 9-tap recursions; used when
  * its records (about 21 doubles per step and grid point) fit in half of the free
- * device memory. RESTEP: every reverse step re-evaluates the four stages and applies
- * their transposed Jacobians in turn (no per-step storage beyond the states). */
-typedef enum { PXA_ADJ_BANDED = 0, PXA_ADJ_RESTEP = 1 } pxa_adjoint;
+ * device memory; the serial chain then takes two steps per halo exchange with the
+ * product bands M_s^T M_{s+1}^T where no lane value is added in between. BANDED_SINGLE:
+ * the same with one step per exchange. RESTEP: every reverse step re-evaluates the four
+ * stages and applies their transposed Jacobians in turn (no per-step storage beyond the
+ * states). */
+typedef enum { PXA_ADJ_BANDED = 0, PXA_ADJ_RESTEP = 1, PXA_ADJ_BANDED_SINGLE = 2 } pxa_adjoint;
 
 typedef struct {
   int kind;   /* pxa_problem */

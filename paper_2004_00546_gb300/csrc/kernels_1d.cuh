@@ -66,6 +66,7 @@ cudaError_t launch_sum_parts(cudaStream_t st, int count, const double* parts, do
 // Banded discrete adjoint of the Burgers RK4 map (kernels_bu1_band.cu). A record holds
 // the 9 taps of row i of M_s^T and the objective's source dJ/du_s[i].
 constexpr int BU1_BAND_RECORD = 10;
+constexpr int BU1_PAIR_RECORD = 18;  // 17 taps of a row of M_s^T M_{s+1}^T + combined source
 constexpr int BU1_BAND_MAX_CHUNK = 1024;  // points per CTA of the banded sweep
 bool bu1_band_valid_cluster(int n, int C);
 int bu1_band_grad_blocks(int64_t K, int n);
@@ -80,6 +81,16 @@ cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int lane
 cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
                                  int64_t li_top, const double* LI, const double* H, const double* jt,
                                  double* partial, const double* extra, double* grad, int* status);
+// Two-step banded chain (kernels_bu1_pair.cu).
+int bu1_chain2_plan(int64_t K, int64_t k, int P, int4* out);
+bool bu1_chain2_valid(int n, int C);
+cudaError_t launch_bu1_band_pair(cudaStream_t st, int n, const double* rec, int64_t m_lo,
+                                 int64_t m_hi, double* rp, int priority);
+cudaError_t launch_bu1_band_chain2(cudaStream_t st, int C, int n, const double* rec, const double* rp,
+                                   const int4* plan, int nplan, int s_hi, const double* W,
+                                   double* out_rows, int* status);
+cudaError_t launch_bu1_band_fill(cudaStream_t st, int n, const double* rec, const int4* plan, int nplan,
+                                 double* rows);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);
 cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);

@@ -82,6 +82,12 @@ struct pxa_ctx {
   double* LI = nullptr;       // [(K+1)][n] adjoint lane rows
   double* Hrows = nullptr;    // [(K+1)][n] homogeneous chain rows
   double* gpart = nullptr;    // [blocks][n] gradient partial sums
+  // two-step chain: pair records and the step plans of the Paraexp and serial chains
+  bool pair_chain = true;
+  double* rp = nullptr;       // [K/2][n][BU1_PAIR_RECORD]
+  int4* plan_par = nullptr;
+  int4* plan_ser = nullptr;
+  int nplan_par = 0, nplan_ser = 0;
   double* Jdev = nullptr;     // 1
   double* errmax = nullptr;   // 1
   int* status = nullptr;      // 1
@@ -156,7 +162,9 @@ void release_workspace(pxa_ctx* c) {
   c->scL = nullptr;
   c->scL_count = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
-  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = nullptr;
+  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = nullptr;
+  c->plan_par = c->plan_ser = nullptr;
+  c->nplan_par = c->nplan_ser = 0;
   if (c->side) {
     cudaStreamDestroy(c->side);
     c->side = nullptr;
@@ -331,8 +339,9 @@ int prepare(pxa_ctx* c) {
     // otherwise the adjoint re-steps the stages (kernels_bu1_cluster.cu).
     if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
     const size_t rows1 = (size_t)(c->K + 1) * n;
+    const size_t pair_doubles = c->pair_chain ? (size_t)(c->K / 2) * n * BU1_PAIR_RECORD : 0;
     const size_t band_doubles = rows1 * BU1_BAND_RECORD + (size_t)c->K * n * BU1_BAND_RECORD +
-                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n;
+                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n + pair_doubles;
     size_t free_b = 0, total_b = 0;
     PXA_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
     if (c->band_req != 0 && band_doubles * sizeof(double) <= free_b / 2) {
@@ -342,6 +351,19 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
       if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
       if ((rc = alloc(c, &c->Jparts, pxa_ctx::kMaxChunks))) return rc;
+      if (c->pair_chain) {
+        if ((rc = alloc(c, &c->rp, pair_doubles))) return rc;
+        // step plans of the chain for the Paraexp partition and for serial stepping
+        std::vector<int4> plan((size_t)c->K);
+        c->nplan_par = bu1_chain2_plan(c->K, k, P, plan.data());
+        if ((rc = alloc(c, &c->plan_par, (size_t)c->nplan_par))) return rc;
+        PXA_CUDA(c, cudaMemcpy(c->plan_par, plan.data(), sizeof(int4) * c->nplan_par, cudaMemcpyHostToDevice),
+                 "copy plan");
+        c->nplan_ser = bu1_chain2_plan(c->K, c->K, 1, plan.data());
+        if ((rc = alloc(c, &c->plan_ser, (size_t)c->nplan_ser))) return rc;
+        PXA_CUDA(c, cudaMemcpy(c->plan_ser, plan.data(), sizeof(int4) * c->nplan_ser, cudaMemcpyHostToDevice),
+                 "copy plan");
+      }
       c->band = true;
       int least = 0, greatest = 0;
       PXA_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
@@ -530,6 +552,9 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
         PXA_CUDA(c, launch_bu1_band_prepass(c->side, n, c->op.L, c->op.nu, dt, c->T, c->omega,
                                             c->control, c->target, c->traj, 0, P, ci == 0 ? 0 : b0 + 1,
                                             b1 + 1, K, c->rec, c->jt, c->prio_lo), "band prepass");
+        if (c->rp)
+          PXA_CUDA(c, launch_bu1_band_pair(c->side, n, c->rec, (b0 + 1) / 2, (b1 + 1) / 2, c->rp,
+                                           c->prio_lo), "pair records");
         const int l0 = (int)(b0 / k), l1 = (int)(b1 / k) < side_lanes ? (int)(b1 / k) : side_lanes;
         if (l1 > l0)
           PXA_CUDA(c, launch_bu1_band_sweep(c->side, c->cl_band_lanes, l1 - l0, l0, n, c->rec, k, P, 0,
@@ -579,6 +604,7 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     PXA_CUDA(c, launch_bu1_band_prepass(st, n, c->op.L, c->op.nu, dt, c->T, c->omega, c->control,
                                         c->target, rows, lane_k, P, 0, K + 1, K, c->rec, c->jt, 0),
              "band prepass");
+    if (c->rp) PXA_CUDA(c, launch_bu1_band_pair(st, n, c->rec, 0, K / 2, c->rp, 0), "pair records");
     if (c->timing && c->ev_ready) {
       cudaEventRecord(c->ev[6], st);
       c->prep_marked = true;
@@ -590,7 +616,15 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (c->band) {
     const double* rows = full ? c->traj : c->scratch;
     const int64_t lane_k = full ? 0 : k;
-    if (chain_top) {
+    if (chain_top && c->rp && bu1_chain2_valid(n, c->cl_band_chain)) {
+      // the top subinterval with its source, then the summed homogeneous problems, two
+      // steps per exchange where the plan allows; then the rows skipped inside pair steps
+      const int4* plan = P == 1 ? c->plan_ser : c->plan_par;
+      const int np = P == 1 ? c->nplan_ser : c->nplan_par;
+      PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan, np, (int)K, c->E,
+                                         c->Hrows, c->status), "band chain");
+      PXA_CUDA(c, launch_bu1_band_fill(st, n, c->rec, plan, np, c->Hrows), "band fill");
+    } else if (chain_top) {
       // the top subinterval with its source, then the summed homogeneous problems
       PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, 0, n, c->rec, k, P, 1, c->E, c->Hrows,
                                         nullptr, c->status, 0, c->q_sweep), "band chain");
@@ -852,8 +886,10 @@ int pxa_set_memory(pxa_ctx* c, int policy) {
 }
 
 int pxa_set_adjoint(pxa_ctx* c, int impl) {
-  if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP)) return PXA_ERR_INVALID;
-  c->band_req = impl == PXA_ADJ_BANDED ? 1 : 0;
+  if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP && impl != PXA_ADJ_BANDED_SINGLE))
+    return PXA_ERR_INVALID;
+  c->band_req = impl == PXA_ADJ_RESTEP ? 0 : 1;
+  c->pair_chain = impl == PXA_ADJ_BANDED;
   release_workspace(c);
   invalidate(c);
   return PXA_OK;
@@ -1091,8 +1127,15 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
     if (rc) continue;
     double J;
     rc = pxa_gradient(c, mode, &J, grad_dev);  // warm-up (and convergence check)
-    if (rc == PXA_ERR_NOT_CONVERGED) continue;
-    if (rc) break;
+    if (rc) {
+      // a candidate that does not converge or cannot be launched is skipped; a device
+      // fault would be sticky and is reported
+      const cudaError_t ce = cudaGetLastError();
+      if (rc == PXA_ERR_CUDA && ce != cudaSuccess && ce != cudaErrorInvalidValue &&
+          ce != cudaErrorInvalidConfiguration)
+        break;
+      continue;
+    }
     PXA_CUDA(c, cudaEventRecord(e0, c->stream), "record");
     rc = enqueue(c, mode, c->Jdev, grad_dev);
     PXA_CUDA(c, cudaEventRecord(e1, c->stream), "record");

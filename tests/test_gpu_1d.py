@@ -394,17 +394,19 @@ def test_burgers_full_size_magnus_matches_oracle(X, torch, bu_full):
     assert rel(host(out), go) < 1e-9
 
 
-@pytest.mark.parametrize("impl", ["banded", "restep"])
+@pytest.mark.parametrize("impl", ["banded", "banded_single", "restep"])
 @pytest.mark.parametrize("memory", ["full", "checkpoints"])
 @pytest.mark.parametrize("P", [1, 6])
 def test_burgers_adjoint_evaluations_match_oracle(X, torch, bu_small, impl, memory, P):
-    """The banded adjoint (rows of M_s^T formed once per step) and the stage-by-stage
-    reverse sweep are the same linear map: both match the oracle's serial gradient,
-    in serial and Paraexp modes, with full storage and with checkpoint recompute."""
+    """The banded adjoint (rows of M_s^T formed once per step; the chain with two-step
+    products M_s^T M_{s+1}^T or one step per exchange) and the stage-by-stage reverse sweep
+    are the same linear map: all match the oracle's serial gradient, in serial and
+    Paraexp modes, with full storage and with checkpoint recompute."""
     b = bu_small
     ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, phi=X.PHI_STEPPER,
                   memory=X.STORE_FULL if memory == "full" else X.STORE_CHECKPOINTS)
-    ctx.set_adjoint(X.ADJ_BANDED if impl == "banded" else X.ADJ_RESTEP)
+    ctx.set_adjoint({"banded": X.ADJ_BANDED, "banded_single": X.ADJ_BANDED_SINGLE,
+                     "restep": X.ADJ_RESTEP}[impl])
     fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
     ctx.set_control(fd)
     ctx.set_target(gd_)
@@ -413,7 +415,7 @@ def test_burgers_adjoint_evaluations_match_oracle(X, torch, bu_small, impl, memo
         J = ctx.gradient(mode, out)
         assert abs(J - b["J"]) / b["J"] < 1e-10
         assert rel(host(out), b["grad"]) < 1e-10
-    assert ctx.stats()["adjoint_band"] == (1 if impl == "banded" else 0)
+    assert ctx.stats()["adjoint_band"] == (0 if impl == "restep" else 1)
 
 
 @pytest.mark.parametrize("n,C", [(3, 1), (8, 2), (64, 16), (37, 5)])
