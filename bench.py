@@ -250,6 +250,8 @@ def run_ours(args, w, rank, world):
         tuned[name] = {"krylov_m": st["krylov_m"], "krylov_substeps": st["krylov_substeps"],
                        "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]],
                        "groups": [st["group_direct"], st["group_sweep"]],
+                       "partition_r": round(float(st["partition_r"]), 6),
+                       "tau_ratio": round(float(st["tau_ratio"]), 6),
                        "autotune_best_ms": best_ms}
         times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
         variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name, "tuned": tuned[name]}
@@ -282,6 +284,7 @@ def run_ours(args, w, rank, world):
     else:
         ctx.set_cluster(*tv["clusters"])
         ctx.set_groups(*tv["groups"])
+        ctx.set_partition(tv["partition_r"])
 
     if world > 1:
         import torch.distributed as dist

@@ -130,6 +130,10 @@ typedef struct {
   int adjoint_band;         /* 1 when the banded adjoint is in use */
   int group_direct;         /* requested steps per halo exchange (0 = cost model) */
   int group_sweep;
+  int chunks;               /* chunks of the overlapped direct solve (last gradient) */
+  float partition_r;        /* ratio of successive chunk lengths in use (0: equal chunks) */
+  float tau_ratio;          /* k = adjoint-preparation time / direct time per step, as
+                               last measured by the autotuner (0: not measured) */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -168,6 +172,21 @@ int pxa_set_adjoint(pxa_ctx* ctx, int impl);
  * stepped (1, default), or run the phases one after another (0). Results are the same
  * up to the summation order of J. */
 int pxa_set_overlap(pxa_ctx* ctx, int enable);
+/* BURGERS_1D overlapped direct solve: lengths of its chunks (at most 8). r == 0 (default):
+ * equal chunks. 0 < r < 1: chunk lengths in geometric progression, Delta_{n+1} = r Delta_n,
+ * i.e. boundaries T_n = T (1 - r^n) / (1 - r^N) (Eq. nonEquiP), each rounded to whole
+ * subintervals (steps when P == 1) with at least one per chunk, so that the adjoint work
+ * left after the last direct step shrinks. Sec. 3.3 takes r = k/(k+1) with
+ * k = tau_I_adj / tau_I (processors that solve their adjoint parts side by side); for one
+ * in-order stream of adjoint work the same equal-finish argument gives r = k. The
+ * autotuner measures k and times both. Other r: PXA_ERR_INVALID. */
+int pxa_set_partition(pxa_ctx* ctx, double r);
+/* Host-only (no device work): the chunk boundaries, in steps, that the overlapped direct
+ * solve uses for K steps and P subintervals (P == 1: chunks of steps) at ratio r, with at
+ * most max_chunks chunks (1..64). Writes NC + 1 increasing values from 0 to K into
+ * bounds (caller-owned, max_chunks + 1 entries) and returns NC >= 1; PXA_ERR_INVALID
+ * for bad arguments (K < 1, P < 1, K % P != 0, r outside [0, 1), NULL bounds). */
+int pxa_partition_bounds(int64_t K, int P, double r, int max_chunks, int64_t* bounds);
 /* BURGERS_1D: steps per halo exchange of the serial RK4 sweep (q_direct) and of the
  * banded adjoint sweeps (q_sweep): 1, 2 or 4 (a CTA then also steps 4(q-1) of its
  * neighbours' points on each side, and needs at least 4q points of its own); 0 = chosen

@@ -81,16 +81,26 @@ cudaError_t launch_bu1_band_sweep(cudaStream_t st, int C, int clusters, int lane
 cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
                                  int64_t li_top, const double* LI, const double* H, const double* jt,
                                  double* partial, const double* extra, double* grad, int* status);
+// The gradient in parts: step blocks [b_lo, b_hi) into their rows of partial, then the
+// fixed-order sum over all blocks.
+int bu1_band_steps_per_block(int64_t K, int n);
+cudaError_t launch_bu1_band_grad_part(cudaStream_t st, int n, double dt, double omega, int64_t K,
+                                      int64_t li_top, const double* LI, const double* H,
+                                      const double* jt, double* partial, int b_lo, int b_hi,
+                                      int priority);
+cudaError_t launch_bu1_band_grad_reduce(cudaStream_t st, int n, int64_t K, const double* partial,
+                                        const double* extra, double* grad, int* status);
 // Two-step banded chain (kernels_bu1_pair.cu).
 int bu1_chain2_plan(int64_t K, int64_t k, int P, int4* out);
 bool bu1_chain2_valid(int n, int C);
 cudaError_t launch_bu1_band_pair(cudaStream_t st, int n, const double* rec, int64_t m_lo,
                                  int64_t m_hi, double* rp, int priority);
 cudaError_t launch_bu1_band_chain2(cudaStream_t st, int C, int n, const double* rec, const double* rp,
-                                   const int4* plan, int nplan, int s_hi, const double* W,
-                                   double* out_rows, int* status);
+                                   const int4* plan, int nplan, int s_hi, const double* from_rows,
+                                   const double* W, double* out_rows, int* status, int priority,
+                                   size_t reserve_smem);
 cudaError_t launch_bu1_band_fill(cudaStream_t st, int n, const double* rec, const int4* plan, int nplan,
-                                 double* rows);
+                                 double* rows, int priority);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);
 cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);

@@ -441,12 +441,13 @@ __global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int
 // (G_s^T lambda_{s+1}), lambda = H (every row, when given) + LI (rows <= li_top).
 __global__ void __launch_bounds__(PT) bu1_band_grad_kernel(
     int n, double dt, double omega, int64_t K, int64_t li_top, const double* __restrict__ LI,
-    const double* __restrict__ H, const double* __restrict__ jt, int steps_per_block,
+    const double* __restrict__ H, const double* __restrict__ jt, int steps_per_block, int block0,
     double* __restrict__ partial) {
   __shared__ double lam[PT + 6], kb4[PT + 6], kb3[PT + 6], kb2[PT + 6];
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * PT;
-  const int64_t sb = (int64_t)blockIdx.y * steps_per_block;
+  const int by = block0 + (int)blockIdx.y;  // step block
+  const int64_t sb = (int64_t)by * steps_per_block;
   int64_t se = sb + steps_per_block;
   if (se > K) se = K;
   const double dt6 = dt / 6.0, dt3 = dt / 3.0, h2 = 0.5 * dt;
@@ -500,7 +501,7 @@ __global__ void __launch_bounds__(PT) bu1_band_grad_kernel(
     }
     __syncthreads();
   }
-  if (i0 + tid < n) partial[(size_t)blockIdx.y * n + i0 + tid] = acc;
+  if (i0 + tid < n) partial[(size_t)by * n + i0 + tid] = acc;
 }
 
 // grad[i] = sum_b partial[b][i] (+ extra[i]), in a fixed order.
@@ -519,8 +520,9 @@ __global__ void bu1_band_reduce_kernel(int n, int blocks, const double* __restri
 // ---- launch wrappers ---------------------------------------------------------------
 int bu1_band_steps_per_block(int64_t K, int n) {
   const int tiles = (n + PT - 1) / PT;
-  // about 8 blocks per SM of a 152-SM part, at least 4 steps per block
-  int64_t per = (K * tiles + 1215) / 1216;
+  // about 32 blocks per SM of a 152-SM part (a quarter of them, the last segment of the
+  // chain, still fill the GPU), at least 4 steps per block
+  int64_t per = (K * tiles + 4863) / 4864;
   if (per < 4) per = 4;
   if (per > 256) per = 256;
   return (int)per;
@@ -636,12 +638,34 @@ int bu1_band_grad_blocks(int64_t K, int n) {
 cudaError_t launch_bu1_band_grad(cudaStream_t st, int n, double dt, double omega, int64_t K,
                                  int64_t li_top, const double* LI, const double* H, const double* jt,
                                  double* partial, const double* extra, double* grad, int* status) {
-  const int spb = bu1_band_steps_per_block(K, n);
-  const int blocks = (int)((K + spb - 1) / spb);
-  dim3 grid((n + PT - 1) / PT, blocks);
-  bu1_band_grad_kernel<<<grid, PT, 0, st>>>(n, dt, omega, K, li_top, LI, H, jt, spb, partial);
-  cudaError_t e = cudaGetLastError();
+  const int blocks = bu1_band_grad_blocks(K, n);
+  cudaError_t e = launch_bu1_band_grad_part(st, n, dt, omega, K, li_top, LI, H, jt, partial, 0, blocks, 0);
   if (e != cudaSuccess) return e;
+  return launch_bu1_band_grad_reduce(st, n, K, partial, extra, grad, status);
+}
+
+cudaError_t launch_bu1_band_grad_part(cudaStream_t st, int n, double dt, double omega, int64_t K,
+                                      int64_t li_top, const double* LI, const double* H,
+                                      const double* jt, double* partial, int b_lo, int b_hi,
+                                      int priority) {
+  if (b_hi <= b_lo) return cudaSuccess;
+  const int spb = bu1_band_steps_per_block(K, n);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((n + PT - 1) / PT, b_hi - b_lo);
+  cfg.blockDim = dim3(PT);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bu1_band_grad_kernel, n, dt, omega, K, li_top, LI, H, jt, spb, b_lo,
+                            partial);
+}
+
+cudaError_t launch_bu1_band_grad_reduce(cudaStream_t st, int n, int64_t K, const double* partial,
+                                        const double* extra, double* grad, int* status) {
+  const int blocks = bu1_band_grad_blocks(K, n);
   bu1_band_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, blocks, partial, extra, grad, status);
   return cudaGetLastError();
 }

@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(PT2) bu1_band_pair_kernel(int n, const double*
 template <int DEPTH>
 __global__ void bu1_band_chain2_kernel(int n, const double* __restrict__ rec,
                                        const double* __restrict__ rp, const int4* __restrict__ plan,
-                                       int nplan, int s_hi, const double* __restrict__ W,
-                                       double* __restrict__ out_rows, int* status) {
+                                       int nplan, int s_hi, const double* __restrict__ from_rows,
+                                       const double* __restrict__ W, double* __restrict__ out_rows,
+                                       int* status) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) double smb[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -122,12 +123,13 @@ __global__ void bu1_band_chain2_kernel(int n, const double* __restrict__ rec,
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // lambda_{s_hi}: the source of the last state, own points and halo
+  // lambda_{s_hi}: row s_hi of from_rows (a chain continued from an earlier launch), or
+  // the source of the last state, own points and halo
   for (int q = tid - HP; q < cnt + HP; q += nt) {
     const int gq = wrapn(start + q, n);
-    const double v = rec[((size_t)s_hi * n + gq) * RW + (RW - 1)];
+    const double v = from_rows ? from_rows[(size_t)s_hi * n + gq] : rec[((size_t)s_hi * n + gq) * RW + (RW - 1)];
     lam0[q] = v;
-    if (q >= 0 && q < cnt) out_rows[(size_t)s_hi * n + start + q] = v;
+    if (!from_rows && q >= 0 && q < cnt) out_rows[(size_t)s_hi * n + start + q] = v;
   }
   const bool sender = multi && act && half == 0;
   const bool to_left = sender && p < HP, to_right = sender && p >= cnt - HP;
@@ -322,12 +324,15 @@ cudaError_t launch_bu1_band_pair(cudaStream_t st, int n, const double* rec, int6
 }
 
 cudaError_t launch_bu1_band_chain2(cudaStream_t st, int C, int n, const double* rec, const double* rp,
-                                   const int4* plan, int nplan, int s_hi, const double* W,
-                                   double* out_rows, int* status) {
+                                   const int4* plan, int nplan, int s_hi, const double* from_rows,
+                                   const double* W, double* out_rows, int* status, int priority,
+                                   size_t reserve_smem) {
+  if (nplan <= 0) return cudaSuccess;
   const int nc = (n + C - 1) / C;
   constexpr int DEPTH = 4;
   const int G = (nc + 31) / 32, nt = 64 * G;  // two warps (halves) per group of 32 points
-  const size_t sh = sizeof(double) * (2 * (size_t)(nc + 2 * HP) + (size_t)G * 32 + (size_t)DEPTH * nt * PW);
+  size_t sh = sizeof(double) * (2 * (size_t)(nc + 2 * HP) + (size_t)G * 32 + (size_t)DEPTH * nt * PW);
+  if (reserve_smem > sh) sh = reserve_smem;  // no other CTA shares the SM
   const void* fn = (const void*)bu1_band_chain2_kernel<DEPTH>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
@@ -335,31 +340,40 @@ cudaError_t launch_bu1_band_chain2(cudaStream_t st, int C, int n, const double* 
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  void* args[] = {&n, &rec, &rp, &plan, &nplan, &s_hi, &W, &out_rows, &status};
+  void* args[] = {&n, &rec, &rp, &plan, &nplan, &s_hi, &from_rows, &W, &out_rows, &status};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = sh;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = priority;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t launch_bu1_band_fill(cudaStream_t st, int n, const double* rec, const int4* plan, int nplan,
-                                 double* rows) {
+                                 double* rows, int priority) {
   if (nplan <= 0) return cudaSuccess;
   const int tiles = (n + PT2 - 1) / PT2;
   int per = (int)(((int64_t)nplan * tiles + 1215) / 1216);
   if (per < 4) per = 4;
-  dim3 grid(tiles, (unsigned)((nplan + per - 1) / per));
-  bu1_band_fill_kernel<<<grid, PT2, 0, st>>>(n, rec, plan, nplan, per, rows);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles, (unsigned)((nplan + per - 1) / per));
+  cfg.blockDim = dim3(PT2);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bu1_band_fill_kernel, n, rec, plan, nplan, per, rows);
 }
 
 }  // namespace pxa

@@ -72,6 +72,7 @@ struct pxa_ctx {
   int q_direct = 0, q_sweep = 0;  // steps per halo exchange of the RK4 / banded sweeps (0 = auto)
   cudaStream_t side = nullptr;
   static constexpr int kMaxChunks = 8;
+  double part_r = 0.0;        // ratio of successive chunk lengths (0: equal chunks)
   cudaEvent_t ev_fork[kMaxChunks] = {};
   cudaEvent_t ev_join = nullptr;
   double* Jparts = nullptr;   // [kMaxChunks] objective of each direct chunk
@@ -88,6 +89,12 @@ struct pxa_ctx {
   int4* plan_par = nullptr;
   int4* plan_ser = nullptr;
   int nplan_par = 0, nplan_ser = 0;
+  std::vector<int4> hplan_par, hplan_ser;  // host copies (segment boundaries)
+  // the chain runs in up to kMaxSeg launches; after each one the side stream fills the
+  // skipped rows and sums the gradient over the finished rows
+  static constexpr int kMaxSeg = 8;
+  int chain_segments = 4;
+  cudaEvent_t ev_seg[kMaxSeg] = {};
   double* Jdev = nullptr;     // 1
   double* errmax = nullptr;   // 1
   int* status = nullptr;      // 1
@@ -165,6 +172,13 @@ void release_workspace(pxa_ctx* c) {
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = nullptr;
   c->plan_par = c->plan_ser = nullptr;
   c->nplan_par = c->nplan_ser = 0;
+  c->hplan_par.clear();
+  c->hplan_ser.clear();
+  for (auto& e : c->ev_seg)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   if (c->side) {
     cudaStreamDestroy(c->side);
     c->side = nullptr;
@@ -359,10 +373,12 @@ int prepare(pxa_ctx* c) {
         if ((rc = alloc(c, &c->plan_par, (size_t)c->nplan_par))) return rc;
         PXA_CUDA(c, cudaMemcpy(c->plan_par, plan.data(), sizeof(int4) * c->nplan_par, cudaMemcpyHostToDevice),
                  "copy plan");
+        c->hplan_par.assign(plan.begin(), plan.begin() + c->nplan_par);
         c->nplan_ser = bu1_chain2_plan(c->K, c->K, 1, plan.data());
         if ((rc = alloc(c, &c->plan_ser, (size_t)c->nplan_ser))) return rc;
         PXA_CUDA(c, cudaMemcpy(c->plan_ser, plan.data(), sizeof(int4) * c->nplan_ser, cudaMemcpyHostToDevice),
                  "copy plan");
+        c->hplan_ser.assign(plan.begin(), plan.begin() + c->nplan_ser);
       }
       c->band = true;
       int least = 0, greatest = 0;
@@ -371,6 +387,7 @@ int prepare(pxa_ctx* c) {
       c->prio_hi = greatest;
       PXA_CUDA(c, cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, least), "side stream");
       for (auto& e : c->ev_fork) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+      for (auto& e : c->ev_seg) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
       PXA_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
       int optin = 0;
       PXA_CUDA(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device),
@@ -501,6 +518,30 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   return PXA_OK;
 }
 
+// Boundaries b[0..NC] (in steps) of the chunks of the overlapped direct solve: NC
+// chunks of whole subintervals (P > 1) or of steps (P == 1). r == 0: equal lengths;
+// 0 < r < 1: the geometric partition T_n = T (1 - r^n) / (1 - r^N) of Eq. nonEquiP,
+// rounded to whole units with at least one unit per chunk. Returns NC.
+int bu1_chunk_bounds(int64_t K, int P, double r, int max_chunks, int64_t* b) {
+  const int64_t units = P > 1 ? P : K, unit = P > 1 ? K / P : 1;
+  const int NC = (int)(units < max_chunks ? units : max_chunks);
+  int64_t prev = 0;
+  b[0] = 0;
+  for (int i = 1; i <= NC; ++i) {
+    double x;
+    if (r > 0.0 && r < 1.0)
+      x = (double)units * (1.0 - std::pow(r, i)) / (1.0 - std::pow(r, NC));
+    else
+      x = (double)units * i / NC;
+    int64_t u = i == NC ? units : (int64_t)std::llround(x);
+    if (u < prev + 1) u = prev + 1;
+    if (u > units - (NC - i)) u = units - (NC - i);
+    b[i] = u * unit;
+    prev = u;
+  }
+  return NC;
+}
+
 // ---- 1D Burgers (forcing control, tracking objective), hybrid scheme ----------
 int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
@@ -533,12 +574,13 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     // stream builds the band records of its rows and runs the adjoint lanes whose
     // subintervals it completed, while the next chunk steps on.
     ev_record(c, 0);
-    const int NC = P > 1 ? (P < pxa_ctx::kMaxChunks ? P : pxa_ctx::kMaxChunks) : pxa_ctx::kMaxChunks;
-    const int64_t kc = P > 1 ? ((int64_t)((P + NC - 1) / NC)) * k : (K + NC - 1) / NC;
+    int64_t bounds[pxa_ctx::kMaxChunks + 1];
+    const int NC = bu1_chunk_bounds(K, P, c->part_r, pxa_ctx::kMaxChunks, bounds);
+    c->stats.chunks = NC;
+    c->stats.partition_r = (float)c->part_r;
     int nch = 0;
     for (int ci = 0; ci < NC; ++ci) {
-      const int64_t b0 = ci * kc, b1 = (ci + 1) * kc < K ? (ci + 1) * kc : K;
-      if (b0 >= K) break;
+      const int64_t b0 = bounds[ci], b1 = bounds[ci + 1];
       PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, b1 - b0,
                                        c->control, sc ? sc + 3 * b0 : nullptr,
                                        ci == 0 ? nullptr : c->traj + (size_t)b0 * n,
@@ -556,8 +598,12 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
           PXA_CUDA(c, launch_bu1_band_pair(c->side, n, c->rec, (b0 + 1) / 2, (b1 + 1) / 2, c->rp,
                                            c->prio_lo), "pair records");
         const int l0 = (int)(b0 / k), l1 = (int)(b1 / k) < side_lanes ? (int)(b1 / k) : side_lanes;
+        // the lanes of the last chunk run with no direct solve beside them: a cluster as
+        // wide as the chain's steps them about twice as fast as the narrow ones that share
+        // the GPU with the direct
+        const int cl = ci == NC - 1 && (l1 - l0) * c->cl_band_chain <= 128 ? c->cl_band_chain : c->cl_band_lanes;
         if (l1 > l0)
-          PXA_CUDA(c, launch_bu1_band_sweep(c->side, c->cl_band_lanes, l1 - l0, l0, n, c->rec, k, P, 0,
+          PXA_CUDA(c, launch_bu1_band_sweep(c->side, cl, l1 - l0, l0, n, c->rec, k, P, 0,
                                             nullptr, c->LI, c->E, c->status, c->prio_lo, c->q_sweep),
                                             "band lanes");
       }
@@ -618,12 +664,49 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     const int64_t lane_k = full ? 0 : k;
     if (chain_top && c->rp && bu1_chain2_valid(n, c->cl_band_chain)) {
       // the top subinterval with its source, then the summed homogeneous problems, two
-      // steps per exchange where the plan allows; then the rows skipped inside pair steps
+      // steps per exchange where the plan allows; then the rows skipped inside pair steps.
+      // With the overlap on, the chain runs in segments: after each one the side stream
+      // fills its skipped rows and sums the gradient over the step blocks whose rows are
+      // final, while the next segment runs (its CTAs own their SMs).
       const int4* plan = P == 1 ? c->plan_ser : c->plan_par;
       const int np = P == 1 ? c->nplan_ser : c->nplan_par;
-      PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan, np, (int)K, c->E,
-                                         c->Hrows, c->status), "band chain");
-      PXA_CUDA(c, launch_bu1_band_fill(st, n, c->rec, plan, np, c->Hrows), "band fill");
+      const std::vector<int4>& hp = P == 1 ? c->hplan_ser : c->hplan_par;
+      int S = (c->overlap && c->side) ? c->chain_segments : 1;
+      if (S > pxa_ctx::kMaxSeg) S = pxa_ctx::kMaxSeg;
+      if (np < 64 * S) S = 1;
+      if (S == 1) {
+        PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan, np, (int)K, nullptr,
+                                           c->E, c->Hrows, c->status, 0, 0), "band chain");
+        PXA_CUDA(c, launch_bu1_band_fill(st, n, c->rec, plan, np, c->Hrows, 0), "band fill");
+      } else {
+        const int spb = bu1_band_steps_per_block(K, n);
+        const int64_t li_top = (int64_t)(P - 1) * k;
+        int b_hi = bu1_band_grad_blocks(K, n);  // blocks [b_hi, end) are summed already
+        for (int i = 0; i < S; ++i) {
+          const int j0 = (int)((int64_t)np * i / S), j1 = (int)((int64_t)np * (i + 1) / S);
+          const int s_hi = i == 0 ? (int)K : hp[j0 - 1].x;
+          PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan + j0, j1 - j0, s_hi,
+                                             i == 0 ? nullptr : c->Hrows, c->E, c->Hrows, c->status,
+                                             c->prio_hi, c->reserve_smem), "band chain");
+          PXA_CUDA(c, cudaEventRecord(c->ev_seg[i], st), "segment");
+          PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_seg[i], 0), "segment wait");
+          PXA_CUDA(c, launch_bu1_band_fill(c->side, n, c->rec, plan + j0, j1 - j0, c->Hrows, c->prio_lo),
+                   "band fill");
+          // rows >= low are final; block b reads rows b spb + 1 .. (b + 1) spb
+          const int64_t low = hp[j1 - 1].x;
+          const int b_lo = i == S - 1 ? 0 : (int)((low - 1 + spb - 1) / spb);
+          PXA_CUDA(c, launch_bu1_band_grad_part(c->side, n, dt, c->omega, K, li_top,
+                                                side_lanes > 0 ? c->LI : nullptr, c->Hrows, c->jt, c->gpart,
+                                                b_lo, b_hi, c->prio_lo), "band gradient");
+          b_hi = b_lo < b_hi ? b_lo : b_hi;
+        }
+        ev_record(c, 4);
+        PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
+        PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
+        PXA_CUDA(c, launch_bu1_band_grad_reduce(st, n, K, c->gpart, nullptr, grad, c->status), "gradient sum");
+        ev_record(c, 5);
+        return PXA_OK;
+      }
     } else if (chain_top) {
       // the top subinterval with its source, then the summed homogeneous problems
       PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, 0, n, c->rec, k, P, 1, c->E, c->Hrows,
@@ -910,6 +993,22 @@ int pxa_set_groups(pxa_ctx* c, int q_direct, int q_sweep) {
 int pxa_set_overlap(pxa_ctx* c, int enable) {
   if (!c) return PXA_ERR_INVALID;
   c->overlap = enable != 0;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_partition_bounds(int64_t K, int P, double r, int max_chunks, int64_t* bounds) {
+  if (K < 1 || P < 1 || K % P != 0 || !(r >= 0.0 && r < 1.0) || max_chunks < 1 || max_chunks > 64 ||
+      !bounds)
+    return PXA_ERR_INVALID;
+  return bu1_chunk_bounds(K, P, r, max_chunks, bounds);
+}
+
+int pxa_set_partition(pxa_ctx* c, double r) {
+  if (!c) return PXA_ERR_INVALID;
+  if (!(r >= 0.0 && r < 1.0)) return fail(c, PXA_ERR_INVALID, "partition ratio must be 0 (equal) or in (0, 1)");
+  c->part_r = r;
+  c->stats.partition_r = (float)r;
   invalidate(c);
   return PXA_OK;
 }
@@ -1210,6 +1309,65 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
     c->q_direct = bqd;
     c->q_sweep = bqs;
     invalidate(c);
+    if (c->overlap && c->memory == PXA_STORE_FULL && c->side) {
+      // third pass: the chunk partition of the overlapped direct solve (Sec. 3.3).
+      // k = tau_I_adj / tau_I comes from one run with the phases in sequence (direct;
+      // band records and adjoint lanes); then equal chunks, r = k/(k+1) and r = k are
+      // timed and the fastest is kept.
+      if (!c->ev_ready) {
+        for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
+        c->ev_ready = true;
+      }
+      const bool graph3 = c->use_graph, timing3 = c->timing;
+      c->use_graph = false;
+      c->overlap = false;
+      c->timing = true;
+      double kr = 0.0;
+      int mrc = enqueue(c, mode, c->Jdev, grad_dev);
+      if (mrc == PXA_OK) mrc = enqueue(c, mode, c->Jdev, grad_dev);
+      if (mrc == PXA_OK) {
+        PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+        float md = 0.f, ma = 0.f;
+        cudaEventElapsedTime(&md, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&ma, c->ev[2], c->ev[3]);
+        if (md > 0.f && read_status(c) == PXA_OK) kr = (double)ma / (double)md;
+      }
+      c->overlap = true;
+      c->timing = false;
+      c->stats.tau_ratio = (float)kr;
+      std::vector<double> rs = {0.0};
+      if (kr > 0.0) {
+        rs.push_back(kr / (kr + 1.0));
+        if (kr < 0.95) rs.push_back(kr);
+      }
+      cudaEvent_t g0, g1;
+      PXA_CUDA(c, cudaEventCreate(&g0), "event");
+      PXA_CUDA(c, cudaEventCreate(&g1), "event");
+      double bms = 1e300, br = c->part_r;
+      for (double r : rs) {
+        c->part_r = r;
+        if (enqueue(c, mode, c->Jdev, grad_dev) != PXA_OK) continue;  // warm-up
+        PXA_CUDA(c, cudaEventRecord(g0, c->stream), "record");
+        int erc = enqueue(c, mode, c->Jdev, grad_dev);
+        PXA_CUDA(c, cudaEventRecord(g1, c->stream), "record");
+        PXA_CUDA(c, cudaEventSynchronize(g1), "sync");
+        if (erc || read_status(c) != PXA_OK) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g0, g1);
+        if (ms < bms) {
+          bms = ms;
+          br = r;
+        }
+      }
+      cudaEventDestroy(g0);
+      cudaEventDestroy(g1);
+      c->part_r = br;
+      c->stats.partition_r = (float)br;
+      if (bms < 1e299) best = bms;
+      c->use_graph = graph3;
+      c->timing = timing3;
+      invalidate(c);
+    }
   }
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;

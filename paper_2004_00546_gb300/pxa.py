@@ -30,7 +30,7 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_groups",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_partition_bounds", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
@@ -60,7 +60,9 @@ class Stats(ctypes.Structure):
                 ("band_taps", ctypes.c_int), ("cluster_direct", ctypes.c_int),
                 ("cluster_lanes", ctypes.c_int), ("cluster_chain", ctypes.c_int),
                 ("ms_adjoint_prep", ctypes.c_float), ("adjoint_band", ctypes.c_int),
-                ("group_direct", ctypes.c_int), ("group_sweep", ctypes.c_int)]
+                ("group_direct", ctypes.c_int), ("group_sweep", ctypes.c_int),
+                ("chunks", ctypes.c_int), ("partition_r", ctypes.c_float),
+                ("tau_ratio", ctypes.c_float)]
 
 
 _lib = None
@@ -88,6 +90,8 @@ def load(path: str = LIB_PATH):
         "pxa_set_memory": [p, i],
         "pxa_set_adjoint": [p, i],
         "pxa_set_overlap": [p, i],
+        "pxa_set_partition": [p, d],
+        "pxa_partition_bounds": [i64, i, d, i, ctypes.POINTER(i64)],
         "pxa_set_groups": [p, i, i],
         "pxa_set_graph": [p, i],
         "pxa_set_cluster": [p, i, i, i],
@@ -207,6 +211,9 @@ class Context:
     def set_overlap(self, enable):
         self._check(self._L.pxa_set_overlap(self._h, 1 if enable else 0))
 
+    def set_partition(self, r):
+        self._check(self._L.pxa_set_partition(self._h, float(r)))
+
     def set_groups(self, q_direct=0, q_sweep=0):
         self._check(self._L.pxa_set_groups(self._h, q_direct, q_sweep))
 
@@ -302,3 +309,14 @@ def expv_static(x, y, n, c, nu, T, K, m, tol, phi, span_steps, substeps=1, trans
     if rc != OK:
         raise PxaError(rc, "pxa_expv_static")
     return err.value
+
+
+def partition_bounds(K, P, r, max_chunks=8):
+    """pxa_partition_bounds: chunk boundaries (in steps) of the overlapped direct solve
+    (host only, no device work)."""
+    lib = load()
+    out = (ctypes.c_int64 * (max_chunks + 1))()
+    rc = lib.pxa_partition_bounds(int(K), int(P), float(r), int(max_chunks), out)
+    if rc < 0:
+        raise PxaError(rc, "pxa_partition_bounds")
+    return [out[i] for i in range(rc + 1)]

@@ -42,3 +42,38 @@ def test_invalid_arguments_are_rejected_without_a_device(pxa_lib):
     h = ctypes.c_void_p()
     assert L.pxa_create(ctypes.byref(h), 4096, None) == pxa.ERR_CUDA
     assert L.pxa_create(None, 0, None) == pxa.ERR_INVALID
+
+
+def test_partition_bounds_follow_the_nonequidistant_partition(pxa_lib):
+    """Host logic of the overlapped direct solve: chunk boundaries are the partition of
+    Eq. nonEquiP (pinned in the oracle), rounded to whole steps or subintervals."""
+    from oracle import partition_nonequi
+    import numpy as np
+
+    # P == 1: chunks of steps; K large enough that rounding moves no boundary by > 1/2
+    K = 1_000_000
+    for r in (0.3, 0.59, 0.7, 0.9):
+        b = pxa.partition_bounds(K, 1, r, 8)
+        kk = r / (1.0 - r)  # k with k/(k+1) = r (the oracle takes k)
+        ref = partition_nonequi(1.0, 8, kk) * K
+        assert len(b) == 9 and b[0] == 0 and b[-1] == K
+        assert np.all(np.abs(np.array(b) - ref) <= 0.5 + 1e-6), (r, b, ref)
+    # r == 0: equal chunks
+    assert pxa.partition_bounds(20000, 32, 0.0, 8) == [2500 * i for i in range(9)]
+    assert pxa.partition_bounds(20000, 1, 0.0, 8) == [2500 * i for i in range(9)]
+    # P > 1: whole subintervals, at least one per chunk, strictly increasing
+    for P, r in ((32, 0.37), (32, 0.59), (8, 0.2), (4, 0.5), (3, 0.9)):
+        K = 625 * P
+        b = pxa.partition_bounds(K, P, r, 8)
+        nc = min(P, 8)
+        assert len(b) == nc + 1 and b[0] == 0 and b[-1] == K
+        d = np.diff(b)
+        assert np.all(d >= 625) and np.all(d % 625 == 0)
+        if P >= 8 and r < 0.6:
+            assert d[0] >= d[-1]  # the chunks shrink towards T
+    # argument errors
+    out = (ctypes.c_int64 * 9)()
+    assert pxa_lib.pxa_partition_bounds(0, 1, 0.0, 8, out) == pxa.ERR_INVALID
+    assert pxa_lib.pxa_partition_bounds(10, 3, 0.0, 8, out) == pxa.ERR_INVALID
+    assert pxa_lib.pxa_partition_bounds(10, 1, 1.0, 8, out) == pxa.ERR_INVALID
+    assert pxa_lib.pxa_partition_bounds(10, 1, 0.5, 8, None) == pxa.ERR_INVALID

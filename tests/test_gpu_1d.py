@@ -485,3 +485,53 @@ def test_burgers_exchange_groups(X, torch, bu_small, qd, qs, C):
         J = ctx.gradient(mode, out)
         assert abs(J - J0) / J0 < 1e-10
         assert rel(host(out), g0) < 1e-10
+
+
+@pytest.mark.parametrize("P", [1, 6])
+def test_burgers_partition_keeps_the_gradient(X, torch, bu_small, P):
+    """Geometric chunk partitions of the overlapped direct solve (Eq. nonEquiP, rounded
+    to whole subintervals) change only when the adjoint work is done: the gradient is
+    bit for bit that of equal chunks, J differs by the summation order of its partials,
+    and both match the oracle."""
+    b = bu_small
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    mode = X.SERIAL if P == 1 else X.PARAEXP
+    res = []
+    for r in (0.0, 0.37, 0.59, 0.9):
+        ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, phi=X.PHI_STEPPER)
+        ctx.set_partition(r)
+        ctx.set_control(fd)
+        ctx.set_target(gd_)
+        out = torch.empty_like(fd)
+        J = ctx.gradient(mode, out)
+        st = ctx.stats()
+        assert st["chunks"] == (8 if P == 1 else 6)
+        assert abs(st["partition_r"] - r) < 1e-6
+        assert abs(J - b["J"]) / b["J"] < 1e-10
+        assert rel(host(out), b["grad"]) < 1e-10
+        res.append((J, host(out)))
+        ctx.close()
+    for J, g in res[1:]:
+        assert abs(J - res[0][0]) <= 1e-14 * abs(res[0][0])
+        assert np.array_equal(g, res[0][1])
+
+
+def test_burgers_autotune_measures_the_partition_ratio(X, torch, bu_small):
+    """The autotuner's third pass measures k = tau_adj / tau_direct and keeps one of
+    r = 0, k/(k+1), k; the tuned context still gives the oracle's gradient."""
+    b = bu_small
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    out = torch.empty_like(fd)
+    ctx.autotune(X.PARAEXP, out)
+    st = ctx.stats()
+    k = st["tau_ratio"]
+    assert k > 0.0
+    cands = [0.0, k / (k + 1.0)] + ([k] if k < 0.95 else [])
+    assert min(abs(st["partition_r"] - c) for c in cands) < 1e-5
+    J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out), b["grad"]) < 1e-10
+    ctx.close()
