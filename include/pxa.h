@@ -91,12 +91,18 @@ typedef enum { PXA_STORE_FULL = 0, PXA_STORE_CHECKPOINTS = 1 } pxa_memory;
  * once as a 9-diagonal band by a parallel pass over the stored (or recomputed) states,
  * and the adjoint lanes and the homogeneous chain become 9-tap recursions; used when
  * its records (about 21 doubles per step and grid point) fit in half of the free
- * device memory; the serial chain then takes two steps per halo exchange with the
- * product bands M_s^T M_{s+1}^T where no lane value is added in between. BANDED_SINGLE:
- * the same with one step per exchange. RESTEP: every reverse step re-evaluates the four
- * stages and applies their transposed Jacobians in turn (no per-step storage beyond the
- * states). */
-typedef enum { PXA_ADJ_BANDED = 0, PXA_ADJ_RESTEP = 1, PXA_ADJ_BANDED_SINGLE = 2 } pxa_adjoint;
+ * device memory; the serial chain then takes four (or two) steps per halo exchange
+ * with the product bands M_s^T ... M_{s+3}^T (33 diagonals) or M_s^T M_{s+1}^T (17) where
+ * no lane value is added on the rows skipped. BANDED_PAIR: the same with at most two steps
+ * per exchange; BANDED_SINGLE: one step per exchange. RESTEP: every reverse step
+ * re-evaluates the four stages and applies their transposed Jacobians in turn (no
+ * per-step storage beyond the states). */
+typedef enum {
+  PXA_ADJ_BANDED = 0,
+  PXA_ADJ_RESTEP = 1,
+  PXA_ADJ_BANDED_SINGLE = 2,
+  PXA_ADJ_BANDED_PAIR = 3
+} pxa_adjoint;
 
 typedef struct {
   int kind;   /* pxa_problem */
@@ -117,7 +123,8 @@ typedef struct {
   int magnus_steps;         /* RK4 steps per Magnus step (Burgers) */
   int lanes;                /* lanes of the last solve */
   int64_t workspace_bytes;  /* device workspace owned by the context */
-  float ms_direct_inhom;    /* phase times of the last pxa_gradient with timing on */
+  float ms_direct_inhom;    /* phase times of the last pxa_gradient with timing on (-1:
+                               the events could not be read) */
   float ms_direct_hom;
   float ms_adjoint_inhom;
   float ms_adjoint_hom;
@@ -219,7 +226,8 @@ int pxa_gradient_async(pxa_ctx* ctx, int mode, double* J_dev, double* grad_dev);
  * synchronise the stream. */
 int pxa_solve_direct(pxa_ctx* ctx, int mode, double* J_host);
 int pxa_solve_adjoint(pxa_ctx* ctx, int mode, double* grad_dev);
-/* Wait for the stream and report device-side errors. */
+/* Wait for the stream and report device-side errors (with timing on, also reads the
+ * phase times of the last gradient into the statistics). */
 int pxa_sync(pxa_ctx* ctx);
 /* End-to-end call with host buffers: copies control_host (n doubles) to the device,
  * runs pxa_gradient and copies the gradient back into grad_host (n doubles). */
@@ -227,7 +235,8 @@ int pxa_gradient_host(pxa_ctx* ctx, int mode, const double* control_host, double
                       double* grad_host);
 /* Statistics of the last solve. */
 int pxa_get_stats(const pxa_ctx* ctx, pxa_stats* out);
-/* Per-phase CUDA-event timing inside pxa_gradient (0 = off, default). */
+/* Per-phase CUDA-event timing inside pxa_gradient (0 = off, default); with graphs on,
+ * the events are part of the captured graph. */
 int pxa_set_timing(pxa_ctx* ctx, int enable);
 /* Autotuner: times one gradient of `mode` for each candidate configuration on the
  * configured problem (control and target must be set) and keeps the fastest whose

@@ -67,6 +67,7 @@ cudaError_t launch_sum_parts(cudaStream_t st, int count, const double* parts, do
 // the 9 taps of row i of M_s^T and the objective's source dJ/du_s[i].
 constexpr int BU1_BAND_RECORD = 10;
 constexpr int BU1_PAIR_RECORD = 18;  // 17 taps of a row of M_s^T M_{s+1}^T + combined source
+constexpr int BU1_QUAD_RECORD = 34;  // 33 taps of a row of M_s^T ... M_{s+3}^T + combined source
 constexpr int BU1_BAND_MAX_CHUNK = 1024;  // points per CTA of the banded sweep
 bool bu1_band_valid_cluster(int n, int C);
 int bu1_band_grad_blocks(int64_t K, int n);
@@ -101,6 +102,17 @@ cudaError_t launch_bu1_band_chain2(cudaStream_t st, int C, int n, const double* 
                                    size_t reserve_smem);
 cudaError_t launch_bu1_band_fill(cudaStream_t st, int n, const double* rec, const int4* plan, int nplan,
                                  double* rows, int priority);
+// Four-step banded chain (kernels_bu1_quad.cu).
+int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out);
+bool bu1_chain4_valid(int n, int C);
+cudaError_t launch_bu1_band_quad(cudaStream_t st, int n, const double* rp, int64_t q_lo, int64_t q_hi,
+                                 double* rq, int priority);
+cudaError_t launch_bu1_band_chain4(cudaStream_t st, int C, int n, const double* rec, const double* rp,
+                                   const double* rq, const int4* plan, int nplan, int s_hi,
+                                   const double* from_rows, const double* W, double* out_rows,
+                                   int* status, int priority, size_t reserve_smem);
+cudaError_t launch_bu1_band_fill4(cudaStream_t st, int n, const double* rec, const double* rp,
+                                  const int4* plan, int nplan, double* rows, int priority);
 cudaError_t launch_sum_lanes(cudaStream_t st, int n, int lanes, const double* G, const double* extra,
                              double* grad, int* status);
 cudaError_t launch_bu1_rhs(cudaStream_t st, Bu1Grid g, const double* u, double* y);

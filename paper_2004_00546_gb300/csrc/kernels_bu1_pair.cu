@@ -254,8 +254,9 @@ __global__ void bu1_band_chain2_kernel(int n, const double* __restrict__ rec,
 }
 
 // ---- rows skipped by pair steps ---------------------------------------------------------
-// Grid (tiles, plan blocks): for every pair entry {s, 2, src, w}, row s+1 =
-// M_{s+1}^T row s+2 (+ r_{s+1} when the source is on).
+// Grid (tiles, plan blocks): for every two- or four-step entry {s, 2|4, src, w}, row
+// s+1 = M_{s+1}^T row s+2 (+ r_{s+1} when the source is on); in a four-step entry row
+// s+2 comes from bu1_band_fill4_kernel, run before.
 __global__ void __launch_bounds__(PT2) bu1_band_fill_kernel(int n, const double* __restrict__ rec,
                                                             const int4* __restrict__ plan, int nplan,
                                                             int entries_per_block,
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(PT2) bu1_band_fill_kernel(int n, const double*
   const int je = min(nplan, jb + entries_per_block);
   for (int j = jb; j < je; ++j) {
     const int4 e = plan[j];
-    if (e.y != 2) continue;
+    if (e.y < 2) continue;
     const int s1 = e.x + 1;
     const double* r = rec + ((size_t)s1 * n + pt) * RW;
     const double* up = rows + (size_t)(s1 + 1) * n;
@@ -278,21 +279,8 @@ __global__ void __launch_bounds__(PT2) bu1_band_fill_kernel(int n, const double*
 }
 
 // ---- host side ----------------------------------------------------------------------
-// Step plan of the chain from row P*k down to 0 (see the file comment). Returns the
-// number of entries; out must hold P*k entries.
-int bu1_chain2_plan(int64_t K, int64_t k, int P, int4* out) {
-  auto inj = [&](int64_t r) { return (r > 0 && r % k == 0 && r / k <= P - 2) ? (int)(r / k) : 0; };
-  auto src = [&](int64_t r) { return r > (int64_t)(P - 1) * k ? 1 : 0; };
-  int cnt = 0;
-  int64_t r = K;
-  while (r > 0) {
-    const bool pair = r >= 2 && (r % 2) == 0 && inj(r - 1) == 0 && src(r - 1) == src(r - 2);
-    const int64_t ro = r - (pair ? 2 : 1);
-    out[cnt++] = make_int4((int)ro, pair ? 2 : 1, src(ro), inj(ro));
-    r = ro;
-  }
-  return cnt;
-}
+// Step plan of the two-step chain from row P*k down to 0 (see the file comment).
+int bu1_chain2_plan(int64_t K, int64_t k, int P, int4* out) { return bu1_chain_plan(K, k, P, 2, out); }
 
 bool bu1_chain2_valid(int n, int C) {
   if (C < 1 || C > 16) return false;

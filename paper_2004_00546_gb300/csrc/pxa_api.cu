@@ -71,10 +71,12 @@ struct pxa_ctx {
   bool overlap = true;
   int q_direct = 0, q_sweep = 0;  // steps per halo exchange of the RK4 / banded sweeps (0 = auto)
   cudaStream_t side = nullptr;
+  cudaStream_t side2 = nullptr;  // adjoint lanes of the overlapped chunks
   static constexpr int kMaxChunks = 8;
   double part_r = 0.0;        // ratio of successive chunk lengths (0: equal chunks)
   cudaEvent_t ev_fork[kMaxChunks] = {};
-  cudaEvent_t ev_join = nullptr;
+  cudaEvent_t ev_prep[kMaxChunks] = {};
+  cudaEvent_t ev_join = nullptr, ev_join2 = nullptr;
   double* Jparts = nullptr;   // [kMaxChunks] objective of each direct chunk
   int prio_hi = 0, prio_lo = 0;
   size_t reserve_smem = 0;    // dynamic shared memory that makes a direct CTA own its SM
@@ -84,12 +86,16 @@ struct pxa_ctx {
   double* Hrows = nullptr;    // [(K+1)][n] homogeneous chain rows
   double* gpart = nullptr;    // [blocks][n] gradient partial sums
   // two-step chain: pair records and the step plans of the Paraexp and serial chains
-  bool pair_chain = true;
+  int chain_len = 4;          // longest step of the chain (1, 2 or 4)
   double* rp = nullptr;       // [K/2][n][BU1_PAIR_RECORD]
-  int4* plan_par = nullptr;
-  int4* plan_ser = nullptr;
-  int nplan_par = 0, nplan_ser = 0;
-  std::vector<int4> hplan_par, hplan_ser;  // host copies (segment boundaries)
+  double* rq = nullptr;       // [K/4][n][BU1_QUAD_RECORD]
+  // step plans of the chain: [Paraexp partition, serial][steps up to 2, up to 4]
+  struct ChainPlan {
+    int4* dev = nullptr;
+    int count = 0;
+    std::vector<int4> host;  // host copy (segment boundaries)
+  };
+  ChainPlan plans[2][2];
   // the chain runs in up to kMaxSeg launches; after each one the side stream fills the
   // skipped rows and sums the gradient over the finished rows
   static constexpr int kMaxSeg = 8;
@@ -127,6 +133,7 @@ struct pxa_ctx {
   int g_mode = -1;
   const double* g_grad = nullptr;
   const double* g_J = nullptr;
+  bool g_prep_marked = false;  // the captured gradient records ev[6]
 
   // statistics
   pxa_stats stats{};
@@ -169,11 +176,13 @@ void release_workspace(pxa_ctx* c) {
   c->scL = nullptr;
   c->scL_count = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
-  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = nullptr;
-  c->plan_par = c->plan_ser = nullptr;
-  c->nplan_par = c->nplan_ser = 0;
-  c->hplan_par.clear();
-  c->hplan_ser.clear();
+  c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = c->rq = nullptr;
+  for (auto& row : c->plans)
+    for (auto& pl : row) {
+      pl.dev = nullptr;  // freed with the workspace
+      pl.count = 0;
+      pl.host.clear();
+    }
   for (auto& e : c->ev_seg)
     if (e) {
       cudaEventDestroy(e);
@@ -183,15 +192,21 @@ void release_workspace(pxa_ctx* c) {
     cudaStreamDestroy(c->side);
     c->side = nullptr;
   }
-  for (auto& e : c->ev_fork)
-    if (e) {
-      cudaEventDestroy(e);
-      e = nullptr;
-    }
-  if (c->ev_join) {
-    cudaEventDestroy(c->ev_join);
-    c->ev_join = nullptr;
+  if (c->side2) {
+    cudaStreamDestroy(c->side2);
+    c->side2 = nullptr;
   }
+  for (auto* arr : {c->ev_fork, c->ev_prep})
+    for (int i = 0; i < pxa_ctx::kMaxChunks; ++i)
+      if (arr[i]) {
+        cudaEventDestroy(arr[i]);
+        arr[i] = nullptr;
+      }
+  for (cudaEvent_t* e : {&c->ev_join, &c->ev_join2})
+    if (*e) {
+      cudaEventDestroy(*e);
+      *e = nullptr;
+    }
   c->band = false;
 }
 
@@ -353,9 +368,11 @@ int prepare(pxa_ctx* c) {
     // otherwise the adjoint re-steps the stages (kernels_bu1_cluster.cu).
     if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
     const size_t rows1 = (size_t)(c->K + 1) * n;
-    const size_t pair_doubles = c->pair_chain ? (size_t)(c->K / 2) * n * BU1_PAIR_RECORD : 0;
+    const size_t pair_doubles = c->chain_len >= 2 ? (size_t)(c->K / 2) * n * BU1_PAIR_RECORD : 0;
+    const size_t quad_doubles = c->chain_len >= 4 ? (size_t)(c->K / 4) * n * BU1_QUAD_RECORD : 0;
     const size_t band_doubles = rows1 * BU1_BAND_RECORD + (size_t)c->K * n * BU1_BAND_RECORD +
-                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n + pair_doubles;
+                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n + pair_doubles +
+                                quad_doubles;
     size_t free_b = 0, total_b = 0;
     PXA_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
     if (c->band_req != 0 && band_doubles * sizeof(double) <= free_b / 2) {
@@ -365,20 +382,21 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
       if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
       if ((rc = alloc(c, &c->Jparts, pxa_ctx::kMaxChunks))) return rc;
-      if (c->pair_chain) {
+      if (c->chain_len >= 2) {
         if ((rc = alloc(c, &c->rp, pair_doubles))) return rc;
-        // step plans of the chain for the Paraexp partition and for serial stepping
+        if (c->chain_len >= 4 && (rc = alloc(c, &c->rq, quad_doubles))) return rc;
+        // step plans of the chain for the Paraexp partition and for serial stepping, with
+        // steps of up to two and of up to four rows
         std::vector<int4> plan((size_t)c->K);
-        c->nplan_par = bu1_chain2_plan(c->K, k, P, plan.data());
-        if ((rc = alloc(c, &c->plan_par, (size_t)c->nplan_par))) return rc;
-        PXA_CUDA(c, cudaMemcpy(c->plan_par, plan.data(), sizeof(int4) * c->nplan_par, cudaMemcpyHostToDevice),
-                 "copy plan");
-        c->hplan_par.assign(plan.begin(), plan.begin() + c->nplan_par);
-        c->nplan_ser = bu1_chain2_plan(c->K, c->K, 1, plan.data());
-        if ((rc = alloc(c, &c->plan_ser, (size_t)c->nplan_ser))) return rc;
-        PXA_CUDA(c, cudaMemcpy(c->plan_ser, plan.data(), sizeof(int4) * c->nplan_ser, cudaMemcpyHostToDevice),
-                 "copy plan");
-        c->hplan_ser.assign(plan.begin(), plan.begin() + c->nplan_ser);
+        for (int ser = 0; ser < 2; ++ser)
+          for (int q4 = 0; q4 < (c->rq ? 2 : 1); ++q4) {
+            pxa_ctx::ChainPlan& pl = c->plans[ser][q4];
+            pl.count = bu1_chain_plan(c->K, ser ? c->K : k, ser ? 1 : P, q4 ? 4 : 2, plan.data());
+            if ((rc = alloc(c, &pl.dev, (size_t)pl.count))) return rc;
+            PXA_CUDA(c, cudaMemcpy(pl.dev, plan.data(), sizeof(int4) * pl.count, cudaMemcpyHostToDevice),
+                     "copy plan");
+            pl.host.assign(plan.begin(), plan.begin() + pl.count);
+          }
       }
       c->band = true;
       int least = 0, greatest = 0;
@@ -386,9 +404,12 @@ int prepare(pxa_ctx* c) {
       c->prio_lo = least;
       c->prio_hi = greatest;
       PXA_CUDA(c, cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, least), "side stream");
+      PXA_CUDA(c, cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, least), "side stream");
       for (auto& e : c->ev_fork) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+      for (auto& e : c->ev_prep) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
       for (auto& e : c->ev_seg) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
       PXA_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+      PXA_CUDA(c, cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming), "event");
       int optin = 0;
       PXA_CUDA(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device),
                "smem opt-in");
@@ -449,8 +470,16 @@ int prepare(pxa_ctx* c) {
   return PXA_OK;
 }
 
+// Phase event i on the context's stream; while a graph is being captured it becomes an
+// external event-record node, which records the event like a stream would at replay.
 void ev_record(pxa_ctx* c, int i) {
-  if (c->timing && c->ev_ready) cudaEventRecord(c->ev[i], c->stream);
+  if (!(c->timing && c->ev_ready)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cs);
+  const cudaError_t e = cs == cudaStreamCaptureStatusActive
+                            ? cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal)
+                            : cudaEventRecord(c->ev[i], c->stream);
+  if (e != cudaSuccess) cudaGetLastError();  // phase times then read as unavailable
 }
 
 // ---- 1D advection-diffusion (IC control, terminal objective) ----------------
@@ -594,16 +623,23 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
         PXA_CUDA(c, launch_bu1_band_prepass(c->side, n, c->op.L, c->op.nu, dt, c->T, c->omega,
                                             c->control, c->target, c->traj, 0, P, ci == 0 ? 0 : b0 + 1,
                                             b1 + 1, K, c->rec, c->jt, c->prio_lo), "band prepass");
+        // the adjoint lanes of the chunk (latency-bound, few SMs) on a second side stream,
+        // beside the product records (throughput-bound) of the chain
+        PXA_CUDA(c, cudaEventRecord(c->ev_prep[ci], c->side), "records ready");
+        PXA_CUDA(c, cudaStreamWaitEvent(c->side2, c->ev_prep[ci], 0), "records wait");
         if (c->rp)
           PXA_CUDA(c, launch_bu1_band_pair(c->side, n, c->rec, (b0 + 1) / 2, (b1 + 1) / 2, c->rp,
                                            c->prio_lo), "pair records");
+        if (c->rq)
+          PXA_CUDA(c, launch_bu1_band_quad(c->side, n, c->rp, (b0 + 1) / 4, (b1 + 1) / 4, c->rq, c->prio_lo),
+                   "four-step records");
         const int l0 = (int)(b0 / k), l1 = (int)(b1 / k) < side_lanes ? (int)(b1 / k) : side_lanes;
         // the lanes of the last chunk run with no direct solve beside them: a cluster as
         // wide as the chain's steps them about twice as fast as the narrow ones that share
         // the GPU with the direct
         const int cl = ci == NC - 1 && (l1 - l0) * c->cl_band_chain <= 128 ? c->cl_band_chain : c->cl_band_lanes;
         if (l1 > l0)
-          PXA_CUDA(c, launch_bu1_band_sweep(c->side, cl, l1 - l0, l0, n, c->rec, k, P, 0,
+          PXA_CUDA(c, launch_bu1_band_sweep(c->side2, cl, l1 - l0, l0, n, c->rec, k, P, 0,
                                             nullptr, c->LI, c->E, c->status, c->prio_lo, c->q_sweep),
                                             "band lanes");
       }
@@ -615,8 +651,10 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       ev_record(c, 2);
       PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
       PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
+      PXA_CUDA(c, cudaEventRecord(c->ev_join2, c->side2), "join");
+      PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join2, 0), "join wait");
       if (c->timing && c->ev_ready) {
-        cudaEventRecord(c->ev[6], st);
+        ev_record(c, 6);
         c->prep_marked = true;
       }
       ev_record(c, 3);
@@ -651,8 +689,9 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                         c->target, rows, lane_k, P, 0, K + 1, K, c->rec, c->jt, 0),
              "band prepass");
     if (c->rp) PXA_CUDA(c, launch_bu1_band_pair(st, n, c->rec, 0, K / 2, c->rp, 0), "pair records");
+    if (c->rq) PXA_CUDA(c, launch_bu1_band_quad(st, n, c->rp, 0, K / 4, c->rq, 0), "four-step records");
     if (c->timing && c->ev_ready) {
-      cudaEventRecord(c->ev[6], st);
+      ev_record(c, 6);
       c->prep_marked = true;
     }
     PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_lanes, side_lanes, 0, n, c->rec, k, P, 0, nullptr,
@@ -662,38 +701,47 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (c->band) {
     const double* rows = full ? c->traj : c->scratch;
     const int64_t lane_k = full ? 0 : k;
-    if (chain_top && c->rp && bu1_chain2_valid(n, c->cl_band_chain)) {
-      // the top subinterval with its source, then the summed homogeneous problems, two
-      // steps per exchange where the plan allows; then the rows skipped inside pair steps.
-      // With the overlap on, the chain runs in segments: after each one the side stream
-      // fills its skipped rows and sums the gradient over the step blocks whose rows are
-      // final, while the next segment runs (its CTAs own their SMs).
-      const int4* plan = P == 1 ? c->plan_ser : c->plan_par;
-      const int np = P == 1 ? c->nplan_ser : c->nplan_par;
-      const std::vector<int4>& hp = P == 1 ? c->hplan_ser : c->hplan_par;
+    const bool four = chain_top && c->rq && bu1_chain4_valid(n, c->cl_band_chain);
+    if (four || (chain_top && c->rp && bu1_chain2_valid(n, c->cl_band_chain))) {
+      // the top subinterval with its source, then the summed homogeneous problems, four
+      // or two steps per exchange where the plan allows; then the rows skipped inside
+      // those steps. With the overlap on, the chain runs in segments: after each one the
+      // side stream fills its skipped rows and sums the gradient over the step blocks
+      // whose rows are final, while the next segment runs (its CTAs own their SMs).
+      const pxa_ctx::ChainPlan& pl = c->plans[P == 1 ? 1 : 0][four ? 1 : 0];
+      const int np = pl.count;
+      auto chain = [&](int j0, int j1, int s_hi, const double* from, int prio, size_t reserve) {
+        return four ? launch_bu1_band_chain4(st, c->cl_band_chain, n, c->rec, c->rp, c->rq, pl.dev + j0, j1 - j0,
+                                             s_hi, from, c->E, c->Hrows, c->status, prio, reserve)
+                    : launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, pl.dev + j0, j1 - j0,
+                                             s_hi, from, c->E, c->Hrows, c->status, prio, reserve);
+      };
+      auto fill = [&](cudaStream_t fs, int j0, int j1, int prio) -> cudaError_t {
+        if (four) {
+          cudaError_t e = launch_bu1_band_fill4(fs, n, c->rec, c->rp, pl.dev + j0, j1 - j0, c->Hrows, prio);
+          if (e != cudaSuccess) return e;
+        }
+        return launch_bu1_band_fill(fs, n, c->rec, pl.dev + j0, j1 - j0, c->Hrows, prio);
+      };
       int S = (c->overlap && c->side) ? c->chain_segments : 1;
       if (S > pxa_ctx::kMaxSeg) S = pxa_ctx::kMaxSeg;
       if (np < 64 * S) S = 1;
       if (S == 1) {
-        PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan, np, (int)K, nullptr,
-                                           c->E, c->Hrows, c->status, 0, 0), "band chain");
-        PXA_CUDA(c, launch_bu1_band_fill(st, n, c->rec, plan, np, c->Hrows, 0), "band fill");
+        PXA_CUDA(c, chain(0, np, (int)K, nullptr, 0, 0), "band chain");
+        PXA_CUDA(c, fill(st, 0, np, 0), "band fill");
       } else {
         const int spb = bu1_band_steps_per_block(K, n);
         const int64_t li_top = (int64_t)(P - 1) * k;
         int b_hi = bu1_band_grad_blocks(K, n);  // blocks [b_hi, end) are summed already
         for (int i = 0; i < S; ++i) {
           const int j0 = (int)((int64_t)np * i / S), j1 = (int)((int64_t)np * (i + 1) / S);
-          const int s_hi = i == 0 ? (int)K : hp[j0 - 1].x;
-          PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, c->rec, c->rp, plan + j0, j1 - j0, s_hi,
-                                             i == 0 ? nullptr : c->Hrows, c->E, c->Hrows, c->status,
-                                             c->prio_hi, c->reserve_smem), "band chain");
+          const int s_hi = i == 0 ? (int)K : pl.host[j0 - 1].x;
+          PXA_CUDA(c, chain(j0, j1, s_hi, i == 0 ? nullptr : c->Hrows, c->prio_hi, c->reserve_smem), "band chain");
           PXA_CUDA(c, cudaEventRecord(c->ev_seg[i], st), "segment");
           PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_seg[i], 0), "segment wait");
-          PXA_CUDA(c, launch_bu1_band_fill(c->side, n, c->rec, plan + j0, j1 - j0, c->Hrows, c->prio_lo),
-                   "band fill");
+          PXA_CUDA(c, fill(c->side, j0, j1, c->prio_lo), "band fill");
           // rows >= low are final; block b reads rows b spb + 1 .. (b + 1) spb
-          const int64_t low = hp[j1 - 1].x;
+          const int64_t low = pl.host[j1 - 1].x;
           const int b_lo = i == S - 1 ? 0 : (int)((low - 1 + spb - 1) / spb);
           PXA_CUDA(c, launch_bu1_band_grad_part(c->side, n, dt, c->omega, K, li_top,
                                                 side_lanes > 0 ? c->LI : nullptr, c->Hrows, c->jt, c->gpart,
@@ -969,10 +1017,11 @@ int pxa_set_memory(pxa_ctx* c, int policy) {
 }
 
 int pxa_set_adjoint(pxa_ctx* c, int impl) {
-  if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP && impl != PXA_ADJ_BANDED_SINGLE))
+  if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP && impl != PXA_ADJ_BANDED_SINGLE &&
+             impl != PXA_ADJ_BANDED_PAIR))
     return PXA_ERR_INVALID;
   c->band_req = impl == PXA_ADJ_RESTEP ? 0 : 1;
-  c->pair_chain = impl == PXA_ADJ_BANDED;
+  c->chain_len = impl == PXA_ADJ_BANDED ? 4 : impl == PXA_ADJ_BANDED_PAIR ? 2 : 1;
   release_workspace(c);
   invalidate(c);
   return PXA_OK;
@@ -1055,7 +1104,8 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;
   c->stats.magnus_steps = c->magnus_M;
-  if (c->use_graph && !c->timing) {
+  if (c->use_graph) {
+    // (with timing on, the phase events are captured as event-record nodes of the graph)
     if (!c->gexec || c->g_mode != mode || c->g_grad != grad_dev || c->g_J != Jd) {
       invalidate(c);
       // Capture on a library-owned stream (the caller's may be the legacy default
@@ -1085,17 +1135,22 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
       c->g_mode = mode;
       c->g_grad = grad_dev;
       c->g_J = Jd;
+      c->g_prep_marked = c->prep_marked;
     }
+    c->prep_marked = c->g_prep_marked;
     PXA_CUDA(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
     return PXA_OK;
   }
   return enqueue(c, mode, Jd, grad_dev);
 }
 
+static void collect_timing(pxa_ctx* c);
+
 int pxa_sync(pxa_ctx* c) {
   if (!c) return PXA_ERR_INVALID;
   if (!c->ready) return PXA_OK;
   PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  collect_timing(c);
   return read_status(c);
 }
 
@@ -1108,19 +1163,33 @@ int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
   PXA_CUDA(c, cudaMemcpy(&J, c->Jdev, sizeof(double), cudaMemcpyDeviceToHost), "read J");
   c->stats.J = J;
   if (J_host) *J_host = J;
+  collect_timing(c);
+  return read_status(c);
+}
+
+// Phase times of the last gradient from its CUDA events (timing on; stream synchronised).
+static void collect_timing(pxa_ctx* c) {
   if (c->timing && c->ev_ready) {
     float a = 0, b = 0, d = 0, e = 0, t = 0;
-    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
-    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    bool ok = true;
+    auto el = [&](float* ms, int i, int j) {
+      if (cudaEventElapsedTime(ms, c->ev[i], c->ev[j]) != cudaSuccess) {
+        cudaGetLastError();  // not left for the caller's next call
+        ok = false;
+      }
+    };
+    el(&a, 0, 1);
+    el(&b, 1, 2);
     float pr = 0;
     if (c->prep_marked) {
-      cudaEventElapsedTime(&pr, c->ev[2], c->ev[6]);
-      cudaEventElapsedTime(&d, c->ev[6], c->ev[3]);
+      el(&pr, 2, 6);
+      el(&d, 6, 3);
     } else {
-      cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+      el(&d, 2, 3);
     }
-    cudaEventElapsedTime(&e, c->ev[3], c->ev[4]);
-    cudaEventElapsedTime(&t, c->ev[0], c->ev[5]);
+    el(&e, 3, 4);
+    el(&t, 0, 5);
+    if (!ok) a = b = pr = d = e = t = -1.f;  // phase times unavailable
     c->stats.ms_direct_inhom = a;
     c->stats.ms_direct_hom = b;
     c->stats.ms_adjoint_prep = pr;
@@ -1128,7 +1197,6 @@ int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
     c->stats.ms_adjoint_hom = e;
     c->stats.ms_total = t;
   }
-  return read_status(c);
 }
 
 int pxa_solve_direct(pxa_ctx* c, int mode, double* J_host) {
@@ -1180,13 +1248,37 @@ int pxa_gradient_host(pxa_ctx* c, int mode, const double* control_host, double* 
   return PXA_OK;
 }
 
+// One configuration's time per gradient for the autotuner: a warm-up call (which also
+// captures the graph when graphs are on), then the best of two timed calls through the
+// same entry point the caller uses (graph replay or direct launches). Returns PXA_OK and
+// *ms, or the error of the warm-up / timed calls.
+static int tune_time(pxa_ctx* c, int mode, double* grad_dev, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+  invalidate(c);
+  int rc = pxa_gradient_async(c, mode, c->Jdev, grad_dev);
+  if (rc == PXA_OK) rc = pxa_sync(c);
+  if (rc) return rc;
+  double best = 1e300;
+  for (int rep = 0; rep < 2; ++rep) {
+    PXA_CUDA(c, cudaEventRecord(e0, c->stream), "record");
+    rc = pxa_gradient_async(c, mode, c->Jdev, grad_dev);
+    PXA_CUDA(c, cudaEventRecord(e1, c->stream), "record");
+    PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
+    if (rc == PXA_OK) rc = read_status(c);
+    if (rc) return rc;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (t < best) best = t;
+  }
+  *ms = best;
+  return PXA_OK;
+}
+
 int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   if (!c || !grad_dev) return PXA_ERR_INVALID;
   if (!c->have_op || !c->have_time || !c->control) return fail(c, PXA_ERR_STATE, "configure the problem first");
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
-  const bool graph = c->use_graph, timing = c->timing;
-  c->use_graph = false;
-  c->timing = false;
+  const bool timing = c->timing;
+  c->timing = false;  // candidates are timed through the caller's path (graph replay when on)
   cudaEvent_t e0, e1;
   PXA_CUDA(c, cudaEventCreate(&e0), "event");
   PXA_CUDA(c, cudaEventCreate(&e1), "event");
@@ -1222,10 +1314,9 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
     }
     release_workspace(c);
     invalidate(c);
-    int rc = prepare(c);
-    if (rc) continue;
-    double J;
-    rc = pxa_gradient(c, mode, &J, grad_dev);  // warm-up (and convergence check)
+    if (prepare(c)) continue;
+    double ms = 0.0;
+    const int rc = tune_time(c, mode, grad_dev, e0, e1, &ms);
     if (rc) {
       // a candidate that does not converge or cannot be launched is skipped; a device
       // fault would be sticky and is reported
@@ -1235,23 +1326,15 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
         break;
       continue;
     }
-    PXA_CUDA(c, cudaEventRecord(e0, c->stream), "record");
-    rc = enqueue(c, mode, c->Jdev, grad_dev);
-    PXA_CUDA(c, cudaEventRecord(e1, c->stream), "record");
-    PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
-    if (rc || read_status(c) != PXA_OK) continue;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
       bestc = cd;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  c->use_graph = graph;
   c->timing = timing;
   if (bestc.a < 0) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     c->kry_m = m0;
     c->kry_sub = s0;
     c->cl_req_direct = rd;
@@ -1272,43 +1355,30 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   release_workspace(c);
   invalidate(c);
   int rc = prepare(c);
-  if (rc) return rc;
+  if (rc) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
   if (c->op.kind == PXA_BURGERS_1D && c->band) {
+    c->timing = false;
     // second pass at the chosen cluster sizes: steps per halo exchange of the direct
     // sweep and of the banded sweeps (no reallocation needed)
-    const int qd0 = c->q_direct, qs0 = c->q_sweep;
-    int bqd = qd0, bqs = qs0;
-    cudaEvent_t f0, f1;
-    PXA_CUDA(c, cudaEventCreate(&f0), "event");
-    PXA_CUDA(c, cudaEventCreate(&f1), "event");
-    const bool graph2 = c->use_graph, timing2 = c->timing;
-    c->use_graph = false;
-    c->timing = false;
+    int bqd = c->q_direct, bqs = c->q_sweep;
     for (int qd : {1, 2, 4})
       for (int qs : {1, 2, 4}) {
         c->q_direct = qd;
         c->q_sweep = qs;
-        if (enqueue(c, mode, c->Jdev, grad_dev) != PXA_OK) continue;  // warm-up
-        PXA_CUDA(c, cudaEventRecord(f0, c->stream), "record");
-        int erc = enqueue(c, mode, c->Jdev, grad_dev);
-        PXA_CUDA(c, cudaEventRecord(f1, c->stream), "record");
-        PXA_CUDA(c, cudaEventSynchronize(f1), "sync");
-        if (erc || read_status(c) != PXA_OK) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, f0, f1);
+        double ms = 0.0;
+        if (tune_time(c, mode, grad_dev, e0, e1, &ms) != PXA_OK) continue;
         if (ms < best) {
           best = ms;
           bqd = qd;
           bqs = qs;
         }
       }
-    cudaEventDestroy(f0);
-    cudaEventDestroy(f1);
-    c->use_graph = graph2;
-    c->timing = timing2;
     c->q_direct = bqd;
     c->q_sweep = bqs;
-    invalidate(c);
     if (c->overlap && c->memory == PXA_STORE_FULL && c->side) {
       // third pass: the chunk partition of the overlapped direct solve (Sec. 3.3).
       // k = tau_I_adj / tau_I comes from one run with the phases in sequence (direct;
@@ -1318,10 +1388,11 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
         for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
         c->ev_ready = true;
       }
-      const bool graph3 = c->use_graph, timing3 = c->timing;
+      const bool graph3 = c->use_graph;
       c->use_graph = false;
       c->overlap = false;
       c->timing = true;
+      invalidate(c);
       double kr = 0.0;
       int mrc = enqueue(c, mode, c->Jdev, grad_dev);
       if (mrc == PXA_OK) mrc = enqueue(c, mode, c->Jdev, grad_dev);
@@ -1334,41 +1405,32 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
       }
       c->overlap = true;
       c->timing = false;
+      c->use_graph = graph3;
       c->stats.tau_ratio = (float)kr;
       std::vector<double> rs = {0.0};
       if (kr > 0.0) {
         rs.push_back(kr / (kr + 1.0));
         if (kr < 0.95) rs.push_back(kr);
       }
-      cudaEvent_t g0, g1;
-      PXA_CUDA(c, cudaEventCreate(&g0), "event");
-      PXA_CUDA(c, cudaEventCreate(&g1), "event");
       double bms = 1e300, br = c->part_r;
       for (double r : rs) {
         c->part_r = r;
-        if (enqueue(c, mode, c->Jdev, grad_dev) != PXA_OK) continue;  // warm-up
-        PXA_CUDA(c, cudaEventRecord(g0, c->stream), "record");
-        int erc = enqueue(c, mode, c->Jdev, grad_dev);
-        PXA_CUDA(c, cudaEventRecord(g1, c->stream), "record");
-        PXA_CUDA(c, cudaEventSynchronize(g1), "sync");
-        if (erc || read_status(c) != PXA_OK) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, g0, g1);
+        double ms = 0.0;
+        if (tune_time(c, mode, grad_dev, e0, e1, &ms) != PXA_OK) continue;
         if (ms < bms) {
           bms = ms;
           br = r;
         }
       }
-      cudaEventDestroy(g0);
-      cudaEventDestroy(g1);
       c->part_r = br;
       c->stats.partition_r = (float)br;
       if (bms < 1e299) best = bms;
-      c->use_graph = graph3;
-      c->timing = timing3;
-      invalidate(c);
     }
+    c->timing = timing;
+    invalidate(c);
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;
   c->stats.group_direct = c->q_direct;

@@ -22,7 +22,7 @@ CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
 SERIAL, PARAEXP = 0, 1
 STORE_FULL, STORE_CHECKPOINTS = 0, 1
-ADJ_BANDED, ADJ_RESTEP, ADJ_BANDED_SINGLE = 0, 1, 2
+ADJ_BANDED, ADJ_RESTEP, ADJ_BANDED_SINGLE, ADJ_BANDED_PAIR = 0, 1, 2, 3
 
 _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
                  ERR_NOT_CONVERGED: "NOT_CONVERGED", ERR_TIMEOUT: "TIMEOUT",

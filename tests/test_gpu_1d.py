@@ -394,19 +394,20 @@ def test_burgers_full_size_magnus_matches_oracle(X, torch, bu_full):
     assert rel(host(out), go) < 1e-9
 
 
-@pytest.mark.parametrize("impl", ["banded", "banded_single", "restep"])
+@pytest.mark.parametrize("impl", ["banded", "banded_pair", "banded_single", "restep"])
 @pytest.mark.parametrize("memory", ["full", "checkpoints"])
 @pytest.mark.parametrize("P", [1, 6])
 def test_burgers_adjoint_evaluations_match_oracle(X, torch, bu_small, impl, memory, P):
-    """The banded adjoint (rows of M_s^T formed once per step; the chain with two-step
-    products M_s^T M_{s+1}^T or one step per exchange) and the stage-by-stage reverse sweep
-    are the same linear map: all match the oracle's serial gradient, in serial and
-    Paraexp modes, with full storage and with checkpoint recompute."""
+    """The banded adjoint (rows of M_s^T formed once per step; the chain with four-step
+    products M_s^T ... M_{s+3}^T, two-step products or one step per exchange) and the
+    stage-by-stage reverse sweep are the same linear map: all match the oracle's serial
+    gradient, in serial and Paraexp modes, with full storage and with checkpoint
+    recompute."""
     b = bu_small
     ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], P, phi=X.PHI_STEPPER,
                   memory=X.STORE_FULL if memory == "full" else X.STORE_CHECKPOINTS)
-    ctx.set_adjoint({"banded": X.ADJ_BANDED, "banded_single": X.ADJ_BANDED_SINGLE,
-                     "restep": X.ADJ_RESTEP}[impl])
+    ctx.set_adjoint({"banded": X.ADJ_BANDED, "banded_pair": X.ADJ_BANDED_PAIR,
+                     "banded_single": X.ADJ_BANDED_SINGLE, "restep": X.ADJ_RESTEP}[impl])
     fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
     ctx.set_control(fd)
     ctx.set_target(gd_)
@@ -535,3 +536,35 @@ def test_burgers_autotune_measures_the_partition_ratio(X, torch, bu_small):
     assert abs(J - b["J"]) / b["J"] < 1e-10
     assert rel(host(out), b["grad"]) < 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("n,C,K,P", [(200, 4, 630, 6), (200, 8, 600, 6), (100, 1, 632, 8),
+                                      (48, 3, 210, 3), (512, 16, 400, 5)])
+def test_burgers_four_step_chain(X, torch, n, C, K, P):
+    """The chain with four-step product bands (33 taps split over four warps, 16-point
+    halos) on clusters from one CTA (halo wrapping the grid) to 16, with subinterval
+    lengths that are not multiples of 4 (so the plan mixes four-, two- and one-step
+    entries around the lane values), gives the oracle's gradient like the two-step
+    chain."""
+    nu, T = 0.02, 0.25
+    f = 2.0 * I.fourier1d(n, 8, 81)
+    g = I.fourier1d(n, 8, 82)
+    J0, g0 = O.bu1_gradient_serial(f, g, nu, T, K, omega=1.5)
+    fd, gd_ = dev(torch, f), dev(torch, g)
+    res = {}
+    for impl in (X.ADJ_BANDED, X.ADJ_BANDED_PAIR):
+        ctx = bu1_ctx(X, n, nu, T, K, P, phi=X.PHI_STEPPER)
+        ctx.set_adjoint(impl)
+        ctx.set_cluster(0, 0, C)
+        ctx.set_control(fd, 1.5)
+        ctx.set_target(gd_)
+        out = torch.empty_like(fd)
+        for mode in (X.SERIAL, X.PARAEXP):
+            J = ctx.gradient(mode, out)
+            assert abs(J - J0) / J0 < 1e-10
+            assert rel(host(out), g0) < 1e-10, (impl, mode)
+            res[(impl, mode)] = host(out)
+        assert ctx.stats()["cluster_chain"] == C
+        ctx.close()
+    for mode in (X.SERIAL, X.PARAEXP):
+        assert rel(res[(X.ADJ_BANDED, mode)], res[(X.ADJ_BANDED_PAIR, mode)]) < 1e-12
