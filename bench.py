@@ -42,7 +42,12 @@ WORKLOADS = {
                       label="2D advection-diffusion 512x512 nu=1e-3 T=1 RK4 1024 steps FP32 stepping P=64"),
     "advdiff2d_lanes": dict(kind="lanes2d", n=2048, lanes=64, steps=10,
                             label="2D RK4 FP32 lanes kernel, 64 lanes x 2048^2 (1 GiB per state array)"),
+    "batched1d": dict(kind="batched1d", count=256, c=1.0, T=1.0, K=4096, P=16,
+                      label="256 independent 1D advection-diffusion problems, n ~ U{128..2048}, "
+                            "nu ~ logU[1e-3, 1e-1], T=1 CN 4096 steps, P=16, FP32 stepping, FP64 Krylov"),
 }
+# FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # Algorithmic FP64 operations per grid point per step of each kernel.
 FLOPS_RK4_DIRECT = 48.0       # four stages of N(u) + s f (8 each), stage states and weights 13, J 3
@@ -433,10 +438,44 @@ def run_once(args, w):
             "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]]}
 
 
+def run_reference_batch(args, w, world):
+    """The reference arm of the batched workload: the serial FP64 oracle of a bounded
+    sample of the problems per step, scaled to the whole batch."""
+    import oracle as O
+    from paper_2004_00546_gb300 import inputs as I
+
+    prob = I.batch1d_problem(count=w["count"], seed=2007)
+    off, cnt, ns = prob["offsets"], w["count"], 4
+
+    def step():
+        for i in range(ns):
+            O.ad1_cn_gradient_serial(prob["q0"][off[i]:off[i + 1]], w["c"], prob["nu"][i], w["T"], w["K"])
+
+    for _ in range(args.warmup):
+        step()
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        t.append(time.perf_counter() - t0)
+    per_full = float(np.mean(t)) * cnt / ns
+    value = cnt / per_full
+    unit = "gradient evals/s (problems x gradients)"
+    sample = f"first {ns} of {cnt} problems per step (serial FP64 CN), scaled by {cnt}/{ns}"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["label"]},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, w, rank, world):
     """The reference arm: the serial FP64 CPU oracle, timed on this host's cores."""
     if rank != 0:
         return None
+    if w["kind"] == "batched1d":
+        return run_reference_batch(args, w, world)
     inp = make_inputs(w)
     # bounded sample per step: the first K_s steps of the window (direct + adjoint);
     # the cost is linear in the number of steps, so throughput scales by K_s / K
@@ -562,6 +601,127 @@ def run_2d(args, w, rank, world):
             "gpu_launches": None}
 
 
+def run_batch(args, w, rank, world):
+    """Many independent problems of uneven size (every phase one launch over the whole
+    batch): Paraexp and serial stepping through pxa_batch_*, graph replay, L2 flushed."""
+    import torch
+
+    import oracle as O
+    from paper_2004_00546_gb300 import build, inputs as I, pxa as X
+
+    build.build()
+    X.load()
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    prob = I.batch1d_problem(count=w["count"], seed=2007)
+    cnt, K, P = w["count"], w["K"], w["P"]
+    q0 = torch.as_tensor(prob["q0"], device="cuda")
+    J = torch.empty(cnt, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    off = prob["offsets"]
+    # sample problems for the accuracy check: the four largest grids and four stiff ones
+    order = np.argsort(-prob["n"])
+    stiff = np.argsort(-(prob["nu"] * prob["n"] ** 2))
+    sample = list(dict.fromkeys(list(order[:4]) + list(stiff[:4])))
+
+    def timed(b, mode, steps, warmup):
+        for _ in range(warmup):
+            b.gradient(mode, q0, J, g)
+        t = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.gradient_async(mode, q0, J, g)
+            e1.record()
+            torch.cuda.synchronize()
+            b.sync()
+            t.append(e0.elapsed_time(e1))
+        return t
+
+    variants, errs, bats = {}, {}, {}
+    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+        b = X.Batch()
+        b.set(prob["n"], prob["nu"], c=w["c"], T=w["T"], K=K, P=P)
+        best = b.autotune(mode, q0, J, g) if mode == X.PARAEXP else None
+        with ClockSampler(dev_index) as clk:
+            t = timed(b, mode, args.steps, args.warmup)
+        st = b.stats()
+        Jh, gh = J.cpu().numpy(), g.cpu().numpy()
+        e = []
+        for i in sample:
+            q = prob["q0"][off[i]:off[i + 1]]
+            if mode == X.SERIAL:
+                Jo, go, _ = O.ad1_cn_gradient_serial(q, w["c"], prob["nu"][i], w["T"], K)
+            else:
+                Jo, go, _ = O.ad1_cn_gradient_paraexp(q, w["c"], prob["nu"][i], w["T"], K, P, O.PHI_EXP)
+            e.append(max(abs(Jh[i] - Jo) / Jo, float(np.linalg.norm(gh[off[i]:off[i + 1]] - go)
+                                                      / np.linalg.norm(go))))
+        variants[name] = {"ms_per_step": float(np.mean(t)), "min_ms": float(np.min(t)),
+                          "rel_err_max_sampled": float(max(e)), "autotune_best_ms": best,
+                          "krylov_m": st["krylov_m"], "krylov_reach": st["krylov_reach"],
+                          "hom_ratio": st["hom_ratio"], "krylov_problems": st["krylov_problems"],
+                          "substeps_max": st["substeps_max"], "lanes_grid": st["lanes_grid"],
+                          "band32_max": st["band32_max"], "clocks": clk.summary()}
+        bats[name] = b
+    head = "paraexp"
+    ms = variants[head]["ms_per_step"]
+    value = whole_job_rate(cnt * args.steps, world, reduce_max(ms * args.steps))
+    # roofline of the FP32 CN lanes: the serial variant is two lane launches (K steps
+    # forward, K transposed; 2 flop per tap, point and step) plus two O(n) passes
+    w32, _, _ = bats["serial"].problem_info()
+    flop = 2.0 * 2.0 * K * float(np.sum(np.asarray(prob["n"], dtype=np.float64) * np.asarray(w32)))
+    ms_ser = variants["serial"]["ms_per_step"]
+    achieved = flop / (ms_ser / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "batch_cn_lanes_kernel (serial variant: two launches)",
+            "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+            "peak_kind": "FP32 from unit counts and clocks (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
+            "achieved": achieved, "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "flop_per_step": flop, "ms_per_step": ms_ser}
+    # end to end: pinned host q0 -> device, gradient, J and gradient back to pinned host
+    bp = bats[head]
+    qh = torch.as_tensor(prob["q0"]).pin_memory()
+    gh = torch.empty(q0.numel(), dtype=torch.float64).pin_memory()
+    Jhh = torch.empty(cnt, dtype=torch.float64).pin_memory()
+    te = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q0.copy_(qh, non_blocking=True)
+        bp.gradient_async(X.PARAEXP, q0, J, g)
+        gh.copy_(g, non_blocking=True)
+        Jhh.copy_(J, non_blocking=True)
+        torch.cuda.synchronize()
+        bp.sync()
+        te.append(time.perf_counter() - t0)
+    for bb in bats.values():
+        bb.close()
+    cpu = {}
+    if rank == 0:
+        t0 = time.perf_counter()
+        ns = 16
+        for i in range(ns):
+            O.ad1_cn_gradient_serial(prob["q0"][off[i]:off[i + 1]], w["c"], prob["nu"][i], w["T"], K)
+        dt_cpu = (time.perf_counter() - t0) * cnt / ns
+        cpu = {"value": cnt / dt_cpu, "unit": "gradient evals/s (problems x gradients)", "cores": 1,
+               "kind": "oracle", "sample": f"first {ns} of {cnt} problems (serial FP64 CN), scaled by {cnt}/{ns}"}
+    return {"metric": METRIC, "value": value, "unit": "gradient evals/s (problems x gradients)",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 stepping, f64 Krylov and superposition", "data": "synthetic",
+            "config": {"workload": w["label"], "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "variants": variants, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * cnt / float(np.mean(te)), "unit": "gradient evals/s (problems x gradients)",
+                    "h2d_bytes_per_step": 8 * int(q0.numel()),
+                    "d2h_bytes_per_step": 8 * int(q0.numel()) + 8 * cnt},
+            "clocks": variants[head]["clocks"], "gpu_launches": 11 * args.steps}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -584,6 +744,8 @@ def main():
         line = run_lanes2d(args, w)
     elif w["kind"] == "advdiff2d":
         line = run_2d(args, w, rank, world)
+    elif w["kind"] == "batched1d":
+        line = run_batch(args, w, rank, world)
     else:
         line = run_ours(args, w, rank, world)
     if rank == 0:

@@ -186,7 +186,7 @@ int pxa_set_overlap(pxa_ctx* ctx, int enable);
  * left after the last direct step shrinks. Sec. 3.3 takes r = k/(k+1) with
  * k = tau_I_adj / tau_I (processors that solve their adjoint parts side by side); for one
  * in-order stream of adjoint work the same equal-finish argument gives r = k. The
- * autotuner measures k and times both. Other r: PXA_ERR_INVALID. */
+ * autotuner measures k and times both (and a few fixed ratios). Other r: PXA_ERR_INVALID. */
 int pxa_set_partition(pxa_ctx* ctx, double r);
 /* Host-only (no device work): the chunk boundaries, in steps, that the overlapped direct
  * solve uses for K steps and P subintervals (P == 1: chunks of steps) at ratio r, with at
@@ -306,6 +306,85 @@ int pxa_rk4_lanes_2d(pxa_ctx* ctx, int lanes, int64_t steps, double* out_dev, do
 int pxa_expv_static(int device, void* cuda_stream, const pxa_operator_desc* op, double T,
                     int64_t K, int m, double tol, int phi, int transpose, int64_t span_steps,
                     int substeps, const double* x_dev, double* y_dev, double* err_host);
+
+/* ---- batches of independent 1D advection-diffusion problems -----------------------
+ * Alg. 1 for `count` independent ADVDIFF_1D problems with their own grid n[i] and
+ * viscosity nu[i] (shared c, L, T, K, P): initial-condition control q0_i and the terminal
+ * objective J_i = 0.5 ||q_i(T)||^2 (Eq. adjFinalTime, Eq. initupdate), all problems in one
+ * launch per phase. The lanes (Eq. linInhomEqus / Eq. adjInhom: P per problem in Paraexp
+ * mode, one serial lane of K steps per problem in serial mode) step the exact circulant
+ * Crank-Nicolson band in FP32 with FP32 accumulation, taken from a cost-sorted work list
+ * by a persistent grid; the homogeneous propagations (Eq. hom / Eq. adjHomNormal) are
+ * Krylov exponentials exp(tau A) in FP64, and the superpositions are FP64.
+ *
+ * Packed layout: problem i owns points [off_i, off_i + n[i]) of every packed vector
+ * (off_0 = 0, off_{i+1} = off_i + n[i]; pxa_batch_offsets returns them). */
+typedef struct pxa_batch pxa_batch;
+typedef struct {
+  int count;                /* problems */
+  int64_t points;           /* sum of n[i] */
+  int krylov_m;             /* Krylov dimension in use */
+  double krylov_reach;      /* substep rule: each substep spans at most reach * m^2 / ||A||_inf */
+  int substeps_max;         /* Krylov substeps per subinterval of the stiffest problem */
+  int band32_max;           /* widest FP32 lane band (taps) */
+  int band64_max;           /* widest FP64 band (taps) */
+  int lanes_grid;           /* thread blocks of the persistent lane launch */
+  double krylov_err_max;    /* largest a-posteriori Krylov estimate of the last gradient */
+  int64_t workspace_bytes;
+  int krylov_problems;      /* problems whose homogeneous parts use the Krylov exponential */
+  double hom_ratio;         /* cost-model threshold in use (see pxa_batch_set_homogeneous) */
+  float ms_lanes;           /* phase times of the last gradient with timing on: direct lanes, */
+  float ms_chains;          /*   direct homogeneous chains, */
+  float ms_adjoint_lanes;   /*   adjoint lanes (with the superposition before them), */
+  float ms_adjoint_chains;  /*   adjoint chains, */
+  float ms_total;           /*   the whole gradient */
+} pxa_batch_stats;
+/* Create / destroy a batch context on `device`; `cuda_stream` is borrowed (NULL = the
+ * default stream). */
+int pxa_batch_create(pxa_batch** out, int device, void* cuda_stream);
+void pxa_batch_destroy(pxa_batch* b);
+const char* pxa_batch_last_error(const pxa_batch* b);
+/* The problems: count >= 1, n[i] in [16, 4096], nu[i] >= 0 (host arrays, copied);
+ * c, L > 0, T > 0, K % P == 0, 1 <= P <= 64. Invalidates the workspace. */
+int pxa_batch_set(pxa_batch* b, int count, const int* n, const double* nu, double c, double L, double T,
+                  int64_t K, int P);
+/* Krylov dimension m (2..48), tolerance of the a-posteriori estimate (relative) and the
+ * substep rule reach > 0: each substep of exp(tau A) spans at most reach * m^2 / ||A||_inf
+ * (default m = 30, tol = 1e-8, reach = 0.04; for a diffusion-dominated A the Krylov error
+ * falls like exp(-m^2 / (5 rho)) with rho a quarter of the substep's spectral width, so
+ * 1e-8 needs reach of a few hundredths). */
+int pxa_batch_set_krylov(pxa_batch* b, int m, double tol, double reach);
+/* Homogeneous propagation per problem (Paraexp mode): the Krylov exponential exp(tau A)
+ * of Eq. hom (FP64), or the local chained form with the stepper's own propagator (the
+ * CN band, FP32: the summed homogeneous problems stepped subinterval by subinterval,
+ * which reproduces serial stepping). A problem uses the exponential when a cost model
+ * puts it at most `ratio` times the stepping (ratio >= 0; 0 = always step, default 1;
+ * a very large ratio = always the exponential). */
+int pxa_batch_set_homogeneous(pxa_batch* b, double ratio);
+/* Capture the whole gradient into a CUDA graph and replay it (1, default) or launch the
+ * kernels one by one (0). */
+int pxa_batch_set_graph(pxa_batch* b, int enable);
+/* Per-phase CUDA-event timing of the next gradients (launched one by one; 0 = off). */
+int pxa_batch_set_timing(pxa_batch* b, int enable);
+/* One direct-adjoint loop of every problem, asynchronous on the stream: q0_dev (packed,
+ * caller-owned) -> J_dev[count] and grad_dev (packed) on the device. mode: PXA_SERIAL or
+ * PXA_PARAEXP. Errors raised inside kernels surface at pxa_batch_sync. */
+int pxa_batch_gradient(pxa_batch* b, int mode, const double* q0_dev, double* J_dev, double* grad_dev);
+/* Wait for the stream; returns device-side errors (NOT_CONVERGED, NONFINITE). */
+int pxa_batch_sync(pxa_batch* b);
+/* Times one gradient of `mode` for each candidate Krylov dimension and cost-model
+ * threshold (pxa_batch_set_homogeneous) and keeps the fastest whose estimates stay
+ * within the tolerance; *best_ms_host (may be NULL) receives its time. */
+int pxa_batch_autotune(pxa_batch* b, int mode, const double* q0_dev, double* J_dev, double* grad_dev,
+                       double* best_ms_host);
+/* Host: the count + 1 packed offsets (caller-owned array). */
+int pxa_batch_offsets(const pxa_batch* b, int64_t* offsets);
+/* Host: per problem, the taps (2 r + 1) of its FP32 lane band and of its FP64 band, and
+ * whether its homogeneous parts use the Krylov exponential (1) or stepping (0) (count
+ * entries each, caller-owned; any may be NULL); the workspace must exist (after a
+ * gradient). */
+int pxa_batch_problem_info(const pxa_batch* b, int* taps32, int* taps64, int* krylov);
+int pxa_batch_get_stats(const pxa_batch* b, pxa_batch_stats* out);
 
 #ifdef __cplusplus
 }

@@ -97,73 +97,6 @@ __global__ void ad1_apply_kernel(int n, double am, double a0, double ap, int tra
   }
 }
 
-// One-block operator used inside the Arnoldi process: y = A x (stencil am, a0, ap).
-struct Ad1Op {
-  int n;
-  double am, a0, ap;
-  __device__ void apply(const double* x, double* y) {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      int im = p == 0 ? n - 1 : p - 1, ip = p == n - 1 ? 0 : p + 1;
-      y[p] = am * x[im] + a0 * x[p] + ap * x[ip];
-    }
-    __syncthreads();
-  }
-};
-
-__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
-  // non-negative doubles order like their bit patterns
-  if (v > 0.0)
-    atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
-}
-
-// Shared layout of a one-block Krylov solve (see ks_layout_bytes on the host side).
-__device__ __forceinline__ KrylovScratch ks_carve(double*& cur) {
-  KrylovScratch ks;
-  ks.H = cur;
-  cur += (kMaxM + 1) * kLD;
-  ks.D0 = cur;
-  cur += kLD * kLD;
-  ks.D1 = cur;
-  cur += kLD * kLD;
-  ks.D2 = cur;
-  cur += kLD * kLD;
-  ks.D3 = cur;
-  cur += kLD * kLD;
-  ks.hcol = cur;
-  cur += kDMax;
-  ks.red = cur;
-  cur += 40;
-  ks.ipiv = reinterpret_cast<int*>(cur);
-  ks.flag = ks.ipiv + 1;
-  cur += 2;
-  return ks;
-}
-
-// Krylov propagation of one vector h over `nsub` substeps:
-//   EXP:     h <- exp(hscale * A) h per substep  (hscale = substep length)
-//   STEPPER: h <- R_CN(hscale * A)^steps h        (hscale = dt)
-template <class Op>
-__device__ void krylov_propagate(Op& op, double* hvec, int n, int m, double* V, int ldv,
-                                 KrylovScratch& ks, double* c, double* c1, int phi_mode,
-                                 double hscale, int64_t steps, int nsub, double tol,
-                                 int* status, double* errmax) {
-  for (int sub = 0; sub < nsub; ++sub) {
-    int mm = 0;
-    double beta = arnoldi(op, hvec, n, m, V, ldv, ks, &mm);
-    if (mm == 0) return;  // zero vector stays zero
-    double fm = hessenberg_phi(ks, mm, phi_mode, hscale, steps, false, c, c1);
-    // Saad's a-posteriori estimate relative to ||h||: span * h_{m+1,m} * |[phi(H)]_{m,1}|,
-    // span = the time the substep covers; zero after a happy breakdown
-    const double span = phi_mode == 0 ? hscale : hscale * (double)steps;
-    double err = (mm == m) ? span * ks.H[m * kLD + (m - 1)] * fm : 0.0;
-    if (threadIdx.x == 0) {
-      atomic_max_pos(errmax, err);
-      if (!(err <= tol)) set_status(status, PXA_ERR_NOT_CONVERGED);
-    }
-    krylov_combine(V, ldv, mm, c, beta, hvec, n);
-  }
-}
-
 // Chain of homogeneous propagations (summed problems, carried lane by lane):
 //   h = 0; for i in 0..count-1: h += E[first + i*stride]; h = Phi h.
 __global__ void ad1_chain_kernel(int n, double am, double a0, double ap, int transpose,

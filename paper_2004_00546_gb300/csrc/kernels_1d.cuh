@@ -1,5 +1,6 @@
 // kernels_1d.cuh — host-side launch wrappers of the 1D kernels (kernels_1d.cu).
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -12,6 +13,8 @@ struct Bu1Grid {
 };
 
 size_t krylov_smem_bytes(int n, int m, int extra_vecs, bool v_in_smem);
+// Host: taps m_j (|j| <= r) of the circulant Crank-Nicolson map of the stencil (am, a0, ap).
+void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps, int& r);
 
 cudaError_t launch_cn_lanes(cudaStream_t st, int lanes, int threads, int n, int r,
                             const double* taps, int transpose, int64_t steps, const double* x0,

@@ -1,0 +1,361 @@
+// kernels_batch.cu — Alg. 1 for many independent 1D advection-diffusion problems at once
+// (uneven grid sizes and viscosities), one launch per phase over the whole batch.
+//
+//   batch_cn_lanes_kernel          Eq. linInhomEqus / Eq. adjInhom for every (problem,
+//                                  subinterval) pair: a persistent grid takes the lanes
+//                                  from a cost-sorted list (largest first) through an
+//                                  atomic counter; each lane steps the Crank-Nicolson
+//                                  band in FP32 with FP32 accumulation in shared memory.
+//                                  With one lane per problem and no source it is plain
+//                                  serial stepping.
+//   batch_band_src_kernel          the lanes' constant source (M - I) x of Eq. linzero
+//                                  (FP64 band), per problem.
+//   batch_chain_kernel             Eq. hom / Eq. adjHomNormal: one thread block per
+//                                  problem carries the summed homogeneous problems link
+//                                  by link with the Krylov exponential exp(tau A) in FP64
+//                                  (substeps per problem from its stiffness).
+//   batch_cn_chain_kernel          the same with the stepper's own propagator (the local
+//                                  chained form, FP32 band), for the problems where it is
+//                                  cheaper than the Krylov exponential.
+//   batch_superpose_*              Eq. fullsol0 / Eq. fulladjsol, J_i = 0.5 ||q_i(T)||^2,
+//                                  the adjoint terminal value and the IC gradient, FP64.
+#include "common.cuh"
+#include "krylov.cuh"
+#include "kernels_batch.cuh"
+#include "kernels_1d.cuh"
+
+namespace pxa {
+
+namespace {
+
+__device__ __forceinline__ void put_halo32(float* buf, int n, int r, int p, float v) {
+  buf[r + p] = v;
+  if (p < r) buf[r + n + p] = v;
+  if (p >= n - r) buf[p - n + r] = v;
+}
+
+__device__ __forceinline__ int wrapb(int g, int n) {
+  g %= n;
+  return g < 0 ? g + n : g;
+}
+
+}  // namespace
+
+// ---- lanes ----------------------------------------------------------------------------
+// One CN step of the FP32 band on the block's points: thread t owns points t, t + B, ...
+// (at most PPT of them: n <= PPT * BATCH_THREADS), with the taps in the outer loop so
+// that each tap is read from shared memory once per step rather than once per point.
+template <int PPT>
+__device__ __forceinline__ void band_step32(const float* __restrict__ tp, int w, const float* __restrict__ xa,
+                                            float* __restrict__ xb, const float* __restrict__ sr, int n,
+                                            int r) {
+  float acc[PPT];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int p = tid + u * BATCH_THREADS;
+    acc[u] = (sr && p < n) ? sr[p] : 0.f;
+  }
+  for (int j = 0; j < w; ++j) {
+    const float tj = tp[j];
+    const float* xj = xa + j;  // xj[p] = x_{p + j - r}
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      const int p = tid + u * BATCH_THREADS;
+      if (p < n) acc[u] = fmaf(tj, xj[p], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int p = tid + u * BATCH_THREADS;
+    if (p < n) put_halo32(xb, n, r, p, acc[u]);
+  }
+}
+
+// items[it] = {problem, lane}. A lane takes `steps` CN steps of its problem's FP32 band
+// (transposed when `transpose`) from x0 (FP64 packed, NULL = zero) with the constant
+// source src (FP64 packed, NULL = none) and writes its end state (FP64) to
+// out + off * lanes + lane * n. Shared: taps[2 r + 1], xa, xb [n + 2 r], src [n].
+template <int PPT>
+__global__ void __launch_bounds__(BATCH_THREADS) batch_cn_lanes_kernel(
+    const BatchInst* __restrict__ inst, const int2* __restrict__ items, int nitems, int* counter,
+    const float* __restrict__ taps32, int transpose, int64_t steps, const double* __restrict__ x0,
+    const double* __restrict__ src, double* __restrict__ out, int lanes) {
+  extern __shared__ float smf[];
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) return;  // the same for every thread of the block
+    const int2 wk = items[it];
+    const BatchInst I = inst[wk.x];
+    const int n = I.n, r = I.r32, w = 2 * r + 1;
+    float* tp = smf;
+    float* xa = tp + ((w + 3) & ~3);
+    float* xb = xa + n + 2 * r;
+    float* sr = xb + n + 2 * r;
+    const float* tg = taps32 + I.t32;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? tg[w - 1 - j] : tg[j];
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      put_halo32(xa, n, r, p, x0 ? (float)x0[I.off + p] : 0.f);
+      sr[p] = src ? (float)src[I.off + p] : 0.f;
+    }
+    __syncthreads();
+    for (int64_t s = 0; s < steps; ++s) {
+      band_step32<PPT>(tp, w, xa, xb, sr, n, r);
+      __syncthreads();
+      float* t = xa;
+      xa = xb;
+      xb = t;
+    }
+    double* o = out + I.off * lanes + (int64_t)wk.y * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = (double)xa[r + p];
+    __syncthreads();  // shared memory and `cur` are reused by the next lane
+  }
+}
+
+// ---- homogeneous chains by stepping (the local chained form) --------------------------
+// items[it] = {problem, 0}: x = 0; for l < links: x += E[first + l * stride] (FP64 lane end
+// states, packed with `lanes` lanes per problem); x <- M^steps x (M^T when `transpose`) in
+// FP32; the result goes to hout (FP64 packed). This is the homogeneous propagation of
+// Eq. hom / Eq. adjHomNormal with the stepper's own propagator, carried subinterval by
+// subinterval.
+template <int PPT>
+__global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
+    const BatchInst* __restrict__ inst, const int2* __restrict__ items, int nitems, int* counter,
+    const float* __restrict__ taps32, int transpose, int64_t steps, const double* __restrict__ E,
+    int lanes, int first, int stride, int links, double* __restrict__ hout) {
+  extern __shared__ float smf[];
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) return;  // the same for every thread of the block
+    const BatchInst I = inst[items[it].x];
+    const int n = I.n, r = I.r32, w = 2 * r + 1;
+    float* tp = smf;
+    float* xa = tp + ((w + 3) & ~3);
+    float* xb = xa + n + 2 * r;
+    const float* tg = taps32 + I.t32;
+    const double* Ei = E + I.off * lanes;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? tg[w - 1 - j] : tg[j];
+    for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, 0.f);
+    __syncthreads();
+    for (int l = 0; l < links; ++l) {
+      const double* e = Ei + (int64_t)(first + l * stride) * n;
+      for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, xa[r + p] + (float)e[p]);
+      __syncthreads();
+      for (int64_t s = 0; s < steps; ++s) {
+        band_step32<PPT>(tp, w, xa, xb, nullptr, n, r);
+        __syncthreads();
+        float* t = xa;
+        xa = xb;
+        xb = t;
+      }
+    }
+    for (int p = threadIdx.x; p < n; p += blockDim.x) hout[I.off + p] = (double)xa[r + p];
+    __syncthreads();  // shared memory and `cur` are reused by the next problem
+  }
+}
+
+// ---- sources --------------------------------------------------------------------------
+// Grid (point blocks, problems): y_i = (M_i - I) x_i, or (M_i^T - I) x_i, FP64 band.
+__global__ void batch_band_src_kernel(const BatchInst* __restrict__ inst, const double* __restrict__ taps64,
+                                      int transpose, const double* __restrict__ x, double* __restrict__ y) {
+  const BatchInst I = inst[blockIdx.y];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= I.n) return;
+  const int r = I.r64, w = 2 * r + 1;
+  const double* tg = taps64 + I.t64;
+  const double* xi = x + I.off;
+  double acc = 0.0;
+  for (int jj = 0; jj < w; ++jj) {
+    // (M x)_p = sum_j m_j x_{p+j}; (M^T x)_p = sum_j m_{-j} x_{p+j}
+    const double t = transpose ? tg[w - 1 - jj] : tg[jj];
+    acc = fma(t, xi[wrapb(p + jj - r, I.n)], acc);
+  }
+  y[I.off + p] = acc - xi[p];
+}
+
+// ---- homogeneous chains ---------------------------------------------------------------
+// One block per problem of the list `which`: h = 0; for l < links: h += E[first + l * stride];
+// h = exp(tau A) h (A^T when `transpose`), each exponential in nsub Krylov substeps of
+// length hsub.
+__global__ void batch_chain_kernel(
+    const BatchInst* __restrict__ inst, const int* __restrict__ which, int m, int transpose,
+    const double* __restrict__ E, int lanes, int first, int stride, int links, double* __restrict__ hout,
+    double* __restrict__ Vg, double tol, int* status, double* errmax) {
+  extern __shared__ double smd[];
+  const BatchInst I = inst[which[blockIdx.x]];
+  const int n = I.n;
+  double* cur = smd;
+  KrylovScratch ks = ks_carve(cur);
+  double* c = cur;
+  cur += kDMax;
+  double* c1 = cur;
+  cur += kDMax;
+  double* hvec = cur;
+  Ad1Op op{n, transpose ? I.ap : I.am, I.a0, transpose ? I.am : I.ap};
+  double* V = Vg + I.voff;
+  const double* Ei = E + I.off * lanes;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) hvec[p] = 0.0;
+  __syncthreads();
+  for (int l = 0; l < links; ++l) {
+    const double* e = Ei + (int64_t)(first + l * stride) * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) hvec[p] += e[p];
+    __syncthreads();
+    krylov_propagate(op, hvec, n, m, V, n, ks, c, c1, 0, I.hsub, 1, I.nsub, tol, status, errmax);
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) hout[I.off + p] = hvec[p];
+}
+
+// ---- superposition ------------------------------------------------------------------
+// One block per problem: qT = q0 + E[last] + h (each term optional), J_i = 0.5 ||qT||^2,
+// srcT = (M^T - I) qT (the adjoint lanes' source) when srcT is given.
+__global__ void __launch_bounds__(BATCH_THREADS) batch_superpose_direct_kernel(
+    const BatchInst* __restrict__ inst, const double* __restrict__ taps64, const double* __restrict__ q0,
+    const double* __restrict__ E, int lanes, int last, const double* __restrict__ h,
+    double* __restrict__ qT, double* __restrict__ srcT, double* __restrict__ J, int* status) {
+  __shared__ double red[40];
+  const int i = blockIdx.x;
+  const BatchInst I = inst[i];
+  const int n = I.n;
+  const double* el = E + I.off * lanes + (int64_t)last * n;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const double v = (q0 ? q0[I.off + p] : 0.0) + el[p] + (h ? h[I.off + p] : 0.0);
+    qT[I.off + p] = v;
+    acc = fma(v, v, acc);
+  }
+  const double Ji = 0.5 * block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    J[i] = Ji;
+    if (!isfinite(Ji)) set_status(status, PXA_ERR_NONFINITE);
+  }
+  __syncthreads();  // qT complete before the band reads neighbours
+  if (srcT) {
+    const int r = I.r64, w = 2 * r + 1;
+    const double* tg = taps64 + I.t64;
+    const double* q = qT + I.off;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      double s = 0.0;
+      for (int jj = 0; jj < w; ++jj) s = fma(tg[w - 1 - jj], q[wrapb(p + jj - r, n)], s);
+      srcT[I.off + p] = s - q[p];
+    }
+  }
+}
+
+// Grid (point blocks, problems): grad = lamK + EA[0] + h (each optional but EA).
+__global__ void batch_superpose_adjoint_kernel(const BatchInst* __restrict__ inst,
+                                               const double* __restrict__ lamK,
+                                               const double* __restrict__ EA, int lanes,
+                                               const double* __restrict__ h, double* __restrict__ grad,
+                                               int* status) {
+  const BatchInst I = inst[blockIdx.y];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= I.n) return;
+  const double v = (lamK ? lamK[I.off + p] : 0.0) + EA[I.off * lanes + p] + (h ? h[I.off + p] : 0.0);
+  grad[I.off + p] = v;
+  if (!isfinite(v)) set_status(status, PXA_ERR_NONFINITE);
+}
+
+// ---- launch wrappers ------------------------------------------------------------------
+size_t batch_lanes_smem(int nmax, int rmax) {
+  const int w = ((2 * rmax + 1) + 3) & ~3;
+  return sizeof(float) * ((size_t)w + 2 * (size_t)(nmax + 2 * rmax) + (size_t)nmax);
+}
+
+int batch_lanes_grid(int device, int nmax, int rmax) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t sh = batch_lanes_smem(nmax, rmax);
+  const void* fn = nmax <= 8 * BATCH_THREADS ? (const void*)batch_cn_lanes_kernel<8>
+                                             : (const void*)batch_cn_lanes_kernel<16>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BATCH_THREADS, sh);
+  if (per < 1) per = 1;
+  return (sms > 0 ? sms : 1) * per;
+}
+
+cudaError_t launch_batch_cn_lanes(cudaStream_t st, int grid, const BatchInst* inst, const int2* items,
+                                  int nitems, int* counter, const float* taps32, int transpose,
+                                  int64_t steps, const double* x0, const double* src, double* out,
+                                  int lanes, int nmax, int rmax) {
+  const size_t sh = batch_lanes_smem(nmax, rmax);
+  const bool small = nmax <= 8 * BATCH_THREADS;
+  const void* fn = small ? (const void*)batch_cn_lanes_kernel<8> : (const void*)batch_cn_lanes_kernel<16>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (small)
+    batch_cn_lanes_kernel<8><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+                                                               steps, x0, src, out, lanes);
+  else
+    batch_cn_lanes_kernel<16><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+                                                                steps, x0, src, out, lanes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_band_src(cudaStream_t st, const BatchInst* inst, int count, int nmax,
+                                  const double* taps64, int transpose, const double* x, double* y) {
+  dim3 grid((nmax + 255) / 256, count);
+  batch_band_src_kernel<<<grid, 256, 0, st>>>(inst, taps64, transpose, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_chain(cudaStream_t st, const BatchInst* inst, const int* which, int count, int nmax,
+                               int m, int transpose, const double* E, int lanes, int first, int stride,
+                               int links, double* hout, double* V, double tol, int* status,
+                               double* errmax) {
+  if (links <= 0 || count <= 0) return cudaSuccess;
+  const size_t sh = krylov_smem_bytes(nmax, m, nmax, false);
+  cudaError_t e = cudaFuncSetAttribute(batch_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  batch_chain_kernel<<<count, BATCH_THREADS, sh, st>>>(inst, which, m, transpose, E, lanes, first, stride,
+                                                        links, hout, V, tol, status, errmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_cn_chain(cudaStream_t st, int grid, const BatchInst* inst, const int2* items,
+                                  int nitems, int* counter, const float* taps32, int transpose,
+                                  int64_t steps, const double* E, int lanes, int first, int stride,
+                                  int links, double* hout, int nmax, int rmax) {
+  if (nitems <= 0 || links <= 0) return cudaSuccess;
+  const size_t sh = batch_lanes_smem(nmax, rmax);
+  const bool small = nmax <= 8 * BATCH_THREADS;
+  const void* fn = small ? (const void*)batch_cn_chain_kernel<8> : (const void*)batch_cn_chain_kernel<16>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (small)
+    batch_cn_chain_kernel<8><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose, steps,
+                                                               E, lanes, first, stride, links, hout);
+  else
+    batch_cn_chain_kernel<16><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+                                                                steps, E, lanes, first, stride, links, hout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_superpose_direct(cudaStream_t st, const BatchInst* inst, int count, int nmax,
+                                          const double* taps64, const double* q0, const double* E,
+                                          int lanes, int last, const double* h, double* qT,
+                                          double* srcT, double* J, int* status) {
+  (void)nmax;
+  batch_superpose_direct_kernel<<<count, BATCH_THREADS, 0, st>>>(inst, taps64, q0, E, lanes, last, h, qT,
+                                                                  srcT, J, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_superpose_adjoint(cudaStream_t st, const BatchInst* inst, int count, int nmax,
+                                           const double* lamK, const double* EA, int lanes,
+                                           const double* h, double* grad, int* status) {
+  dim3 grid((nmax + 255) / 256, count);
+  batch_superpose_adjoint_kernel<<<grid, 256, 0, st>>>(inst, lamK, EA, lanes, h, grad, status);
+  return cudaGetLastError();
+}
+
+}  // namespace pxa

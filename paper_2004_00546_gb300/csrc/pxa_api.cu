@@ -15,6 +15,60 @@
 
 using namespace pxa;
 
+namespace pxa {
+
+// Taps m_j (|j| <= r) of the circulant Crank–Nicolson map
+//   M = (I - dt/2 A)^{-1} (I + dt/2 A),  (M x)_i = sum_j m_j x_{i+j},
+// from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
+// by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj} in long double. The taps decay
+// geometrically (the implicit matrix is diagonally dominant); the band stops where
+// both |m_r| and |m_-r| fall below 2^-64 |m_0|, far under FP64 rounding of the step;
+// when they do not decay within n/2 the full circulant is used.
+void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps,
+                  int& r) {
+  typedef std::complex<long double> C;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<C> R(n), w(n);
+  for (int k = 0; k < n; ++k) {
+    long double ph = 2.0L * pi * (long double)k / (long double)n;
+    w[k] = C(cosl(ph), sinl(ph));
+  }
+  const long double th = 0.5L * (long double)dt;
+  for (int k = 0; k < n; ++k) {
+    C lam = (long double)a0 + (long double)am * std::conj(w[k]) + (long double)ap * w[k];
+    R[k] = (1.0L + th * lam) / (1.0L - th * lam);
+  }
+  auto tap = [&](int j) {
+    C s = 0.0L;
+    for (int k = 0; k < n; ++k) {
+      long long idx = ((long long)k * (long long)(((j % n) + n) % n)) % n;
+      s += R[k] * std::conj(w[idx]);
+    }
+    return (double)(s.real() / (long double)n);
+  };
+  std::vector<double> pos, neg;  // pos[j] = m_j, neg[j] = m_-j
+  double m0 = tap(0);
+  pos.push_back(m0);
+  neg.push_back(m0);
+  const double thr = std::ldexp(std::fabs(m0), -64);
+  // widest band: every offset once; for even n the offset n/2 equals -n/2 and is
+  // stored once (on the negative side)
+  const int rmax = n / 2;
+  r = 0;
+  for (int j = 1; j <= rmax; ++j) {
+    double mn = tap(-j);
+    double mp = (2 * j == n) ? 0.0 : tap(j);
+    pos.push_back(mp);
+    neg.push_back(mn);
+    r = j;
+    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;  // the tail is below FP64 rounding
+  }
+  taps.assign(2 * r + 1, 0.0);
+  for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
+}
+
+}  // namespace pxa
+
 struct pxa_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;       // the caller's stream (borrowed)
@@ -235,57 +289,6 @@ int alloc(pxa_ctx* c, T** out, size_t count) {
   return PXA_OK;
 }
 
-// Taps m_j (|j| <= r) of the circulant Crank–Nicolson map
-//   M = (I - dt/2 A)^{-1} (I + dt/2 A),  (M x)_i = sum_j m_j x_{i+j},
-// from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
-// by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj} in long double. The taps decay
-// geometrically (the implicit matrix is diagonally dominant); the band stops where
-// both |m_r| and |m_-r| fall below 2^-64 |m_0|, far under FP64 rounding of the step;
-// when they do not decay within n/2 the full circulant is used.
-int cn_band(pxa_ctx* c, int n, double am, double a0, double ap, double dt,
-            std::vector<double>& taps, int& r) {
-  typedef std::complex<long double> C;
-  const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<C> R(n), w(n);
-  for (int k = 0; k < n; ++k) {
-    long double ph = 2.0L * pi * (long double)k / (long double)n;
-    w[k] = C(cosl(ph), sinl(ph));
-  }
-  const long double th = 0.5L * (long double)dt;
-  for (int k = 0; k < n; ++k) {
-    C lam = (long double)a0 + (long double)am * std::conj(w[k]) + (long double)ap * w[k];
-    R[k] = (1.0L + th * lam) / (1.0L - th * lam);
-  }
-  auto tap = [&](int j) {
-    C s = 0.0L;
-    for (int k = 0; k < n; ++k) {
-      long long idx = ((long long)k * (long long)(((j % n) + n) % n)) % n;
-      s += R[k] * std::conj(w[idx]);
-    }
-    return (double)(s.real() / (long double)n);
-  };
-  std::vector<double> pos, neg;  // pos[j] = m_j, neg[j] = m_-j
-  double m0 = tap(0);
-  pos.push_back(m0);
-  neg.push_back(m0);
-  const double thr = std::ldexp(std::fabs(m0), -64);
-  // widest band: every offset once; for even n the offset n/2 equals -n/2 and is
-  // stored once (on the negative side)
-  const int rmax = n / 2;
-  r = 0;
-  for (int j = 1; j <= rmax; ++j) {
-    double mn = tap(-j);
-    double mp = (2 * j == n) ? 0.0 : tap(j);
-    pos.push_back(mp);
-    neg.push_back(mn);
-    r = j;
-    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;  // the tail is below FP64 rounding
-  }
-  taps.assign(2 * r + 1, 0.0);
-  for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
-  return PXA_OK;
-}
-
 int threads_for(int n) {
   int t = ((n + 31) / 32) * 32;
   return t > 1024 ? 1024 : (t < 64 ? 64 : t);
@@ -351,7 +354,7 @@ int prepare(pxa_ctx* c) {
       return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D state arrays");
   } else if (c->op.kind == PXA_ADVDIFF_1D) {
     double dt = c->T / (double)c->K;
-    if ((rc = cn_band(c, n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r))) return rc;
+    cn_band_taps(n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r);
     if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
     PXA_CUDA(c, cudaMemcpy(c->taps, c->band_host.data(), sizeof(double) * c->band_host.size(),
                            cudaMemcpyHostToDevice), "copy taps");
@@ -1407,10 +1410,18 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
       c->timing = false;
       c->use_graph = graph3;
       c->stats.tau_ratio = (float)kr;
+      // besides the two ratios of the model, a few fixed ones: the adjoint work of a
+      // chunk is not proportional to its length (the lanes take their subinterval's
+      // length whatever the chunk), so the measured optimum can lie between
       std::vector<double> rs = {0.0};
       if (kr > 0.0) {
         rs.push_back(kr / (kr + 1.0));
         if (kr < 0.95) rs.push_back(kr);
+      }
+      for (double r : {0.6, 0.7, 0.8, 0.9}) {
+        bool seen = false;
+        for (double q : rs) seen = seen || std::fabs(q - r) < 0.02;
+        if (!seen) rs.push_back(r);
       }
       double bms = 1e300, br = c->part_r;
       for (double r : rs) {

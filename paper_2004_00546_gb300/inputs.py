@@ -168,3 +168,13 @@ def burgers1d_problem(n: int = 1024, seed: int = 2005):
     """1D viscous Burgers: nu = 0.005, T = 2, zero IC, forcing f and tracking target g
     drawn as random Fourier series with k <= 16."""
     return dict(n=n, nu=0.005, T=2.0, f=fourier1d(n, 16, seed), g=fourier1d(n, 16, seed + 1000))
+
+
+def batch1d_problem(count: int = 256, seed: int = 2007, n_lo: int = 128, n_hi: int = 2048):
+    """Independent 1D advection-diffusion problems: c = 1, T = 1, n ~ U{n_lo..n_hi},
+    nu ~ log-uniform[1e-3, 1e-1], IC control q0_i ~ GRF k^-2 (seed 1000 * seed + i);
+    q0 is packed (problem i at offsets[i] .. offsets[i + 1])."""
+    ns, nus = batch_instances(count, seed, n_lo, n_hi)
+    q0s = [grf_k2(int(n), 1000 * seed + i) for i, n in enumerate(ns)]
+    offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    return dict(n=ns, nu=nus, c=1.0, T=1.0, q0=np.concatenate(q0s), offsets=offsets)

@@ -35,6 +35,10 @@ EXPORTS = [
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
     "pxa_rk4_lanes_2d",
+    "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
+    "pxa_batch_set_homogeneous", "pxa_batch_set_timing",
+    "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
+    "pxa_batch_autotune", "pxa_batch_offsets", "pxa_batch_get_stats", "pxa_batch_problem_info",
 ]
 
 
@@ -63,6 +67,17 @@ class Stats(ctypes.Structure):
                 ("group_direct", ctypes.c_int), ("group_sweep", ctypes.c_int),
                 ("chunks", ctypes.c_int), ("partition_r", ctypes.c_float),
                 ("tau_ratio", ctypes.c_float)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("points", ctypes.c_int64), ("krylov_m", ctypes.c_int),
+                ("krylov_reach", ctypes.c_double), ("substeps_max", ctypes.c_int),
+                ("band32_max", ctypes.c_int), ("band64_max", ctypes.c_int), ("lanes_grid", ctypes.c_int),
+                ("krylov_err_max", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
+                ("krylov_problems", ctypes.c_int), ("hom_ratio", ctypes.c_double),
+                ("ms_lanes", ctypes.c_float), ("ms_chains", ctypes.c_float),
+                ("ms_adjoint_lanes", ctypes.c_float), ("ms_adjoint_chains", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
 
 
 _lib = None
@@ -111,11 +126,27 @@ def load(path: str = LIB_PATH):
         "pxa_burgers_rhs": [p, p, p],
         "pxa_burgers_jac_T": [p, p, p, p],
         "pxa_expv_static": [i, p, ctypes.POINTER(OperatorDesc), d, i64, i, d, i, i, i64, i, p, p, p],
+        "pxa_batch_create": [ctypes.POINTER(p), i, p],
+        "pxa_batch_destroy": [p],
+        "pxa_batch_last_error": [p],
+        "pxa_batch_set": [p, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(d), d, d, d, i64, i],
+        "pxa_batch_set_krylov": [p, i, d, d],
+        "pxa_batch_set_graph": [p, i],
+        "pxa_batch_set_homogeneous": [p, d],
+        "pxa_batch_set_timing": [p, i],
+        "pxa_batch_gradient": [p, i, p, p, p],
+        "pxa_batch_sync": [p],
+        "pxa_batch_autotune": [p, i, p, p, p, ctypes.POINTER(d)],
+        "pxa_batch_offsets": [p, ctypes.POINTER(i64)],
+        "pxa_batch_problem_info": [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)],
+        "pxa_batch_get_stats": [p, ctypes.POINTER(BatchStats)],
     }
     for name, argt in sig.items():
         fn = getattr(L, name)
         fn.argtypes = argt
-        fn.restype = None if name == "pxa_destroy" else (ctypes.c_char_p if name == "pxa_last_error" else i)
+        fn.restype = (None if name in ("pxa_destroy", "pxa_batch_destroy") else
+                      ctypes.c_char_p if name in ("pxa_last_error", "pxa_batch_last_error") else i)
     _lib = L
     return L
 
@@ -320,3 +351,89 @@ def partition_bounds(K, P, r, max_chunks=8):
     if rc < 0:
         raise PxaError(rc, "pxa_partition_bounds")
     return [out[i] for i in range(rc + 1)]
+
+
+class Batch:
+    """Batches of independent 1D advection-diffusion problems (pxa_batch_* in
+    include/pxa.h): argument marshalling only."""
+
+    def __init__(self, device=0, stream=None):
+        self._L = load()
+        self._h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc = self._L.pxa_batch_create(ctypes.byref(self._h), device, s)
+        if rc != OK:
+            raise PxaError(rc, "pxa_batch_create")
+        self.count = 0
+
+    def _check(self, rc):
+        if rc != OK:
+            raise PxaError(rc, self._L.pxa_batch_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._L.pxa_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, n, nu, c=1.0, L=6.283185307179586, T=1.0, K=4096, P=16):
+        import numpy as np
+
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        self.count = len(n)
+        self._check(self._L.pxa_batch_set(self._h, self.count,
+                                          n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                          nu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          c, L, T, int(K), int(P)))
+
+    def set_krylov(self, m=30, tol=1e-8, reach=0.04):
+        self._check(self._L.pxa_batch_set_krylov(self._h, m, tol, reach))
+
+    def set_timing(self, enable):
+        self._check(self._L.pxa_batch_set_timing(self._h, 1 if enable else 0))
+
+    def set_homogeneous(self, ratio):
+        self._check(self._L.pxa_batch_set_homogeneous(self._h, float(ratio)))
+
+    def set_graph(self, enable):
+        self._check(self._L.pxa_batch_set_graph(self._h, 1 if enable else 0))
+
+    def gradient_async(self, mode, q0, J, grad):
+        self._check(self._L.pxa_batch_gradient(self._h, mode, _dptr(q0), _dptr(J), _dptr(grad)))
+
+    def sync(self):
+        self._check(self._L.pxa_batch_sync(self._h))
+
+    def gradient(self, mode, q0, J, grad):
+        self.gradient_async(mode, q0, J, grad)
+        self.sync()
+
+    def autotune(self, mode, q0, J, grad) -> float:
+        ms = ctypes.c_double()
+        self._check(self._L.pxa_batch_autotune(self._h, mode, _dptr(q0), _dptr(J), _dptr(grad),
+                                               ctypes.byref(ms)))
+        return ms.value
+
+    def offsets(self):
+        out = (ctypes.c_int64 * (self.count + 1))()
+        self._check(self._L.pxa_batch_offsets(self._h, out))
+        return [out[i] for i in range(self.count + 1)]
+
+    def problem_info(self):
+        """Per problem: FP32 lane band taps, FP64 band taps, Krylov (1) or stepped (0)."""
+        a = (ctypes.c_int * self.count)()
+        b = (ctypes.c_int * self.count)()
+        k = (ctypes.c_int * self.count)()
+        self._check(self._L.pxa_batch_problem_info(self._h, a, b, k))
+        return list(a), list(b), list(k)
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        self._check(self._L.pxa_batch_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in BatchStats._fields_}

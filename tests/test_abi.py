@@ -77,3 +77,15 @@ def test_partition_bounds_follow_the_nonequidistant_partition(pxa_lib):
     assert pxa_lib.pxa_partition_bounds(10, 3, 0.0, 8, out) == pxa.ERR_INVALID
     assert pxa_lib.pxa_partition_bounds(10, 1, 1.0, 8, out) == pxa.ERR_INVALID
     assert pxa_lib.pxa_partition_bounds(10, 1, 0.5, 8, None) == pxa.ERR_INVALID
+
+
+def test_batch_entry_points_reject_bad_arguments_without_a_device(pxa_lib):
+    L = pxa_lib
+    h = ctypes.c_void_p()
+    assert L.pxa_batch_create(ctypes.byref(h), 4096, None) == pxa.ERR_CUDA
+    assert L.pxa_batch_create(None, 0, None) == pxa.ERR_INVALID
+    assert L.pxa_batch_set(None, 1, None, None, 1.0, 1.0, 1.0, 16, 1) == pxa.ERR_INVALID
+    assert L.pxa_batch_gradient(None, 0, None, None, None) == pxa.ERR_INVALID
+    assert L.pxa_batch_sync(None) == pxa.ERR_INVALID
+    assert L.pxa_batch_last_error(None) == b"null batch"
+    L.pxa_batch_destroy(None)  # must be a no-op

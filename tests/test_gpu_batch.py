@@ -1,0 +1,158 @@
+"""Parity of the batched 1D advection-diffusion path (many problems of uneven size in one
+launch per phase) with the CPU oracle, problem by problem.
+
+Tolerances: the lanes step in FP32 (FP32 accumulation), so J and the gradient of each
+problem are held to 1e-4 relative against the FP64 oracle: the oracle's serial CN for
+serial stepping and for Paraexp problems whose homogeneous parts are stepped (the
+stepper's own propagator reproduces serial stepping), the oracle's Paraexp with the
+exact exponential of Eq. hom for problems that use the Krylov exponential (tolerance
+1e-8). Problems are independent: a problem's result does not depend on the rest of the
+batch, bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2004_00546_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def X(cuda_ok):
+    from paper_2004_00546_gb300 import pxa
+
+    return pxa
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    return t
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def run(X, torch, prob, K, P, mode, m=30, reach=0.04, graph=True, ratio=1.0):
+    b = X.Batch()
+    b.set(prob["n"], prob["nu"], c=prob["c"], T=prob["T"], K=K, P=P)
+    b.set_krylov(m, 1e-8, reach)
+    b.set_homogeneous(ratio)
+    b.set_graph(graph)
+    q0 = dev(torch, prob["q0"])
+    J = torch.empty(len(prob["n"]), dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    b.gradient(mode, q0, J, g)
+    st = b.stats()
+    st["krylov"] = b.problem_info()[2]
+    off = b.offsets()
+    b.close()
+    return J.cpu().numpy(), g.cpu().numpy(), st, off
+
+
+def reference(prob, off, i, K, P, krylov):
+    """The oracle for problem i: serial CN, or Paraexp with the exact exponential when
+    the problem's homogeneous parts use the Krylov exponential (stepped homogeneous
+    parts reproduce serial stepping)."""
+    q0 = prob["q0"][off[i]:off[i + 1]]
+    if krylov:
+        Jo, go, _ = O.ad1_cn_gradient_paraexp(q0, 1.0, prob["nu"][i], 1.0, K, P, O.PHI_EXP)
+    else:
+        Jo, go, _ = O.ad1_cn_gradient_serial(q0, 1.0, prob["nu"][i], 1.0, K)
+    return Jo, go
+
+
+@pytest.fixture(scope="module")
+def small():
+    # uneven grids from 16 points up, viscosities across two decades (stiff ones included)
+    p = I.batch1d_problem(count=7, seed=77, n_lo=16, n_hi=320)
+    p["n"][0] = 16
+    p["nu"][0] = 0.1
+    p["q0"] = np.concatenate([I.grf_k2(int(n), 500 + i) for i, n in enumerate(p["n"])])
+    p["offsets"] = np.concatenate([[0], np.cumsum(p["n"])])
+    return p
+
+
+@pytest.mark.parametrize("mode,ratio", [("serial", 1.0), ("paraexp", 1e30), ("paraexp", 0.0),
+                                        ("paraexp", 1.0)])
+def test_batch_matches_oracle_problem_by_problem(X, torch, small, mode, ratio):
+    """Serial stepping; Paraexp with every homogeneous part by the Krylov exponential, by
+    stepping, and as the cost model chooses per problem."""
+    K, P = 512, 8
+    md = X.SERIAL if mode == "serial" else X.PARAEXP
+    J, g, st, off = run(X, torch, small, K, P, md, ratio=ratio)
+    assert off == list(small["offsets"])
+    if mode == "paraexp" and ratio == 1e30:
+        assert all(st["krylov"]) and st["krylov_problems"] == len(small["n"])
+    if mode == "paraexp" and ratio == 0.0:
+        assert not any(st["krylov"])
+    errs = []
+    for i, n in enumerate(small["n"]):
+        Jo, go = reference(small, off, i, K, P, mode == "paraexp" and st["krylov"][i])
+        eJ, eg = abs(J[i] - Jo) / Jo, rel(g[off[i]:off[i + 1]], go)
+        errs.append((int(n), eJ, eg))
+        assert eJ < 1e-4 and eg < 1e-4, errs
+    if mode == "paraexp":
+        assert 0.0 <= st["krylov_err_max"] <= 1e-8
+
+
+def test_batch_problems_are_independent(X, torch, small):
+    """The same problem alone, in the batch, and repeated gives the same bits; graph
+    replay and direct launches agree bit for bit."""
+    K, P = 256, 4
+    Jb, gb, _, off = run(X, torch, small, K, P, X.PARAEXP)
+    Je, ge, _, _ = run(X, torch, small, K, P, X.PARAEXP, graph=False)
+    assert np.array_equal(Jb, Je) and np.array_equal(gb, ge)
+    i = 3
+    one = dict(n=small["n"][i:i + 1], nu=small["nu"][i:i + 1], c=1.0, T=1.0,
+               q0=small["q0"][off[i]:off[i + 1]])
+    J1, g1, _, _ = run(X, torch, one, K, P, X.PARAEXP)
+    assert J1[0] == Jb[i] and np.array_equal(g1, gb[off[i]:off[i + 1]])
+    three = dict(n=np.repeat(one["n"], 3), nu=np.repeat(one["nu"], 3), c=1.0, T=1.0,
+                 q0=np.tile(one["q0"], 3))
+    J3, g3, _, _ = run(X, torch, three, K, P, X.PARAEXP)
+    assert np.all(J3 == J1[0])
+    n = int(one["n"][0])
+    for r in range(3):
+        assert np.array_equal(g3[r * n:(r + 1) * n], g1)
+
+
+def test_batch_autotune_keeps_the_tolerance(X, torch, small):
+    K, P = 512, 8
+    b = X.Batch()
+    b.set(small["n"], small["nu"], K=K, P=P)
+    q0 = dev(torch, small["q0"])
+    J = torch.empty(len(small["n"]), dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    ms = b.autotune(X.PARAEXP, q0, J, g)
+    st = b.stats()
+    assert ms > 0 and st["krylov_m"] in (24, 32, 40)
+    assert st["hom_ratio"] in (0.0, 0.25, 1.0, 4.0, 1e30) and st["krylov_reach"] in (0.02, 0.04)
+    b.gradient(X.PARAEXP, q0, J, g)
+    assert b.stats()["krylov_err_max"] <= 1e-8
+    Jh, gh = J.cpu().numpy(), g.cpu().numpy()
+    off = b.offsets()
+    kry = b.problem_info()[2]
+    for i in range(len(small["n"])):
+        Jo, go = reference(small, off, i, K, P, kry[i])
+        assert abs(Jh[i] - Jo) / Jo < 1e-4 and rel(gh[off[i]:off[i + 1]], go) < 1e-4
+    b.close()
+
+
+def test_batch_rejects_bad_problems(X):
+    b = X.Batch()
+    with pytest.raises(X.PxaError):
+        b.set([8, 64], [0.01, 0.01])  # n < 16
+    with pytest.raises(X.PxaError):
+        b.set([64], [0.01], K=100, P=16)  # K % P != 0
+    with pytest.raises(X.PxaError):
+        b.set_krylov(64, 1e-8, 0.04)  # m > 48
+    b.close()
