@@ -72,6 +72,8 @@ TRAFFIC = {
     # rows stay in L2 during the launch)
     "bu1_rk4_sweep_kernel": 8 * 61.95e3,
     "bu1_band_sweep_kernel": 1.6407e9 + 0.1587e9,
+    # the four-step chain: 4 segment launches of 348.8 MB read + 10.8 MB written each
+    "bu1_band_chain4_kernel": 4 * (348.8e6 + 10.8e6),
     "bu1_band_prepass_kernel": 8 * (30.49e6 + 357.0e6),
 }
 
@@ -350,11 +352,10 @@ def run_ours(args, w, rank, world):
             kernels["bu1_band_sweep_kernel (lanes)"] = (ph["ms_adjoint_inhom"], FLOPS_BAND_SWEEP * n * K,
                                                         P * cl[1], None)
             if head == "paraexp_stepper":
-                kernels["bu1_band_sweep_kernel (chain)"] = (ph["ms_adjoint_hom"],
-                                                            FLOPS_BAND_SWEEP * n * k * (P - 1), cl[2],
-                                                            TRAFFIC.get("bu1_band_sweep_kernel"))
-                floors["bu1_band_sweep_kernel (chain)"] = (k * (P - 1) * FP64_INSTR_BAND_STEP * 64
-                                                           / SM_CLOCK_HZ * 1e3)
+                # the chain phase: bu1_band_chain4_kernel in 4 segments (four-step entries,
+                # 33 taps = 66 flop per point per 4 steps) with the fill of the skipped rows
+                kernels["bu1_band_chain4_kernel (chain)"] = (ph["ms_adjoint_hom"], 66.0 / 4 * n * K, cl[2],
+                                                             TRAFFIC.get("bu1_band_chain4_kernel"))
         else:
             kernels["bu1c_adjoint_lanes_kernel"] = (ph["ms_adjoint_inhom"], FLOPS_RK4_ADJOINT * n * K,
                                                     P * cl[1], None)
@@ -408,6 +409,35 @@ def run_ours(args, w, rank, world):
     }
     ctx.close()
     return line
+
+
+def run_batch_once(args, w):
+    """W warm-up gradients and one more of the batched workload in each mode (Paraexp
+    with the homogeneous parts stepped, then serial), launched one by one with phase
+    events, for ncu: no autotuner."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, inputs as I, pxa as X
+
+    build.build()
+    X.load()
+    prob = I.batch1d_problem(count=w["count"], seed=2007)
+    q0 = torch.as_tensor(prob["q0"], device="cuda")
+    J = torch.empty(w["count"], dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    out = {"once": w["label"], "warmup": args.warmup}
+    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+        b = X.Batch()
+        b.set(prob["n"], prob["nu"], c=w["c"], T=w["T"], K=w["K"], P=w["P"])
+        b.set_homogeneous(0.0)
+        b.set_timing(True)
+        for _ in range(args.warmup + 1):
+            b.gradient(mode, q0, J, g)
+        st = b.stats()
+        out[name] = {k: st[k] for k in ("ms_lanes", "ms_chains", "ms_adjoint_lanes", "ms_adjoint_chains",
+                                        "ms_total", "lanes_grid", "band32_max")}
+        b.close()
+    return out
 
 
 def run_once(args, w):
@@ -740,6 +770,8 @@ def main():
         dist.init_process_group("nccl")
     if args.once and w["kind"] in ("burgers1d", "advdiff1d"):
         line = run_once(args, w)
+    elif args.once and w["kind"] == "batched1d":
+        line = run_batch_once(args, w)
     elif w["kind"] == "lanes2d":
         line = run_lanes2d(args, w)
     elif w["kind"] == "advdiff2d":
