@@ -42,33 +42,55 @@ __device__ __forceinline__ int wrapb(int g, int n) {
 }  // namespace
 
 // ---- lanes ----------------------------------------------------------------------------
-// One CN step of the FP32 band on the block's points: thread t owns points t, t + B, ...
-// (at most PPT of them: n <= PPT * BATCH_THREADS), with the taps in the outer loop so
-// that each tap is read from shared memory once per step rather than once per point.
+// One CN step of the FP32 band on the block's points. Thread t owns the PPT consecutive
+// points t*PPT .. t*PPT+PPT-1 (PPT odd, so that the threads of a warp read shared memory
+// at a stride coprime with the 32 banks) and keeps a window of 2*PPT state values in
+// registers: taps are taken PPT at a time (the band is zero-padded to a multiple of
+// PPT), each tap and each new state value is read from shared memory once and feeds PPT
+// FMAs. xa[i] = x_{i-r}; the tap j of point p reads xa[p + j].
 template <int PPT>
-__device__ __forceinline__ void band_step32(const float* __restrict__ tp, int w, const float* __restrict__ xa,
+__device__ __forceinline__ void band_step32(const float* __restrict__ tp, int wp, const float* __restrict__ xa,
                                             float* __restrict__ xb, const float* __restrict__ sr, int n,
                                             int r) {
-  float acc[PPT];
-  const int tid = threadIdx.x;
+  const int b = threadIdx.x * PPT;
+  if (b >= n) return;
+  float acc[PPT], w1[PPT], w2[PPT];
 #pragma unroll
   for (int u = 0; u < PPT; ++u) {
-    const int p = tid + u * BATCH_THREADS;
-    acc[u] = (sr && p < n) ? sr[p] : 0.f;
+    acc[u] = (sr && b + u < n) ? sr[b + u] : 0.f;
+    w1[u] = xa[b + u];
   }
-  for (int j = 0; j < w; ++j) {
-    const float tj = tp[j];
-    const float* xj = xa + j;  // xj[p] = x_{p + j - r}
+  for (int jb = 0; jb < wp; jb += PPT) {
 #pragma unroll
-    for (int u = 0; u < PPT; ++u) {
-      const int p = tid + u * BATCH_THREADS;
-      if (p < n) acc[u] = fmaf(tj, xj[p], acc[u]);
+    for (int u = 0; u < PPT; ++u) w2[u] = xa[b + jb + PPT + u];
+#pragma unroll
+    for (int jj = 0; jj < PPT; ++jj) {
+      const float tj = tp[jb + jj];
+#pragma unroll
+      for (int u = 0; u < PPT; ++u) acc[u] = fmaf(tj, u + jj < PPT ? w1[u + jj] : w2[u + jj - PPT], acc[u]);
     }
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) w1[u] = w2[u];
   }
 #pragma unroll
-  for (int u = 0; u < PPT; ++u) {
-    const int p = tid + u * BATCH_THREADS;
-    if (p < n) put_halo32(xb, n, r, p, acc[u]);
+  for (int u = 0; u < PPT; ++u)
+    if (b + u < n) put_halo32(xb, n, r, b + u, acc[u]);
+}
+
+// Shared layout of one lane: taps [wp] (zero beyond 2r+1), xa and xb [n + 2r + 2 PPT]
+// (the tail past the halo is zero: it meets only the zero taps), src [n].
+template <int PPT>
+__device__ __forceinline__ void lane_layout(float* smf, int n, int r, int w, float*& tp, int& wp, float*& xa,
+                                            float*& xb, float*& sr) {
+  wp = ((w + PPT - 1) / PPT) * PPT;
+  tp = smf;
+  xa = tp + ((wp + 3) & ~3);
+  const int len = n + 2 * r + 2 * PPT;
+  xb = xa + len;
+  sr = xb + len;
+  for (int j = threadIdx.x; j < 2 * PPT; j += blockDim.x) {
+    xa[n + 2 * r + j] = 0.f;
+    xb[n + 2 * r + j] = 0.f;
   }
 }
 
@@ -91,19 +113,18 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_lanes_kernel(
     const int2 wk = items[it];
     const BatchInst I = inst[wk.x];
     const int n = I.n, r = I.r32, w = 2 * r + 1;
-    float* tp = smf;
-    float* xa = tp + ((w + 3) & ~3);
-    float* xb = xa + n + 2 * r;
-    float* sr = xb + n + 2 * r;
+    float *tp, *xa, *xb, *sr;
+    int wp;
+    lane_layout<PPT>(smf, n, r, w, tp, wp, xa, xb, sr);
     const float* tg = taps32 + I.t32;
-    for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? tg[w - 1 - j] : tg[j];
+    for (int j = threadIdx.x; j < wp; j += blockDim.x) tp[j] = j < w ? (transpose ? tg[w - 1 - j] : tg[j]) : 0.f;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
       put_halo32(xa, n, r, p, x0 ? (float)x0[I.off + p] : 0.f);
       sr[p] = src ? (float)src[I.off + p] : 0.f;
     }
     __syncthreads();
     for (int64_t s = 0; s < steps; ++s) {
-      band_step32<PPT>(tp, w, xa, xb, sr, n, r);
+      band_step32<PPT>(tp, wp, xa, xb, src ? sr : nullptr, n, r);
       __syncthreads();
       float* t = xa;
       xa = xb;
@@ -135,12 +156,12 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
     if (it >= nitems) return;  // the same for every thread of the block
     const BatchInst I = inst[items[it].x];
     const int n = I.n, r = I.r32, w = 2 * r + 1;
-    float* tp = smf;
-    float* xa = tp + ((w + 3) & ~3);
-    float* xb = xa + n + 2 * r;
+    float *tp, *xa, *xb, *sr;
+    int wp;
+    lane_layout<PPT>(smf, n, r, w, tp, wp, xa, xb, sr);
     const float* tg = taps32 + I.t32;
     const double* Ei = E + I.off * lanes;
-    for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? tg[w - 1 - j] : tg[j];
+    for (int j = threadIdx.x; j < wp; j += blockDim.x) tp[j] = j < w ? (transpose ? tg[w - 1 - j] : tg[j]) : 0.f;
     for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, 0.f);
     __syncthreads();
     for (int l = 0; l < links; ++l) {
@@ -148,7 +169,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
       for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, xa[r + p] + (float)e[p]);
       __syncthreads();
       for (int64_t s = 0; s < steps; ++s) {
-        band_step32<PPT>(tp, w, xa, xb, nullptr, n, r);
+        band_step32<PPT>(tp, wp, xa, xb, nullptr, n, r);
         __syncthreads();
         float* t = xa;
         xa = xb;
@@ -262,17 +283,23 @@ __global__ void batch_superpose_adjoint_kernel(const BatchInst* __restrict__ ins
 }
 
 // ---- launch wrappers ------------------------------------------------------------------
+namespace {
+constexpr int PPT_SMALL = 9, PPT_LARGE = 17;  // odd: coprime with the 32 shared-memory banks
+bool small_lanes(int nmax) { return nmax <= PPT_SMALL * BATCH_THREADS; }
+}  // namespace
+
 size_t batch_lanes_smem(int nmax, int rmax) {
-  const int w = ((2 * rmax + 1) + 3) & ~3;
-  return sizeof(float) * ((size_t)w + 2 * (size_t)(nmax + 2 * rmax) + (size_t)nmax);
+  const int ppt = small_lanes(nmax) ? PPT_SMALL : PPT_LARGE;
+  const int wp = ((2 * rmax + 1 + ppt - 1) / ppt) * ppt;
+  return sizeof(float) * ((size_t)((wp + 3) & ~3) + 2 * (size_t)(nmax + 2 * rmax + 2 * ppt) + (size_t)nmax);
 }
 
 int batch_lanes_grid(int device, int nmax, int rmax) {
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   const size_t sh = batch_lanes_smem(nmax, rmax);
-  const void* fn = nmax <= 8 * BATCH_THREADS ? (const void*)batch_cn_lanes_kernel<8>
-                                             : (const void*)batch_cn_lanes_kernel<16>;
+  const void* fn = small_lanes(nmax) ? (const void*)batch_cn_lanes_kernel<PPT_SMALL>
+                                     : (const void*)batch_cn_lanes_kernel<PPT_LARGE>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BATCH_THREADS, sh);
   if (per < 1) per = 1;
@@ -284,17 +311,17 @@ cudaError_t launch_batch_cn_lanes(cudaStream_t st, int grid, const BatchInst* in
                                   int64_t steps, const double* x0, const double* src, double* out,
                                   int lanes, int nmax, int rmax) {
   const size_t sh = batch_lanes_smem(nmax, rmax);
-  const bool small = nmax <= 8 * BATCH_THREADS;
-  const void* fn = small ? (const void*)batch_cn_lanes_kernel<8> : (const void*)batch_cn_lanes_kernel<16>;
+  const bool small = small_lanes(nmax);
+  const void* fn = small ? (const void*)batch_cn_lanes_kernel<PPT_SMALL> : (const void*)batch_cn_lanes_kernel<PPT_LARGE>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (small)
-    batch_cn_lanes_kernel<8><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+    batch_cn_lanes_kernel<PPT_SMALL><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
                                                                steps, x0, src, out, lanes);
   else
-    batch_cn_lanes_kernel<16><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+    batch_cn_lanes_kernel<PPT_LARGE><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
                                                                 steps, x0, src, out, lanes);
   return cudaGetLastError();
 }
@@ -325,17 +352,17 @@ cudaError_t launch_batch_cn_chain(cudaStream_t st, int grid, const BatchInst* in
                                   int links, double* hout, int nmax, int rmax) {
   if (nitems <= 0 || links <= 0) return cudaSuccess;
   const size_t sh = batch_lanes_smem(nmax, rmax);
-  const bool small = nmax <= 8 * BATCH_THREADS;
-  const void* fn = small ? (const void*)batch_cn_chain_kernel<8> : (const void*)batch_cn_chain_kernel<16>;
+  const bool small = small_lanes(nmax);
+  const void* fn = small ? (const void*)batch_cn_chain_kernel<PPT_SMALL> : (const void*)batch_cn_chain_kernel<PPT_LARGE>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (small)
-    batch_cn_chain_kernel<8><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose, steps,
+    batch_cn_chain_kernel<PPT_SMALL><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose, steps,
                                                                E, lanes, first, stride, links, hout);
   else
-    batch_cn_chain_kernel<16><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
+    batch_cn_chain_kernel<PPT_LARGE><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
                                                                 steps, E, lanes, first, stride, links, hout);
   return cudaGetLastError();
 }

@@ -11,8 +11,8 @@
 //    rows 4q and 4q+2: Q_s = P_s P_{s+2}, src = src_P(s) + P_s src_P(s+2).
 //  - bu1_band_chain4_kernel (one cluster): follows a step plan of 4-, 2- and 1-step
 //    entries (a longer step is taken where nothing happens on the rows it skips). Each
-//    point's taps are split over four warps on the four SM sub-partitions, each with
-//    three independent accumulators; 16 boundary values per side are exchanged.
+//    point's taps are split over four warps on the four SM sub-partitions; 16 boundary
+//    values per side are exchanged.
 //  - bu1_band_fill4_kernel (parallel): rows s+3 = M_{s+3}^T row s+4 (+ r) and
 //    s+2 = P_{s+2} row s+4 (+ combined source) inside four-step entries; the two-step
 //    fill then gives row s+1 from row s+2 for two- and four-step entries alike.
@@ -225,16 +225,13 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
     double acc = 0.0;
     if (act) {
       const double* L = Lp + p + o0;
-      double a0 = (qq == 0 && e.z) ? r[9] : 0.0, a1 = 0.0, a2 = 0.0;
+      // one accumulator: the two warps that share an SM sub-partition's FP64 unit hide
+      // each other's dependent-FMA latency, and merges of partial accumulators would
+      // cost FP64 instructions of their own
+      acc = (qq == 0 && e.z) ? r[9] : 0.0;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        if (t < ntap) {
-          if (t % 3 == 0) a0 = fma(r[t], L[t], a0);
-          else if (t % 3 == 1) a1 = fma(r[t], L[t], a1);
-          else a2 = fma(r[t], L[t], a2);
-        }
-      }
-      acc = (a0 + a1) + a2;
+      for (int t = 0; t < 9; ++t)
+        if (t < ntap) acc = fma(r[t], L[t], acc);
     }
     // quarters 1-3 hand their partial sums to quarter 0 (barrier of the group's four warps)
     if (qq > 0 && act) part[(qq - 1) * G * 32 + p] = acc;
