@@ -65,6 +65,8 @@ def lib():
                 "pxo_expm": [_i, _p, _p],
                 "pxo_ad1_krylov_expv": [_i, _d, _d, _d, _d, _i, _p, _p, _p],
                 "pxo_partition_nonequi": [_d, _i, _d, _p],
+                "pxo_leja_points": [_i, _p],
+                "pxo_ad1_relpm_expv": [_i, _d, _d, _d, _d, _d, _i, _p, _p, _p, _p],
                 "pxo_ad2_apply": [_i, _i, _d, _d, _p, _p, _p, _p],
                 "pxo_ad2_apply_T": [_i, _i, _d, _d, _p, _p, _p, _p],
                 "pxo_ad2_rk4_step": [_i, _i, _d, _d, _p, _p, _d, _d, _d, _p, _p, _p],
@@ -148,6 +150,24 @@ def ad1_cn_gradient_paraexp(q0, c, nu, T, K, P, phi_mode, L=TWO_PI):
                                              _ptr(q0), ctypes.byref(J), _ptr(g), _ptr(qT)),
            "cn_paraexp")
     return J.value, g, qT
+
+
+def leja_points(m):
+    out = np.empty(m)
+    _check(lib().pxo_leja_points(m, _ptr(out)), "leja_points")
+    return out
+
+
+def ad1_relpm_expv(v, c, nu, t, tol=1e-13, mmax=120, L=TWO_PI):
+    """exp(t A) v by the real Leja points method; returns (y, degree, substeps). Raises
+    when the Newton series has not converged within mmax terms."""
+    v = _in(v)
+    y = np.empty_like(v)
+    deg = ctypes.c_int()
+    sub = ctypes.c_int()
+    _check(lib().pxo_ad1_relpm_expv(v.size, L, c, nu, t, tol, mmax, _ptr(v), _ptr(y),
+                                     ctypes.byref(deg), ctypes.byref(sub)), "relpm_expv")
+    return y, deg.value, sub.value
 
 
 def ad1_krylov_expv(v, c, nu, t, m, L=TWO_PI):

@@ -639,6 +639,135 @@ int pxo_ad1_krylov_expv(int n, double L, double c, double nu, double t, int m,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Real Leja points method (Sec. 4.1): exp(B) v = v + B phi(B) v with        */
+/* phi(z) = (e^z - 1)/z, and phi(B) v by Newton interpolation of phi at      */
+/* real Leja points of a focal interval [mu - f, mu + f] of the spectrum.    */
+/* ------------------------------------------------------------------------- */
+
+/* Leja points on [-2, 2]: xi_0 = 2; each further point maximises the product of its
+ * distances to the points chosen so far (searched on a uniform grid of 2^16 + 1
+ * points, which is all an interpolation sequence needs). */
+int pxo_leja_points(int m, double* xi) {
+  if (m < 1 || !xi) return -1;
+  const int G = 65537;
+  double* logd = (double*)calloc(G, sizeof(double)); /* sum of log distances per grid point */
+  char* used = (char*)calloc(G, 1);
+  int cur = G - 1; /* the grid point +2 */
+  for (int j = 0; j < m; ++j) {
+    xi[j] = -2.0 + 4.0 * cur / (G - 1);
+    used[cur] = 1;
+    int best = -1;
+    double bv = -INFINITY;
+    for (int g = 0; g < G; ++g) {
+      if (used[g]) continue;
+      double x = -2.0 + 4.0 * g / (G - 1);
+      logd[g] += log(fabs(x - xi[j]));
+      if (logd[g] > bv) {
+        bv = logd[g];
+        best = g;
+      }
+    }
+    cur = best;
+  }
+  free(logd);
+  free(used);
+  return 0;
+}
+
+/* Newton divided differences D_j = phi[z_0, .., z_j] of phi(z) = (e^z - 1)/z at the
+ * nodes z_0..z_m (coincident nodes allowed): by Opitz's theorem they form the first
+ * column of phi(Z), Z lower bidiagonal with the nodes on the diagonal and ones below it,
+ * and phi(Z) e_1 is the last column of exp([[Z, e_1], [0, 0]]). */
+static int relpm_divdiff(int m, const double* z, double* D) {
+  const int d = m + 2;
+  double* A = (double*)calloc((size_t)d * d, sizeof(double));
+  double* E = (double*)malloc(sizeof(double) * (size_t)d * d);
+  for (int i = 0; i <= m; ++i) {
+    A[(size_t)i * d + i] = z[i];
+    if (i > 0) A[(size_t)i * d + (i - 1)] = 1.0;
+  }
+  A[(size_t)0 * d + (m + 1)] = 1.0;
+  int rc = pxo_expm(d, A, E);
+  for (int i = 0; i <= m; ++i) D[i] = E[(size_t)i * d + (m + 1)];
+  free(A);
+  free(E);
+  return rc;
+}
+
+int pxo_ad1_relpm_expv(int n, double L, double c, double nu, double t, double tol, int mmax,
+                       const double* v, double* out, int* degree_out, int* substeps_out) {
+  if (bad_grid(n, L) || mmax < 2 || mmax > 200 || !(tol > 0.0) || !v || !out) return -1;
+  double am, a0, ap;
+  ad1_coeffs(n, L, c, nu, &am, &a0, &ap);
+  /* spectrum of A: the ellipse a0 + (am + ap) cos th + i (ap - am) sin th, th in
+   * [0, 2 pi): centre a0, real semi-axis |am + ap|, imaginary semi-axis |ap - am| */
+  const double alpha = fabs(am + ap), beta = fabs(ap - am);
+  const double mu_t = a0;                                   /* centre (per unit time) */
+  const double f_t = sqrt(fmax(alpha * alpha - beta * beta, 0.0)); /* focal half-length */
+  /* capacity of the smallest confocal ellipse containing the spectrum: (A + B)/2 with
+   * B = beta, A = sqrt(beta^2 + f^2) >= alpha; substeps keep it <= 4 per substep */
+  const double cap = 0.5 * (fmax(alpha, sqrt(beta * beta + f_t * f_t)) + beta);
+  int nsub = (int)ceil(t * cap / 4.0 - 1e-12);
+  if (nsub < 1) nsub = 1;
+  const double ts = t / nsub;
+  double* xi = (double*)malloc(sizeof(double) * (mmax + 1));
+  double* z = (double*)malloc(sizeof(double) * (mmax + 1));
+  double* D = (double*)malloc(sizeof(double) * (mmax + 1));
+  pxo_leja_points(mmax + 1, xi);
+  for (int j = 0; j <= mmax; ++j) z[j] = ts * mu_t + 0.5 * ts * f_t * xi[j];
+  relpm_divdiff(mmax, z, D);
+  double* x = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* p = (double*)malloc(sizeof(double) * n);
+  double* y = (double*)malloc(sizeof(double) * n);
+  memcpy(x, v, sizeof(double) * n);
+  int deg_max = 0, ok = 1;
+  for (int sub = 0; sub < nsub; ++sub) {
+    double vn = 0.0;
+    for (int i = 0; i < n; ++i) vn += x[i] * x[i];
+    vn = sqrt(vn);
+    /* p = sum_j D_j prod_{i<j} (B - z_i I) x,  B = ts A */
+    memcpy(w, x, sizeof(double) * n);
+    for (int i = 0; i < n; ++i) p[i] = D[0] * w[i];
+    double prev = fabs(D[0]) * vn;
+    int j = 1, conv = 0;
+    for (; j <= mmax; ++j) {
+      pxo_ad1_apply(n, L, c, nu, w, y);
+      double wn = 0.0;
+      for (int i = 0; i < n; ++i) {
+        w[i] = ts * y[i] - z[j - 1] * w[i];
+        wn += w[i] * w[i];
+      }
+      wn = sqrt(wn);
+      for (int i = 0; i < n; ++i) p[i] += D[j] * w[i];
+      /* a-posteriori estimate: the last two terms of the Newton series */
+      const double est = fabs(D[j]) * wn;
+      if (est + prev <= tol * vn) {
+        conv = 1;
+        break;
+      }
+      prev = est;
+    }
+    if (!conv) ok = 0;
+    if (j > deg_max) deg_max = j;
+    /* exp(B) x = x + B phi(B) x */
+    pxo_ad1_apply(n, L, c, nu, p, y);
+    for (int i = 0; i < n; ++i) x[i] = x[i] + ts * y[i];
+  }
+  memcpy(out, x, sizeof(double) * n);
+  if (degree_out) *degree_out = deg_max;
+  if (substeps_out) *substeps_out = nsub;
+  free(xi);
+  free(z);
+  free(D);
+  free(x);
+  free(w);
+  free(p);
+  free(y);
+  return ok ? 0 : -2;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Hybrid serial-direct / parallel-adjoint loop for 1D Burgers (Sec. 3.3).   */
 /* ------------------------------------------------------------------------- */
 

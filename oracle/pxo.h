@@ -118,6 +118,17 @@ int pxo_expm(int d, const double* A, double* E);
 int pxo_ad1_krylov_expv(int n, double L, double c, double nu, double t, int m,
                         const double* v, double* out_exp, double* out_phi1);
 
+/* Real Leja points method (Sec. 4.1): m Leja points of [-2, 2] (xi_0 = 2, each next one
+ * maximising the product of distances to the previous ones).                    */
+int pxo_leja_points(int m, double* xi);
+/* exp(t A) v for the 1D advection-diffusion operator by ReLPM: Newton interpolation of
+ * phi(z) = (e^z - 1)/z at Leja points of the focal interval of the spectral ellipse,
+ * exp(B) v = v + B phi(B) v, substeps keeping the ellipse's capacity <= 4, degree up to
+ * mmax until the last two Newton terms fall below tol ||v||. Returns 0, -1 (bad
+ * arguments) or -2 (not converged); *degree_out / *substeps_out (may be NULL).       */
+int pxo_ad1_relpm_expv(int n, double L, double c, double nu, double t, double tol, int mmax,
+                       const double* v, double* out, int* degree_out, int* substeps_out);
+
 /* Non-equidistant partition of Eq. nonEquiP: T_j = T (1 - r^j)/(1 - r^N),
  * r = k/(k+1); out has N+1 entries.                                              */
 int pxo_partition_nonequi(double T, int N, double k, double* out);

@@ -390,3 +390,47 @@ def test_partition_paper_ratio():
     w = np.diff(Tn)
     assert np.allclose(w[1:] / w[:-1], 2.11 / 3.11, rtol=1e-13)
     assert Tn[0] == 0.0 and abs(Tn[-1] - 1.0) < 1e-15
+
+
+# ---- real Leja points method (Sec. 4.1) ----------------------------------------------------
+def test_leja_points_sequence():
+    """Leja points of [-2, 2]: 2, -2, 0 first; every point maximises the product of its
+    distances to the earlier ones over the interval (checked on a fine grid); the points
+    are distinct and, like Chebyshev points, crowd towards the ends (arcsine law)."""
+    xi = O.leja_points(120)
+    assert xi[0] == 2.0 and xi[1] == -2.0 and abs(xi[2]) < 1e-12
+    assert len(set(np.round(xi, 12))) == len(xi) and np.all(np.abs(xi) <= 2.0)
+    grid = np.linspace(-2.0, 2.0, 20001)
+    for j in range(1, 25):
+        prod = lambda x: np.sum(np.log(np.abs(x[:, None] - xi[None, :j]) + 1e-300), axis=1)
+        assert prod(np.array([xi[j]]))[0] >= prod(grid).max() - 1e-3
+    # arcsine law: the fraction of points in |x| > sqrt(2) tends to 1/2
+    frac = np.mean(np.abs(xi) > np.sqrt(2.0))
+    assert 0.4 < frac < 0.6
+
+
+@pytest.mark.parametrize("n,c,nu,t", [(256, 1.0, 0.01, 0.125), (64, 1.0, 0.0, 0.3), (128, 0.0, 0.05, 0.2),
+                                      (200, 2.0, 0.003, 1.0), (31, 1.0, 0.1, 0.5), (512, 1.0, 0.05, 0.25)])
+def test_relpm_matches_the_exact_exponential(n, c, nu, t):
+    """ReLPM (pure advection: degenerate focal interval; pure diffusion; mixed; stiff)
+    against exp(t A) from the closed-form Fourier symbol."""
+    v = I.grf_k2(n, 3)
+    y, deg, sub = O.ad1_relpm_expv(v, c, nu, t, tol=1e-13)
+    ye = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=t)
+    assert np.linalg.norm(y - ye) / np.linalg.norm(ye) < 1e-12
+    assert 2 <= deg <= 120 and sub >= 1
+
+
+def test_relpm_error_follows_its_tolerance():
+    v = I.grf_k2(256, 4)
+    ye = O.ad1_phi_dft(v, 1.0, 0.01, O.PHI_EXP, t=0.125)
+    errs = []
+    for tol in (1e-4, 1e-8, 1e-12):
+        y, deg, _ = O.ad1_relpm_expv(v, 1.0, 0.01, 0.125, tol=tol)
+        errs.append((np.linalg.norm(y - ye) / np.linalg.norm(v), deg))
+    assert errs[0][0] > errs[1][0] > errs[2][0]
+    assert errs[0][1] < errs[1][1] < errs[2][1]
+    for (e, _), tol in zip(errs, (1e-4, 1e-8, 1e-12)):
+        assert e < 10 * tol
+    with pytest.raises(ValueError):  # the Newton series cannot converge in 4 terms
+        O.ad1_relpm_expv(v, 1.0, 0.01, 0.125, tol=1e-14, mmax=4)
