@@ -79,6 +79,11 @@ typedef enum { PXA_CN = 1, PXA_RK4 = 2 } pxa_stepper;
  * own amplification R(dt A)^k (R_CN(z) = (1+z/2)/(1-z/2)), which makes Paraexp
  * reproduce serial stepping up to the Krylov tolerance. */
 typedef enum { PXA_PHI_EXP = 0, PXA_PHI_STEPPER = 1 } pxa_phi;
+/* How the homogeneous propagations of ADVDIFF_1D are computed: Arnoldi/Krylov (default)
+ * or the real Leja points method (Sec. 4.1: Newton interpolation of phi(z) = (e^z - 1)/z
+ * at Leja points of the focal interval of the spectrum; exp(B) v = v + B phi(B) v; three
+ * vectors of workspace instead of a Krylov basis; PXA_PHI_EXP only). */
+typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1 } pxa_propagator;
 /* SERIAL: one lane over [0, T] (plain serial stepping, same kernels).
  * PARAEXP: P lanes + homogeneous propagation + superposition. */
 typedef enum { PXA_SERIAL = 0, PXA_PARAEXP = 1 } pxa_mode;
@@ -161,6 +166,12 @@ int pxa_set_time(pxa_ctx* ctx, double T, int64_t K, int stepper, int P);
  * substeps per subinterval (>= 1; each substep spans K/(P*substeps) steps, which
  * must be an integer). */
 int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
+/* ADVDIFF_1D homogeneous propagator (pxa_propagator). With PXA_PROP_RELPM the Newton
+ * series runs up to max_degree (2..200) terms per substep until its last two terms fall
+ * below the tolerance of pxa_set_krylov times ||v|| (else PXA_ERR_NOT_CONVERGED); the
+ * substeps keep the capacity of the spectral ellipse <= 4 each (automatic). Invalidates
+ * the workspace. */
+int pxa_set_propagator(pxa_ctx* ctx, int method, int max_degree);
 /* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
 int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);
 /* Control (Eq. initupdate / paramupdate): ADVDIFF_1D: q0_dev = initial condition.

@@ -8,6 +8,8 @@
 //   ad1_chain_kernel         Eq. hom / Eq. adjHomNormal: Krylov exponential (or CN
 //                            stepper power) of the summed homogeneous problems,
 //                            carried subinterval by subinterval.
+//   ad1_relpm_chain_kernel   the same chain with the real Leja points method (Sec. 4.1):
+//                            Newton interpolation of phi(z) = (e^z - 1)/z.
 //   ad1_superpose_*          Eq. fullsol0 and Eq. fulladjsol at the end points,
 //                            J, the adjoint terminal value (Eq. adjFinalTime) and the
 //                            initial-condition gradient (Eq. initupdate).
@@ -131,6 +133,119 @@ __global__ void ad1_chain_kernel(int n, double am, double a0, double ap, int tra
                      tol, status, errmax);
   }
   for (int p = threadIdx.x; p < n; p += blockDim.x) hout[p] = hvec[p];
+}
+
+// Real Leja points method (Sec. 4.1): h <- exp(ts A)^nsub h, each substep as
+// h + ts A p with p = phi(ts A) h, phi(z) = (e^z - 1)/z, interpolated in Newton form at
+// the nodes z_j (Leja points of the spectrum's focal interval, scaled by ts):
+//   w_0 = h, w_j = (ts A - z_{j-1}) w_{j-1}, p = sum_j D_j w_j,
+// stopping when the last two terms fall below tol ||h||. Vectors w, p, t in shared
+// memory (n each); D, z: the divided differences and nodes (mmax + 1 each).
+template <class Op>
+__device__ void relpm_propagate(Op& op, double* h, double* w, double* p, double* t, int n,
+                                const double* D, const double* z, int mmax, double ts, int nsub,
+                                double tol, double* red, int* status, double* errmax) {
+  for (int sub = 0; sub < nsub; ++sub) {
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = h[i];
+      w[i] = v;
+      p[i] = D[0] * v;
+      ss = fma(v, v, ss);
+    }
+    const double hn = sqrt(block_sum(ss, red));
+    if (hn == 0.0) continue;  // h stays zero
+    double prev = fabs(D[0]) * hn, est = 0.0;
+    bool conv = false;
+    for (int j = 1; j <= mmax; ++j) {
+      op.apply(w, t);  // t = A w (ends with a barrier)
+      double s2 = 0.0;
+      const double zj = z[j - 1], dj = D[j];
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = fma(ts, t[i], -zj * w[i]);
+        w[i] = v;
+        p[i] = fma(dj, v, p[i]);
+        s2 = fma(v, v, s2);
+      }
+      est = fabs(dj) * sqrt(block_sum(s2, red));  // (the block sum ends with a barrier)
+      if (est + prev <= tol * hn) {
+        conv = true;
+        break;
+      }
+      prev = est;
+    }
+    if (threadIdx.x == 0) {
+      atomic_max_pos(errmax, (est + prev) / hn);
+      if (!conv) set_status(status, PXA_ERR_NOT_CONVERGED);
+    }
+    op.apply(p, t);  // h <- h + ts A p
+    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = fma(ts, t[i], h[i]);
+    __syncthreads();
+  }
+}
+
+// Shared layout of the ReLPM kernels: h, w, p, t [n], D, z [mmax + 1], red [40].
+__device__ __forceinline__ void relpm_carve(double* sm, int n, int mmax, const double* Dg, const double* zg,
+                                            double*& h, double*& w, double*& p, double*& t, double*& D,
+                                            double*& z, double*& red) {
+  h = sm;
+  w = h + n;
+  p = w + n;
+  t = p + n;
+  D = t + n;
+  z = D + mmax + 1;
+  red = z + mmax + 1;
+  for (int j = threadIdx.x; j <= mmax; j += blockDim.x) {
+    D[j] = Dg[j];
+    z[j] = zg[j];
+  }
+}
+
+// The chain of Eq. hom / Eq. adjHomNormal with ReLPM exponentials (as ad1_chain_kernel):
+//   h = 0; for i in 0..count-1: h += E[first + i*stride]; h = exp(tau A) h.
+__global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, int transpose,
+                                       const double* __restrict__ E, int first, int stride, int count,
+                                       double* __restrict__ hout, const double* __restrict__ Dg,
+                                       const double* __restrict__ zg, int mmax, double ts, int nsub,
+                                       double tol, int* status, double* errmax) {
+  extern __shared__ double sm[];
+  double *h, *w, *p, *t, *D, *z, *red;
+  relpm_carve(sm, n, mmax, Dg, zg, h, w, p, t, D, z, red);
+  if (transpose) {
+    const double x = am;
+    am = ap;
+    ap = x;
+  }
+  Ad1Op op{n, am, a0, ap};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0.0;
+  __syncthreads();
+  for (int l = 0; l < count; ++l) {
+    const double* e = E + (size_t)(first + l * stride) * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] += e[i];
+    __syncthreads();
+    relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, tol, red, status, errmax);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) hout[i] = h[i];
+}
+
+// One vector: y = exp(ts A)^nsub x (building block).
+__global__ void ad1_relpm_expv_kernel(int n, double am, double a0, double ap, int transpose,
+                                      const double* __restrict__ x, double* __restrict__ y,
+                                      const double* __restrict__ Dg, const double* __restrict__ zg, int mmax,
+                                      double ts, int nsub, double tol, int* status, double* errmax) {
+  extern __shared__ double sm[];
+  double *h, *w, *p, *t, *D, *z, *red;
+  relpm_carve(sm, n, mmax, Dg, zg, h, w, p, t, D, z, red);
+  if (transpose) {
+    const double s = am;
+    am = ap;
+    ap = s;
+  }
+  Ad1Op op{n, am, a0, ap};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = x[i];
+  __syncthreads();
+  relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, tol, red, status, errmax);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = h[i];
 }
 
 // Direct superposition at t = T (Eq. fullsol0): qT = q0 + e_{P-1} + hsum;
@@ -486,6 +601,31 @@ cudaError_t launch_ad1_chain(cudaStream_t st, int threads, int n, double am, dou
   ad1_chain_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, E, first, stride, count,
                                             hout, Vglob, m, phi_mode, hscale, steps_per_sub, nsub,
                                             tol, v_in_smem, status, errmax);
+  return cudaGetLastError();
+}
+
+static size_t relpm_smem(int n, int mmax) { return sizeof(double) * (4 * (size_t)n + 2 * (size_t)(mmax + 1) + 40); }
+
+cudaError_t launch_ad1_relpm_chain(cudaStream_t st, int threads, int n, double am, double a0, double ap,
+                                   int transpose, const double* E, int first, int stride, int count,
+                                   double* hout, const double* D, const double* z, int mmax, double ts,
+                                   int nsub, double tol, int* status, double* errmax) {
+  const size_t sh = relpm_smem(n, mmax);
+  cudaError_t e = cudaFuncSetAttribute(ad1_relpm_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  ad1_relpm_chain_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, E, first, stride, count, hout, D, z,
+                                                  mmax, ts, nsub, tol, status, errmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad1_relpm_expv(cudaStream_t st, int threads, int n, double am, double a0, double ap,
+                                  int transpose, const double* x, double* y, const double* D, const double* z,
+                                  int mmax, double ts, int nsub, double tol, int* status, double* errmax) {
+  const size_t sh = relpm_smem(n, mmax);
+  cudaError_t e = cudaFuncSetAttribute(ad1_relpm_expv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  ad1_relpm_expv_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, x, y, D, z, mmax, ts, nsub, tol,
+                                                 status, errmax);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // orchestration of the Paraexp direct-adjoint loop on one stream, CUDA-graph replay.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -67,6 +68,104 @@ void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector
   for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
 }
 
+
+// Real Leja points method (Sec. 4.1), host part. Leja points of [-2, 2]: 2 first, then
+// each point maximises the sum of log distances to the earlier ones, searched on a
+// uniform grid of 2^15 + 1 points.
+static void leja_host(int m1, std::vector<double>& xi) {
+  const int G = 32769;
+  std::vector<double> acc(G, 0.0);
+  std::vector<char> taken(G, 0);
+  xi.assign(m1, 0.0);
+  int g = G - 1;
+  for (int j = 0; j < m1; ++j) {
+    const double x = -2.0 + 4.0 * g / (G - 1);
+    xi[j] = x;
+    taken[g] = 1;
+    int best = 0;
+    double bv = -1e300;
+    for (int q = 0; q < G; ++q) {
+      if (taken[q]) continue;
+      acc[q] += std::log(std::fabs(-2.0 + 4.0 * q / (G - 1) - x));
+      if (acc[q] > bv) {
+        bv = acc[q];
+        best = q;
+      }
+    }
+    g = best;
+  }
+}
+
+// exp of a d x d row-major matrix in double: Taylor polynomial of degree 18 at norm <= 1/2
+// (remainder below 1e-23), then repeated squaring.
+static void expm_host(int d, std::vector<double> A, std::vector<double>& E) {
+  double nrm = 0.0;
+  for (int i = 0; i < d; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < d; ++j) r += std::fabs(A[(size_t)i * d + j]);
+    nrm = std::max(nrm, r);
+  }
+  int sq = 0;
+  while (nrm > 0.5) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double sc = std::ldexp(1.0, -sq);
+  for (double& v : A) v *= sc;
+  std::vector<double> term((size_t)d * d, 0.0), next((size_t)d * d);
+  E.assign((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i) term[(size_t)i * d + i] = E[(size_t)i * d + i] = 1.0;
+  for (int k = 1; k <= 18; ++k) {
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < d; ++l) s += term[(size_t)i * d + l] * A[(size_t)l * d + j];
+        next[(size_t)i * d + j] = s / k;
+      }
+    term.swap(next);
+    for (size_t e = 0; e < E.size(); ++e) E[e] += term[e];
+  }
+  for (int r = 0; r < sq; ++r) {
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < d; ++l) s += E[(size_t)i * d + l] * E[(size_t)l * d + j];
+        next[(size_t)i * d + j] = s;
+      }
+    E.swap(next);
+  }
+}
+
+// Substeps, nodes and Newton divided differences of phi(z) = (e^z - 1)/z for exp(t A).
+// The spectrum of A is the ellipse a0 + (am + ap) cos th + i (ap - am) sin th: centre
+// a0, semi-axes |am + ap| (real) and |ap - am| (imaginary). Its confocal family with real
+// foci a0 +- f, f^2 = max(|am+ap|^2 - |ap-am|^2, 0), gives the focal interval; substeps
+// keep the capacity of the smallest such ellipse containing the spectrum <= 4 per
+// substep. Divided differences by Opitz's theorem: the first column of phi(Z), Z lower
+// bidiagonal (nodes on the diagonal, ones below), read off exp([[Z, e_1], [0, 0]]).
+void relpm_setup_host(double t, double am, double a0, double ap, int mmax, int& nsub, double& ts,
+                      std::vector<double>& z, std::vector<double>& D) {
+  const double ra = std::fabs(am + ap), ib = std::fabs(ap - am);
+  const double f = std::sqrt(std::max(ra * ra - ib * ib, 0.0));
+  const double cap = 0.5 * (std::max(ra, std::sqrt(ib * ib + f * f)) + ib);
+  nsub = std::max(1, (int)std::ceil(std::fabs(t) * cap / 4.0 - 1e-12));
+  ts = t / nsub;
+  std::vector<double> xi;
+  leja_host(mmax + 1, xi);
+  z.resize(mmax + 1);
+  for (int j = 0; j <= mmax; ++j) z[j] = ts * a0 + 0.5 * ts * f * xi[j];
+  const int d = mmax + 2;
+  std::vector<double> M((size_t)d * d, 0.0), E;
+  for (int i = 0; i <= mmax; ++i) {
+    M[(size_t)i * d + i] = z[i];
+    if (i > 0) M[(size_t)i * d + i - 1] = 1.0;
+  }
+  M[(size_t)mmax + 1] = 1.0;  // row 0, column mmax + 1
+  expm_host(d, M, E);
+  D.resize(mmax + 1);
+  for (int i = 0; i <= mmax; ++i) D[i] = E[(size_t)i * d + mmax + 1];
+}
+
 }  // namespace pxa
 
 struct pxa_ctx {
@@ -82,6 +181,12 @@ struct pxa_ctx {
   int64_t K = 0;
   int stepper = 0, P = 1;
   int kry_m = 30, kry_phi = PXA_PHI_STEPPER, kry_sub = 1;
+  int prop = PXA_PROP_KRYLOV;  // homogeneous propagator method (ADVDIFF_1D)
+  int relpm_mmax = 120;
+  double* relpm_D = nullptr;   // Newton divided differences and nodes of the chain's substeps
+  double* relpm_z = nullptr;
+  int relpm_nsub = 1;
+  double relpm_ts = 0.0;
   double kry_tol = 1e-11;
   int magnus_M = 25;
   const double* control = nullptr;
@@ -223,6 +328,7 @@ void release_workspace(pxa_ctx* c) {
   c->ws_bytes = 0;
   c->ready = false;
   c->taps = c->E = c->EA = c->src = c->srcA = c->hsum = c->hsumA = c->qT = c->tmp = nullptr;
+  c->relpm_D = c->relpm_z = nullptr;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
   c->status = nullptr;
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
@@ -358,6 +464,15 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
     PXA_CUDA(c, cudaMemcpy(c->taps, c->band_host.data(), sizeof(double) * c->band_host.size(),
                            cudaMemcpyHostToDevice), "copy taps");
+    if (c->prop == PXA_PROP_RELPM) {
+      // the chain's exponential over one subinterval tau = T / P
+      std::vector<double> z, D;
+      relpm_setup_host(c->T / P, c->am, c->a0, c->ap, c->relpm_mmax, c->relpm_nsub, c->relpm_ts, z, D);
+      if ((rc = alloc(c, &c->relpm_D, D.size()))) return rc;
+      if ((rc = alloc(c, &c->relpm_z, z.size()))) return rc;
+      PXA_CUDA(c, cudaMemcpy(c->relpm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice), "copy");
+      PXA_CUDA(c, cudaMemcpy(c->relpm_z, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice), "copy");
+    }
   } else {
     int64_t k = c->K / P;
     if (c->memory == PXA_STORE_FULL) {
@@ -517,6 +632,9 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   const int64_t steps_sub = k / nsub;
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)steps_sub : dt;
   const int kth = 256;
+  const bool relpm = c->prop == PXA_PROP_RELPM;
+  if (relpm && c->kry_phi != PXA_PHI_EXP)
+    return fail(c, PXA_ERR_INVALID, "the real Leja points method propagates exp(tA): set PXA_PHI_EXP");
   if (do_d) {
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
   ev_record(c, 0);
@@ -525,7 +643,11 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   PXA_CUDA(c, launch_band_minus_identity(st, n, r, c->taps, 0, q0, c->src), "src");
   PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 0, k, nullptr, c->src, c->E), "lanes");
   ev_record(c, 1);
-  if (P > 1) {
+  if (P > 1 && relpm) {
+    PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
+                                       c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
+                                       c->kry_tol, c->status, c->errmax), "chain");
+  } else if (P > 1) {
     PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
                                  c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub, c->kry_tol,
                                  c->v_in_smem, c->status, c->errmax), "chain");
@@ -538,7 +660,11 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (!do_a) return PXA_OK;
   PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 1, k, nullptr, c->srcA, c->EA), "adj lanes");
   ev_record(c, 3);
-  if (P > 1) {
+  if (P > 1 && relpm) {
+    PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1, c->hsumA,
+                                       c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
+                                       c->kry_tol, c->status, c->errmax), "adj chain");
+  } else if (P > 1) {
     PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1,
                                  c->hsumA, c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub,
                                  c->kry_tol, c->v_in_smem, c->status, c->errmax), "adj chain");
@@ -1056,6 +1182,16 @@ int pxa_partition_bounds(int64_t K, int P, double r, int max_chunks, int64_t* bo
   return bu1_chunk_bounds(K, P, r, max_chunks, bounds);
 }
 
+int pxa_set_propagator(pxa_ctx* c, int method, int max_degree) {
+  if (!c || (method != PXA_PROP_KRYLOV && method != PXA_PROP_RELPM) || max_degree < 2 || max_degree > 200)
+    return PXA_ERR_INVALID;
+  c->prop = method;
+  c->relpm_mmax = max_degree;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
 int pxa_set_partition(pxa_ctx* c, double r) {
   if (!c) return PXA_ERR_INVALID;
   if (!(r >= 0.0 && r < 1.0)) return fail(c, PXA_ERR_INVALID, "partition ratio must be 0 (equal) or in (0, 1)");
@@ -1490,9 +1626,30 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   const int64_t sps = span_steps / substeps;
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)sps : dt;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), c->stream), "reset errmax");
-  PXA_CUDA(c, launch_ad1_expv(c->stream, 256, n, c->am, c->a0, c->ap, transpose, x_dev, y_dev, c->V,
-                              c->kry_m, c->kry_phi, hscale, sps, substeps, c->kry_tol, c->v_in_smem,
-                              c->status, c->errmax), "expv");
+  if (c->prop == PXA_PROP_RELPM) {
+    if (c->kry_phi != PXA_PHI_EXP)
+      return fail(c, PXA_ERR_INVALID, "the real Leja points method propagates exp(tA): set PXA_PHI_EXP");
+    // ReLPM picks its own substeps for the whole span
+    std::vector<double> z, D;
+    int ns = 1;
+    double ts = 0.0;
+    relpm_setup_host(dt * (double)span_steps, c->am, c->a0, c->ap, c->relpm_mmax, ns, ts, z, D);
+    double *Dd = nullptr, *zd = nullptr;
+    PXA_CUDA(c, cudaMalloc(&Dd, sizeof(double) * D.size()), "alloc");
+    PXA_CUDA(c, cudaMalloc(&zd, sizeof(double) * z.size()), "alloc");
+    cudaMemcpy(Dd, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(zd, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = launch_ad1_relpm_expv(c->stream, 256, n, c->am, c->a0, c->ap, transpose, x_dev, y_dev, Dd, zd,
+                                          c->relpm_mmax, ts, ns, c->kry_tol, c->status, c->errmax);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(Dd);
+    cudaFree(zd);
+    PXA_CUDA(c, e, "relpm expv");
+  } else {
+    PXA_CUDA(c, launch_ad1_expv(c->stream, 256, n, c->am, c->a0, c->ap, transpose, x_dev, y_dev, c->V,
+                                c->kry_m, c->kry_phi, hscale, sps, substeps, c->kry_tol, c->v_in_smem,
+                                c->status, c->errmax), "expv");
+  }
   PXA_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
   rc = read_status(c);
   if (err_host) *err_host = c->stats.krylov_err_max;

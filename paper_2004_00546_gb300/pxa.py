@@ -20,6 +20,7 @@ EXPV_STATIC_MAX_DOUBLES = 131072
 ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D = 1, 2, 3
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
+PROP_KRYLOV, PROP_RELPM = 0, 1
 SERIAL, PARAEXP = 0, 1
 STORE_FULL, STORE_CHECKPOINTS = 0, 1
 ADJ_BANDED, ADJ_RESTEP, ADJ_BANDED_SINGLE, ADJ_BANDED_PAIR = 0, 1, 2, 3
@@ -30,7 +31,7 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_partition_bounds", "pxa_set_groups",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
         "pxa_set_adjoint": [p, i],
         "pxa_set_overlap": [p, i],
         "pxa_set_partition": [p, d],
+        "pxa_set_propagator": [p, i, i],
         "pxa_partition_bounds": [i64, i, d, i, ctypes.POINTER(i64)],
         "pxa_set_groups": [p, i, i],
         "pxa_set_graph": [p, i],
@@ -241,6 +243,9 @@ class Context:
 
     def set_overlap(self, enable):
         self._check(self._L.pxa_set_overlap(self._h, 1 if enable else 0))
+
+    def set_propagator(self, method, max_degree=120):
+        self._check(self._L.pxa_set_propagator(self._h, method, max_degree))
 
     def set_partition(self, r):
         self._check(self._L.pxa_set_partition(self._h, float(r)))

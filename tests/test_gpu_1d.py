@@ -569,3 +569,61 @@ def test_burgers_four_step_chain(X, torch, n, C, K, P):
         ctx.close()
     for mode in (X.SERIAL, X.PARAEXP):
         assert rel(res[(X.ADJ_BANDED, mode)], res[(X.ADJ_BANDED_PAIR, mode)]) < 1e-12
+
+
+# ---- real Leja points method (Sec. 4.1) ----------------------------------------------------
+@pytest.mark.parametrize("n,c,nu,span", [(256, 1.0, 0.01, 512), (64, 1.0, 0.0, 1200), (128, 0.0, 0.05, 800),
+                                         (1000, 1.0, 0.002, 4096), (37, 2.0, 0.1, 300)])
+def test_relpm_expv_matches_exact_exponential(X, torch, n, c, nu, span):
+    """exp(t A) v and exp(t A^T) v by the real Leja points method (pure advection:
+    degenerate focal interval; pure diffusion; mixed; stiff) against the closed-form
+    Fourier exponential."""
+    T, K = 1.0, 4096
+    ctx = ad1_ctx(X, n, c, nu, T, K, 8, m=30, tol=1e-13, phi=X.PHI_EXP)
+    ctx.set_propagator(X.PROP_RELPM, 150)
+    v = I.grf_k2(n, 9)
+    xd = dev(torch, v)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        err = ctx.expv(xd, y, span, transpose=tr)
+        ref = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=span * T / K, transpose=tr)
+        assert rel(host(y), ref) < 1e-12
+        assert err < 1e-12
+
+
+def test_relpm_not_converged_is_reported(X, torch):
+    n = 256
+    ctx = ad1_ctx(X, n, 1.0, 0.01, 1.0, 4096, 1, m=30, tol=1e-14, phi=X.PHI_EXP)
+    ctx.set_propagator(X.PROP_RELPM, 4)
+    xd = dev(torch, I.grf_k2(n, 1))
+    y = torch.empty_like(xd)
+    with pytest.raises(X.PxaError) as ei:
+        ctx.expv(xd, y, 4096)
+    assert ei.value.code == X.ERR_NOT_CONVERGED
+    ctx.set_propagator(X.PROP_KRYLOV, 120)
+    ctx.set_krylov(30, 1e-10, X.PHI_EXP, 1)
+    ctx.expv(xd, y, 64)  # the same context keeps working
+
+
+@pytest.mark.parametrize("n,nu,K,P", [(256, 0.01, 4096, 8), (100, 0.0, 512, 4), (333, 0.05, 1024, 16)])
+def test_relpm_paraexp_gradient_matches_oracle(X, torch, n, nu, K, P):
+    """The Paraexp loop with ReLPM homogeneous exponentials (Eq. hom, Eq. adjHomNormal)
+    equals the oracle's Paraexp with the exact exponential, and the Krylov path."""
+    c, T = 1.0, 1.0
+    q0 = I.grf_k2(n, 21)
+    Jo, go, _ = O.ad1_cn_gradient_paraexp(q0, c, nu, T, K, P, O.PHI_EXP)
+    qd = dev(torch, q0)
+    res = {}
+    for prop in (X.PROP_RELPM, X.PROP_KRYLOV):
+        ctx = ad1_ctx(X, n, c, nu, T, K, P, m=40, tol=1e-12, phi=X.PHI_EXP)
+        ctx.set_propagator(prop, 150)
+        if prop == X.PROP_KRYLOV:
+            ctx.set_krylov(40, 1e-12, X.PHI_EXP, 4)
+        ctx.set_control(qd)
+        out = torch.empty_like(qd)
+        J = ctx.gradient(X.PARAEXP, out)
+        assert abs(J - Jo) / Jo < 1e-10
+        assert rel(host(out), go) < 1e-10
+        res[prop] = host(out)
+        ctx.close()
+    assert rel(res[X.PROP_RELPM], res[X.PROP_KRYLOV]) < 1e-10
