@@ -139,12 +139,13 @@ __global__ void ad1_chain_kernel(int n, double am, double a0, double ap, int tra
 // h + ts A p with p = phi(ts A) h, phi(z) = (e^z - 1)/z, interpolated in Newton form at
 // the nodes z_j (Leja points of the spectrum's focal interval, scaled by ts):
 //   w_0 = h, w_j = (ts A - z_{j-1}) w_{j-1}, p = sum_j D_j w_j,
-// stopping when the last two terms fall below tol ||h||. Vectors w, p, t in shared
+// stopping when the last two terms fall below tol ||h||. With `direct` the interpolated
+// function is the substep's propagator itself (the CN power) and h <- p. Vectors w, p, t in shared
 // memory (n each); D, z: the divided differences and nodes (mmax + 1 each).
 template <class Op>
 __device__ void relpm_propagate(Op& op, double* h, double* w, double* p, double* t, int n,
                                 const double* D, const double* z, int mmax, double ts, int nsub,
-                                double tol, double* red, int* status, double* errmax) {
+                                int direct, double tol, double* red, int* status, double* errmax) {
   for (int sub = 0; sub < nsub; ++sub) {
     double ss = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -178,8 +179,12 @@ __device__ void relpm_propagate(Op& op, double* h, double* w, double* p, double*
       atomic_max_pos(errmax, (est + prev) / hn);
       if (!conv) set_status(status, PXA_ERR_NOT_CONVERGED);
     }
-    op.apply(p, t);  // h <- h + ts A p
-    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = fma(ts, t[i], h[i]);
+    if (direct) {  // the interpolated function is the propagator itself: h <- p
+      for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = p[i];
+    } else {  // phi: h <- h + ts A p
+      op.apply(p, t);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = fma(ts, t[i], h[i]);
+    }
     __syncthreads();
   }
 }
@@ -207,7 +212,7 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
                                        const double* __restrict__ E, int first, int stride, int count,
                                        double* __restrict__ hout, const double* __restrict__ Dg,
                                        const double* __restrict__ zg, int mmax, double ts, int nsub,
-                                       double tol, int* status, double* errmax) {
+                                       int direct, double tol, int* status, double* errmax) {
   extern __shared__ double sm[];
   double *h, *w, *p, *t, *D, *z, *red;
   relpm_carve(sm, n, mmax, Dg, zg, h, w, p, t, D, z, red);
@@ -223,7 +228,7 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
     const double* e = E + (size_t)(first + l * stride) * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] += e[i];
     __syncthreads();
-    relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, tol, red, status, errmax);
+    relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, direct, tol, red, status, errmax);
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) hout[i] = h[i];
 }
@@ -232,7 +237,8 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
 __global__ void ad1_relpm_expv_kernel(int n, double am, double a0, double ap, int transpose,
                                       const double* __restrict__ x, double* __restrict__ y,
                                       const double* __restrict__ Dg, const double* __restrict__ zg, int mmax,
-                                      double ts, int nsub, double tol, int* status, double* errmax) {
+                                      double ts, int nsub, int direct, double tol, int* status,
+                                      double* errmax) {
   extern __shared__ double sm[];
   double *h, *w, *p, *t, *D, *z, *red;
   relpm_carve(sm, n, mmax, Dg, zg, h, w, p, t, D, z, red);
@@ -244,7 +250,7 @@ __global__ void ad1_relpm_expv_kernel(int n, double am, double a0, double ap, in
   Ad1Op op{n, am, a0, ap};
   for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = x[i];
   __syncthreads();
-  relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, tol, red, status, errmax);
+  relpm_propagate(op, h, w, p, t, n, D, z, mmax, ts, nsub, direct, tol, red, status, errmax);
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = h[i];
 }
 
@@ -609,23 +615,24 @@ static size_t relpm_smem(int n, int mmax) { return sizeof(double) * (4 * (size_t
 cudaError_t launch_ad1_relpm_chain(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                                    int transpose, const double* E, int first, int stride, int count,
                                    double* hout, const double* D, const double* z, int mmax, double ts,
-                                   int nsub, double tol, int* status, double* errmax) {
+                                   int nsub, int direct, double tol, int* status, double* errmax) {
   const size_t sh = relpm_smem(n, mmax);
   cudaError_t e = cudaFuncSetAttribute(ad1_relpm_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   ad1_relpm_chain_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, E, first, stride, count, hout, D, z,
-                                                  mmax, ts, nsub, tol, status, errmax);
+                                                  mmax, ts, nsub, direct, tol, status, errmax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ad1_relpm_expv(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                                   int transpose, const double* x, double* y, const double* D, const double* z,
-                                  int mmax, double ts, int nsub, double tol, int* status, double* errmax) {
+                                  int mmax, double ts, int nsub, int direct, double tol, int* status,
+                                  double* errmax) {
   const size_t sh = relpm_smem(n, mmax);
   cudaError_t e = cudaFuncSetAttribute(ad1_relpm_expv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  ad1_relpm_expv_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, x, y, D, z, mmax, ts, nsub, tol,
-                                                 status, errmax);
+  ad1_relpm_expv_kernel<<<1, threads, sh, st>>>(n, am, a0, ap, transpose, x, y, D, z, mmax, ts, nsub, direct,
+                                                 tol, status, errmax);
   return cudaGetLastError();
 }
 

@@ -31,14 +31,16 @@ cudaError_t launch_ad1_chain(cudaStream_t st, int threads, int n, double am, dou
 cudaError_t launch_ad1_relpm_chain(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                                    int transpose, const double* E, int first, int stride, int count,
                                    double* hout, const double* D, const double* z, int mmax, double ts,
-                                   int nsub, double tol, int* status, double* errmax);
+                                   int nsub, int direct, double tol, int* status, double* errmax);
 cudaError_t launch_ad1_relpm_expv(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                                   int transpose, const double* x, double* y, const double* D, const double* z,
-                                  int mmax, double ts, int nsub, double tol, int* status, double* errmax);
-// Host: the real Leja points method for exp(t A) of the stencil (am, a0, ap): substeps,
-// their length and the Newton nodes and divided differences (mmax + 1 each).
+                                  int mmax, double ts, int nsub, int direct, double tol, int* status,
+                                  double* errmax);
+// Host: the real Leja points method for the propagator over a span t of the stencil
+// (am, a0, ap): exp(t A) (steps == 0) or the CN power R(dt A)^steps; substeps, their
+// length and the Newton nodes and divided differences (mmax + 1 each).
 void relpm_setup_host(double t, double am, double a0, double ap, int mmax, int& nsub, double& ts,
-                      std::vector<double>& z, std::vector<double>& D);
+                      std::vector<double>& z, std::vector<double>& D, int64_t steps);
 cudaError_t launch_ad1_expv(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                             int transpose, const double* x, double* y, double* Vglob, int m,
                             int phi_mode, double hscale, int64_t steps_per_sub, int nsub,

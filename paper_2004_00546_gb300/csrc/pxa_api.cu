@@ -136,34 +136,76 @@ static void expm_host(int d, std::vector<double> A, std::vector<double>& E) {
   }
 }
 
-// Substeps, nodes and Newton divided differences of phi(z) = (e^z - 1)/z for exp(t A).
+// Substeps, nodes and Newton divided differences for the homogeneous propagator over a
+// span t. steps == 0: exp(t A), interpolating phi(z) = (e^z - 1)/z (exp(B) = I + B phi(B));
+// steps > 0: the Crank-Nicolson power R(dt A)^steps with dt = t / steps, interpolated
+// directly as f(z) = R(z/m)^m on each substep of m steps (R(x) = (1 + x/2)/(1 - x/2)).
 // The spectrum of A is the ellipse a0 + (am + ap) cos th + i (ap - am) sin th: centre
 // a0, semi-axes |am + ap| (real) and |ap - am| (imaginary). Its confocal family with real
 // foci a0 +- f, f^2 = max(|am+ap|^2 - |ap-am|^2, 0), gives the focal interval; substeps
 // keep the capacity of the smallest such ellipse containing the spectrum <= 4 per
-// substep. Divided differences by Opitz's theorem: the first column of phi(Z), Z lower
-// bidiagonal (nodes on the diagonal, ones below), read off exp([[Z, e_1], [0, 0]]).
+// substep (for the CN power, the smallest divisor of `steps` that does). Divided
+// differences by Opitz's theorem: the first column of f(Z), Z lower bidiagonal (nodes on
+// the diagonal, ones below); for phi read off exp([[Z, e_1], [0, 0]]).
 void relpm_setup_host(double t, double am, double a0, double ap, int mmax, int& nsub, double& ts,
-                      std::vector<double>& z, std::vector<double>& D) {
+                      std::vector<double>& z, std::vector<double>& D, int64_t steps) {
   const double ra = std::fabs(am + ap), ib = std::fabs(ap - am);
   const double f = std::sqrt(std::max(ra * ra - ib * ib, 0.0));
   const double cap = 0.5 * (std::max(ra, std::sqrt(ib * ib + f * f)) + ib);
   nsub = std::max(1, (int)std::ceil(std::fabs(t) * cap / 4.0 - 1e-12));
+  if (steps > 0) {
+    while (nsub < steps && steps % nsub != 0) ++nsub;
+    if (nsub > steps) nsub = (int)steps;
+  }
   ts = t / nsub;
   std::vector<double> xi;
   leja_host(mmax + 1, xi);
   z.resize(mmax + 1);
   for (int j = 0; j <= mmax; ++j) z[j] = ts * a0 + 0.5 * ts * f * xi[j];
-  const int d = mmax + 2;
-  std::vector<double> M((size_t)d * d, 0.0), E;
-  for (int i = 0; i <= mmax; ++i) {
-    M[(size_t)i * d + i] = z[i];
-    if (i > 0) M[(size_t)i * d + i - 1] = 1.0;
-  }
-  M[(size_t)mmax + 1] = 1.0;  // row 0, column mmax + 1
-  expm_host(d, M, E);
   D.resize(mmax + 1);
-  for (int i = 0; i <= mmax; ++i) D[i] = E[(size_t)i * d + mmax + 1];
+  if (steps == 0) {
+    const int d = mmax + 2;
+    std::vector<double> M((size_t)d * d, 0.0), E;
+    for (int i = 0; i <= mmax; ++i) {
+      M[(size_t)i * d + i] = z[i];
+      if (i > 0) M[(size_t)i * d + i - 1] = 1.0;
+    }
+    M[(size_t)mmax + 1] = 1.0;  // row 0, column mmax + 1
+    expm_host(d, M, E);
+    for (int i = 0; i <= mmax; ++i) D[i] = E[(size_t)i * d + mmax + 1];
+    return;
+  }
+  // R(Z/m) = (I - Z/(2m))^{-1} (I + Z/(2m)), lower triangular (forward substitution on
+  // the lower bidiagonal I - Z/(2m)), then its m-th power by repeated squaring
+  const int d = mmax + 1;
+  const int64_t m = steps / nsub;
+  const double hm = 0.5 / (double)m;
+  std::vector<double> R((size_t)d * d, 0.0);
+  for (int col = 0; col < d; ++col) {
+    // column col of (I + Z/(2m)): 1 + z_col hm on the diagonal, hm below it
+    for (int i = col; i < d; ++i) {
+      double rhs = i == col ? 1.0 + z[i] * hm : (i == col + 1 ? hm : 0.0);
+      if (i > col) rhs += hm * R[(size_t)(i - 1) * d + col];  // (I - Z hm) x = rhs: x_i (1 - z_i hm) - hm x_{i-1}
+      R[(size_t)i * d + col] = rhs / (1.0 - z[i] * hm);
+    }
+  }
+  auto mul = [&](const std::vector<double>& X, const std::vector<double>& Y) {
+    std::vector<double> W((size_t)d * d, 0.0);
+    for (int i = 0; i < d; ++i)
+      for (int l = 0; l <= i; ++l) {
+        const double x = X[(size_t)i * d + l];
+        if (x == 0.0) continue;
+        for (int j = 0; j <= l; ++j) W[(size_t)i * d + j] += x * Y[(size_t)l * d + j];
+      }
+    return W;
+  };
+  std::vector<double> F((size_t)d * d, 0.0), P = R;
+  for (int i = 0; i < d; ++i) F[(size_t)i * d + i] = 1.0;
+  for (int64_t e = m; e > 0; e >>= 1) {
+    if (e & 1) F = mul(F, P);
+    if (e > 1) P = mul(P, P);
+  }
+  for (int i = 0; i < d; ++i) D[i] = F[(size_t)i * d];
 }
 
 }  // namespace pxa
@@ -467,7 +509,8 @@ int prepare(pxa_ctx* c) {
     if (c->prop == PXA_PROP_RELPM) {
       // the chain's exponential over one subinterval tau = T / P
       std::vector<double> z, D;
-      relpm_setup_host(c->T / P, c->am, c->a0, c->ap, c->relpm_mmax, c->relpm_nsub, c->relpm_ts, z, D);
+      relpm_setup_host(c->T / P, c->am, c->a0, c->ap, c->relpm_mmax, c->relpm_nsub, c->relpm_ts, z, D,
+                       c->kry_phi == PXA_PHI_STEPPER ? c->K / P : 0);
       if ((rc = alloc(c, &c->relpm_D, D.size()))) return rc;
       if ((rc = alloc(c, &c->relpm_z, z.size()))) return rc;
       PXA_CUDA(c, cudaMemcpy(c->relpm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice), "copy");
@@ -633,8 +676,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)steps_sub : dt;
   const int kth = 256;
   const bool relpm = c->prop == PXA_PROP_RELPM;
-  if (relpm && c->kry_phi != PXA_PHI_EXP)
-    return fail(c, PXA_ERR_INVALID, "the real Leja points method propagates exp(tA): set PXA_PHI_EXP");
+  const int relpm_direct = c->kry_phi == PXA_PHI_STEPPER ? 1 : 0;
   if (do_d) {
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
   ev_record(c, 0);
@@ -646,7 +688,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (P > 1 && relpm) {
     PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
                                        c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
-                                       c->kry_tol, c->status, c->errmax), "chain");
+                                       relpm_direct, c->kry_tol, c->status, c->errmax), "chain");
   } else if (P > 1) {
     PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
                                  c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub, c->kry_tol,
@@ -663,7 +705,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (P > 1 && relpm) {
     PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1, c->hsumA,
                                        c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
-                                       c->kry_tol, c->status, c->errmax), "adj chain");
+                                       relpm_direct, c->kry_tol, c->status, c->errmax), "adj chain");
   } else if (P > 1) {
     PXA_CUDA(c, launch_ad1_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1,
                                  c->hsumA, c->V, c->kry_m, c->kry_phi, hscale, steps_sub, nsub,
@@ -1627,20 +1669,21 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)sps : dt;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), c->stream), "reset errmax");
   if (c->prop == PXA_PROP_RELPM) {
-    if (c->kry_phi != PXA_PHI_EXP)
-      return fail(c, PXA_ERR_INVALID, "the real Leja points method propagates exp(tA): set PXA_PHI_EXP");
     // ReLPM picks its own substeps for the whole span
     std::vector<double> z, D;
     int ns = 1;
     double ts = 0.0;
-    relpm_setup_host(dt * (double)span_steps, c->am, c->a0, c->ap, c->relpm_mmax, ns, ts, z, D);
+    const bool stepper = c->kry_phi == PXA_PHI_STEPPER;
+    relpm_setup_host(dt * (double)span_steps, c->am, c->a0, c->ap, c->relpm_mmax, ns, ts, z, D,
+                     stepper ? span_steps : 0);
     double *Dd = nullptr, *zd = nullptr;
     PXA_CUDA(c, cudaMalloc(&Dd, sizeof(double) * D.size()), "alloc");
     PXA_CUDA(c, cudaMalloc(&zd, sizeof(double) * z.size()), "alloc");
     cudaMemcpy(Dd, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(zd, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice);
     cudaError_t e = launch_ad1_relpm_expv(c->stream, 256, n, c->am, c->a0, c->ap, transpose, x_dev, y_dev, Dd, zd,
-                                          c->relpm_mmax, ts, ns, c->kry_tol, c->status, c->errmax);
+                                          c->relpm_mmax, ts, ns, stepper ? 1 : 0, c->kry_tol, c->status,
+                                          c->errmax);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(Dd);
     cudaFree(zd);

@@ -572,22 +572,28 @@ def test_burgers_four_step_chain(X, torch, n, C, K, P):
 
 
 # ---- real Leja points method (Sec. 4.1) ----------------------------------------------------
+@pytest.mark.parametrize("phi", ["exp", "stepper"])
 @pytest.mark.parametrize("n,c,nu,span", [(256, 1.0, 0.01, 512), (64, 1.0, 0.0, 1200), (128, 0.0, 0.05, 800),
                                          (1000, 1.0, 0.002, 4096), (37, 2.0, 0.1, 300)])
-def test_relpm_expv_matches_exact_exponential(X, torch, n, c, nu, span):
-    """exp(t A) v and exp(t A^T) v by the real Leja points method (pure advection:
+def test_relpm_expv_matches_exact_propagators(X, torch, n, c, nu, span, phi):
+    """exp(t A) v (Newton interpolation of phi) and the CN power R(dt A)^k v (interpolated
+    directly), and their transposes, by the real Leja points method (pure advection:
     degenerate focal interval; pure diffusion; mixed; stiff) against the closed-form
-    Fourier exponential."""
+    Fourier propagators."""
     T, K = 1.0, 4096
-    ctx = ad1_ctx(X, n, c, nu, T, K, 8, m=30, tol=1e-13, phi=X.PHI_EXP)
+    ph = X.PHI_EXP if phi == "exp" else X.PHI_STEPPER
+    ctx = ad1_ctx(X, n, c, nu, T, K, 8, m=30, tol=1e-13, phi=ph)
     ctx.set_propagator(X.PROP_RELPM, 150)
     v = I.grf_k2(n, 9)
     xd = dev(torch, v)
     y = torch.empty_like(xd)
     for tr in (False, True):
         err = ctx.expv(xd, y, span, transpose=tr)
-        ref = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=span * T / K, transpose=tr)
-        assert rel(host(y), ref) < 1e-12
+        if phi == "exp":
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=span * T / K, transpose=tr)
+        else:
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_CN, dt=T / K, steps=span, transpose=tr)
+        assert rel(host(y), ref) < 1e-11
         assert err < 1e-12
 
 
@@ -627,3 +633,21 @@ def test_relpm_paraexp_gradient_matches_oracle(X, torch, n, nu, K, P):
         res[prop] = host(out)
         ctx.close()
     assert rel(res[X.PROP_RELPM], res[X.PROP_KRYLOV]) < 1e-10
+
+
+
+@pytest.mark.parametrize("n,nu,K,P", [(256, 0.01, 4096, 8), (100, 0.0, 512, 4), (333, 0.05, 1024, 16)])
+def test_relpm_stepper_paraexp_equals_serial_stepping(X, torch, n, nu, K, P):
+    """With the CN power interpolated by ReLPM, the Paraexp loop reproduces serial CN
+    stepping (the oracle's serial gradient) to 1e-10."""
+    c, T = 1.0, 1.0
+    q0 = I.grf_k2(n, 23)
+    Jo, go, _ = O.ad1_cn_gradient_serial(q0, c, nu, T, K)
+    ctx = ad1_ctx(X, n, c, nu, T, K, P, m=30, tol=1e-13, phi=X.PHI_STEPPER)
+    ctx.set_propagator(X.PROP_RELPM, 150)
+    qd = dev(torch, q0)
+    ctx.set_control(qd)
+    out = torch.empty_like(qd)
+    J = ctx.gradient(X.PARAEXP, out)
+    assert abs(J - Jo) / Jo < 1e-10
+    assert rel(host(out), go) < 1e-10
