@@ -42,6 +42,9 @@ WORKLOADS = {
                       label="2D advection-diffusion 512x512 nu=1e-3 T=1 RK4 1024 steps FP32 stepping P=64"),
     "advdiff2d_lanes": dict(kind="lanes2d", n=2048, lanes=64, steps=10,
                             label="2D RK4 FP32 lanes kernel, 64 lanes x 2048^2 (1 GiB per state array)"),
+    "advdiff1d_lanes": dict(kind="lanes1d", n=1 << 22, lanes=64, steps=10,
+                            label="1D FP32 CN band lanes kernel, 64 lanes x 2^22 points (1 GiB per state array), "
+                                  "c=1 nu=1e-6 dt=h/8 (21-tap band)"),
     "batched1d": dict(kind="batched1d", count=256, c=1.0, T=1.0, K=4096, P=16,
                       label="256 independent 1D advection-diffusion problems, n ~ U{128..2048}, "
                             "nu ~ logU[1e-3, 1e-1], T=1 CN 4096 steps, P=16, FP32 stepping, FP64 Krylov"),
@@ -593,6 +596,41 @@ def run_lanes2d(args, w):
             "clocks": clk.summary(), "gpu_launches": steps}
 
 
+def run_lanes1d(args, w):
+    """HBM roofline of the 1D FP32 CN band lanes kernel with its states in global memory,
+    at a size far above L2: algorithmic bytes = lanes * n * (4 read + 4 write) per step.
+    c = 1, nu = 1e-6, dt = h/8: the CN band then holds 21 taps, like the 1D
+    advection-diffusion workload's (n = 256, nu = 0.01, dt = 1/4096)."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, inputs as I, pxa as X
+
+    build.build()
+    X.load()
+    n, lanes, steps = w["n"], w["lanes"], max(args.steps, 2)
+    h = 2.0 * np.pi / n
+    K = 1024
+    ctx = X.Context()
+    ctx.set_operator(X.ADVDIFF_1D, n, c=1.0, nu=1e-6)
+    ctx.set_time(K * 0.125 * h, K, X.CN, 1)
+    q0 = torch.as_tensor(I.grf_k2(n, 5), device="cuda")
+    ctx.set_control(q0)
+    for _ in range(max(args.warmup, 1)):
+        ctx.cn_lanes_1d(lanes, 2)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms = ctx.cn_lanes_1d(lanes, steps)
+    alg = lanes * n * 8.0 * steps
+    peak = measured_hbm_peak()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"metric": "HBM GB/s of the 1D FP32 CN band lanes kernel", "value": gbs, "unit": "GB/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": w["label"], "lanes": lanes},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "peak_kind": "measured copy bandwidth"},
+            "clocks": clk.summary(), "gpu_launches": steps}
+
+
 def measured_hbm_peak():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -786,6 +824,8 @@ def main():
         line = run_batch_once(args, w)
     elif w["kind"] == "lanes2d":
         line = run_lanes2d(args, w)
+    elif w["kind"] == "lanes1d":
+        line = run_lanes1d(args, w)
     elif w["kind"] == "advdiff2d":
         line = run_2d(args, w, rank, world)
     elif w["kind"] == "batched1d":

@@ -111,7 +111,9 @@ typedef enum {
 
 typedef struct {
   int kind;   /* pxa_problem */
-  int n;      /* 1D: grid points, 3 <= n <= 4096; 2D: ignored (set to nx * ny) */
+  int n;      /* 1D: grid points, 3 <= n <= 4096 (ADVDIFF_1D up to 2^26 for
+                 pxa_cn_lanes_1d and pxa_apply_operator; the gradient needs <= 4096);
+                 2D: ignored (set to nx * ny) */
   double L;   /* domain length (> 0), h = L / n (2D: L / nx on both axes) */
   double c;   /* advection speed (PXA_ADVDIFF_1D) */
   double nu;  /* diffusion coefficient (>= 0) */
@@ -275,6 +277,13 @@ int pxa_expv(pxa_ctx* ctx, int transpose, int64_t span_steps, int substeps,
 int pxa_burgers_rhs(pxa_ctx* ctx, const double* u_dev, double* y_dev);
 int pxa_burgers_jac_T(pxa_ctx* ctx, const double* u_dev, const double* x_dev, double* y_dev);
 
+/* ADVDIFF_1D: `steps` FP32 Crank-Nicolson steps of `lanes` lanes whose states live in
+ * global memory (n % 4 == 0; every lane starts from the configured control), one launch
+ * per step over all lanes: the exact circulant CN band, FP32 arithmetic and accumulation.
+ * Timed with CUDA events on the context's stream; allocates 2 * lanes * n floats on the
+ * first call for a given lane count. *ms_host receives the elapsed time; out_dev
+ * (optional, lanes * n doubles) the final states. */
+int pxa_cn_lanes_1d(pxa_ctx* ctx, int lanes, int64_t steps, double* out_dev, double* ms_host);
 /* ADVDIFF_2D: `steps` FP32 RK4 steps of `lanes` zero-initial-value inhomogeneous
  * lanes (Eq. linInhomEqus with the forcing s(t) f of the configured control; lane l
  * starts at step l * steps) on the TMA halo-tile kernel, timed with CUDA events on the

@@ -13,6 +13,12 @@ struct Bu1Grid {
 };
 
 size_t krylov_smem_bytes(int n, int m, int extra_vecs, bool v_in_smem);
+// FP32 CN band lanes with their states in global memory (kernels_ad1_stream.cu).
+int ad1_stream_padded_taps(int r);
+cudaError_t launch_ad1_stream_step(cudaStream_t st, int lanes, int n, int r, const float* taps_padded,
+                                   const float* x, float* y);
+cudaError_t launch_ad1_stream_fill(cudaStream_t st, int n, int lanes, const double* q0, float* x);
+cudaError_t launch_ad1_stream_out(cudaStream_t st, size_t total, const float* x, double* out);
 // Host: taps m_j (|j| <= r) of the circulant Crank-Nicolson map of the stencil (am, a0, ap).
 void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps, int& r);
 

@@ -18,40 +18,34 @@ using namespace pxa;
 
 namespace pxa {
 
-// Taps m_j (|j| <= r) of the circulant Crank–Nicolson map
-//   M = (I - dt/2 A)^{-1} (I + dt/2 A),  (M x)_i = sum_j m_j x_{i+j},
-// from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
-// by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj} in long double. The taps decay
-// geometrically (the implicit matrix is diagonally dominant); the band stops where
-// both |m_r| and |m_-r| fall below 2^-64 |m_0|, far under FP64 rounding of the step;
-// when they do not decay within n/2 the full circulant is used.
-void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps,
-                  int& r) {
-  typedef std::complex<long double> C;
-  const long double pi = 3.141592653589793238462643383279502884L;
+template <typename Real>
+static void cn_band_taps_t(int n, double am, double a0, double ap, double dt, int cut_exp,
+                           std::vector<double>& taps, int& r) {
+  typedef std::complex<Real> C;
+  const Real pi = (Real)3.141592653589793238462643383279502884L;
   std::vector<C> R(n), w(n);
   for (int k = 0; k < n; ++k) {
-    long double ph = 2.0L * pi * (long double)k / (long double)n;
-    w[k] = C(cosl(ph), sinl(ph));
+    Real ph = (Real)2 * pi * (Real)k / (Real)n;
+    w[k] = C(std::cos(ph), std::sin(ph));
   }
-  const long double th = 0.5L * (long double)dt;
+  const Real th = (Real)0.5 * (Real)dt;
   for (int k = 0; k < n; ++k) {
-    C lam = (long double)a0 + (long double)am * std::conj(w[k]) + (long double)ap * w[k];
-    R[k] = (1.0L + th * lam) / (1.0L - th * lam);
+    C lam = (Real)a0 + (Real)am * std::conj(w[k]) + (Real)ap * w[k];
+    R[k] = ((Real)1 + th * lam) / ((Real)1 - th * lam);
   }
   auto tap = [&](int j) {
-    C s = 0.0L;
+    C s = (Real)0;
     for (int k = 0; k < n; ++k) {
       long long idx = ((long long)k * (long long)(((j % n) + n) % n)) % n;
       s += R[k] * std::conj(w[idx]);
     }
-    return (double)(s.real() / (long double)n);
+    return (double)(s.real() / (Real)n);
   };
   std::vector<double> pos, neg;  // pos[j] = m_j, neg[j] = m_-j
   double m0 = tap(0);
   pos.push_back(m0);
   neg.push_back(m0);
-  const double thr = std::ldexp(std::fabs(m0), -64);
+  const double thr = std::ldexp(std::fabs(m0), -cut_exp);
   // widest band: every offset once; for even n the offset n/2 equals -n/2 and is
   // stored once (on the negative side)
   const int rmax = n / 2;
@@ -62,12 +56,26 @@ void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector
     pos.push_back(mp);
     neg.push_back(mn);
     r = j;
-    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;  // the tail is below FP64 rounding
+    if (std::fabs(mp) < thr && std::fabs(mn) < thr) break;  // the tail is below the cut
   }
   taps.assign(2 * r + 1, 0.0);
   for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
 }
 
+// Taps m_j (|j| <= r) of the circulant Crank–Nicolson map
+//   M = (I - dt/2 A)^{-1} (I + dt/2 A),  (M x)_i = sum_j m_j x_{i+j},
+// from its eigenvalues R_k = (1 + dt/2 lam_k)/(1 - dt/2 lam_k), lam_k = a0 + am w^-k + ap w^k,
+// by the inverse DFT m_j = (1/n) sum_k R_k w^{-kj}. The taps decay geometrically (the
+// implicit matrix is diagonally dominant); the band stops where both |m_r| and |m_-r| fall
+// below 2^-64 |m_0| (long double sums, n <= 65536), far under FP64 rounding of the step,
+// or below 2^-50 |m_0| (double sums, longer grids, used by the FP32 lane kernels only);
+// when they do not decay within n/2 the full circulant is used.
+void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps, int& r) {
+  if (n <= 65536)
+    cn_band_taps_t<long double>(n, am, a0, ap, dt, 64, taps, r);
+  else
+    cn_band_taps_t<double>(n, am, a0, ap, dt, 50, taps, r);
+}
 
 // Real Leja points method (Sec. 4.1), host part. Leja points of [-2, 2]: 2 first, then
 // each point maximises the sum of log distances to the earlier ones, searched on a
@@ -229,6 +237,11 @@ struct pxa_ctx {
   double* relpm_z = nullptr;
   int relpm_nsub = 1;
   double relpm_ts = 0.0;
+  // pxa_cn_lanes_1d: FP32 lane states in global memory and the padded FP32 band
+  float* st1d = nullptr;
+  int lanes1d = 0;
+  float* taps1d = nullptr;
+  int r1d = 0;
   double kry_tol = 1e-11;
   int magnus_M = 25;
   const double* control = nullptr;
@@ -371,6 +384,8 @@ void release_workspace(pxa_ctx* c) {
   c->ready = false;
   c->taps = c->E = c->EA = c->src = c->srcA = c->hsum = c->hsumA = c->qT = c->tmp = nullptr;
   c->relpm_D = c->relpm_z = nullptr;
+  c->st1d = c->taps1d = nullptr;
+  c->lanes1d = 0;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
   c->status = nullptr;
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
@@ -454,7 +469,8 @@ int prepare(pxa_ctx* c) {
   if ((rc = alloc(c, &c->status, 1))) return rc;
   if ((rc = alloc(c, &c->ctl_buf, n))) return rc;
   if ((rc = alloc(c, &c->grad_buf, n))) return rc;
-  if (c->op.kind != PXA_ADVDIFF_2D) {
+  const bool long1d = c->op.kind == PXA_ADVDIFF_1D && n > 4096;  // lanes in global memory only
+  if (c->op.kind != PXA_ADVDIFF_2D && !long1d) {
     if ((rc = alloc(c, &c->E, (size_t)P * n))) return rc;
     if ((rc = alloc(c, &c->EA, (size_t)P * n))) return rc;
     if ((rc = alloc(c, &c->src, n))) return rc;
@@ -649,6 +665,9 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
   const bool do_d = parts & 1, do_a = parts & 2;
   const int n = c->op.n, P = c->P, r = c->band_r, th = threads_for(n);
+  if (n > 4096)
+    return fail(c, PXA_ERR_INVALID, "ADVDIFF_1D with n > 4096: the lanes and chains keep a lane in shared memory "
+                                    "(pxa_cn_lanes_1d steps longer grids)");
   const int64_t K = c->K;
   const double dt = c->T / (double)K;
   const double* q0 = c->control;
@@ -1109,8 +1128,9 @@ int pxa_set_operator(pxa_ctx* c, const pxa_operator_desc* op) {
     invalidate(c);
     return PXA_OK;
   }
-  if (op->n < 3 || op->n > 4096 || !(op->L > 0.0) || !(op->nu >= 0.0))
-    return fail(c, PXA_ERR_INVALID, "operator parameters (3 <= n <= 4096, L > 0, nu >= 0)");
+  const int nmax = op->kind == PXA_ADVDIFF_1D ? (1 << 26) : 4096;
+  if (op->n < 3 || op->n > nmax || !(op->L > 0.0) || !(op->nu >= 0.0))
+    return fail(c, PXA_ERR_INVALID, "operator parameters (3 <= n <= 4096 (ADVDIFF_1D: 2^26), L > 0, nu >= 0)");
   c->op = *op;
   double h = op->L / op->n;
   c->am = op->c / (2.0 * h) + op->nu / (h * h);
@@ -1647,6 +1667,7 @@ int pxa_apply_operator(pxa_ctx* c, int transpose, const double* x_dev, double* y
 int pxa_step(pxa_ctx* c, int transpose, int64_t steps, const double* x_dev, double* y_dev) {
   if (!c || !x_dev || !y_dev || steps < 0) return PXA_ERR_INVALID;
   if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  if (c->op.n > 4096) return fail(c, PXA_ERR_INVALID, "pxa_step needs n <= 4096 (one block holds the lane)");
   int rc = prepare(c);
   if (rc) return rc;
   const int n = c->op.n;
@@ -1661,6 +1682,7 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   if (!c || !x_dev || !y_dev || span_steps < 1 || substeps < 1 || span_steps % substeps != 0)
     return PXA_ERR_INVALID;
   if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  if (c->op.n > 4096) return fail(c, PXA_ERR_INVALID, "pxa_expv needs n <= 4096 (one block holds the vectors)");
   int rc = prepare(c);
   if (rc) return rc;
   const int n = c->op.n;
@@ -1697,6 +1719,63 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   rc = read_status(c);
   if (err_host) *err_host = c->stats.krylov_err_max;
   return rc;
+}
+
+int pxa_cn_lanes_1d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, double* ms_host) {
+  if (!c || lanes < 1 || steps < 1) return PXA_ERR_INVALID;
+  if (!c->have_op || c->op.kind != PXA_ADVDIFF_1D) return fail(c, PXA_ERR_STATE, "ADVDIFF_1D operator required");
+  if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first (the lanes' initial state)");
+  const int n = c->op.n;
+  if (n % 4 != 0) return fail(c, PXA_ERR_INVALID, "pxa_cn_lanes_1d needs n % 4 == 0");
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->taps1d) {
+    // FP32 band: the taps above 2^-40 of the centre one, zero-padded for the kernel
+    const int r = c->band_r;
+    const double cut = std::ldexp(std::fabs(c->band_host[r]), -40);
+    int r32 = 0;
+    for (int j = 1; j <= r; ++j)
+      if (std::fabs(c->band_host[r + j]) >= cut || std::fabs(c->band_host[r - j]) >= cut) r32 = j;
+    std::vector<float> t(ad1_stream_padded_taps(r32), 0.f);
+    for (int j = -r32; j <= r32; ++j) t[r32 + j] = (float)c->band_host[r + j];
+    if ((rc = alloc(c, &c->taps1d, t.size()))) return rc;
+    PXA_CUDA(c, cudaMemcpy(c->taps1d, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice), "copy taps");
+    c->r1d = r32;
+  }
+  if (c->lanes1d != lanes) {
+    if ((rc = alloc(c, &c->st1d, 2 * (size_t)lanes * n))) return rc;
+    c->lanes1d = lanes;
+  }
+  cudaStream_t st = c->stream;
+  float* x = c->st1d;
+  float* y = c->st1d + (size_t)lanes * n;
+  PXA_CUDA(c, launch_ad1_stream_fill(st, n, lanes, c->control, x), "fill lanes");
+  cudaEvent_t e0, e1;
+  PXA_CUDA(c, cudaEventCreate(&e0), "event");
+  PXA_CUDA(c, cudaEventCreate(&e1), "event");
+  PXA_CUDA(c, cudaEventRecord(e0, st), "record");
+  for (int64_t s = 0; s < steps; ++s) {
+    cudaError_t e = launch_ad1_stream_step(st, lanes, n, c->r1d, c->taps1d, x, y);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(c, e, "1d lane step");
+    }
+    std::swap(x, y);
+  }
+  PXA_CUDA(c, cudaEventRecord(e1, st), "record");
+  PXA_CUDA(c, cudaEventSynchronize(e1), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_host) *ms_host = ms;
+  if (out_dev) {
+    PXA_CUDA(c, launch_ad1_stream_out(st, (size_t)lanes * n, x, out_dev), "lanes out");
+    PXA_CUDA(c, cudaStreamSynchronize(st), "sync");
+  }
+  return read_status(c);
 }
 
 int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, double* ms_host) {

@@ -35,7 +35,7 @@ EXPORTS = [
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
-    "pxa_rk4_lanes_2d",
+    "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
     "pxa_batch_set_homogeneous", "pxa_batch_set_timing",
     "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "pxa_autotune": [p, i, p, p],
         "pxa_solve_direct": [p, i, p],
         "pxa_rk4_lanes_2d": [p, i, i64, p, p],
+        "pxa_cn_lanes_1d": [p, i, i64, p, p],
         "pxa_solve_adjoint": [p, i, p],
         "pxa_set_timing": [p, i],
         "pxa_gradient": [p, i, p, p],
@@ -314,6 +315,12 @@ class Context:
         self._check(self._L.pxa_expv(self._h, int(transpose), int(span_steps), int(substeps),
                                      _dptr(x), _dptr(y), ctypes.byref(err)))
         return err.value
+
+    def cn_lanes_1d(self, lanes, steps, out=None) -> float:
+        ms = ctypes.c_double()
+        self._check(self._L.pxa_cn_lanes_1d(self._h, lanes, int(steps), _dptr(out) if out is not None else None,
+                                            ctypes.byref(ms)))
+        return ms.value
 
     def rk4_lanes_2d(self, lanes, steps, out=None) -> float:
         ms = ctypes.c_double()

@@ -651,3 +651,24 @@ def test_relpm_stepper_paraexp_equals_serial_stepping(X, torch, n, nu, K, P):
     J = ctx.gradient(X.PARAEXP, out)
     assert abs(J - Jo) / Jo < 1e-10
     assert rel(host(out), go) < 1e-10
+
+
+@pytest.mark.parametrize("n,nu", [(4608, 0.01), (5000, 0.002), (64, 0.05), (2304 * 3 + 4, 0.0)])
+def test_cn_lanes_1d_streaming_matches_oracle(X, torch, n, nu):
+    """FP32 CN band lanes with their states in global memory (tiles of 2304 points,
+    periodic halos across tile and lane ends, a partial last tile) against the oracle's
+    FP64 CN steps, within FP32 roundoff."""
+    c, T, K, steps, lanes = 1.0, 1.0, 4096, 7, 3
+    ctx = ad1_ctx(X, n, c, nu, T, K, 1)
+    q0 = I.grf_k2(n, 31)
+    qd = dev(torch, q0)
+    ctx.set_control(qd)
+    out = torch.empty(lanes * n, dtype=torch.float64, device="cuda")
+    ms = ctx.cn_lanes_1d(lanes, steps, out)
+    assert ms > 0.0
+    ref = q0.copy()
+    for _ in range(steps):
+        ref = O.ad1_cn_step(ref, c, nu, T / K)
+    o = host(out).reshape(lanes, n)
+    for l in range(lanes):
+        assert rel(o[l], ref) < 1e-5
