@@ -35,7 +35,7 @@ SMS = 152
 
 WORKLOADS = {
     "burgers1d": dict(kind="burgers1d", n=1024, nu=0.005, T=2.0, K=20000, P=32, M=25, m=20,
-                      tol=1e-9, label="1D viscous Burgers n=1024 nu=0.005 T=2 RK4 dt=1e-4 FP64 P=32"),
+                      tol=1e-9, checkpoints=5, label="1D viscous Burgers n=1024 nu=0.005 T=2 RK4 dt=1e-4 FP64 P=32"),
     "advdiff1d": dict(kind="advdiff1d", n=256, c=1.0, nu=0.01, T=1.0, K=4096, P=8, m=30, sub=1,
                       tol=1e-11, label="1D advection-diffusion n=256 nu=0.01 T=1 CN 4096 steps FP64 P=8 (Krylov m autotuned)"),
     "advdiff2d": dict(kind="advdiff2d", n=512, nu=1e-3, T=1.0, K=1024, P=64,
@@ -247,6 +247,11 @@ def run_ours(args, w, rank, world):
         # and for the CN power (which keeps Paraexp equal to serial stepping)
         phis.insert(2, ("paraexp_exp_relpm", X.PARAEXP, X.PHI_EXP))
         phis.insert(0, ("paraexp_stepper_relpm", X.PARAEXP, X.PHI_STEPPER))
+    if w["kind"] == "burgers1d":
+        # the multi-checkpoint scheme (Sec. 3.5): C + 1 checkpoints, every interval re-stepped
+        # and solved by the Paraexp adjoint over its own P subintervals (not a headline
+        # candidate: it trades a second direct pass for memory)
+        phis.append((f"checkpoints{w['checkpoints']}_paraexp_stepper", X.PARAEXP, X.PHI_STEPPER))
     grads = {}
     tuned = {}
     for name, mode, phi in phis:
@@ -256,6 +261,8 @@ def run_ours(args, w, rank, world):
             ctx.set_target(tgt)
         best_ms = None
         ctx.set_graph(True)  # candidates are timed as graph replays, the path timed below
+        if name.startswith("checkpoints"):
+            ctx.set_checkpoints(w["checkpoints"])
         if name.endswith("_relpm"):
             ctx.set_propagator(X.PROP_RELPM, 150)
         elif not (w["kind"] == "burgers1d" and phi == X.PHI_EXP):
@@ -269,7 +276,8 @@ def run_ours(args, w, rank, world):
                        "tau_ratio": round(float(st["tau_ratio"]), 6),
                        "autotune_best_ms": best_ms}
         times, _, g = time_mode(X, torch, ctx, mode, max(1, min(args.steps, 3)), 1, flush)
-        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name, "tuned": tuned[name]}
+        variants[name] = {"ms_per_step": float(np.mean(times)), "mode": name, "tuned": tuned[name],
+                          "workspace_bytes": int(ctx.stats()["workspace_bytes"])}
         grads[name] = g.detach().cpu().numpy()
         ctx.close()
 

@@ -148,6 +148,7 @@ typedef struct {
   float partition_r;        /* ratio of successive chunk lengths in use (0: equal chunks) */
   float tau_ratio;          /* k = adjoint-preparation time / direct time per step, as
                                last measured by the autotuner (0: not measured) */
+  int checkpoint_intervals; /* C of the multi-checkpoint scheme in use (0: off) */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -183,6 +184,21 @@ int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
 int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
 /* Direct-state storage policy (pxa_memory). */
 int pxa_set_memory(pxa_ctx* ctx, int policy);
+/* Multi-checkpoint scheme (Sec. 3.5), BURGERS_1D with the banded adjoint
+ * (PXA_ADJ_BANDED or PXA_ADJ_BANDED_PAIR). With intervals = C >= 2 the direct solve is a
+ * rough pass that keeps J and the C + 1 states at t = iT/C. The adjoint then takes the
+ * intervals [iT/C, (i+1)T/C] from the top: each is re-stepped from its checkpoint and
+ * solved by the Paraexp adjoint over its own P equal subintervals (K/(CP) steps each;
+ * the placement of the checkpoints does not depend on the partition), starting from the
+ * adjoint value at its top row that the interval above computed. Device memory for the
+ * trajectory, the band records and the adjoint rows falls from K + 1 rows to
+ * 2 (K/C + 1) rows: two interval buffer sets, so that the re-step, records and lanes of
+ * one interval run beside the chain of the other. The gradient equals that of full
+ * storage up to rounding order. Requires K % (C * P) == 0 (checked when the workspace is
+ * built: PXA_ERR_INVALID) and, for Paraexp, PXA_PHI_STEPPER. The memory policy of
+ * pxa_set_memory is not used while the scheme is on. intervals = 0 or 1: off (default).
+ * intervals < 0 or > 65536: PXA_ERR_INVALID. Invalidates the workspace. */
+int pxa_set_checkpoints(pxa_ctx* ctx, int intervals);
 /* BURGERS_1D adjoint evaluation (pxa_adjoint). BANDED falls back to RESTEP when its
  * records do not fit; pxa_get_stats reports which one is in use. */
 int pxa_set_adjoint(pxa_ctx* ctx, int impl);

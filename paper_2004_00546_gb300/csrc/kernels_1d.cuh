@@ -113,6 +113,17 @@ cudaError_t launch_bu1_band_grad_part(cudaStream_t st, int n, double dt, double 
                                       int priority);
 cudaError_t launch_bu1_band_grad_reduce(cudaStream_t st, int n, int64_t K, const double* partial,
                                         const double* extra, double* grad, int* status);
+// The gradient over steps [s_begin, s_end) in blocks of spb steps into partial rows
+// block0, block0 + 1, ...; the fixed-order sum of the first `blocks` rows of partial.
+cudaError_t launch_bu1_band_grad_range(cudaStream_t st, int n, double dt, double omega, int64_t s_begin,
+                                       int64_t s_end, int spb, int64_t li_top, const double* LI,
+                                       const double* H, const double* jt, double* partial, int block0,
+                                       int priority);
+cudaError_t launch_bu1_band_reduce_blocks(cudaStream_t st, int n, int blocks, const double* partial,
+                                          double* grad, int* status);
+// out = H_row + the source entries of rec_row (one row of n points).
+cudaError_t launch_bu1_band_top(cudaStream_t st, int n, const double* H_row, const double* rec_row,
+                                double* out);
 // Two-step banded chain (kernels_bu1_pair.cu).
 int bu1_chain2_plan(int64_t K, int64_t k, int P, int4* out);
 bool bu1_chain2_valid(int n, int C);
@@ -126,6 +137,8 @@ cudaError_t launch_bu1_band_fill(cudaStream_t st, int n, const double* rec, cons
                                  double* rows, int priority);
 // Four-step banded chain (kernels_bu1_quad.cu).
 int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out);
+int bu1_chain_plan_range(int64_t s_hi, int64_t s_lo, int64_t k, int64_t src_lo, int64_t lane_lo,
+                         int64_t lane_hi, int max_len, int4* out);
 bool bu1_chain4_valid(int n, int C);
 cudaError_t launch_bu1_band_quad(cudaStream_t st, int n, const double* rp, int64_t q_lo, int64_t q_hi,
                                  double* rq, int priority);

@@ -437,19 +437,20 @@ __global__ void bu1_band_sweep_kernel(int n, const double* __restrict__ rec, int
 }
 
 // ---- 3. forcing gradient --------------------------------------------------------------
-// Grid (tiles, step blocks); partial[block_y][n] = sum over the block's steps s of
-// (G_s^T lambda_{s+1}), lambda = H (every row, when given) + LI (rows <= li_top).
+// Grid (tiles, step blocks); block y covers the steps s_begin + y spb .. (capped at s_end)
+// and writes partial[block0 + y][n] = sum over its steps s of (G_s^T lambda_{s+1}),
+// lambda = H (every row, when given) + LI (rows <= li_top).
 __global__ void __launch_bounds__(PT) bu1_band_grad_kernel(
-    int n, double dt, double omega, int64_t K, int64_t li_top, const double* __restrict__ LI,
-    const double* __restrict__ H, const double* __restrict__ jt, int steps_per_block, int block0,
-    double* __restrict__ partial) {
+    int n, double dt, double omega, int64_t s_begin, int64_t s_end, int64_t li_top,
+    const double* __restrict__ LI, const double* __restrict__ H, const double* __restrict__ jt,
+    int steps_per_block, int block0, double* __restrict__ partial) {
   __shared__ double lam[PT + 6], kb4[PT + 6], kb3[PT + 6], kb2[PT + 6];
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * PT;
-  const int by = block0 + (int)blockIdx.y;  // step block
-  const int64_t sb = (int64_t)by * steps_per_block;
+  const int by = block0 + (int)blockIdx.y;  // row of partial
+  const int64_t sb = s_begin + (int64_t)blockIdx.y * steps_per_block;
   int64_t se = sb + steps_per_block;
-  if (se > K) se = K;
+  if (se > s_end) se = s_end;
   const double dt6 = dt / 6.0, dt3 = dt / 3.0, h2 = 0.5 * dt;
   double acc = 0.0;
   constexpr int O = 3;  // halo offset
@@ -650,8 +651,18 @@ cudaError_t launch_bu1_band_grad_part(cudaStream_t st, int n, double dt, double 
                                       int priority) {
   if (b_hi <= b_lo) return cudaSuccess;
   const int spb = bu1_band_steps_per_block(K, n);
+  const int64_t s_end = (int64_t)b_hi * spb < K ? (int64_t)b_hi * spb : K;
+  return launch_bu1_band_grad_range(st, n, dt, omega, (int64_t)b_lo * spb, s_end, spb, li_top, LI, H, jt,
+                                    partial, b_lo, priority);
+}
+
+cudaError_t launch_bu1_band_grad_range(cudaStream_t st, int n, double dt, double omega, int64_t s_begin,
+                                       int64_t s_end, int spb, int64_t li_top, const double* LI,
+                                       const double* H, const double* jt, double* partial, int block0,
+                                       int priority) {
+  if (s_end <= s_begin) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((n + PT - 1) / PT, b_hi - b_lo);
+  cfg.gridDim = dim3((n + PT - 1) / PT, (unsigned)((s_end - s_begin + spb - 1) / spb));
   cfg.blockDim = dim3(PT);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -659,14 +670,34 @@ cudaError_t launch_bu1_band_grad_part(cudaStream_t st, int n, double dt, double 
   at[0].val.priority = priority;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, bu1_band_grad_kernel, n, dt, omega, K, li_top, LI, H, jt, spb, b_lo,
-                            partial);
+  return cudaLaunchKernelEx(&cfg, bu1_band_grad_kernel, n, dt, omega, s_begin, s_end, li_top, LI, H, jt, spb,
+                            block0, partial);
 }
 
 cudaError_t launch_bu1_band_grad_reduce(cudaStream_t st, int n, int64_t K, const double* partial,
                                         const double* extra, double* grad, int* status) {
   const int blocks = bu1_band_grad_blocks(K, n);
   bu1_band_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, blocks, partial, extra, grad, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bu1_band_reduce_blocks(cudaStream_t st, int n, int blocks, const double* partial,
+                                          double* grad, int* status) {
+  bu1_band_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, blocks, partial, nullptr, grad, status);
+  return cudaGetLastError();
+}
+
+// lambda at the bottom row of a checkpoint interval: the chain's row (homogeneous carry
+// and the bottom lane's value) plus the objective's source of that row.
+__global__ void bu1_band_top_kernel(int n, const double* __restrict__ H, const double* __restrict__ rec,
+                                    double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = H[i] + rec[(size_t)i * RW + (RW - 1)];
+}
+
+cudaError_t launch_bu1_band_top(cudaStream_t st, int n, const double* H_row, const double* rec_row,
+                                double* out) {
+  bu1_band_top_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, H_row, rec_row, out);
   return cudaGetLastError();
 }
 

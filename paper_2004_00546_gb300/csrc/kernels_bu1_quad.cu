@@ -296,20 +296,27 @@ __global__ void __launch_bounds__(QT) bu1_band_fill4_kernel(int n, const double*
 }
 
 // ---- host side ----------------------------------------------------------------------
-// Step plan of the chain from row P*k down to 0 with steps of up to max_len (1, 2 or 4)
-// rows: a longer step is taken from row r where r is a multiple of its length, no lane
-// value is added on the rows it skips and the source is on for all of its rows or for
-// none. Entries {row produced, steps, source on, lane added at that row}. Returns the
-// number of entries; out must hold P*k entries.
-int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out) {
-  auto inj = [&](int64_t r) { return (r > 0 && r % k == 0 && r / k <= P - 2) ? (int)(r / k) : 0; };
-  auto src = [&](int64_t r) { return r > (int64_t)(P - 1) * k ? 1 : 0; };
+// Step plan of the chain from row s_hi down to s_lo with steps of up to max_len (1, 2 or
+// 4) rows: a longer step is taken from row r where r is a multiple of its length (the
+// pair and four-step records sit at rows 2j and 4j), it stays above s_lo, no lane value
+// is added on the rows it skips and the source is on for all of its rows or for none.
+// The source is on for rows above src_lo; the value of lane j (subintervals of k steps)
+// is added at row j k for j in [lane_lo, lane_hi], j >= 1. Entries {row produced, steps,
+// source on, lane added at that row}. Returns the number of entries; out must hold
+// s_hi - s_lo entries.
+int bu1_chain_plan_range(int64_t s_hi, int64_t s_lo, int64_t k, int64_t src_lo, int64_t lane_lo,
+                         int64_t lane_hi, int max_len, int4* out) {
+  auto inj = [&](int64_t r) {
+    const int64_t j = r / k;
+    return (r % k == 0 && j >= 1 && j >= lane_lo && j <= lane_hi) ? (int)j : 0;
+  };
+  auto src = [&](int64_t r) { return r > src_lo ? 1 : 0; };
   int cnt = 0;
-  int64_t r = K;
-  while (r > 0) {
+  int64_t r = s_hi;
+  while (r > s_lo) {
     int len = 1;
     for (int L = max_len; L >= 2; L /= 2) {
-      if (r < L || r % L != 0 || src(r - 1) != src(r - L)) continue;
+      if (r - L < s_lo || r % L != 0 || src(r - 1) != src(r - L)) continue;
       bool clear = true;
       for (int u = 1; u < L; ++u) clear = clear && inj(r - u) == 0;
       if (clear) {
@@ -322,6 +329,12 @@ int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out) {
     r = ro;
   }
   return cnt;
+}
+
+// The plan of the whole chain: rows P k down to 0, the source on the top subinterval, the
+// values of lanes 1 .. P-2 added at their bottom rows.
+int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out) {
+  return bu1_chain_plan_range(K, 0, k, (int64_t)(P - 1) * k, 1, P - 2, max_len, out);
 }
 
 bool bu1_chain4_valid(int n, int C) {

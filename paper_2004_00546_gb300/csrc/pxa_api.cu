@@ -286,6 +286,7 @@ struct pxa_ctx {
   int q_direct = 0, q_sweep = 0;  // steps per halo exchange of the RK4 / banded sweeps (0 = auto)
   cudaStream_t side = nullptr;
   cudaStream_t side2 = nullptr;  // adjoint lanes of the overlapped chunks
+  cudaStream_t side3 = nullptr;  // re-step and records of the second interval buffer set
   static constexpr int kMaxChunks = 8;
   double part_r = 0.0;        // ratio of successive chunk lengths (0: equal chunks)
   cudaEvent_t ev_fork[kMaxChunks] = {};
@@ -315,6 +316,30 @@ struct pxa_ctx {
   static constexpr int kMaxSeg = 8;
   int chain_segments = 4;
   cudaEvent_t ev_seg[kMaxSeg] = {};
+  // multi-checkpoint scheme (Sec. 3.5): C intervals of K/C steps, each re-stepped from its
+  // checkpoint and solved by the Paraexp adjoint over its own P subintervals. Two interval
+  // buffer sets alternate, so that one interval's re-step, records and lanes run on the
+  // side streams while the chain of the other runs.
+  int intervals = 0;  // C (0: off)
+  struct IntervalSet {
+    double* traj = nullptr;  // [(K/C+1)][n] direct states of the interval
+    double* rec = nullptr;   // [(K/C+1)][n][BU1_BAND_RECORD]
+    double* jt = nullptr;    // [(K/C)][n][BU1_BAND_RECORD]
+    double* rp = nullptr;    // [(K/(2C)+1)][n][BU1_PAIR_RECORD]
+    double* rq = nullptr;    // [(K/(4C)+1)][n][BU1_QUAD_RECORD]
+    double* LI = nullptr;    // [(K/C+1)][n] adjoint lane rows
+    double* H = nullptr;     // [(K/C+1)][n] chain rows
+  };
+  IntervalSet iv[2];
+  double* ckpt = nullptr;     // [(C+1)][n] direct states at t = jT/C
+  double* lamtop = nullptr;   // [n] adjoint value at the bottom row of the interval last done
+  double* ivW = nullptr;      // [C*P][n] values of the adjoint lanes at their bottom rows
+  // chain plans of all intervals: [Paraexp partition, serial][steps up to 2, up to 4]
+  int4* iplan_dev[2][2] = {};
+  std::vector<int> iplan_off[2][2];  // C+1 offsets into iplan_dev
+  int iv_spb = 1, iv_blocks = 1;  // gradient steps per block and blocks per interval
+  // per buffer set: records built, lanes done, chain done, buffers free
+  cudaEvent_t ev_iv[4][2] = {};
   double* Jdev = nullptr;     // 1
   double* errmax = nullptr;   // 1
   int* status = nullptr;      // 1
@@ -405,9 +430,26 @@ void release_workspace(pxa_ctx* c) {
       cudaEventDestroy(e);
       e = nullptr;
     }
+  for (auto& set : c->iv) set = pxa_ctx::IntervalSet{};
+  c->ckpt = c->lamtop = c->ivW = nullptr;
+  for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < 2; ++q) {
+      c->iplan_dev[s][q] = nullptr;
+      c->iplan_off[s][q].clear();
+    }
+  for (auto& row : c->ev_iv)
+    for (auto& e : row)
+      if (e) {
+        cudaEventDestroy(e);
+        e = nullptr;
+      }
   if (c->side) {
     cudaStreamDestroy(c->side);
     c->side = nullptr;
+  }
+  if (c->side3) {
+    cudaStreamDestroy(c->side3);
+    c->side3 = nullptr;
   }
   if (c->side2) {
     cudaStreamDestroy(c->side2);
@@ -534,47 +576,8 @@ int prepare(pxa_ctx* c) {
     }
   } else {
     int64_t k = c->K / P;
-    if (c->memory == PXA_STORE_FULL) {
-      if ((rc = alloc(c, &c->traj, (size_t)(c->K + 1) * n))) return rc;
-    } else {
-      if ((rc = alloc(c, &c->traj, (size_t)(P + 1) * n))) return rc;
-      if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
-    }
-    // The banded adjoint keeps two records per step and point plus two lambda
-    // trajectories; it is used when that takes at most half of the free memory,
-    // otherwise the adjoint re-steps the stages (kernels_bu1_cluster.cu).
-    if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
-    const size_t rows1 = (size_t)(c->K + 1) * n;
-    const size_t pair_doubles = c->chain_len >= 2 ? (size_t)(c->K / 2) * n * BU1_PAIR_RECORD : 0;
-    const size_t quad_doubles = c->chain_len >= 4 ? (size_t)(c->K / 4) * n * BU1_QUAD_RECORD : 0;
-    const size_t band_doubles = rows1 * BU1_BAND_RECORD + (size_t)c->K * n * BU1_BAND_RECORD +
-                                2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n + pair_doubles +
-                                quad_doubles;
-    size_t free_b = 0, total_b = 0;
-    PXA_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    if (c->band_req != 0 && band_doubles * sizeof(double) <= free_b / 2) {
-      if ((rc = alloc(c, &c->rec, rows1 * BU1_BAND_RECORD))) return rc;
-      if ((rc = alloc(c, &c->jt, (size_t)c->K * n * BU1_BAND_RECORD))) return rc;
-      if ((rc = alloc(c, &c->LI, rows1))) return rc;
-      if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
-      if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
-      if ((rc = alloc(c, &c->Jparts, pxa_ctx::kMaxChunks))) return rc;
-      if (c->chain_len >= 2) {
-        if ((rc = alloc(c, &c->rp, pair_doubles))) return rc;
-        if (c->chain_len >= 4 && (rc = alloc(c, &c->rq, quad_doubles))) return rc;
-        // step plans of the chain for the Paraexp partition and for serial stepping, with
-        // steps of up to two and of up to four rows
-        std::vector<int4> plan((size_t)c->K);
-        for (int ser = 0; ser < 2; ++ser)
-          for (int q4 = 0; q4 < (c->rq ? 2 : 1); ++q4) {
-            pxa_ctx::ChainPlan& pl = c->plans[ser][q4];
-            pl.count = bu1_chain_plan(c->K, ser ? c->K : k, ser ? 1 : P, q4 ? 4 : 2, plan.data());
-            if ((rc = alloc(c, &pl.dev, (size_t)pl.count))) return rc;
-            PXA_CUDA(c, cudaMemcpy(pl.dev, plan.data(), sizeof(int4) * pl.count, cudaMemcpyHostToDevice),
-                     "copy plan");
-            pl.host.assign(plan.begin(), plan.begin() + pl.count);
-          }
-      }
+    // the side streams, events and priorities of the banded adjoint
+    auto band_streams = [&]() -> int {
       c->band = true;
       int least = 0, greatest = 0;
       PXA_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
@@ -592,6 +595,105 @@ int prepare(pxa_ctx* c) {
                "smem opt-in");
       // leave room for the kernel's static shared memory within the per-CTA limit
       c->reserve_smem = optin > 4096 ? (size_t)(optin - 2048) : 0;
+      return PXA_OK;
+    };
+    if (c->intervals >= 2) {
+      // multi-checkpoint scheme: C + 1 checkpoints and two interval buffer sets
+      const int C = c->intervals;
+      if (c->band_req == 0 || c->chain_len < 2)
+        return fail(c, PXA_ERR_INVALID, "the multi-checkpoint scheme needs the banded adjoint with two- or "
+                                        "four-step chain records (PXA_ADJ_BANDED or PXA_ADJ_BANDED_PAIR)");
+      if (c->K % ((int64_t)C * P) != 0)
+        return fail(c, PXA_ERR_INVALID, "the multi-checkpoint scheme needs K to be a multiple of C * P");
+      const int64_t Kc = c->K / C;
+      const size_t rows = (size_t)(Kc + 1) * n;
+      c->iv_spb = bu1_band_steps_per_block(Kc, n);
+      c->iv_blocks = (int)((Kc + c->iv_spb - 1) / c->iv_spb);
+      if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
+      if ((rc = alloc(c, &c->ckpt, (size_t)(C + 1) * n))) return rc;
+      if ((rc = alloc(c, &c->lamtop, n))) return rc;
+      if ((rc = alloc(c, &c->Jparts, 2))) return rc;
+      if ((rc = alloc(c, &c->ivW, (size_t)C * P * n))) return rc;
+      if ((rc = alloc(c, &c->gpart, (size_t)C * c->iv_blocks * n))) return rc;
+      for (auto& set : c->iv) {
+        if ((rc = alloc(c, &set.traj, rows))) return rc;
+        if ((rc = alloc(c, &set.rec, rows * BU1_BAND_RECORD))) return rc;
+        if ((rc = alloc(c, &set.jt, (size_t)Kc * n * BU1_BAND_RECORD))) return rc;
+        if ((rc = alloc(c, &set.rp, (size_t)(Kc / 2 + 1) * n * BU1_PAIR_RECORD))) return rc;
+        if (c->chain_len >= 4 && (rc = alloc(c, &set.rq, (size_t)(Kc / 4 + 1) * n * BU1_QUAD_RECORD)))
+          return rc;
+        if ((rc = alloc(c, &set.LI, rows))) return rc;
+        if ((rc = alloc(c, &set.H, rows))) return rc;
+      }
+      // chain plans of every interval, for the Paraexp partition (P subintervals of each
+      // interval) and for serial stepping: rows (i+1)K/C down to iK/C, the source on the
+      // interval's top subinterval, the lanes' values at the subinterval boundaries
+      // including the interval's bottom row
+      std::vector<int4> plan((size_t)c->K);
+      for (int ser = 0; ser < 2; ++ser)
+        for (int q4 = 0; q4 < (c->chain_len >= 4 ? 2 : 1); ++q4) {
+          const int Pe = ser ? 1 : P;
+          const int64_t kc = Kc / Pe;
+          std::vector<int>& off = c->iplan_off[ser][q4];
+          off.assign(1, 0);
+          for (int ci = 0; ci < C; ++ci) {
+            const int64_t a = ci * Kc;
+            const int cnt = bu1_chain_plan_range(a + Kc, a, kc, a + (Pe - 1) * kc, (int64_t)ci * Pe,
+                                                 (int64_t)ci * Pe + Pe - 2, q4 ? 4 : 2, plan.data() + off.back());
+            off.push_back(off.back() + cnt);
+          }
+          if ((rc = alloc(c, &c->iplan_dev[ser][q4], (size_t)off.back()))) return rc;
+          PXA_CUDA(c, cudaMemcpy(c->iplan_dev[ser][q4], plan.data(), sizeof(int4) * off.back(),
+                                 cudaMemcpyHostToDevice), "copy plan");
+        }
+      if ((rc = band_streams())) return rc;
+      PXA_CUDA(c, cudaStreamCreateWithPriority(&c->side3, cudaStreamNonBlocking, c->prio_lo), "side stream");
+      for (auto& row : c->ev_iv)
+        for (auto& e : row) PXA_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    } else {
+      if (c->memory == PXA_STORE_FULL) {
+        if ((rc = alloc(c, &c->traj, (size_t)(c->K + 1) * n))) return rc;
+      } else {
+        if ((rc = alloc(c, &c->traj, (size_t)(P + 1) * n))) return rc;
+        if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
+      }
+      // The banded adjoint keeps two records per step and point plus two lambda
+      // trajectories; it is used when that takes at most half of the free memory,
+      // otherwise the adjoint re-steps the stages (kernels_bu1_cluster.cu).
+      if ((rc = alloc(c, &c->sc, (size_t)3 * c->K))) return rc;
+      const size_t rows1 = (size_t)(c->K + 1) * n;
+      const size_t pair_doubles = c->chain_len >= 2 ? (size_t)(c->K / 2) * n * BU1_PAIR_RECORD : 0;
+      const size_t quad_doubles = c->chain_len >= 4 ? (size_t)(c->K / 4) * n * BU1_QUAD_RECORD : 0;
+      const size_t band_doubles = rows1 * BU1_BAND_RECORD + (size_t)c->K * n * BU1_BAND_RECORD +
+                                  2 * rows1 + (size_t)bu1_band_grad_blocks(c->K, n) * n + pair_doubles +
+                                  quad_doubles;
+      size_t free_b = 0, total_b = 0;
+      PXA_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+      if (c->band_req != 0 && band_doubles * sizeof(double) <= free_b / 2) {
+        if ((rc = alloc(c, &c->rec, rows1 * BU1_BAND_RECORD))) return rc;
+        if ((rc = alloc(c, &c->jt, (size_t)c->K * n * BU1_BAND_RECORD))) return rc;
+        if ((rc = alloc(c, &c->LI, rows1))) return rc;
+        if ((rc = alloc(c, &c->Hrows, rows1))) return rc;
+        if ((rc = alloc(c, &c->gpart, (size_t)bu1_band_grad_blocks(c->K, n) * n))) return rc;
+        if ((rc = alloc(c, &c->Jparts, pxa_ctx::kMaxChunks))) return rc;
+        if (c->chain_len >= 2) {
+          if ((rc = alloc(c, &c->rp, pair_doubles))) return rc;
+          if (c->chain_len >= 4 && (rc = alloc(c, &c->rq, quad_doubles))) return rc;
+          // step plans of the chain for the Paraexp partition and for serial stepping, with
+          // steps of up to two and of up to four rows
+          std::vector<int4> plan((size_t)c->K);
+          for (int ser = 0; ser < 2; ++ser)
+            for (int q4 = 0; q4 < (c->rq ? 2 : 1); ++q4) {
+              pxa_ctx::ChainPlan& pl = c->plans[ser][q4];
+              pl.count = bu1_chain_plan(c->K, ser ? c->K : k, ser ? 1 : P, q4 ? 4 : 2, plan.data());
+              if ((rc = alloc(c, &pl.dev, (size_t)pl.count))) return rc;
+              PXA_CUDA(c, cudaMemcpy(pl.dev, plan.data(), sizeof(int4) * pl.count, cudaMemcpyHostToDevice),
+                       "copy plan");
+              pl.host.assign(plan.begin(), plan.begin() + pl.count);
+            }
+        }
+        if ((rc = band_streams())) return rc;
+      }
     }
   }
   if (c->op.kind == PXA_BURGERS_1D) {
@@ -761,6 +863,148 @@ int bu1_chunk_bounds(int64_t K, int P, double r, int max_chunks, int64_t* b) {
   return NC;
 }
 
+// Base pointer of a buffer that holds rows first_row, first_row + 1, ... of row_len
+// doubles each, such that base + row * row_len addresses row `row`: the kernels index
+// their rows by absolute step and only touch the rows the buffer holds.
+double* rows_from(double* buf, int64_t first_row, size_t row_len) {
+  return reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(buf) -
+                                   (uintptr_t)((size_t)first_row * row_len * sizeof(double)));
+}
+
+// ---- 1D Burgers, multi-checkpoint scheme (Sec. 3.5) ----------------------------------
+// The direct keeps the states at t = iT/C and J (the rough pass). The adjoint takes the
+// intervals [iK/C, (i+1)K/C] from the top; interval i is re-stepped from its checkpoint,
+// its band (pair, four-step) records are built, the adjoint lanes of its lower P-1
+// subintervals run, and the chain steps it from lambda at its top row (computed by the
+// interval above; the objective's source at t = T for the top interval) down to its
+// bottom row with the source of its top subinterval and the lanes' values at the
+// subinterval boundaries. Then its skipped rows are filled and its gradient blocks
+// summed. Two buffer sets alternate, each prepared on a stream of its own: while the
+// chain runs on one interval, the next two intervals are being re-stepped and recorded.
+int enqueue_bu1_iv(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad, const double* sc) {
+  cudaStream_t st = c->stream;
+  const bool do_d = parts & 1, do_a = parts & 2;
+  const int n = c->op.n, C = c->intervals;
+  const int64_t K = c->K, Kc = K / C;
+  const int P = mode == PXA_SERIAL ? 1 : c->P;
+  const int64_t kc = Kc / P;
+  const double dt = c->T / (double)K;
+  if (P > 1 && c->kry_phi != PXA_PHI_STEPPER)
+    return fail(c, PXA_ERR_INVALID, "the multi-checkpoint scheme uses the stepper propagator (PXA_PHI_STEPPER)");
+  // with the adjoint in the same call, the rough pass keeps the top interval's states in
+  // buffer set 0 (its last K/C steps in a launch of their own), which spares their re-step
+  const bool keep_top = do_d && do_a;
+  if (do_d) {
+    ev_record(c, 0);
+    if (keep_top) {
+      PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, K - Kc, c->control, sc,
+                                       nullptr, nullptr, 0, c->target, c->T, c->Jparts, c->ckpt, Kc, c->status, 0,
+                                       0, c->q_direct), "rough direct");
+      PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, Kc, c->control,
+                                       sc ? sc + 3 * (K - Kc) : nullptr, c->ckpt + (size_t)(C - 1) * n,
+                                       c->iv[0].traj, Kc + 1, c->target, c->T, c->Jparts + 1, nullptr, 1,
+                                       c->status, 0, 0, c->q_direct), "rough direct, top interval");
+      PXA_CUDA(c, launch_sum_parts(st, 2, c->Jparts, Jdev, c->status), "J");
+    } else {
+      PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, K, c->control, sc,
+                                       nullptr, nullptr, 0, c->target, c->T, Jdev, c->ckpt, Kc, c->status, 0, 0,
+                                       c->q_direct), "rough direct");
+    }
+    ev_record(c, 1);
+  }
+  if (!do_a) return PXA_OK;
+  ev_record(c, 2);
+  ev_record(c, 3);
+  const bool four = c->chain_len >= 4 && bu1_chain4_valid(n, c->cl_band_chain);
+  if (!four && !bu1_chain2_valid(n, c->cl_band_chain))
+    return fail(c, PXA_ERR_INVALID, "no chain kernel fits the grid for the multi-checkpoint scheme");
+  const int ser = P == 1 ? 1 : 0;
+  const int4* plans = c->iplan_dev[ser][four ? 1 : 0];
+  const std::vector<int>& off = c->iplan_off[ser][four ? 1 : 0];
+  constexpr size_t RWd = BU1_BAND_RECORD, PWd = BU1_PAIR_RECORD, QWd = BU1_QUAD_RECORD;
+  cudaEvent_t* const ev_rec = c->ev_iv[0];
+  cudaEvent_t* const ev_chain = c->ev_iv[2];
+  cudaEvent_t* const ev_free = c->ev_iv[3];
+  // each buffer set has its own stream for the re-step, records and lanes, so that the
+  // two sets are prepared at the same time; the fills and gradients go to side2
+  cudaStream_t const prep_st[2] = {c->side, c->side3};
+  PXA_CUDA(c, cudaEventRecord(c->ev_fork[0], st), "fork");
+  for (cudaStream_t s2 : {c->side, c->side2, c->side3}) PXA_CUDA(c, cudaStreamWaitEvent(s2, c->ev_fork[0], 0), "fork wait");
+  // re-step, records and lanes of interval number idx (from the top) into its buffer set
+  auto prep = [&](int idx) -> int {
+    const int ci = C - 1 - idx, set = idx & 1;
+    const int64_t a = ci * Kc, b = a + Kc;
+    const pxa_ctx::IntervalSet& B = c->iv[set];
+    cudaStream_t ps = prep_st[set];
+    if (idx >= 2) PXA_CUDA(c, cudaStreamWaitEvent(ps, ev_free[set], 0), "buffers free");
+    if (!(idx == 0 && keep_top))
+      PXA_CUDA(c, launch_bu1_rk4_sweep(ps, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, Kc, c->control,
+                                       sc ? sc + 3 * a : nullptr, c->ckpt + (size_t)ci * n, B.traj, Kc + 1,
+                                       nullptr, c->T, nullptr, nullptr, 1, c->status, c->prio_lo, 0,
+                                       c->q_direct), "interval re-step");
+    double* rec = rows_from(B.rec, a, n * RWd);
+    PXA_CUDA(c, launch_bu1_band_prepass(ps, n, c->op.L, c->op.nu, dt, c->T, c->omega, c->control,
+                                        c->target, rows_from(B.traj, a, n), 0, 1, a, b == K ? b + 1 : b, K,
+                                        rec, rows_from(B.jt, a, n * RWd), c->prio_lo), "band prepass");
+    const int64_t m_lo = (a + 1) / 2, q_lo = (a + 3) / 4;
+    PXA_CUDA(c, launch_bu1_band_pair(ps, n, rec, m_lo, b / 2, rows_from(B.rp, m_lo, n * PWd), c->prio_lo),
+             "pair records");
+    if (four)
+      PXA_CUDA(c, launch_bu1_band_quad(ps, n, rows_from(B.rp, m_lo, n * PWd), q_lo, b / 4,
+                                       rows_from(B.rq, q_lo, n * QWd), c->prio_lo), "four-step records");
+    if (P > 1)
+      PXA_CUDA(c, launch_bu1_band_sweep(ps, c->cl_band_lanes, P - 1, ci * P, n, rec, kc, P, 0, nullptr,
+                                        rows_from(B.LI, a, n), c->ivW, c->status, c->prio_lo, c->q_sweep),
+               "band lanes");
+    PXA_CUDA(c, cudaEventRecord(ev_rec[set], ps), "interval ready");
+    return PXA_OK;
+  };
+  int rc;
+  if ((rc = prep(0))) return rc;
+  if (C > 1 && (rc = prep(1))) return rc;
+  for (int idx = 0; idx < C; ++idx) {
+    const int ci = C - 1 - idx, set = idx & 1;
+    const int64_t a = ci * Kc, b = a + Kc;
+    const pxa_ctx::IntervalSet& B = c->iv[set];
+    const double* rec = rows_from(B.rec, a, n * RWd);
+    const double* rp = rows_from(B.rp, (a + 1) / 2, n * PWd);
+    double* H = rows_from(B.H, a, n);
+    PXA_CUDA(c, cudaStreamWaitEvent(st, ev_rec[set], 0), "interval wait");
+    // lambda at the top row: the value the interval above left
+    if (idx > 0)
+      PXA_CUDA(c, cudaMemcpyAsync(B.H + (size_t)Kc * n, c->lamtop, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                  st), "interval top");
+    const int4* pl = plans + off[ci];
+    const int np = off[ci + 1] - off[ci];
+    const double* from = idx > 0 ? H : nullptr;
+    if (four)
+      PXA_CUDA(c, launch_bu1_band_chain4(st, c->cl_band_chain, n, rec, rp, rows_from(B.rq, (a + 3) / 4, n * QWd),
+                                         pl, np, (int)b, from, c->ivW, H, c->status, c->prio_hi,
+                                         c->reserve_smem), "band chain");
+    else
+      PXA_CUDA(c, launch_bu1_band_chain2(st, c->cl_band_chain, n, rec, rp, pl, np, (int)b, from, c->ivW, H,
+                                         c->status, c->prio_hi, c->reserve_smem), "band chain");
+    if (ci > 0) PXA_CUDA(c, launch_bu1_band_top(st, n, B.H, B.rec, c->lamtop), "interval bottom");
+    PXA_CUDA(c, cudaEventRecord(ev_chain[set], st), "chain done");
+    // the rows skipped by the chain's steps, then the interval's gradient blocks
+    PXA_CUDA(c, cudaStreamWaitEvent(c->side2, ev_chain[set], 0), "chain wait");
+    if (four) PXA_CUDA(c, launch_bu1_band_fill4(c->side2, n, rec, rp, pl, np, H, c->prio_lo), "band fill");
+    PXA_CUDA(c, launch_bu1_band_fill(c->side2, n, rec, pl, np, H, c->prio_lo), "band fill");
+    PXA_CUDA(c, launch_bu1_band_grad_range(c->side2, n, dt, c->omega, a, b, c->iv_spb, a + (P - 1) * kc,
+                                           P > 1 ? rows_from(B.LI, a, n) : nullptr, H,
+                                           rows_from(B.jt, a, n * RWd), c->gpart, ci * c->iv_blocks,
+                                           c->prio_lo), "band gradient");
+    PXA_CUDA(c, cudaEventRecord(ev_free[set], c->side2), "buffers free");
+    if (idx + 2 < C && (rc = prep(idx + 2))) return rc;
+  }
+  ev_record(c, 4);
+  PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side2), "join");
+  PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
+  PXA_CUDA(c, launch_bu1_band_reduce_blocks(st, n, C * c->iv_blocks, c->gpart, grad, c->status), "gradient sum");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
 // ---- 1D Burgers (forcing control, tracking objective), hybrid scheme ----------
 int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
@@ -779,6 +1023,7 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     PXA_CUDA(c, launch_bu1_forcing_table(st, K, dt, c->omega, c->sc), "forcing table");
     sc = c->sc;
   }
+  if (c->intervals >= 2) return enqueue_bu1_iv(c, mode, parts, Jdev, grad, sc);
   // Banded adjoint layout: the stepper chain covers the top subinterval itself (so lanes
   // 0..P-2 run separately); with exp(tA) (Magnus) all P lanes run and the chain uses W[P-1].
   const bool chain_top = c->band && (P == 1 || c->kry_phi == PXA_PHI_STEPPER);
@@ -1207,6 +1452,15 @@ int pxa_set_memory(pxa_ctx* c, int policy) {
   return PXA_OK;
 }
 
+int pxa_set_checkpoints(pxa_ctx* c, int intervals) {
+  if (!c || intervals < 0 || intervals > 65536) return PXA_ERR_INVALID;
+  c->intervals = intervals >= 2 ? intervals : 0;
+  c->stats.checkpoint_intervals = c->intervals;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
 int pxa_set_adjoint(pxa_ctx* c, int impl) {
   if (!c || (impl != PXA_ADJ_BANDED && impl != PXA_ADJ_RESTEP && impl != PXA_ADJ_BANDED_SINGLE &&
              impl != PXA_ADJ_BANDED_PAIR))
@@ -1580,7 +1834,7 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
       }
     c->q_direct = bqd;
     c->q_sweep = bqs;
-    if (c->overlap && c->memory == PXA_STORE_FULL && c->side) {
+    if (c->overlap && c->memory == PXA_STORE_FULL && c->side && c->intervals < 2) {
       // third pass: the chunk partition of the overlapped direct solve (Sec. 3.3).
       // k = tau_I_adj / tau_I comes from one run with the phases in sequence (direct;
       // band records and adjoint lanes); then equal chunks, r = k/(k+1) and r = k are

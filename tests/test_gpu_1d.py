@@ -571,6 +571,88 @@ def test_burgers_four_step_chain(X, torch, n, C, K, P):
         assert rel(res[(X.ADJ_BANDED, mode)], res[(X.ADJ_BANDED_PAIR, mode)]) < 1e-12
 
 
+# ---- multi-checkpoint scheme (Sec. 3.5) ----------------------------------------------------
+@pytest.mark.parametrize("n,C,K,P,nint", [(200, 4, 630, 6, 5), (100, 1, 600, 4, 3), (48, 3, 210, 3, 7),
+                                           (512, 16, 400, 5, 2), (64, 2, 105, 1, 5), (64, 2, 120, 4, 30),
+                                           (96, 4, 132, 2, 6)])
+def test_burgers_multi_checkpoint_matches_oracle(X, torch, n, C, K, P, nint):
+    """The rough pass keeps nint + 1 checkpoints; every interval is re-stepped and solved by
+    the Paraexp adjoint over its own P subintervals from the adjoint value its upper
+    neighbour left. Intervals starting on rows that are not multiples of 2 or 4 (pair and
+    four-step records offset), one-step subintervals (a lane value on every row), odd
+    interval counts (the two buffer sets end unevenly), clusters of 1 to 16 CTAs, serial
+    and Paraexp modes, with sin(omega t) forcing: the gradient is the oracle's and that of
+    full storage."""
+    nu, T = 0.02, 0.25
+    f = 2.0 * I.fourier1d(n, 8, 91)
+    g = I.fourier1d(n, 8, 92)
+    J0, g0 = O.bu1_gradient_serial(f, g, nu, T, K, omega=1.5)
+    fd, gd_ = dev(torch, f), dev(torch, g)
+    for impl in (X.ADJ_BANDED, X.ADJ_BANDED_PAIR):
+        ref = bu1_ctx(X, n, nu, T, K, P, phi=X.PHI_STEPPER)
+        ref.set_adjoint(impl)
+        ref.set_cluster(0, 0, C)
+        ref.set_control(fd, 1.5)
+        ref.set_target(gd_)
+        ctx = bu1_ctx(X, n, nu, T, K, P, phi=X.PHI_STEPPER)
+        ctx.set_adjoint(impl)
+        ctx.set_cluster(0, 0, C)
+        ctx.set_checkpoints(nint)
+        ctx.set_control(fd, 1.5)
+        ctx.set_target(gd_)
+        out, out_ref = torch.empty_like(fd), torch.empty_like(fd)
+        for mode in (X.SERIAL, X.PARAEXP):
+            J = ctx.gradient(mode, out)
+            ref.gradient(mode, out_ref)
+            assert abs(J - J0) / J0 < 1e-10
+            assert rel(host(out), g0) < 1e-10, (impl, mode)
+            assert rel(host(out), host(out_ref)) < 1e-12, (impl, mode)
+        st = ctx.stats()
+        assert st["checkpoint_intervals"] == nint
+        assert st["cluster_chain"] == C
+        ctx.close()
+        ref.close()
+
+
+def test_burgers_multi_checkpoint_graph_split_and_memory(X, torch, bu_small):
+    """Graph replay, a direct solve followed by the adjoint solve, and the workspace: two
+    interval buffer sets take a fraction of the full-storage workspace."""
+    b = bu_small
+    fd, gd_ = dev(torch, b["f"]), dev(torch, b["g"])
+    full = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    full.set_control(fd)
+    full.set_target(gd_)
+    out = torch.empty_like(fd)
+    full.gradient(X.PARAEXP, out)
+    ws_full = full.stats()["workspace_bytes"]
+    full.close()
+    ctx = bu1_ctx(X, b["n"], b["nu"], b["T"], b["K"], 6, phi=X.PHI_STEPPER)
+    ctx.set_checkpoints(10)
+    ctx.set_control(fd)
+    ctx.set_target(gd_)
+    ctx.set_graph(True)
+    for _ in range(2):
+        J = ctx.gradient(X.PARAEXP, out)
+        assert abs(J - b["J"]) / b["J"] < 1e-10
+        assert rel(host(out), b["grad"]) < 1e-10
+    ctx.set_graph(False)
+    out2 = torch.zeros_like(fd)
+    J = ctx.solve_direct(X.PARAEXP)
+    ctx.solve_adjoint(X.PARAEXP, out2)
+    assert abs(J - b["J"]) / b["J"] < 1e-10
+    assert rel(host(out2), host(out)) < 1e-14
+    assert ctx.stats()["workspace_bytes"] < 0.35 * ws_full
+    # K = 600 is not a multiple of 7 x 6; the exponential propagator is not supported
+    ctx.set_checkpoints(7)
+    with pytest.raises(X.PxaError):
+        ctx.gradient(X.PARAEXP, out)
+    ctx.set_checkpoints(5)
+    ctx.set_krylov(30, 1e-10, X.PHI_EXP, 1)
+    with pytest.raises(X.PxaError):
+        ctx.gradient(X.PARAEXP, out)
+    ctx.close()
+
+
 # ---- real Leja points method (Sec. 4.1) ----------------------------------------------------
 @pytest.mark.parametrize("phi", ["exp", "stepper"])
 @pytest.mark.parametrize("n,c,nu,span", [(256, 1.0, 0.01, 512), (64, 1.0, 0.0, 1200), (128, 0.0, 0.05, 800),
