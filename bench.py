@@ -731,9 +731,13 @@ def run_batch(args, w, rank, world):
         return t
 
     variants, errs, bats = {}, {}, {}
-    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+    # Paraexp with the stepper's subinterval propagator as one band of M^(K/P) (default),
+    # Paraexp with K/P CN steps per link instead, and serial stepping
+    for name, mode, power in (("paraexp", X.PARAEXP, True), ("paraexp_stepped_links", X.PARAEXP, False),
+                              ("serial", X.SERIAL, True)):
         b = X.Batch()
         b.set(prob["n"], prob["nu"], c=w["c"], T=w["T"], K=K, P=P)
+        b.set_power(power)
         best = b.autotune(mode, q0, J, g) if mode == X.PARAEXP else None
         with ClockSampler(dev_index) as clk:
             t = timed(b, mode, args.steps, args.warmup)
@@ -753,7 +757,13 @@ def run_batch(args, w, rank, world):
                           "krylov_m": st["krylov_m"], "krylov_reach": st["krylov_reach"],
                           "hom_ratio": st["hom_ratio"], "krylov_problems": st["krylov_problems"],
                           "substeps_max": st["substeps_max"], "lanes_grid": st["lanes_grid"],
-                          "band32_max": st["band32_max"], "clocks": clk.summary()}
+                          "band32_max": st["band32_max"], "power_problems": st["power_problems"],
+                          "band_power_max": st["band_power_max"], "clocks": clk.summary()}
+        # kernels per gradient: sources, lanes, superposition, adjoint lanes, gradient, and
+        # per direction one chain launch for each kind of homogeneous propagation in use
+        kinds = sum(1 for c in (st["krylov_problems"], st["power_problems"],
+                                cnt - st["krylov_problems"] - st["power_problems"]) if c > 0)
+        variants[name]["kernels_per_step"] = 4 if mode == X.SERIAL else 5 + 2 * kinds
         bats[name] = b
     head = "paraexp"
     ms = variants[head]["ms_per_step"]
@@ -807,7 +817,7 @@ def run_batch(args, w, rank, world):
             "e2e": {"value": world * cnt / float(np.mean(te)), "unit": "gradient evals/s (problems x gradients)",
                     "h2d_bytes_per_step": 8 * int(q0.numel()),
                     "d2h_bytes_per_step": 8 * int(q0.numel()) + 8 * cnt},
-            "clocks": variants[head]["clocks"], "gpu_launches": 11 * args.steps}
+            "clocks": variants[head]["clocks"], "gpu_launches": variants[head]["kernels_per_step"] * args.steps}
 
 
 def main():

@@ -351,7 +351,8 @@ int pxa_expv_static(int device, void* cuda_stream, const pxa_operator_desc* op, 
  * mode, one serial lane of K steps per problem in serial mode) step the exact circulant
  * Crank-Nicolson band in FP32 with FP32 accumulation, taken from a cost-sorted work list
  * by a persistent grid; the homogeneous propagations (Eq. hom / Eq. adjHomNormal) are
- * Krylov exponentials exp(tau A) in FP64, and the superpositions are FP64.
+ * Krylov exponentials exp(tau A) in FP64 or the stepper's own propagator M^(K/P) in FP32
+ * (pxa_batch_set_homogeneous, pxa_batch_set_power), and the superpositions are FP64.
  *
  * Packed layout: problem i owns points [off_i, off_i + n[i]) of every packed vector
  * (off_0 = 0, off_{i+1} = off_i + n[i]; pxa_batch_offsets returns them). */
@@ -374,6 +375,8 @@ typedef struct {
   float ms_adjoint_lanes;   /*   adjoint lanes (with the superposition before them), */
   float ms_adjoint_chains;  /*   adjoint chains, */
   float ms_total;           /*   the whole gradient */
+  int power_problems;       /* problems whose homogeneous parts apply the band of M^(K/P) */
+  int band_power_max;       /* widest band of M^(K/P) in use (taps; 0: none) */
 } pxa_batch_stats;
 /* Create / destroy a batch context on `device`; `cuda_stream` is borrowed (NULL = the
  * default stream). */
@@ -391,12 +394,20 @@ int pxa_batch_set(pxa_batch* b, int count, const int* n, const double* nu, doubl
  * 1e-8 needs reach of a few hundredths). */
 int pxa_batch_set_krylov(pxa_batch* b, int m, double tol, double reach);
 /* Homogeneous propagation per problem (Paraexp mode): the Krylov exponential exp(tau A)
- * of Eq. hom (FP64), or the local chained form with the stepper's own propagator (the
- * CN band, FP32: the summed homogeneous problems stepped subinterval by subinterval,
- * which reproduces serial stepping). A problem uses the exponential when a cost model
- * puts it at most `ratio` times the stepping (ratio >= 0; 0 = always step, default 1;
- * a very large ratio = always the exponential). */
+ * of Eq. hom (FP64), or the local chained form with the stepper's own propagator M^(K/P)
+ * (FP32: the summed homogeneous problems carried subinterval by subinterval, which
+ * reproduces serial stepping). A problem uses the exponential when a cost model puts it
+ * at most `ratio` times the stepper's propagator (ratio >= 0; 0 = never, default 1; a
+ * very large ratio = always the exponential). */
 int pxa_batch_set_homogeneous(pxa_batch* b, double ratio);
+/* How the stepper's propagator M^(K/P) is applied (Paraexp mode). enable = 1 (default):
+ * M is circulant (periodic grid, constant coefficients), so M^(K/P) is the circulant band
+ * whose taps are the inverse DFT of R_k^(K/P) (R_k the CN eigenvalues; taps kept to
+ * 2^-36 of the largest), built on the host and applied once per link in FP32: a link
+ * costs one band product instead of K/P CN steps. Problems whose band is wider than
+ * 2 BATCH_MAX_RP + 1 = 2049 taps step instead. enable = 0: every link takes K/P CN steps.
+ * Invalidates the workspace. */
+int pxa_batch_set_power(pxa_batch* b, int enable);
 /* Capture the whole gradient into a CUDA graph and replay it (1, default) or launch the
  * kernels one by one (0). */
 int pxa_batch_set_graph(pxa_batch* b, int enable);

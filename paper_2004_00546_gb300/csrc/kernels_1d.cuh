@@ -21,6 +21,8 @@ cudaError_t launch_ad1_stream_fill(cudaStream_t st, int n, int lanes, const doub
 cudaError_t launch_ad1_stream_out(cudaStream_t st, size_t total, const float* x, double* out);
 // Host: taps m_j (|j| <= r) of the circulant Crank-Nicolson map of the stencil (am, a0, ap).
 void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps, int& r);
+void cn_power_taps(int n, double am, double a0, double ap, double dt, int64_t steps, int cut_exp,
+                   std::vector<double>& taps, int& r);
 
 cudaError_t launch_cn_lanes(cudaStream_t st, int lanes, int threads, int n, int r,
                             const double* taps, int transpose, int64_t steps, const double* x0,

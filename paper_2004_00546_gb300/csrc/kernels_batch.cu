@@ -136,17 +136,19 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_lanes_kernel(
   }
 }
 
-// ---- homogeneous chains by stepping (the local chained form) --------------------------
+// ---- homogeneous chains with the stepper's own propagator (the local chained form) ---
 // items[it] = {problem, 0}: x = 0; for l < links: x += E[first + l * stride] (FP64 lane end
 // states, packed with `lanes` lanes per problem); x <- M^steps x (M^T when `transpose`) in
 // FP32; the result goes to hout (FP64 packed). This is the homogeneous propagation of
 // Eq. hom / Eq. adjHomNormal with the stepper's own propagator, carried subinterval by
-// subinterval.
+// subinterval: by `steps` CN steps, or (power == 1) by one application of the circulant
+// band of M^(K/P) itself (the problem's rp, tpw), whose taps the host takes from the
+// eigenvalues R_k^(K/P). A link then costs one band product instead of K/P.
 template <int PPT>
 __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
     const BatchInst* __restrict__ inst, const int2* __restrict__ items, int nitems, int* counter,
     const float* __restrict__ taps32, int transpose, int64_t steps, const double* __restrict__ E,
-    int lanes, int first, int stride, int links, double* __restrict__ hout) {
+    int lanes, int first, int stride, int links, double* __restrict__ hout, int power) {
   extern __shared__ float smf[];
   __shared__ int cur;
   for (;;) {
@@ -155,11 +157,12 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
     const int it = cur;
     if (it >= nitems) return;  // the same for every thread of the block
     const BatchInst I = inst[items[it].x];
-    const int n = I.n, r = I.r32, w = 2 * r + 1;
+    const int n = I.n, r = power ? I.rp : I.r32, w = 2 * r + 1;
+    const int64_t nst = power ? 1 : steps;
     float *tp, *xa, *xb, *sr;
     int wp;
     lane_layout<PPT>(smf, n, r, w, tp, wp, xa, xb, sr);
-    const float* tg = taps32 + I.t32;
+    const float* tg = taps32 + (power ? I.tpw : I.t32);
     const double* Ei = E + I.off * lanes;
     for (int j = threadIdx.x; j < wp; j += blockDim.x) tp[j] = j < w ? (transpose ? tg[w - 1 - j] : tg[j]) : 0.f;
     for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, 0.f);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_cn_chain_kernel(
       const double* e = Ei + (int64_t)(first + l * stride) * n;
       for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, xa[r + p] + (float)e[p]);
       __syncthreads();
-      for (int64_t s = 0; s < steps; ++s) {
+      for (int64_t s = 0; s < nst; ++s) {
         band_step32<PPT>(tp, wp, xa, xb, nullptr, n, r);
         __syncthreads();
         float* t = xa;
@@ -349,7 +352,7 @@ cudaError_t launch_batch_chain(cudaStream_t st, const BatchInst* inst, const int
 cudaError_t launch_batch_cn_chain(cudaStream_t st, int grid, const BatchInst* inst, const int2* items,
                                   int nitems, int* counter, const float* taps32, int transpose,
                                   int64_t steps, const double* E, int lanes, int first, int stride,
-                                  int links, double* hout, int nmax, int rmax) {
+                                  int links, double* hout, int nmax, int rmax, int power) {
   if (nitems <= 0 || links <= 0) return cudaSuccess;
   const size_t sh = batch_lanes_smem(nmax, rmax);
   const bool small = small_lanes(nmax);
@@ -360,10 +363,10 @@ cudaError_t launch_batch_cn_chain(cudaStream_t st, int grid, const BatchInst* in
   if (e != cudaSuccess) return e;
   if (small)
     batch_cn_chain_kernel<PPT_SMALL><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose, steps,
-                                                               E, lanes, first, stride, links, hout);
+                                                               E, lanes, first, stride, links, hout, power);
   else
     batch_cn_chain_kernel<PPT_LARGE><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, counter, taps32, transpose,
-                                                                steps, E, lanes, first, stride, links, hout);
+                                                                steps, E, lanes, first, stride, links, hout, power);
   return cudaGetLastError();
 }
 

@@ -13,10 +13,12 @@ struct BatchInst {
   int r32;       // half-width of the FP32 Crank-Nicolson band used by the lanes
   int r64;       // half-width of the FP64 band used for the sources
   int nsub;      // Krylov substeps per subinterval
+  int rp;        // half-width of the FP32 band of M^(K/P), the subinterval propagator (0: none)
   int64_t off;   // first point of the problem in the packed vectors
   int64_t t32;   // first tap of its FP32 band
   int64_t t64;   // first tap of its FP64 band
   int64_t voff;  // first double of its Krylov basis ((m+1) x n)
+  int64_t tpw;   // first tap of its subinterval-propagator band (in the FP32 taps)
   double am, a0, ap;  // stencil of A
   double hsub;   // Krylov substep length (tau / nsub)
 };
@@ -24,6 +26,7 @@ struct BatchInst {
 constexpr int BATCH_THREADS = 256;
 constexpr int BATCH_MAX_N = 4096;
 constexpr int BATCH_MAX_R = 255;  // widest FP32 band a lane keeps in shared memory
+constexpr int BATCH_MAX_RP = 1024;  // widest subinterval-propagator band a chain applies
 
 size_t batch_lanes_smem(int nmax, int rmax);
 int batch_lanes_grid(int device, int nmax, int rmax);
@@ -37,10 +40,12 @@ cudaError_t launch_batch_chain(cudaStream_t st, const BatchInst* inst, const int
                                int m, int transpose, const double* E, int lanes, int first, int stride,
                                int links, double* hout, double* V, double tol, int* status,
                                double* errmax);
+// power == 1: one application per link of the problem's band of M^(K/P) (rp, tpw)
+// instead of `steps` CN steps.
 cudaError_t launch_batch_cn_chain(cudaStream_t st, int grid, const BatchInst* inst, const int2* items,
                                   int nitems, int* counter, const float* taps32, int transpose,
                                   int64_t steps, const double* E, int lanes, int first, int stride,
-                                  int links, double* hout, int nmax, int rmax);
+                                  int links, double* hout, int nmax, int rmax, int power);
 cudaError_t launch_batch_superpose_direct(cudaStream_t st, const BatchInst* inst, int count, int nmax,
                                           const double* taps64, const double* q0, const double* E,
                                           int lanes, int last, const double* h, double* qT,

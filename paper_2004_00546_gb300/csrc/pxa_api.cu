@@ -77,6 +77,61 @@ void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector
     cn_band_taps_t<double>(n, am, a0, ap, dt, 50, taps, r);
 }
 
+// Taps m_j (|j| <= r) of the power M^steps of the circulant Crank-Nicolson map: the
+// propagator of the stepper over `steps` steps, itself circulant with eigenvalues R_k^steps
+// (R_k as in cn_band_taps; powers by repeated squaring, double sums). Advection shifts its
+// peak by about (am - ap) steps dt points, so the band is cut relative to the largest tap:
+// past the shift, once both |m_j| and |m_-j| stay below 2^-cut_exp max|m| for four
+// consecutive offsets (or at n/2, the full circulant). The band is stored symmetric.
+void cn_power_taps(int n, double am, double a0, double ap, double dt, int64_t steps, int cut_exp,
+                   std::vector<double>& taps, int& r) {
+  typedef std::complex<double> C;
+  const double pi = 3.141592653589793238462643383279502884;
+  std::vector<C> Rp(n), w(n);
+  for (int k = 0; k < n; ++k) {
+    const double ph = 2.0 * pi * (double)k / (double)n;
+    w[k] = C(std::cos(ph), std::sin(ph));
+  }
+  const double th = 0.5 * dt;
+  for (int k = 0; k < n; ++k) {
+    const C lam = a0 + am * std::conj(w[k]) + ap * w[k];
+    C base = (1.0 + th * lam) / (1.0 - th * lam), acc = 1.0;
+    for (int64_t e = steps; e > 0; e >>= 1) {
+      if (e & 1) acc *= base;
+      base *= base;
+    }
+    Rp[k] = acc;
+  }
+  auto tap = [&](int j) {
+    C s = 0.0;
+    const long long jj = ((j % n) + n) % n;
+    for (int k = 0; k < n; ++k) s += Rp[k] * std::conj(w[(size_t)(((long long)k * jj) % n)]);
+    return s.real() / (double)n;
+  };
+  const double shift = std::fabs(am - ap) * (double)steps * dt;
+  std::vector<double> pos, neg;  // pos[j] = m_j, neg[j] = m_-j
+  const double m0 = tap(0);
+  pos.push_back(m0);
+  neg.push_back(m0);
+  double big = std::fabs(m0);
+  const int rmax = n / 2;
+  int quiet = 0;
+  r = 0;
+  for (int j = 1; j <= rmax; ++j) {
+    const double mn = tap(-j);
+    const double mp = (2 * j == n) ? 0.0 : tap(j);
+    pos.push_back(mp);
+    neg.push_back(mn);
+    r = j;
+    big = std::max(big, std::max(std::fabs(mp), std::fabs(mn)));
+    const double thr = std::ldexp(big, -cut_exp);
+    quiet = (std::fabs(mp) < thr && std::fabs(mn) < thr) ? quiet + 1 : 0;
+    if ((double)j > shift + 4.0 && quiet >= 4) break;
+  }
+  taps.assign(2 * r + 1, 0.0);
+  for (int j = -r; j <= r; ++j) taps[r + j] = j >= 0 ? pos[j] : neg[-j];
+}
+
 // Real Leja points method (Sec. 4.1), host part. Leja points of [-2, 2]: 2 first, then
 // each point maximises the sum of log distances to the earlier ones, searched on a
 // uniform grid of 2^15 + 1 points.

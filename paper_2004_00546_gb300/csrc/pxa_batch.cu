@@ -34,7 +34,8 @@ struct pxa_batch {
   int P = 1;
   int m = 30;
   double tol = 1e-8, reach = 0.04;
-  double hom_ratio = 1.0;  // Krylov exponential where the cost model puts it <= ratio x stepping
+  double hom_ratio = 1.0;  // Krylov exponential where the cost model puts it <= ratio x the stepper's propagator
+  bool power = true;       // the stepper's propagator over a subinterval as one band of M^(K/P)
   bool use_graph = true;
 
   // set-up (host)
@@ -43,6 +44,7 @@ struct pxa_batch {
   std::vector<int64_t> off;
   int64_t total = 0;
   int nmax = 0, r32max = 0, r64max = 0, subs_max = 0, lanes_grid = 0;
+  int rpmax = 0, pow_grid = 0;  // widest subinterval-propagator band; its chains' grid
 
   // workspace (device)
   std::vector<void*> allocs;
@@ -53,7 +55,8 @@ struct pxa_batch {
   int2* items_ser = nullptr;
   int2* items_step = nullptr;  // problems whose homogeneous parts are stepped
   int* kry_list = nullptr;     // problems whose homogeneous parts use the exponential
-  int n_step = 0, n_kry = 0;
+  int2* items_pow = nullptr;   // problems whose homogeneous parts apply the band of M^(K/P)
+  int n_step = 0, n_kry = 0, n_pow = 0;
   std::vector<int> uses_krylov;  // per problem
   int* counter = nullptr;
   double *src = nullptr, *E = nullptr, *EA = nullptr, *h = nullptr, *hA = nullptr, *qT = nullptr,
@@ -102,9 +105,9 @@ void brelease(pxa_batch* b) {
   b->inst = nullptr;
   b->taps32 = nullptr;
   b->taps64 = nullptr;
-  b->items_par = b->items_ser = b->items_step = nullptr;
+  b->items_par = b->items_ser = b->items_step = b->items_pow = nullptr;
   b->kry_list = nullptr;
-  b->n_step = b->n_kry = 0;
+  b->n_step = b->n_kry = b->n_pow = 0;
   b->counter = b->status = nullptr;
   b->src = b->E = b->EA = b->h = b->hA = b->qT = b->srcT = b->V = b->errmax = nullptr;
   b->bytes = 0;
@@ -137,7 +140,8 @@ int bprepare(pxa_batch* b) {
   b->off.assign(cnt + 1, 0);
   std::vector<float> t32;
   std::vector<double> t64;
-  b->nmax = b->r32max = b->r64max = b->subs_max = 0;
+  b->nmax = b->r32max = b->r64max = b->subs_max = b->rpmax = 0;
+  const int64_t kp = b->K / P;  // steps per subinterval
   for (int i = 0; i < cnt; ++i) {
     const int n = b->n[i];
     const double h = b->L / n;
@@ -161,6 +165,20 @@ int bprepare(pxa_batch* b) {
     I.t32 = (int64_t)t32.size();
     t64.insert(t64.end(), taps.begin(), taps.end());
     for (int j = -r32; j <= r32; ++j) t32.push_back((float)taps[r + j]);
+    // the subinterval propagator M^(K/P) as one band, kept to 2^-36 of its largest tap
+    // (far below FP32 rounding); problems whose band is wider step instead
+    I.rp = 0;
+    I.tpw = 0;
+    if (b->power && P > 1) {
+      std::vector<double> pt;
+      int rp = 0;
+      cn_power_taps(n, I.am, I.a0, I.ap, dt, kp, 36, pt, rp);
+      if (rp <= BATCH_MAX_RP) {
+        I.rp = rp;
+        I.tpw = (int64_t)t32.size();
+        for (double v : pt) t32.push_back((float)v);
+      }
+    }
     I.off = b->off[i];
     b->off[i + 1] = b->off[i] + n;
     I.voff = (int64_t)(kMaxM + 1) * I.off;
@@ -172,6 +190,7 @@ int bprepare(pxa_batch* b) {
     b->nmax = std::max(b->nmax, n);
     b->r32max = std::max(b->r32max, r32);
     b->r64max = std::max(b->r64max, r);
+    b->rpmax = std::max(b->rpmax, I.rp);
     b->subs_max = std::max(b->subs_max, I.nsub);
   }
   b->total = b->off[cnt];
@@ -196,25 +215,33 @@ int bprepare(pxa_batch* b) {
   });
   // homogeneous propagation per problem: the Krylov exponential (FP64, one block per
   // problem: nsub substeps of an m-step Arnoldi with CGS2, ~2 m^2 n + 10 m n flop, at
-  // one SM's FP64 rate) or stepping (k CN steps per link in FP32 at one SM's FP32 rate,
-  // but at least ~0.5 us per step, the latency of a step's barrier and band loads)
+  // one SM's FP64 rate) or the stepper's own propagator: one product with the band of
+  // M^(K/P) per link where it exists, else k CN steps per link, in FP32 at one SM's FP32
+  // rate but at least ~0.5 us per product (the latency of its barrier and band loads)
   const int64_t k = b->K / P;
   std::vector<int> kry;
-  std::vector<int2> istep;
+  std::vector<int2> istep, ipow;
   for (int i : order) {
     const BatchInst& I = b->hinst[i];
     const double n = I.n, mm = b->m;
     const double t_kry = I.nsub * (2.0 * mm * mm * n + 10.0 * mm * n) / 8.2e9;
-    const double t_step = (double)k * std::max(2.0 * n * (2 * I.r32 + 1) / 2.65e11, 5e-7);
+    const double t_step = I.rp > 0 ? std::max(2.0 * n * (2 * I.rp + 1) / 2.65e11, 5e-7)
+                                   : (double)k * std::max(2.0 * n * (2 * I.r32 + 1) / 2.65e11, 5e-7);
     if (P > 1 && t_kry <= b->hom_ratio * t_step)
       kry.push_back(i);
+    else if (I.rp > 0)
+      ipow.push_back(make_int2(i, 0));
     else
       istep.push_back(make_int2(i, 0));
   }
+  std::stable_sort(ipow.begin(), ipow.end(), [&](const int2& x, const int2& y) {
+    return (double)b->hinst[x.x].n * (2 * b->hinst[x.x].rp + 1) > (double)b->hinst[y.x].n * (2 * b->hinst[y.x].rp + 1);
+  });
   b->uses_krylov.assign(cnt, 0);
   for (int i : kry) b->uses_krylov[i] = 1;
   b->n_kry = (int)kry.size();
   b->n_step = (int)istep.size();
+  b->n_pow = (int)ipow.size();
   int rc;
   const size_t tot = (size_t)b->total;
   if ((rc = balloc(b, &b->inst, cnt))) return rc;
@@ -223,6 +250,7 @@ int bprepare(pxa_batch* b) {
   if ((rc = balloc(b, &b->items_par, ipar.size()))) return rc;
   if ((rc = balloc(b, &b->items_ser, iser.size()))) return rc;
   if ((rc = balloc(b, &b->items_step, istep.size()))) return rc;
+  if ((rc = balloc(b, &b->items_pow, ipow.size()))) return rc;
   if ((rc = balloc(b, &b->kry_list, kry.size()))) return rc;
   if ((rc = balloc(b, &b->counter, 1))) return rc;
   if ((rc = balloc(b, &b->status, 1))) return rc;
@@ -243,6 +271,9 @@ int bprepare(pxa_batch* b) {
   if (!istep.empty())
     BCUDA(b, cudaMemcpy(b->items_step, istep.data(), sizeof(int2) * istep.size(), cudaMemcpyHostToDevice),
           "copy chains");
+  if (!ipow.empty())
+    BCUDA(b, cudaMemcpy(b->items_pow, ipow.data(), sizeof(int2) * ipow.size(), cudaMemcpyHostToDevice),
+          "copy chains");
   if (!kry.empty())
     BCUDA(b, cudaMemcpy(b->kry_list, kry.data(), sizeof(int) * kry.size(), cudaMemcpyHostToDevice), "copy chains");
   BCUDA(b, cudaMemset(b->status, 0, sizeof(int)), "reset status");
@@ -252,6 +283,7 @@ int bprepare(pxa_batch* b) {
     BCUDA(b, cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event");
   }
   b->lanes_grid = batch_lanes_grid(b->device, b->nmax, b->r32max);
+  b->pow_grid = b->rpmax > 0 ? batch_lanes_grid(b->device, b->nmax, b->rpmax) : 1;
   BCUDA(b, cudaGetLastError(), "lane grid");
   b->ready = true;
   return PXA_OK;
@@ -295,7 +327,10 @@ int benqueue(pxa_batch* b, cudaStream_t st, int mode, const double* q0, double* 
                               b->h, b->V, b->tol, b->status, b->errmax), "chains");
   BCUDA(b, cudaEventRecord(b->ev_join, b->side), "join");
   BCUDA(b, launch_batch_cn_chain(st, std::min(b->lanes_grid, std::max(b->n_step, 1)), b->inst, b->items_step, b->n_step, b->counter, b->taps32, 0, k,
-                                 b->E, P, 0, 1, P - 1, b->h, b->nmax, b->r32max), "stepped chains");
+                                 b->E, P, 0, 1, P - 1, b->h, b->nmax, b->r32max, 0), "stepped chains");
+  BCUDA(b, launch_batch_cn_chain(st, std::min(b->pow_grid, std::max(b->n_pow, 1)), b->inst, b->items_pow, b->n_pow,
+                                 b->counter, b->taps32, 0, k, b->E, P, 0, 1, P - 1, b->h, b->nmax, b->rpmax, 1),
+        "propagator-band chains");
   BCUDA(b, cudaStreamWaitEvent(st, b->ev_join, 0), "join wait");
   mark(2);
   BCUDA(b, launch_batch_superpose_direct(st, b->inst, cnt, b->nmax, b->taps64, q0, b->E, P, P - 1, b->h, b->qT,
@@ -309,7 +344,10 @@ int benqueue(pxa_batch* b, cudaStream_t st, int mode, const double* q0, double* 
                               P - 1, b->hA, b->V, b->tol, b->status, b->errmax), "adjoint chains");
   BCUDA(b, cudaEventRecord(b->ev_join, b->side), "join");
   BCUDA(b, launch_batch_cn_chain(st, std::min(b->lanes_grid, std::max(b->n_step, 1)), b->inst, b->items_step, b->n_step, b->counter, b->taps32, 1, k,
-                                 b->EA, P, P - 1, -1, P - 1, b->hA, b->nmax, b->r32max), "stepped adjoint chains");
+                                 b->EA, P, P - 1, -1, P - 1, b->hA, b->nmax, b->r32max, 0), "stepped adjoint chains");
+  BCUDA(b, launch_batch_cn_chain(st, std::min(b->pow_grid, std::max(b->n_pow, 1)), b->inst, b->items_pow, b->n_pow,
+                                 b->counter, b->taps32, 1, k, b->EA, P, P - 1, -1, P - 1, b->hA, b->nmax, b->rpmax, 1),
+        "propagator-band adjoint chains");
   BCUDA(b, cudaStreamWaitEvent(st, b->ev_join, 0), "join wait");
   mark(4);
   BCUDA(b, launch_batch_superpose_adjoint(st, b->inst, cnt, b->nmax, b->qT, b->EA, P, b->hA, grad, b->status),
@@ -411,6 +449,13 @@ int pxa_batch_set_krylov(pxa_batch* b, int m, double tol, double reach) {
 int pxa_batch_set_homogeneous(pxa_batch* b, double ratio) {
   if (!b || !(ratio >= 0.0)) return PXA_ERR_INVALID;
   b->hom_ratio = ratio;
+  brelease(b);
+  return PXA_OK;
+}
+
+int pxa_batch_set_power(pxa_batch* b, int enable) {
+  if (!b) return PXA_ERR_INVALID;
+  b->power = enable != 0;
   brelease(b);
   return PXA_OK;
 }
@@ -570,6 +615,8 @@ int pxa_batch_get_stats(const pxa_batch* b, pxa_batch_stats* out) {
   s.krylov_err_max = b->err_last;
   s.workspace_bytes = b->bytes;
   s.krylov_problems = b->n_kry;
+  s.power_problems = b->n_pow;
+  s.band_power_max = b->rpmax > 0 ? 2 * b->rpmax + 1 : 0;
   s.hom_ratio = b->hom_ratio;
   s.ms_lanes = b->ms[0];
   s.ms_chains = b->ms[1];

@@ -37,7 +37,7 @@ EXPORTS = [
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
     "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
-    "pxa_batch_set_homogeneous", "pxa_batch_set_timing",
+    "pxa_batch_set_homogeneous", "pxa_batch_set_power", "pxa_batch_set_timing",
     "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
     "pxa_batch_autotune", "pxa_batch_offsets", "pxa_batch_get_stats", "pxa_batch_problem_info",
 ]
@@ -78,7 +78,8 @@ class BatchStats(ctypes.Structure):
                 ("krylov_problems", ctypes.c_int), ("hom_ratio", ctypes.c_double),
                 ("ms_lanes", ctypes.c_float), ("ms_chains", ctypes.c_float),
                 ("ms_adjoint_lanes", ctypes.c_float), ("ms_adjoint_chains", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("power_problems", ctypes.c_int),
+                ("band_power_max", ctypes.c_int)]
 
 
 _lib = None
@@ -137,6 +138,7 @@ def load(path: str = LIB_PATH):
         "pxa_batch_set_krylov": [p, i, d, d],
         "pxa_batch_set_graph": [p, i],
         "pxa_batch_set_homogeneous": [p, d],
+        "pxa_batch_set_power": [p, i],
         "pxa_batch_set_timing": [p, i],
         "pxa_batch_gradient": [p, i, p, p, p],
         "pxa_batch_sync": [p],
@@ -417,6 +419,10 @@ class Batch:
 
     def set_homogeneous(self, ratio):
         self._check(self._L.pxa_batch_set_homogeneous(self._h, float(ratio)))
+
+    def set_power(self, enable):
+        """Apply the stepper's subinterval propagator as one band of M^(K/P) (1) or step it (0)."""
+        self._check(self._L.pxa_batch_set_power(self._h, 1 if enable else 0))
 
     def set_graph(self, enable):
         self._check(self._L.pxa_batch_set_graph(self._h, 1 if enable else 0))

@@ -147,6 +147,44 @@ def test_batch_autotune_keeps_the_tolerance(X, torch, small):
     b.close()
 
 
+@pytest.mark.parametrize("K,P", [(512, 8), (1024, 16), (96, 2)])
+def test_batch_propagator_band_equals_stepped_chain(X, torch, small, K, P):
+    """The subinterval propagator M^(K/P) applied once per link as a circulant band (taps
+    from the eigenvalues R_k^(K/P)) and the chains of K/P CN steps per link both match the
+    oracle's serial stepping within the FP32-stepping tolerance, and each other. (The band
+    rounds 15 times where the stepped chain rounds K/P times per link: at K = 1024, P = 16
+    the band's J is 2e-6 from the oracle, the stepped chain's 4e-5.)"""
+    q0 = dev(torch, small["q0"])
+    nprob = len(small["n"])
+    res = {}
+    for power in (True, False):
+        b = X.Batch()
+        b.set(small["n"], small["nu"], c=small["c"], T=small["T"], K=K, P=P)
+        b.set_homogeneous(0.0)
+        b.set_power(power)
+        J = torch.empty(nprob, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(q0)
+        b.gradient(X.PARAEXP, q0, J, g)
+        b.sync()
+        st = b.stats()
+        if power:
+            assert st["power_problems"] == nprob and st["band_power_max"] >= 3
+        else:
+            assert st["power_problems"] == 0 and st["band_power_max"] == 0
+        assert st["krylov_problems"] == 0
+        res[power] = (J.cpu().numpy(), g.cpu().numpy(), b.offsets())
+        b.close()
+    off = res[True][2]
+    for i in range(nprob):
+        sl = slice(off[i], off[i + 1])
+        Jo, go = reference(small, off, i, K, P, False)
+        for power in (True, False):
+            J, g, _ = res[power]
+            assert abs(J[i] - Jo) / Jo < 1e-4 and rel(g[sl], go) < 1e-4, (i, power)
+        assert abs(res[True][0][i] - res[False][0][i]) / Jo < 1e-4
+        assert rel(res[True][1][sl], res[False][1][sl]) < 1e-4, i
+
+
 def test_batch_rejects_bad_problems(X):
     b = X.Batch()
     with pytest.raises(X.PxaError):
