@@ -247,6 +247,10 @@ def run_ours(args, w, rank, world):
         # and for the CN power (which keeps Paraexp equal to serial stepping)
         phis.insert(2, ("paraexp_exp_relpm", X.PARAEXP, X.PHI_EXP))
         phis.insert(0, ("paraexp_stepper_relpm", X.PARAEXP, X.PHI_STEPPER))
+        # the subinterval propagator itself as a circulant band (exact for this periodic
+        # constant-coefficient operator): exp(tau A), and the CN power M^(K/P)
+        phis.insert(3, ("paraexp_exp_band", X.PARAEXP, X.PHI_EXP))
+        phis.insert(0, ("paraexp_stepper_band", X.PARAEXP, X.PHI_STEPPER))
     if w["kind"] == "burgers1d":
         # the multi-checkpoint scheme (Sec. 3.5): C + 1 checkpoints, every interval re-stepped
         # and solved by the Paraexp adjoint over its own P subintervals (not a headline
@@ -265,6 +269,8 @@ def run_ours(args, w, rank, world):
             ctx.set_checkpoints(w["checkpoints"])
         if name.endswith("_relpm"):
             ctx.set_propagator(X.PROP_RELPM, 150)
+        elif name.endswith("_band"):
+            ctx.set_propagator(X.PROP_BAND, 150)
         elif not (w["kind"] == "burgers1d" and phi == X.PHI_EXP):
             # autotuner (outside any timed region): Krylov m / substeps, or cluster sizes
             best_ms = ctx.autotune(mode, torch.empty(w["n"], dtype=torch.float64, device="cuda"))
@@ -304,6 +310,9 @@ def run_ours(args, w, rank, world):
     if w["kind"] == "advdiff1d" and head.endswith("_relpm"):
         ctx.set_krylov(w["m"], w["tol"], phi, w["sub"])
         ctx.set_propagator(X.PROP_RELPM, 150)
+    elif w["kind"] == "advdiff1d" and head.endswith("_band"):
+        ctx.set_krylov(w["m"], w["tol"], phi, w["sub"])
+        ctx.set_propagator(X.PROP_BAND, 150)
     elif w["kind"] == "advdiff1d":
         ctx.set_krylov(tv["krylov_m"], w["tol"], phi, tv["krylov_substeps"])
     else:
@@ -388,9 +397,10 @@ def run_ours(args, w, rank, world):
         m, sub = st["krylov_m"], st["krylov_substeps"]
         arnoldi = (8 * m + 4 * m * (m + 1) + 2 * m) * n  # operator, CGS2, norms, combine
         dense = 2 * (m ** 3) * (1 + int(np.log2(k // sub)))  # solve + squarings
+        chain = {"band": ("ad1_band_chain_kernel", None), "relpm": ("ad1_relpm_chain_kernel", None)}.get(
+            head.rsplit("_", 1)[-1], ("ad1_chain_kernel", (P - 1) * sub * (arnoldi + dense)))
         kernels = {
-            "ad1_chain_kernel": (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]),
-                                 (P - 1) * sub * (arnoldi + dense), 1, TRAFFIC.get("ad1_chain_kernel")),
+            chain[0]: (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]), chain[1], 1, TRAFFIC.get(chain[0])),
             "cn_lanes_kernel": (0.5 * (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"]),
                                 FLOPS_CN_BAND_TAP * st["band_taps"] * n * k * P, P,
                                 TRAFFIC.get("cn_lanes_kernel")),
@@ -433,8 +443,8 @@ def run_ours(args, w, rank, world):
 
 def run_batch_once(args, w):
     """W warm-up gradients and one more of the batched workload in each mode (Paraexp
-    with the homogeneous parts stepped, then serial), launched one by one with phase
-    events, for ncu: no autotuner."""
+    with the stepper's subinterval propagator applied as one band of M^(K/P), then
+    serial), launched one by one with phase events, for ncu: no autotuner."""
     import torch
 
     from paper_2004_00546_gb300 import build, inputs as I, pxa as X
@@ -455,14 +465,15 @@ def run_batch_once(args, w):
             b.gradient(mode, q0, J, g)
         st = b.stats()
         out[name] = {k: st[k] for k in ("ms_lanes", "ms_chains", "ms_adjoint_lanes", "ms_adjoint_chains",
-                                        "ms_total", "lanes_grid", "band32_max")}
+                                        "ms_total", "lanes_grid", "band32_max", "power_problems",
+                                        "band_power_max")}
         b.close()
     return out
 
 
 def run_once(args, w):
     """W warm-up gradients and one more (Paraexp, stepper propagator; for the 1D
-    advection-diffusion workload through the real Leja points method), for ncu: the
+    advection-diffusion workload as one circulant band of M^(K/P) per link), for ncu: the
     kernels of gradient W+1 are the launches after the first W of each name."""
     import torch
 
@@ -474,7 +485,7 @@ def run_once(args, w):
     ctl = torch.as_tensor(inp["control"], device="cuda")
     ctx = make_ctx(X, w, X.PHI_STEPPER)
     if w["kind"] == "advdiff1d":
-        ctx.set_propagator(X.PROP_RELPM, 150)  # the fastest variant that meets the 1e-8 gate
+        ctx.set_propagator(X.PROP_BAND, 150)  # the fastest variant that meets the 1e-8 gate
     ctx.set_control(ctl)
     if "target" in inp:
         ctx.set_target(torch.as_tensor(inp["target"], device="cuda"))

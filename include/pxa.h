@@ -83,7 +83,7 @@ typedef enum { PXA_PHI_EXP = 0, PXA_PHI_STEPPER = 1 } pxa_phi;
  * or the real Leja points method (Sec. 4.1: Newton interpolation of phi(z) = (e^z - 1)/z
  * at Leja points of the focal interval of the spectrum; exp(B) v = v + B phi(B) v; three
  * vectors of workspace instead of a Krylov basis; PXA_PHI_EXP only). */
-typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1 } pxa_propagator;
+typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1, PXA_PROP_BAND = 2 } pxa_propagator;
 /* SERIAL: one lane over [0, T] (plain serial stepping, same kernels).
  * PARAEXP: P lanes + homogeneous propagation + superposition. */
 typedef enum { PXA_SERIAL = 0, PXA_PARAEXP = 1 } pxa_mode;
@@ -172,8 +172,12 @@ int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
 /* ADVDIFF_1D homogeneous propagator (pxa_propagator). With PXA_PROP_RELPM the Newton
  * series runs up to max_degree (2..200) terms per substep until its last two terms fall
  * below the tolerance of pxa_set_krylov times ||v|| (else PXA_ERR_NOT_CONVERGED); the
- * substeps keep the capacity of the spectral ellipse <= 4 each (automatic). Invalidates
- * the workspace. */
+ * substeps keep the capacity of the spectral ellipse <= 4 each (automatic). With
+ * PXA_PROP_BAND the subinterval propagator itself, exp(tau A) (PXA_PHI_EXP) or the CN
+ * power M^(K/P) (PXA_PHI_STEPPER), is applied once per link as a circulant band: A is
+ * circulant (periodic grid, constant coefficients), so the propagator's taps are the
+ * inverse DFT of its eigenvalues, built on the host (FP64, kept to 2^-50 of the largest
+ * tap; max_degree is not used). Invalidates the workspace. */
 int pxa_set_propagator(pxa_ctx* ctx, int method, int max_degree);
 /* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
 int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);

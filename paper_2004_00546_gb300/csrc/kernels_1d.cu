@@ -233,6 +233,48 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
   for (int i = threadIdx.x; i < n; i += blockDim.x) hout[i] = h[i];
 }
 
+// Eq. hom / Eq. adjHomNormal with the subinterval propagator B itself as a circulant band
+// (exp(tau A) or the CN power M^(K/P); periodic grid, constant coefficients):
+// h = 0; for l < count: h += E[first + l stride]; h = B h (B^T: taps reversed). One block;
+// shared layout taps[2r+1], xa[n+2r], xb[n+2r] with r-point halos as in cn_lanes_kernel.
+__global__ void ad1_band_chain_kernel(int n, int r, const double* __restrict__ taps, int transpose,
+                                      const double* __restrict__ E, int first, int stride, int count,
+                                      double* __restrict__ hout) {
+  extern __shared__ double sm[];
+  const int w = 2 * r + 1;
+  double* tp = sm;
+  double* xa = tp + w;
+  double* xb = xa + n + 2 * r;
+  for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? taps[w - 1 - j] : taps[j];
+  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, 0.0);
+  __syncthreads();
+  for (int l = 0; l < count; ++l) {
+    const double* e = E + (size_t)(first + l * stride) * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, xa[r + p] + e[p]);
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const double* xp = xa + p;  // xp[r + j] = x_{p+j}
+      double acc = 0.0;
+      for (int j = 0; j < w; ++j) acc = fma(tp[j], xp[j], acc);
+      put_halo(xb, n, r, p, acc);
+    }
+    __syncthreads();
+    double* t = xa;
+    xa = xb;
+    xb = t;
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) hout[p] = xa[r + p];
+}
+
+cudaError_t launch_ad1_band_chain(cudaStream_t st, int n, int r, const double* taps, int transpose,
+                                  const double* E, int first, int stride, int count, double* hout) {
+  const size_t sh = sizeof(double) * ((size_t)(2 * r + 1) + 2 * (size_t)(n + 2 * r));
+  cudaError_t e = cudaFuncSetAttribute(ad1_band_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  ad1_band_chain_kernel<<<1, 512, sh, st>>>(n, r, taps, transpose, E, first, stride, count, hout);
+  return cudaGetLastError();
+}
+
 // One vector: y = exp(ts A)^nsub x (building block).
 __global__ void ad1_relpm_expv_kernel(int n, double am, double a0, double ap, int transpose,
                                       const double* __restrict__ x, double* __restrict__ y,

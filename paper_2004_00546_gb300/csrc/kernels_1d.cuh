@@ -22,7 +22,7 @@ cudaError_t launch_ad1_stream_out(cudaStream_t st, size_t total, const float* x,
 // Host: taps m_j (|j| <= r) of the circulant Crank-Nicolson map of the stencil (am, a0, ap).
 void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector<double>& taps, int& r);
 void cn_power_taps(int n, double am, double a0, double ap, double dt, int64_t steps, int cut_exp,
-                   std::vector<double>& taps, int& r);
+                   std::vector<double>& taps, int& r, bool expo = false);
 
 cudaError_t launch_cn_lanes(cudaStream_t st, int lanes, int threads, int n, int r,
                             const double* taps, int transpose, int64_t steps, const double* x0,
@@ -36,6 +36,10 @@ cudaError_t launch_ad1_chain(cudaStream_t st, int threads, int n, double am, dou
                              double* hout, double* Vglob, int m, int phi_mode, double hscale,
                              int64_t steps_per_sub, int nsub, double tol, int v_in_smem,
                              int* status, double* errmax);
+// h = 0; for l < count: h += E[first + l stride]; h = B h (B^T when transpose) with B the
+// circulant band taps[2r+1] of the subinterval propagator; hout = h. One block, FP64.
+cudaError_t launch_ad1_band_chain(cudaStream_t st, int n, int r, const double* taps, int transpose,
+                                  const double* E, int first, int stride, int count, double* hout);
 cudaError_t launch_ad1_relpm_chain(cudaStream_t st, int threads, int n, double am, double a0, double ap,
                                    int transpose, const double* E, int first, int stride, int count,
                                    double* hout, const double* D, const double* z, int mmax, double ts,

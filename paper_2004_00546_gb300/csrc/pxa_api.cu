@@ -79,12 +79,13 @@ void cn_band_taps(int n, double am, double a0, double ap, double dt, std::vector
 
 // Taps m_j (|j| <= r) of the power M^steps of the circulant Crank-Nicolson map: the
 // propagator of the stepper over `steps` steps, itself circulant with eigenvalues R_k^steps
-// (R_k as in cn_band_taps; powers by repeated squaring, double sums). Advection shifts its
+// (R_k as in cn_band_taps; powers by repeated squaring, double sums); with expo, of
+// exp(steps dt A) (eigenvalues exp(steps dt lam_k)). Advection shifts its
 // peak by about (am - ap) steps dt points, so the band is cut relative to the largest tap:
 // past the shift, once both |m_j| and |m_-j| stay below 2^-cut_exp max|m| for four
 // consecutive offsets (or at n/2, the full circulant). The band is stored symmetric.
 void cn_power_taps(int n, double am, double a0, double ap, double dt, int64_t steps, int cut_exp,
-                   std::vector<double>& taps, int& r) {
+                   std::vector<double>& taps, int& r, bool expo) {
   typedef std::complex<double> C;
   const double pi = 3.141592653589793238462643383279502884;
   std::vector<C> Rp(n), w(n);
@@ -95,6 +96,10 @@ void cn_power_taps(int n, double am, double a0, double ap, double dt, int64_t st
   const double th = 0.5 * dt;
   for (int k = 0; k < n; ++k) {
     const C lam = a0 + am * std::conj(w[k]) + ap * w[k];
+    if (expo) {  // exp(steps dt A) instead of the CN power
+      Rp[k] = std::exp((double)steps * dt * lam);
+      continue;
+    }
     C base = (1.0 + th * lam) / (1.0 - th * lam), acc = 1.0;
     for (int64_t e = steps; e > 0; e >>= 1) {
       if (e & 1) acc *= base;
@@ -291,6 +296,8 @@ struct pxa_ctx {
   double* relpm_D = nullptr;   // Newton divided differences and nodes of the chain's substeps
   double* relpm_z = nullptr;
   int relpm_nsub = 1;
+  double* band_p = nullptr;    // taps of the subinterval propagator as a circulant band
+  int band_pr = 0;             // its half-width
   double relpm_ts = 0.0;
   // pxa_cn_lanes_1d: FP32 lane states in global memory and the padded FP32 band
   float* st1d = nullptr;
@@ -463,7 +470,8 @@ void release_workspace(pxa_ctx* c) {
   c->ws_bytes = 0;
   c->ready = false;
   c->taps = c->E = c->EA = c->src = c->srcA = c->hsum = c->hsumA = c->qT = c->tmp = nullptr;
-  c->relpm_D = c->relpm_z = nullptr;
+  c->relpm_D = c->relpm_z = c->band_p = nullptr;
+  c->band_pr = 0;
   c->st1d = c->taps1d = nullptr;
   c->lanes1d = 0;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
@@ -619,6 +627,13 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
     PXA_CUDA(c, cudaMemcpy(c->taps, c->band_host.data(), sizeof(double) * c->band_host.size(),
                            cudaMemcpyHostToDevice), "copy taps");
+    if (c->prop == PXA_PROP_BAND) {
+      // the subinterval propagator exp(tau A) or M^(K/P) as one circulant band
+      std::vector<double> bt;
+      cn_power_taps(n, c->am, c->a0, c->ap, dt, c->K / P, 50, bt, c->band_pr, c->kry_phi == PXA_PHI_EXP);
+      if ((rc = alloc(c, &c->band_p, bt.size()))) return rc;
+      PXA_CUDA(c, cudaMemcpy(c->band_p, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice), "copy");
+    }
     if (c->prop == PXA_PROP_RELPM) {
       // the chain's exponential over one subinterval tau = T / P
       std::vector<double> z, D;
@@ -861,7 +876,9 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   PXA_CUDA(c, launch_band_minus_identity(st, n, r, c->taps, 0, q0, c->src), "src");
   PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 0, k, nullptr, c->src, c->E), "lanes");
   ev_record(c, 1);
-  if (P > 1 && relpm) {
+  if (P > 1 && c->prop == PXA_PROP_BAND) {
+    PXA_CUDA(c, launch_ad1_band_chain(st, n, c->band_pr, c->band_p, 0, c->E, 0, 1, P - 1, c->hsum), "chain");
+  } else if (P > 1 && relpm) {
     PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 0, c->E, 0, 1, P - 1, c->hsum,
                                        c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
                                        relpm_direct, c->kry_tol, c->status, c->errmax), "chain");
@@ -878,7 +895,10 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (!do_a) return PXA_OK;
   PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 1, k, nullptr, c->srcA, c->EA), "adj lanes");
   ev_record(c, 3);
-  if (P > 1 && relpm) {
+  if (P > 1 && c->prop == PXA_PROP_BAND) {
+    PXA_CUDA(c, launch_ad1_band_chain(st, n, c->band_pr, c->band_p, 1, c->EA, P - 1, -1, P - 1, c->hsumA),
+             "adj chain");
+  } else if (P > 1 && relpm) {
     PXA_CUDA(c, launch_ad1_relpm_chain(st, kth, n, c->am, c->a0, c->ap, 1, c->EA, P - 1, -1, P - 1, c->hsumA,
                                        c->relpm_D, c->relpm_z, c->relpm_mmax, c->relpm_ts, c->relpm_nsub,
                                        relpm_direct, c->kry_tol, c->status, c->errmax), "adj chain");
@@ -1554,7 +1574,8 @@ int pxa_partition_bounds(int64_t K, int P, double r, int max_chunks, int64_t* bo
 }
 
 int pxa_set_propagator(pxa_ctx* c, int method, int max_degree) {
-  if (!c || (method != PXA_PROP_KRYLOV && method != PXA_PROP_RELPM) || max_degree < 2 || max_degree > 200)
+  if (!c || (method != PXA_PROP_KRYLOV && method != PXA_PROP_RELPM && method != PXA_PROP_BAND) ||
+      max_degree < 2 || max_degree > 200)
     return PXA_ERR_INVALID;
   c->prop = method;
   c->relpm_mmax = max_degree;
@@ -1999,7 +2020,19 @@ int pxa_expv(pxa_ctx* c, int transpose, int64_t span_steps, int substeps, const 
   const int64_t sps = span_steps / substeps;
   const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)sps : dt;
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), c->stream), "reset errmax");
-  if (c->prop == PXA_PROP_RELPM) {
+  if (c->prop == PXA_PROP_BAND) {
+    // the propagator of the whole span as one circulant band (substeps not used)
+    std::vector<double> bt;
+    int br = 0;
+    cn_power_taps(n, c->am, c->a0, c->ap, dt, span_steps, 50, bt, br, c->kry_phi == PXA_PHI_EXP);
+    double* bd = nullptr;
+    PXA_CUDA(c, cudaMalloc(&bd, sizeof(double) * bt.size()), "alloc");
+    cudaError_t e = cudaMemcpy(bd, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_ad1_band_chain(c->stream, n, br, bd, transpose, x_dev, 0, 0, 1, y_dev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(bd);
+    PXA_CUDA(c, e, "band expv");
+  } else if (c->prop == PXA_PROP_RELPM) {
     // ReLPM picks its own substeps for the whole span
     std::vector<double> z, D;
     int ns = 1;

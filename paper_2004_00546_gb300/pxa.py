@@ -20,7 +20,7 @@ EXPV_STATIC_MAX_DOUBLES = 131072
 ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D = 1, 2, 3
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
-PROP_KRYLOV, PROP_RELPM = 0, 1
+PROP_KRYLOV, PROP_RELPM, PROP_BAND = 0, 1, 2
 SERIAL, PARAEXP = 0, 1
 STORE_FULL, STORE_CHECKPOINTS = 0, 1
 ADJ_BANDED, ADJ_RESTEP, ADJ_BANDED_SINGLE, ADJ_BANDED_PAIR = 0, 1, 2, 3

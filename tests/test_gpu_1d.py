@@ -735,6 +735,56 @@ def test_relpm_stepper_paraexp_equals_serial_stepping(X, torch, n, nu, K, P):
     assert rel(host(out), go) < 1e-10
 
 
+# ---- the subinterval propagator as a circulant band -------------------------------------------
+@pytest.mark.parametrize("phi", ["exp", "stepper"])
+@pytest.mark.parametrize("n,c,nu,span", [(256, 1.0, 0.01, 512), (64, 1.0, 0.0, 1200), (128, 0.0, 0.05, 800),
+                                         (1000, 1.0, 0.002, 4096), (37, 2.0, 0.1, 300), (4096, 1.0, 0.02, 2048)])
+def test_band_expv_matches_exact_propagators(X, torch, n, c, nu, span, phi):
+    """exp(t A) v and the CN power R(dt A)^k v, and their transposes, applied as one
+    circulant band whose taps come from the propagator's eigenvalues (pure advection, pure
+    diffusion, mixed, stiff, a long grid), against the closed-form Fourier propagators."""
+    T, K = 1.0, 4096
+    ph = X.PHI_EXP if phi == "exp" else X.PHI_STEPPER
+    ctx = ad1_ctx(X, n, c, nu, T, K, 8, m=30, tol=1e-13, phi=ph)
+    ctx.set_propagator(X.PROP_BAND, 150)
+    v = I.grf_k2(n, 19)
+    xd = dev(torch, v)
+    y = torch.empty_like(xd)
+    for tr in (False, True):
+        ctx.expv(xd, y, span, transpose=tr)
+        if phi == "exp":
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_EXP, t=span * T / K, transpose=tr)
+        else:
+            ref = O.ad1_phi_dft(v, c, nu, O.PHI_CN, dt=T / K, steps=span, transpose=tr)
+        assert rel(host(y), ref) < 1e-12, tr
+
+
+@pytest.mark.parametrize("n,nu,K,P", [(256, 0.01, 4096, 8), (100, 0.0, 512, 4), (333, 0.05, 1024, 16),
+                                      (17, 0.1, 64, 64)])
+def test_band_paraexp_gradient_matches_oracle(X, torch, n, nu, K, P):
+    """The Paraexp loop with the band of exp(tau A) equals the oracle's Paraexp with the
+    exact exponential; with the band of M^(K/P) it equals the oracle's serial CN stepping
+    (graph replay included)."""
+    c, T = 1.0, 1.0
+    q0 = I.grf_k2(n, 27)
+    qd = dev(torch, q0)
+    for phi in (X.PHI_EXP, X.PHI_STEPPER):
+        if phi == X.PHI_EXP:
+            Jo, go, _ = O.ad1_cn_gradient_paraexp(q0, c, nu, T, K, P, O.PHI_EXP)
+        else:
+            Jo, go, _ = O.ad1_cn_gradient_serial(q0, c, nu, T, K)
+        ctx = ad1_ctx(X, n, c, nu, T, K, P, m=30, tol=1e-12, phi=phi)
+        ctx.set_propagator(X.PROP_BAND, 150)
+        ctx.set_control(qd)
+        out = torch.empty_like(qd)
+        for graph in (False, True):
+            ctx.set_graph(graph)
+            J = ctx.gradient(X.PARAEXP, out)
+            assert abs(J - Jo) / Jo < 1e-10
+            assert rel(host(out), go) < 1e-10, (phi, graph)
+        ctx.close()
+
+
 @pytest.mark.parametrize("n,nu", [(4608, 0.01), (5000, 0.002), (64, 0.05), (2304 * 3 + 4, 0.0)])
 def test_cn_lanes_1d_streaming_matches_oracle(X, torch, n, nu):
     """FP32 CN band lanes with their states in global memory (tiles of 2304 points,
