@@ -62,6 +62,7 @@ def lib():
                 "pxo_bu1_gradient_serial": [_i, _d, _d, _d, _i64, _d, _p, _p, _p, _p, _p, _p],
                 "pxo_bu1_gradient_hybrid": [_i, _d, _d, _d, _i64, _d, _i, _i, _i, _i, _p, _p, _p,
                                             _p, _p],
+                "pxo_bu1_nl_paraexp": [_i, _d, _d, _d, _i64, _i, _d, _p, _p, _p, _d, _i, _p, _p, _p],
                 "pxo_expm": [_i, _p, _p],
                 "pxo_ad1_krylov_expv": [_i, _d, _d, _d, _d, _i, _p, _p, _p],
                 "pxo_partition_nonequi": [_d, _i, _d, _p],
@@ -228,6 +229,24 @@ def bu1_gradient_hybrid(f, g, nu, T, K, P, hom_mode=HOM_MAGNUS, M_mag=25, m_kry=
                                          int(M_mag), int(m_kry), _ptr(u0a), _ptr(f), _ptr(g),
                                          ctypes.byref(J), _ptr(grad)), "bu1_hybrid")
     return J.value, grad
+
+
+def bu1_nl_paraexp_direct(f, nu, T, K, P, omega=0.0, u0=None, guess=None, tol=1e-12, max_iter=50,
+                          L=TWO_PI):
+    """Iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2): returns (trajectory (K+1, n),
+    errors of the iterations, converged)."""
+    f = _in(f)
+    n = f.size
+    u0a = None if u0 is None else _in(u0)
+    ga = None if guess is None else _in(guess)
+    traj = np.empty((int(K) + 1, n))
+    errs = np.zeros(int(max_iter))
+    it = ctypes.c_int(0)
+    rc = lib().pxo_bu1_nl_paraexp(n, L, nu, T, int(K), int(P), omega, _ptr(u0a), _ptr(f), _ptr(ga),
+                                  float(tol), int(max_iter), _ptr(traj), _ptr(errs), ctypes.byref(it))
+    if rc < 0:
+        _check(rc, "bu1_nl_paraexp")
+    return traj, errs[:it.value].copy(), rc == 0
 
 
 # ---- small helpers -----------------------------------------------------------

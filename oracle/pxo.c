@@ -467,6 +467,165 @@ static double bu1_direct(int n, double L, double nu, double T, int64_t K, double
   return J;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2).                    */
+/* ------------------------------------------------------------------------- */
+/* Source of the linearised problems at a stage (Eq. nonlinTrans): N(Y) - J Y + c f with
+ * N(Y) = -Y dY/dx and J = dN/dq at qbar, J Y = -Y dqbar/dx - qbar dY/dx. */
+static void nl_source(int n, double L, const double* qbar, const double* Y, double c,
+                      const double* f, double* out) {
+  double h = L / n;
+  for (int i = 0; i < n; ++i) {
+    int im = (i - 1 + n) % n, ip = (i + 1) % n;
+    double Yx = (Y[ip] - Y[im]) / (2.0 * h);
+    double qx = (qbar[ip] - qbar[im]) / (2.0 * h);
+    out[i] = -Y[i] * Yx + (Y[i] * qx + qbar[i] * Yx) + c * f[i];
+  }
+}
+
+/* One RK4 step of dy/dt = (A + J) y + S_q (stage sources S[0..3], NULL = none) from y,
+ * with (A + J) w = pxo_bu1_jac(qbar, w) (diffusion plus the averaged Jacobian of N). */
+static void nl_lin_step(int n, double L, double nu, double dt, const double* qbar, double* const S[4],
+                        double* y, double* k, double* ys, double* acc) {
+  static const double cst[4] = {0.5, 0.5, 1.0, 0.0};
+  static const double wgt[4] = {1.0, 2.0, 2.0, 1.0};
+  for (int i = 0; i < n; ++i) acc[i] = 0.0;
+  memcpy(ys, y, sizeof(double) * n);
+  for (int q = 0; q < 4; ++q) {
+    pxo_bu1_jac(n, L, nu, qbar, ys, k);
+    if (S[0])
+      for (int i = 0; i < n; ++i) k[i] += S[q][i];
+    for (int i = 0; i < n; ++i) acc[i] += wgt[q] * k[i];
+    if (q < 3)
+      for (int i = 0; i < n; ++i) ys[i] = y[i] + cst[q] * dt * k[i];
+  }
+  for (int i = 0; i < n; ++i) y[i] += dt / 6.0 * acc[i];
+}
+
+int pxo_bu1_nl_paraexp(int n, double L, double nu, double T, int64_t K, int P, double omega,
+                       const double* u0, const double* f, const double* guess, double tol,
+                       int max_iter, double* traj, double* errs, int* iters) {
+  if (bad_grid(n, L) || !f || !traj || !iters || K < 1 || P < 1 || K % P != 0 || max_iter < 1 ||
+      !(tol > 0.0))
+    return -1;
+  const int64_t k = K / P;
+  const double dt = T / (double)K;
+  const size_t nb = sizeof(double) * n, rows = (size_t)(K + 1) * n;
+  double* Q = traj;                               /* iterate q_i, then q_{i+1} */
+  double* Qn = (double*)malloc(sizeof(double) * rows);
+  double* V = (double*)malloc(sizeof(double) * rows); /* lane solutions (Eq. nonlinTrans) */
+  double* qbar = (double*)malloc(nb * (size_t)P); /* qbar_p of every subinterval */
+  double* S[4];
+  double* Y = (double*)malloc(nb);
+  double* kk = (double*)malloc(nb);
+  double* ys = (double*)malloc(nb);
+  double* acc = (double*)malloc(nb);
+  double* y = (double*)malloc(nb);
+  for (int q = 0; q < 4; ++q) S[q] = (double*)malloc(nb);
+  int bad = !Qn || !V || !qbar || !Y || !kk || !ys || !acc || !y;
+  for (int q = 0; q < 4; ++q) bad = bad || !S[q];
+  int rc = -2;
+  if (bad) goto done;
+  /* Alg. 2: the initial guess of the direct solution */
+  for (int64_t s = 0; s <= K; ++s) {
+    double* row = Q + (size_t)s * n;
+    if (guess)
+      memcpy(row, guess + (size_t)s * n, nb);
+    else if (u0)
+      memcpy(row, u0, nb);
+    else
+      memset(row, 0, nb);
+  }
+  rc = 1;
+  *iters = 0;
+  for (int it = 0; it < max_iter; ++it) {
+    /* lanes (Eq. nonlinTrans) on every subinterval from zero */
+    for (int p = 0; p < P; ++p) {
+      const int64_t a = (int64_t)p * k;
+      /* Eq. Jacobians: dN/dq is linear in q, so its average over [T_p, T_{p+1}] is dN/dq
+       * at the average of q_i there (trapezoid rule over the step states) */
+      double* qb = qbar + (size_t)p * n;
+      for (int i = 0; i < n; ++i) {
+        double sum = 0.5 * (Q[(size_t)a * n + i] + Q[(size_t)(a + k) * n + i]);
+        for (int64_t s = a + 1; s < a + k; ++s) sum += Q[(size_t)s * n + i];
+        qb[i] = sum / (double)k;
+      }
+      /* the lane starts from zero at T_p; row a of V keeps lane p-1's end value */
+      memset(y, 0, nb);
+      for (int64_t s = a; s < a + k; ++s) {
+        const double t = (double)s * dt;
+        const double c1 = forcing_s(omega, t), c2 = forcing_s(omega, t + 0.5 * dt),
+                     c4 = forcing_s(omega, t + dt);
+        const double* qs = Q + (size_t)s * n;
+        /* the nonlinear RK4 stages of q_i(t_s) and the sources there */
+        nl_source(n, L, qb, qs, c1, f, S[0]);
+        pxo_bu1_rhs(n, L, nu, qs, kk);
+        for (int i = 0; i < n; ++i) Y[i] = qs[i] + 0.5 * dt * (kk[i] + c1 * f[i]);
+        nl_source(n, L, qb, Y, c2, f, S[1]);
+        pxo_bu1_rhs(n, L, nu, Y, kk);
+        for (int i = 0; i < n; ++i) Y[i] = qs[i] + 0.5 * dt * (kk[i] + c2 * f[i]);
+        nl_source(n, L, qb, Y, c2, f, S[2]);
+        pxo_bu1_rhs(n, L, nu, Y, kk);
+        for (int i = 0; i < n; ++i) Y[i] = qs[i] + dt * (kk[i] + c2 * f[i]);
+        nl_source(n, L, qb, Y, c4, f, S[3]);
+        nl_lin_step(n, L, nu, dt, qb, S, y, kk, ys, acc);
+        memcpy(V + (size_t)(s + 1) * n, y, nb);
+      }
+    }
+    /* homogeneous problems (Eq. nlHomIter), carried as their sum from T_p with the
+     * stepper's own propagator, and the sum Eq. fullsolIter on every step */
+    double* const none[4] = {NULL, NULL, NULL, NULL};
+    if (u0)
+      memcpy(y, u0, nb); /* q_{i+1}(0) = q0 */
+    else
+      memset(y, 0, nb);
+    for (int p = 0; p < P; ++p) {
+      const int64_t a = (int64_t)p * k;
+      const double* qb = qbar + (size_t)p * n;
+      memcpy(Qn + (size_t)a * n, y, nb); /* q_{i+1}(T_p): lane value 0 plus the carried sum */
+      for (int64_t s = a; s < a + k; ++s) {
+        nl_lin_step(n, L, nu, dt, qb, none, y, kk, ys, acc);
+        double* row = Qn + (size_t)(s + 1) * n;
+        const double* v = V + (size_t)(s + 1) * n;
+        for (int i = 0; i < n; ++i) row[i] = v[i] + y[i];
+      }
+      memcpy(y, Qn + (size_t)(a + k) * n, nb); /* the carried sum at T_{p+1} */
+    }
+    /* the error of the iteration, then q_i <- q_{i+1} */
+    double dmax = 0.0, qmax = 0.0;
+    for (int64_t s = 0; s <= K; ++s) {
+      double d2 = 0.0, q2 = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double d = Qn[(size_t)s * n + i] - Q[(size_t)s * n + i];
+        d2 += d * d;
+        q2 += Qn[(size_t)s * n + i] * Qn[(size_t)s * n + i];
+      }
+      if (d2 > dmax) dmax = d2;
+      if (q2 > qmax) qmax = q2;
+    }
+    const double err = qmax > 0.0 ? sqrt(dmax / qmax) : sqrt(dmax);
+    if (errs) errs[it] = err;
+    memcpy(Q, Qn, sizeof(double) * rows);
+    *iters = it + 1;
+    if (!(err == err) || isinf(err)) break; /* diverged to non-finite values */
+    if (err <= tol) {
+      rc = 0;
+      break;
+    }
+  }
+done:
+  free(Qn);
+  free(V);
+  free(qbar);
+  free(Y);
+  free(kk);
+  free(ys);
+  free(acc);
+  free(y);
+  for (int q = 0; q < 4; ++q) free(S[q]);
+  return rc;
+}
+
 int pxo_bu1_gradient_serial(int n, double L, double nu, double T, int64_t K, double omega,
                             const double* u0, const double* f, const double* g, double* J,
                             double* grad, double* traj) {

@@ -77,6 +77,22 @@ int pxo_bu1_gradient_serial(int n, double L, double nu, double T, int64_t K, dou
                             const double* u0, const double* f, const double* g, double* J,
                             double* grad, double* traj);
 
+/* Iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2, Eqs. nl, nlIter, nonlinTrans,
+ * Jacobians, nlHomIter, fullsolIter) on P equal subintervals, forcing s(t) f, u(0) = u0
+ * (NULL = 0). Split: A = nu d2/dx2, N(q) = -q dq/dx. Each iteration averages the
+ * Jacobian of N over every subinterval at iterate q_i, solves the P inhomogeneous
+ * problems from zero, carries the homogeneous problems (the stepper's own propagator)
+ * and sums them into q_{i+1}; the linear problems take the serial direct's RK4 steps with
+ * their source taken at the nonlinear RK4 stages of q_i, so that the fixed point is the
+ * serial RK4 trajectory. Initial guess: guess ((K+1)*n) or q = u0 at every step. Stops
+ * when max_s ||q_{i+1}(t_s) - q_i(t_s)|| <= tol max_s ||q_{i+1}(t_s)||, or after
+ * max_iter iterations. traj ((K+1)*n) receives the last iterate, errs (max_iter) the
+ * error of every iteration, *iters their number. Returns 0 when converged, 1 when not,
+ * -1 on bad arguments, -2 when out of memory.                                      */
+int pxo_bu1_nl_paraexp(int n, double L, double nu, double T, int64_t K, int P, double omega,
+                       const double* u0, const double* f, const double* guess, double tol,
+                       int max_iter, double* traj, double* errs, int* iters);
+
 /* Hybrid serial-direct / parallel-adjoint loop (Sec. 3.3; Eqs. seriesDirect,
  * hybadjinhom, adjHomNormal, fullAdjSolHyb) with the equal partition into P parts.
  * Adjoint inhomogeneous parts: exact discrete RK4 adjoint per subinterval.

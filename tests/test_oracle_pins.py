@@ -434,3 +434,52 @@ def test_relpm_error_follows_its_tolerance():
         assert e < 10 * tol
     with pytest.raises(ValueError):  # the Newton series cannot converge in 4 terms
         O.ad1_relpm_expv(v, 1.0, 0.01, 0.125, tol=1e-14, mmax=4)
+
+
+# ---- iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2) -------------------------------
+# The iteration's linear problems take the serial direct's RK4 steps with the nonlinear
+# source taken at the RK4 stages of the previous iterate, so its fixed point is the serial
+# RK4 trajectory (the oracle's pinned serial direct): a dropped source term, a wrong
+# Jacobian or a lost lane value in the carry moves the fixed point.
+@pytest.mark.parametrize("P,omega", [(1, 0.0), (4, 0.0), (8, 1.5), (32, 1.5)])
+def test_nl_paraexp_fixed_point_is_the_serial_rk4_trajectory(P, omega):
+    n, nu, T, K = 32, 0.05, 0.5, 128
+    f = 3.0 * I.fourier1d(n, 8, 61)
+    g = I.fourier1d(n, 8, 62)
+    u0 = 0.5 * I.fourier1d(n, 4, 63)
+    _, _, tr = O.bu1_gradient_serial(f, g, nu, T, K, omega=omega, u0=u0, want_traj=True)
+    traj, errs, ok = O.bu1_nl_paraexp_direct(f, nu, T, K, P, omega=omega, u0=u0, guess=tr, max_iter=1)
+    assert ok and len(errs) == 1 and errs[0] < 1e-14
+    assert np.abs(traj - tr).max() / np.abs(tr).max() < 1e-14
+
+
+@pytest.mark.parametrize("P", [1, 2, 4, 8, 16])
+def test_nl_paraexp_converges_to_the_serial_rk4_trajectory(P):
+    """From the guess q(t) = q0 the iterates converge to the serial RK4 trajectory."""
+    n, nu, T, K = 32, 0.05, 0.5, 128
+    f = 3.0 * I.fourier1d(n, 8, 71)
+    g = I.fourier1d(n, 8, 72)
+    u0 = 0.5 * I.fourier1d(n, 4, 73)
+    _, _, tr = O.bu1_gradient_serial(f, g, nu, T, K, omega=1.5, u0=u0, want_traj=True)
+    traj, errs, ok = O.bu1_nl_paraexp_direct(f, nu, T, K, P, omega=1.5, u0=u0, tol=1e-13, max_iter=60)
+    assert ok and errs[-1] <= 1e-13
+    assert np.all(np.diff(np.log(errs[1:])) < 0)  # contracting after the first iterate
+    assert np.abs(traj - tr).max() / np.abs(tr).max() < 1e-12
+
+
+def test_nl_paraexp_iterations_fall_with_the_subintervals_and_the_nonlinearity():
+    """Averaging the Jacobian over shorter subintervals makes each linearisation closer to
+    the local one (fewer iterations); a nearly linear problem converges at once."""
+    n, nu, T, K = 32, 0.05, 0.5, 128
+    g = I.fourier1d(n, 8, 62)
+    f = 10.0 * I.fourier1d(n, 8, 61)
+    its = []
+    for P in (1, 4, 16):
+        _, errs, ok = O.bu1_nl_paraexp_direct(f, nu, T, K, P, max_iter=60)
+        assert ok
+        its.append(len(errs))
+    assert its[0] > its[1] > its[2]
+    _, errs, ok = O.bu1_nl_paraexp_direct(1e-6 * f, nu, T, K, 4, max_iter=60)
+    assert ok and len(errs) <= 4
+    _, errs, ok = O.bu1_nl_paraexp_direct(f, nu, T, K, 4, max_iter=2)
+    assert not ok and len(errs) == 2
