@@ -769,7 +769,8 @@ def run_batch(args, w, rank, world):
                           "hom_ratio": st["hom_ratio"], "krylov_problems": st["krylov_problems"],
                           "substeps_max": st["substeps_max"], "lanes_grid": st["lanes_grid"],
                           "band32_max": st["band32_max"], "power_problems": st["power_problems"],
-                          "band_power_max": st["band_power_max"], "clocks": clk.summary()}
+                          "band_power_max": st["band_power_max"], "lane_steps": st["lane_steps"],
+                          "clocks": clk.summary()}
         # kernels per gradient: sources, lanes, superposition, adjoint lanes, gradient, and
         # per direction one chain launch for each kind of homogeneous propagation in use
         kinds = sum(1 for c in (st["krylov_problems"], st["power_problems"],
@@ -780,11 +781,13 @@ def run_batch(args, w, rank, world):
     ms = variants[head]["ms_per_step"]
     value = whole_job_rate(cnt * args.steps, world, reduce_max(ms * args.steps))
     # roofline of the headline's dominant kernel, the Paraexp lanes: P x count lanes of
-    # K/P CN steps, 2 flop per tap, point and step, i.e. 2 K sum_i n_i taps_i per
-    # direction. Its duration comes from the phase events around the direct lanes'
-    # launch (with the 0.03 ms source pass before it), in launches after the timed region.
-    w32, _, _ = bats["serial"].problem_info()
-    flop = 2.0 * 2.0 * K * float(np.sum(np.asarray(prob["n"], dtype=np.float64) * np.asarray(w32)))
+    # K/P CN steps taken as K/(P q) applications of the band of M^q, 2 flop per tap of
+    # that band, point and application, i.e. 2 (K/q) sum_i n_i taps_i per direction. Its
+    # duration comes from the phase events around the direct lanes' launch (with the
+    # 0.03 ms source pass before it), in launches after the timed region.
+    w32, _, _ = bats[head].problem_info()
+    q = bats[head].stats()["lane_steps"]
+    flop = 2.0 * 2.0 * (K / q) * float(np.sum(np.asarray(prob["n"], dtype=np.float64) * np.asarray(w32)))
     bp = bats[head]
     bp.set_timing(True)
     lanes_ms = []
@@ -800,7 +803,7 @@ def run_batch(args, w, rank, world):
             "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
             "peak_kind": "FP32 from unit counts and clocks (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
             "achieved": achieved, "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "flop_per_launch": 0.5 * flop, "ms_per_launch": ms_lanes,
+            "flop_per_launch": 0.5 * flop, "ms_per_launch": ms_lanes, "cn_steps_per_band": q,
             "serial_lanes_tflops": flop / (ms_ser / 1e3) / 1e12}
     # end to end: pinned host q0 -> device, gradient, J and gradient back to pinned host
     qh = torch.as_tensor(prob["q0"]).pin_memory()

@@ -353,7 +353,8 @@ int pxa_expv_static(int device, void* cuda_stream, const pxa_operator_desc* op, 
  * objective J_i = 0.5 ||q_i(T)||^2 (Eq. adjFinalTime, Eq. initupdate), all problems in one
  * launch per phase. The lanes (Eq. linInhomEqus / Eq. adjInhom: P per problem in Paraexp
  * mode, one serial lane of K steps per problem in serial mode) step the exact circulant
- * Crank-Nicolson band in FP32 with FP32 accumulation, taken from a cost-sorted work list
+ * Crank-Nicolson band in FP32 with FP32 accumulation (q steps per band application,
+ * pxa_batch_set_lane_steps), taken from a cost-sorted work list
  * by a persistent grid; the homogeneous propagations (Eq. hom / Eq. adjHomNormal) are
  * Krylov exponentials exp(tau A) in FP64 or the stepper's own propagator M^(K/P) in FP32
  * (pxa_batch_set_homogeneous, pxa_batch_set_power), and the superpositions are FP64.
@@ -381,6 +382,7 @@ typedef struct {
   float ms_total;           /*   the whole gradient */
   int power_problems;       /* problems whose homogeneous parts apply the band of M^(K/P) */
   int band_power_max;       /* widest band of M^(K/P) in use (taps; 0: none) */
+  int lane_steps;           /* q: the lanes apply the band of M^q, q CN steps at a time */
 } pxa_batch_stats;
 /* Create / destroy a batch context on `device`; `cuda_stream` is borrowed (NULL = the
  * default stream). */
@@ -412,6 +414,13 @@ int pxa_batch_set_homogeneous(pxa_batch* b, double ratio);
  * 2 BATCH_MAX_RP + 1 = 2049 taps step instead. enable = 0: every link takes K/P CN steps.
  * Invalidates the workspace. */
 int pxa_batch_set_power(pxa_batch* b, int enable);
+/* CN steps per band application of the lanes and stepped chains: q = 1, 2 or 4 (the
+ * lanes apply the exact product band of M^q, built on the host from the eigenvalues
+ * R_k^q; FP32 taps kept to 2^-40 of the largest, FP64 taps of M^q for the sources
+ * (M^q - I) x), or 0 (default): the largest of 4, 2, 1 that divides K/P and whose bands
+ * fit the lanes (2 BATCH_MAX_R + 1 = 511 taps). A q that does not divide K/P makes the
+ * next gradient fail with PXA_ERR_INVALID. Invalidates the workspace. */
+int pxa_batch_set_lane_steps(pxa_batch* b, int q);
 /* Capture the whole gradient into a CUDA graph and replay it (1, default) or launch the
  * kernels one by one (0). */
 int pxa_batch_set_graph(pxa_batch* b, int enable);
@@ -430,8 +439,9 @@ int pxa_batch_autotune(pxa_batch* b, int mode, const double* q0_dev, double* J_d
                        double* best_ms_host);
 /* Host: the count + 1 packed offsets (caller-owned array). */
 int pxa_batch_offsets(const pxa_batch* b, int64_t* offsets);
-/* Host: per problem, the taps (2 r + 1) of its FP32 lane band and of its FP64 band, and
- * whether its homogeneous parts use the Krylov exponential (1) or stepping (0) (count
+/* Host: per problem, the taps (2 r + 1) of its FP32 lane band and of its FP64 band (both
+ * of M^q, q = the lane_steps of pxa_batch_get_stats), and whether its homogeneous parts
+ * use the Krylov exponential (1) or the stepper's own propagator (0) (count
  * entries each, caller-owned; any may be NULL); the workspace must exist (after a
  * gradient). */
 int pxa_batch_problem_info(const pxa_batch* b, int* taps32, int* taps64, int* krylov);

@@ -36,6 +36,8 @@ struct pxa_batch {
   double tol = 1e-8, reach = 0.04;
   double hom_ratio = 1.0;  // Krylov exponential where the cost model puts it <= ratio x the stepper's propagator
   bool power = true;       // the stepper's propagator over a subinterval as one band of M^(K/P)
+  int lane_q_req = 0;      // CN steps per lane band application requested (0: automatic)
+  int lane_q = 1;          // in use: the lanes and stepped chains apply the band of M^q
   bool use_graph = true;
 
   // set-up (host)
@@ -142,23 +144,59 @@ int bprepare(pxa_batch* b) {
   std::vector<double> t64;
   b->nmax = b->r32max = b->r64max = b->subs_max = b->rpmax = 0;
   const int64_t kp = b->K / P;  // steps per subinterval
-  for (int i = 0; i < cnt; ++i) {
-    const int n = b->n[i];
-    const double h = b->L / n;
-    BatchInst& I = b->hinst[i];
-    I.n = n;
+  // The lanes and the stepped chains apply the product band of M^q, the CN map taken q
+  // times (q = 4, 2 or 1, dividing K/P): the same FMAs per CN step as q applications of
+  // M, but one barrier and halo refresh per q steps and q times less zero padding of the
+  // narrow bands; the FP64 band of M^q gives the sources (M^q - I) x. q = 1 keeps the
+  // long-double band of M. The widest q whose FP32 bands fit the lanes is taken.
+  auto stencil = [&](int i, BatchInst& I) {
+    const double h = b->L / b->n[i];
+    I.n = b->n[i];
     I.am = b->c / (2.0 * h) + b->nu[i] / (h * h);
     I.a0 = -2.0 * b->nu[i] / (h * h);
     I.ap = -b->c / (2.0 * h) + b->nu[i] / (h * h);
-    std::vector<double> taps;
-    int r = 0;
-    cn_band_taps(n, I.am, I.a0, I.ap, dt, taps, r);
-    // the FP32 lanes keep the taps above 2^-40 |m_0| (far below FP32 rounding)
-    const double cut = std::ldexp(std::fabs(taps[r]), -40);
-    int r32 = 0;
+  };
+  auto lane_band = [&](const BatchInst& I, int q, std::vector<double>& taps, int& r, int& r32) {
+    if (q == 1)
+      cn_band_taps(I.n, I.am, I.a0, I.ap, dt, taps, r);
+    else
+      cn_power_taps(I.n, I.am, I.a0, I.ap, dt, q, 50, taps, r);
+    // the FP32 lanes keep the taps above 2^-40 of the largest (far below FP32 rounding)
+    double big = 0.0;
+    for (double v : taps) big = std::max(big, std::fabs(v));
+    const double cut = std::ldexp(big, -40);
+    r32 = 0;
     for (int j = 1; j <= r; ++j)
       if (std::fabs(taps[r + j]) >= cut || std::fabs(taps[r - j]) >= cut) r32 = j;
-    if (r32 > BATCH_MAX_R) return bfail(b, PXA_ERR_INVALID, "a problem's CN band is wider than the lanes hold");
+  };
+  b->lane_q = 0;
+  for (int q : {4, 2, 1}) {
+    if ((b->lane_q_req != 0 && q != b->lane_q_req) || kp % q != 0) continue;
+    bool fits = true;
+    for (int i = 0; i < cnt && fits; ++i) {
+      BatchInst I{};
+      stencil(i, I);
+      std::vector<double> taps;
+      int r = 0, r32 = 0;
+      lane_band(I, q, taps, r, r32);
+      fits = r32 <= BATCH_MAX_R;
+    }
+    if (fits) {
+      b->lane_q = q;
+      break;
+    }
+  }
+  if (b->lane_q == 0)
+    return bfail(b, PXA_ERR_INVALID, b->lane_q_req != 0 && kp % b->lane_q_req != 0
+                                         ? "the requested CN steps per lane band do not divide K/P"
+                                         : "a problem's CN band is wider than the lanes hold");
+  for (int i = 0; i < cnt; ++i) {
+    const int n = b->n[i];
+    BatchInst& I = b->hinst[i];
+    stencil(i, I);
+    std::vector<double> taps;
+    int r = 0, r32 = 0;
+    lane_band(I, b->lane_q, taps, r, r32);
     I.r64 = r;
     I.r32 = r32;
     I.t64 = (int64_t)t64.size();
@@ -226,7 +264,7 @@ int bprepare(pxa_batch* b) {
     const double n = I.n, mm = b->m;
     const double t_kry = I.nsub * (2.0 * mm * mm * n + 10.0 * mm * n) / 8.2e9;
     const double t_step = I.rp > 0 ? std::max(2.0 * n * (2 * I.rp + 1) / 2.65e11, 5e-7)
-                                   : (double)k * std::max(2.0 * n * (2 * I.r32 + 1) / 2.65e11, 5e-7);
+                                   : (double)(k / b->lane_q) * std::max(2.0 * n * (2 * I.r32 + 1) / 2.65e11, 5e-7);
     if (P > 1 && t_kry <= b->hom_ratio * t_step)
       kry.push_back(i);
     else if (I.rp > 0)
@@ -292,7 +330,8 @@ int bprepare(pxa_batch* b) {
 // The whole gradient of every problem on stream st.
 int benqueue(pxa_batch* b, cudaStream_t st, int mode, const double* q0, double* J, double* grad) {
   const int cnt = b->count, P = mode == PXA_SERIAL ? 1 : b->P;
-  const int64_t K = b->K, k = K / b->P;
+  // band applications of M^q: K / q for a serial lane, K / (P q) per subinterval
+  const int64_t K = b->K / b->lane_q, k = b->K / b->P / b->lane_q;
   auto mark = [&](int i) {
     if (b->timing && b->ev[i]) cudaEventRecord(b->ev[i], st);
   };
@@ -460,6 +499,13 @@ int pxa_batch_set_power(pxa_batch* b, int enable) {
   return PXA_OK;
 }
 
+int pxa_batch_set_lane_steps(pxa_batch* b, int q) {
+  if (!b || (q != 0 && q != 1 && q != 2 && q != 4)) return PXA_ERR_INVALID;
+  b->lane_q_req = q;
+  brelease(b);
+  return PXA_OK;
+}
+
 int pxa_batch_set_timing(pxa_batch* b, int enable) {
   if (!b) return PXA_ERR_INVALID;
   BCUDA(b, cudaSetDevice(b->device), "cudaSetDevice");
@@ -617,6 +663,7 @@ int pxa_batch_get_stats(const pxa_batch* b, pxa_batch_stats* out) {
   s.krylov_problems = b->n_kry;
   s.power_problems = b->n_pow;
   s.band_power_max = b->rpmax > 0 ? 2 * b->rpmax + 1 : 0;
+  s.lane_steps = b->ready ? b->lane_q : 0;
   s.hom_ratio = b->hom_ratio;
   s.ms_lanes = b->ms[0];
   s.ms_chains = b->ms[1];

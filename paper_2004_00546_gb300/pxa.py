@@ -37,7 +37,7 @@ EXPORTS = [
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
     "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
-    "pxa_batch_set_homogeneous", "pxa_batch_set_power", "pxa_batch_set_timing",
+    "pxa_batch_set_homogeneous", "pxa_batch_set_power", "pxa_batch_set_lane_steps", "pxa_batch_set_timing",
     "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
     "pxa_batch_autotune", "pxa_batch_offsets", "pxa_batch_get_stats", "pxa_batch_problem_info",
 ]
@@ -79,7 +79,7 @@ class BatchStats(ctypes.Structure):
                 ("ms_lanes", ctypes.c_float), ("ms_chains", ctypes.c_float),
                 ("ms_adjoint_lanes", ctypes.c_float), ("ms_adjoint_chains", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("power_problems", ctypes.c_int),
-                ("band_power_max", ctypes.c_int)]
+                ("band_power_max", ctypes.c_int), ("lane_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -139,6 +139,7 @@ def load(path: str = LIB_PATH):
         "pxa_batch_set_graph": [p, i],
         "pxa_batch_set_homogeneous": [p, d],
         "pxa_batch_set_power": [p, i],
+        "pxa_batch_set_lane_steps": [p, i],
         "pxa_batch_set_timing": [p, i],
         "pxa_batch_gradient": [p, i, p, p, p],
         "pxa_batch_sync": [p],
@@ -419,6 +420,10 @@ class Batch:
 
     def set_homogeneous(self, ratio):
         self._check(self._L.pxa_batch_set_homogeneous(self._h, float(ratio)))
+
+    def set_lane_steps(self, q):
+        """CN steps per lane band application: 1, 2, 4, or 0 (automatic)."""
+        self._check(self._L.pxa_batch_set_lane_steps(self._h, int(q)))
 
     def set_power(self, enable):
         """Apply the stepper's subinterval propagator as one band of M^(K/P) (1) or step it (0)."""

@@ -185,6 +185,42 @@ def test_batch_propagator_band_equals_stepped_chain(X, torch, small, K, P):
         assert rel(res[True][1][sl], res[False][1][sl]) < 1e-4, i
 
 
+@pytest.mark.parametrize("K,P", [(512, 8), (96, 16)])
+def test_batch_lane_product_bands(X, torch, small, K, P):
+    """Lanes that apply the band of M^q (q CN steps at a time, q = 1, 2, 4 or chosen) give
+    the oracle's gradients within the FP32-stepping tolerance and agree with each other;
+    q = 4 is refused when it does not divide K/P (96/16 = 6, where the choice is 2)."""
+    q0 = dev(torch, small["q0"])
+    nprob = len(small["n"])
+    res = {}
+    for q in (1, 2, 4, 0):
+        b = X.Batch()
+        b.set(small["n"], small["nu"], c=small["c"], T=small["T"], K=K, P=P)
+        b.set_homogeneous(0.0)
+        b.set_lane_steps(q)
+        J = torch.empty(nprob, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(q0)
+        if (K // P) % max(q, 1) != 0:
+            with pytest.raises(X.PxaError):
+                b.gradient(X.PARAEXP, q0, J, g)
+            b.close()
+            continue
+        for mode in (X.PARAEXP, X.SERIAL):
+            b.gradient(mode, q0, J, g)
+            res[(q, mode)] = (J.cpu().numpy(), g.cpu().numpy())
+        used = b.stats()["lane_steps"]
+        assert used == (q if q else (4 if (K // P) % 4 == 0 else 2))
+        off = b.offsets()
+        b.close()
+    for (q, mode), (J, g) in res.items():
+        for i in range(nprob):
+            sl = slice(off[i], off[i + 1])
+            Jo, go = reference(small, off, i, K, P, False)
+            assert abs(J[i] - Jo) / Jo < 1e-4 and rel(g[sl], go) < 1e-4, (q, mode, i)
+            J1, g1 = res[(1, mode)]
+            assert abs(J[i] - J1[i]) / Jo < 1e-4 and rel(g[sl], g1[sl]) < 1e-4, (q, mode, i)
+
+
 def test_batch_rejects_bad_problems(X):
     b = X.Batch()
     with pytest.raises(X.PxaError):
