@@ -397,13 +397,16 @@ def run_ours(args, w, rank, world):
         m, sub = st["krylov_m"], st["krylov_substeps"]
         arnoldi = (8 * m + 4 * m * (m + 1) + 2 * m) * n  # operator, CGS2, norms, combine
         dense = 2 * (m ** 3) * (1 + int(np.log2(k // sub)))  # solve + squarings
-        chain = {"band": ("ad1_band_chain_kernel", None), "relpm": ("ad1_relpm_chain_kernel", None)}.get(
+        # the band chain: P - 1 links of one band product (2 flop per tap and point)
+        band_flop = 2.0 * st["prop_band_taps"] * n * (P - 1)
+        chain = {"band": ("ad1_band_chain_kernel", band_flop), "relpm": ("ad1_relpm_chain_kernel", None)}.get(
             head.rsplit("_", 1)[-1], ("ad1_chain_kernel", (P - 1) * sub * (arnoldi + dense)))
         kernels = {
             chain[0]: (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]), chain[1], 1, TRAFFIC.get(chain[0])),
+            # the lanes apply the band of M^q (lane_band_taps taps) k/q times per lane
             "cn_lanes_kernel": (0.5 * (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"]),
-                                FLOPS_CN_BAND_TAP * st["band_taps"] * n * k * P, P,
-                                TRAFFIC.get("cn_lanes_kernel")),
+                                FLOPS_CN_BAND_TAP * st["lane_band_taps"] * n * (k // max(st["lane_steps"], 1)) * P,
+                                P, TRAFFIC.get("cn_lanes_kernel")),
         }
     dom = max(kernels, key=lambda kk: kernels[kk][0])
     ms_dom, flops, sms_used, traffic = kernels[dom]

@@ -149,6 +149,9 @@ typedef struct {
   float tau_ratio;          /* k = adjoint-preparation time / direct time per step, as
                                last measured by the autotuner (0: not measured) */
   int checkpoint_intervals; /* C of the multi-checkpoint scheme in use (0: off) */
+  int lane_steps;           /* ADVDIFF_1D: q, the lanes apply the band of M^q */
+  int lane_band_taps;       /* ADVDIFF_1D: taps of that band */
+  int prop_band_taps;       /* ADVDIFF_1D with PXA_PROP_BAND: taps of the subinterval propagator's band */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -203,6 +206,12 @@ int pxa_set_memory(pxa_ctx* ctx, int policy);
  * pxa_set_memory is not used while the scheme is on. intervals = 0 or 1: off (default).
  * intervals < 0 or > 65536: PXA_ERR_INVALID. Invalidates the workspace. */
 int pxa_set_checkpoints(pxa_ctx* ctx, int intervals);
+/* ADVDIFF_1D: CN steps per band application of the Paraexp and serial lanes, q = 1, 2
+ * or 4 (the exact product band of M^q from the eigenvalues R_k^q, FP64 taps kept to
+ * 2^-52 of the largest; the sources become (M^q - I) x), or 0 (default): the largest of
+ * 4, 2, 1 that divides K/P. pxa_step keeps single steps. A q that does not divide K/P
+ * makes the next solve fail with PXA_ERR_INVALID. Invalidates the workspace. */
+int pxa_set_lane_steps(pxa_ctx* ctx, int q);
 /* BURGERS_1D adjoint evaluation (pxa_adjoint). BANDED falls back to RESTEP when its
  * records do not fit; pxa_get_stats reports which one is in use. */
 int pxa_set_adjoint(pxa_ctx* ctx, int impl);

@@ -319,6 +319,9 @@ struct pxa_ctx {
   // derived
   double am = 0, a0 = 0, ap = 0;  // advection-diffusion stencil
   int band_r = 0;
+  // ADVDIFF_1D lanes: the band of M^q (q CN steps per application) and q
+  double* taps_q = nullptr;
+  int band_rq = 0, lane_q = 1, lane_q_req = 0;
   std::vector<double> band_host;
 
   // workspace (device)
@@ -473,6 +476,8 @@ void release_workspace(pxa_ctx* c) {
   c->relpm_D = c->relpm_z = c->band_p = nullptr;
   c->band_pr = 0;
   c->st1d = c->taps1d = nullptr;
+  c->taps_q = nullptr;
+  c->band_rq = 0;
   c->lanes1d = 0;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
   c->status = nullptr;
@@ -627,10 +632,34 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->taps, c->band_host.size()))) return rc;
     PXA_CUDA(c, cudaMemcpy(c->taps, c->band_host.data(), sizeof(double) * c->band_host.size(),
                            cudaMemcpyHostToDevice), "copy taps");
+    // The lanes take K/P CN steps as K/(P q) applications of the band of M^q (q = 4, 2
+    // or 1, dividing K/P): M^q is circulant with taps from the eigenvalues R_k^q, and
+    // since the implicit map's taps decay geometrically its band is barely wider than
+    // M's, so q steps cost about one (FP64 taps kept to 2^-52 of the largest).
+    c->lane_q = 0;
+    for (int q : {4, 2, 1})
+      if ((c->lane_q_req == 0 || q == c->lane_q_req) && (c->K / P) % q == 0 && (q == 1 || n <= 4096)) {
+        c->lane_q = q;
+        break;
+      }
+    if (c->lane_q == 0) return fail(c, PXA_ERR_INVALID, "the requested CN steps per lane band do not divide K/P");
+    if (c->lane_q == 1) {
+      c->taps_q = c->taps;
+      c->band_rq = c->band_r;
+    } else {
+      std::vector<double> tq;
+      cn_power_taps(n, c->am, c->a0, c->ap, dt, c->lane_q, 52, tq, c->band_rq);
+      if ((rc = alloc(c, &c->taps_q, tq.size()))) return rc;
+      PXA_CUDA(c, cudaMemcpy(c->taps_q, tq.data(), sizeof(double) * tq.size(), cudaMemcpyHostToDevice),
+               "copy taps");
+    }
+    c->stats.lane_steps = c->lane_q;
+    c->stats.lane_band_taps = 2 * c->band_rq + 1;
     if (c->prop == PXA_PROP_BAND) {
       // the subinterval propagator exp(tau A) or M^(K/P) as one circulant band
       std::vector<double> bt;
       cn_power_taps(n, c->am, c->a0, c->ap, dt, c->K / P, 50, bt, c->band_pr, c->kry_phi == PXA_PHI_EXP);
+      c->stats.prop_band_taps = 2 * c->band_pr + 1;
       if ((rc = alloc(c, &c->band_p, bt.size()))) return rc;
       PXA_CUDA(c, cudaMemcpy(c->band_p, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice), "copy");
     }
@@ -836,7 +865,10 @@ void ev_record(pxa_ctx* c, int i) {
 int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   cudaStream_t st = c->stream;
   const bool do_d = parts & 1, do_a = parts & 2;
-  const int n = c->op.n, P = c->P, r = c->band_r, th = threads_for(n);
+  // the lanes apply the band of M^q (taps_q, half-width r) K/q or K/(P q) times
+  const int n = c->op.n, P = c->P, r = c->band_rq, th = threads_for(n);
+  const double* taps = c->taps_q;
+  const int64_t lq = c->lane_q;
   if (n > 4096)
     return fail(c, PXA_ERR_INVALID, "ADVDIFF_1D with n > 4096: the lanes and chains keep a lane in shared memory "
                                     "(pxa_cn_lanes_1d steps longer grids)");
@@ -846,14 +878,14 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (mode == PXA_SERIAL) {
     if (do_d) {
       ev_record(c, 0);
-      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 0, K, q0, nullptr, c->E), "cn serial");
+      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, taps, 0, K / lq, q0, nullptr, c->E), "cn serial");
       ev_record(c, 1);
       ev_record(c, 2);
-      PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, nullptr, c->E, nullptr, c->qT,
+      PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, taps, nullptr, c->E, nullptr, c->qT,
                                               nullptr, Jdev, c->status), "superpose");
     }
     if (do_a) {
-      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, c->taps, 1, K, c->qT, nullptr, c->EA), "cn serial T");
+      PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, taps, 1, K / lq, c->qT, nullptr, c->EA), "cn serial T");
       ev_record(c, 3);
       ev_record(c, 4);
       PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, nullptr, c->EA, nullptr, grad, c->status), "grad");
@@ -872,9 +904,10 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
   ev_record(c, 0);
   // Eq. linzero: the shifted problem has zero IC and source A q0; in CN form the
-  // lane recursion is q~' = M q~ + (M - I) q0.
-  PXA_CUDA(c, launch_band_minus_identity(st, n, r, c->taps, 0, q0, c->src), "src");
-  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 0, k, nullptr, c->src, c->E), "lanes");
+  // lane recursion is q~' = M q~ + (M - I) q0, and over q steps
+  // q~'' = M^q q~ + (M^q - I) q0.
+  PXA_CUDA(c, launch_band_minus_identity(st, n, r, taps, 0, q0, c->src), "src");
+  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, taps, 0, k / lq, nullptr, c->src, c->E), "lanes");
   ev_record(c, 1);
   if (P > 1 && c->prop == PXA_PROP_BAND) {
     PXA_CUDA(c, launch_ad1_band_chain(st, n, c->band_pr, c->band_p, 0, c->E, 0, 1, P - 1, c->hsum), "chain");
@@ -888,12 +921,12 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                  c->v_in_smem, c->status, c->errmax), "chain");
   }
   ev_record(c, 2);
-  PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, c->taps, q0, c->E + (size_t)(P - 1) * n,
+  PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, taps, q0, c->E + (size_t)(P - 1) * n,
                                           P > 1 ? c->hsum : nullptr, c->qT, c->srcA, Jdev,
                                           c->status), "superpose");
   }
   if (!do_a) return PXA_OK;
-  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, c->taps, 1, k, nullptr, c->srcA, c->EA), "adj lanes");
+  PXA_CUDA(c, launch_cn_lanes(st, P, th, n, r, taps, 1, k / lq, nullptr, c->srcA, c->EA), "adj lanes");
   ev_record(c, 3);
   if (P > 1 && c->prop == PXA_PROP_BAND) {
     PXA_CUDA(c, launch_ad1_band_chain(st, n, c->band_pr, c->band_p, 1, c->EA, P - 1, -1, P - 1, c->hsumA),
@@ -1522,6 +1555,14 @@ int pxa_set_target(pxa_ctx* c, const double* target_dev) {
 int pxa_set_memory(pxa_ctx* c, int policy) {
   if (!c || (policy != PXA_STORE_FULL && policy != PXA_STORE_CHECKPOINTS)) return PXA_ERR_INVALID;
   c->memory = policy;
+  release_workspace(c);
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_lane_steps(pxa_ctx* c, int q) {
+  if (!c || (q != 0 && q != 1 && q != 2 && q != 4)) return PXA_ERR_INVALID;
+  c->lane_q_req = q;
   release_workspace(c);
   invalidate(c);
   return PXA_OK;

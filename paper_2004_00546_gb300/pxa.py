@@ -31,7 +31,7 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_set_checkpoints", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_set_checkpoints", "pxa_set_lane_steps", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
@@ -67,7 +67,9 @@ class Stats(ctypes.Structure):
                 ("ms_adjoint_prep", ctypes.c_float), ("adjoint_band", ctypes.c_int),
                 ("group_direct", ctypes.c_int), ("group_sweep", ctypes.c_int),
                 ("chunks", ctypes.c_int), ("partition_r", ctypes.c_float),
-                ("tau_ratio", ctypes.c_float), ("checkpoint_intervals", ctypes.c_int)]
+                ("tau_ratio", ctypes.c_float), ("checkpoint_intervals", ctypes.c_int),
+                ("lane_steps", ctypes.c_int), ("lane_band_taps", ctypes.c_int),
+                ("prop_band_taps", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):
@@ -109,6 +111,7 @@ def load(path: str = LIB_PATH):
         "pxa_set_overlap": [p, i],
         "pxa_set_partition": [p, d],
         "pxa_set_checkpoints": [p, i],
+        "pxa_set_lane_steps": [p, i],
         "pxa_set_propagator": [p, i, i],
         "pxa_partition_bounds": [i64, i, d, i, ctypes.POINTER(i64)],
         "pxa_set_groups": [p, i, i],
@@ -254,6 +257,10 @@ class Context:
 
     def set_partition(self, r):
         self._check(self._L.pxa_set_partition(self._h, float(r)))
+
+    def set_lane_steps(self, q):
+        """CN steps per lane band application (1D advection-diffusion): 1, 2, 4 or 0 (auto)."""
+        self._check(self._L.pxa_set_lane_steps(self._h, int(q)))
 
     def set_checkpoints(self, intervals):
         """Multi-checkpoint scheme (Sec. 3.5) with `intervals` equal intervals (0: off)."""

@@ -735,6 +735,39 @@ def test_relpm_stepper_paraexp_equals_serial_stepping(X, torch, n, nu, K, P):
     assert rel(host(out), go) < 1e-10
 
 
+# ---- lanes stepping with the product band of M^q ------------------------------------------------
+@pytest.mark.parametrize("n,nu,K,P", [(256, 0.01, 4096, 8), (100, 0.0, 512, 4), (333, 0.05, 1024, 16),
+                                      (64, 0.02, 96, 16), (17, 0.1, 64, 64)])
+def test_lane_product_bands_keep_the_gradient(X, torch, n, nu, K, P):
+    """The lanes apply the band of M^q, q CN steps at a time (q = 1, 2, 4 or the widest
+    dividing K/P): serial stepping and Paraexp with the stepper propagator match the
+    oracle's serial CN gradient for every q, and q = 4 is refused where K/P = 6."""
+    c, T = 1.0, 1.0
+    q0 = I.grf_k2(n, 29)
+    Jo, go, _ = O.ad1_cn_gradient_serial(q0, c, nu, T, K)
+    qd = dev(torch, q0)
+    k = K // P
+    for q in (1, 2, 4, 0):
+        ctx = ad1_ctx(X, n, c, nu, T, K, P, m=30, tol=1e-12, phi=X.PHI_STEPPER)
+        ctx.set_propagator(X.PROP_BAND, 150)
+        ctx.set_lane_steps(q)
+        ctx.set_control(qd)
+        out = torch.empty_like(qd)
+        if q and k % q:
+            with pytest.raises(X.PxaError):
+                ctx.gradient(X.PARAEXP, out)
+            ctx.close()
+            continue
+        for mode in (X.SERIAL, X.PARAEXP):
+            J = ctx.gradient(mode, out)
+            assert abs(J - Jo) / Jo < 1e-10, (q, mode)
+            assert rel(host(out), go) < 1e-10, (q, mode)
+        st = ctx.stats()
+        assert st["lane_steps"] == (q if q else (4 if k % 4 == 0 else 2 if k % 2 == 0 else 1))
+        assert st["lane_band_taps"] >= st["band_taps"]
+        ctx.close()
+
+
 # ---- the subinterval propagator as a circulant band -------------------------------------------
 @pytest.mark.parametrize("phi", ["exp", "stepper"])
 @pytest.mark.parametrize("n,c,nu,span", [(256, 1.0, 0.01, 512), (64, 1.0, 0.0, 1200), (128, 0.0, 0.05, 800),
