@@ -19,16 +19,27 @@
 //                            4th-order Magnus steps, Krylov exp and phi_1.
 //   sum_lanes_kernel         Eq. fullAdjSolHyb integrated against s(t): the forcing
 //                            gradient of Eq. paramupdate.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "krylov.cuh"
 #include "kernels_1d.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace pxa {
 
 // ----------------------------------------------------------------------------
-// Circulant band stepper: (M x)_i = sum_{j=-r..r} m_j x_{i+j} (+ src_i).
-// Shared layout: taps[2r+1], xa[n+2r], xb[n+2r], src[n]. The halo of width r is
-// refreshed after every step so that the inner loop has no wrap-around test.
+// Circulant band stepper: x <- M x + src, (M x)_i = sum_{j=-r..r} m_j x_{i+j} (M^T: taps
+// reversed), `steps` times, one thread-block cluster of CNL_CL CTAs per lane. A step costs
+// n (2r+1) FP64 FMAs, microseconds on one SM (its FP64 units take one warp instruction per
+// 64 cycles whatever the active lanes), so the lane is spread over the cluster: every CTA
+// keeps the whole vector (X0, X1 with r-point halos, refreshed with every write so that
+// the inner loop has no wrap-around test), forms the outputs of its slice 64 points per
+// pass (two point groups, the taps of each point split over four warps whose partial
+// sums are added in a fixed order), and writes them with their halo copies into the next
+// buffer of every CTA through distributed shared memory; one cluster barrier ends a step
+// and keeps any CTA from writing into a buffer that another may still read.
 // ----------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void put_halo(T* buf, int n, int r, int p, T v) {
@@ -37,35 +48,55 @@ __device__ __forceinline__ void put_halo(T* buf, int n, int r, int p, T v) {
   if (p >= n - r) buf[p - n + r] = v;
 }
 
-__global__ void cn_lanes_kernel(int n, int r, const double* __restrict__ taps, int transpose,
-                                int64_t steps, const double* __restrict__ x0,
-                                const double* __restrict__ src, double* __restrict__ out) {
+constexpr int CNL_CL = 8;         // CTAs per lane
+constexpr int CNL_THREADS = 256;  // 8 warps: 2 point groups x 4 tap groups
+constexpr int CNL_TG = 4;
+
+__global__ void __launch_bounds__(CNL_THREADS) cn_lanes_kernel(int n, int r, const double* __restrict__ taps,
+                                                               int transpose, int64_t steps,
+                                                               const double* __restrict__ x0,
+                                                               const double* __restrict__ src,
+                                                               double* __restrict__ out) {
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int lane = (int)blockIdx.x / C;
   const int w = 2 * r + 1;
   double* tp = sm;
-  double* xa = tp + w;
-  double* xb = xa + n + 2 * r;
-  double* sr = xb + n + 2 * r;
-  const int lane = blockIdx.x;
+  double* X[2] = {tp + w, tp + w + n + 2 * r};
+  double* sr = X[1] + n + 2 * r;  // [n] the source (own slice)
+  double* part = sr + n;          // [8 warps][32] partial sums
+  const int nc = (n + C - 1) / C, p0 = rank * nc, p1 = min(n, p0 + nc);
+  const int wid = (int)threadIdx.x >> 5, ln = (int)threadIdx.x & 31;
+  const int tg = wid % CNL_TG, pg = wid / CNL_TG;
+  const int j0 = tg * w / CNL_TG, j1 = (tg + 1) * w / CNL_TG;  // this warp's run of taps
   for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? taps[w - 1 - j] : taps[j];
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    put_halo(xa, n, r, p, x0 ? x0[p] : 0.0);
-    sr[p] = src ? src[p] : 0.0;
-  }
-  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(X[0], n, r, p, x0 ? x0[p] : 0.0);
+  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) sr[p] = src ? src[p] : 0.0;
+  cl.sync();  // every CTA of the cluster runs before any remote write
+  int cur = 0;
   for (int64_t s = 0; s < steps; ++s) {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const double* xp = xa + p;  // xp[r + j] = x_{p+j}
-      double acc = sr[p];
-      for (int j = 0; j < w; ++j) acc = fma(tp[j], xp[j], acc);
-      put_halo(xb, n, r, p, acc);
+    const double* xa = X[cur];
+    for (int pb = p0; pb < p1; pb += 64) {
+      const int p = pb + 32 * pg + ln;
+      double acc = 0.0;
+      if (p < p1) {
+        const double* xp = xa + p;  // xp[r + j] = x_{p+j}
+        for (int j = j0; j < j1; ++j) acc = fma(tp[j], xp[j], acc);
+      }
+      part[wid * 32 + ln] = acc;
+      __syncthreads();
+      if (tg == 0 && p < p1) {
+        const double* pp = part + pg * CNL_TG * 32 + ln;
+        const double y = sr[p] + ((pp[0] + pp[32]) + (pp[64] + pp[96]));
+        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(X[cur ^ 1], d), n, r, p, y);
+      }
+      __syncthreads();  // part is reused by the next pass
     }
-    __syncthreads();
-    double* t = xa;
-    xa = xb;
-    xb = t;
+    cl.sync();
+    cur ^= 1;
   }
-  for (int p = threadIdx.x; p < n; p += blockDim.x) out[(size_t)lane * n + p] = xa[r + p];
+  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) out[(size_t)lane * n + p] = X[cur][r + p];
 }
 
 // y = M x - x (or M^T x - x) for the circulant band: the source of the shifted lanes.
@@ -235,44 +266,79 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
 
 // Eq. hom / Eq. adjHomNormal with the subinterval propagator B itself as a circulant band
 // (exp(tau A) or the CN power M^(K/P); periodic grid, constant coefficients):
-// h = 0; for l < count: h += E[first + l stride]; h = B h (B^T: taps reversed). One block;
-// shared layout taps[2r+1], xa[n+2r], xb[n+2r] with r-point halos as in cn_lanes_kernel.
+// h = 0; for l < count: h += E[first + l stride]; h = B h (B^T: taps reversed).
+// One thread-block cluster: B's band can span the whole circulant, so every CTA keeps the
+// whole vector (buffers X0, X1 with r-point halos as in cn_lanes_kernel); in link l
+// each CTA adds E's row to its copy of X[l % 2], forms the outputs of its slice of points
+// (32 at a time, each point's taps split over the CTA's warps, whose partial sums warp 0
+// adds in a fixed order: an FP64 warp instruction costs the same with idle lanes, so the
+// split, not the lane count, sets the time) and writes them, with their halo copies,
+// into X[(l + 1) % 2] of every CTA of the cluster through distributed shared memory. The cluster barrier that ends a link makes
+// the new vector complete everywhere and keeps any CTA from writing into a buffer that
+// another may still read.
 __global__ void ad1_band_chain_kernel(int n, int r, const double* __restrict__ taps, int transpose,
                                       const double* __restrict__ E, int first, int stride, int count,
                                       double* __restrict__ hout) {
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int w = 2 * r + 1;
   double* tp = sm;
-  double* xa = tp + w;
-  double* xb = xa + n + 2 * r;
+  double* X[2] = {tp + w, tp + w + n + 2 * r};
+  double* part = X[1] + n + 2 * r;  // [warps][32] partial sums
+  const int nc = (n + C - 1) / C, p0 = rank * nc, p1 = min(n, p0 + nc);
+  const int G = (int)blockDim.x / 32, lane = (int)threadIdx.x & 31, g = (int)threadIdx.x >> 5;
+  const int j0 = g * w / G, j1 = (g + 1) * w / G;  // this warp's run of taps
   for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? taps[w - 1 - j] : taps[j];
-  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, 0.0);
-  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(X[0], n, r, p, 0.0);
+  cl.sync();  // every CTA of the cluster runs before any remote write
+  int cur = 0;
   for (int l = 0; l < count; ++l) {
+    double* xa = X[cur];
     const double* e = E + (size_t)(first + l * stride) * n;
     for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, xa[r + p] + e[p]);
     __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const double* xp = xa + p;  // xp[r + j] = x_{p+j}
+    for (int pb = p0; pb < p1; pb += 32) {
+      const int p = pb + lane;
       double acc = 0.0;
-      for (int j = 0; j < w; ++j) acc = fma(tp[j], xp[j], acc);
-      put_halo(xb, n, r, p, acc);
+      if (p < p1) {
+        const double* xp = xa + p;  // xp[r + j] = x_{p+j}
+        for (int j = j0; j < j1; ++j) acc = fma(tp[j], xp[j], acc);
+      }
+      part[g * 32 + lane] = acc;
+      __syncthreads();
+      if (g == 0 && p < p1) {
+        double y = part[lane];
+        for (int q = 1; q < G; ++q) y += part[q * 32 + lane];
+        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(X[cur ^ 1], d), n, r, p, y);
+      }
+      __syncthreads();  // part is reused by the next 32 points
     }
-    __syncthreads();
-    double* t = xa;
-    xa = xb;
-    xb = t;
+    cl.sync();
+    cur ^= 1;
   }
-  for (int p = threadIdx.x; p < n; p += blockDim.x) hout[p] = xa[r + p];
+  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) hout[p] = X[cur][r + p];
 }
 
 cudaError_t launch_ad1_band_chain(cudaStream_t st, int n, int r, const double* taps, int transpose,
                                   const double* E, int first, int stride, int count, double* hout) {
-  const size_t sh = sizeof(double) * ((size_t)(2 * r + 1) + 2 * (size_t)(n + 2 * r));
+  constexpr int CL = 8;  // CTAs of the cluster (portable size)
+  const size_t sh = sizeof(double) * ((size_t)(2 * r + 1) + 2 * (size_t)(n + 2 * r) + 256);
   cudaError_t e = cudaFuncSetAttribute(ad1_band_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
-  ad1_band_chain_kernel<<<1, 512, sh, st>>>(n, r, taps, transpose, E, first, stride, count, hout);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sh;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ad1_band_chain_kernel, n, r, taps, transpose, E, first, stride, count, hout);
 }
 
 // One vector: y = exp(ts A)^nsub x (building block).
@@ -609,13 +675,23 @@ size_t ks_layout_doubles() {
 cudaError_t launch_cn_lanes(cudaStream_t st, int lanes, int threads, int n, int r,
                             const double* taps, int transpose, int64_t steps, const double* x0,
                             const double* src, double* out) {
-  size_t sh = sizeof(double) * ((size_t)(2 * r + 1) + 2 * (size_t)(n + 2 * r) + n);
-  if (sh > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(cn_lanes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-  }
-  cn_lanes_kernel<<<lanes, threads, sh, st>>>(n, r, taps, transpose, steps, x0, src, out);
-  return cudaGetLastError();
+  (void)threads;  // the cluster kernel's block shape is fixed
+  const size_t sh = sizeof(double) * ((size_t)(2 * r + 1) + 2 * (size_t)(n + 2 * r) + n + 8 * 32);
+  cudaError_t e = cudaFuncSetAttribute(cn_lanes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(lanes * CNL_CL);
+  cfg.blockDim = dim3(CNL_THREADS);
+  cfg.dynamicSmemBytes = sh;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CNL_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cn_lanes_kernel, n, r, taps, transpose, steps, x0, src, out);
 }
 
 cudaError_t launch_band_minus_identity(cudaStream_t st, int n, int r, const double* taps,
