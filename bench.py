@@ -70,7 +70,7 @@ SM_CLOCK_HZ = 2.07e9
 # kernel changed after the capture.
 TRAFFIC = {
     "ad1_chain_kernel": 82.7e3,
-    "cn_lanes_kernel": None,  # the lane kernel now runs on thread-block clusters
+    "cn_lanes_kernel": 15.9e3,
     # the direct solve is 8 chunk launches of 61.95 KB DRAM reads each (the trajectory
     # rows stay in L2 during the launch)
     "bu1_rk4_sweep_kernel": 8 * 61.95e3,
