@@ -89,3 +89,17 @@ def test_batch_entry_points_reject_bad_arguments_without_a_device(pxa_lib):
     assert L.pxa_batch_sync(None) == pxa.ERR_INVALID
     assert L.pxa_batch_last_error(None) == b"null batch"
     L.pxa_batch_destroy(None)  # must be a no-op
+    assert L.pxa_batch_set_power(None, 1) == pxa.ERR_INVALID
+    assert L.pxa_batch_set_lane_steps(None, 4) == pxa.ERR_INVALID
+    assert L.pxa_batch_set_homogeneous(None, 1.0) == pxa.ERR_INVALID
+
+
+def test_setters_reject_null_contexts_and_bad_values_without_a_device(pxa_lib):
+    """The configuration calls added for the multi-checkpoint scheme, the lanes' product
+    bands and the propagator choice answer on the host: a null context, an interval
+    count, a CN-steps-per-band value or a propagator outside their ranges."""
+    L = pxa_lib
+    assert L.pxa_set_checkpoints(None, 5) == pxa.ERR_INVALID
+    assert L.pxa_set_lane_steps(None, 4) == pxa.ERR_INVALID
+    assert L.pxa_set_propagator(None, pxa.PROP_BAND, 150) == pxa.ERR_INVALID
+    assert L.pxa_set_partition(None, 0.5) == pxa.ERR_INVALID
