@@ -63,20 +63,19 @@ __global__ void __launch_bounds__(CNL_THREADS) cn_lanes_kernel(int n, int r, con
   const int lane = (int)blockIdx.x / C;
   const int w = 2 * r + 1;
   double* tp = sm;
-  double* X[2] = {tp + w, tp + w + n + 2 * r};
-  double* sr = X[1] + n + 2 * r;  // [n] the source (own slice)
+  double* xa = tp + w;            // the current vector (same offset in every CTA)
+  double* xb = xa + n + 2 * r;    // the next one
+  double* sr = xb + n + 2 * r;    // [n] the source (own slice)
   double* part = sr + n;          // [8 warps][32] partial sums
   const int nc = (n + C - 1) / C, p0 = rank * nc, p1 = min(n, p0 + nc);
   const int wid = (int)threadIdx.x >> 5, ln = (int)threadIdx.x & 31;
   const int tg = wid % CNL_TG, pg = wid / CNL_TG;
   const int j0 = tg * w / CNL_TG, j1 = (tg + 1) * w / CNL_TG;  // this warp's run of taps
   for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? taps[w - 1 - j] : taps[j];
-  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(X[0], n, r, p, x0 ? x0[p] : 0.0);
+  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, x0 ? x0[p] : 0.0);
   for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) sr[p] = src ? src[p] : 0.0;
   cl.sync();  // every CTA of the cluster runs before any remote write
-  int cur = 0;
   for (int64_t s = 0; s < steps; ++s) {
-    const double* xa = X[cur];
     for (int pb = p0; pb < p1; pb += 64) {
       const int p = pb + 32 * pg + ln;
       double acc = 0.0;
@@ -89,14 +88,16 @@ __global__ void __launch_bounds__(CNL_THREADS) cn_lanes_kernel(int n, int r, con
       if (tg == 0 && p < p1) {
         const double* pp = part + pg * CNL_TG * 32 + ln;
         const double y = sr[p] + ((pp[0] + pp[32]) + (pp[64] + pp[96]));
-        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(X[cur ^ 1], d), n, r, p, y);
+        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(xb, d), n, r, p, y);
       }
       __syncthreads();  // part is reused by the next pass
     }
     cl.sync();
-    cur ^= 1;
+    double* t = xa;
+    xa = xb;
+    xb = t;
   }
-  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) out[(size_t)lane * n + p] = X[cur][r + p];
+  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) out[(size_t)lane * n + p] = xa[r + p];
 }
 
 // y = M x - x (or M^T x - x) for the circulant band: the source of the shifted lanes.
@@ -273,9 +274,9 @@ __global__ void ad1_relpm_chain_kernel(int n, double am, double a0, double ap, i
 // (32 at a time, each point's taps split over the CTA's warps, whose partial sums warp 0
 // adds in a fixed order: an FP64 warp instruction costs the same with idle lanes, so the
 // split, not the lane count, sets the time) and writes them, with their halo copies,
-// into X[(l + 1) % 2] of every CTA of the cluster through distributed shared memory. The cluster barrier that ends a link makes
-// the new vector complete everywhere and keeps any CTA from writing into a buffer that
-// another may still read.
+// into X[(l + 1) % 2] of every CTA of the cluster through distributed shared memory.
+// The cluster barrier that ends a link makes the new vector complete everywhere and
+// keeps any CTA from writing into a buffer that another may still read.
 __global__ void ad1_band_chain_kernel(int n, int r, const double* __restrict__ taps, int transpose,
                                       const double* __restrict__ E, int first, int stride, int count,
                                       double* __restrict__ hout) {
@@ -284,17 +285,16 @@ __global__ void ad1_band_chain_kernel(int n, int r, const double* __restrict__ t
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int w = 2 * r + 1;
   double* tp = sm;
-  double* X[2] = {tp + w, tp + w + n + 2 * r};
-  double* part = X[1] + n + 2 * r;  // [warps][32] partial sums
+  double* xa = tp + w;              // the current vector (same offset in every CTA)
+  double* xb = xa + n + 2 * r;      // the next one
+  double* part = xb + n + 2 * r;    // [warps][32] partial sums
   const int nc = (n + C - 1) / C, p0 = rank * nc, p1 = min(n, p0 + nc);
   const int G = (int)blockDim.x / 32, lane = (int)threadIdx.x & 31, g = (int)threadIdx.x >> 5;
   const int j0 = g * w / G, j1 = (g + 1) * w / G;  // this warp's run of taps
   for (int j = threadIdx.x; j < w; j += blockDim.x) tp[j] = transpose ? taps[w - 1 - j] : taps[j];
-  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(X[0], n, r, p, 0.0);
+  for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, 0.0);
   cl.sync();  // every CTA of the cluster runs before any remote write
-  int cur = 0;
   for (int l = 0; l < count; ++l) {
-    double* xa = X[cur];
     const double* e = E + (size_t)(first + l * stride) * n;
     for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo(xa, n, r, p, xa[r + p] + e[p]);
     __syncthreads();
@@ -310,14 +310,16 @@ __global__ void ad1_band_chain_kernel(int n, int r, const double* __restrict__ t
       if (g == 0 && p < p1) {
         double y = part[lane];
         for (int q = 1; q < G; ++q) y += part[q * 32 + lane];
-        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(X[cur ^ 1], d), n, r, p, y);
+        for (int d = 0; d < C; ++d) put_halo(cl.map_shared_rank(xb, d), n, r, p, y);
       }
       __syncthreads();  // part is reused by the next 32 points
     }
     cl.sync();
-    cur ^= 1;
+    double* t = xa;
+    xa = xb;
+    xb = t;
   }
-  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) hout[p] = X[cur][r + p];
+  for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) hout[p] = xa[r + p];
 }
 
 cudaError_t launch_ad1_band_chain(cudaStream_t st, int n, int r, const double* taps, int transpose,
