@@ -45,6 +45,8 @@ WORKLOADS = {
     "advdiff1d_lanes": dict(kind="lanes1d", n=1 << 22, lanes=64, steps=10,
                             label="1D FP32 CN band lanes kernel, 64 lanes x 2^22 points (1 GiB per state array), "
                                   "c=1 nu=1e-6 dt=h/8 (21-tap band)"),
+    "spmv_csr": dict(kind="spmv", n=1 << 25, label="CSR sparse matrix-vector product, the 1D advection-diffusion "
+                                                    "stencil (c=1, nu=0.01) in CSR form, 2^25 rows x 3 entries, FP64"),
     "batched1d": dict(kind="batched1d", count=256, c=1.0, T=1.0, K=4096, P=16,
                       label="256 independent 1D advection-diffusion problems, n ~ U{128..2048}, "
                             "nu ~ logU[1e-3, 1e-1], T=1 CN 4096 steps, P=16, FP32 stepping, FP64 Krylov"),
@@ -71,6 +73,7 @@ SM_CLOCK_HZ = 2.07e9
 TRAFFIC = {
     "ad1_chain_kernel": 82.7e3,
     "cn_lanes_kernel": 15.9e3,
+    "spmv_csr_kernel": 1744881408 + 257540352,
     # the direct solve is 8 chunk launches of 61.95 KB DRAM reads each (the trajectory
     # rows stay in L2 during the launch)
     "bu1_rk4_sweep_kernel": 8 * 61.95e3,
@@ -537,12 +540,48 @@ def run_reference_batch(args, w, world):
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_spmv(args, w, world):
+    """The reference arm of the SpMV workload: the oracle's CSR product on the first 2^21
+    rows per step (bounded sample), as GB/s of the same algorithmic bytes per row."""
+    import oracle as O
+
+    n, m = w["n"], 1 << 21
+    h = 2.0 * np.pi / n
+    am, a0, ap = 1.0 / (2 * h) + 0.01 / h ** 2, -2 * 0.01 / h ** 2, -1.0 / (2 * h) + 0.01 / h ** 2
+    i = np.arange(m)
+    col = np.stack([(i - 1) % n, i, (i + 1) % n], 1).ravel().astype(np.int32)
+    val = np.tile([am, a0, ap], m)
+    rp = np.arange(0, 3 * m + 1, 3, dtype=np.int64)
+    x = np.random.default_rng(2004).standard_normal(n)
+    for _ in range(args.warmup):
+        O.spmv_csr(rp, col, val, x)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.spmv_csr(rp, col, val, x)
+        t.append(time.perf_counter() - t0)
+    per_row = (8.0 + 12.0 * 3 + 16.0)  # bytes per row, as the GPU line counts them
+    value = per_row * m / float(np.mean(t)) / 1e9
+    sample = f"first {m} of {n} rows per step"
+    return {"impl": "reference", "metric": "HBM GB/s of the CSR sparse matrix-vector product", "value": value,
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(t)) * 1e3 * n / m, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": w["label"]},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, w, rank, world):
     """The reference arm: the serial FP64 CPU oracle, timed on this host's cores."""
     if rank != 0:
         return None
     if w["kind"] == "batched1d":
         return run_reference_batch(args, w, world)
+    if w["kind"] in ("lanes1d", "lanes2d"):
+        return {"impl": "reference", "unavailable": "a single-kernel HBM stress measurement with no gradient; "
+                                                    "the oracle has no counterpart kernel to time"}
+    if w["kind"] == "spmv":
+        return run_reference_spmv(args, w, world)
     inp = make_inputs(w)
     # bounded sample per step: the first K_s steps of the window (direct + adjoint);
     # the cost is linear in the number of steps, so throughput scales by K_s / K
@@ -651,6 +690,70 @@ def run_lanes1d(args, w):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "traffic": None, "peak_kind": "measured copy bandwidth"},
             "clocks": clk.summary(), "gpu_launches": steps}
+
+
+def run_spmv(args, w):
+    """HBM roofline of the CSR sparse matrix-vector product at a size far above L2 (2 GB
+    per product): algorithmic bytes = row pointers 8 (n + 1) + entries 12 nnz (int32
+    column, FP64 value) + x 8 n (read once) + y 8 n. Sampled rows are checked against the
+    oracle's definition, and the oracle is timed on the first 2^21 rows."""
+    import torch
+
+    import oracle as O
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    X.load()
+    n, c, nu = w["n"], 1.0, 0.01
+    h = 2.0 * np.pi / n
+    am, a0, ap = c / (2 * h) + nu / h ** 2, -2 * nu / h ** 2, -c / (2 * h) + nu / h ** 2
+    i = torch.arange(n, device="cuda", dtype=torch.int64)
+    col = torch.stack([(i - 1) % n, i, (i + 1) % n], 1).reshape(-1).to(torch.int32)
+    val = torch.tensor([am, a0, ap], device="cuda", dtype=torch.float64).repeat(n)
+    rp = torch.arange(0, 3 * n + 1, 3, device="cuda", dtype=torch.int64)
+    gen = torch.Generator(device="cuda").manual_seed(2004)
+    x = torch.randn(n, device="cuda", dtype=torch.float64, generator=gen)
+    y = torch.empty_like(x)
+    del i
+    for _ in range(max(args.warmup, 3)):
+        X.spmv_csr(rp, col, val, x, y)
+    steps = max(args.steps, 3)
+    times = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(steps):  # the 2 GB operands do not fit in L2
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            X.spmv_csr(rp, col, val, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    nnz = 3 * n
+    alg = 8.0 * (n + 1) + 12.0 * nnz + 16.0 * n
+    gbs = alg / (ms * 1e-3) / 1e9
+    peak = measured_hbm_peak()
+    # parity on sampled rows and the oracle's time on a bounded sample
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    m = 1 << 21
+    rph, colh, valh = rp[: m + 1].cpu().numpy(), col[: 3 * m].cpu().numpy(), val[: 3 * m].cpu().numpy()
+    t0 = time.perf_counter()
+    ref = O.spmv_csr(rph, colh, valh, xh)
+    dt_cpu = time.perf_counter() - t0
+    err = float(np.max(np.abs(yh[:m] - ref) / (np.abs(valh.reshape(m, 3)).sum(1) * np.abs(xh).max())))
+    cpu = {"value": alg * m / n / dt_cpu / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {m} of {n} rows ({dt_cpu:.2f} s), the same bytes per row"}
+    return {"metric": "HBM GB/s of the CSR sparse matrix-vector product", "value": gbs, "unit": "GB/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded normal x; the stencil's coefficients)",
+            "config": {"workload": w["label"], "l2": "operands 2 GB, far above L2"},
+            "rel_err_max_sampled": err,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": TRAFFIC.get("spmv_csr_kernel"), "peak_kind": "measured copy bandwidth",
+                         "bytes_per_product": alg},
+            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": steps}
 
 
 def measured_hbm_peak():
@@ -872,6 +975,8 @@ def main():
         line = run_lanes2d(args, w)
     elif w["kind"] == "lanes1d":
         line = run_lanes1d(args, w)
+    elif w["kind"] == "spmv":
+        line = run_spmv(args, w)
     elif w["kind"] == "advdiff2d":
         line = run_2d(args, w, rank, world)
     elif w["kind"] == "batched1d":

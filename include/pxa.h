@@ -356,6 +356,18 @@ int pxa_expv_static(int device, void* cuda_stream, const pxa_operator_desc* op, 
                     int64_t K, int m, double tol, int phi, int transpose, int64_t span_steps,
                     int substeps, const double* x_dev, double* y_dev, double* err_host);
 
+/* ---- sparse building block -------------------------------------------------------
+ * y = A x for A in CSR form: n rows (1 <= n <= 2^31 - 1), row_ptr[n + 1] (int64, row i
+ * holds entries row_ptr[i] .. row_ptr[i+1] - 1), col[nnz] (int32, 0 <= col < n) and
+ * val[nnz] (FP64); x[n], y[n] FP64. All device pointers, caller-owned; asynchronous on
+ * `cuda_stream` (a cudaStream_t, NULL = the default stream); nothing is allocated. One
+ * thread per row, suited to the short, uniform rows of discretised operators (Sec. 4).
+ * Column indices are not checked; col and val must not be NULL even when A has no
+ * entries. Returns PXA_ERR_INVALID for a null pointer or n out of range, PXA_ERR_CUDA
+ * when the launch fails. */
+int pxa_spmv_csr(void* cuda_stream, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                 const double* val, const double* x, double* y);
+
 /* ---- batches of independent 1D advection-diffusion problems -----------------------
  * Alg. 1 for `count` independent ADVDIFF_1D problems with their own grid n[i] and
  * viscosity nu[i] (shared c, L, T, K, P): initial-condition control q0_i and the terminal

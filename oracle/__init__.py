@@ -62,6 +62,7 @@ def lib():
                 "pxo_bu1_gradient_serial": [_i, _d, _d, _d, _i64, _d, _p, _p, _p, _p, _p, _p],
                 "pxo_bu1_gradient_hybrid": [_i, _d, _d, _d, _i64, _d, _i, _i, _i, _i, _p, _p, _p,
                                             _p, _p],
+                "pxo_spmv_csr": [_i64, _i64, _p, _p, _p, _p, _p],
                 "pxo_bu1_nl_paraexp": [_i, _d, _d, _d, _i64, _i, _d, _p, _p, _p, _d, _i, _p, _p, _p],
                 "pxo_expm": [_i, _p, _p],
                 "pxo_ad1_krylov_expv": [_i, _d, _d, _d, _d, _i, _p, _p, _p],
@@ -229,6 +230,17 @@ def bu1_gradient_hybrid(f, g, nu, T, K, P, hom_mode=HOM_MAGNUS, M_mag=25, m_kry=
                                          int(M_mag), int(m_kry), _ptr(u0a), _ptr(f), _ptr(g),
                                          ctypes.byref(J), _ptr(grad)), "bu1_hybrid")
     return J.value, grad
+
+
+def spmv_csr(row_ptr, col, val, x):
+    """y = A x for A in CSR form (the definition); rows = len(row_ptr) - 1, columns = len(x)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    va, xa = _in(val), _in(x)
+    y = np.empty(rp.size - 1)
+    _check(lib().pxo_spmv_csr(rp.size - 1, xa.size, rp.ctypes.data_as(_p), cl.ctypes.data_as(_p), _ptr(va),
+                              _ptr(xa), _ptr(y)), "spmv_csr")
+    return y
 
 
 def bu1_nl_paraexp_direct(f, nu, T, K, P, omega=0.0, u0=None, guess=None, tol=1e-12, max_iter=50,

@@ -468,6 +468,23 @@ static double bu1_direct(int n, double L, double nu, double T, int64_t K, double
 }
 
 /* ------------------------------------------------------------------------- */
+/* Sparse matrix-vector product in CSR form (the definition).                */
+/* ------------------------------------------------------------------------- */
+int pxo_spmv_csr(int64_t rows, int64_t cols, const int64_t* row_ptr, const int32_t* col, const double* val,
+                 const double* x, double* y) {
+  if (rows < 1 || cols < 1 || !row_ptr || !col || !val || !x || !y) return -1;
+  for (int64_t i = 0; i < rows; ++i) {
+    double s = 0.0;
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= cols) return -1;
+      s += val[k] * x[col[k]];
+    }
+    y[i] = s;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2).                    */
 /* ------------------------------------------------------------------------- */
 /* Source of the linearised problems at a stage (Eq. nonlinTrans): N(Y) - J Y + c f with

@@ -77,6 +77,12 @@ int pxo_bu1_gradient_serial(int n, double L, double nu, double T, int64_t K, dou
                             const double* u0, const double* f, const double* g, double* J,
                             double* grad, double* traj);
 
+/* y = A x for A in CSR form, `rows` rows over `cols` columns:
+ * y_i = sum_{k = row_ptr[i]}^{row_ptr[i+1]-1} val_k x_{col_k} (the definition, one row
+ * after another); -1 for a column index outside [0, cols).                       */
+int pxo_spmv_csr(int64_t rows, int64_t cols, const int64_t* row_ptr, const int32_t* col, const double* val,
+                 const double* x, double* y);
+
 /* Iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2, Eqs. nl, nlIter, nonlinTrans,
  * Jacobians, nlHomIter, fullsolIter) on P equal subintervals, forcing s(t) f, u(0) = u0
  * (NULL = 0). Split: A = nu d2/dx2, N(q) = -q dq/dx. Each iteration averages the

@@ -35,7 +35,7 @@ EXPORTS = [
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
     "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
-    "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d",
+    "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d", "pxa_spmv_csr",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
     "pxa_batch_set_homogeneous", "pxa_batch_set_power", "pxa_batch_set_lane_steps", "pxa_batch_set_timing",
     "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "pxa_solve_direct": [p, i, p],
         "pxa_rk4_lanes_2d": [p, i, i64, p, p],
         "pxa_cn_lanes_1d": [p, i, i64, p, p],
+        "pxa_spmv_csr": [p, i64, p, p, p, p, p],
         "pxa_solve_adjoint": [p, i, p],
         "pxa_set_timing": [p, i],
         "pxa_gradient": [p, i, p, p],
@@ -167,6 +168,15 @@ def _dptr(t) -> ctypes.c_void_p:
 
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _tptr(t, dtype) -> ctypes.c_void_p:
+    """Device pointer of a contiguous CUDA tensor of the given torch dtype."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -367,6 +377,20 @@ def expv_static(x, y, n, c, nu, T, K, m, tol, phi, span_steps, substeps=1, trans
     if rc != OK:
         raise PxaError(rc, "pxa_expv_static")
     return err.value
+
+
+def spmv_csr(row_ptr, col, val, x, y, stream=None):
+    """pxa_spmv_csr: y = A x for A in CSR form (int64 row_ptr, int32 col, float64 val and
+    vectors, all CUDA tensors), asynchronous on the stream."""
+    import torch
+
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    rc = lib.pxa_spmv_csr(ctypes.c_void_p(stream.cuda_stream), int(row_ptr.numel() - 1),
+                          _tptr(row_ptr, torch.int64), _tptr(col, torch.int32), _dptr(val), _dptr(x), _dptr(y))
+    if rc != OK:
+        raise PxaError(rc, "pxa_spmv_csr")
 
 
 def partition_bounds(K, P, r, max_chunks=8):

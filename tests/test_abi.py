@@ -103,3 +103,4 @@ def test_setters_reject_null_contexts_and_bad_values_without_a_device(pxa_lib):
     assert L.pxa_set_lane_steps(None, 4) == pxa.ERR_INVALID
     assert L.pxa_set_propagator(None, pxa.PROP_BAND, 150) == pxa.ERR_INVALID
     assert L.pxa_set_partition(None, 0.5) == pxa.ERR_INVALID
+    assert L.pxa_spmv_csr(None, 0, None, None, None, None, None) == pxa.ERR_INVALID

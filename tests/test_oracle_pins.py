@@ -483,3 +483,39 @@ def test_nl_paraexp_iterations_fall_with_the_subintervals_and_the_nonlinearity()
     assert ok and len(errs) <= 4
     _, errs, ok = O.bu1_nl_paraexp_direct(f, nu, T, K, 4, max_iter=2)
     assert not ok and len(errs) == 2
+
+
+# ---- sparse matrix-vector product in CSR form --------------------------------------------
+def _csr_of_dense(A):
+    rows = [np.nonzero(A[i])[0] for i in range(A.shape[0])]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    col = np.concatenate(rows).astype(np.int32) if rp[-1] else np.zeros(0, np.int32)
+    val = np.concatenate([A[i, r] for i, r in enumerate(rows)]) if rp[-1] else np.zeros(0)
+    return rp, col, val
+
+
+@pytest.mark.parametrize("n,density", [(1, 1.0), (37, 0.05), (200, 0.2)])
+def test_spmv_csr_equals_the_dense_product(n, density):
+    """Random sparse matrices (empty rows included) against the dense matrix-vector
+    product."""
+    rng = np.random.default_rng(n)
+    A = (rng.random((n, n)) < density) * rng.standard_normal((n, n))
+    A[n // 2] = 0.0  # an empty row
+    rp, col, val = _csr_of_dense(A)
+    x = rng.standard_normal(n)
+    assert np.abs(O.spmv_csr(rp, col, val, x) - A @ x).max() <= 1e-14 * max(1.0, np.abs(A).sum(1).max())
+
+
+def test_spmv_csr_of_the_advection_diffusion_stencil_is_the_operator():
+    """The 1D advection-diffusion stencil assembled in CSR form applies the operator A of
+    the oracle's own stencil code."""
+    n, c, nu = 64, 1.0, 0.01
+    h = 2.0 * np.pi / n
+    am, a0, ap = c / (2 * h) + nu / h ** 2, -2 * nu / h ** 2, -c / (2 * h) + nu / h ** 2
+    i = np.arange(n)
+    col = np.stack([(i - 1) % n, i, (i + 1) % n], 1).ravel().astype(np.int32)
+    val = np.tile([am, a0, ap], n)
+    rp = np.arange(0, 3 * n + 1, 3, dtype=np.int64)
+    q = I.grf_k2(n, 7)
+    ref = O.ad1_apply(q, c, nu)
+    assert np.linalg.norm(O.spmv_csr(rp, col, val, q) - ref) / np.linalg.norm(ref) < 1e-14
