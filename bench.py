@@ -72,14 +72,14 @@ SM_CLOCK_HZ = 2.07e9
 # kernel changed after the capture.
 TRAFFIC = {
     "ad1_chain_kernel": 82.7e3,
-    "cn_lanes_kernel": 15.9e3,
+    "cn_lanes_kernel": 16128.0,
     "spmv_csr_kernel": 1744881408 + 257540352,
     # the direct solve is 8 chunk launches of 61.95 KB DRAM reads each (the trajectory
     # rows stay in L2 during the launch)
     "bu1_rk4_sweep_kernel": 8 * 61.95e3,
     "bu1_band_sweep_kernel": 1.6407e9 + 0.1587e9,
-    # the four-step chain: 4 segment launches of 348.8 MB read + 10.8 MB written each
-    "bu1_band_chain4_kernel": 4 * (348.8e6 + 10.8e6),
+    # the four-step chain: 4 segment launches of 348.8 MB read + 10.5 MB written each
+    "bu1_band_chain4_kernel": 4 * (348767488.0 + 10518528.0),
     "bu1_band_prepass_kernel": 8 * (30.49e6 + 357.0e6),
 }
 
