@@ -54,7 +54,8 @@ WORKLOADS = {
 # FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# Algorithmic FP64 operations per grid point per step of each kernel.
+# Algorithmic FP64 operations per grid point per step of each kernel (counted from the
+# kernels' arithmetic; the roofline divides them by the measured kernel time).
 FLOPS_RK4_DIRECT = 48.0       # four stages of N(u) + s f (8 each), stage states and weights 13, J 3
 FLOPS_BAND_PREPASS = 190.0    # stage states 36, Jacobian rows 28, tangent column of M_s 124, source 2
 FLOPS_BAND_SWEEP = 18.0       # nine FMAs of a row of M_s^T
