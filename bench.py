@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--once", action="store_true",
                     help="profiling run: W warm-up gradients then one more of the headline "
                          "configuration (1D workloads), default cluster sizes, no autotuning")
+    ap.add_argument("--checkpoints", type=int, default=0,
+                    help="with --once on the Burgers workload: the multi-checkpoint scheme with this many intervals")
     return ap.parse_args()
 
 
@@ -493,6 +495,8 @@ def run_once(args, w):
     ctx = make_ctx(X, w, X.PHI_STEPPER)
     if w["kind"] == "advdiff1d":
         ctx.set_propagator(X.PROP_BAND, 150)  # the fastest variant that meets the 1e-8 gate
+    if w["kind"] == "burgers1d" and args.checkpoints:
+        ctx.set_checkpoints(args.checkpoints)
     ctx.set_control(ctl)
     if "target" in inp:
         ctx.set_target(torch.as_tensor(inp["target"], device="cuda"))
