@@ -519,3 +519,15 @@ def test_spmv_csr_of_the_advection_diffusion_stencil_is_the_operator():
     q = I.grf_k2(n, 7)
     ref = O.ad1_apply(q, c, nu)
     assert np.linalg.norm(O.spmv_csr(rp, col, val, q) - ref) / np.linalg.norm(ref) < 1e-14
+
+
+def test_nl_paraexp_diverges_on_the_burgers_workload():
+    """Alg. 2 from the guess q(t) = q0 on the 1D Burgers workload (n = 1024, nu = 0.005,
+    T = 2, K = 20000, P = 32, the benchmark's forcing): the iterates' changes stop falling
+    after the third iterate and turn non-finite; the paper warns that convergence is not
+    guaranteed, and this is why the iterative direct is not built on the GPU."""
+    p = I.burgers1d_problem(n=1024)
+    _, errs, ok = O.bu1_nl_paraexp_direct(p["f"], 0.005, 2.0, 20000, 32, max_iter=6)
+    assert not ok
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert not np.isfinite(errs[-1]) or errs[-1] >= errs[2]
