@@ -104,3 +104,17 @@ def test_setters_reject_null_contexts_and_bad_values_without_a_device(pxa_lib):
     assert L.pxa_set_propagator(None, pxa.PROP_BAND, 150) == pxa.ERR_INVALID
     assert L.pxa_set_partition(None, 0.5) == pxa.ERR_INVALID
     assert L.pxa_spmv_csr(None, 0, None, None, None, None, None) == pxa.ERR_INVALID
+
+
+def test_header_is_plain_c():
+    """include/pxa.h compiles on its own as C99 and as C++17 (a C ABI: no C++ types)."""
+    import shutil
+    import subprocess
+
+    hdr = os.path.join(ROOT, "include", "pxa.h")
+    for cc, std, lang in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "c++")):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not available")
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
