@@ -531,3 +531,108 @@ def test_nl_paraexp_diverges_on_the_burgers_workload():
     assert not ok
     assert errs[1] < errs[0] and errs[2] < errs[1]
     assert not np.isfinite(errs[-1]) or errs[-1] >= errs[2]
+
+
+# ---- Burgers advection term, Jacobian and RK4 stage times in closed form (P6, R2) -------
+def _cd_symbols(k, n, L=2 * np.pi):
+    """Central differences on a Fourier mode of wavenumber k (k in units of 2 pi / L):
+    delta_x maps sin/cos(k x) to k~ cos/-sin with k~ = sin(k h)/h, and the 3-point
+    Laplacian multiplies the mode by -d~ with d~ = 4 sin^2(k h / 2) / h^2."""
+    h = L / n
+    kt = np.sin(2 * np.pi * k / L * h) / h
+    dt_ = 4 * np.sin(2 * np.pi * k / L * h / 2) ** 2 / h**2
+    return kt, dt_
+
+
+def _round_bound(n, amp_sq, amp, nu, L=2 * np.pi):
+    """Rounding bound of a central-difference evaluation of mode samples: the samples
+    carry absolute errors ~1e-16 x amplitude (and ~1e-16 x k x in their arguments), which
+    the differences divide by 2h and h^2."""
+    h = L / n
+    return 1e-13 * (amp_sq / h + nu * amp / h**2)
+
+
+@pytest.mark.parametrize("n,k,A,nu", [(16, 3, 1.0, 0.0), (64, 5, 1.7, 0.02), (1024, 16, 0.8, 0.005),
+                                      (37, 11, 2.0, 0.1)])
+def test_burgers_rhs_of_a_sine_mode_closed_form(n, k, A, nu):
+    """u = A sin(k x): (u_x)_i = A k~ cos(k x_i), (u_xx)_i = -A d~ sin(k x_i), so the
+    advective central-difference Burgers term is -u_i (u_x)_i = -A^2 k~ sin cos (Sec. 4.3,
+    R2) and the diffusion term -nu A d~ sin(k x_i). O(1) amplitude: the quadratic term is
+    of the same size as the linear one, so its sign and its advective (not conservative)
+    form are both tested; the conservative form -(u^2)_x / 2 by central differences would
+    give -A^2 sin(2 k h) sin(2 k x) / (4 h) instead."""
+    x = 2 * np.pi * np.arange(n) / n
+    kt, dd = _cd_symbols(k, n)
+    u = A * np.sin(k * x)
+    ref = -A * A * kt * np.sin(k * x) * np.cos(k * x) - nu * A * dd * np.sin(k * x)
+    got = O.bu1_rhs(u, nu)
+    scale = A * A * abs(kt) + nu * A * dd
+    assert np.abs(got - ref).max() < _round_bound(n, A * A, A, nu)
+    cons = -A * A * np.sin(2 * k * 2 * np.pi / n) * np.sin(2 * k * x) / (4 * 2 * np.pi / n)
+    assert np.abs(got - (cons - nu * A * dd * np.sin(k * x))).max() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("n,k,A,B,nu", [(32, 2, 1.3, 0.4, 0.01), (200, 9, 0.6, -1.1, 0.003)])
+def test_burgers_rhs_of_a_shifted_cosine_closed_form(n, k, A, B, nu):
+    """u = A cos(k x) + B: -u u_x = (A cos + B) A k~ sin(k x) and nu u_xx = -nu A d~ cos(k x);
+    the mean B advects the mode, which the product form carries exactly."""
+    x = 2 * np.pi * np.arange(n) / n
+    kt, dd = _cd_symbols(k, n)
+    u = A * np.cos(k * x) + B
+    ref = (A * np.cos(k * x) + B) * A * kt * np.sin(k * x) - nu * A * dd * np.cos(k * x)
+    got = O.bu1_rhs(u, nu)
+    assert np.abs(got - ref).max() < _round_bound(n, abs(A) * (abs(A) + abs(B)), abs(A), nu)
+
+
+@pytest.mark.parametrize("n,k,l,A,B,nu", [(48, 3, 5, 1.2, 0.7, 0.02), (256, 7, 1, 0.9, 1.4, 0.005)])
+def test_burgers_jacobian_closed_form_linearisation(n, k, l, A, B, nu):
+    """Linearisation of N(u) = -u u_x + nu u_xx about u = A sin(k x) in direction
+    w = B cos(l x): J(u) w = -w u_x - u w_x + nu w_xx
+      = -B cos(l x) A k~ cos(k x) + A sin(k x) B l~ sin(l x) - nu B e~ cos(l x),
+    k~, l~ and e~ the central-difference symbols of k and l. The transposed Jacobian must
+    satisfy <J w, z> = <w, J^T z> with the closed-form J w."""
+    x = 2 * np.pi * np.arange(n) / n
+    kt, _ = _cd_symbols(k, n)
+    lt, ee = _cd_symbols(l, n)
+    u = A * np.sin(k * x)
+    w = B * np.cos(l * x)
+    ref = (-B * np.cos(l * x) * A * kt * np.cos(k * x) + A * np.sin(k * x) * B * lt * np.sin(l * x)
+           - nu * B * ee * np.cos(l * x))
+    got = O.bu1_jac(u, w, nu)
+    scale = abs(A * B) * (abs(kt) + abs(lt)) + nu * abs(B) * ee
+    assert np.abs(got - ref).max() < _round_bound(n, abs(A * B), abs(B), nu)
+    z = np.random.default_rng(n + k).standard_normal(n)
+    assert abs(ref @ z - w @ O.bu1_jac(u, z, nu, transpose=True)) < 1e-12 * scale * np.abs(z).sum()
+
+
+@pytest.mark.parametrize("omega,t,dt", [(0.0, 0.0, 0.1), (3.0, 0.37, 0.05), (40.0, 1.1, 0.01),
+                                        (1.0, 0.0, 0.5)])
+def test_burgers_rk4_forcing_stage_times_simpson(omega, t, dt):
+    """du/dt = s(t) f with a spatially uniform state and forcing (N(u) = 0 for uniform u):
+    the classical RK4 step is then Simpson's rule, u(t + dt) = u(t) + dt/6 (s(t)
+    + 4 s(t + dt/2) + s(t + dt)) f. A forcing sampled at the wrong stage times fails it."""
+    n, nu = 24, 0.05
+    c0, fc = 0.8, -1.3
+    u = np.full(n, c0)
+    f = np.full(n, fc)
+    s = (lambda tt: 1.0) if omega == 0.0 else (lambda tt: math.sin(omega * tt))
+    ref = c0 + dt / 6 * (s(t) + 4 * s(t + dt / 2) + s(t + dt)) * fc
+    got = O.bu1_rk4_step(u, f, nu, dt, t=t, omega=omega)
+    assert np.abs(got - ref).max() < 1e-15 * max(1.0, abs(ref))
+    # the stage times really matter here: the left-point and mid-point rules differ
+    if omega != 0.0:
+        assert abs(c0 + dt * s(t) * fc - ref) > 1e-8 and abs(c0 + dt * s(t + dt / 2) * fc - ref) > 1e-12
+
+
+def test_burgers_tracking_objective_of_a_uniform_trajectory():
+    """A uniform initial state and a uniform forcing stay uniform: u_j = u0 + j dt fc
+    exactly (Simpson of a constant), so the tracking objective of Eq. cost in the
+    rectangle rule J = (1/T) sum_{j=1..K} dt ||u_j - g||^2 has the closed form
+    (1/K) sum_j sum_i (u0 + j dt fc - g_i)^2."""
+    n, nu, T, K = 20, 0.01, 0.5, 50
+    dt = T / K
+    u0, fc = 0.3, 0.9
+    g = I.fourier1d(n, 3, 41)
+    J, _ = O.bu1_gradient_serial(np.full(n, fc), g, nu, T, K, u0=np.full(n, u0))
+    ref = sum(((u0 + j * dt * fc - g) ** 2).sum() for j in range(1, K + 1)) / K
+    assert abs(J - ref) < 1e-13 * ref
