@@ -152,6 +152,16 @@ typedef struct {
   int lane_steps;           /* ADVDIFF_1D: q, the lanes apply the band of M^q */
   int lane_band_taps;       /* ADVDIFF_1D: taps of that band */
   int prop_band_taps;       /* ADVDIFF_1D with PXA_PROP_BAND: taps of the subinterval propagator's band */
+  /* BURGERS_1D with the hybrid overlap and timing on: kernel time of the work that ran on
+   * the side streams beside the direct chunks, each summed over the chunks from events
+   * recorded on its own stream (0 when nothing ran there; -1: the events could not be
+   * read): the band pre-pass, the pair records, the four-step records and the adjoint
+   * lanes. */
+  int side_chunks;          /* chunks whose side-stream work was timed */
+  float ms_side_prepass;
+  float ms_side_pair;
+  float ms_side_quad;
+  float ms_side_lanes;
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -343,7 +353,10 @@ int pxa_rk4_lanes_2d(pxa_ctx* ctx, int lanes, int64_t steps, double* out_dev, do
  * PXA_ERR_TOO_LARGE before touching the device.
  *
  * Set-up: the first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream capture.
+ * device current) and caches it for the life of the process; make that first call
+ * before any stream capture. The cached address does not survive a cudaDeviceReset
+ * (or any other teardown of the device's primary context): do not call this entry
+ * point on a device after it has been reset.
  * The call runs on `cuda_stream` of device `device` and synchronises that stream
  * before returning. Every call shares the one array, which keeps the last call's
  * contents: the status word and the error estimate are cleared by each call, the

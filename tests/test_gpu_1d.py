@@ -10,13 +10,9 @@ import pytest
 
 import oracle as O
 from paper_2004_00546_gb300 import inputs as I
+from parity import rel
 
 pytestmark = pytest.mark.gpu
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -715,7 +711,6 @@ def test_relpm_paraexp_gradient_matches_oracle(X, torch, n, nu, K, P):
         res[prop] = host(out)
         ctx.close()
     assert rel(res[X.PROP_RELPM], res[X.PROP_KRYLOV]) < 1e-10
-
 
 
 @pytest.mark.parametrize("n,nu,K,P", [(256, 0.01, 4096, 8), (100, 0.0, 512, 4), (333, 0.05, 1024, 16)])

@@ -10,15 +10,11 @@ import pytest
 
 import oracle as O
 from paper_2004_00546_gb300 import inputs as I
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")

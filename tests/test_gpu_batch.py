@@ -14,13 +14,9 @@ import pytest
 
 import oracle as O
 from paper_2004_00546_gb300 import inputs as I
+from parity import rel
 
 pytestmark = pytest.mark.gpu
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -230,3 +226,45 @@ def test_batch_rejects_bad_problems(X):
     with pytest.raises(X.PxaError):
         b.set_krylov(64, 1e-8, 0.04)  # m > 48
     b.close()
+
+
+def test_batch_full_size_matches_oracle_on_a_stride(X, torch):
+    """The benchmarked batch at full size (256 problems, n ~ U{128..2048}, CN K = 4096,
+    P = 16, seed 2007) in the benchmark's launch configuration (the stepper's propagator
+    as a band of M^(K/P), autotuned Paraexp; serial stepping), compared with the FP64
+    oracle on every 16th problem, point by point. Tolerance from the arithmetic: FP32
+    stepping rounds the state once per band application, so a contractive recursion of s
+    steps loses at most about s u_32 (u_32 = 2^-24 = 6e-8): serial stepping's K = 4096
+    steps give 2.4e-4, held to 2 K u_32 = 5e-4; Paraexp's lanes take K/P = 256 steps and
+    its chains 15 band products, held to the small-case 1e-4."""
+    prob = I.batch1d_problem(count=256, seed=2007)
+    K, P, cnt = 4096, 16, 256
+    q0 = dev(torch, prob["q0"])
+    J = torch.empty(cnt, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    off = prob["offsets"]
+    stride = list(range(0, cnt, 16))
+    oracle_serial = {}
+    for i in stride:
+        oracle_serial[i] = O.ad1_cn_gradient_serial(prob["q0"][off[i]:off[i + 1]], 1.0, prob["nu"][i], 1.0, K)[:2]
+    for mode, tol in ((X.PARAEXP, 1e-4), (X.SERIAL, 2 * K * 2.0 ** -24)):
+        b = X.Batch()
+        b.set(prob["n"], prob["nu"], c=1.0, T=1.0, K=K, P=P)
+        b.set_power(True)
+        if mode == X.PARAEXP:
+            b.autotune(mode, q0, J, g)
+        b.gradient(mode, q0, J, g)
+        b.sync()
+        kry = b.problem_info()[2] if mode == X.PARAEXP else [0] * cnt
+        assert list(b.offsets()) == list(off)
+        Jh, gh = J.cpu().numpy(), g.cpu().numpy()
+        b.close()
+        assert np.all(np.isfinite(Jh)) and np.all(np.isfinite(gh))
+        for i in stride:
+            if kry[i]:
+                Jo, go, _ = O.ad1_cn_gradient_paraexp(prob["q0"][off[i]:off[i + 1]], 1.0, prob["nu"][i], 1.0,
+                                                      K, P, O.PHI_EXP)
+            else:
+                Jo, go = oracle_serial[i]
+            eJ, eg = abs(Jh[i] - Jo) / Jo, rel(gh[off[i]:off[i + 1]], go)
+            assert eJ < tol and eg < tol, (mode, i, int(prob["n"][i]), eJ, eg)
