@@ -73,6 +73,10 @@ def lib():
                 "pxo_ad2_apply_T": [_i, _i, _d, _d, _p, _p, _p, _p],
                 "pxo_ad2_rk4_step": [_i, _i, _d, _d, _p, _p, _d, _d, _d, _p, _p, _p],
                 "pxo_ad2_gradient_serial": [_i, _i, _d, _d, _p, _p, _d, _i64, _d, _p, _p, _p, _p],
+                "pxo_csr_transpose": [_i64, _p, _p, _p, _p, _p, _p],
+                "pxo_csr_rk4_step": [_i64, _p, _p, _p, _d, _p, _p, _p],
+                "pxo_csr_gradient_serial": [_i64, _p, _p, _p, _d, _i64, _p, _p, _p, _p, _p],
+                "pxo_csr_gradient_paraexp": [_i64, _p, _p, _p, _d, _i64, _i, _i, _p, _p, _p, _p, _p],
             }
             for name, argt in sigs.items():
                 fn = getattr(L, name)
@@ -303,3 +307,58 @@ def ad2_gradient_serial(f, f_true, u, v, nu, T, K, omega=1.0, L=TWO_PI):
     _check(lib().pxo_ad2_gradient_serial(nx, ny, L, nu, _ptr(u), _ptr(v), T, int(K), omega, _ptr(f),
                                          _ptr(ft), ctypes.byref(J), _ptr(g)), "ad2_serial")
     return J.value, g
+
+
+# ---- general sparse operator in CSR form -------------------------------------
+def _csr(rp, col, val):
+    return (np.ascontiguousarray(rp, dtype=np.int64), np.ascontiguousarray(col, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=np.float64))
+
+
+def csr_transpose(rp, col, val):
+    rp, col, val = _csr(rp, col, val)
+    n = rp.size - 1
+    rpT = np.empty_like(rp)
+    colT = np.empty(max(col.size, 1), dtype=np.int32)
+    valT = np.empty(max(val.size, 1))
+    _check(lib().pxo_csr_transpose(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(rpT), _ptr(colT), _ptr(valT)),
+           "csr_transpose")
+    return rpT, colT[:col.size], valT[:val.size]
+
+
+def csr_rk4_step(rp, col, val, q, dt, src=None):
+    rp, col, val = _csr(rp, col, val)
+    q = _in(q)
+    s = None if src is None else _in(src)
+    out = np.empty_like(q)
+    _check(lib().pxo_csr_rk4_step(q.size, _ptr(rp), _ptr(col), _ptr(val), dt, _ptr(s), _ptr(q), _ptr(out)),
+           "csr_rk4_step")
+    return out
+
+
+def csr_gradient_serial(rp, col, val, q0, T, K, g=None):
+    rp, col, val = _csr(rp, col, val)
+    q0 = _in(q0)
+    ga = None if g is None else _in(g)
+    J = ctypes.c_double()
+    grad = np.empty_like(q0)
+    qT = np.empty_like(q0)
+    _check(lib().pxo_csr_gradient_serial(q0.size, _ptr(rp), _ptr(col), _ptr(val), T, int(K), _ptr(q0), _ptr(ga),
+                                         ctypes.byref(J), _ptr(grad), _ptr(qT)), "csr_serial")
+    return J.value, grad, qT
+
+
+CSR_PHI_EXP, CSR_PHI_RK4 = 0, 2
+
+
+def csr_gradient_paraexp(rp, col, val, q0, T, K, P, phi_mode, g=None):
+    rp, col, val = _csr(rp, col, val)
+    q0 = _in(q0)
+    ga = None if g is None else _in(g)
+    J = ctypes.c_double()
+    grad = np.empty_like(q0)
+    qT = np.empty_like(q0)
+    _check(lib().pxo_csr_gradient_paraexp(q0.size, _ptr(rp), _ptr(col), _ptr(val), T, int(K), int(P),
+                                          int(phi_mode), _ptr(q0), _ptr(ga), ctypes.byref(J), _ptr(grad),
+                                          _ptr(qT)), "csr_paraexp")
+    return J.value, grad, qT

@@ -1209,3 +1209,279 @@ int pxo_ad2_gradient_serial(int nx, int ny, double L, double nu, const double* u
   free(d); free(traj); free(lam); free(mu); free(nv); free(acc);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Linear problem with a general sparse operator in CSR form (Sec. 2: the    */
+/* state equation dq/dt = A q with a constant discretised operator A; the    */
+/* paper's Sec. 4 operators are such matrices). Classical RK4, control =     */
+/* q(0), objective J = 0.5 ||q(T) - g||^2 (g = 0 when absent), Alg. 1 for     */
+/* Paraexp with exact propagators formed densely (small n only).             */
+/* ------------------------------------------------------------------------- */
+static int csr_bad(int64_t n, const int64_t* rp, const int32_t* col, const double* val) {
+  if (n < 1 || !rp || !col || !val || rp[0] != 0) return 1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) return 1;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] < 0 || col[k] >= n) return 1;
+  }
+  return 0;
+}
+
+/* A^T in CSR form, entry by entry: entry (i, j, a) of A becomes (j, i, a). */
+int pxo_csr_transpose(int64_t n, const int64_t* rp, const int32_t* col, const double* val, int64_t* rpT,
+                      int32_t* colT, double* valT) {
+  if (csr_bad(n, rp, col, val) || !rpT || !colT || !valT) return -1;
+  for (int64_t j = 0; j <= n; ++j) rpT[j] = 0;
+  for (int64_t k = 0; k < rp[n]; ++k) rpT[col[k] + 1] += 1;
+  for (int64_t j = 0; j < n; ++j) rpT[j + 1] += rpT[j];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t j = 0; j < n; ++j) fill[j] = rpT[j];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      int64_t dst = fill[col[k]]++;
+      colT[dst] = (int32_t)i;
+      valT[dst] = val[k];
+    }
+  free(fill);
+  return 0;
+}
+
+/* y = A x + src (src may be NULL). */
+static void csr_apply_src(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                          const double* x, const double* src, double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = src ? src[i] : 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * x[col[k]];
+    y[i] = s;
+  }
+}
+
+/* One classical RK4 step of dq/dt = A q + src (src constant, may be NULL). */
+int pxo_csr_rk4_step(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double dt,
+                     const double* src, const double* q, double* out) {
+  if (csr_bad(n, rp, col, val) || !q || !out) return -1;
+  size_t nb = sizeof(double) * (size_t)n;
+  double* k1 = (double*)malloc(nb);
+  double* k2 = (double*)malloc(nb);
+  double* k3 = (double*)malloc(nb);
+  double* k4 = (double*)malloc(nb);
+  double* y = (double*)malloc(nb);
+  csr_apply_src(n, rp, col, val, q, src, k1);
+  for (int64_t i = 0; i < n; ++i) y[i] = q[i] + 0.5 * dt * k1[i];
+  csr_apply_src(n, rp, col, val, y, src, k2);
+  for (int64_t i = 0; i < n; ++i) y[i] = q[i] + 0.5 * dt * k2[i];
+  csr_apply_src(n, rp, col, val, y, src, k3);
+  for (int64_t i = 0; i < n; ++i) y[i] = q[i] + dt * k3[i];
+  csr_apply_src(n, rp, col, val, y, src, k4);
+  for (int64_t i = 0; i < n; ++i) out[i] = q[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  free(k1);
+  free(k2);
+  free(k3);
+  free(k4);
+  free(y);
+  return 0;
+}
+
+/* Reverse sweep of one RK4 step of dq/dt = A q (exact discrete adjoint, the stages
+ * in reverse order with A^T given as rpT/colT/valT): lam_out = M^T lam. */
+static void csr_rk4_adjoint_step(int64_t n, const int64_t* rpT, const int32_t* colT, const double* valT,
+                                 double dt, const double* lam, double* lam_out) {
+  size_t nb = sizeof(double) * (size_t)n;
+  double* mu = (double*)malloc(nb);
+  double* nv = (double*)malloc(nb);
+  for (int64_t i = 0; i < n; ++i) lam_out[i] = lam[i];
+  /* stage 4: kbar4 = dt/6 lam, Ybar4 = A^T kbar4 */
+  for (int64_t i = 0; i < n; ++i) mu[i] = dt / 6.0 * lam[i];
+  csr_apply_src(n, rpT, colT, valT, mu, NULL, nv);
+  for (int64_t i = 0; i < n; ++i) lam_out[i] += nv[i];
+  /* stage 3: kbar3 = dt/3 lam + dt Ybar4 */
+  for (int64_t i = 0; i < n; ++i) mu[i] = dt / 3.0 * lam[i] + dt * nv[i];
+  csr_apply_src(n, rpT, colT, valT, mu, NULL, nv);
+  for (int64_t i = 0; i < n; ++i) lam_out[i] += nv[i];
+  /* stage 2: kbar2 = dt/3 lam + dt/2 Ybar3 */
+  for (int64_t i = 0; i < n; ++i) mu[i] = dt / 3.0 * lam[i] + 0.5 * dt * nv[i];
+  csr_apply_src(n, rpT, colT, valT, mu, NULL, nv);
+  for (int64_t i = 0; i < n; ++i) lam_out[i] += nv[i];
+  /* stage 1: kbar1 = dt/6 lam + dt/2 Ybar2 */
+  for (int64_t i = 0; i < n; ++i) mu[i] = dt / 6.0 * lam[i] + 0.5 * dt * nv[i];
+  csr_apply_src(n, rpT, colT, valT, mu, NULL, nv);
+  for (int64_t i = 0; i < n; ++i) lam_out[i] += nv[i];
+  free(mu);
+  free(nv);
+}
+
+static double terminal_objective(int64_t n, const double* q, const double* g, double* lam) {
+  double J = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double d = q[i] - (g ? g[i] : 0.0);
+    J += 0.5 * d * d;
+    if (lam) lam[i] = d; /* dJ/dq(T) (Eq. adjFinalTime) */
+  }
+  return J;
+}
+
+/* Serial stepping (the plain definition): K RK4 steps from q0, J, the reverse sweep of
+ * every step from lam(T) = q(T) - g, grad = lam(0) (Eq. initupdate). */
+int pxo_csr_gradient_serial(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double T,
+                            int64_t K, const double* q0, const double* g, double* J, double* grad,
+                            double* qT) {
+  if (csr_bad(n, rp, col, val) || !(T > 0.0) || K < 1 || !q0 || !J || !grad) return -1;
+  size_t nb = sizeof(double) * (size_t)n;
+  const double dt = T / (double)K;
+  double* q = (double*)malloc(nb);
+  double* q2 = (double*)malloc(nb);
+  int64_t* rpT = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t* colT = (int32_t*)malloc(sizeof(int32_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  double* valT = (double*)malloc(sizeof(double) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  pxo_csr_transpose(n, rp, col, val, rpT, colT, valT);
+  memcpy(q, q0, nb);
+  for (int64_t s = 0; s < K; ++s) {
+    pxo_csr_rk4_step(n, rp, col, val, dt, NULL, q, q2);
+    memcpy(q, q2, nb);
+  }
+  if (qT) memcpy(qT, q, nb);
+  *J = terminal_objective(n, q, g, q2); /* q2 = lam(T) */
+  for (int64_t s = K - 1; s >= 0; --s) {
+    csr_rk4_adjoint_step(n, rpT, colT, valT, dt, q2, q);
+    memcpy(q2, q, nb);
+  }
+  memcpy(grad, q2, nb);
+  free(q);
+  free(q2);
+  free(rpT);
+  free(colT);
+  free(valT);
+  return 0;
+}
+
+/* Dense n x n matrix of the CSR operator (row-major). */
+static double* csr_dense(int64_t n, const int64_t* rp, const int32_t* col, const double* val) {
+  double* D = (double*)calloc((size_t)(n * n), sizeof(double));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) D[i * n + col[k]] += val[k];
+  return D;
+}
+
+static void dense_matvec(int64_t n, const double* M, int transpose, const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += (transpose ? M[j * n + i] : M[i * n + j]) * x[j];
+    y[i] = s;
+  }
+}
+
+/* Paraexp (Alg. 1) for the CSR problem, with the homogeneous propagator of one
+ * subinterval formed densely: phi_mode 0 = exp(tau A) (Eq. hom), 2 = the RK4 stepper's
+ * own R(dt A)^(K/P), R(Z) = I + Z + Z^2/2 + Z^3/6 + Z^4/24 (reproduces serial stepping).
+ * Inhomogeneous lanes (Eq. linzero, linInhomEqus): zero initial value and the constant
+ * source A q0 on every subinterval; homogeneous problems in the global form, each
+ * boundary value propagated from T_j to T; superposition Eq. fullsol0; the adjoint
+ * mirrored (Eq. adjInhom, adjHomNormal, fulladjsol) with A^T and Phi^T; Eq. initupdate. */
+int pxo_csr_gradient_paraexp(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double T,
+                             int64_t K, int P, int phi_mode, const double* q0, const double* g, double* J,
+                             double* grad, double* qT) {
+  if (csr_bad(n, rp, col, val) || !(T > 0.0) || K < 1 || P < 1 || K % P != 0 || !q0 || !J || !grad ||
+      (phi_mode != 0 && phi_mode != 2) || n > 2048)
+    return -1;
+  const int64_t k = K / P;
+  const double dt = T / (double)K, tau = T / (double)P;
+  size_t nb = sizeof(double) * (size_t)n;
+  int64_t* rpT = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t* colT = (int32_t*)malloc(sizeof(int32_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  double* valT = (double*)malloc(sizeof(double) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  pxo_csr_transpose(n, rp, col, val, rpT, colT, valT);
+  /* the subinterval propagator Phi, densely */
+  double* A = csr_dense(n, rp, col, val);
+  double* Phi = (double*)malloc(nb * (size_t)n);
+  if (phi_mode == 0) {
+    for (int64_t e = 0; e < n * n; ++e) A[e] *= tau;
+    pxo_expm((int)n, A, Phi);
+  } else {
+    /* R(dt A) column by column (one RK4 step of each unit vector), then R^k */
+    double* R = (double*)malloc(nb * (size_t)n);
+    double* e = (double*)calloc((size_t)n, sizeof(double));
+    double* col_out = (double*)malloc(nb);
+    for (int64_t j = 0; j < n; ++j) {
+      e[j] = 1.0;
+      pxo_csr_rk4_step(n, rp, col, val, dt, NULL, e, col_out);
+      for (int64_t i = 0; i < n; ++i) R[i * n + j] = col_out[i];
+      e[j] = 0.0;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) Phi[i * n + j] = (i == j) ? 1.0 : 0.0;
+    double* W = (double*)malloc(nb * (size_t)n);
+    for (int64_t s = 0; s < k; ++s) { /* Phi <- R Phi */
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+          double acc = 0.0;
+          for (int64_t l = 0; l < n; ++l) acc += R[i * n + l] * Phi[l * n + j];
+          W[i * n + j] = acc;
+        }
+      memcpy(Phi, W, nb * (size_t)n);
+    }
+    free(W);
+    free(R);
+    free(e);
+    free(col_out);
+  }
+  double* src = (double*)malloc(nb);
+  double* w = (double*)malloc(nb * (size_t)P);
+  double* x = (double*)malloc(nb);
+  double* y = (double*)malloc(nb);
+  double* qTT = (double*)malloc(nb);
+  double* lamT = (double*)malloc(nb);
+  /* direct lanes: q~_p(T_p) = 0, dq~/dt = A q~ + A q0 */
+  csr_apply_src(n, rp, col, val, q0, NULL, src);
+  for (int p = 0; p < P; ++p) {
+    double* wp = w + (size_t)p * n;
+    memset(wp, 0, nb);
+    for (int64_t s = 0; s < k; ++s) {
+      pxo_csr_rk4_step(n, rp, col, val, dt, src, wp, y);
+      memcpy(wp, y, nb);
+    }
+  }
+  /* q(T) = q0 + w_{P-1} + sum_{j=1}^{P-1} Phi^{P-j} w_{j-1} */
+  for (int64_t i = 0; i < n; ++i) qTT[i] = q0[i] + w[(size_t)(P - 1) * n + i];
+  for (int j = 1; j < P; ++j) {
+    memcpy(x, w + (size_t)(j - 1) * n, nb);
+    for (int r = 0; r < P - j; ++r) {
+      dense_matvec(n, Phi, 0, x, y);
+      memcpy(x, y, nb);
+    }
+    for (int64_t i = 0; i < n; ++i) qTT[i] += x[i];
+  }
+  if (qT) memcpy(qT, qTT, nb);
+  *J = terminal_objective(n, qTT, g, lamT);
+  /* adjoint lanes: lam~_p(T_{p+1}) = 0, backward k steps with A^T and the source A^T lam(T) */
+  csr_apply_src(n, rpT, colT, valT, lamT, NULL, src);
+  for (int p = 0; p < P; ++p) {
+    double* wp = w + (size_t)p * n;
+    memset(wp, 0, nb);
+    for (int64_t s = 0; s < k; ++s) {
+      pxo_csr_rk4_step(n, rpT, colT, valT, dt, src, wp, y);
+      memcpy(wp, y, nb);
+    }
+  }
+  /* grad = lam(0) = lam(T) + w_0 + sum_{j=1}^{P-1} (Phi^T)^j w_j */
+  for (int64_t i = 0; i < n; ++i) grad[i] = lamT[i] + w[i];
+  for (int j = 1; j < P; ++j) {
+    memcpy(x, w + (size_t)j * n, nb);
+    for (int r = 0; r < j; ++r) {
+      dense_matvec(n, Phi, 1, x, y);
+      memcpy(x, y, nb);
+    }
+    for (int64_t i = 0; i < n; ++i) grad[i] += x[i];
+  }
+  free(rpT);
+  free(colT);
+  free(valT);
+  free(A);
+  free(Phi);
+  free(src);
+  free(w);
+  free(x);
+  free(y);
+  free(qTT);
+  free(lamT);
+  return 0;
+}

@@ -155,6 +155,20 @@ int pxo_ad1_relpm_expv(int n, double L, double c, double nu, double t, double to
  * r = k/(k+1); out has N+1 entries.                                              */
 int pxo_partition_nonequi(double T, int N, double k, double* out);
 
+/* General sparse linear operator in CSR form (row_ptr int64, col int32, val FP64):
+ * dq/dt = A q with classical RK4, control q(0), J = 0.5 ||q(T) - g||^2 (g may be NULL). */
+int pxo_csr_transpose(int64_t n, const int64_t* rp, const int32_t* col, const double* val, int64_t* rpT,
+                      int32_t* colT, double* valT);
+int pxo_csr_rk4_step(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double dt,
+                     const double* src, const double* q, double* out);
+int pxo_csr_gradient_serial(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double T,
+                            int64_t K, const double* q0, const double* g, double* J, double* grad,
+                            double* qT);
+/* phi_mode 0: exp(tau A) (Eq. hom); 2: the RK4 stepper's R(dt A)^(K/P). n <= 2048. */
+int pxo_csr_gradient_paraexp(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double T,
+                             int64_t K, int P, int phi_mode, const double* q0, const double* g, double* J,
+                             double* grad, double* qT);
+
 #ifdef __cplusplus
 }
 #endif

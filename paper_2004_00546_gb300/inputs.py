@@ -178,3 +178,32 @@ def batch1d_problem(count: int = 256, seed: int = 2007, n_lo: int = 128, n_hi: i
     q0s = [grf_k2(int(n), 1000 * seed + i) for i, n in enumerate(ns)]
     offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
     return dict(n=ns, nu=nus, c=1.0, T=1.0, q0=np.concatenate(q0s), offsets=offsets)
+
+
+def sparse_operator(n: int, per_row: int, seed: int, shift: float = 1.0):
+    """A seeded sparse n x n matrix in CSR form (int64 row pointers, int32 columns, FP64
+    values) with the structure of a discretised dissipative operator: every row holds its
+    diagonal and `per_row` off-diagonal entries at distinct random columns, with values
+    ~ N(0, 1); the diagonal is -(sum of the row's |off-diagonal| + shift), so every
+    Gershgorin disc lies in the left half-plane (the operator is stable). Columns are
+    sorted within each row."""
+    s = Stream(seed)
+    cols, vals = [], []
+    rp = [0]
+    for i in range(n):
+        u = s.uniform(4 * per_row + 8)
+        picked = []
+        for x in u:
+            j = int(x * n)
+            if j != i and j not in picked:
+                picked.append(j)
+            if len(picked) == min(per_row, n - 1):
+                break
+        off = s.normal(len(picked))
+        diag = -(float(np.abs(off).sum()) + shift)
+        entries = sorted([(i, diag)] + list(zip(picked, off.tolist())))
+        cols.extend(j for j, _ in entries)
+        vals.extend(v for _, v in entries)
+        rp.append(len(cols))
+    return (np.asarray(rp, dtype=np.int64), np.asarray(cols, dtype=np.int32),
+            np.asarray(vals, dtype=np.float64))
