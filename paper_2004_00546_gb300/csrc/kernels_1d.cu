@@ -364,13 +364,15 @@ __global__ void ad1_relpm_expv_kernel(int n, double am, double a0, double ap, in
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = h[i];
 }
 
-// Direct superposition at t = T (Eq. fullsol0): qT = q0 + e_{P-1} + hsum;
-// J = 0.5 ||qT||^2; lambda_K = qT (Eq. adjFinalTime) and the adjoint lanes' source
-// (M^T - I) lambda_K of the shifted adjoint (Eq. adjInhom, discrete form).
+// Direct superposition at t = T (Eq. fullsol0): q(T) = q0 + e_{P-1} + hsum;
+// J = 0.5 ||q(T) - g||^2 (g = 0 when NULL); qT receives lambda_K = q(T) - g
+// (Eq. adjFinalTime) and srcT the adjoint lanes' source (M^T - I) lambda_K of the shifted
+// adjoint (Eq. adjInhom, discrete form).
 __global__ void ad1_superpose_direct_kernel(int n, int r, const double* __restrict__ taps,
                                             const double* __restrict__ q0,
                                             const double* __restrict__ elast,
                                             const double* __restrict__ hsum,
+                                            const double* __restrict__ g,
                                             double* __restrict__ qT, double* __restrict__ srcT,
                                             double* __restrict__ Jdev, int* status) {
   extern __shared__ double sm[];
@@ -379,7 +381,8 @@ __global__ void ad1_superpose_direct_kernel(int n, int r, const double* __restri
   const int w = 2 * r + 1;
   double acc = 0.0;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    double v = (q0 ? q0[p] : 0.0) + (elast ? elast[p] : 0.0) + (hsum ? hsum[p] : 0.0);
+    // lambda(T) = dJ/dq(T) = q(T) - g for J = 0.5 ||q(T) - g||^2 (g = 0 when absent)
+    double v = (q0 ? q0[p] : 0.0) + (elast ? elast[p] : 0.0) + (hsum ? hsum[p] : 0.0) - (g ? g[p] : 0.0);
     q[p] = v;
     qT[p] = v;
     acc = fma(v, v, acc);
@@ -771,14 +774,14 @@ cudaError_t launch_ad1_expv(cudaStream_t st, int threads, int n, double am, doub
 
 cudaError_t launch_ad1_superpose_direct(cudaStream_t st, int threads, int n, int r,
                                         const double* taps, const double* q0, const double* elast,
-                                        const double* hsum, double* qT, double* srcT, double* J,
-                                        int* status) {
+                                        const double* hsum, const double* g, double* qT, double* srcT,
+                                        double* J, int* status) {
   size_t sh = sizeof(double) * (40 + (size_t)n);
   if (sh > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(ad1_superpose_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
   }
-  ad1_superpose_direct_kernel<<<1, threads, sh, st>>>(n, r, taps, q0, elast, hsum, qT, srcT, J,
+  ad1_superpose_direct_kernel<<<1, threads, sh, st>>>(n, r, taps, q0, elast, hsum, g, qT, srcT, J,
                                                        status);
   return cudaGetLastError();
 }

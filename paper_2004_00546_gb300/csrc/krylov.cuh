@@ -109,8 +109,10 @@ __device__ __forceinline__ void krylov_combine(const double* V, int ldv, int mm,
 }
 
 // Homogeneous propagator on the Krylov space.
-//   phi_mode 0 (EXP):      F = exp(H)            (H already carries the time span)
-//   phi_mode 1 (CN power): F = [(I - H/2)^{-1} (I + H/2)]^steps
+//   phi_mode 0 (EXP):       F = exp(H)            (H already carries the time span)
+//   phi_mode 1 (CN power):  F = [(I - H/2)^{-1} (I + H/2)]^steps
+//   phi_mode 2 (RK4 power): F = [I + H + H^2/2 + H^3/6 + H^4/24]^steps (classical RK4's
+//                           amplification polynomial, by Horner's rule)
 // with H = dt * H_m for the stepper modes. Writes the first column of F to c[0..mm)
 // and returns |F[mm-1][0]| for Saad's a-posteriori estimate beta*h_{mm+1,mm}*|F[mm-1][0]|.
 // `want_phi1`: also writes phi_1(H) e_1 to c1 (EXP only), through the augmented
@@ -130,6 +132,17 @@ __device__ inline double hessenberg_phi(KrylovScratch& ks, int mm, int phi_mode,
   double* F = ks.D1;
   if (phi_mode == 0) {
     dense_expm(ks.D1, ks.D0, ks.D2, ks.D3, d, ks.red);  // D1 = exp(D0)
+  } else if (phi_mode == 2) {
+    // R(Z) = I + Z (I + Z/2 (I + Z/3 (I + Z/4))), Z = D0
+    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+      int i = e / d, j = e % d;
+      ks.D2[i * kLD + j] = (i == j ? 1.0 : 0.0) + 0.25 * ks.D0[i * kLD + j];
+    }
+    __syncthreads();
+    dense_gemm(ks.D3, ks.D0, ks.D2, d, 1.0 / 3.0, 1.0);
+    dense_gemm(ks.D2, ks.D0, ks.D3, d, 0.5, 1.0);
+    dense_gemm(ks.D1, ks.D0, ks.D2, d, 1.0, 1.0);  // D1 = R
+    F = dense_pow(ks.D1, ks.D0, ks.D2, ks.D3, d, steps);  // F = R^steps
   } else {
     // R = (I - Z/2)^{-1} (I + Z/2): A = I - Z/2 in D2, B = I + Z/2 in D1
     for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
