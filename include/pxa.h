@@ -5,13 +5,20 @@
  * direct-adjoint studies" (arXiv 2004.00546). The time window [0, T] is split into
  * P subintervals (Alg. 1, equal partition T_p = p T / P). The zero-initial-value
  * inhomogeneous subproblems of every subinterval (Eq. linInhomEqus, Eq. adjInhom,
- * Eq. hybadjinhom) are time-stepped concurrently, one CUDA thread block per
- * subinterval ("lane"). The homogeneous problems (Eq. hom, Eq. adjHomNormal) are
- * propagated by Krylov matrix-exponential actions (Sec. 4.1, Saad 1992); by
- * linearity the problems active on one subinterval are carried as their sum. The
- * full solution is the superposition of Eq. fullsol0 / Eq. fulladjsol, and the
- * gradient follows from Eq. initupdate (initial-condition control) or
- * Eq. paramupdate (forcing control).
+ * Eq. hybadjinhom) are time-stepped concurrently, one "lane" per subinterval: a
+ * thread-block cluster (1D problems: the lane's grid split over the cluster's CTAs,
+ * halos exchanged through distributed shared memory), one thread block (batches,
+ * CSR), or a set of thread blocks over the lane's tiles (2D). The homogeneous problems
+ * (Eq. hom, Eq. adjHomNormal) are carried, by linearity, as their sum over the
+ * problems active on one subinterval, by one of the propagators pxa_set_propagator
+ * selects: Krylov matrix-exponential actions (Sec. 4.1, Saad 1992; the default), the
+ * real Leja points method (Sec. 4.1), or, for periodic constant-coefficient 1D
+ * operators, the subinterval propagator itself as a circulant band (the fastest and the
+ * one the benchmarks use); the time-varying Burgers adjoint uses the stepper's own
+ * transposed step maps (or 4th-order Magnus steps with Krylov exponentials). The full
+ * solution is the superposition of Eq. fullsol0 / Eq. fulladjsol, and the gradient
+ * follows from Eq. initupdate (initial-condition control) or Eq. paramupdate (forcing
+ * control).
  *
  * Problems (Sec. 4.2, 4.3, restricted to what this library implements):
  *   PXA_ADVDIFF_1D: dq/dt = A q,  (A q)_i = -c (q_{i+1}-q_{i-1})/(2h)
@@ -32,15 +39,25 @@
  *                   J = (1/T) sum_{j=1..K} dt ||u_j - g||^2 (rectangle rule of
  *                   Eq. cost). The direct problem is solved in series and the
  *                   adjoint in parallel (hybrid scheme, Sec. 3.3); its homogeneous
- *                   parts use 4th-order Magnus steps with Krylov exponentials.
+ *                   parts are carried by the exact transposed RK4 step maps (banded,
+ *                   several steps per halo exchange; PXA_PHI_STEPPER, the default) or
+ *                   by 4th-order Magnus steps with Krylov exponentials (PXA_PHI_EXP).
+ *   PXA_CSR:        dq/dt = A q for a constant sparse matrix A given in CSR form (any
+ *                   discretised operator, Sec. 2), classical RK4; control = q(0);
+ *                   objective J = 0.5 ||q(T) - g||^2 (g from pxa_set_objective or
+ *                   pxa_set_target, 0 when none is set). Alg. 1 with Krylov
+ *                   propagators: exp(tau A) (PXA_PHI_EXP) or the RK4 stepper's own
+ *                   R(dt A)^(K/P), R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24
+ *                   (PXA_PHI_STEPPER), evaluated on the Hessenberg matrix.
  *
  * Conventions:
  *   - Every call returns a pxa_status (0 = PXA_OK). No call aborts, traps or
  *     throws. Errors raised inside kernels are written to a device status word and
  *     reported by the next call that synchronises (pxa_gradient, pxa_sync).
  *   - Device pointers ("_dev") are caller-owned, borrowed for the duration of the
- *     call (or, for pxa_set_control / pxa_set_objective, until the next set_* call
- *     or pxa_destroy) and never freed by the library. Host pointers ("_host") are
+ *     call (or, for pxa_set_operator, pxa_set_control, pxa_set_target and
+ *     pxa_set_objective, until the next call of the same setter or pxa_destroy) and
+ *     never freed by the library. Host pointers ("_host") are
  *     read or written before the call returns.
  *   - All vectors are FP64, contiguous, n elements (the grid points in order).
  *   - The library owns its workspace. It is (re)allocated by the first solve after
@@ -73,7 +90,7 @@ typedef enum {
   PXA_ERR_TOO_LARGE = -8       /* request exceeds the fixed buffer of pxa_expv_static */
 } pxa_status;
 
-typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2, PXA_ADVDIFF_2D = 3 } pxa_problem;
+typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2, PXA_ADVDIFF_2D = 3, PXA_CSR = 4 } pxa_problem;
 typedef enum { PXA_CN = 1, PXA_RK4 = 2 } pxa_stepper;
 /* Homogeneous propagator. EXP: exp(t A) (the paper's choice). STEPPER: the stepper's
  * own amplification R(dt A)^k (R_CN(z) = (1+z/2)/(1-z/2)), which makes Paraexp
@@ -120,7 +137,34 @@ typedef struct {
   int nx, ny; /* PXA_ADVDIFF_2D: grid, nx == ny, nx % 4 == 0, 8 <= nx <= 8192 */
   const double* u_dev; /* PXA_ADVDIFF_2D: velocity components (device, [ny][nx] row-major, */
   const double* v_dev; /*   x fastest), borrowed until the next set_operator */
+  /* PXA_CSR: A with n rows (1 <= n <= 16384) in CSR form on the device, borrowed until
+   * the next set_operator: row i holds entries row_ptr_dev[i] .. row_ptr_dev[i+1] - 1
+   * (n + 1 int64 values, row_ptr_dev[0] == 0), col_dev (int32, 0 <= col < n) and val_dev
+   * (FP64). The library copies A once to the host when it builds its workspace (first
+   * solve after a set_* call) to form A^T for the adjoint; column indices out of range
+   * make that solve fail with PXA_ERR_INVALID. L, c, nu, nx, ny, u_dev, v_dev unused. */
+  const int64_t* row_ptr_dev;
+  const int32_t* col_dev;
+  const double* val_dev;
 } pxa_operator_desc;
+
+/* Objective (Sec. 2, Eq. cost and its terminal form). TERMINAL_L2:
+ * J = 0.5 ||q(T) - g||^2 (ADVDIFF_1D, CSR; g = 0 when target_dev is NULL).
+ * INTEGRAL_TRACKING: J = (1/T) sum_{j=1..K} dt ||q_j - g_j||^2, the rectangle rule of
+ * Eq. cost, with a static target g (BURGERS_1D; target_dev required) or the trajectory
+ * driven by the true forcing f_true = target_dev (ADVDIFF_2D; required). */
+typedef enum { PXA_OBJ_TERMINAL_L2 = 1, PXA_OBJ_INTEGRAL_TRACKING = 2 } pxa_objective_kind;
+typedef struct {
+  int kind;                 /* pxa_objective_kind */
+  const double* target_dev; /* device, n doubles, borrowed until the next pxa_set_objective or
+                               pxa_set_target; may be NULL for TERMINAL_L2 */
+} pxa_objective_desc;
+
+/* Precision of the time stepping (the benchmark spec's split: Krylov, superposition and the
+ * objective stay FP64). F64: FP64 stepping (ADVDIFF_1D, BURGERS_1D, CSR; the default for
+ * them). F32: FP32 stepping with FP32 accumulation (ADVDIFF_2D, whose only mode it is,
+ * and ADVDIFF_1D with 16 <= n <= 4096, run by the batched lanes as a batch of one). */
+typedef enum { PXA_F64 = 0, PXA_F32 = 1 } pxa_precision;
 
 typedef struct {
   double J;                 /* objective of the last gradient */
@@ -172,11 +216,28 @@ void pxa_destroy(pxa_ctx* ctx);
 /* Text of the last error raised on this context ("" if none). Never NULL. */
 const char* pxa_last_error(const pxa_ctx* ctx);
 
-/* Operator and grid (Sec. 4.2 / 4.3). Invalidates the workspace. */
+/* Operator and grid (Sec. 2 state equation; Sec. 4.2 / 4.3 problems). Resets the
+ * objective to the operator's default (TERMINAL_L2 for ADVDIFF_1D and CSR,
+ * INTEGRAL_TRACKING otherwise) and the precision to its default. Invalidates the
+ * workspace. */
 int pxa_set_operator(pxa_ctx* ctx, const pxa_operator_desc* op);
 /* Time window [0, T], K steps of `stepper` (PXA_CN for ADVDIFF_1D, PXA_RK4 for
- * BURGERS_1D), P equal subintervals (Alg. 1). K % P == 0 is required. */
+ * BURGERS_1D, ADVDIFF_2D and CSR), P equal subintervals (Alg. 1: T_p = p T / P).
+ * K % P == 0 is required. */
 int pxa_set_time(pxa_ctx* ctx, double T, int64_t K, int stepper, int P);
+/* Objective (pxa_objective_desc). A kind the operator does not support returns
+ * PXA_ERR_INVALID (set the operator first: PXA_ERR_STATE otherwise). Same as
+ * pxa_set_target for the target. Invalidates the stored direct state. */
+int pxa_set_objective(pxa_ctx* ctx, const pxa_objective_desc* obj);
+/* Stepping precision (pxa_precision). ADVDIFF_1D with PXA_F32 runs the whole gradient
+ * through the batched FP32 lanes (pxa_batch_* with one problem: FP32 lanes, FP64
+ * superposition; PXA_PHI_STEPPER carries the homogeneous parts by the stepper's own
+ * propagator as an FP32 band, PXA_PHI_EXP by FP64 Krylov exponentials); with it,
+ * pxa_gradient, pxa_gradient_async, pxa_sync and pxa_gradient_host are available and
+ * the split solves return PXA_ERR_INVALID. FP32 stepping of K steps loses about
+ * K * 2^-24 relative in J and the gradient. Unsupported combinations: PXA_ERR_INVALID.
+ * Invalidates the workspace. */
+int pxa_set_precision(pxa_ctx* ctx, int step_precision);
 /* Krylov dimension m (2 <= m <= 48), tolerance on the a-posteriori estimate
  * (relative to ||v||), homogeneous propagator (pxa_phi) and the number of Krylov
  * substeps per subinterval (>= 1; each substep spans K/(P*substeps) steps, which
@@ -194,10 +255,12 @@ int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
 int pxa_set_propagator(pxa_ctx* ctx, int method, int max_degree);
 /* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
 int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);
-/* Control (Eq. initupdate / paramupdate): ADVDIFF_1D: q0_dev = initial condition.
- * BURGERS_1D: f_dev = forcing, s(t) = sin(omega t) or 1 when omega == 0. */
+/* Control (Eq. initupdate / paramupdate): ADVDIFF_1D, CSR: q0_dev = initial condition.
+ * BURGERS_1D: f_dev = forcing, s(t) = sin(omega t) or 1 when omega == 0. ADVDIFF_2D:
+ * f_dev = forcing, s(t) = sin(omega t). */
 int pxa_set_control(pxa_ctx* ctx, const double* control_dev, double omega);
-/* Tracking target g (BURGERS_1D), or the true forcing f_true (ADVDIFF_2D). */
+/* The objective's target (see pxa_objective_desc): g (ADVDIFF_1D, CSR: terminal;
+ * BURGERS_1D: tracking), or the true forcing f_true (ADVDIFF_2D). */
 int pxa_set_target(pxa_ctx* ctx, const double* target_dev);
 /* Direct-state storage policy (pxa_memory). */
 int pxa_set_memory(pxa_ctx* ctx, int policy);
@@ -261,9 +324,11 @@ int pxa_set_cluster(pxa_ctx* ctx, int direct, int lanes, int chain);
  * one by one (0, default). */
 int pxa_set_graph(pxa_ctx* ctx, int enable);
 
-/* One direct-adjoint loop: J into *J_host (may be NULL), dJ/d(control) into
- * grad_dev (n doubles, caller-owned). Synchronises the stream; returns device-side
- * errors (NOT_CONVERGED, NONFINITE). */
+/* One direct-adjoint loop (Sec. 2: state, adjoint, gradient; Alg. 1 in PXA_PARAEXP
+ * mode, the hybrid scheme of Sec. 3.3 for BURGERS_1D and ADVDIFF_2D): J into *J_host
+ * (may be NULL), dJ/d(control) into grad_dev (n doubles, caller-owned; Eq. initupdate
+ * for an initial-condition control, Eq. paramupdate for a forcing). Synchronises the
+ * stream; returns device-side errors (NOT_CONVERGED, NONFINITE, TIMEOUT). */
 int pxa_gradient(pxa_ctx* ctx, int mode, double* J_host, double* grad_dev);
 /* Same, asynchronous: J is written to J_dev (one double, device). Errors raised
  * inside kernels surface at the next pxa_sync. Graph-capturable once the workspace
@@ -271,11 +336,13 @@ int pxa_gradient(pxa_ctx* ctx, int mode, double* J_host, double* grad_dev);
 int pxa_gradient_async(pxa_ctx* ctx, int mode, double* J_dev, double* grad_dev);
 /* The two halves of pxa_gradient, for a caller that differentiates through the
  * direct solve (e.g. an autograd function): pxa_solve_direct runs the direct problem
- * and stores what the adjoint needs (q(T) and the adjoint source, or the Burgers
- * trajectory / checkpoints) in the context, returning J; pxa_solve_adjoint then runs
- * the adjoint problem of the same mode and writes dJ/d(control) to grad_dev. Any
- * set_* call in between invalidates the stored state (PXA_ERR_STATE). Both
- * synchronise the stream. */
+ * (Eq. seriesDirect serially; in PXA_PARAEXP mode Eq. linzero, linInhomEqus, hom and
+ * fullsol0) and stores what the adjoint needs (q(T) and the adjoint source, or the
+ * Burgers trajectory / checkpoints) in the context, returning J; pxa_solve_adjoint
+ * then runs the adjoint problem of the same mode (Eq. adjInhom or hybadjinhom,
+ * adjHomNormal, fulladjsol) and writes dJ/d(control) to grad_dev (Eq. initupdate /
+ * paramupdate). Any set_* call in between invalidates the stored state
+ * (PXA_ERR_STATE). Both synchronise the stream. */
 int pxa_solve_direct(pxa_ctx* ctx, int mode, double* J_host);
 int pxa_solve_adjoint(pxa_ctx* ctx, int mode, double* grad_dev);
 /* Wait for the stream and report device-side errors (with timing on, also reads the
@@ -285,8 +352,39 @@ int pxa_sync(pxa_ctx* ctx);
  * runs pxa_gradient and copies the gradient back into grad_host (n doubles). */
 int pxa_gradient_host(pxa_ctx* ctx, int mode, const double* control_host, double* J_host,
                       double* grad_host);
+/* Iterative nonlinear Paraexp direct of Alg. 2 (Sec. 3.2, Eq. nonlinTrans, Jacobians,
+ * nlHomIter, fullsolIter) for BURGERS_1D (n <= 1024, u(0) = 0, the forcing of
+ * pxa_set_control): from the guess q_0(t) (guess_dev, (K+1) x n device rows, or NULL:
+ * q_0(t) = 0), each iteration linearises about q_i with the Jacobian averaged over each
+ * subinterval (dN/dq at the trapezoid-rule average of q_i there), steps the P linear
+ * inhomogeneous problems from zero concurrently (one thread block each; their source at
+ * each RK4 stage is N(Y) - J_p Y + s(t) f at the stage states Y of q_i's nonlinear RK4
+ * step), carries their homogeneous problems from q0 with the stepper's own propagator of
+ * (A + J_p) and sums them into q_{i+1} at every step. It stops when
+ * max_s ||q_{i+1}(t_s) - q_i(t_s)|| / max_s ||q_{i+1}(t_s)|| <= tol or after max_iter
+ * iterations. The fixed point is the serial RK4 trajectory. traj_dev ((K+1) x n,
+ * caller-owned) receives the last iterate; changes_host (max_iter doubles, may be NULL)
+ * the change of each iteration; *iters_host (may be NULL) their number. Allocates its
+ * buffers (three trajectories) on the first call. Returns PXA_OK (converged),
+ * PXA_ERR_NOT_CONVERGED (max_iter reached; traj_dev holds the last iterate),
+ * PXA_ERR_NONFINITE (diverged), or a set-up error. Synchronous. */
+int pxa_nl_paraexp(pxa_ctx* ctx, const double* guess_dev, double tol, int max_iter, double* traj_dev,
+                   double* changes_host, int* iters_host);
 /* Statistics of the last solve. */
 int pxa_get_stats(const pxa_ctx* ctx, pxa_stats* out);
+/* Limit of the context's bounded device waits (the mbarrier waits of the cluster halo
+ * exchanges), in SM clock cycles: 0 = the default, 2^31 cycles (about 1 s at 2 GHz);
+ * otherwise 1024 <= cycles <= 2^41 (rounded down to a multiple of 1024). A wait that
+ * runs out sets PXA_ERR_TIMEOUT, which the next synchronising call returns; the kernel
+ * then runs to its end (its results are not valid), the later waits of that launch give
+ * up early, and the context stays usable. Other values: PXA_ERR_INVALID. */
+int pxa_set_wait_limit(pxa_ctx* ctx, int64_t cycles);
+/* Test of the failure path of the bounded waits (no counterpart in the paper): launches
+ * one thread block that waits, with the context's wait limit, on an mbarrier that
+ * nothing completes (no copy is issued, no peer exists), then synchronises like
+ * pxa_sync. Returns PXA_ERR_TIMEOUT after the limit (the expected result), or an error
+ * of the set-up. Builds the workspace if needed (the operator and time must be set). */
+int pxa_wait_probe(pxa_ctx* ctx);
 /* Per-phase CUDA-event timing inside pxa_gradient (0 = off, default); with graphs on,
  * the events are part of the captured graph. */
 int pxa_set_timing(pxa_ctx* ctx, int enable);
@@ -417,6 +515,8 @@ typedef struct {
   int power_problems;       /* problems whose homogeneous parts apply the band of M^(K/P) */
   int band_power_max;       /* widest band of M^(K/P) in use (taps; 0: none) */
   int lane_steps;           /* q: the lanes apply the band of M^q, q CN steps at a time */
+  int one_launch;           /* 1 when the last gradient ran as one persistent launch */
+  int flow_grid;            /* thread blocks of that launch */
 } pxa_batch_stats;
 /* Create / destroy a batch context on `device`; `cuda_stream` is borrowed (NULL = the
  * default stream). */
@@ -458,6 +558,18 @@ int pxa_batch_set_lane_steps(pxa_batch* b, int q);
 /* Capture the whole gradient into a CUDA graph and replay it (1, default) or launch the
  * kernels one by one (0). */
 int pxa_batch_set_graph(pxa_batch* b, int enable);
+/* Schedule of a Paraexp gradient. one_launch = 1 (default): when no problem uses the
+ * Krylov exponential, the whole gradient of every problem is one persistent launch: a
+ * grid of resident thread blocks takes (problem, subinterval, phase) items (the source,
+ * each direct lane, the chain with the superposition, each adjoint lane, the adjoint
+ * chain with the gradient) from a dependency-ordered queue through an atomic counter,
+ * and an item starts once per-problem counters in device memory show its inputs done
+ * (a bounded wait: PXA_ERR_TIMEOUT after about 2^31 cycles). A problem's chain thus
+ * starts as soon as its own lanes are done instead of after every problem's. The
+ * results are bit-identical to the phase schedule. one_launch = 0: one launch per phase
+ * (seven). Serial stepping and batches with Krylov problems always use the phases.
+ * Other values: PXA_ERR_INVALID. Invalidates the captured graph. */
+int pxa_batch_set_schedule(pxa_batch* b, int one_launch);
 /* Per-phase CUDA-event timing of the next gradients (launched one by one; 0 = off). */
 int pxa_batch_set_timing(pxa_batch* b, int enable);
 /* One direct-adjoint loop of every problem, asynchronous on the stream: q0_dev (packed,

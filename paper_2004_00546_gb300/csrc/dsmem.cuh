@@ -46,16 +46,20 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait: gives up after ~2^31 cycles (about 1 s) or as soon as another CTA has
-// reported an error, setting PXA_ERR_TIMEOUT so that the host sees it.
+// Bounded wait: gives up after the context's wait limit (status[1] x 1024 cycles; 0 means
+// 2^31 cycles, about 1 s) or as soon as another CTA has reported an error, setting
+// PXA_ERR_TIMEOUT so that the host sees it. `status` points to the context's two-int
+// status block (status word, wait limit).
 __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
   if (mbar_try(bar, parity)) return;
+  const int units = ((volatile int*)status)[1];
+  const long long limit = units > 0 ? (long long)units << 10 : (1LL << 31);
   const long long t0 = clock64();
   for (int it = 1;; ++it) {
     if (mbar_try(bar, parity)) return;
     if ((it & 255) == 0) {
       if (*(volatile int*)status != 0) return;
-      if (clock64() - t0 > (1LL << 31)) {
+      if (clock64() - t0 > limit) {
         set_status(status, PXA_ERR_TIMEOUT);
         return;
       }

@@ -59,8 +59,8 @@ cudaError_t launch_ad1_expv(cudaStream_t st, int threads, int n, double am, doub
                             double tol, int v_in_smem, int* status, double* errmax);
 cudaError_t launch_ad1_superpose_direct(cudaStream_t st, int threads, int n, int r,
                                         const double* taps, const double* q0, const double* elast,
-                                        const double* hsum, double* qT, double* srcT, double* J,
-                                        int* status);
+                                        const double* hsum, const double* g, double* qT, double* srcT,
+                                        double* J, int* status);
 cudaError_t launch_ad1_superpose_adjoint(cudaStream_t st, int n, const double* lamK,
                                          const double* e0, const double* hsum, double* grad,
                                          int* status);
@@ -79,6 +79,14 @@ cudaError_t launch_bu1c_stepper_chain(cudaStream_t st, int C, int n, double L, d
                                       const double* W, double* gH);
 // Serial RK4 sweeps of the Burgers direct problem on clusters (kernels_bu1_rk4.cu).
 bool bu1_rk4_valid_cluster(int n, int C);
+// One iteration of Alg. 2 for 1D Burgers (kernels_bu1_nl.cu): Q -> Qn (every step), lanes
+// into V, qbar [P][n]; change[0] = max_s ||Qn_s - Q_s||^2, change[1] = max_s ||Qn_s||^2,
+// change[2] != 0 when non-finite. n <= 1024.
+cudaError_t launch_nl_iteration(cudaStream_t st, int n, int64_t K, int P, double L, double nu, double dt,
+                                const double* f, const double* sc, const double* Q, double* Qn, double* V,
+                                double* qbar, double* change);
+// One block waiting on an mbarrier that nothing completes (the bounded wait's failure path).
+cudaError_t launch_wait_probe(cudaStream_t st, int* status);
 cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, double omega, double* sc);
 // reserve_smem > 0 requests that much dynamic shared memory per CTA, so that no other
 // kernel's CTA fits beside the sweep on its SMs while it runs concurrently with them.

@@ -183,6 +183,9 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
   bool ok = mbar_wait(&t.bar[0], 0);
   if (!ok) {
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    // let the two copies issued above land (bounded again) before the block can leave
+    (void)mbar_wait(&t.bar[0], 0);
+    (void)mbar_wait(&t.bar[1], 0);
     return;
   }
   // per-point stencil coefficients: (A x)_c = cE x_e + cW x_w + cN x_n + cS x_s + cC x_c
@@ -221,6 +224,10 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
     ok = mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1);
     if (!ok) {
       if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+      // this lane's copy and the next lane's prefetch may still be in flight: let them
+      // land (bounded again) before the block can leave
+      (void)mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1);
+      if (l + 1 < l_end) (void)mbar_wait(&t.bar[1 + ((li + 1) & 1)], ((li + 1) >> 1) & 1);
       return;
     }
     const float* Q = t.q[0] + (li & 1) * TILE2;
@@ -355,6 +362,11 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
     ok = mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1) && ok;
     if (!ok) {
       if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+      // the coefficient copy, this lane's copy and the next lane's prefetch may still be
+      // in flight: let them land (bounded again) before the block can leave
+      (void)mbar_wait(&t.bar[0], 0);
+      (void)mbar_wait(&t.bar[1 + (li & 1)], (li >> 1) & 1);
+      if (l + 1 < l_end) (void)mbar_wait(&t.bar[1 + ((li + 1) & 1)], ((li + 1) >> 1) & 1);
       return;
     }
     const float* L = t.q[0] + (li & 1) * TILE2;

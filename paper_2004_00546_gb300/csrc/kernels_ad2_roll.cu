@@ -242,7 +242,15 @@ __device__ __forceinline__ void roll_task(const CUtensorMap* qmap, const CUtenso
       make_coef(CF[I & 3], un, vn, fn, A, mA, D);  // row i (slot of row i-4, used above for the last time)
     }
   }
-  if (!ok && t == 0) set_status(status, PXA_ERR_TIMEOUT);
+  if (!ok) {
+    if (t == 0) set_status(status, PXA_ERR_TIMEOUT);
+    // a copy whose wait gave up may still be in flight: wait (bounded again) for the last
+    // block issued to each ring slot before the warp's next task or the block's exit
+    for (int s = 0; s < NB && s < nblocks; ++s) {
+      const int last = s + NB * ((nblocks - 1 - s) / NB);  // the last block of slot s
+      (void)bar_wait(&bars[s], (uint32_t)((last / NB) & 1));
+    }
+  }
 }
 
 }  // namespace

@@ -19,6 +19,8 @@
 //                                  cheaper than the Krylov exponential.
 //   batch_superpose_*              Eq. fullsol0 / Eq. fulladjsol, J_i = 0.5 ||q_i(T)||^2,
 //                                  the adjoint terminal value and the IC gradient, FP64.
+#include <algorithm>
+
 #include "common.cuh"
 #include "krylov.cuh"
 #include "kernels_batch.cuh"
@@ -285,6 +287,180 @@ __global__ void batch_superpose_adjoint_kernel(const BatchInst* __restrict__ ins
   if (!isfinite(v)) set_status(status, PXA_ERR_NONFINITE);
 }
 
+// ---- one persistent launch with device-side dependencies --------------------------------
+// The whole Paraexp gradient of every problem as one launch: a persistent grid takes work
+// items from a queue through an atomic counter. Items (int4 {type, problem, lane, 0}):
+//   FLOW_SRC        the lanes' source (M - I) q0_i of Eq. linzero (FP64 band)
+//   FLOW_LANE       one direct lane (Eq. linInhomEqus), after its problem's source
+//   FLOW_CHAIN_SUP  the direct chain (Eq. hom) and the superposition (Eq. fullsol0, J_i,
+//                   the adjoint lanes' source (M^T - I) q_i(T)), after all P lanes
+//   FLOW_ALANE      one adjoint lane (Eq. adjInhom), after the superposition
+//   FLOW_ACHAIN_GRAD the adjoint chain (Eq. adjHomNormal) and the gradient (Eq. fulladjsol,
+//                   Eq. initupdate), after all P adjoint lanes
+// A finished item publishes its results (every thread fences its writes, then one thread
+// adds to the problem's counter in `flags`); an item first waits, one thread polling with
+// acquire loads and a bounded spin (PXA_ERR_TIMEOUT after ~2^31 cycles), for its counter
+// to reach the target. The queue lists every item after the items it depends on, and a
+// block claims an item only while it runs, so every awaited item is held by a running
+// block that waits only on earlier items: the waits end. Results read from other blocks
+// go through L2 (__ldcg). The arithmetic of each item is that of the phase kernels above,
+// so the results are bit-identical to theirs.
+enum { FLOW_SRC = 0, FLOW_LANE = 1, FLOW_CHAIN_SUP = 2, FLOW_ALANE = 3, FLOW_ACHAIN_GRAD = 4 };
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits (bounded) until *flag >= target; ends with a block barrier.
+__device__ __forceinline__ void flow_wait(const int* flag, int target, int* status) {
+  if (threadIdx.x == 0 && ld_acquire(flag) < target) {
+    const long long t0 = clock64();
+    for (int it = 1;; ++it) {
+      if (ld_acquire(flag) >= target) break;
+      __nanosleep(64);
+      if ((it & 63) == 0) {
+        if (*(volatile int*)status != 0) break;
+        if (clock64() - t0 > (1LL << 31)) {
+          set_status(status, PXA_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Every thread fences its global writes; after the barrier one thread publishes.
+__device__ __forceinline__ void flow_signal(int* flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(flag, 1);
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(BATCH_THREADS) batch_flow_kernel(
+    const BatchInst* __restrict__ inst, const int4* __restrict__ items, int nitems, int* counter, int* flags,
+    int count, int P, const float* __restrict__ taps32, const double* __restrict__ taps64, int64_t k,
+    const double* __restrict__ q0, double* src, double* E, double* qT, double* srcT, double* EA,
+    double* __restrict__ J, double* __restrict__ grad, int* status) {
+  extern __shared__ float smf[];
+  __shared__ int cur;
+  __shared__ double red[40];
+  int* const f_src = flags;
+  int* const f_lanes = flags + count;
+  int* const f_sup = flags + 2 * count;
+  int* const f_alanes = flags + 3 * count;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) return;  // the same for every thread of the block
+    const int4 wk = items[it];
+    const int type = wk.x, i = wk.y, lane = wk.z;
+    const BatchInst I = inst[i];
+    const int n = I.n;
+    if (type == FLOW_SRC) {
+      const int r = I.r64, w = 2 * r + 1;
+      const double* tg = taps64 + I.t64;
+      const double* xi = q0 + I.off;
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        double acc = 0.0;
+        for (int jj = 0; jj < w; ++jj) acc = fma(tg[jj], xi[wrapb(p + jj - r, n)], acc);
+        src[I.off + p] = acc - xi[p];
+      }
+      flow_signal(f_src + i);
+    } else if (type == FLOW_LANE || type == FLOW_ALANE) {
+      const bool adj = type == FLOW_ALANE;
+      flow_wait(adj ? f_sup + i : f_src + i, 1, status);
+      const double* sg = adj ? srcT : src;
+      const int r = I.r32, w = 2 * r + 1;
+      float *tp, *xa, *xb, *sr;
+      int wp;
+      lane_layout<PPT>(smf, n, r, w, tp, wp, xa, xb, sr);
+      const float* tg = taps32 + I.t32;
+      for (int j = threadIdx.x; j < wp; j += blockDim.x) tp[j] = j < w ? (adj ? tg[w - 1 - j] : tg[j]) : 0.f;
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        put_halo32(xa, n, r, p, 0.f);
+        sr[p] = (float)__ldcg(sg + I.off + p);
+      }
+      __syncthreads();
+      for (int64_t s = 0; s < k; ++s) {
+        band_step32<PPT>(tp, wp, xa, xb, sr, n, r);
+        __syncthreads();
+        float* t = xa;
+        xa = xb;
+        xb = t;
+      }
+      double* o = (adj ? EA : E) + I.off * P + (int64_t)lane * n;
+      for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = (double)xa[r + p];
+      flow_signal((adj ? f_alanes : f_lanes) + i);
+    } else {
+      // the chain of the summed homogeneous problems (direct: links over E[0 .. P-2];
+      // adjoint: over EA[P-1 .. 1] with the transposed band), then the superposition
+      const bool adj = type == FLOW_ACHAIN_GRAD;
+      flow_wait(adj ? f_alanes + i : f_lanes + i, P, status);
+      const bool power = I.rp > 0;
+      const int r = power ? I.rp : I.r32, w = 2 * r + 1;
+      const int64_t nst = power ? 1 : k;
+      float *tp, *xa, *xb, *sr;
+      int wp;
+      lane_layout<PPT>(smf, n, r, w, tp, wp, xa, xb, sr);
+      const float* tg = taps32 + (power ? I.tpw : I.t32);
+      const double* Ei = (adj ? EA : E) + I.off * P;
+      for (int j = threadIdx.x; j < wp; j += blockDim.x) tp[j] = j < w ? (adj ? tg[w - 1 - j] : tg[j]) : 0.f;
+      for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, 0.f);
+      __syncthreads();
+      const int first = adj ? P - 1 : 0, stride = adj ? -1 : 1;
+      for (int l = 0; l < P - 1; ++l) {
+        const double* e = Ei + (int64_t)(first + l * stride) * n;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) put_halo32(xa, n, r, p, xa[r + p] + (float)__ldcg(e + p));
+        __syncthreads();
+        for (int64_t s = 0; s < nst; ++s) {
+          band_step32<PPT>(tp, wp, xa, xb, nullptr, n, r);
+          __syncthreads();
+          float* t = xa;
+          xa = xb;
+          xb = t;
+        }
+      }
+      if (!adj) {
+        // qT = q0 + E[P-1] + h, J_i = 0.5 ||qT||^2, srcT = (M^T - I) qT
+        const double* el = Ei + (int64_t)(P - 1) * n;
+        double acc = 0.0;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          const double v = q0[I.off + p] + __ldcg(el + p) + (P > 1 ? (double)xa[r + p] : 0.0);
+          qT[I.off + p] = v;
+          acc = fma(v, v, acc);
+        }
+        const double Ji = 0.5 * block_sum(acc, red);
+        if (threadIdx.x == 0) {
+          J[i] = Ji;
+          if (!isfinite(Ji)) set_status(status, PXA_ERR_NONFINITE);
+        }
+        __syncthreads();  // qT complete before the band reads neighbours
+        const int r6 = I.r64, w6 = 2 * r6 + 1;
+        const double* t6 = taps64 + I.t64;
+        const double* q = qT + I.off;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          double s2 = 0.0;
+          for (int jj = 0; jj < w6; ++jj) s2 = fma(t6[w6 - 1 - jj], q[wrapb(p + jj - r6, n)], s2);
+          srcT[I.off + p] = s2 - q[p];
+        }
+        flow_signal(f_sup + i);
+      } else {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          const double v = __ldcg(qT + I.off + p) + __ldcg(Ei + p) + (P > 1 ? (double)xa[r + p] : 0.0);
+          grad[I.off + p] = v;
+          if (!isfinite(v)) set_status(status, PXA_ERR_NONFINITE);
+        }
+        __syncthreads();  // shared memory and `cur` are reused by the next item
+      }
+    }
+  }
+}
+
 // ---- launch wrappers ------------------------------------------------------------------
 namespace {
 constexpr int PPT_SMALL = 9, PPT_LARGE = 17;  // odd: coprime with the 32 shared-memory banks
@@ -385,6 +561,42 @@ cudaError_t launch_batch_superpose_adjoint(cudaStream_t st, const BatchInst* ins
                                            const double* h, double* grad, int* status) {
   dim3 grid((nmax + 255) / 256, count);
   batch_superpose_adjoint_kernel<<<grid, 256, 0, st>>>(inst, lamK, EA, lanes, h, grad, status);
+  return cudaGetLastError();
+}
+
+size_t batch_flow_smem(int nmax, int rmax, int rpmax) {
+  return std::max(batch_lanes_smem(nmax, rmax), batch_lanes_smem(nmax, std::max(rpmax, rmax)));
+}
+
+int batch_flow_grid(int device, int nmax, int rmax, int rpmax) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t sh = batch_flow_smem(nmax, rmax, rpmax);
+  const void* fn = small_lanes(nmax) ? (const void*)batch_flow_kernel<PPT_SMALL> : (const void*)batch_flow_kernel<PPT_LARGE>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BATCH_THREADS, sh);
+  if (per < 1) per = 1;
+  return (sms > 0 ? sms : 1) * per;
+}
+
+cudaError_t launch_batch_flow(cudaStream_t st, int grid, const BatchInst* inst, const int4* items, int nitems,
+                              int* state, int count, int P, const float* taps32, const double* taps64, int64_t k,
+                              const double* q0, double* src, double* E, double* qT, double* srcT, double* EA,
+                              double* J, double* grad, int* status, int nmax, int rmax, int rpmax) {
+  const size_t sh = batch_flow_smem(nmax, rmax, rpmax);
+  const bool small = small_lanes(nmax);
+  const void* fn = small ? (const void*)batch_flow_kernel<PPT_SMALL> : (const void*)batch_flow_kernel<PPT_LARGE>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  // state: [0] the queue counter, [1 ..] the per-problem counters (4 count)
+  e = cudaMemsetAsync(state, 0, sizeof(int) * (1 + 4 * (size_t)count), st);
+  if (e != cudaSuccess) return e;
+  if (small)
+    batch_flow_kernel<PPT_SMALL><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, state, state + 1, count, P, taps32,
+                                                           taps64, k, q0, src, E, qT, srcT, EA, J, grad, status);
+  else
+    batch_flow_kernel<PPT_LARGE><<<grid, BATCH_THREADS, sh, st>>>(inst, items, nitems, state, state + 1, count, P, taps32,
+                                                            taps64, k, q0, src, E, qT, srcT, EA, J, grad, status);
   return cudaGetLastError();
 }
 

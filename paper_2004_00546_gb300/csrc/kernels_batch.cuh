@@ -54,4 +54,14 @@ cudaError_t launch_batch_superpose_adjoint(cudaStream_t st, const BatchInst* ins
                                            const double* lamK, const double* EA, int lanes,
                                            const double* h, double* grad, int* status);
 
+// The whole Paraexp gradient as one persistent launch with device-side dependencies
+// (kernels_batch.cu, batch_flow_kernel). items: the queue (int4 {type, problem, lane, 0},
+// every item after the items it depends on); state: 1 + 4 count ints, zeroed here.
+size_t batch_flow_smem(int nmax, int rmax, int rpmax);
+int batch_flow_grid(int device, int nmax, int rmax, int rpmax);
+cudaError_t launch_batch_flow(cudaStream_t st, int grid, const BatchInst* inst, const int4* items, int nitems,
+                              int* state, int count, int P, const float* taps32, const double* taps64, int64_t k,
+                              const double* q0, double* src, double* E, double* qT, double* srcT, double* EA,
+                              double* J, double* grad, int* status, int nmax, int rmax, int rpmax);
+
 }  // namespace pxa

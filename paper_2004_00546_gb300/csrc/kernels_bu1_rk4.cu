@@ -323,6 +323,214 @@ __global__ void bu1_rk4_sweep_kernel(int n, double b, double a, double dt, int k
   if (multi) cl.sync();  // no CTA leaves while a neighbour could still address it
 }
 
+// ---- register wavefront form of the same sweep ---------------------------------------
+// The lane's points live in registers, one per thread. Warp w of a CTA holds the 32
+// consecutive local points p = base_w + lane, base_w = 24 w - 4Q, and keeps valid the
+// 24 points of lanes 4..27: the four stages of one RK4 step shrink the valid range by
+// one point per side and stage, so a stage takes its neighbours' values by warp
+// shuffles, and each step ends at one block barrier where every warp passes its first
+// and last 4 valid values to the adjacent warps through shared memory (double-buffered
+// by step parity, so one barrier per step suffices). All four SM sub-partitions get one
+// warp each at C2's size (64 points per CTA, Q = 4: 4 warps), where the shared-memory
+// form runs 3 warps and four barriers per step. After a group of Q steps each CTA sends
+// its first and last 4Q values to its cluster neighbours with st.async (double-buffered
+// by group parity, completing on the receiver's mbarrier), exactly like
+// bu1_rk4_sweep_kernel; a single CTA wraps its own values around the periodic grid.
+constexpr int WF_OWN = 24;
+
+template <bool FORCED, int Q>
+__global__ void bu1_rk4_wave_kernel(int n, double b, double a, double dt, int k,
+                                    const double* __restrict__ f, const double* __restrict__ sc,
+                                    const double* __restrict__ x0, double* __restrict__ out,
+                                    int lane_rows, const double* __restrict__ gt, double T,
+                                    double* __restrict__ Jdev, double* __restrict__ ckpt,
+                                    int ck_every, int* status) {
+  constexpr int HQ = 4 * Q;  // halo of a group
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double red[56];  // [0, 16): the cluster's partial sums; [16, 56): block_sum scratch
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int nc = (n + C - 1) / C, start = rank * nc, cnt = min(nc, n - start);
+  const int lane = (int)(blockIdx.x / C);
+  const int s0 = lane * k;
+  const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), ln = (int)(threadIdx.x & 31);
+  double* const xb = sm;           // [2 step parity][W][8]: first 4 and last 4 valid values
+  double* const rb = sm + 16 * W;  // [2 group parity][2 side][HQ]: received halos
+  const bool multi = C > 1;
+  const int left = (rank + C - 1) % C, right = (rank + 1) % C;
+  const int cnt_left = min(nc, n - left * nc);
+  const int p = WF_OWN * warp - HQ + ln;  // local point of this thread
+  const bool own = ln >= 4 && ln < 4 + WF_OWN && p >= 0 && p < cnt;
+  const int gi = ((start + p) % n + n) % n;
+  const double fp = f[gi];
+  const double gp = (own && gt) ? gt[start + p] : 0.0;
+  const double a2 = 2.0 * a, h2 = 0.5 * dt, dt6 = dt / 6.0;
+  // halo slots this thread fills in the neighbours (own boundary points) and reads here
+  const bool to_left = own && p < HQ, to_right = own && p >= cnt - HQ;
+  const int in_left = p + HQ;   // 0 <= in_left < HQ: point p of the left halo
+  const int in_right = p - cnt; // 0 <= in_right < HQ: point p of the right halo
+  uint32_t rl0 = 0u, rl1 = 0u, rr0 = 0u, rr1 = 0u, bl0 = 0u, bl1 = 0u, br0 = 0u, br1 = 0u;
+  if (multi && threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (multi && to_left) {  // my point p (< HQ) is point cnt_left + p of the left neighbour
+    rl0 = map_rank(smem_u32(rb + 1 * HQ + p), left);
+    rl1 = map_rank(smem_u32(rb + 3 * HQ + p), left);
+    bl0 = map_rank(smem_u32(&bar[0]), left);
+    bl1 = map_rank(smem_u32(&bar[1]), left);
+  }
+  if (multi && to_right) {  // my point p (>= cnt - HQ) is point p - cnt of the right neighbour
+    rr0 = map_rank(smem_u32(rb + 0 * HQ + (p - (cnt - HQ))), right);
+    rr1 = map_rank(smem_u32(rb + 2 * HQ + (p - (cnt - HQ))), right);
+    br0 = map_rank(smem_u32(&bar[0]), right);
+    br1 = map_rank(smem_u32(&bar[1]), right);
+  }
+  double u = x0 ? x0[(size_t)lane * n + gi] : 0.0;
+  if (own) {
+    if (out) out[((size_t)lane * lane_rows) * n + start + p] = u;
+    if (ckpt && s0 % ck_every == 0) ckpt[(size_t)(s0 / ck_every) * n + start + p] = u;
+  }
+  int ck_left = ckpt ? ck_every - (s0 % ck_every) : 0;  // steps until the next checkpoint
+  int ck_row = ckpt ? s0 / ck_every + 1 : 0;             // row of the next checkpoint
+  double* orow = (out && own) ? out + ((size_t)lane * lane_rows + 1) * n + start + p : nullptr;
+  const int groups = (k + Q - 1) / Q;
+  if (multi) {
+    if (threadIdx.x == 0) {
+      if (groups > 1) mbar_arm(&bar[0], 2 * HQ * (int)sizeof(double));
+      if (groups > 2) mbar_arm(&bar[1], 2 * HQ * (int)sizeof(double));
+    }
+    cl.sync();  // every CTA's barriers exist before any st.async targets them
+  }
+  // s(t) at the stage times of the current step; the next step's are loaded a step ahead
+  double c1 = 1.0, c2 = 1.0, c4 = 1.0;
+  if (FORCED) {
+    c1 = sc[3 * (size_t)s0];
+    c2 = sc[3 * (size_t)s0 + 1];
+    c4 = sc[3 * (size_t)s0 + 2];
+  }
+  const double* scp = FORCED ? sc + 3 * ((size_t)s0 + 1) : nullptr;
+  uint32_t ph0 = 0u, ph1 = 0u;
+  double jp = 0.0;
+  const unsigned FULL = 0xffffffffu;
+  for (int j = 0; j < k; ++j) {
+    double n1 = 1.0, n2 = 1.0, n4 = 1.0;
+    if (FORCED && j + 1 < k) {
+      n1 = scp[0];
+      n2 = scp[1];
+      n4 = scp[2];
+      scp += 3;
+    }
+    const double cf1 = FORCED ? c1 * fp : fp, cf2 = FORCED ? c2 * fp : fp, cf4 = FORCED ? c4 * fp : fp;
+    // stage 1
+    double ym = __shfl_up_sync(FULL, u, 1), yp = __shfl_down_sync(FULL, u, 1);
+    double kk = stage_k(b, a, a2, ym, u, yp, cf1);
+    double acc = kk;
+    double y = fma(h2, kk, u);
+    // stage 2
+    ym = __shfl_up_sync(FULL, y, 1);
+    yp = __shfl_down_sync(FULL, y, 1);
+    kk = stage_k(b, a, a2, ym, y, yp, cf2);
+    acc = fma(2.0, kk, acc);
+    y = fma(h2, kk, u);
+    // stage 3
+    ym = __shfl_up_sync(FULL, y, 1);
+    yp = __shfl_down_sync(FULL, y, 1);
+    kk = stage_k(b, a, a2, ym, y, yp, cf2);
+    acc = fma(2.0, kk, acc);
+    y = fma(dt, kk, u);
+    // stage 4
+    ym = __shfl_up_sync(FULL, y, 1);
+    yp = __shfl_down_sync(FULL, y, 1);
+    kk = stage_k(b, a, a2, ym, y, yp, cf4);
+    const double un = fma(dt6, acc + kk, u);
+    if (FORCED) {
+      c1 = n1;
+      c2 = n2;
+      c4 = n4;
+    }
+    const bool group_end = ((j + 1) % Q == 0) && (j + 1 < k);
+    const int gx = (j / Q) & 1;  // group parity
+    if (group_end) {
+      if (multi) {
+        if (to_left) st_async_f64(gx ? rl1 : rl0, un, gx ? bl1 : bl0);
+        if (to_right) st_async_f64(gx ? rr1 : rr0, un, gx ? br1 : br0);
+      } else {
+        if (to_left) rb[(2 * gx + 1) * HQ + p] = un;
+        if (to_right) rb[(2 * gx + 0) * HQ + (p - (cnt - HQ))] = un;
+      }
+    }
+    if (own) {
+      if (Jdev) {
+        const double d = un - gp;
+        jp = fma(d, d, jp);
+      }
+      if (orow) {
+        *orow = un;
+        orow += n;
+      }
+      if (ckpt && ck_left == 1) ckpt[(size_t)ck_row * n + start + p] = un;
+    }
+    if (ckpt) {
+      if (ck_left == 1) {
+        ck_left = ck_every;
+        ++ck_row;
+      } else {
+        --ck_left;
+      }
+    }
+    // pass the first and last valid values to the adjacent warps
+    double* const xs = xb + (size_t)(j & 1) * W * 8;
+    if (ln >= 4 && ln < 8) xs[warp * 8 + (ln - 4)] = un;
+    if (ln >= 24 && ln < 28) xs[warp * 8 + 4 + (ln - 24)] = un;
+    if (group_end && multi) {
+      mbar_wait_bounded(&bar[gx], gx ? ph1 : ph0, status);
+      if (gx) ph1 ^= 1u; else ph0 ^= 1u;
+    }
+    __syncthreads();
+    u = un;
+    if (ln < 4 && warp > 0) u = xs[(warp - 1) * 8 + 4 + ln];
+    if (ln >= 28 && warp < W - 1) u = xs[(warp + 1) * 8 + (ln - 28)];
+    if (group_end) {
+      if (in_left >= 0 && in_left < HQ) u = rb[(2 * gx + 0) * HQ + in_left];
+      if (in_right >= 0 && in_right < HQ) u = rb[(2 * gx + 1) * HQ + in_right];
+      // re-arm this parity's barrier for the exchange two groups on (every thread has
+      // passed its wait of this phase: the block barrier above)
+      if (multi && threadIdx.x == 0 && j / Q + 3 < groups) mbar_arm(&bar[gx], 2 * HQ * (int)sizeof(double));
+    }
+  }
+  if (Jdev) {
+    const double part = block_sum(jp, red + 16);
+    if (multi) {
+      double* r0 = cl.map_shared_rank(red, 0);
+      if (threadIdx.x == 0) r0[rank] = part;
+      cl.sync();
+    } else if (threadIdx.x == 0) {
+      red[0] = part;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      double J = 0.0;
+      for (int r = 0; r < C; ++r) J += red[r];
+      J *= dt / T;
+      *Jdev = J;
+      if (!isfinite(J)) set_status(status, PXA_ERR_NONFINITE);
+    }
+  }
+  if (multi) cl.sync();  // no CTA leaves while a neighbour could still address it
+}
+
+// Warps of the register wavefront for CTAs of nc points in clusters of C and groups of
+// Q steps; 0 when the shared-memory form must run instead: more than 32 warps, or a
+// single CTA whose grid is shorter than the 4Q-point halo (the halo would wrap around
+// the periodic grid more than once).
+static int wave_warps(int nc, int C, int q) {
+  if (C == 1 && nc < 4 * q) return 0;
+  const int w = (nc + 8 * (q - 1) + WF_OWN - 1) / WF_OWN;
+  return w <= 32 ? w : 0;
+}
+
 // Steps per exchange Q in {1, 2, 4}: every CTA must own the 4Q-point halo its neighbours
 // need and the threads (chunk + 2 (4Q - 1) points) must fit in one CTA; among those, the
 // Q with the least estimated time per step (27 FP64 warp instructions per step at 64
@@ -345,7 +553,8 @@ static int rk4_group(int n, int C, int want) {
   for (int q : {1, 2, 4}) {
     const int npts = nc + 2 * (4 * q - 1);
     if (!rk4_group_ok(n, C, q)) continue;
-    const int warps = (npts + 31) / 32;
+    const int ww = wave_warps(nc, C, q);
+    const int warps = ww > 0 ? ww : (npts + 31) / 32;
     const double cost = (double)((warps + 3) / 4) * 27 * 64 + (C > 1 ? 600.0 : 100.0) / q;
     if (cost < best_cost) {
       best_cost = cost;
@@ -372,6 +581,25 @@ __global__ void sum_parts_kernel(int count, const double* __restrict__ parts, do
   if (!isfinite(s)) set_status(status, PXA_ERR_NONFINITE);
 }
 
+// The failure path of the bounded waits, for tests: one thread block waits on an
+// mbarrier that nothing completes (one expected arrival that never comes, no copy is
+// issued, no peer exists), so the wait runs out after the context's wait limit and sets
+// PXA_ERR_TIMEOUT. Nothing targets the block's shared memory, so it may leave then.
+__global__ void wait_probe_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  mbar_wait_bounded(&bar, 0u, status);
+}
+
+cudaError_t launch_wait_probe(cudaStream_t st, int* status) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sum_parts(cudaStream_t st, int count, const double* parts, double* out, int* status) {
   sum_parts_kernel<<<1, 1, 0, st>>>(count, parts, out, status);
   return cudaGetLastError();
@@ -386,9 +614,11 @@ cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, doub
 template <bool FORCED, int Q>
 static cudaError_t launch_rk4_q(cudaStream_t st, int C, int lanes, int nc, void** args,
                                 int priority, size_t reserve) {
-  size_t sh = sizeof(double) * (6 * (size_t)(nc + 8 * Q) + 64);
+  const int W = wave_warps(nc, C, Q);
+  size_t sh = W > 0 ? sizeof(double) * (16 * (size_t)W + 16 * Q)
+                    : sizeof(double) * (6 * (size_t)(nc + 8 * Q) + 64);
   if (reserve > sh) sh = reserve;
-  const void* fn = (const void*)bu1_rk4_sweep_kernel<FORCED, Q>;
+  const void* fn = W > 0 ? (const void*)bu1_rk4_wave_kernel<FORCED, Q> : (const void*)bu1_rk4_sweep_kernel<FORCED, Q>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
   if (C > 8) {
@@ -398,7 +628,7 @@ static cudaError_t launch_rk4_q(cudaStream_t st, int C, int lanes, int nc, void*
   const int npts = nc + 2 * (4 * Q - 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * lanes);
-  cfg.blockDim = dim3(((npts + 31) / 32) * 32);
+  cfg.blockDim = dim3(W > 0 ? 32 * W : ((npts + 31) / 32) * 32);
   cfg.dynamicSmemBytes = sh;
   cfg.stream = st;
   cudaLaunchAttribute at[2];

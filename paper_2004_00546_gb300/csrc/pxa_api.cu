@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pxa.h"
+#include "kernels_csr.cuh"
 #include "kernels_1d.cuh"
 #include "kernels_ad2.cuh"
 
@@ -309,6 +310,17 @@ struct pxa_ctx {
   const double* control = nullptr;
   double omega = 0.0;
   const double* target = nullptr;
+  int wait_limit_units = 0;    // bounded device waits give up after this many x 1024 cycles (0: 2^31 cycles)
+  int obj_kind = 0;            // pxa_objective_kind in use (0: the operator's default)
+  int step_prec = PXA_F64;     // pxa_precision of the time stepping
+  pxa_batch* inner = nullptr;  // ADVDIFF_1D with FP32 stepping: a batch of one problem
+  // PXA_CSR: A^T (library-owned, formed on the host from A) and the lanes' vectors
+  int64_t* rpT = nullptr;
+  int32_t* colT = nullptr;
+  double* valT = nullptr;
+  double* csr_work = nullptr;  // [P][4][n] lane vectors when they do not fit in shared memory
+  // Alg. 2 (pxa_nl_paraexp): the iterate, the next iterate, the lanes, qbar, the change
+  double *nl_Q = nullptr, *nl_Qn = nullptr, *nl_V = nullptr, *nl_qbar = nullptr, *nl_change = nullptr;
   int memory = PXA_STORE_FULL;
   int band_req = 1;  // pxa_set_adjoint: 1 = banded adjoint when it fits, 0 = stage re-stepping
   bool use_graph = false, timing = false;
@@ -444,6 +456,13 @@ struct pxa_ctx {
   cudaEvent_t ev[7] = {};
   bool ev_ready = false;
   bool prep_marked = false;  // ev[6] marks the end of the adjoint preparation
+  // timing events of the overlapped side-stream work, per direct chunk: on the records
+  // stream [0] start, [1] after the band pre-pass, [2] after the pair records, [3] after
+  // the four-step records; on the lanes stream [4] start and [5] end of the adjoint lanes
+  cudaEvent_t ev_side[kMaxChunks][6] = {};
+  int side_marked = 0, g_side_marked = 0;  // chunks whose side events were recorded
+  bool side_lanes_marked[kMaxChunks] = {};
+  bool g_side_lanes_marked[kMaxChunks] = {};
 };
 
 namespace {
@@ -483,6 +502,14 @@ void release_workspace(pxa_ctx* c) {
   c->status = nullptr;
   c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
   c->lanesL = 0;
+  c->rpT = nullptr;
+  c->colT = nullptr;
+  c->valT = c->csr_work = nullptr;
+  c->nl_Q = c->nl_Qn = c->nl_V = c->nl_qbar = c->nl_change = nullptr;
+  if (c->inner) {
+    pxa_batch_destroy(c->inner);
+    c->inner = nullptr;
+  }
   c->scL = nullptr;
   c->scL_count = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
@@ -576,7 +603,9 @@ int prepare(pxa_ctx* c) {
   int rc;
   if ((rc = alloc(c, &c->Jdev, 1))) return rc;
   if ((rc = alloc(c, &c->errmax, 1))) return rc;
-  if ((rc = alloc(c, &c->status, 1))) return rc;
+  // [0] the status word, [1] the wait limit of the bounded device waits (units of 1024
+  // cycles, 0: the default)
+  if ((rc = alloc(c, &c->status, 2))) return rc;
   if ((rc = alloc(c, &c->ctl_buf, n))) return rc;
   if ((rc = alloc(c, &c->grad_buf, n))) return rc;
   const bool long1d = c->op.kind == PXA_ADVDIFF_1D && n > 4096;  // lanes in global memory only
@@ -590,7 +619,7 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->qT, n))) return rc;
     if ((rc = alloc(c, &c->tmp, n))) return rc;
     // Krylov basis: in shared memory when it fits beside the dense scratch
-    int extra = c->op.kind == PXA_ADVDIFF_1D ? n : 5 * (n + 2) + n;
+    int extra = (c->op.kind == PXA_ADVDIFF_1D || c->op.kind == PXA_CSR) ? n : 5 * (n + 2) + n;
     size_t with_v = krylov_smem_bytes(n, c->kry_m, extra, true);
     c->v_in_smem = with_v <= 200 * 1024;
     if ((rc = alloc(c, &c->V, (size_t)(c->kry_m + 1) * n))) return rc;
@@ -673,6 +702,45 @@ int prepare(pxa_ctx* c) {
       PXA_CUDA(c, cudaMemcpy(c->relpm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice), "copy");
       PXA_CUDA(c, cudaMemcpy(c->relpm_z, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice), "copy");
     }
+  } else if (c->op.kind == PXA_CSR) {
+    // A^T for the adjoint lanes and chain: A is copied to the host once and transposed
+    // entry by entry (set-up, not the solve path)
+    const int64_t* rp = c->op.row_ptr_dev;
+    std::vector<int64_t> hrp((size_t)n + 1);
+    PXA_CUDA(c, cudaMemcpy(hrp.data(), rp, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost), "copy A");
+    const int64_t nnz = hrp[n];
+    if (hrp[0] != 0 || nnz < 0 || nnz > (int64_t)INT32_MAX)
+      return fail(c, PXA_ERR_INVALID, "CSR row pointers (row_ptr[0] == 0, nnz < 2^31)");
+    for (int i = 0; i < n; ++i)
+      if (hrp[i + 1] < hrp[i]) return fail(c, PXA_ERR_INVALID, "CSR row pointers must not decrease");
+    std::vector<int32_t> hcol((size_t)(nnz > 0 ? nnz : 1));
+    std::vector<double> hval((size_t)(nnz > 0 ? nnz : 1));
+    if (nnz > 0) {
+      PXA_CUDA(c, cudaMemcpy(hcol.data(), c->op.col_dev, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost), "copy A");
+      PXA_CUDA(c, cudaMemcpy(hval.data(), c->op.val_dev, sizeof(double) * nnz, cudaMemcpyDeviceToHost), "copy A");
+    }
+    std::vector<int64_t> trp((size_t)n + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) {
+      if (hcol[e] < 0 || hcol[e] >= n) return fail(c, PXA_ERR_INVALID, "CSR column index out of range");
+      ++trp[(size_t)hcol[e] + 1];
+    }
+    for (int j = 0; j < n; ++j) trp[j + 1] += trp[j];
+    std::vector<int64_t> fill(trp.begin(), trp.end() - 1);
+    std::vector<int32_t> tcol((size_t)(nnz > 0 ? nnz : 1));
+    std::vector<double> tval((size_t)(nnz > 0 ? nnz : 1));
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = hrp[i]; e < hrp[i + 1]; ++e) {
+        const int64_t d = fill[hcol[e]]++;
+        tcol[d] = i;
+        tval[d] = hval[e];
+      }
+    if ((rc = alloc(c, &c->rpT, (size_t)n + 1))) return rc;
+    if ((rc = alloc(c, &c->colT, tcol.size()))) return rc;
+    if ((rc = alloc(c, &c->valT, tval.size()))) return rc;
+    PXA_CUDA(c, cudaMemcpy(c->rpT, trp.data(), sizeof(int64_t) * trp.size(), cudaMemcpyHostToDevice), "copy A^T");
+    PXA_CUDA(c, cudaMemcpy(c->colT, tcol.data(), sizeof(int32_t) * tcol.size(), cudaMemcpyHostToDevice), "copy A^T");
+    PXA_CUDA(c, cudaMemcpy(c->valT, tval.data(), sizeof(double) * tval.size(), cudaMemcpyHostToDevice), "copy A^T");
+    if (!csr_lanes_fit_smem(n) && (rc = alloc(c, &c->csr_work, (size_t)4 * n * P))) return rc;
   } else {
     int64_t k = c->K / P;
     // the side streams, events and priorities of the banded adjoint
@@ -836,6 +904,7 @@ int prepare(pxa_ctx* c) {
       return fail(c, PXA_ERR_INVALID, "no cluster size fits the banded adjoint sweep");
   }
   PXA_CUDA(c, cudaMemset(c->status, 0, sizeof(int)), "memset status");
+  PXA_CUDA(c, cudaMemcpy(c->status + 1, &c->wait_limit_units, sizeof(int), cudaMemcpyHostToDevice), "wait limit");
   c->stats.workspace_bytes = c->ws_bytes;
   c->stats.band_taps = c->op.kind == PXA_ADVDIFF_1D ? 2 * c->band_r + 1 : 0;
   c->stats.cluster_direct = c->op.kind == PXA_BURGERS_1D ? c->cl_rk4_direct : c->cl_direct;
@@ -848,16 +917,30 @@ int prepare(pxa_ctx* c) {
   return PXA_OK;
 }
 
-// Phase event i on the context's stream; while a graph is being captured it becomes an
+// Timing event `ev` on stream `s`; while a graph is being captured it becomes an
 // external event-record node, which records the event like a stream would at replay.
-void ev_record(pxa_ctx* c, int i) {
-  if (!(c->timing && c->ev_ready)) return;
+void ev_record_on(pxa_ctx* c, cudaEvent_t ev, cudaStream_t s) {
+  if (!(c->timing && c->ev_ready) || !ev) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(c->stream, &cs);
+  cudaStreamIsCapturing(s, &cs);
   const cudaError_t e = cs == cudaStreamCaptureStatusActive
-                            ? cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal)
-                            : cudaEventRecord(c->ev[i], c->stream);
+                            ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                            : cudaEventRecord(ev, s);
   if (e != cudaSuccess) cudaGetLastError();  // phase times then read as unavailable
+}
+
+// Phase event i on the context's stream.
+void ev_record(pxa_ctx* c, int i) { ev_record_on(c, c->ev[i], c->stream); }
+
+// The timing events (phases on the context's stream, side-stream work per chunk), created
+// once per context.
+int ensure_timing_events(pxa_ctx* c) {
+  if (c->ev_ready) return PXA_OK;
+  for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
+  for (auto& row : c->ev_side)
+    for (auto& e : row) PXA_CUDA(c, cudaEventCreate(&e), "event create");
+  c->ev_ready = true;
+  return PXA_OK;
 }
 
 // ---- 1D advection-diffusion (IC control, terminal objective) ----------------
@@ -881,7 +964,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       PXA_CUDA(c, launch_cn_lanes(st, 1, th, n, r, taps, 0, K / lq, q0, nullptr, c->E), "cn serial");
       ev_record(c, 1);
       ev_record(c, 2);
-      PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, taps, nullptr, c->E, nullptr, c->qT,
+      PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, taps, nullptr, c->E, nullptr, c->target, c->qT,
                                               nullptr, Jdev, c->status), "superpose");
     }
     if (do_a) {
@@ -922,7 +1005,7 @@ int enqueue_ad1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   }
   ev_record(c, 2);
   PXA_CUDA(c, launch_ad1_superpose_direct(st, th, n, r, taps, q0, c->E + (size_t)(P - 1) * n,
-                                          P > 1 ? c->hsum : nullptr, c->qT, c->srcA, Jdev,
+                                          P > 1 ? c->hsum : nullptr, c->target, c->qT, c->srcA, Jdev,
                                           c->status), "superpose");
   }
   if (!do_a) return PXA_OK;
@@ -1163,9 +1246,11 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       if (overlap) {
         PXA_CUDA(c, cudaEventRecord(c->ev_fork[ci], st), "fork");
         PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork[ci], 0), "fork wait");
+        ev_record_on(c, c->ev_side[ci][0], c->side);
         PXA_CUDA(c, launch_bu1_band_prepass(c->side, n, c->op.L, c->op.nu, dt, c->T, c->omega,
                                             c->control, c->target, c->traj, 0, P, ci == 0 ? 0 : b0 + 1,
                                             b1 + 1, K, c->rec, c->jt, c->prio_lo), "band prepass");
+        ev_record_on(c, c->ev_side[ci][1], c->side);
         // the adjoint lanes of the chunk (latency-bound, few SMs) on a second side stream,
         // beside the product records (throughput-bound) of the chain
         PXA_CUDA(c, cudaEventRecord(c->ev_prep[ci], c->side), "records ready");
@@ -1173,18 +1258,27 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
         if (c->rp)
           PXA_CUDA(c, launch_bu1_band_pair(c->side, n, c->rec, (b0 + 1) / 2, (b1 + 1) / 2, c->rp,
                                            c->prio_lo), "pair records");
+        ev_record_on(c, c->ev_side[ci][2], c->side);
         if (c->rq)
           PXA_CUDA(c, launch_bu1_band_quad(c->side, n, c->rp, (b0 + 1) / 4, (b1 + 1) / 4, c->rq, c->prio_lo),
                    "four-step records");
+        ev_record_on(c, c->ev_side[ci][3], c->side);
         const int l0 = (int)(b0 / k), l1 = (int)(b1 / k) < side_lanes ? (int)(b1 / k) : side_lanes;
         // the lanes of the last chunk run with no direct solve beside them: a cluster as
         // wide as the chain's steps them about twice as fast as the narrow ones that share
         // the GPU with the direct
         const int cl = ci == NC - 1 && (l1 - l0) * c->cl_band_chain <= 128 ? c->cl_band_chain : c->cl_band_lanes;
-        if (l1 > l0)
+        if (l1 > l0) {
+          ev_record_on(c, c->ev_side[ci][4], c->side2);
           PXA_CUDA(c, launch_bu1_band_sweep(c->side2, cl, l1 - l0, l0, n, c->rec, k, P, 0,
                                             nullptr, c->LI, c->E, c->status, c->prio_lo, c->q_sweep),
                                             "band lanes");
+          ev_record_on(c, c->ev_side[ci][5], c->side2);
+        }
+        if (c->timing && c->ev_ready) {
+          c->side_marked = ci + 1;
+          c->side_lanes_marked[ci] = l1 > l0;
+        }
       }
       ++nch;
     }
@@ -1403,13 +1497,100 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   return PXA_OK;
 }
 
+// ---- general sparse operator (CSR), classical RK4, IC control, terminal objective -----
+// parts: bit 0 = direct solve (J, lambda(T), adjoint source), bit 1 = adjoint solve
+int enqueue_csr(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
+  cudaStream_t st = c->stream;
+  const bool do_d = parts & 1, do_a = parts & 2;
+  const int n = c->op.n;
+  const int64_t* rp = c->op.row_ptr_dev;
+  const int32_t* col = c->op.col_dev;
+  const double* val = c->op.val_dev;
+  const int64_t K = c->K;
+  const double dt = c->T / (double)K;
+  const double* q0 = c->control;
+  if (mode == PXA_SERIAL) {
+    // Eq. seriesDirect: one lane of K steps from q0; lambda(T) = q(T) - g; the adjoint
+    // sweep of K transposed steps from lambda(T) gives lambda(0) = grad (Eq. initupdate)
+    if (do_d) {
+      ev_record(c, 0);
+      PXA_CUDA(c, launch_csr_rk4_lanes(st, 1, n, rp, col, val, nullptr, dt, K, q0, c->E, c->csr_work), "serial");
+      ev_record(c, 1);
+      ev_record(c, 2);
+      PXA_CUDA(c, launch_csr_superpose(st, n, nullptr, c->E, nullptr, c->target, c->qT, Jdev, c->status),
+               "objective");
+    }
+    if (do_a) {
+      PXA_CUDA(c, launch_csr_rk4_lanes(st, 1, n, c->rpT, c->colT, c->valT, nullptr, dt, K, c->qT, c->EA,
+                                       c->csr_work), "serial adjoint");
+      ev_record(c, 3);
+      ev_record(c, 4);
+      PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, nullptr, c->EA, nullptr, grad, c->status), "grad");
+      ev_record(c, 5);
+    }
+    return PXA_OK;
+  }
+  const int P = c->P;
+  const int64_t k = K / P;
+  const int nsub = c->kry_sub;
+  const int64_t steps_sub = k / nsub;
+  const int phi_mode = c->kry_phi == PXA_PHI_EXP ? 0 : 2;  // exp(tau A) or the RK4 power
+  const double hscale = c->kry_phi == PXA_PHI_EXP ? dt * (double)steps_sub : dt;
+  if (do_d) {
+    PXA_CUDA(c, cudaMemsetAsync(c->errmax, 0, sizeof(double), st), "reset errmax");
+    ev_record(c, 0);
+    // Eq. linzero / linInhomEqus: the shifted lanes start from zero with the source A q0
+    PXA_CUDA(c, (pxa_spmv_csr(st, n, rp, col, val, q0, c->src) == PXA_OK ? cudaSuccess : cudaErrorLaunchFailure),
+             "source");
+    PXA_CUDA(c, launch_csr_rk4_lanes(st, P, n, rp, col, val, c->src, dt, k, nullptr, c->E, c->csr_work), "lanes");
+    ev_record(c, 1);
+    // Eq. hom: the summed homogeneous problems, h <- Phi (h + e_j), j = 0 .. P-2
+    if (P > 1)
+      PXA_CUDA(c, launch_csr_chain(st, n, rp, col, val, c->E, 0, 1, P - 1, c->hsum, c->V, c->kry_m, phi_mode,
+                                   hscale, steps_sub, nsub, c->kry_tol, c->v_in_smem, c->status, c->errmax),
+               "chain");
+    ev_record(c, 2);
+    // Eq. fullsol0 at T, J and lambda(T) = q(T) - g; the adjoint lanes' source A^T lambda(T)
+    PXA_CUDA(c, launch_csr_superpose(st, n, q0, c->E + (size_t)(P - 1) * n, P > 1 ? c->hsum : nullptr, c->target,
+                                     c->qT, Jdev, c->status), "superpose");
+    PXA_CUDA(c, (pxa_spmv_csr(st, n, c->rpT, c->colT, c->valT, c->qT, c->srcA) == PXA_OK ? cudaSuccess
+                                                                                         : cudaErrorLaunchFailure),
+             "adjoint source");
+  }
+  if (!do_a) return PXA_OK;
+  // Eq. adjInhom: the shifted adjoint lanes from zero at T_{p+1} with A^T and A^T lambda(T)
+  PXA_CUDA(c, launch_csr_rk4_lanes(st, P, n, c->rpT, c->colT, c->valT, c->srcA, dt, k, nullptr, c->EA,
+                                   c->csr_work), "adjoint lanes");
+  ev_record(c, 3);
+  // Eq. adjHomNormal: carried down from the top with Phi^T
+  if (P > 1)
+    PXA_CUDA(c, launch_csr_chain(st, n, c->rpT, c->colT, c->valT, c->EA, P - 1, -1, P - 1, c->hsumA, c->V,
+                                 c->kry_m, phi_mode, hscale, steps_sub, nsub, c->kry_tol, c->v_in_smem, c->status,
+                                 c->errmax), "adjoint chain");
+  ev_record(c, 4);
+  // Eq. fulladjsol at 0, Eq. initupdate: grad = lambda(T) + e_0 + h
+  PXA_CUDA(c, launch_ad1_superpose_adjoint(st, n, c->qT, c->EA, P > 1 ? c->hsumA : nullptr, grad, c->status),
+           "grad");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
+// The objective kinds each operator supports (0: the operator's default).
+bool objective_ok(int kind, int obj) {
+  if (obj == 0) return true;
+  if (kind == PXA_ADVDIFF_1D || kind == PXA_CSR) return obj == PXA_OBJ_TERMINAL_L2;
+  return obj == PXA_OBJ_INTEGRAL_TRACKING;
+}
+
 int enqueue_parts(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (mode != PXA_SERIAL && mode != PXA_PARAEXP) return fail(c, PXA_ERR_INVALID, "mode");
   if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first");
   if (c->op.kind == PXA_BURGERS_1D && !c->target) return fail(c, PXA_ERR_STATE, "set_target first");
   if (c->op.kind == PXA_ADVDIFF_2D && !c->target) return fail(c, PXA_ERR_STATE, "set_target (f_true) first");
+  if (!objective_ok(c->op.kind, c->obj_kind)) return fail(c, PXA_ERR_INVALID, "objective kind for this operator");
   if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, parts, Jdev, grad);
   if (c->op.kind == PXA_ADVDIFF_2D) return enqueue_ad2(c, mode, parts, Jdev, grad);
+  if (c->op.kind == PXA_CSR) return enqueue_csr(c, mode, parts, Jdev, grad);
   return enqueue_bu1(c, mode, parts, Jdev, grad);
 }
 
@@ -1459,8 +1640,11 @@ void pxa_destroy(pxa_ctx* c) {
   cudaSetDevice(c->device);
   release_workspace(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  if (c->ev_ready)
-    for (auto& e : c->ev) cudaEventDestroy(e);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& row : c->ev_side)
+    for (auto& e : row)
+      if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -1468,8 +1652,20 @@ const char* pxa_last_error(const pxa_ctx* c) { return c ? c->err.c_str() : "null
 
 int pxa_set_operator(pxa_ctx* c, const pxa_operator_desc* op) {
   if (!c || !op) return PXA_ERR_INVALID;
-  if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D && op->kind != PXA_ADVDIFF_2D)
+  if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D && op->kind != PXA_ADVDIFF_2D &&
+      op->kind != PXA_CSR)
     return fail(c, PXA_ERR_INVALID, "operator kind");
+  c->obj_kind = 0;
+  c->step_prec = op->kind == PXA_ADVDIFF_2D ? PXA_F32 : PXA_F64;
+  if (op->kind == PXA_CSR) {
+    if (op->n < 1 || op->n > 16384 || !op->row_ptr_dev || !op->col_dev || !op->val_dev)
+      return fail(c, PXA_ERR_INVALID, "CSR operator (1 <= n <= 16384, row_ptr, col, val)");
+    c->op = *op;
+    c->have_op = true;
+    release_workspace(c);
+    invalidate(c);
+    return PXA_OK;
+  }
   if (op->kind == PXA_ADVDIFF_2D) {
     if (op->nx != op->ny || op->nx % 4 != 0 || op->nx < 8 || op->nx > 8192 || !(op->L > 0.0) ||
         !(op->nu >= 0.0) || !op->u_dev || !op->v_dev)
@@ -1502,6 +1698,7 @@ int pxa_set_time(pxa_ctx* c, double T, int64_t K, int stepper, int P) {
   if (c->op.kind == PXA_ADVDIFF_1D && stepper != PXA_CN) return fail(c, PXA_ERR_INVALID, "ADVDIFF_1D uses PXA_CN");
   if (c->op.kind == PXA_BURGERS_1D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "BURGERS_1D uses PXA_RK4");
   if (c->op.kind == PXA_ADVDIFF_2D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D uses PXA_RK4");
+  if (c->op.kind == PXA_CSR && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "CSR uses PXA_RK4");
   if (c->op.kind == PXA_BURGERS_1D && K < 4) return fail(c, PXA_ERR_INVALID, "K >= 4 for time interpolation");
   c->T = T;
   c->K = K;
@@ -1548,6 +1745,41 @@ int pxa_set_control(pxa_ctx* c, const double* control_dev, double omega) {
 int pxa_set_target(pxa_ctx* c, const double* target_dev) {
   if (!c || !target_dev) return PXA_ERR_INVALID;
   c->target = target_dev;
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_objective(pxa_ctx* c, const pxa_objective_desc* obj) {
+  if (!c || !obj) return PXA_ERR_INVALID;
+  if (obj->kind != PXA_OBJ_TERMINAL_L2 && obj->kind != PXA_OBJ_INTEGRAL_TRACKING)
+    return fail(c, PXA_ERR_INVALID, "objective kind");
+  if (!c->have_op) return fail(c, PXA_ERR_STATE, "set_operator first");
+  if (!objective_ok(c->op.kind, obj->kind))
+    return fail(c, PXA_ERR_INVALID, "this operator supports TERMINAL_L2 (ADVDIFF_1D, CSR) or INTEGRAL_TRACKING "
+                                    "(BURGERS_1D, ADVDIFF_2D) only");
+  if (obj->kind == PXA_OBJ_INTEGRAL_TRACKING && !obj->target_dev)
+    return fail(c, PXA_ERR_INVALID, "INTEGRAL_TRACKING needs a target");
+  c->obj_kind = obj->kind;
+  c->target = obj->target_dev;
+  if (c->inner) {  // the batch of one keeps J = 0.5 ||q(T)||^2: rebuilt at the next solve
+    pxa_batch_destroy(c->inner);
+    c->inner = nullptr;
+  }
+  invalidate(c);
+  return PXA_OK;
+}
+
+int pxa_set_precision(pxa_ctx* c, int prec) {
+  if (!c || (prec != PXA_F64 && prec != PXA_F32)) return PXA_ERR_INVALID;
+  if (!c->have_op) return fail(c, PXA_ERR_STATE, "set_operator first");
+  const int kind = c->op.kind;
+  if (kind == PXA_ADVDIFF_2D && prec != PXA_F32) return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D steps in FP32 only");
+  if ((kind == PXA_BURGERS_1D || kind == PXA_CSR) && prec != PXA_F64)
+    return fail(c, PXA_ERR_INVALID, "BURGERS_1D and CSR step in FP64 only");
+  if (kind == PXA_ADVDIFF_1D && prec == PXA_F32 && (c->op.n < 16 || c->op.n > 4096))
+    return fail(c, PXA_ERR_INVALID, "FP32 stepping of ADVDIFF_1D needs 16 <= n <= 4096");
+  c->step_prec = prec;
+  release_workspace(c);
   invalidate(c);
   return PXA_OK;
 }
@@ -1649,6 +1881,7 @@ int pxa_set_cluster(pxa_ctx* c, int direct, int lanes, int chain) {
 int pxa_set_graph(pxa_ctx* c, int enable) {
   if (!c) return PXA_ERR_INVALID;
   c->use_graph = enable != 0;
+  if (c->inner) pxa_batch_set_graph(c->inner, enable != 0);
   invalidate(c);
   return PXA_OK;
 }
@@ -1656,12 +1889,42 @@ int pxa_set_graph(pxa_ctx* c, int enable) {
 int pxa_set_timing(pxa_ctx* c, int enable) {
   if (!c) return PXA_ERR_INVALID;
   if (enable && !c->ev_ready) {
-    cudaSetDevice(c->device);
-    for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
-    c->ev_ready = true;
+    PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+    if (int rc = ensure_timing_events(c)) return rc;
   }
   c->timing = enable != 0;
   invalidate(c);
+  return PXA_OK;
+}
+
+// ADVDIFF_1D with FP32 stepping runs as a batch of one problem (FP32 lanes, FP64
+// superposition and Krylov), built at the first solve after a set_* call.
+static bool f32_path(const pxa_ctx* c) { return c->op.kind == PXA_ADVDIFF_1D && c->step_prec == PXA_F32; }
+
+static int f32_ready(pxa_ctx* c) {
+  if (c->inner) return PXA_OK;
+  if (c->target) return fail(c, PXA_ERR_INVALID, "FP32 stepping of ADVDIFF_1D has J = 0.5 ||q(T)||^2 (no target)");
+  pxa_batch* b = nullptr;
+  int rc = pxa_batch_create(&b, c->device, c->stream);
+  if (rc) return fail(c, rc, "FP32 stepping: batch context");
+  c->inner = b;
+  const int n = c->op.n;
+  const double nu = c->op.nu;
+  rc = pxa_batch_set(b, 1, &n, &nu, c->op.c, c->op.L, c->T, c->K, c->P);
+  if (!rc) rc = pxa_batch_set_krylov(b, c->kry_m, c->kry_tol, 0.04);
+  // the stepper's own propagator as one FP32 band per link, or FP64 Krylov exp(tau A)
+  if (!rc) rc = pxa_batch_set_homogeneous(b, c->kry_phi == PXA_PHI_EXP ? 1e30 : 0.0);
+  if (!rc) rc = pxa_batch_set_power(b, 1);
+  if (!rc) rc = pxa_batch_set_graph(b, c->use_graph ? 1 : 0);
+  if (!rc && c->lane_q_req) rc = pxa_batch_set_lane_steps(b, c->lane_q_req);
+  if (rc) return fail(c, rc, std::string("FP32 stepping: ") + pxa_batch_last_error(b));
+  return PXA_OK;
+}
+
+static int f32_sync(pxa_ctx* c) {
+  if (!c->inner) return PXA_OK;
+  const int rc = pxa_batch_sync(c->inner);
+  if (rc) return fail(c, rc, std::string("FP32 stepping: ") + pxa_batch_last_error(c->inner));
   return PXA_OK;
 }
 
@@ -1671,7 +1934,18 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
   if (rc) return rc;
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   double* Jd = J_dev ? J_dev : c->Jdev;
+  if (f32_path(c)) {
+    if (mode != PXA_SERIAL && mode != PXA_PARAEXP) return fail(c, PXA_ERR_INVALID, "mode");
+    if (!c->control) return fail(c, PXA_ERR_STATE, "set_control first");
+    if ((rc = f32_ready(c))) return rc;
+    rc = pxa_batch_gradient(c->inner, mode, c->control, Jd, grad_dev);
+    if (rc) return fail(c, rc, std::string("FP32 stepping: ") + pxa_batch_last_error(c->inner));
+    c->stats.lanes = mode == PXA_SERIAL ? 1 : c->P;
+    return PXA_OK;
+  }
   c->prep_marked = false;
+  c->side_marked = 0;
+  for (bool& b : c->side_lanes_marked) b = false;
   c->stats.lanes = mode == PXA_SERIAL ? 1 : c->P;
   c->stats.krylov_m = c->kry_m;
   c->stats.krylov_substeps = c->kry_sub;
@@ -1708,8 +1982,12 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
       c->g_grad = grad_dev;
       c->g_J = Jd;
       c->g_prep_marked = c->prep_marked;
+      c->g_side_marked = c->side_marked;
+      for (int i = 0; i < pxa_ctx::kMaxChunks; ++i) c->g_side_lanes_marked[i] = c->side_lanes_marked[i];
     }
     c->prep_marked = c->g_prep_marked;
+    c->side_marked = c->g_side_marked;
+    for (int i = 0; i < pxa_ctx::kMaxChunks; ++i) c->side_lanes_marked[i] = c->g_side_lanes_marked[i];
     PXA_CUDA(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
     return PXA_OK;
   }
@@ -1721,6 +1999,10 @@ static void collect_timing(pxa_ctx* c);
 int pxa_sync(pxa_ctx* c) {
   if (!c) return PXA_ERR_INVALID;
   if (!c->ready) return PXA_OK;
+  if (f32_path(c)) {
+    int rc = f32_sync(c);
+    if (rc) return rc;
+  }
   PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   collect_timing(c);
   return read_status(c);
@@ -1730,6 +2012,7 @@ int pxa_gradient(pxa_ctx* c, int mode, double* J_host, double* grad_dev) {
   if (!c || !grad_dev) return PXA_ERR_INVALID;
   int rc = pxa_gradient_async(c, mode, nullptr, grad_dev);
   if (rc) return rc;
+  if (f32_path(c) && (rc = f32_sync(c))) return rc;
   PXA_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   double J = 0.0;
   PXA_CUDA(c, cudaMemcpy(&J, c->Jdev, sizeof(double), cudaMemcpyDeviceToHost), "read J");
@@ -1768,11 +2051,36 @@ static void collect_timing(pxa_ctx* c) {
     c->stats.ms_adjoint_inhom = d;
     c->stats.ms_adjoint_hom = e;
     c->stats.ms_total = t;
+    // kernel time of the overlapped side-stream work, summed over the chunks
+    float pre = 0.f, pair = 0.f, quad = 0.f, lanes = 0.f;
+    bool sok = ok;
+    for (int ci = 0; ci < c->side_marked && sok; ++ci) {
+      float x = 0.f;
+      auto side_el = [&](float* acc, cudaEvent_t a, cudaEvent_t b) {
+        if (cudaEventElapsedTime(&x, a, b) != cudaSuccess) {
+          cudaGetLastError();
+          sok = false;
+        } else {
+          *acc += x;
+        }
+      };
+      side_el(&pre, c->ev_side[ci][0], c->ev_side[ci][1]);
+      side_el(&pair, c->ev_side[ci][1], c->ev_side[ci][2]);
+      side_el(&quad, c->ev_side[ci][2], c->ev_side[ci][3]);
+      if (c->side_lanes_marked[ci]) side_el(&lanes, c->ev_side[ci][4], c->ev_side[ci][5]);
+    }
+    if (!sok) pre = pair = quad = lanes = -1.f;
+    c->stats.side_chunks = c->side_marked;
+    c->stats.ms_side_prepass = c->side_marked ? pre : 0.f;
+    c->stats.ms_side_pair = c->side_marked ? pair : 0.f;
+    c->stats.ms_side_quad = c->side_marked ? quad : 0.f;
+    c->stats.ms_side_lanes = c->side_marked ? lanes : 0.f;
   }
 }
 
 int pxa_solve_direct(pxa_ctx* c, int mode, double* J_host) {
   if (!c) return PXA_ERR_INVALID;
+  if (f32_path(c)) return fail(c, PXA_ERR_INVALID, "FP32 stepping runs whole gradients (pxa_gradient)");
   int rc = prepare(c);
   if (rc) return rc;
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -1790,6 +2098,7 @@ int pxa_solve_direct(pxa_ctx* c, int mode, double* J_host) {
 
 int pxa_solve_adjoint(pxa_ctx* c, int mode, double* grad_dev) {
   if (!c || !grad_dev) return PXA_ERR_INVALID;
+  if (f32_path(c)) return fail(c, PXA_ERR_INVALID, "FP32 stepping runs whole gradients (pxa_gradient)");
   if (!c->ready || c->direct_mode != mode)
     return fail(c, PXA_ERR_STATE, "pxa_solve_adjoint needs a pxa_solve_direct of the same mode first");
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
@@ -1849,6 +2158,13 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   if (!c || !grad_dev) return PXA_ERR_INVALID;
   if (!c->have_op || !c->have_time || !c->control) return fail(c, PXA_ERR_STATE, "configure the problem first");
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  if (f32_path(c)) {  // the batch of one has its own autotuner
+    int rc = prepare(c);
+    if (!rc) rc = f32_ready(c);
+    if (!rc) rc = pxa_batch_autotune(c->inner, mode, c->control, c->Jdev, grad_dev, best_ms_host);
+    if (rc) return fail(c, rc, std::string("FP32 stepping: ") + pxa_batch_last_error(c->inner));
+    return PXA_OK;
+  }
   const bool timing = c->timing;
   c->timing = false;  // candidates are timed through the caller's path (graph replay when on)
   cudaEvent_t e0, e1;
@@ -1956,10 +2272,7 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
       // k = tau_I_adj / tau_I comes from one run with the phases in sequence (direct;
       // band records and adjoint lanes); then equal chunks, r = k/(k+1) and r = k are
       // timed and the fastest is kept.
-      if (!c->ev_ready) {
-        for (auto& e : c->ev) PXA_CUDA(c, cudaEventCreate(&e), "event create");
-        c->ev_ready = true;
-      }
+      if (int erc = ensure_timing_events(c)) return erc;
       const bool graph3 = c->use_graph;
       c->use_graph = false;
       c->overlap = false;
@@ -2017,6 +2330,92 @@ int pxa_autotune(pxa_ctx* c, int mode, double* grad_dev, double* best_ms_host) {
   c->stats.group_sweep = c->q_sweep;
   if (best_ms_host) *best_ms_host = best;
   return PXA_OK;
+}
+
+int pxa_nl_paraexp(pxa_ctx* c, const double* guess_dev, double tol, int max_iter, double* traj_dev,
+                   double* changes_host, int* iters_host) {
+  if (!c || !traj_dev || max_iter < 1 || !(tol > 0.0)) return PXA_ERR_INVALID;
+  if (!c->have_op || !c->have_time || c->op.kind != PXA_BURGERS_1D)
+    return fail(c, PXA_ERR_STATE, "pxa_nl_paraexp needs a BURGERS_1D operator and set_time");
+  if (c->op.n > 1024) return fail(c, PXA_ERR_INVALID, "pxa_nl_paraexp: n <= 1024 (one thread per grid point)");
+  if (!c->control) return fail(c, PXA_ERR_STATE, "set_control (the forcing) first");
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const int n = c->op.n, P = c->P;
+  const int64_t K = c->K;
+  const double dt = c->T / (double)K;
+  const size_t rows = (size_t)(K + 1) * n;
+  if (!c->nl_Q) {
+    if ((rc = alloc(c, &c->nl_Q, rows))) return rc;
+    if ((rc = alloc(c, &c->nl_Qn, rows))) return rc;
+    if ((rc = alloc(c, &c->nl_V, rows))) return rc;
+    if ((rc = alloc(c, &c->nl_qbar, (size_t)P * n))) return rc;
+    if ((rc = alloc(c, &c->nl_change, 3))) return rc;
+    c->stats.workspace_bytes = c->ws_bytes;
+  }
+  cudaStream_t st = c->stream;
+  const double* sc = nullptr;
+  if (c->omega != 0.0) {
+    PXA_CUDA(c, launch_bu1_forcing_table(st, K, dt, c->omega, c->sc), "forcing table");
+    sc = c->sc;
+  }
+  // Alg. 2: the initial guess of the direct solution (q(t) = q0 = 0 when none is given)
+  if (guess_dev)
+    PXA_CUDA(c, cudaMemcpyAsync(c->nl_Q, guess_dev, sizeof(double) * rows, cudaMemcpyDeviceToDevice, st), "guess");
+  else
+    PXA_CUDA(c, cudaMemsetAsync(c->nl_Q, 0, sizeof(double) * rows, st), "guess");
+  PXA_CUDA(c, cudaMemsetAsync(c->nl_V, 0, sizeof(double) * (size_t)n, st), "lane rows");
+  double* Q = c->nl_Q;
+  double* Qn = c->nl_Qn;
+  int result = PXA_ERR_NOT_CONVERGED, it = 0;
+  for (; it < max_iter;) {
+    PXA_CUDA(c, launch_nl_iteration(st, n, K, P, c->op.L, c->op.nu, dt, c->control, sc, Q, Qn, c->nl_V, c->nl_qbar,
+                                    c->nl_change), "iteration");
+    double ch[3] = {0.0, 0.0, 0.0};
+    PXA_CUDA(c, cudaMemcpyAsync(ch, c->nl_change, sizeof(ch), cudaMemcpyDeviceToHost, st), "read change");
+    PXA_CUDA(c, cudaStreamSynchronize(st), "stream sync");
+    std::swap(Q, Qn);  // q_i <- q_{i+1}
+    ++it;
+    const double err = ch[2] != 0.0 ? NAN : (ch[1] > 0.0 ? std::sqrt(ch[0] / ch[1]) : std::sqrt(ch[0]));
+    if (changes_host) changes_host[it - 1] = err;
+    if (!std::isfinite(err)) {
+      result = PXA_ERR_NONFINITE;
+      break;
+    }
+    if (err <= tol) {
+      result = PXA_OK;
+      break;
+    }
+  }
+  if (iters_host) *iters_host = it;
+  PXA_CUDA(c, cudaMemcpyAsync(traj_dev, Q, sizeof(double) * rows, cudaMemcpyDeviceToDevice, st), "trajectory");
+  PXA_CUDA(c, cudaStreamSynchronize(st), "stream sync");
+  if (result == PXA_ERR_NONFINITE) return fail(c, result, "the iteration diverged to non-finite values");
+  if (result == PXA_ERR_NOT_CONVERGED)
+    return fail(c, result, "the iteration's change stayed above the tolerance for max_iter iterations");
+  return PXA_OK;
+}
+
+int pxa_set_wait_limit(pxa_ctx* c, int64_t cycles) {
+  if (!c || cycles < 0 || (cycles > 0 && (cycles < 1024 || cycles > ((int64_t)INT32_MAX << 10))))
+    return PXA_ERR_INVALID;
+  c->wait_limit_units = (int)(cycles >> 10);
+  if (c->ready) {
+    PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+    PXA_CUDA(c, cudaMemcpy(c->status + 1, &c->wait_limit_units, sizeof(int), cudaMemcpyHostToDevice),
+             "wait limit");
+  }
+  return PXA_OK;
+}
+
+int pxa_wait_probe(pxa_ctx* c) {
+  if (!c) return PXA_ERR_INVALID;
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  PXA_CUDA(c, launch_wait_probe(c->stream, c->status), "wait probe");
+  return pxa_sync(c);
 }
 
 int pxa_get_stats(const pxa_ctx* c, pxa_stats* out) {

@@ -61,6 +61,12 @@ struct pxa_batch {
   int n_step = 0, n_kry = 0, n_pow = 0;
   std::vector<int> uses_krylov;  // per problem
   int* counter = nullptr;
+  // one persistent launch with device-side dependencies (pxa_batch_set_schedule)
+  int schedule = 1;          // requested: 1 = one launch when no problem uses Krylov, 0 = phases
+  int4* items_flow = nullptr;
+  int n_flow = 0, flow_grid = 0;
+  int* flow_state = nullptr;  // [1 + 4 count]: queue counter, per-problem counters
+  bool flow_last = false;     // the last gradient ran as one launch
   double *src = nullptr, *E = nullptr, *EA = nullptr, *h = nullptr, *hA = nullptr, *qT = nullptr,
          *srcT = nullptr, *V = nullptr, *errmax = nullptr;
   int* status = nullptr;
@@ -111,6 +117,9 @@ void brelease(pxa_batch* b) {
   b->kry_list = nullptr;
   b->n_step = b->n_kry = b->n_pow = 0;
   b->counter = b->status = nullptr;
+  b->items_flow = nullptr;
+  b->flow_state = nullptr;
+  b->n_flow = b->flow_grid = 0;
   b->src = b->E = b->EA = b->h = b->hA = b->qT = b->srcT = b->V = b->errmax = nullptr;
   b->bytes = 0;
   b->ready = false;
@@ -292,6 +301,34 @@ int bprepare(pxa_batch* b) {
   if ((rc = balloc(b, &b->kry_list, kry.size()))) return rc;
   if ((rc = balloc(b, &b->counter, 1))) return rc;
   if ((rc = balloc(b, &b->status, 1))) return rc;
+  // the queue of the one-launch schedule (Paraexp, no Krylov problems): sources; the
+  // direct lanes in the order above, each problem's chain + superposition placed one
+  // grid's worth of items after its last lane (so that its lanes are usually done when a
+  // block takes it); then the adjoint lanes and each problem's adjoint chain + gradient
+  // in the same way. Every item comes after the items it depends on.
+  b->flow_grid = batch_flow_grid(b->device, b->nmax, b->r32max, b->rpmax);
+  std::vector<int4> flow;
+  if (P > 1 && kry.empty()) {
+    for (int i : order) flow.push_back(make_int4(0, i, 0, 0));
+    for (int phase = 0; phase < 2; ++phase) {
+      std::vector<std::pair<double, int4>> keyed;
+      std::vector<double> last(cnt, -1.0);
+      for (size_t x = 0; x < ipar.size(); ++x) {
+        keyed.push_back({(double)x, make_int4(phase ? 3 : 1, ipar[x].x, ipar[x].y, 0)});
+        last[ipar[x].x] = (double)x;
+      }
+      for (int i = 0; i < cnt; ++i) keyed.push_back({last[i] + b->flow_grid + 0.5, make_int4(phase ? 4 : 2, i, 0, 0)});
+      std::stable_sort(keyed.begin(), keyed.end(),
+                       [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) { return x.first < y.first; });
+      for (auto& kv : keyed) flow.push_back(kv.second);
+    }
+  }
+  b->n_flow = (int)flow.size();
+  if (!flow.empty()) {
+    if ((rc = balloc(b, &b->items_flow, flow.size()))) return rc;
+    if ((rc = balloc(b, &b->flow_state, 1 + 4 * (size_t)cnt))) return rc;
+    BCUDA(b, cudaMemcpy(b->items_flow, flow.data(), sizeof(int4) * flow.size(), cudaMemcpyHostToDevice), "copy queue");
+  }
   if ((rc = balloc(b, &b->errmax, 1))) return rc;
   if ((rc = balloc(b, &b->src, tot))) return rc;
   if ((rc = balloc(b, &b->E, (size_t)P * tot))) return rc;
@@ -351,6 +388,19 @@ int benqueue(pxa_batch* b, cudaStream_t st, int mode, const double* q0, double* 
     mark(4);
     BCUDA(b, launch_batch_superpose_adjoint(st, b->inst, cnt, b->nmax, nullptr, b->EA, 1, nullptr, grad,
                                             b->status), "gradient");
+    mark(5);
+    return PXA_OK;
+  }
+  b->flow_last = b->schedule == 1 && b->n_flow > 0;
+  if (b->flow_last) {
+    // one persistent launch: every phase of every problem, ordered by device-side counters
+    BCUDA(b, launch_batch_flow(st, b->flow_grid, b->inst, b->items_flow, b->n_flow, b->flow_state, cnt, P,
+                               b->taps32, b->taps64, k, q0, b->src, b->E, b->qT, b->srcT, b->EA, J, grad,
+                               b->status, b->nmax, b->r32max, b->rpmax), "one-launch gradient");
+    mark(1);
+    mark(2);
+    mark(3);
+    mark(4);
     mark(5);
     return PXA_OK;
   }
@@ -515,6 +565,13 @@ int pxa_batch_set_timing(pxa_batch* b, int enable) {
   return PXA_OK;
 }
 
+int pxa_batch_set_schedule(pxa_batch* b, int one_launch) {
+  if (!b || (one_launch != 0 && one_launch != 1)) return PXA_ERR_INVALID;
+  b->schedule = one_launch;
+  binvalidate(b);
+  return PXA_OK;
+}
+
 int pxa_batch_set_graph(pxa_batch* b, int enable) {
   if (!b) return PXA_ERR_INVALID;
   b->use_graph = enable != 0;
@@ -658,6 +715,8 @@ int pxa_batch_get_stats(const pxa_batch* b, pxa_batch_stats* out) {
   s.band32_max = 2 * b->r32max + 1;
   s.band64_max = 2 * b->r64max + 1;
   s.lanes_grid = b->lanes_grid;
+  s.one_launch = b->flow_last ? 1 : 0;
+  s.flow_grid = b->flow_grid;
   s.krylov_err_max = b->err_last;
   s.workspace_bytes = b->bytes;
   s.krylov_problems = b->n_kry;

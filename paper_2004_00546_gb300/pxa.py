@@ -17,7 +17,9 @@ OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINIT
     0, -1, -2, -3, -4, -5, -6, -7)
 ERR_TOO_LARGE = -8
 EXPV_STATIC_MAX_DOUBLES = 131072
-ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D = 1, 2, 3
+ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D, CSR = 1, 2, 3, 4
+OBJ_TERMINAL_L2, OBJ_INTEGRAL_TRACKING = 1, 2
+F64, F32 = 0, 1
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
 PROP_KRYLOV, PROP_RELPM, PROP_BAND = 0, 1, 2
@@ -31,14 +33,15 @@ _STATUS_NAMES = {ERR_INVALID: "INVALID", ERR_CUDA: "CUDA", ERR_OOM: "OOM",
 
 EXPORTS = [
     "pxa_create", "pxa_destroy", "pxa_last_error", "pxa_set_operator", "pxa_set_time",
-    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_set_checkpoints", "pxa_set_lane_steps", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
+    "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_objective",
+    "pxa_set_precision", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_set_checkpoints", "pxa_set_lane_steps", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
-    "pxa_get_stats", "pxa_set_timing", "pxa_apply_operator", "pxa_step", "pxa_expv",
+    "pxa_get_stats", "pxa_set_timing", "pxa_set_wait_limit", "pxa_wait_probe", "pxa_nl_paraexp", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
     "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d", "pxa_spmv_csr",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
     "pxa_batch_set_homogeneous", "pxa_batch_set_power", "pxa_batch_set_lane_steps", "pxa_batch_set_timing",
-    "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_gradient", "pxa_batch_sync",
+    "pxa_batch_set_krylov", "pxa_batch_set_graph", "pxa_batch_set_schedule", "pxa_batch_gradient", "pxa_batch_sync",
     "pxa_batch_autotune", "pxa_batch_offsets", "pxa_batch_get_stats", "pxa_batch_problem_info",
 ]
 
@@ -52,7 +55,12 @@ class PxaError(RuntimeError):
 class OperatorDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("L", ctypes.c_double),
                 ("c", ctypes.c_double), ("nu", ctypes.c_double), ("nx", ctypes.c_int),
-                ("ny", ctypes.c_int), ("u_dev", ctypes.c_void_p), ("v_dev", ctypes.c_void_p)]
+                ("ny", ctypes.c_int), ("u_dev", ctypes.c_void_p), ("v_dev", ctypes.c_void_p),
+                ("row_ptr_dev", ctypes.c_void_p), ("col_dev", ctypes.c_void_p), ("val_dev", ctypes.c_void_p)]
+
+
+class ObjectiveDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("target_dev", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -69,7 +77,9 @@ class Stats(ctypes.Structure):
                 ("chunks", ctypes.c_int), ("partition_r", ctypes.c_float),
                 ("tau_ratio", ctypes.c_float), ("checkpoint_intervals", ctypes.c_int),
                 ("lane_steps", ctypes.c_int), ("lane_band_taps", ctypes.c_int),
-                ("prop_band_taps", ctypes.c_int)]
+                ("prop_band_taps", ctypes.c_int), ("side_chunks", ctypes.c_int),
+                ("ms_side_prepass", ctypes.c_float), ("ms_side_pair", ctypes.c_float),
+                ("ms_side_quad", ctypes.c_float), ("ms_side_lanes", ctypes.c_float)]
 
 
 class BatchStats(ctypes.Structure):
@@ -81,7 +91,8 @@ class BatchStats(ctypes.Structure):
                 ("ms_lanes", ctypes.c_float), ("ms_chains", ctypes.c_float),
                 ("ms_adjoint_lanes", ctypes.c_float), ("ms_adjoint_chains", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("power_problems", ctypes.c_int),
-                ("band_power_max", ctypes.c_int), ("lane_steps", ctypes.c_int)]
+                ("band_power_max", ctypes.c_int), ("lane_steps", ctypes.c_int), ("one_launch", ctypes.c_int),
+                ("flow_grid", ctypes.c_int)]
 
 
 _lib = None
@@ -106,6 +117,8 @@ def load(path: str = LIB_PATH):
         "pxa_set_magnus": [p, i],
         "pxa_set_control": [p, p, d],
         "pxa_set_target": [p, p],
+        "pxa_set_objective": [p, ctypes.POINTER(ObjectiveDesc)],
+        "pxa_set_precision": [p, i],
         "pxa_set_memory": [p, i],
         "pxa_set_adjoint": [p, i],
         "pxa_set_overlap": [p, i],
@@ -129,6 +142,9 @@ def load(path: str = LIB_PATH):
         "pxa_sync": [p],
         "pxa_gradient_host": [p, i, p, p, p],
         "pxa_get_stats": [p, ctypes.POINTER(Stats)],
+        "pxa_set_wait_limit": [p, i64],
+        "pxa_nl_paraexp": [p, p, d, i, p, p, ctypes.POINTER(i)],
+        "pxa_wait_probe": [p],
         "pxa_apply_operator": [p, i, p, p],
         "pxa_step": [p, i, i64, p, p],
         "pxa_expv": [p, i, i64, i, p, p, p],
@@ -141,6 +157,7 @@ def load(path: str = LIB_PATH):
         "pxa_batch_set": [p, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(d), d, d, d, i64, i],
         "pxa_batch_set_krylov": [p, i, d, d],
         "pxa_batch_set_graph": [p, i],
+        "pxa_batch_set_schedule": [p, i],
         "pxa_batch_set_homogeneous": [p, d],
         "pxa_batch_set_power": [p, i],
         "pxa_batch_set_lane_steps": [p, i],
@@ -225,16 +242,37 @@ class Context:
 
     # -- configuration ---------------------------------------------------------------
     def set_operator(self, kind, n, L=6.283185307179586, c=0.0, nu=0.0):
-        desc = OperatorDesc(kind, n, L, c, nu, 0, 0, None, None)
+        desc = OperatorDesc(kind, n, L, c, nu, 0, 0, None, None, None, None, None)
         self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
         self.n = n
 
     def set_operator_2d(self, nx, ny, u, v, nu, L=6.283185307179586):
         """2D advection-diffusion with a frozen velocity (u, v: CUDA float64 (ny, nx))."""
         self._keep["u"], self._keep["v"] = u, v
-        desc = OperatorDesc(ADVDIFF_2D, nx * ny, L, 0.0, nu, nx, ny, _dptr(u).value, _dptr(v).value)
+        desc = OperatorDesc(ADVDIFF_2D, nx * ny, L, 0.0, nu, nx, ny, _dptr(u).value, _dptr(v).value, None, None,
+                            None)
         self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
         self.n = nx * ny
+
+    def set_operator_csr(self, row_ptr, col, val):
+        """General sparse operator A (CSR on the device: int64 row_ptr[n + 1], int32 col,
+        float64 val), borrowed until the next set_operator."""
+        import torch
+
+        n = int(row_ptr.numel()) - 1
+        self._keep["csr"] = (row_ptr, col, val)
+        desc = OperatorDesc(CSR, n, 0.0, 0.0, 0.0, 0, 0, None, None, _tptr(row_ptr, torch.int64).value,
+                            _tptr(col, torch.int32).value, _dptr(val).value)
+        self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
+        self.n = n
+
+    def set_objective(self, kind, target=None):
+        self._keep["target"] = target
+        desc = ObjectiveDesc(kind, None if target is None else _dptr(target).value)
+        self._check(self._L.pxa_set_objective(self._h, ctypes.byref(desc)))
+
+    def set_precision(self, precision):
+        self._check(self._L.pxa_set_precision(self._h, int(precision)))
 
     def set_time(self, T, K, stepper, P):
         self._check(self._L.pxa_set_time(self._h, T, int(K), stepper, int(P)))
@@ -287,6 +325,28 @@ class Context:
 
     def set_timing(self, enable):
         self._check(self._L.pxa_set_timing(self._h, int(bool(enable))))
+
+    def set_wait_limit(self, cycles):
+        """Limit of the bounded device waits in SM cycles (0: the default, 2^31)."""
+        self._check(self._L.pxa_set_wait_limit(self._h, int(cycles)))
+
+    def nl_paraexp(self, traj, guess=None, tol=1e-12, max_iter=50):
+        """Alg. 2 for the configured Burgers problem: the last iterate into traj (CUDA
+        float64 (K+1, n)); returns (changes per iteration, converged). Raises PxaError for
+        a non-finite iterate or a set-up error."""
+        import numpy as np
+
+        ch = np.zeros(int(max_iter))
+        it = ctypes.c_int(0)
+        rc = self._L.pxa_nl_paraexp(self._h, None if guess is None else _dptr(guess), float(tol), int(max_iter),
+                                    _dptr(traj), ch.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            self._check(rc)
+        return ch[:it.value].copy(), rc == OK
+
+    def wait_probe(self):
+        """Runs the failure path of the bounded waits; raises PxaError(ERR_TIMEOUT)."""
+        self._check(self._L.pxa_wait_probe(self._h))
 
     # -- solves ------------------------------------------------------------------------
     def gradient(self, mode, grad) -> float:
@@ -462,6 +522,10 @@ class Batch:
 
     def set_graph(self, enable):
         self._check(self._L.pxa_batch_set_graph(self._h, 1 if enable else 0))
+
+    def set_schedule(self, one_launch):
+        """1: the whole Paraexp gradient as one persistent launch (default); 0: phases."""
+        self._check(self._L.pxa_batch_set_schedule(self._h, 1 if one_launch else 0))
 
     def gradient_async(self, mode, q0, J, grad):
         self._check(self._L.pxa_batch_gradient(self._h, mode, _dptr(q0), _dptr(J), _dptr(grad)))

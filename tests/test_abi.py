@@ -118,3 +118,42 @@ def test_header_is_plain_c():
         r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", lang, hdr],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_objective_and_precision_setters_reject_null_contexts(pxa_lib):
+    L = pxa_lib
+    assert L.pxa_set_objective(None, None) == pxa.ERR_INVALID
+    d = pxa.ObjectiveDesc(pxa.OBJ_TERMINAL_L2, None)
+    assert L.pxa_set_objective(None, ctypes.byref(d)) == pxa.ERR_INVALID
+    assert L.pxa_set_precision(None, pxa.F32) == pxa.ERR_INVALID
+
+
+def test_binding_structs_have_the_header_layout(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets of the C
+    structures in include/pxa.h (compiled by the host C compiler)."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    fields = {"pxa_operator_desc": (pxa.OperatorDesc, ["n", "L", "u_dev", "row_ptr_dev", "col_dev", "val_dev"]),
+              "pxa_objective_desc": (pxa.ObjectiveDesc, ["kind", "target_dev"]),
+              "pxa_stats": (pxa.Stats, ["workspace_bytes", "prop_band_taps", "side_chunks", "ms_side_lanes"]),
+              "pxa_batch_stats": (pxa.BatchStats, ["krylov_reach", "ms_total", "lane_steps"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "pxa.h")}"',
+             "int main(void) {"]
+    for name, (_, fl) in fields.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in fl:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                    check=True).stdout.splitlines())
+    for name, (cls, fl) in fields.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f in fl:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)

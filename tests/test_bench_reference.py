@@ -12,12 +12,17 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _run(*args):
+    import time
+
+    t0 = time.perf_counter()
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
                        capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1, r.stdout
-    return json.loads(lines[0])
+    d = json.loads(lines[0])
+    d["_wall_s"] = time.perf_counter() - t0
+    return d
 
 
 @pytest.mark.parametrize("workload", ["burgers1d", "advdiff1d", "batched1d", "spmv_csr"])
@@ -33,6 +38,10 @@ def test_reference_line_follows_the_contract(workload):
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # the timed steps fit inside the run: ms_per_step is a measured (sampled) step, and the
+    # scaling to the full workload is stated in the sample
+    assert d["steps"] * d["ms_per_step"] / 1e3 <= d["_wall_s"]
+    assert "scaled sample" in cb["sample"]
 
 
 @pytest.mark.parametrize("workload", ["advdiff1d_lanes", "advdiff2d_lanes"])

@@ -832,3 +832,86 @@ def test_cn_lanes_1d_streaming_matches_oracle(X, torch, n, nu):
     o = host(out).reshape(lanes, n)
     for l in range(lanes):
         assert rel(o[l], ref) < 1e-5
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(X, torch):
+    """The failure path of the bounded device waits: a thread block waits on an mbarrier
+    that nothing completes (no copy, no peer) and gives up after the context's wait
+    limit (2^20 cycles, about 0.5 ms), which the host reads as PXA_ERR_TIMEOUT; a Burgers
+    gradient on the same context, whose cluster halo exchanges wait under the same short
+    limit, then matches the oracle."""
+    n, nu, T, K, P = 256, 0.02, 0.05, 100, 4
+    f = I.fourier1d(n, 8, 61)
+    tg = I.fourier1d(n, 8, 62)
+    ctx = X.Context()
+    ctx.set_operator(X.BURGERS_1D, n, nu=nu)
+    ctx.set_time(T, K, X.RK4, P)
+    ctx.set_krylov(20, 1e-10, X.PHI_STEPPER, 1)
+    fd, td = dev(torch, f), dev(torch, tg)
+    ctx.set_control(fd)
+    ctx.set_target(td)
+    with pytest.raises(X.PxaError):
+        ctx.set_wait_limit(100)  # below 1024 cycles
+    ctx.set_wait_limit(1 << 20)
+    for _ in range(2):
+        with pytest.raises(X.PxaError) as ei:
+            ctx.wait_probe()
+        assert ei.value.code == X.ERR_TIMEOUT
+    out = torch.empty_like(fd)
+    J = ctx.gradient(X.PARAEXP, out)
+    Jo, go = O.bu1_gradient_serial(f, tg, nu, T, K)
+    assert abs(J - Jo) / Jo < 1e-10 and rel(host(out), go) < 1e-10
+    ctx.set_wait_limit(0)
+    with pytest.raises(X.PxaError) as ei:  # the default limit (2^31 cycles, about 1 s)
+        ctx.wait_probe()
+    assert ei.value.code == X.ERR_TIMEOUT
+    ctx.close()
+
+
+# ---- iterative nonlinear Paraexp direct (Sec. 3.2, Alg. 2) --------------------------------
+NL_CASES = {"n32": (32, 0.05, 0.5, 128, 4, 3.0, 1.5), "n256": (256, 0.02, 0.25, 400, 8, 2.0, 0.0),
+            "n1000": (1000, 0.02, 0.1, 200, 10, 1.0, 2.0)}
+
+
+def nl_setup(X, torch, case):
+    n, nu, T, K, P, amp, om = NL_CASES[case]
+    f = amp * I.fourier1d(n, 8, 71)
+    ctx = bu1_ctx(X, n, nu, T, K, P, phi=X.PHI_STEPPER)
+    fd = dev(torch, f)
+    ctx.set_control(fd, om)
+    traj = torch.empty((K + 1, n), dtype=torch.float64, device="cuda")
+    return ctx, fd, traj, f
+
+
+@pytest.mark.parametrize("case", sorted(NL_CASES))
+def test_nl_paraexp_matches_the_oracle_iteration_by_iteration(X, torch, case):
+    """After 1, 2 and 3 iterations from q(t) = 0 the GPU iterate equals the oracle's point
+    by point (1e-10 of its largest value) and so do the iterations' changes."""
+    n, nu, T, K, P, amp, om = NL_CASES[case]
+    ctx, fd, traj, f = nl_setup(X, torch, case)
+    for iters in (1, 2, 3):
+        tr_o, ch_o, _ = O.bu1_nl_paraexp_direct(f, nu, T, K, P, omega=om, tol=1e-300, max_iter=iters)
+        ch, ok = ctx.nl_paraexp(traj, tol=1e-300, max_iter=iters)
+        assert not ok and len(ch) == iters == len(ch_o)
+        assert rel(traj.cpu().numpy(), tr_o) < 1e-10, (case, iters)
+        assert np.all(np.abs(ch - ch_o) <= 1e-10 * np.maximum(ch_o, 1e-3)), (ch, ch_o)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", sorted(NL_CASES))
+def test_nl_paraexp_converges_to_the_serial_rk4_trajectory(X, torch, case):
+    """Iterated to a change of 1e-12 the iterate is the serial RK4 trajectory (the
+    iteration's fixed point), in as many iterations as the oracle takes (within one)."""
+    n, nu, T, K, P, amp, om = NL_CASES[case]
+    ctx, fd, traj, f = nl_setup(X, torch, case)
+    g = I.fourier1d(n, 8, 72)
+    _, _, ts = O.bu1_gradient_serial(f, g, nu, T, K, omega=om, want_traj=True)
+    _, ch_o, ok_o = O.bu1_nl_paraexp_direct(f, nu, T, K, P, omega=om, tol=1e-12, max_iter=60)
+    ch, ok = ctx.nl_paraexp(traj, tol=1e-12, max_iter=60)
+    assert ok and ok_o and abs(len(ch) - len(ch_o)) <= 1 and ch[-1] <= 1e-12
+    assert rel(traj.cpu().numpy(), ts) < 1e-10
+    # the serial trajectory as the guess is a fixed point: one iteration changes nothing
+    guess = dev(torch, ts)
+    ch1, ok1 = ctx.nl_paraexp(traj, guess=guess, tol=1e-12, max_iter=1)
+    assert ok1 and ch1[0] < 1e-13 and rel(traj.cpu().numpy(), ts) < 1e-13
+    ctx.close()

@@ -268,3 +268,36 @@ def test_batch_full_size_matches_oracle_on_a_stride(X, torch):
                 Jo, go = oracle_serial[i]
             eJ, eg = abs(Jh[i] - Jo) / Jo, rel(gh[off[i]:off[i + 1]], go)
             assert eJ < tol and eg < tol, (mode, i, int(prob["n"][i]), eJ, eg)
+
+
+@pytest.mark.parametrize("K,P", [(512, 8), (96, 2), (4096, 16)])
+def test_batch_one_launch_equals_the_phases(X, torch, small, K, P):
+    """The one-launch schedule (a persistent grid taking dependency-ordered items: sources,
+    lanes, chain + superposition, adjoint lanes, adjoint chain + gradient) gives the same
+    bits as the seven-phase schedule, launched directly and as a graph replay, and the
+    oracle's gradients within the FP32 tolerance."""
+    q0 = dev(torch, small["q0"])
+    nprob = len(small["n"])
+    res = {}
+    for sched, graph in ((0, True), (1, True), (1, False)):
+        b = X.Batch()
+        b.set(small["n"], small["nu"], c=small["c"], T=small["T"], K=K, P=P)
+        b.set_homogeneous(0.0)
+        b.set_schedule(sched)
+        b.set_graph(graph)
+        J = torch.empty(nprob, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(q0)
+        for _ in range(2):  # a second gradient reuses the queue and its counters
+            b.gradient(X.PARAEXP, q0, J, g)
+        b.sync()
+        assert b.stats()["one_launch"] == sched
+        res[(sched, graph)] = (J.cpu().numpy(), g.cpu().numpy())
+        off = b.offsets()
+        b.close()
+    for key in ((1, True), (1, False)):
+        assert np.array_equal(res[key][0], res[(0, True)][0]) and np.array_equal(res[key][1], res[(0, True)][1])
+    tol = 1e-4 if K <= 512 else 2 * K * 2.0 ** -24
+    J, g = res[(1, True)]
+    for i in range(nprob):
+        Jo, go = reference(small, off, i, K, P, False)
+        assert abs(J[i] - Jo) / Jo < tol and rel(g[off[i]:off[i + 1]], go) < tol, i
