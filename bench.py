@@ -68,6 +68,15 @@ FLOPS_CN_BAND_TAP = 2.0       # one FMA per tap of the circulant CN band per poi
 FP64_INSTR_RK4_STEP = 27
 FP64_INSTR_BAND_STEP = 9
 SM_CLOCK_HZ = 2.07e9
+# CTAs per thread-block cluster of the 1D advection-diffusion lane and band-chain kernels
+# (fixed in the kernels: every lane and the chain run on one cluster of 8 CTAs)
+AD1_LANE_CLUSTER = 8
+AD1_CHAIN_CLUSTER = 8
+# Method flops of one Crank-Nicolson step per grid point (the tridiagonal right-hand side
+# 5, the periodic tridiagonal solve by Sherman-Morrison and Thomas 8): what the method
+# computes, independent of how the library evaluates the step
+FLOPS_CN_STEP = 13.0
+GATE = 1e-8  # the metric's accuracy gate on FP64 gradients against the serial oracle
 
 # DRAM bytes per launch from the committed ncu captures (profiles/*.md); None when the
 # kernel changed after the capture.
@@ -77,7 +86,8 @@ TRAFFIC = {
     "spmv_csr_kernel": 1744881408 + 257540352,
     # the direct solve is 8 chunk launches of 61.95 KB DRAM reads each (the trajectory
     # rows stay in L2 during the launch)
-    "bu1_rk4_sweep_kernel": 8 * 61.95e3,
+    "bu1_rk4_sweep_kernel": 8 * 61.95e3,  # the shared-memory form (grids with > 744 points per CTA)
+    "bu1_rk4_wave_kernel": None,
     "bu1_band_sweep_kernel": 1.6407e9 + 0.1587e9,
     # the four-step chain: 4 segment launches of 348.8 MB read + 10.5 MB written each
     "bu1_band_chain4_kernel": 4 * (348767488.0 + 10518528.0),
@@ -96,6 +106,11 @@ def parse():
     ap.add_argument("--once", action="store_true",
                     help="profiling run: W warm-up gradients then one more of the headline "
                          "configuration (1D workloads), default cluster sizes, no autotuning")
+    ap.add_argument("--K", type=int, default=0,
+                    help="with --once on the 1D workloads: this many time steps at the workload's dt (a "
+                         "shorter window for profiling captures)")
+    ap.add_argument("--no-compare", dest="no_compare", action="store_true",
+                    help="skip the Paraexp-against-serial comparison of the other workloads")
     ap.add_argument("--checkpoints", type=int, default=0,
                     help="with --once on the Burgers workload: the multi-checkpoint scheme with this many intervals")
     return ap.parse_args()
@@ -167,6 +182,18 @@ def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
     return world * units_per_rank / (max_ms / 1e3)
 
 
+def rel_err(a, b):
+    """Larger of the point-wise error relative to max|b| and the norm-wise relative error."""
+    a, b = np.asarray(a, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()
+    pw = float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    nw = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return max(pw, nw)
+
+
+def gate_mark(err, tol=GATE):
+    return None if err is None else ("pass" if err <= tol else "fail")
+
+
 def make_inputs(w):
     from paper_2004_00546_gb300 import inputs as I
 
@@ -229,6 +256,189 @@ def time_mode(X, torch, ctx, mode, steps, warmup, flush, timing=False):
         if timing:
             phases.append(ctx.stats())
     return times, phases, grad
+
+
+def time_pair(X, torch, make, steps, warmup, flush):
+    """Paraexp and serial stepping of one workload timed the same way: the same steps and
+    warm-up, graph replays, L2 flushed before every step, CUDA events on the context's
+    stream. make(mode) returns a configured context. Returns {name: (mean ms, gradient)}."""
+    out = {}
+    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+        ctx = make(mode)
+        times, _, g = time_mode(X, torch, ctx, mode, steps, warmup, flush)
+        out[name] = (float(np.mean(times)), g.detach().cpu().numpy())
+        ctx.close()
+    return out
+
+
+def pair_entry(label, res, g_ref, tol, note):
+    """One workload of the Paraexp-against-serial comparison."""
+    pe, se = rel_err(res["paraexp"][1], g_ref), rel_err(res["serial"][1], g_ref)
+    return {"workload": label, "paraexp_ms": res["paraexp"][0], "serial_ms": res["serial"][0],
+            "speedup": res["serial"][0] / res["paraexp"][0], "rel_err_paraexp": pe, "rel_err_serial": se,
+            "tolerance": tol, "gate": gate_mark(pe, tol), "note": note}
+
+
+def compare_advdiff1d(args, X, torch, flush):
+    """C1: Paraexp with the stepper's subinterval propagator as one circulant band per link
+    against serial stepping (both with the lanes on the band of M^4), and Paraexp with the
+    autotuned Krylov propagator; errors against the serial FP64 oracle."""
+    w = WORKLOADS["advdiff1d"]
+    inp = make_inputs(w)
+    ctl = torch.as_tensor(inp["control"], device="cuda")
+
+    def make(mode, prop=X.PROP_BAND):
+        ctx = make_ctx(X, w, X.PHI_STEPPER)
+        ctx.set_control(ctl)
+        if mode == X.PARAEXP and prop == X.PROP_BAND:
+            ctx.set_propagator(X.PROP_BAND, 150)
+        return ctx
+
+    res = time_pair(X, torch, make, args.steps, args.warmup, flush)
+    _, g_ref = oracle_gradient(w, inp)
+    e = pair_entry(w["label"].replace(" (Krylov m autotuned)", ""), res, g_ref, GATE,
+                   "homogeneous parts: the stepper's subinterval propagator M^(K/P) as one circulant band "
+                   "per link (exact for this periodic constant-coefficient operator)")
+    # the north star's Krylov propagator, autotuned (m, substeps), timed the same way
+    ctx = make(X.PARAEXP, X.PROP_KRYLOV)
+    ctx.autotune(X.PARAEXP, torch.empty(w["n"], dtype=torch.float64, device="cuda"))
+    st = ctx.stats()
+    times, _, g = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush)
+    ctx.close()
+    ek = rel_err(g.cpu().numpy(), g_ref)
+    e["paraexp_krylov"] = {"ms": float(np.mean(times)), "speedup": e["serial_ms"] / float(np.mean(times)),
+                           "rel_err": ek, "gate": gate_mark(ek), "krylov_m": st["krylov_m"],
+                           "krylov_substeps": st["krylov_substeps"]}
+    return e
+
+
+def compare_batched(args, X, torch, flush):
+    """C4: 256 problems of uneven size; Paraexp (stepper's propagator as a band of M^(K/P),
+    FP32) against serial stepping, and Paraexp with every homogeneous part by the FP64
+    Krylov exponential; errors against the FP64 oracle on sampled problems."""
+    import oracle as O
+    from paper_2004_00546_gb300 import inputs as I
+
+    w = WORKLOADS["batched1d"]
+    prob = I.batch1d_problem(count=w["count"], seed=2007)
+    cnt, K, P, off = w["count"], w["K"], w["P"], prob["offsets"]
+    q0 = torch.as_tensor(prob["q0"], device="cuda")
+    J = torch.empty(cnt, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(q0)
+    order = np.argsort(-prob["n"])
+    stiff = np.argsort(-(prob["nu"] * prob["n"] ** 2))
+    sample = list(dict.fromkeys(list(order[:4]) + list(stiff[:4])))
+
+    def timed(b, mode):
+        for _ in range(args.warmup):
+            b.gradient(mode, q0, J, g)
+        t = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.gradient_async(mode, q0, J, g)
+            e1.record()
+            torch.cuda.synchronize()
+            b.sync()
+            t.append(e0.elapsed_time(e1))
+        return float(np.mean(t)), g.cpu().numpy()
+
+    def timed_once(b, mode):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.gradient_async(mode, q0, J, g)
+        e1.record()
+        torch.cuda.synchronize()
+        b.sync()
+        return float(e0.elapsed_time(e1)), g.cpu().numpy()
+
+    out = {}
+    kry_setting = None
+    for name, mode, ratio in (("paraexp", X.PARAEXP, None), ("paraexp_phases", X.PARAEXP, None),
+                              ("serial", X.SERIAL, None), ("paraexp_krylov_fp64", X.PARAEXP, 1e30)):
+        b = X.Batch()
+        b.set(prob["n"], prob["nu"], c=w["c"], T=w["T"], K=K, P=P)
+        b.set_schedule(0 if name == "paraexp_phases" else 1)
+        if ratio is None:
+            b.set_power(True)
+            if mode == X.PARAEXP:
+                b.autotune(mode, q0, J, g)
+            out[name] = timed(b, mode) + (b.problem_info()[2],)
+        else:
+            # every homogeneous part by the Krylov exponential: the first (m, substep reach)
+            # whose a-posteriori estimates meet the 1e-8 tolerance on every problem
+            b.set_homogeneous(ratio)
+            # (seconds per gradient: the stiff problems need up to ~75 substeps per link, so
+            # it is timed on one step after the trial gradient that checks the estimates)
+            for m, reach in ((48, 0.01), (48, 0.005)):
+                b.set_krylov(m, 1e-8, reach)
+                try:
+                    b.gradient(mode, q0, J, g)
+                except X.PxaError as e:
+                    if e.code != X.ERR_NOT_CONVERGED:
+                        raise
+                    continue
+                kry_setting = {"krylov_m": m, "krylov_reach": reach,
+                               "substeps_max": b.stats()["substeps_max"], "timed_steps": 1}
+                out[name] = timed_once(b, mode) + (b.problem_info()[2],)
+                break
+        b.close()
+    errs = {}
+    if "paraexp_krylov_fp64" not in out:
+        out["paraexp_krylov_fp64"] = (float("nan"), None, None)
+    for name, (_, gh, kry) in out.items():
+        if gh is None:
+            errs[name] = None
+            continue
+        e = []
+        for i in (sample if name != "paraexp_krylov_fp64" else sample[:4]):
+            q = prob["q0"][off[i]:off[i + 1]]
+            if kry[i]:
+                _, go, _ = O.ad1_cn_gradient_paraexp(q, w["c"], prob["nu"][i], w["T"], K, P, O.PHI_EXP)
+            else:
+                _, go, _ = O.ad1_cn_gradient_serial(q, w["c"], prob["nu"][i], w["T"], K)
+            e.append(rel_err(gh[off[i]:off[i + 1]], go))
+        errs[name] = max(e)
+    tol = 5e-4  # FP32 stepping: 2 K u_32 for K = 4096 (the full-size test's bound)
+    entry = {"workload": w["label"], "paraexp_ms": out["paraexp"][0], "serial_ms": out["serial"][0],
+             "speedup": out["serial"][0] / out["paraexp"][0], "rel_err_paraexp": errs["paraexp"],
+             "rel_err_serial": errs["serial"], "tolerance": tol, "gate": gate_mark(errs["paraexp"], tol),
+             "sample": "8 problems (the 4 largest grids, the 4 stiffest); errors against the FP64 oracle",
+             "paraexp_phases_ms": out["paraexp_phases"][0], "rel_err_paraexp_phases": errs["paraexp_phases"],
+             "schedule": "one persistent launch with device-side dependencies (paraexp_phases_ms: seven launches)",
+             "note": "FP32 stepping; the homogeneous parts use the stepper's own propagator M^(K/P) as one "
+                     "FP32 circulant band per link (not FP64 Krylov); FP64 superposition",
+             "paraexp_krylov_fp64": {"ms": None if kry_setting is None else out["paraexp_krylov_fp64"][0],
+                                     "speedup": None if kry_setting is None else
+                                     out["serial"][0] / out["paraexp_krylov_fp64"][0],
+                                     "rel_err": errs["paraexp_krylov_fp64"], "setting": kry_setting,
+                                     "sample": "the 4 largest grids, against the oracle's Paraexp with exp(tau A)",
+                                     "note": "every homogeneous part by the FP64 Krylov exponential exp(tau A) "
+                                             "(the paper's propagator), FP32 lanes"}}
+    return entry
+
+
+def compare_advdiff2d(args, X, torch, flush):
+    """C3: the hybrid scheme (serial FP32 direct, Paraexp adjoint) against serial stepping
+    of both. The full-size FP64 oracle takes about 700 s on one core, so the entry gives
+    the difference of the two GPU gradients (the tests hold both to the oracle at 64^2)."""
+    w = WORKLOADS["advdiff2d"]
+    ctx, keep = ctx_2d(X, torch, w, w["n"], w["P"], w["K"])
+    res = {}
+    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+        times, _, g = time_mode(X, torch, ctx, mode, args.steps, args.warmup, flush)
+        res[name] = (float(np.mean(times)), g.detach().cpu().numpy())
+    ctx.close()
+    del keep
+    d = rel_err(res["paraexp"][1], res["serial"][1])
+    return {"workload": w["label"], "paraexp_ms": res["paraexp"][0], "serial_ms": res["serial"][0],
+            "speedup": res["serial"][0] / res["paraexp"][0], "rel_err_paraexp": None, "rel_err_serial": None,
+            "rel_diff_paraexp_vs_serial": d, "tolerance": 1e-4, "gate": gate_mark(d, 1e-4),
+            "note": "FP32 stepping, FP64 accumulation; the FP64 oracle at full size is not run here"}
 
 
 def run_ours(args, w, rank, world):
@@ -302,7 +512,8 @@ def run_ours(args, w, rank, world):
         cpu = {"value": 1.0 / dt_cpu, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
                "sample": f"one full serial FP64 gradient of the {w['kind']} workload ({dt_cpu:.2f} s)"}
         for name in variants:
-            variants[name]["rel_err"] = float(np.linalg.norm(grads[name] - g_ref) / np.linalg.norm(g_ref))
+            variants[name]["rel_err"] = rel_err(grads[name], g_ref)
+            variants[name]["gate_1e-8"] = gate_mark(variants[name]["rel_err"])
 
     # the headline: fastest Paraexp variant whose gradient meets rel.err <= 1e-8
     ok = [k for k in variants if k.startswith("paraexp") and variants[k].get("rel_err", 0.0) <= 1e-8]
@@ -365,27 +576,70 @@ def run_ours(args, w, rank, world):
     e2e = {"value": world / float(np.mean(e2e_t)), "unit": "gradient evals/s",
            "h2d_bytes_per_step": 8 * w["n"], "d2h_bytes_per_step": 8 * w["n"] + 8}
 
+    # Paraexp against serial stepping on every workload of the metric, each pair timed the
+    # same way (steps, warm-up, L2 flush); errors against the FP64 oracle
+    comparison = None
+    if w["kind"] == "burgers1d" and not args.no_compare:
+        _, g_ref = oracle_gradient(w, inp) if rank == 0 else (None, None)
+
+        def make_bu(mode):
+            c2 = make_ctx(X, w, X.PHI_STEPPER)
+            c2.set_control(ctl)
+            c2.set_target(tgt)
+            tvv = tuned["paraexp_stepper" if mode == X.PARAEXP else "serial"]
+            c2.set_cluster(*tvv["clusters"])
+            c2.set_groups(*tvv["groups"])
+            c2.set_partition(tvv["partition_r"])
+            return c2
+
+        res = time_pair(X, torch, make_bu, args.steps, args.warmup, flush)
+        comparison = {}
+        if rank == 0:
+            comparison["C2"] = pair_entry(
+                w["label"], res, g_ref, GATE,
+                "hybrid scheme: serial RK4 direct in both modes; the time-varying homogeneous adjoint is "
+                "carried by the stepper's own transposed step maps, so its chain sweeps all K steps like the "
+                "serial adjoint")
+            comparison["C1"] = compare_advdiff1d(args, X, torch, flush)
+            comparison["C3"] = compare_advdiff2d(args, X, torch, flush)
+            comparison["C4"] = compare_batched(args, X, torch, flush)
+
     # roofline of the dominant kernel, from the per-phase CUDA events of the timed steps
     ph = {k: float(np.mean([p[k] for p in phases])) for k in
           ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_prep", "ms_adjoint_inhom",
-           "ms_adjoint_hom", "ms_total")}
+           "ms_adjoint_hom", "ms_total", "ms_side_prepass", "ms_side_pair", "ms_side_quad",
+           "ms_side_lanes")}
+    side_chunks = int(phases[-1]["side_chunks"]) if phases else 0
     st = ctx.stats()
     n, K, P = w["n"], w["K"], w["P"]
     k = K // P
     floors = {}
     if w["kind"] == "burgers1d":
         cl = ctx.cluster_sizes()
+        # the direct: the register-wavefront form runs when a CTA's chunk (n / cluster size)
+        # has at most 744 points, else the shared-memory form
+        direct = "bu1_rk4_wave_kernel" if (n + cl[0] - 1) // cl[0] <= 744 else "bu1_rk4_sweep_kernel"
         kernels = {
             # name: (ms per launch, algorithmic FP64 flop per launch, SMs used, DRAM bytes per launch)
-            "bu1_rk4_sweep_kernel": (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K, cl[0],
-                                     TRAFFIC.get("bu1_rk4_sweep_kernel")),
+            direct: (ph["ms_direct_inhom"], FLOPS_RK4_DIRECT * n * K, cl[0], TRAFFIC.get(direct)),
         }
-        floors["bu1_rk4_sweep_kernel"] = K * FP64_INSTR_RK4_STEP * 64 / SM_CLOCK_HZ * 1e3
-        if st["adjoint_band"]:
+        floors[direct] = K * FP64_INSTR_RK4_STEP * 64 / SM_CLOCK_HZ * 1e3
+        if st["adjoint_band"] and side_chunks > 0:
+            # overlapped with the direct chunks on the side streams: kernel times from
+            # events recorded on those streams, summed over the chunks
+            kernels["bu1_band_prepass_kernel"] = (ph["ms_side_prepass"], FLOPS_BAND_PREPASS * n * (K + 1),
+                                                  SMS, TRAFFIC.get("bu1_band_prepass_kernel"))
+            kernels["bu1_band_pair_kernel + bu1_band_quad_kernel"] = (
+                ph["ms_side_pair"] + ph["ms_side_quad"],
+                (2.0 * 9 * 9 + 18) * n * K / 2 + (2.0 * 17 * 17 + 34) * n * K / 4, SMS, None)
+            kernels["bu1_band_sweep_kernel (lanes)"] = (ph["ms_side_lanes"], FLOPS_BAND_SWEEP * n * (K - k),
+                                                        (P - 1) * cl[1], None)
+        elif st["adjoint_band"]:
             kernels["bu1_band_prepass_kernel"] = (ph["ms_adjoint_prep"], FLOPS_BAND_PREPASS * n * (K + 1),
                                                   SMS, TRAFFIC.get("bu1_band_prepass_kernel"))
             kernels["bu1_band_sweep_kernel (lanes)"] = (ph["ms_adjoint_inhom"], FLOPS_BAND_SWEEP * n * K,
                                                         P * cl[1], None)
+        if st["adjoint_band"]:
             if head == "paraexp_stepper":
                 # the chain phase: bu1_band_chain4_kernel in 4 segments (four-step entries,
                 # 33 taps = 66 flop per point per 4 steps) with the fill of the skipped rows
@@ -407,12 +661,15 @@ def run_ours(args, w, rank, world):
         band_flop = 2.0 * st["prop_band_taps"] * n * (P - 1)
         chain = {"band": ("ad1_band_chain_kernel", band_flop), "relpm": ("ad1_relpm_chain_kernel", None)}.get(
             head.rsplit("_", 1)[-1], ("ad1_chain_kernel", (P - 1) * sub * (arnoldi + dense)))
+        chain_sms = AD1_CHAIN_CLUSTER if chain[0] == "ad1_band_chain_kernel" else 1
         kernels = {
-            chain[0]: (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]), chain[1], 1, TRAFFIC.get(chain[0])),
-            # the lanes apply the band of M^q (lane_band_taps taps) k/q times per lane
+            chain[0]: (0.5 * (ph["ms_direct_hom"] + ph["ms_adjoint_hom"]), chain[1], chain_sms,
+                       TRAFFIC.get(chain[0])),
+            # the lanes apply the band of M^q (lane_band_taps taps) k/q times per lane; each
+            # lane is one cluster of AD1_LANE_CLUSTER CTAs
             "cn_lanes_kernel": (0.5 * (ph["ms_direct_inhom"] + ph["ms_adjoint_inhom"]),
                                 FLOPS_CN_BAND_TAP * st["lane_band_taps"] * n * (k // max(st["lane_steps"], 1)) * P,
-                                P, TRAFFIC.get("cn_lanes_kernel")),
+                                P * AD1_LANE_CLUSTER, TRAFFIC.get("cn_lanes_kernel")),
         }
     dom = max(kernels, key=lambda kk: kernels[kk][0])
     ms_dom, flops, sms_used, traffic = kernels[dom]
@@ -444,6 +701,7 @@ def run_ours(args, w, rank, world):
         "config": {"workload": w["label"], "homogeneous": head, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "variants": variants, "phases_ms": ph, "phases_source": phases_source, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "paraexp_vs_serial": comparison,
         "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
     }
     ctx.close()
@@ -536,9 +794,11 @@ def run_reference_batch(args, w, world):
     per_full = float(np.mean(t)) * cnt / ns
     value = cnt / per_full
     unit = "gradient evals/s (problems x gradients)"
-    sample = f"first {ns} of {cnt} problems per step (serial FP64 CN), scaled by {cnt}/{ns}"
+    sample = (f"scaled sample: each timed step is the first {ns} of {cnt} problems (serial FP64 CN); "
+              f"value = {cnt} / (sample time x {cnt}/{ns})")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(t)) * 1e3,
+            "ms_per_step_kind": "measured time of one sampled step", "ms_per_batch_scaled": per_full * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w["label"]},
             "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
@@ -567,10 +827,11 @@ def run_reference_spmv(args, w, world):
         t.append(time.perf_counter() - t0)
     per_row = (8.0 + 12.0 * 3 + 16.0)  # bytes per row, as the GPU line counts them
     value = per_row * m / float(np.mean(t)) / 1e9
-    sample = f"first {m} of {n} rows per step"
+    sample = f"scaled sample: each timed step is the product of the first {m} of {n} rows"
     return {"impl": "reference", "metric": "HBM GB/s of the CSR sparse matrix-vector product", "value": value,
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": float(np.mean(t)) * 1e3 * n / m, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": float(np.mean(t)) * 1e3, "ms_per_step_kind": "measured time of one sampled step",
+            "ms_per_product_scaled": float(np.mean(t)) * 1e3 * n / m, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": w["label"]},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -602,10 +863,12 @@ def run_reference(args, w, rank, world):
         t.append(time.perf_counter() - t0)
     per_full = float(np.mean(t)) * w["K"] / K_s
     value = 1.0 / per_full
-    sample = f"first {K_s} of {w['K']} time steps (direct + adjoint), scaled by {K_s}/{w['K']}"
+    sample = (f"scaled sample: each timed step is the first {K_s} of {w['K']} time steps (direct + adjoint); "
+              f"value = 1 / (sample time x {w['K']}/{K_s}), the cost being linear in the steps")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "gradient evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": float(np.mean(t)) * 1e3, "ms_per_step_kind": "measured time of one sampled step",
+            "ms_per_gradient_scaled": per_full * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["label"]},
             "cpu_baseline": {"value": value, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
@@ -855,11 +1118,12 @@ def run_batch(args, w, rank, world):
     variants, errs, bats = {}, {}, {}
     # Paraexp with the stepper's subinterval propagator as one band of M^(K/P) (default),
     # Paraexp with K/P CN steps per link instead, and serial stepping
-    for name, mode, power in (("paraexp", X.PARAEXP, True), ("paraexp_stepped_links", X.PARAEXP, False),
-                              ("serial", X.SERIAL, True)):
+    for name, mode, power, sched in (("paraexp", X.PARAEXP, True, 1), ("paraexp_phases", X.PARAEXP, True, 0),
+                                     ("paraexp_stepped_links", X.PARAEXP, False, 1), ("serial", X.SERIAL, True, 1)):
         b = X.Batch()
         b.set(prob["n"], prob["nu"], c=w["c"], T=w["T"], K=K, P=P)
         b.set_power(power)
+        b.set_schedule(sched)
         best = b.autotune(mode, q0, J, g) if mode == X.PARAEXP else None
         with ClockSampler(dev_index) as clk:
             t = timed(b, mode, args.steps, args.warmup)
@@ -881,12 +1145,14 @@ def run_batch(args, w, rank, world):
                           "substeps_max": st["substeps_max"], "lanes_grid": st["lanes_grid"],
                           "band32_max": st["band32_max"], "power_problems": st["power_problems"],
                           "band_power_max": st["band_power_max"], "lane_steps": st["lane_steps"],
+                          "one_launch": st["one_launch"], "flow_grid": st["flow_grid"],
                           "clocks": clk.summary()}
         # kernels per gradient: sources, lanes, superposition, adjoint lanes, gradient, and
         # per direction one chain launch for each kind of homogeneous propagation in use
         kinds = sum(1 for c in (st["krylov_problems"], st["power_problems"],
                                 cnt - st["krylov_problems"] - st["power_problems"]) if c > 0)
-        variants[name]["kernels_per_step"] = 4 if mode == X.SERIAL else 5 + 2 * kinds
+        variants[name]["kernels_per_step"] = (4 if mode == X.SERIAL else 1 if st["one_launch"]
+                                              else 5 + 2 * kinds)
         bats[name] = b
     head = "paraexp"
     ms = variants[head]["ms_per_step"]
@@ -899,7 +1165,7 @@ def run_batch(args, w, rank, world):
     w32, _, _ = bats[head].problem_info()
     q = bats[head].stats()["lane_steps"]
     flop = 2.0 * 2.0 * (K / q) * float(np.sum(np.asarray(prob["n"], dtype=np.float64) * np.asarray(w32)))
-    bp = bats[head]
+    bp = bats["paraexp_phases"]
     bp.set_timing(True)
     lanes_ms = []
     for _ in range(3):
@@ -908,14 +1174,23 @@ def run_batch(args, w, rank, world):
         lanes_ms.append(float(bp.stats()["ms_lanes"]))
     bp.set_timing(False)
     ms_lanes = float(np.median(lanes_ms))
-    achieved = 0.5 * flop / (ms_lanes / 1e3) / 1e12
+    # the method's work: one CN step of every point of every lane, FLOPS_CN_STEP flop per
+    # point and step; the P lanes of a problem take K/P steps each, K steps in all
+    method_flop = FLOPS_CN_STEP * K * float(np.sum(np.asarray(prob["n"], dtype=np.float64)))
+    achieved = method_flop / (ms_lanes / 1e3) / 1e12
+    impl = 0.5 * flop / (ms_lanes / 1e3) / 1e12
     ms_ser = variants["serial"]["ms_per_step"]
     roof = {"bound": "alu", "kernel": "batch_cn_lanes_kernel (Paraexp lanes, one direction)",
             "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
             "peak_kind": "FP32 from unit counts and clocks (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
             "achieved": achieved, "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-            "flop_per_launch": 0.5 * flop, "ms_per_launch": ms_lanes, "cn_steps_per_band": q,
-            "serial_lanes_tflops": flop / (ms_ser / 1e3) / 1e12}
+            "flop_per_launch": method_flop,
+            "flop_kind": f"method flops: {FLOPS_CN_STEP:g} per point per CN step (tridiagonal right-hand side "
+                         "and periodic tridiagonal solve), K steps per problem",
+            "implementation_tflops": impl,
+            "implementation_flop_kind": "2 flop per tap of the band of M^q per point and application",
+            "ms_per_launch": ms_lanes, "cn_steps_per_band": q,
+            "serial_lanes_tflops_implementation": flop / (ms_ser / 1e3) / 1e12}
     # end to end: pinned host q0 -> device, gradient, J and gradient back to pinned host
     qh = torch.as_tensor(prob["q0"]).pin_memory()
     gh = torch.empty(q0.numel(), dtype=torch.float64).pin_memory()
@@ -973,6 +1248,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     if args.once and w["kind"] in ("burgers1d", "advdiff1d"):
+        if args.K:
+            w = dict(w, K=args.K, T=w["T"] * args.K / w["K"])
         line = run_once(args, w)
     elif args.once and w["kind"] == "batched1d":
         line = run_batch_once(args, w)
