@@ -74,6 +74,12 @@ def lib():
                 "pxo_ad2_rk4_step": [_i, _i, _d, _d, _p, _p, _d, _d, _d, _p, _p, _p],
                 "pxo_ad2_gradient_serial": [_i, _i, _d, _d, _p, _p, _d, _i64, _d, _p, _p, _p, _p],
                 "pxo_csr_transpose": [_i64, _p, _p, _p, _p, _p, _p],
+                "pxo_bu2_rhs": [_i, _d, _d, _p, _p, _p, _p],
+                "pxo_bu2_jac": [_i, _d, _d, _p, _p, _p, _p, _p, _p],
+                "pxo_bu2_jac_T": [_i, _d, _d, _p, _p, _p, _p, _p, _p],
+                "pxo_bu2_rk4_step": [_i, _d, _d, _d, _p, _p, _p, _p],
+                "pxo_bu2_direct": [_i, _d, _d, _d, _i64, _p, _p, _p, _p],
+                "pxo_bu2_gradient_serial": [_i, _d, _d, _d, _i64, _p, _p, _p, _p, _p, _p, _p],
                 "pxo_csr_rk4_step": [_i64, _p, _p, _p, _d, _p, _p, _p],
                 "pxo_csr_gradient_serial": [_i64, _p, _p, _p, _d, _i64, _p, _p, _p, _p, _p],
                 "pxo_csr_gradient_paraexp": [_i64, _p, _p, _p, _d, _i64, _i, _i, _p, _p, _p, _p, _p],
@@ -362,3 +368,49 @@ def csr_gradient_paraexp(rp, col, val, q0, T, K, P, phi_mode, g=None):
                                           int(phi_mode), _ptr(q0), _ptr(ga), ctypes.byref(J), _ptr(grad),
                                           _ptr(qT)), "csr_paraexp")
     return J.value, grad, qT
+
+
+# ---- 2D viscous Burgers (fields shaped (n, n), x fastest) ------------------------------
+def _sq(a):
+    a = _in(a)
+    assert a.ndim == 2 and a.shape[0] == a.shape[1]
+    return a
+
+
+def bu2_rhs(U, V, nu, L=TWO_PI):
+    U, V = _sq(U), _sq(V)
+    oU, oV = np.empty_like(U), np.empty_like(V)
+    _check(lib().pxo_bu2_rhs(U.shape[0], L, nu, _ptr(U), _ptr(V), _ptr(oU), _ptr(oV)), "bu2_rhs")
+    return oU, oV
+
+
+def bu2_jac(U, V, W1, W2, nu, L=TWO_PI, transpose=False):
+    U, V, W1, W2 = _sq(U), _sq(V), _sq(W1), _sq(W2)
+    o1, o2 = np.empty_like(U), np.empty_like(V)
+    fn = lib().pxo_bu2_jac_T if transpose else lib().pxo_bu2_jac
+    _check(fn(U.shape[0], L, nu, _ptr(U), _ptr(V), _ptr(W1), _ptr(W2), _ptr(o1), _ptr(o2)), "bu2_jac")
+    return o1, o2
+
+
+def bu2_rk4_step(U, V, nu, dt, L=TWO_PI):
+    U, V = _sq(U), _sq(V)
+    oU, oV = np.empty_like(U), np.empty_like(V)
+    _check(lib().pxo_bu2_rk4_step(U.shape[0], L, nu, dt, _ptr(U), _ptr(V), _ptr(oU), _ptr(oV)), "bu2_rk4_step")
+    return oU, oV
+
+
+def bu2_direct(U0, V0, nu, T, K, L=TWO_PI):
+    U0, V0 = _sq(U0), _sq(V0)
+    UT, VT = np.empty_like(U0), np.empty_like(V0)
+    _check(lib().pxo_bu2_direct(U0.shape[0], L, nu, T, int(K), _ptr(U0), _ptr(V0), _ptr(UT), _ptr(VT)), "bu2_direct")
+    return UT, VT
+
+
+def bu2_gradient_serial(U0, V0, Ut, Vt, nu, T, K, L=TWO_PI):
+    U0, V0, Ut, Vt = _sq(U0), _sq(V0), _sq(Ut), _sq(Vt)
+    J = ctypes.c_double()
+    gU, gV = np.empty_like(U0), np.empty_like(V0)
+    rc = lib().pxo_bu2_gradient_serial(U0.shape[0], L, nu, T, int(K), _ptr(U0), _ptr(V0), _ptr(Ut), _ptr(Vt),
+                                       ctypes.byref(J), _ptr(gU), _ptr(gV))
+    _check(rc, "bu2_gradient_serial")
+    return J.value, gU, gV

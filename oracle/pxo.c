@@ -1485,3 +1485,248 @@ int pxo_csr_gradient_paraexp(int64_t n, const int64_t* rp, const int32_t* col, c
   free(lamT);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* 2D viscous Burgers (Sec. 4.3): the vector field (u, v) on an n x n periodic grid   */
+/* (arrays [n][n], row = y, x fastest, h = L / n), advective central differences:    */
+/*   N_u = -u u_x - v u_y + nu lap u,   N_v = -u v_x - v v_y + nu lap v,              */
+/* classical RK4, control = the initial state, J = 0.5 ||q(T) - q_target||^2.        */
+/* ------------------------------------------------------------------------- */
+#define B2(a, i, j) (a)[(size_t)(((i) + n) % n) * n + (size_t)(((j) + n) % n)]
+
+static double dxc(const double* a, int n, int i, int j, double h) { return (B2(a, i, j + 1) - B2(a, i, j - 1)) / (2.0 * h); }
+static double dyc(const double* a, int n, int i, int j, double h) { return (B2(a, i + 1, j) - B2(a, i - 1, j)) / (2.0 * h); }
+static double lap(const double* a, int n, int i, int j, double h) {
+  return (B2(a, i, j + 1) + B2(a, i, j - 1) + B2(a, i + 1, j) + B2(a, i - 1, j) - 4.0 * B2(a, i, j)) / (h * h);
+}
+
+int pxo_bu2_rhs(int n, double L, double nu, const double* U, const double* V, double* oU, double* oV) {
+  if (n < 3 || !(L > 0.0) || !U || !V || !oU || !oV) return -1;
+  const double h = L / n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double u = B2(U, i, j), v = B2(V, i, j);
+      oU[(size_t)i * n + j] = -u * dxc(U, n, i, j, h) - v * dyc(U, n, i, j, h) + nu * lap(U, n, i, j, h);
+      oV[(size_t)i * n + j] = -u * dxc(V, n, i, j, h) - v * dyc(V, n, i, j, h) + nu * lap(V, n, i, j, h);
+    }
+  return 0;
+}
+
+/* Linearisation about (U, V) in the direction (W1, W2) (the linearised Burgers operator
+ * of Sec. 4.3): J_u = -W1 U_x - U W1_x - W2 U_y - V W1_y + nu lap W1,
+ *                J_v = -W1 V_x - U W2_x - W2 V_y - V W2_y + nu lap W2. */
+int pxo_bu2_jac(int n, double L, double nu, const double* U, const double* V, const double* W1, const double* W2,
+                double* o1, double* o2) {
+  if (n < 3 || !(L > 0.0) || !U || !V || !W1 || !W2 || !o1 || !o2) return -1;
+  const double h = L / n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double u = B2(U, i, j), v = B2(V, i, j), w1 = B2(W1, i, j), w2 = B2(W2, i, j);
+      o1[(size_t)i * n + j] = -w1 * dxc(U, n, i, j, h) - u * dxc(W1, n, i, j, h) - w2 * dyc(U, n, i, j, h) -
+                              v * dyc(W1, n, i, j, h) + nu * lap(W1, n, i, j, h);
+      o2[(size_t)i * n + j] = -w1 * dxc(V, n, i, j, h) - u * dxc(W2, n, i, j, h) - w2 * dyc(V, n, i, j, h) -
+                              v * dyc(W2, n, i, j, h) + nu * lap(W2, n, i, j, h);
+    }
+  return 0;
+}
+
+/* Transpose of the linearisation, term by term: a pointwise factor c (as in -W1 U_x)
+ * stays pointwise (-U_x Z1); a factor a in front of a central difference D (as in
+ * -U W1_x) becomes D(a Z), since D^T = -D on the periodic grid; the 5-point Laplacian
+ * is symmetric:
+ *   (J^T Z)_1 = -U_x Z1 + D_x(U Z1) + D_y(V Z1) + nu lap Z1 - V_x Z2,
+ *   (J^T Z)_2 = -U_y Z1 + D_x(U Z2) + D_y(V Z2) + nu lap Z2 - V_y Z2. */
+int pxo_bu2_jac_T(int n, double L, double nu, const double* U, const double* V, const double* Z1, const double* Z2,
+                  double* o1, double* o2) {
+  if (n < 3 || !(L > 0.0) || !U || !V || !Z1 || !Z2 || !o1 || !o2) return -1;
+  const double h = L / n;
+  const size_t nn = (size_t)n * n;
+  double* UZ1 = (double*)malloc(sizeof(double) * nn);
+  double* VZ1 = (double*)malloc(sizeof(double) * nn);
+  double* UZ2 = (double*)malloc(sizeof(double) * nn);
+  double* VZ2 = (double*)malloc(sizeof(double) * nn);
+  for (size_t e = 0; e < nn; ++e) {
+    UZ1[e] = U[e] * Z1[e];
+    VZ1[e] = V[e] * Z1[e];
+    UZ2[e] = U[e] * Z2[e];
+    VZ2[e] = V[e] * Z2[e];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const size_t e = (size_t)i * n + j;
+      o1[e] = -dxc(U, n, i, j, h) * Z1[e] + dxc(UZ1, n, i, j, h) + dyc(VZ1, n, i, j, h) + nu * lap(Z1, n, i, j, h) -
+              dxc(V, n, i, j, h) * Z2[e];
+      o2[e] = -dyc(U, n, i, j, h) * Z1[e] + dxc(UZ2, n, i, j, h) + dyc(VZ2, n, i, j, h) + nu * lap(Z2, n, i, j, h) -
+              dyc(V, n, i, j, h) * Z2[e];
+    }
+  free(UZ1);
+  free(VZ1);
+  free(UZ2);
+  free(VZ2);
+  return 0;
+}
+
+/* One classical RK4 step of dq/dt = N(q), q = (U, V). */
+int pxo_bu2_rk4_step(int n, double L, double nu, double dt, const double* U, const double* V, double* oU,
+                     double* oV) {
+  if (n < 3 || !(L > 0.0) || !U || !V || !oU || !oV) return -1;
+  const size_t nn = (size_t)n * n, nb = sizeof(double) * nn;
+  double* kU = (double*)malloc(nb);
+  double* kV = (double*)malloc(nb);
+  double* aU = (double*)malloc(nb);
+  double* aV = (double*)malloc(nb);
+  double* yU = (double*)malloc(nb);
+  double* yV = (double*)malloc(nb);
+  static const double cst[3] = {0.5, 0.5, 1.0};
+  static const double wgt[4] = {1.0, 2.0, 2.0, 1.0};
+  memcpy(yU, U, nb);
+  memcpy(yV, V, nb);
+  memset(aU, 0, nb);
+  memset(aV, 0, nb);
+  for (int q = 0; q < 4; ++q) {
+    pxo_bu2_rhs(n, L, nu, yU, yV, kU, kV);
+    for (size_t e = 0; e < nn; ++e) {
+      aU[e] += wgt[q] * kU[e];
+      aV[e] += wgt[q] * kV[e];
+    }
+    if (q < 3)
+      for (size_t e = 0; e < nn; ++e) {
+        yU[e] = U[e] + cst[q] * dt * kU[e];
+        yV[e] = V[e] + cst[q] * dt * kV[e];
+      }
+  }
+  for (size_t e = 0; e < nn; ++e) {
+    oU[e] = U[e] + dt / 6.0 * aU[e];
+    oV[e] = V[e] + dt / 6.0 * aV[e];
+  }
+  free(kU);
+  free(kV);
+  free(aU);
+  free(aV);
+  free(yU);
+  free(yV);
+  return 0;
+}
+
+/* Reverse sweep of one RK4 step taken at (U, V): given lam = dJ/dq_{s+1} (l1, l2), adds
+ * M_s^T lam to (o1, o2) (which must hold lam on entry): the stage states are recomputed
+ * and their transposed Jacobians applied in reverse order. */
+static void bu2_rk4_adjoint_step(int n, double L, double nu, double dt, const double* U, const double* V,
+                                 const double* l1, const double* l2, double* o1, double* o2) {
+  const size_t nn = (size_t)n * n, nb = sizeof(double) * nn;
+  double *Y1[4], *Y2[4];
+  for (int q = 0; q < 4; ++q) {
+    Y1[q] = (double*)malloc(nb);
+    Y2[q] = (double*)malloc(nb);
+  }
+  double* kU = (double*)malloc(nb);
+  double* kV = (double*)malloc(nb);
+  double* m1 = (double*)malloc(nb);
+  double* m2 = (double*)malloc(nb);
+  double* n1 = (double*)malloc(nb);
+  double* n2 = (double*)malloc(nb);
+  static const double cst[3] = {0.5, 0.5, 1.0};
+  memcpy(Y1[0], U, nb);
+  memcpy(Y2[0], V, nb);
+  for (int q = 0; q < 3; ++q) {
+    pxo_bu2_rhs(n, L, nu, Y1[q], Y2[q], kU, kV);
+    for (size_t e = 0; e < nn; ++e) {
+      Y1[q + 1][e] = U[e] + cst[q] * dt * kU[e];
+      Y2[q + 1][e] = V[e] + cst[q] * dt * kV[e];
+    }
+  }
+  /* kbar4 = dt/6 lam; Ybar4 = J(Y4)^T kbar4; kbar3 = dt/3 lam + dt Ybar4; ...
+   * kbar_q = b_q dt lam + c_q dt Ybar_{q+1}; q(U) receives every Ybar_q */
+  static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (size_t e = 0; e < nn; ++e) {
+    n1[e] = 0.0;
+    n2[e] = 0.0;
+  }
+  for (int q = 3; q >= 0; --q) {
+    const double c = q < 3 ? cst[q] : 0.0; /* Y_{q+1} = U + c_q dt k_q */
+    for (size_t e = 0; e < nn; ++e) {
+      m1[e] = bw[q] * dt * l1[e] + c * dt * n1[e];
+      m2[e] = bw[q] * dt * l2[e] + c * dt * n2[e];
+    }
+    pxo_bu2_jac_T(n, L, nu, Y1[q], Y2[q], m1, m2, n1, n2); /* Ybar_q */
+    for (size_t e = 0; e < nn; ++e) {
+      o1[e] += n1[e];
+      o2[e] += n2[e];
+    }
+  }
+  for (int q = 0; q < 4; ++q) {
+    free(Y1[q]);
+    free(Y2[q]);
+  }
+  free(kU);
+  free(kV);
+  free(m1);
+  free(m2);
+  free(n1);
+  free(n2);
+}
+
+/* q(T) after K RK4 steps from (U0, V0). */
+int pxo_bu2_direct(int n, double L, double nu, double T, int64_t K, const double* U0, const double* V0, double* UT,
+                   double* VT) {
+  if (n < 3 || !(L > 0.0) || !(T > 0.0) || K < 1 || !U0 || !V0 || !UT || !VT) return -1;
+  const size_t nb = sizeof(double) * (size_t)n * n;
+  double* a = (double*)malloc(nb);
+  double* b = (double*)malloc(nb);
+  memcpy(UT, U0, nb);
+  memcpy(VT, V0, nb);
+  for (int64_t s = 0; s < K; ++s) {
+    pxo_bu2_rk4_step(n, L, nu, T / (double)K, UT, VT, a, b);
+    memcpy(UT, a, nb);
+    memcpy(VT, b, nb);
+  }
+  free(a);
+  free(b);
+  return 0;
+}
+
+/* Serial stepping (the plain definition): K RK4 steps from (U0, V0) keeping every state,
+ * J = 0.5 ||q(T) - q_target||^2, lam(T) = q(T) - q_target, the reverse sweep of every
+ * step, grad = lam(0) (initial-condition control, Eq. initupdate). */
+int pxo_bu2_gradient_serial(int n, double L, double nu, double T, int64_t K, const double* U0, const double* V0,
+                            const double* Ut, const double* Vt, double* J, double* gU, double* gV) {
+  if (n < 3 || !(L > 0.0) || !(T > 0.0) || K < 1 || !U0 || !V0 || !Ut || !Vt || !J || !gU || !gV) return -1;
+  const size_t nn = (size_t)n * n, nb = sizeof(double) * nn;
+  const double dt = T / (double)K;
+  double* tr = (double*)malloc(nb * 2 * (size_t)(K + 1));
+  if (!tr) return -2;
+  memcpy(tr, U0, nb);
+  memcpy(tr + nn, V0, nb);
+  for (int64_t s = 0; s < K; ++s)
+    pxo_bu2_rk4_step(n, L, nu, dt, tr + 2 * nn * s, tr + 2 * nn * s + nn, tr + 2 * nn * (s + 1),
+                     tr + 2 * nn * (s + 1) + nn);
+  const double* qU = tr + 2 * nn * K;
+  const double* qV = qU + nn;
+  double acc = 0.0;
+  double* l1 = (double*)malloc(nb);
+  double* l2 = (double*)malloc(nb);
+  double* o1 = (double*)malloc(nb);
+  double* o2 = (double*)malloc(nb);
+  for (size_t e = 0; e < nn; ++e) {
+    l1[e] = qU[e] - Ut[e];
+    l2[e] = qV[e] - Vt[e];
+    acc += l1[e] * l1[e] + l2[e] * l2[e];
+  }
+  *J = 0.5 * acc;
+  for (int64_t s = K - 1; s >= 0; --s) {
+    memcpy(o1, l1, nb);
+    memcpy(o2, l2, nb);
+    bu2_rk4_adjoint_step(n, L, nu, dt, tr + 2 * nn * s, tr + 2 * nn * s + nn, l1, l2, o1, o2);
+    memcpy(l1, o1, nb);
+    memcpy(l2, o2, nb);
+  }
+  memcpy(gU, l1, nb);
+  memcpy(gV, l2, nb);
+  free(tr);
+  free(l1);
+  free(l2);
+  free(o1);
+  free(o2);
+  return 0;
+}
+#undef B2

@@ -169,6 +169,20 @@ int pxo_csr_gradient_paraexp(int64_t n, const int64_t* rp, const int32_t* col, c
                              int64_t K, int P, int phi_mode, const double* q0, const double* g, double* J,
                              double* grad, double* qT);
 
+/* 2D viscous Burgers on an n x n periodic grid (arrays [n][n], x fastest), RK4, control =
+ * the initial state, J = 0.5 ||q(T) - q_target||^2. */
+int pxo_bu2_rhs(int n, double L, double nu, const double* U, const double* V, double* oU, double* oV);
+int pxo_bu2_jac(int n, double L, double nu, const double* U, const double* V, const double* W1, const double* W2,
+                double* o1, double* o2);
+int pxo_bu2_jac_T(int n, double L, double nu, const double* U, const double* V, const double* Z1, const double* Z2,
+                  double* o1, double* o2);
+int pxo_bu2_rk4_step(int n, double L, double nu, double dt, const double* U, const double* V, double* oU,
+                     double* oV);
+int pxo_bu2_direct(int n, double L, double nu, double T, int64_t K, const double* U0, const double* V0, double* UT,
+                   double* VT);
+int pxo_bu2_gradient_serial(int n, double L, double nu, double T, int64_t K, const double* U0, const double* V0,
+                            const double* Ut, const double* Vt, double* J, double* gU, double* gV);
+
 #ifdef __cplusplus
 }
 #endif
