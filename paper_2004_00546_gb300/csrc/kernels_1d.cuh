@@ -85,6 +85,12 @@ bool bu1_rk4_valid_cluster(int n, int C);
 cudaError_t launch_nl_iteration(cudaStream_t st, int n, int64_t K, int P, double L, double nu, double dt,
                                 const double* f, const double* sc, const double* Q, double* Qn, double* V,
                                 double* qbar, double* change);
+// The tracking objective from stored trajectory rows: Jrow[s] = ||u_s - g||^2 for s in
+// [s0, s1), then J = scale * sum_{s=1..K} Jrow[s] in a fixed order.
+cudaError_t launch_bu1_objective_rows(cudaStream_t st, const double* traj, const double* g, int n, int64_t s0,
+                                      int64_t s1, double* Jrow, int priority);
+cudaError_t launch_bu1_objective_sum(cudaStream_t st, const double* Jrow, int64_t K, double scale, double* Jdev,
+                                     int* status);
 // One block waiting on an mbarrier that nothing completes (the bounded wait's failure path).
 cudaError_t launch_wait_probe(cudaStream_t st, int* status);
 cudaError_t launch_bu1_forcing_table(cudaStream_t st, int64_t K, double dt, double omega, double* sc);

@@ -415,55 +415,73 @@ __global__ void bu1_rk4_wave_kernel(int n, double b, double a, double dt, int k,
   uint32_t ph0 = 0u, ph1 = 0u;
   double jp = 0.0;
   const unsigned FULL = 0xffffffffu;
-  for (int j = 0; j < k; ++j) {
-    double n1 = 1.0, n2 = 1.0, n4 = 1.0;
-    if (FORCED && j + 1 < k) {
-      n1 = scp[0];
-      n2 = scp[1];
-      n4 = scp[2];
-      scp += 3;
-    }
-    const double cf1 = FORCED ? c1 * fp : fp, cf2 = FORCED ? c2 * fp : fp, cf4 = FORCED ? c4 * fp : fp;
-    // stage 1
-    double ym = __shfl_up_sync(FULL, u, 1), yp = __shfl_down_sync(FULL, u, 1);
-    double kk = stage_k(b, a, a2, ym, u, yp, cf1);
-    double acc = kk;
-    double y = fma(h2, kk, u);
-    // stage 2
-    ym = __shfl_up_sync(FULL, y, 1);
-    yp = __shfl_down_sync(FULL, y, 1);
-    kk = stage_k(b, a, a2, ym, y, yp, cf2);
-    acc = fma(2.0, kk, acc);
-    y = fma(h2, kk, u);
-    // stage 3
-    ym = __shfl_up_sync(FULL, y, 1);
-    yp = __shfl_down_sync(FULL, y, 1);
-    kk = stage_k(b, a, a2, ym, y, yp, cf2);
-    acc = fma(2.0, kk, acc);
-    y = fma(dt, kk, u);
-    // stage 4
-    ym = __shfl_up_sync(FULL, y, 1);
-    yp = __shfl_down_sync(FULL, y, 1);
-    kk = stage_k(b, a, a2, ym, y, yp, cf4);
-    const double un = fma(dt6, acc + kk, u);
-    if (FORCED) {
-      c1 = n1;
-      c2 = n2;
-      c4 = n4;
-    }
-    const bool group_end = ((j + 1) % Q == 0) && (j + 1 < k);
-    const int gx = (j / Q) & 1;  // group parity
-    if (group_end) {
-      if (multi) {
-        if (to_left) st_async_f64(gx ? rl1 : rl0, un, gx ? bl1 : bl0);
-        if (to_right) st_async_f64(gx ? rr1 : rr0, un, gx ? br1 : br0);
-      } else {
-        if (to_left) rb[(2 * gx + 1) * HQ + p] = un;
-        if (to_right) rb[(2 * gx + 0) * HQ + (p - (cnt - HQ))] = un;
+  // per-thread constants of the step's exchanges, hoisted out of the loop
+  const bool put_lo = ln >= 4 && ln < 8, put_hi = ln >= 24 && ln < 28;
+  // (indices of lanes that do not access are set to 0: every address stays in bounds)
+  const int put_at = put_lo ? warp * 8 + (ln - 4) : put_hi ? warp * 8 + 4 + (ln - 24) : 0;
+  const bool get_lo = ln < 4 && warp > 0, get_hi = ln >= 28 && warp < W - 1;
+  const int get_at = get_lo ? (warp - 1) * 8 + 4 + ln : get_hi ? (warp + 1) * 8 + (ln - 28) : 0;
+  const bool halo_l = in_left >= 0 && in_left < HQ, halo_r = in_right >= 0 && in_right < HQ;
+  const int halo_at = halo_l ? in_left : halo_r ? HQ + in_right : 0;  // within rb[2 gx .. 2 gx + 1]
+  const bool with_j = Jdev != nullptr && own;
+  const bool with_ck = ckpt != nullptr;
+  int j = 0;  // steps done
+  for (int grp = 0; grp < groups; ++grp) {
+    const bool more = grp + 1 < groups;
+    const int steps_here = min(Q, k - grp * Q);
+    const int gx = grp & 1;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      if (m >= steps_here) break;  // the last group may be shorter (uniform)
+      double n1 = 1.0, n2 = 1.0, n4 = 1.0;
+      if (FORCED && j + 1 < k) {
+        n1 = scp[0];
+        n2 = scp[1];
+        n4 = scp[2];
+        scp += 3;
       }
-    }
-    if (own) {
-      if (Jdev) {
+      const double cf1 = FORCED ? c1 * fp : fp, cf2 = FORCED ? c2 * fp : fp, cf4 = FORCED ? c4 * fp : fp;
+      // stage 1
+      double ym = __shfl_up_sync(FULL, u, 1), yp = __shfl_down_sync(FULL, u, 1);
+      double kk = stage_k(b, a, a2, ym, u, yp, cf1);
+      double acc = kk;
+      double y = fma(h2, kk, u);
+      // stage 2
+      ym = __shfl_up_sync(FULL, y, 1);
+      yp = __shfl_down_sync(FULL, y, 1);
+      kk = stage_k(b, a, a2, ym, y, yp, cf2);
+      acc = fma(2.0, kk, acc);
+      y = fma(h2, kk, u);
+      // stage 3
+      ym = __shfl_up_sync(FULL, y, 1);
+      yp = __shfl_down_sync(FULL, y, 1);
+      kk = stage_k(b, a, a2, ym, y, yp, cf2);
+      acc = fma(2.0, kk, acc);
+      y = fma(dt, kk, u);
+      // stage 4
+      ym = __shfl_up_sync(FULL, y, 1);
+      yp = __shfl_down_sync(FULL, y, 1);
+      kk = stage_k(b, a, a2, ym, y, yp, cf4);
+      const double un = fma(dt6, acc + kk, u);
+      if (FORCED) {
+        c1 = n1;
+        c2 = n2;
+        c4 = n4;
+      }
+      const bool group_end = more && m == Q - 1;  // compile-time m; `more` uniform
+      if (group_end) {
+        if (multi) {
+          if (to_left) st_async_f64(gx ? rl1 : rl0, un, gx ? bl1 : bl0);
+          if (to_right) st_async_f64(gx ? rr1 : rr0, un, gx ? br1 : br0);
+        } else {
+          if (to_left) rb[(2 * gx + 1) * HQ + p] = un;
+          if (to_right) rb[(2 * gx + 0) * HQ + (p - (cnt - HQ))] = un;
+        }
+      }
+      // pass the first and last valid values to the adjacent warps (parity of step j)
+      double* const xs = xb + (size_t)((Q % 2 == 0 ? m : grp * Q + m) & 1) * W * 8;
+      if (put_lo || put_hi) xs[put_at] = un;
+      if (with_j) {
         const double d = un - gp;
         jp = fma(d, d, jp);
       }
@@ -471,34 +489,28 @@ __global__ void bu1_rk4_wave_kernel(int n, double b, double a, double dt, int k,
         *orow = un;
         orow += n;
       }
-      if (ckpt && ck_left == 1) ckpt[(size_t)ck_row * n + start + p] = un;
-    }
-    if (ckpt) {
-      if (ck_left == 1) {
-        ck_left = ck_every;
-        ++ck_row;
-      } else {
-        --ck_left;
+      if (with_ck) {
+        if (own && ck_left == 1) ckpt[(size_t)ck_row * n + start + p] = un;
+        if (ck_left == 1) {
+          ck_left = ck_every;
+          ++ck_row;
+        } else {
+          --ck_left;
+        }
       }
-    }
-    // pass the first and last valid values to the adjacent warps
-    double* const xs = xb + (size_t)(j & 1) * W * 8;
-    if (ln >= 4 && ln < 8) xs[warp * 8 + (ln - 4)] = un;
-    if (ln >= 24 && ln < 28) xs[warp * 8 + 4 + (ln - 24)] = un;
-    if (group_end && multi) {
-      mbar_wait_bounded(&bar[gx], gx ? ph1 : ph0, status);
-      if (gx) ph1 ^= 1u; else ph0 ^= 1u;
-    }
-    __syncthreads();
-    u = un;
-    if (ln < 4 && warp > 0) u = xs[(warp - 1) * 8 + 4 + ln];
-    if (ln >= 28 && warp < W - 1) u = xs[(warp + 1) * 8 + (ln - 28)];
-    if (group_end) {
-      if (in_left >= 0 && in_left < HQ) u = rb[(2 * gx + 0) * HQ + in_left];
-      if (in_right >= 0 && in_right < HQ) u = rb[(2 * gx + 1) * HQ + in_right];
-      // re-arm this parity's barrier for the exchange two groups on (every thread has
-      // passed its wait of this phase: the block barrier above)
-      if (multi && threadIdx.x == 0 && j / Q + 3 < groups) mbar_arm(&bar[gx], 2 * HQ * (int)sizeof(double));
+      if (group_end && multi) {
+        mbar_wait_bounded(&bar[gx], gx ? ph1 : ph0, status);
+        if (gx) ph1 ^= 1u; else ph0 ^= 1u;
+      }
+      __syncthreads();
+      u = (get_lo || get_hi) ? xs[get_at] : un;
+      if (group_end) {
+        if (halo_l || halo_r) u = rb[2 * gx * HQ + halo_at];
+        // re-arm this parity's barrier for the exchange two groups on (every thread has
+        // passed its wait of this phase: the block barrier above)
+        if (multi && threadIdx.x == 0 && grp + 3 < groups) mbar_arm(&bar[gx], 2 * HQ * (int)sizeof(double));
+      }
+      ++j;
     }
   }
   if (Jdev) {
@@ -579,6 +591,63 @@ __global__ void sum_parts_kernel(int count, const double* __restrict__ parts, do
   for (int i = 0; i < count; ++i) s += parts[i];
   *out = s;
   if (!isfinite(s)) set_status(status, PXA_ERR_NONFINITE);
+}
+
+// The tracking objective from stored rows (Eq. cost, rectangle rule): one warp per row s
+// in [s0, s1) writes Jrow[s] = sum_i (u_s,i - g_i)^2 (lane-strided sums, then a fixed
+// shuffle tree: deterministic). With every row of the trajectory stored this takes the
+// objective's two FP64 instructions per point and step off the serial direct's path.
+__global__ void bu1_objective_rows_kernel(const double* __restrict__ traj, const double* __restrict__ g, int n,
+                                          int64_t s0, int64_t s1, double* __restrict__ Jrow) {
+  const int64_t s = s0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int ln = threadIdx.x & 31;
+  if (s >= s1) return;
+  const double* row = traj + (size_t)s * n;
+  double acc = 0.0;
+  for (int i = ln; i < n; i += 32) {
+    const double d = row[i] - g[i];
+    acc = fma(d, d, acc);
+  }
+  acc = warp_sum(acc);
+  if (ln == 0) Jrow[s] = acc;
+}
+
+// J = scale * sum_{s=1..K} Jrow[s]: each thread sums a contiguous run of rows, then a
+// fixed block tree (the order does not depend on how the rows were produced).
+__global__ void bu1_objective_sum_kernel(const double* __restrict__ Jrow, int64_t K, double scale,
+                                         double* __restrict__ Jdev, int* status) {
+  __shared__ double red[40];
+  const int64_t per = (K + blockDim.x - 1) / blockDim.x;
+  const int64_t a = 1 + (int64_t)threadIdx.x * per, b = min(K + 1, a + per);
+  double acc = 0.0;
+  for (int64_t s = a; s < b; ++s) acc += Jrow[s];
+  const double J = scale * block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    *Jdev = J;
+    if (!isfinite(J)) set_status(status, PXA_ERR_NONFINITE);
+  }
+}
+
+cudaError_t launch_bu1_objective_rows(cudaStream_t st, const double* traj, const double* g, int n, int64_t s0,
+                                      int64_t s1, double* Jrow, int priority) {
+  if (s1 <= s0) return cudaSuccess;
+  const int64_t blocks = (s1 - s0 + 7) / 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bu1_objective_rows_kernel, traj, g, n, s0, s1, Jrow);
+}
+
+cudaError_t launch_bu1_objective_sum(cudaStream_t st, const double* Jrow, int64_t K, double scale, double* Jdev,
+                                     int* status) {
+  bu1_objective_sum_kernel<<<1, 256, 0, st>>>(Jrow, K, scale, Jdev, status);
+  return cudaGetLastError();
 }
 
 // The failure path of the bounded waits, for tests: one thread block waits on an
