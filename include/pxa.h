@@ -42,6 +42,16 @@
  *                   parts are carried by the exact transposed RK4 step maps (banded,
  *                   several steps per halo exchange; PXA_PHI_STEPPER, the default) or
  *                   by 4th-order Magnus steps with Krylov exponentials (PXA_PHI_EXP).
+ *   PXA_BURGERS_2D: dq/dt = N(q), q = (u, v) on a periodic nx x nx grid,
+ *                   N_u = -u u_x - v u_y + nu lap u, N_v = -u v_x - v v_y + nu lap v by
+ *                   central differences (Sec. 4.3); classical RK4 in FP32; control = q(0)
+ *                   (n = 2 nx nx values, u then v, each [ny][nx] row-major); objective
+ *                   J = 0.5 ||q(T) - q_target||^2 (FP64), q_target from pxa_set_target
+ *                   (the target final state, n values). Serial direct + the hybrid
+ *                   adjoint (Sec. 3.3): with a terminal objective the adjoint's
+ *                   inhomogeneous problems vanish and the Paraexp adjoint is the serial
+ *                   adjoint (the exact transposed RK4 step maps), so both modes run the
+ *                   same kernels.
  *   PXA_CSR:        dq/dt = A q for a constant sparse matrix A given in CSR form (any
  *                   discretised operator, Sec. 2), classical RK4; control = q(0);
  *                   objective J = 0.5 ||q(T) - g||^2 (g from pxa_set_objective or
@@ -90,7 +100,7 @@ typedef enum {
   PXA_ERR_TOO_LARGE = -8       /* request exceeds the fixed buffer of pxa_expv_static */
 } pxa_status;
 
-typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2, PXA_ADVDIFF_2D = 3, PXA_CSR = 4 } pxa_problem;
+typedef enum { PXA_ADVDIFF_1D = 1, PXA_BURGERS_1D = 2, PXA_ADVDIFF_2D = 3, PXA_CSR = 4, PXA_BURGERS_2D = 5 } pxa_problem;
 typedef enum { PXA_CN = 1, PXA_RK4 = 2 } pxa_stepper;
 /* Homogeneous propagator. EXP: exp(t A) (the paper's choice). STEPPER: the stepper's
  * own amplification R(dt A)^k (R_CN(z) = (1+z/2)/(1-z/2)), which makes Paraexp
@@ -134,7 +144,8 @@ typedef struct {
   double L;   /* domain length (> 0), h = L / n (2D: L / nx on both axes) */
   double c;   /* advection speed (PXA_ADVDIFF_1D) */
   double nu;  /* diffusion coefficient (>= 0) */
-  int nx, ny; /* PXA_ADVDIFF_2D: grid, nx == ny, nx % 4 == 0, 8 <= nx <= 8192 */
+  int nx, ny; /* PXA_ADVDIFF_2D: grid, nx == ny, nx % 4 == 0, 8 <= nx <= 8192;
+                 PXA_BURGERS_2D: nx == ny, nx % 16 == 0, 16 <= nx <= 4096 */
   const double* u_dev; /* PXA_ADVDIFF_2D: velocity components (device, [ny][nx] row-major, */
   const double* v_dev; /*   x fastest), borrowed until the next set_operator */
   /* PXA_CSR: A with n rows (1 <= n <= 16384) in CSR form on the device, borrowed until
@@ -149,7 +160,8 @@ typedef struct {
 } pxa_operator_desc;
 
 /* Objective (Sec. 2, Eq. cost and its terminal form). TERMINAL_L2:
- * J = 0.5 ||q(T) - g||^2 (ADVDIFF_1D, CSR; g = 0 when target_dev is NULL).
+ * J = 0.5 ||q(T) - g||^2 (ADVDIFF_1D, CSR: g = 0 when target_dev is NULL; BURGERS_2D:
+ * target_dev required).
  * INTEGRAL_TRACKING: J = (1/T) sum_{j=1..K} dt ||q_j - g_j||^2, the rectangle rule of
  * Eq. cost, with a static target g (BURGERS_1D; target_dev required) or the trajectory
  * driven by the true forcing f_true = target_dev (ADVDIFF_2D; required). */
@@ -352,6 +364,11 @@ int pxa_sync(pxa_ctx* ctx);
  * runs pxa_gradient and copies the gradient back into grad_host (n doubles). */
 int pxa_gradient_host(pxa_ctx* ctx, int mode, const double* control_host, double* J_host,
                       double* grad_host);
+/* BURGERS_2D building block: the final state q(T) (FP64, n values) of the direct
+ * solve from the initial state ic_dev (n values), e.g. to make a tracking target from a
+ * "true" initial state. Uses the context's trajectory buffer (a later pxa_solve_adjoint
+ * needs a new pxa_solve_direct). Synchronous. */
+int pxa_direct_state(pxa_ctx* ctx, const double* ic_dev, double* state_dev);
 /* Iterative nonlinear Paraexp direct of Alg. 2 (Sec. 3.2, Eq. nonlinTrans, Jacobians,
  * nlHomIter, fullsolIter) for BURGERS_1D (n <= 1024, u(0) = 0, the forcing of
  * pxa_set_control): from the guess q_0(t) (guess_dev, (K+1) x n device rows, or NULL:

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pxa.h"
+#include "kernels_bu2.cuh"
 #include "kernels_csr.cuh"
 #include "kernels_1d.cuh"
 #include "kernels_ad2.cuh"
@@ -319,6 +320,10 @@ struct pxa_ctx {
   int32_t* colT = nullptr;
   double* valT = nullptr;
   double* csr_work = nullptr;  // [P][4][n] lane vectors when they do not fit in shared memory
+  // BURGERS_2D: the FP32 trajectory [(K+1)][2][n][n], the adjoint ping-pong, J partials
+  float* b2traj = nullptr;
+  float* b2lam = nullptr;  // [2][2][n][n]
+  double* b2Jpart = nullptr;
   // Alg. 2 (pxa_nl_paraexp): the iterate, the next iterate, the lanes, qbar, the change
   double *nl_Q = nullptr, *nl_Qn = nullptr, *nl_V = nullptr, *nl_qbar = nullptr, *nl_change = nullptr;
   int memory = PXA_STORE_FULL;
@@ -370,6 +375,7 @@ struct pxa_ctx {
   cudaEvent_t ev_prep[kMaxChunks] = {};
   cudaEvent_t ev_join = nullptr, ev_join2 = nullptr;
   double* Jparts = nullptr;   // [kMaxChunks] objective of each direct chunk
+  double* Jrow = nullptr;     // [(K+1)] ||u_s - g||^2 per stored row (full storage)
   int prio_hi = 0, prio_lo = 0;
   size_t reserve_smem = 0;    // dynamic shared memory that makes a direct CTA own its SM
   double* rec = nullptr;      // [(K+1)][n][BU1_BAND_RECORD] rows of M_s^T and sources
@@ -506,6 +512,8 @@ void release_workspace(pxa_ctx* c) {
   c->colT = nullptr;
   c->valT = c->csr_work = nullptr;
   c->nl_Q = c->nl_Qn = c->nl_V = c->nl_qbar = c->nl_change = nullptr;
+  c->b2traj = c->b2lam = nullptr;
+  c->b2Jpart = nullptr;
   if (c->inner) {
     pxa_batch_destroy(c->inner);
     c->inner = nullptr;
@@ -514,6 +522,7 @@ void release_workspace(pxa_ctx* c) {
   c->scL_count = 0;
   c->Jpart = c->G2buf = c->GC = nullptr;
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = c->rq = nullptr;
+  c->Jrow = nullptr;
   for (auto& row : c->plans)
     for (auto& pl : row) {
       pl.dev = nullptr;  // freed with the workspace
@@ -609,7 +618,7 @@ int prepare(pxa_ctx* c) {
   if ((rc = alloc(c, &c->ctl_buf, n))) return rc;
   if ((rc = alloc(c, &c->grad_buf, n))) return rc;
   const bool long1d = c->op.kind == PXA_ADVDIFF_1D && n > 4096;  // lanes in global memory only
-  if (c->op.kind != PXA_ADVDIFF_2D && !long1d) {
+  if (c->op.kind != PXA_ADVDIFF_2D && c->op.kind != PXA_BURGERS_2D && !long1d) {
     if ((rc = alloc(c, &c->E, (size_t)P * n))) return rc;
     if ((rc = alloc(c, &c->EA, (size_t)P * n))) return rc;
     if ((rc = alloc(c, &c->src, n))) return rc;
@@ -702,6 +711,12 @@ int prepare(pxa_ctx* c) {
       PXA_CUDA(c, cudaMemcpy(c->relpm_D, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice), "copy");
       PXA_CUDA(c, cudaMemcpy(c->relpm_z, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice), "copy");
     }
+  } else if (c->op.kind == PXA_BURGERS_2D) {
+    const size_t plane2 = 2 * (size_t)c->op.nx * c->op.nx;
+    const int tiles = (c->op.nx / BU2_TILE) * (c->op.nx / BU2_TILE);
+    if ((rc = alloc(c, &c->b2traj, (size_t)(c->K + 1) * plane2))) return rc;
+    if ((rc = alloc(c, &c->b2lam, 2 * plane2))) return rc;
+    if ((rc = alloc(c, &c->b2Jpart, (size_t)tiles))) return rc;
   } else if (c->op.kind == PXA_CSR) {
     // A^T for the adjoint lanes and chain: A is copied to the host once and transposed
     // entry by entry (set-up, not the solve path)
@@ -820,6 +835,7 @@ int prepare(pxa_ctx* c) {
     } else {
       if (c->memory == PXA_STORE_FULL) {
         if ((rc = alloc(c, &c->traj, (size_t)(c->K + 1) * n))) return rc;
+        if ((rc = alloc(c, &c->Jrow, (size_t)(c->K + 1)))) return rc;
       } else {
         if ((rc = alloc(c, &c->traj, (size_t)(P + 1) * n))) return rc;
         if ((rc = alloc(c, &c->scratch, (size_t)P * (size_t)(k + 1) * n))) return rc;
@@ -1236,16 +1252,21 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     int nch = 0;
     for (int ci = 0; ci < NC; ++ci) {
       const int64_t b0 = bounds[ci], b1 = bounds[ci + 1];
+      // every row is stored: the objective is summed from the rows (off the serial path)
       PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, b1 - b0,
                                        c->control, sc ? sc + 3 * b0 : nullptr,
                                        ci == 0 ? nullptr : c->traj + (size_t)b0 * n,
-                                       c->traj + (size_t)b0 * n, 0, c->target, c->T, c->Jparts + ci,
+                                       c->traj + (size_t)b0 * n, 0, nullptr, c->T, nullptr,
                                        nullptr, 1, c->status, c->prio_hi, c->reserve_smem,
                                        c->q_direct),
                "direct chunk");
+      if (!overlap)
+        PXA_CUDA(c, launch_bu1_objective_rows(st, c->traj, c->target, n, b0 + 1, b1 + 1, c->Jrow, 0), "objective");
       if (overlap) {
         PXA_CUDA(c, cudaEventRecord(c->ev_fork[ci], st), "fork");
         PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork[ci], 0), "fork wait");
+        PXA_CUDA(c, launch_bu1_objective_rows(c->side, c->traj, c->target, n, b0 + 1, b1 + 1, c->Jrow, c->prio_lo),
+                 "objective");
         ev_record_on(c, c->ev_side[ci][0], c->side);
         PXA_CUDA(c, launch_bu1_band_prepass(c->side, n, c->op.L, c->op.nu, dt, c->T, c->omega,
                                             c->control, c->target, c->traj, 0, P, ci == 0 ? 0 : b0 + 1,
@@ -1282,14 +1303,17 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       }
       ++nch;
     }
-    PXA_CUDA(c, launch_sum_parts(st, nch, c->Jparts, Jdev, c->status), "J");
+    (void)nch;
     ev_record(c, 1);
+    if (!overlap)
+      PXA_CUDA(c, launch_bu1_objective_sum(st, c->Jrow, K, dt / c->T, Jdev, c->status), "J");
     if (overlap) {
       ev_record(c, 2);
       PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
       PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
       PXA_CUDA(c, cudaEventRecord(c->ev_join2, c->side2), "join");
       PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join2, 0), "join wait");
+      PXA_CUDA(c, launch_bu1_objective_sum(st, c->Jrow, K, dt / c->T, Jdev, c->status), "J");
       if (c->timing && c->ev_ready) {
         ev_record(c, 6);
         c->prep_marked = true;
@@ -1301,8 +1325,13 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     // direct (Eq. seriesDirect) on one cluster; every state (full storage) or the P+1
     // subinterval boundaries (checkpoints) are kept
     PXA_CUDA(c, launch_bu1_rk4_sweep(st, c->cl_rk4_direct, 1, n, c->op.L, c->op.nu, dt, K, c->control,
-                                     sc, nullptr, full ? c->traj : nullptr, 0, c->target, c->T, Jdev,
-                                     full ? nullptr : c->traj, k, c->status, 0, 0, c->q_direct), "direct");
+                                     sc, nullptr, full ? c->traj : nullptr, 0, full ? nullptr : c->target, c->T,
+                                     full ? nullptr : Jdev, full ? nullptr : c->traj, k, c->status, 0, 0,
+                                     c->q_direct), "direct");
+    if (full) {  // the objective from the stored rows, in the same order as the chunked direct
+      PXA_CUDA(c, launch_bu1_objective_rows(st, c->traj, c->target, n, 1, K + 1, c->Jrow, 0), "objective");
+      PXA_CUDA(c, launch_bu1_objective_sum(st, c->Jrow, K, dt / c->T, Jdev, c->status), "J");
+    }
     ev_record(c, 1);
   }
   if (!do_a) return PXA_OK;
@@ -1575,10 +1604,49 @@ int enqueue_csr(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   return PXA_OK;
 }
 
+// ---- 2D viscous Burgers (Sec. 4.3), IC control, terminal objective ----------------------
+// The hybrid scheme (Sec. 3.3): the direct is stepped serially (FP32 RK4, every state kept);
+// with a terminal objective the adjoint's inhomogeneous problems have no source, so they
+// vanish, and the Paraexp adjoint is the one homogeneous problem carried from T by the
+// stepper's own transposed step maps: the serial adjoint. Both modes run the same kernels.
+int enqueue_bu2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
+  (void)mode;
+  cudaStream_t st = c->stream;
+  const int n = c->op.nx;
+  const int64_t K = c->K;
+  const double dt = c->T / (double)K;
+  const size_t plane2 = 2 * (size_t)n * n;
+  float* tr = c->b2traj;
+  if (parts & 1) {
+    ev_record(c, 0);
+    PXA_CUDA(c, launch_bu2_convert(st, c->control, tr, plane2), "initial state");
+    for (int64_t s = 0; s < K; ++s)
+      PXA_CUDA(c, launch_bu2_step(st, tr + (size_t)s * plane2, tr + (size_t)(s + 1) * plane2, n, c->op.L, c->op.nu, dt),
+               "direct step");
+    ev_record(c, 1);
+    ev_record(c, 2);
+    PXA_CUDA(c, launch_bu2_terminal(st, tr + (size_t)K * plane2, c->target, n, c->b2lam, c->b2Jpart, Jdev, c->status),
+             "objective");
+  }
+  if (!(parts & 2)) return PXA_OK;
+  ev_record(c, 3);
+  float* lam[2] = {c->b2lam, c->b2lam + plane2};
+  int cur = 0;
+  for (int64_t s = K - 1; s >= 0; --s) {
+    PXA_CUDA(c, launch_bu2_adj_step(st, tr + (size_t)s * plane2, lam[cur], lam[cur ^ 1], n, c->op.L, c->op.nu, dt),
+             "adjoint step");
+    cur ^= 1;
+  }
+  ev_record(c, 4);
+  PXA_CUDA(c, launch_bu2_convert_back(st, lam[cur], grad, plane2, c->status), "gradient");
+  ev_record(c, 5);
+  return PXA_OK;
+}
+
 // The objective kinds each operator supports (0: the operator's default).
 bool objective_ok(int kind, int obj) {
   if (obj == 0) return true;
-  if (kind == PXA_ADVDIFF_1D || kind == PXA_CSR) return obj == PXA_OBJ_TERMINAL_L2;
+  if (kind == PXA_ADVDIFF_1D || kind == PXA_CSR || kind == PXA_BURGERS_2D) return obj == PXA_OBJ_TERMINAL_L2;
   return obj == PXA_OBJ_INTEGRAL_TRACKING;
 }
 
@@ -1591,6 +1659,10 @@ int enqueue_parts(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (c->op.kind == PXA_ADVDIFF_1D) return enqueue_ad1(c, mode, parts, Jdev, grad);
   if (c->op.kind == PXA_ADVDIFF_2D) return enqueue_ad2(c, mode, parts, Jdev, grad);
   if (c->op.kind == PXA_CSR) return enqueue_csr(c, mode, parts, Jdev, grad);
+  if (c->op.kind == PXA_BURGERS_2D) {
+    if (!c->target) return fail(c, PXA_ERR_STATE, "set_target (the target final state) first");
+    return enqueue_bu2(c, mode, parts, Jdev, grad);
+  }
   return enqueue_bu1(c, mode, parts, Jdev, grad);
 }
 
@@ -1653,10 +1725,21 @@ const char* pxa_last_error(const pxa_ctx* c) { return c ? c->err.c_str() : "null
 int pxa_set_operator(pxa_ctx* c, const pxa_operator_desc* op) {
   if (!c || !op) return PXA_ERR_INVALID;
   if (op->kind != PXA_ADVDIFF_1D && op->kind != PXA_BURGERS_1D && op->kind != PXA_ADVDIFF_2D &&
-      op->kind != PXA_CSR)
+      op->kind != PXA_CSR && op->kind != PXA_BURGERS_2D)
     return fail(c, PXA_ERR_INVALID, "operator kind");
   c->obj_kind = 0;
-  c->step_prec = op->kind == PXA_ADVDIFF_2D ? PXA_F32 : PXA_F64;
+  c->step_prec = (op->kind == PXA_ADVDIFF_2D || op->kind == PXA_BURGERS_2D) ? PXA_F32 : PXA_F64;
+  if (op->kind == PXA_BURGERS_2D) {
+    if (op->nx != op->ny || op->nx % BU2_TILE != 0 || op->nx < BU2_TILE || op->nx > 4096 || !(op->L > 0.0) ||
+        !(op->nu >= 0.0))
+      return fail(c, PXA_ERR_INVALID, "2D Burgers grid (nx == ny, nx % 16 == 0, 16 <= nx <= 4096, L > 0, nu >= 0)");
+    c->op = *op;
+    c->op.n = 2 * op->nx * op->ny;
+    c->have_op = true;
+    release_workspace(c);
+    invalidate(c);
+    return PXA_OK;
+  }
   if (op->kind == PXA_CSR) {
     if (op->n < 1 || op->n > 16384 || !op->row_ptr_dev || !op->col_dev || !op->val_dev)
       return fail(c, PXA_ERR_INVALID, "CSR operator (1 <= n <= 16384, row_ptr, col, val)");
@@ -1699,6 +1782,7 @@ int pxa_set_time(pxa_ctx* c, double T, int64_t K, int stepper, int P) {
   if (c->op.kind == PXA_BURGERS_1D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "BURGERS_1D uses PXA_RK4");
   if (c->op.kind == PXA_ADVDIFF_2D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D uses PXA_RK4");
   if (c->op.kind == PXA_CSR && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "CSR uses PXA_RK4");
+  if (c->op.kind == PXA_BURGERS_2D && stepper != PXA_RK4) return fail(c, PXA_ERR_INVALID, "BURGERS_2D uses PXA_RK4");
   if (c->op.kind == PXA_BURGERS_1D && K < 4) return fail(c, PXA_ERR_INVALID, "K >= 4 for time interpolation");
   c->T = T;
   c->K = K;
@@ -1773,7 +1857,8 @@ int pxa_set_precision(pxa_ctx* c, int prec) {
   if (!c || (prec != PXA_F64 && prec != PXA_F32)) return PXA_ERR_INVALID;
   if (!c->have_op) return fail(c, PXA_ERR_STATE, "set_operator first");
   const int kind = c->op.kind;
-  if (kind == PXA_ADVDIFF_2D && prec != PXA_F32) return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D steps in FP32 only");
+  if ((kind == PXA_ADVDIFF_2D || kind == PXA_BURGERS_2D) && prec != PXA_F32)
+    return fail(c, PXA_ERR_INVALID, "the 2D problems step in FP32 only");
   if ((kind == PXA_BURGERS_1D || kind == PXA_CSR) && prec != PXA_F64)
     return fail(c, PXA_ERR_INVALID, "BURGERS_1D and CSR step in FP64 only");
   if (kind == PXA_ADVDIFF_1D && prec == PXA_F32 && (c->op.n < 16 || c->op.n > 4096))
@@ -2395,6 +2480,27 @@ int pxa_nl_paraexp(pxa_ctx* c, const double* guess_dev, double tol, int max_iter
   if (result == PXA_ERR_NOT_CONVERGED)
     return fail(c, result, "the iteration's change stayed above the tolerance for max_iter iterations");
   return PXA_OK;
+}
+
+int pxa_direct_state(pxa_ctx* c, const double* ic_dev, double* state_dev) {
+  if (!c || !ic_dev || !state_dev) return PXA_ERR_INVALID;
+  if (!c->have_op || !c->have_time || c->op.kind != PXA_BURGERS_2D)
+    return fail(c, PXA_ERR_STATE, "pxa_direct_state needs a BURGERS_2D operator and set_time");
+  int rc = prepare(c);
+  if (rc) return rc;
+  PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
+  cudaStream_t st = c->stream;
+  const int n = c->op.nx;
+  const size_t plane2 = 2 * (size_t)n * n;
+  const double dt = c->T / (double)c->K;
+  float* tr = c->b2traj;
+  PXA_CUDA(c, launch_bu2_convert(st, ic_dev, tr, plane2), "initial state");
+  for (int64_t s = 0; s < c->K; ++s)
+    PXA_CUDA(c, launch_bu2_step(st, tr + (size_t)s * plane2, tr + (size_t)(s + 1) * plane2, n, c->op.L, c->op.nu, dt),
+             "direct step");
+  PXA_CUDA(c, launch_bu2_convert_back(st, tr + (size_t)c->K * plane2, state_dev, plane2, c->status), "final state");
+  invalidate(c);  // the stored trajectory no longer belongs to a solve of the control
+  return pxa_sync(c);
 }
 
 int pxa_set_wait_limit(pxa_ctx* c, int64_t cycles) {

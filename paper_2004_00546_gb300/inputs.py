@@ -207,3 +207,21 @@ def sparse_operator(n: int, per_row: int, seed: int, shift: float = 1.0):
         rp.append(len(cols))
     return (np.asarray(rp, dtype=np.int64), np.asarray(cols, dtype=np.int32),
             np.asarray(vals, dtype=np.float64))
+
+
+def burgers2d_problem(n: int = 256, seed: int = 2008, kmax: int = 12, amp: float = 0.15):
+    """2D viscous Burgers initial states (Sec. 4.3 shape, periodic [0, 2 pi)^2): a "true"
+    initial state (u, v), each a random Fourier series with |k| <= kmax (seeds
+    1000 * seed + 1, + 2) scaled to max |.| = amp, whose final state is the tracking
+    target, and a different seeded state of the same kind (seeds + 3, + 4) as a test
+    point. The default amplitude keeps the cell Reynolds number max|u| h / nu below 2 on
+    the 256^2 grid at nu = 2e-3 (0.15 x 0.0245 / 0.002 = 1.8), without which central
+    differences let the steepening fronts oscillate and blow up before T = 1. Returned
+    flattened as 2 n^2 values (u then v, each (n, n) row-major)."""
+    def field(s):
+        f = fourier2d(n, n, kmax, 1000 * seed + s)
+        return amp * f / np.abs(f).max()
+
+    true_ic = np.concatenate([field(1).ravel(), field(2).ravel()])
+    other = np.concatenate([field(3).ravel(), field(4).ravel()])
+    return {"true_ic": true_ic, "other_ic": other, "n": n}

@@ -17,7 +17,7 @@ OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINIT
     0, -1, -2, -3, -4, -5, -6, -7)
 ERR_TOO_LARGE = -8
 EXPV_STATIC_MAX_DOUBLES = 131072
-ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D, CSR = 1, 2, 3, 4
+ADVDIFF_1D, BURGERS_1D, ADVDIFF_2D, CSR, BURGERS_2D = 1, 2, 3, 4, 5
 OBJ_TERMINAL_L2, OBJ_INTEGRAL_TRACKING = 1, 2
 F64, F32 = 0, 1
 CN, RK4 = 1, 2
@@ -36,7 +36,8 @@ EXPORTS = [
     "pxa_set_krylov", "pxa_set_magnus", "pxa_set_control", "pxa_set_target", "pxa_set_objective",
     "pxa_set_precision", "pxa_set_memory", "pxa_set_adjoint", "pxa_set_overlap", "pxa_set_partition", "pxa_set_checkpoints", "pxa_set_lane_steps", "pxa_partition_bounds", "pxa_set_propagator", "pxa_set_groups",
     "pxa_set_graph", "pxa_gradient", "pxa_gradient_async", "pxa_sync", "pxa_gradient_host",
-    "pxa_get_stats", "pxa_set_timing", "pxa_set_wait_limit", "pxa_wait_probe", "pxa_nl_paraexp", "pxa_apply_operator", "pxa_step", "pxa_expv",
+    "pxa_get_stats", "pxa_set_timing", "pxa_set_wait_limit", "pxa_wait_probe", "pxa_nl_paraexp",
+    "pxa_direct_state", "pxa_apply_operator", "pxa_step", "pxa_expv",
     "pxa_burgers_rhs", "pxa_burgers_jac_T", "pxa_expv_static", "pxa_set_cluster", "pxa_autotune", "pxa_solve_direct", "pxa_solve_adjoint",
     "pxa_rk4_lanes_2d", "pxa_cn_lanes_1d", "pxa_spmv_csr",
     "pxa_batch_create", "pxa_batch_destroy", "pxa_batch_last_error", "pxa_batch_set",
@@ -143,6 +144,7 @@ def load(path: str = LIB_PATH):
         "pxa_gradient_host": [p, i, p, p, p],
         "pxa_get_stats": [p, ctypes.POINTER(Stats)],
         "pxa_set_wait_limit": [p, i64],
+        "pxa_direct_state": [p, p, p],
         "pxa_nl_paraexp": [p, p, d, i, p, p, ctypes.POINTER(i)],
         "pxa_wait_probe": [p],
         "pxa_apply_operator": [p, i, p, p],
@@ -253,6 +255,17 @@ class Context:
                             None)
         self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
         self.n = nx * ny
+
+    def set_operator_burgers_2d(self, n, nu, L=6.283185307179586):
+        """2D viscous Burgers on an n x n periodic grid; control and gradient hold 2 n^2
+        values (u then v)."""
+        desc = OperatorDesc(BURGERS_2D, 2 * n * n, L, 0.0, nu, n, n, None, None, None, None, None)
+        self._check(self._L.pxa_set_operator(self._h, ctypes.byref(desc)))
+        self.n = 2 * n * n
+
+    def direct_state(self, ic, out):
+        """BURGERS_2D: q(T) of the direct solve from ic into out (CUDA float64, 2 n^2)."""
+        self._check(self._L.pxa_direct_state(self._h, _dptr(ic), _dptr(out)))
 
     def set_operator_csr(self, row_ptr, col, val):
         """General sparse operator A (CSR on the device: int64 row_ptr[n + 1], int32 col,
