@@ -25,7 +25,7 @@ def _run(*args):
     return d
 
 
-@pytest.mark.parametrize("workload", ["burgers1d", "advdiff1d", "batched1d", "spmv_csr"])
+@pytest.mark.parametrize("workload", ["burgers1d", "advdiff1d", "batched1d", "spmv_csr", "burgers2d"])
 def test_reference_line_follows_the_contract(workload):
     d = _run("--workload", workload, "--steps", "1", "--warmup", "0")
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
