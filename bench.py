@@ -474,7 +474,8 @@ def compare_burgers2d(args, X, torch, flush):
     d = rel_err(res["paraexp"][1], res["serial"][1])
     return {"workload": w["label"], "paraexp_ms": res["paraexp"][0], "serial_ms": res["serial"][0],
             "speedup": res["serial"][0] / res["paraexp"][0], "rel_err_paraexp": None, "rel_err_serial": None,
-            "rel_diff_paraexp_vs_serial": d, "tolerance": 4 * w["K"] * 2.0 ** -24, "gate": gate_mark(d, 1e-12),
+            "rel_diff_paraexp_vs_serial": d, "tolerance": 4 * w["K"] * 2.0 ** -24,
+            "gate": gate_mark(d, 4 * w["K"] * 2.0 ** -24),
             "note": "terminal objective: the adjoint lanes vanish, Paraexp = serial by construction; FP32 stepping; "
                     "the FP64 oracle at full size is not run here (the tests hold both to it at 16^2-48^2 and check "
                     "the full size by central differences)"}
@@ -707,6 +708,13 @@ def run_ours(args, w, rank, world):
             return c2
 
         res = time_pair(X, torch, make_bu, args.steps, args.warmup, flush)
+        # plain serial stepping: the adjoint takes one transposed step per exchange (no
+        # product records), timed the same way
+        c1 = make_bu(X.SERIAL)
+        c1.set_adjoint(X.ADJ_BANDED_SINGLE)
+        t1, _, g1 = time_mode(X, torch, c1, X.SERIAL, args.steps, args.warmup, flush)
+        c1.close()
+        one_step = (float(np.mean(t1)), g1.detach().cpu().numpy())
         # the phases of each mode (events on the streams each phase runs on), after the pair
         mode_phases = {}
         for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
@@ -724,6 +732,13 @@ def run_ours(args, w, rank, world):
                 "carried by the stepper's own transposed step maps, so its chain sweeps all K steps like the "
                 "serial adjoint")
             comparison["C2"]["phases_ms"] = mode_phases
+            comparison["C2"]["serial_one_step_ms"] = one_step[0]
+            comparison["C2"]["rel_err_serial_one_step"] = rel_err(one_step[1], g_ref)
+            comparison["C2"]["speedup_vs_one_step"] = one_step[0] / res["paraexp"][0]
+            comparison["C2"]["serial_note"] = (
+                "serial_ms: serial RK4 direct, adjoint chain on four-step product records built beside "
+                "the direct (the fastest serial form here); serial_one_step_ms: the adjoint one transposed "
+                "step at a time")
             comparison["C1"] = compare_advdiff1d(args, X, torch, flush)
             comparison["C3"] = compare_advdiff2d(args, X, torch, flush)
             comparison["C4"] = compare_batched(args, X, torch, flush)
