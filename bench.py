@@ -52,7 +52,8 @@ WORKLOADS = {
                             "initial-state control, terminal tracking objective"),
     "batched1d": dict(kind="batched1d", count=256, c=1.0, T=1.0, K=4096, P=16,
                       label="256 independent 1D advection-diffusion problems, n ~ U{128..2048}, "
-                            "nu ~ logU[1e-3, 1e-1], T=1 CN 4096 steps, P=16, FP32 stepping, FP64 Krylov"),
+                            "nu ~ logU[1e-3, 1e-1], T=1 CN 4096 steps, P=16, FP32 stepping, "
+                            "homogeneous parts by the FP32 band of M^(K/P), FP64 superposition"),
 }
 # FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

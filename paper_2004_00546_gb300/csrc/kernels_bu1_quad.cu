@@ -33,7 +33,6 @@ constexpr int PW = BU1_PAIR_RECORD;   // two-step record: 17 taps + source
 constexpr int QW = BU1_QUAD_RECORD;   // four-step record: 33 taps + source
 constexpr int HQ = 16;                // halo of a four-step entry
 constexpr int QT = 128;               // points per tile of the parallel kernels
-constexpr int SLOT = 10;              // doubles of a record one thread keeps per step
 
 __device__ __forceinline__ int wrapq(int g, int n) {
   g %= n;
@@ -93,37 +92,15 @@ __global__ void __launch_bounds__(QT) bu1_band_quad_kernel(int n, const double* 
 // lambda_{s_hi} is row s_hi of from_rows (a chain continued from an earlier launch) or
 // the source of the last state; rows produced go to out_rows.
 //
-// With G = ceil(chunk / 32) point groups, warp w serves group w % G and quarter w / G.
+// With G = ceil(chunk / 32) point groups, warp w serves group w / 4 and quarter w % 4.
 // The quarters take consecutive runs of taps (four-step: -16..-9 with the source,
 // -8..-1, 0..7, 8..16; two-step: -8..-5 with the source, -4..-1, 0..3, 4..8; one-step:
 // quarter 0 alone). Quarters 1-3 hand their partial sums over through shared memory at a
 // barrier of the group's four warps; quarter 0 finishes, stores and sends the value.
-// Each thread keeps its quarter's part of a record (at most 10 doubles) in a DEPTH-deep
-// ring filled by cp.async DEPTH-1 steps ahead.
-
-// The 16-byte chunks of a record that quarter qq reads, stored at slot[2 i]: taps first,
-// the source (quarter 0) in slot[9].
-__device__ __forceinline__ void quad_prefetch(double* d, const double* rec, const double* rp,
-                                              const double* rq, int n, int pt, int4 e, int qq) {
-  if (e.y == 4) {
-    const double* s = rq + ((size_t)(e.x / 4) * n + pt) * QW;
-    const int c0 = 4 * qq;  // chunks 4qq .. 4qq+3 (+ chunk 16)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) cp_async16(d + 2 * i, s + 2 * (c0 + i));
-    if (qq == 0 || qq == 3) cp_async16(d + 8, s + 32);
-  } else if (e.y == 2) {
-    const double* s = rp + ((size_t)(e.x / 2) * n + pt) * PW;
-    const int c0 = 2 * qq;  // chunks 2qq, 2qq+1 (quarter 3: + chunk 8; quarter 0: chunk 8 at slot 8)
-    cp_async16(d, s + 2 * c0);
-    cp_async16(d + 2, s + 2 * (c0 + 1));
-    if (qq == 3) cp_async16(d + 4, s + 16);
-    if (qq == 0) cp_async16(d + 8, s + 16);
-  } else if (qq == 0) {
-    const double* s = rec + ((size_t)e.x * n + pt) * RW;
-#pragma unroll
-    for (int i = 0; i < RW / 2; ++i) cp_async16(d + 2 * i, s + 2 * i);
-  }
-}
+// The records of an entry for the CTA's points are contiguous in global memory (one row
+// of the one-, two- or four-step records): one thread brings them into a DEPTH-deep ring
+// in shared memory with a single bulk copy DEPTH-1 entries ahead, completing on the
+// slot's mbarrier.
 
 template <int DEPTH>
 __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
@@ -142,18 +119,29 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
   double* const lam0 = smq + HQ;
   double* const lam1 = smq + Wd + HQ;
   double* const part = smq + 2 * Wd;   // [3][G * 32] partial sums of quarters 1-3
-  double* const ring = part + 3 * G * 32;  // [DEPTH][4 * G * 32][SLOT]
+  double* const ring = part + 3 * G * 32;  // [DEPTH][nc * QW]: the records of one entry per slot
+  __shared__ __align__(8) uint64_t rbar[DEPTH];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lanei = tid & 31;
-  const int g = warp % G, qq = warp / G;
-  const int p = g * 32 + lanei;  // this thread's point
-  const bool act = p < cnt;
+  // warp w = 4 g + qq: the four quarters of a group sit on the four SM sub-partitions
+  // (w mod 4), and each sub-partition holds one warp of every group
+  const int g = warp >> 2, qq = warp & 3;
+  // The last group holds the 2 x HQ edge points, the only ones whose taps reach the
+  // neighbours' values: it alone waits for the halo, while the other groups work through
+  // the interior points [HQ, cnt - HQ) of the same entry.
+  const bool edge = g == G - 1;
+  const int p = edge ? (cnt >= 2 * HQ && lanei >= HQ ? cnt - 2 * HQ + lanei : lanei)
+                     : HQ + g * 32 + lanei;  // this thread's point
+  const bool act = edge ? p < cnt : p < cnt - HQ;
   const bool multi = C > 1;
   const int left = (rank + C - 1) % C, right = (rank + 1) % C;
   const int cnt_left = min(nc, n - left * nc);
-  if (multi && tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+  if (tid == 0) {
+    if (multi) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+    }
+    for (int s = 0; s < DEPTH; ++s) mbar_init(&rbar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int q = tid - HQ; q < cnt + HQ; q += nt) {
@@ -177,21 +165,35 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
     br0 = map_rank(smem_u32(&bar[0]), right);
     br1 = map_rank(smem_u32(&bar[1]), right);
   }
-  double* const my_ring = ring + (size_t)tid * SLOT;
-  const int slot_stride = nt * SLOT;
+  const int slot_stride = nc * QW;  // doubles per ring slot (a multiple of 2: 16-byte slots)
   const int4 none = make_int4(0, 0, 0, 0);
   int4 e0 = nplan > 0 ? plan[0] : none, e1 = nplan > 1 ? plan[1] : none,
        e2 = nplan > 2 ? plan[2] : none, e3 = nplan > 3 ? plan[3] : none;
+  // records of entry e: row e.x of the one-step, e.x / 2 of the two-step or e.x / 4 of
+  // the four-step records, W doubles per point (taps from offset -W/2 + 1 and the source)
+  auto rec_width = [](const int4& e) { return e.y == 4 ? QW : e.y == 2 ? PW : RW; };
   auto prefetch = [&](const int4& e, bool valid, int slot) {
-    if (act && valid) quad_prefetch(my_ring + slot * slot_stride, rec, rp, rq, n, start + p, e, qq);
-    cp_async_commit();
+    if (tid != 0 || !valid) return;
+    const double* src = e.y == 4   ? rq + ((size_t)(e.x / 4) * n + start) * QW
+                        : e.y == 2 ? rp + ((size_t)(e.x / 2) * n + start) * PW
+                                   : rec + ((size_t)e.x * n + start) * RW;
+    const uint32_t bytes = (uint32_t)(cnt * rec_width(e) * sizeof(double));
+    // the slot's previous entry was read before the block barrier that precedes this
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arm(&rbar[slot], (int)bytes);
+    bulk_g2s(ring + (size_t)slot * slot_stride, src, bytes, &rbar[slot]);
   };
   static_assert(DEPTH == 4, "the plan queue holds DEPTH entries");
   prefetch(e0, nplan > 0, 0);
   prefetch(e1, nplan > 1, 1);
   prefetch(e2, nplan > 2, 2);
+  // the halo of entry e (sent unless e is the last) lands in buffer (e + 1) & 1 and
+  // completes on bar[(e + 1) & 1]; entries 0 and 1 are armed here, entry e + 1 by the
+  // edge group right after its wait for entry e - 1 on the same barrier
+  const bool armer = edge && qq == 0 && lanei == 0;
   if (multi) {
     if (tid == 0 && nplan > 1) mbar_arm(&bar[1], 2 * HQ * (int)sizeof(double));
+    if (tid == 0 && nplan > 2) mbar_arm(&bar[0], 2 * HQ * (int)sizeof(double));
     cl.sync();
   } else {
     __syncthreads();
@@ -199,7 +201,17 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
   uint32_t ph0 = 0u, ph1 = 0u;
   for (int j = 0; j < nplan; ++j) {
     prefetch(e3, j + 3 < nplan, (j + 3) & (DEPTH - 1));
-    cp_async_wait<DEPTH - 1>();
+    if (multi && j > 0) {
+      // buffer of lambda after entry j - 1 (read now): j & 1
+      uint64_t* hb = (j & 1) ? &bar[1] : &bar[0];
+      uint32_t& ph = (j & 1) ? ph1 : ph0;
+      if (edge) {
+        mbar_wait_bounded(hb, ph, status);
+        if (armer && j + 2 < nplan) mbar_arm(hb, 2 * HQ * (int)sizeof(double));
+      }
+      ph ^= 1u;
+    }
+    mbar_wait_bounded(&rbar[j & (DEPTH - 1)], (uint32_t)((j / DEPTH) & 1), status);
     const int4 e = e0;
     e0 = e1;
     e1 = e2;
@@ -209,7 +221,8 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
     double* const Ln = b ? lam1 : lam0;
     const double* const Lp = b ? lam0 : lam1;
     const bool last = j + 1 == nplan;
-    const double* r = my_ring + (j & (DEPTH - 1)) * slot_stride;
+    const int rw = rec_width(e);
+    const double* rr = ring + (size_t)(j & (DEPTH - 1)) * slot_stride + (size_t)p * rw;
     // this quarter's run of taps: ntap taps from offset o0
     int ntap = 0, o0 = 0;
     if (e.y == 4) {
@@ -224,14 +237,24 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
     }
     double acc = 0.0;
     if (act) {
+      // record index of tap offset o: o + rw / 2 - 1; the source is the last entry. All
+      // nine loads are issued before the first FMA (the ones past the quarter's taps stay
+      // inside the slot and the lambda buffer and are not used).
       const double* L = Lp + p + o0;
+      const double* rt = rr + o0 + rw / 2 - 1;
+      double cv[9], lv[9];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        cv[t] = rt[t];
+        lv[t] = L[t];
+      }
       // one accumulator: the two warps that share an SM sub-partition's FP64 unit hide
       // each other's dependent-FMA latency, and merges of partial accumulators would
       // cost FP64 instructions of their own
-      acc = (qq == 0 && e.z) ? r[9] : 0.0;
+      acc = (qq == 0 && e.z) ? rr[rw - 1] : 0.0;
 #pragma unroll
       for (int t = 0; t < 9; ++t)
-        if (t < ntap) acc = fma(r[t], L[t], acc);
+        if (t < ntap) acc = fma(cv[t], lv[t], acc);
     }
     // quarters 1-3 hand their partial sums to quarter 0 (barrier of the group's four warps)
     if (qq > 0 && act) part[(qq - 1) * G * 32 + p] = acc;
@@ -248,9 +271,6 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
     }
     if (!last) {
       if (multi) {
-        if (tid == 0 && j + 2 < nplan) mbar_arm(b ? &bar[0] : &bar[1], 2 * HQ * (int)sizeof(double));
-        mbar_wait_bounded(b ? &bar[1] : &bar[0], b ? ph1 : ph0, status);
-        if (b) ph1 ^= 1u; else ph0 ^= 1u;
         __syncthreads();
       } else {
         __syncthreads();
@@ -262,8 +282,13 @@ __global__ void bu1_band_chain4_kernel(int n, const double* __restrict__ rec,
       }
     }
   }
-  cp_async_wait<0>();
+  // every entry's copy was waited for above; after a wait that gave up, a copy may still
+  // be in flight: let the last one of each slot land before the block leaves
+  if (tid == 0 && *(volatile int*)status != 0)
+    for (int s = 0; s < DEPTH && s < nplan; ++s)
+      mbar_drain(&rbar[s], (uint32_t)(((s + DEPTH * ((nplan - 1 - s) / DEPTH)) / DEPTH) & 1));
   if (multi) cl.sync();  // no CTA leaves while a neighbour could still address it
+  else __syncthreads();
 }
 
 // ---- rows skipped by four-step entries ----------------------------------------------
@@ -340,8 +365,8 @@ int bu1_chain_plan(int64_t K, int64_t k, int P, int max_len, int4* out) {
 bool bu1_chain4_valid(int n, int C) {
   if (C < 1 || C > 16) return false;
   const int nc = (n + C - 1) / C;
-  // four threads per point: at most 4 groups of 32 points (512 threads, a 4-deep ring of
-  // 80-byte slots per thread in 160 KB)
+  // four threads per point: at most 4 groups of 32 points (512 threads; a 4-deep ring of
+  // the entries' records, 4 x 128 x 272 B = 139 KB)
   if ((nc + 31) / 32 > 4) return false;
   if (C == 1) return n >= HQ;
   return n - (C - 1) * nc >= HQ;  // every CTA owns the 16 points a neighbour needs
@@ -374,7 +399,7 @@ cudaError_t launch_bu1_band_chain4(cudaStream_t st, int C, int n, const double* 
   const int nc = (n + C - 1) / C;
   constexpr int DEPTH = 4;
   const int G = (nc + 31) / 32, nt = 128 * G;  // four warps (quarters) per group of 32 points
-  size_t sh = sizeof(double) * (2 * (size_t)(nc + 2 * HQ) + 3 * (size_t)G * 32 + (size_t)DEPTH * nt * SLOT);
+  size_t sh = sizeof(double) * (2 * (size_t)(nc + 2 * HQ) + 3 * (size_t)G * 32 + (size_t)DEPTH * nc * QW);
   if (reserve_smem > sh) sh = reserve_smem;  // no other CTA shares the SM
   const void* fn = (const void*)bu1_band_chain4_kernel<DEPTH>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);

@@ -536,13 +536,16 @@ def test_burgers_autotune_measures_the_partition_ratio(X, torch, bu_small):
 
 
 @pytest.mark.parametrize("n,C,K,P", [(200, 4, 630, 6), (200, 8, 600, 6), (100, 1, 632, 8),
-                                      (48, 3, 210, 3), (512, 16, 400, 5)])
+                                      (48, 3, 210, 3), (512, 16, 400, 5), (290, 4, 630, 6),
+                                      (1000, 9, 400, 5)])
 def test_burgers_four_step_chain(X, torch, n, C, K, P):
     """The chain with four-step product bands (33 taps split over four warps, 16-point
     halos) on clusters from one CTA (halo wrapping the grid) to 16, with subinterval
     lengths that are not multiples of 4 (so the plan mixes four-, two- and one-step
     entries around the lane values), gives the oracle's gradient like the two-step
-    chain."""
+    chain. The point groups cover one to four groups of 32 per CTA, with a shorter last
+    CTA (290 over 4, 1000 over 9): the edge group and the interior groups split the
+    points differently in each."""
     nu, T = 0.02, 0.25
     f = 2.0 * I.fourier1d(n, 8, 81)
     g = I.fourier1d(n, 8, 82)
