@@ -1239,6 +1239,9 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   // solve alone), so that J is summed in the same order whichever call computed it.
   const bool chunked = c->band && c->overlap && full && c->side;
   const bool overlap = chunked && do_d && do_a;
+  // with the overlap, this stream waits for the last chunk's adjoint lanes only where the
+  // chain first adds a lane value (the chain's top entries need the records alone)
+  bool lanes_pending = false;
   if (do_d && chunked) {
     // Hybrid overlap (Sec. 3.3): the serial direct runs in chunks of whole subintervals on
     // this stream (high priority, each CTA owning its SM); after each chunk the side
@@ -1312,7 +1315,9 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       PXA_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
       PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join, 0), "join wait");
       PXA_CUDA(c, cudaEventRecord(c->ev_join2, c->side2), "join");
-      PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join2, 0), "join wait");
+      // the fills and gradient segments on the side stream read the lanes' values
+      PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_join2, 0), "join wait");
+      lanes_pending = true;
       PXA_CUDA(c, launch_bu1_objective_sum(st, c->Jrow, K, dt / c->T, Jdev, c->status), "J");
       if (c->timing && c->ev_ready) {
         ev_record(c, 6);
@@ -1364,6 +1369,14 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                       c->LI, c->E, c->status, 0, c->q_sweep), "band lanes");
     ev_record(c, 3);
   }
+  auto join_lanes = [&]() -> int {
+    if (lanes_pending) {
+      PXA_CUDA(c, cudaStreamWaitEvent(st, c->ev_join2, 0), "join wait");
+      lanes_pending = false;
+    }
+    return PXA_OK;
+  };
+  int rc_join = PXA_OK;
   if (c->band) {
     const double* rows = full ? c->traj : c->scratch;
     const int64_t lane_k = full ? 0 : k;
@@ -1393,16 +1406,30 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       if (S > pxa_ctx::kMaxSeg) S = pxa_ctx::kMaxSeg;
       if (np < 64 * S) S = 1;
       if (S == 1) {
+        if ((rc_join = join_lanes())) return rc_join;
         PXA_CUDA(c, chain(0, np, (int)K, nullptr, 0, 0), "band chain");
         PXA_CUDA(c, fill(st, 0, np, 0), "band fill");
       } else {
         const int spb = bu1_band_steps_per_block(K, n);
         const int64_t li_top = (int64_t)(P - 1) * k;
         int b_hi = bu1_band_grad_blocks(K, n);  // blocks [b_hi, end) are summed already
+        // the first plan entry that adds a lane value
+        int ja = 0;
+        while (ja < np && pl.host[ja].w == 0) ++ja;
         for (int i = 0; i < S; ++i) {
           const int j0 = (int)((int64_t)np * i / S), j1 = (int)((int64_t)np * (i + 1) / S);
           const int s_hi = i == 0 ? (int)K : pl.host[j0 - 1].x;
-          PXA_CUDA(c, chain(j0, j1, s_hi, i == 0 ? nullptr : c->Hrows, c->prio_hi, c->reserve_smem), "band chain");
+          if (lanes_pending && ja > j0 && ja < j1) {
+            // the entries above the first lane value run while the last lanes finish
+            PXA_CUDA(c, chain(j0, ja, s_hi, i == 0 ? nullptr : c->Hrows, c->prio_hi, c->reserve_smem),
+                     "band chain");
+            if ((rc_join = join_lanes())) return rc_join;
+            PXA_CUDA(c, chain(ja, j1, pl.host[ja - 1].x, c->Hrows, c->prio_hi, c->reserve_smem), "band chain");
+          } else {
+            if ((rc_join = join_lanes())) return rc_join;
+            PXA_CUDA(c, chain(j0, j1, s_hi, i == 0 ? nullptr : c->Hrows, c->prio_hi, c->reserve_smem),
+                     "band chain");
+          }
           PXA_CUDA(c, cudaEventRecord(c->ev_seg[i], st), "segment");
           PXA_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_seg[i], 0), "segment wait");
           PXA_CUDA(c, fill(c->side, j0, j1, c->prio_lo), "band fill");
@@ -1423,9 +1450,11 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       }
     } else if (chain_top) {
       // the top subinterval with its source, then the summed homogeneous problems
+      if ((rc_join = join_lanes())) return rc_join;
       PXA_CUDA(c, launch_bu1_band_sweep(st, c->cl_band_chain, 1, 0, n, c->rec, k, P, 1, c->E, c->Hrows,
                                         nullptr, c->status, 0, c->q_sweep), "band chain");
     } else {
+      if ((rc_join = join_lanes())) return rc_join;
       PXA_CUDA(c, launch_bu1_magnus_chain(st, n > 2048 ? 1024 : 512, g, dt, K, P, k, c->magnus_M,
                                           c->omega, rows, lane_k, c->E, c->hsum, c->V, c->kry_m,
                                           c->kry_tol, c->v_in_smem, c->status, c->errmax),
@@ -1439,6 +1468,7 @@ int enqueue_bu1(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     ev_record(c, 5);
     return PXA_OK;
   }
+  if ((rc_join = join_lanes())) return rc_join;
   const int cl_lane = P == 1 ? c->cl_direct : c->cl_lanes;
   PXA_CUDA(c, launch_bu1c_adjoint_lanes(st, cl_lane, P, n, c->op.L, c->op.nu, dt, c->T, k, c->omega,
                                         c->control, c->target, full ? c->traj : nullptr,
