@@ -1228,7 +1228,7 @@ def run_2d(args, w, rank, world):
         times, phases, _ = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush, timing=True)
     total_ms = float(sum(times))
     ph = {k: float(np.mean([p[k] for p in phases])) for k in
-          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom")}
+          ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom", "ms_side_lanes")}
     cpu = {}
     if rank == 0:
         import oracle as O

@@ -371,6 +371,23 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
     }
     const float* L = t.q[0] + (li & 1) * TILE2;
     const int64_t s_abs = lane_off + (int64_t)l * lane_k + s_local;
+    // the source and gradient values of this thread's interior points, loaded now so
+    // that their global-memory latency passes during the four stencil phases below
+    constexpr int NQ = (TX2 * TY2 + 255) / 256;
+    double* Gl = G + (size_t)l * p.nx * p.ny;
+    const float* es = traj ? traj + (size_t)s_abs * p.nx * p.ny : nullptr;
+    const bool add_src = with_source && s_local > 0 && es;
+    float srcv[NQ];
+    double gold[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int x = x0 + e % TX2, y = y0 + e / TX2;
+      const bool in = e < TX2 * TY2 && x < p.nx && y < p.ny;
+      const size_t gi = in ? (size_t)y * p.nx + x : 0;
+      srcv[q] = (in && add_src) ? __ldg(es + gi) : 0.0f;
+      gold[q] = in ? Gl[gi] : 0.0;
+    }
     if (threadIdx.x == 0) {
       const double tabs = (double)s_abs * p.dtd;
       t.sc[0] = (float)forcing_s(p.omega, tabs);
@@ -393,9 +410,9 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
     // the gradient terms in FP32 per step, kept in registers per interior point below;
     // halo 2: Ybar3 = A^T kbar3; kbar2 = dt/3 lambda + dt/2 Ybar3
     // (kbar4 is still in ma on the interior: read it before ma is overwritten)
-    float g4[ (TX2 * TY2 + 255) / 256 ];
+    float g4[NQ];
 #pragma unroll
-    for (int q = 0; q < (TX2 * TY2 + 255) / 256; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       int e = threadIdx.x + q * 256;
       int c = (G2 + e / TX2) * BX2 + (G2 + e % TX2);
       g4[q] = c4 * ma[c] + c2 * mb[c];
@@ -418,10 +435,8 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
     __syncthreads();
     // interior: Ybar1 = A^T kbar1; lambda_s = Ln + Ybar1 (+ source); gradient terms
     float* out = outbase + (size_t)l * p.Hp * p.Wp;
-    double* Gl = G + (size_t)l * p.nx * p.ny;
-    const float* es = traj ? traj + (size_t)s_abs * p.nx * p.ny : nullptr;
 #pragma unroll
-    for (int q = 0; q < (TX2 * TY2 + 255) / 256; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       int e = threadIdx.x + q * 256;
       const int xx = e % TX2, yy = e / TX2;
       const int c = (G2 + yy) * BX2 + (G2 + xx);
@@ -430,10 +445,10 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
       float nv = AT_at(p, mb, u, v, c);
       float lam = Ln[c] + nv;
       const size_t gi = (size_t)y * p.nx + x;
-      if (with_source && s_local > 0) lam += (float)src_scale * es[gi];
+      if (add_src) lam += (float)src_scale * srcv[q];
       store_with_ghosts(out, p, x, y, lam);
       float gstep = g4[q] + c2 * ma[c] + c1 * mb[c];
-      Gl[gi] += (double)gstep;
+      Gl[gi] = gold[q] + (double)gstep;
     }
     __syncthreads();
   }
@@ -451,6 +466,26 @@ __global__ void ad2_pack_coef_kernel(Ad2Params p, const double* __restrict__ u,
     store_with_ghosts(coef + plane, p, x, y, (float)v[i]);
     store_with_ghosts(coef + 2 * plane, p, x, y, (float)(f[i] - (ft ? ft[i] : 0.0)));
   }
+}
+
+// The coefficients of A^T at every padded point (periodic indices): (A^T x)_c =
+// tE x_E + tW x_W + tN x_N + tS x_S - 4 d x_c with tE = d + a u_E, tW = d - a u_W,
+// tN = d + a v_N, tS = d - a v_S (a = 1/(2h), d = nu/h^2): the neighbour's entry of A in
+// the column of c. tc = [4][Hp][Wp] FP32 (tE, tW, tN, tS).
+__global__ void ad2_pack_coefT_kernel(Ad2Params p, const double* __restrict__ u,
+                                      const double* __restrict__ v, float* __restrict__ tc) {
+  const size_t plane = (size_t)p.Hp * p.Wp;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const int X = (int)(i % p.Wp), Y = (int)(i / p.Wp);
+  const int x = ((X - G2) % p.nx + p.nx) % p.nx, y = ((Y - G2) % p.ny + p.ny) % p.ny;
+  const int xe = (x + 1) % p.nx, xw = (x + p.nx - 1) % p.nx;
+  const int yn = (y + 1) % p.ny, ys = (y + p.ny - 1) % p.ny;
+  const float a = p.inv2h, d = p.nu * p.invh2;
+  tc[i] = (float)u[(size_t)y * p.nx + xe] * a + d;
+  tc[plane + i] = -(float)u[(size_t)y * p.nx + xw] * a + d;
+  tc[2 * plane + i] = (float)v[(size_t)yn * p.nx + x] * a + d;
+  tc[3 * plane + i] = -(float)v[(size_t)ys * p.nx + x] * a + d;
 }
 
 // Fill lanes' padded states: zero (src == nullptr), or scale * row(row0 + l*row_step)
@@ -539,6 +574,20 @@ bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int dep
   return r == CUDA_SUCCESS;
 }
 
+bool ad2_make_map_plain(CUtensorMap* map, void* base, int elem_bytes, int nx, int ny, int depth, int box_x,
+                        int box_y) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (elem_bytes != 4 && elem_bytes != 8)) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)depth};
+  cuuint64_t strides[2] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                  base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static cudaError_t set_smem(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ad2_smem_bytes());
 }
@@ -585,6 +634,13 @@ cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const doub
                                  const double* v, const double* f, const double* ft, float* coef) {
   int threads = 256, blocks = (p.nx * p.ny + threads - 1) / threads;
   ad2_pack_coef_kernel<<<blocks, threads, 0, st>>>(p, u, v, f, ft, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_pack_coefT(cudaStream_t st, const Ad2Params& p, const double* u, const double* v,
+                                  float* tc) {
+  const size_t plane = (size_t)p.Hp * p.Wp;
+  ad2_pack_coefT_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(p, u, v, tc);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,25 @@ constexpr int AD2_ROLL_BR = 4;
 cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                                 const Ad2Params& p, float* states, int lanes, int buf_in,
                                 const float* sc, int sc_stride, int* status);
+// 3D map over [depth][ny][nx] unpadded planes of FP32 (elem_bytes 4) or FP64 (8), box
+// {box_x, box_y, 1}.
+bool ad2_make_map_plain(CUtensorMap* map, void* base, int elem_bytes, int nx, int ny, int depth, int box_x,
+                        int box_y);
+// tc = [4][Hp][Wp]: the coefficients of A^T (tE, tW, tN, tS) at every padded point.
+cudaError_t launch_ad2_pack_coefT(cudaStream_t st, const Ad2Params& p, const double* u, const double* v,
+                                  float* tc);
+// One reverse step of the adjoint lanes as a register wavefront (kernels_ad2_roll.cu; needs
+// ad2_roll_ok): qmap over the lane states (depth 2*lanes, box {64, AD2_ROLL_BR, 1}), tmap
+// over tc (box {64, AD2_ROLL_BR, 4}), smap over the FP32 trajectory [K+1][ny][nx] and gmap
+// over the FP64 lane gradients G [lanes][ny][nx] (both ad2_make_map_plain, box
+// {64, AD2_ROLL_BR}). Steps lanes lane0 .. lane0 + count - 1 of `lanes`; lane l is at step
+// zsrc0 + l z_stride: its source row and its forcing factors sc[3 step + {0, 1, 2}]; the
+// source is added when add_src is set.
+cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& tmap,
+                                 const CUtensorMap& smap, const CUtensorMap& gmap, const Ad2Params& p,
+                                 float* states, double* G, int lanes, int lane0, int count, int buf_in,
+                                 const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
+                                 int* status);
 cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
                                 const double* extra, double* grad, int* status);
 

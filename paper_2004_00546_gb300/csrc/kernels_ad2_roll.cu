@@ -253,6 +253,171 @@ __device__ __forceinline__ void roll_task(const CUtensorMap* qmap, const CUtenso
   }
 }
 
+// ---- reverse steps of the exact discrete adjoint for many lanes ----------------------
+// One reverse step of the transposed RK4 map (the adjoint lanes of Eq. hybadjinhom):
+// kbar4 = dt/6 lambda; Y3 = A^T kbar4, kbar3 = dt/3 lambda + dt Y3; Y2 = A^T kbar3,
+// kbar2 = dt/3 lambda + dt/2 Y2; Y1 = A^T kbar2, kbar1 = dt/6 lambda + dt/2 Y1;
+// lambda_new = lambda + Y3 + Y2 + Y1 + A^T kbar1 (+ the objective's source); the forcing
+// gradient gains c4 kbar4 + c2 kbar3 + c2 kbar2 + c1 kbar1 (Eq. paramupdate), in FP64.
+// The same wavefront as the forward step: stage A on row i-1, B on i-2, C on i-3, D on
+// i-4, every A^T from the rows of the previous stage held in registers. A block of rows
+// brings, by four TMA copies on one mbarrier, the lambda rows, the four A^T coefficient
+// rows (tE, tW, tN, tS), and, eight rows behind (the rows that stage D finishes), the
+// source rows of the lane's step and its FP64 gradient rows.
+
+constexpr int TB_FLOATS = 8 * BR * 64;    // lambda, 4 coefficient planes, source, FP64 gradient
+constexpr int TRING_FLOATS = NB * TB_FLOATS;
+constexpr int TWARPS = 4;
+
+struct CoefT2 {  // A^T coefficients of the thread's two points on one row
+  f2 e, w, n, s;
+};
+
+// (A^T x) at the thread's two points of the centre row x (neighbours xs below, xn above).
+__device__ __forceinline__ f2 stage_t2(const CoefT2& c, f2 CC, f2 x, f2 xs, f2 xn) {
+  const float x0 = lo_of(x), x1 = hi_of(x);
+  const float w0 = __shfl_up_sync(0xffffffffu, x1, 1);    // column 2t-1
+  const float e1 = __shfl_down_sync(0xffffffffu, x0, 1);  // column 2t+2
+  f2 k = mul2(c.e, pk(x1, e1));
+  k = fma2(c.w, pk(w0, x0), k);
+  k = fma2(c.n, xn, k);
+  k = fma2(c.s, xs, k);
+  return fma2(CC, x, k);
+}
+
+struct RollTTask {
+  int X0, Y0, l, buf_in, lanes, zsrc, own_x0, own_y0;
+};
+
+__device__ __forceinline__ void issue_tblock(const CUtensorMap* qmap, const CUtensorMap* tmap,
+                                             const CUtensorMap* smap, const CUtensorMap* gmap,
+                                             const RollTTask& tk, float* ring, uint64_t* bars, int b,
+                                             int slot) {
+  float* dst = ring + slot * TB_FLOATS;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bars[slot])),
+               "r"((int)(TB_FLOATS * sizeof(float)))
+               : "memory");
+  const int yrow = tk.Y0 + b * BR;
+  tma3d(dst, qmap, tk.X0, yrow, tk.buf_in * tk.lanes + tk.l, &bars[slot]);
+  tma3d(dst + BR * 64, tmap, tk.X0, yrow, 0, &bars[slot]);
+  // domain coordinates of the rows stage D finishes in this block: padded row - 2 G2
+  tma3d(dst + 5 * BR * 64, smap, tk.X0 - G2, yrow - 2 * G2, tk.zsrc, &bars[slot]);
+  tma3d(dst + 6 * BR * 64, gmap, tk.X0 - G2, yrow - 2 * G2, tk.l, &bars[slot]);
+}
+
+template <bool INNER>
+__device__ __forceinline__ void rollT_task(const CUtensorMap* qmap, const CUtensorMap* tmap,
+                                           const CUtensorMap* smap, const CUtensorMap* gmap,
+                                           const Ad2Params& p, const RollTTask& tk, float* qo,
+                                           double* G, float* ring, uint64_t* bars, int Hs, float c1,
+                                           float c2, float c4, float src_scale, bool add_src,
+                                           int* status) {
+  const int t = threadIdx.x & 31;
+  const float d = p.nu * p.invh2, h = p.dt;
+  const f2 CC = pk(-4.0f * d, -4.0f * d);
+  const f2 H = pk(h, h), H2 = pk(0.5f * h, 0.5f * h), H3 = pk(h / 3.0f, h / 3.0f), H6 = pk(h / 6.0f, h / 6.0f);
+  const f2 C1 = pk(c1, c1), C2 = pk(c2, c2), C4H6 = pk(c4 * (h / 6.0f), c4 * (h / 6.0f));
+  const f2 SRC = pk(src_scale, src_scale);
+  const bool out_col = t >= 2 && t < 30;  // strip columns 4 .. 59
+  const int xd = tk.X0 - G2 + 2 * t;      // domain column of the thread's first point
+  const bool own_col = out_col && xd >= tk.own_x0;  // gradient points this task updates
+  const int rows = Hs + 8, nblocks = rows / BR;
+  f2 Q[4], KB3[4], KB2[4], KB1[4], LN[4], GG[4];
+  CoefT2 CT[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) Q[j] = KB3[j] = KB2[j] = KB1[j] = LN[j] = GG[j] = 0ull;
+  if (t == 0)
+    for (int b = 0; b < NB - 1 && b < nblocks; ++b) issue_tblock(qmap, tmap, smap, gmap, tk, ring, bars, b, b);
+  float* orow = qo + (size_t)(tk.Y0 + G2) * p.Wp + xd + G2;
+  double* grow = G + ((size_t)tk.l * p.ny + tk.Y0) * p.nx + xd;
+  bool ok = true;
+  for (int i0 = 0; i0 < rows; i0 += 8) {
+#pragma unroll
+    for (int I = 0; I < 8; ++I) {
+      const int i = i0 + I;
+      constexpr int slot_of_I[8] = {0, 0, 0, 0, 1, 1, 1, 1};  // (i / BR) % NB with BR = 4, NB = 2
+      if (I % BR == 0) {
+        const int b = i / BR;
+        __syncwarp();
+        if (t == 0 && b + NB - 1 < nblocks) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue_tblock(qmap, tmap, smap, gmap, tk, ring, bars, b + NB - 1, (b + NB - 1) % NB);
+        }
+        ok &= bar_wait(&bars[slot_of_I[I]], (uint32_t)((b / NB) & 1));
+      }
+      const float* src = ring + slot_of_I[I] * TB_FLOATS + (I % BR) * 64 + 2 * t;
+      Q[I & 3] = *reinterpret_cast<const f2*>(src);
+      const f2 te = *reinterpret_cast<const f2*>(src + BR * 64);
+      const f2 tw = *reinterpret_cast<const f2*>(src + 2 * BR * 64);
+      const f2 tn = *reinterpret_cast<const f2*>(src + 3 * BR * 64);
+      const f2 ts = *reinterpret_cast<const f2*>(src + 4 * BR * 64);
+      const f2 sv = *reinterpret_cast<const f2*>(src + 5 * BR * 64);
+      const double2 gold = *reinterpret_cast<const double2*>(
+          reinterpret_cast<const double*>(ring + slot_of_I[I] * TB_FLOATS + 6 * BR * 64) + (I % BR) * 64 + 2 * t);
+      // stage A on row i-1: Y3 = A^T (dt/6 lambda)
+      {
+        const f2 x = Q[(I + 3) & 3];
+        const f2 y3 = mul2(H6, stage_t2(CT[(I + 3) & 3], CC, x, Q[(I + 2) & 3], Q[I & 3]));
+        const f2 kb3 = fma2(H, y3, mul2(H3, x));
+        KB3[(I + 3) & 3] = kb3;
+        LN[(I + 3) & 3] = add2(x, y3);
+        GG[(I + 3) & 3] = fma2(C2, kb3, mul2(C4H6, x));
+      }
+      // stage B on row i-2: Y2 = A^T kbar3
+      {
+        const f2 y2 = stage_t2(CT[(I + 2) & 3], CC, KB3[(I + 2) & 3], KB3[(I + 1) & 3], KB3[(I + 3) & 3]);
+        const f2 kb2 = fma2(H2, y2, mul2(H3, Q[(I + 2) & 3]));
+        KB2[(I + 2) & 3] = kb2;
+        LN[(I + 2) & 3] = add2(LN[(I + 2) & 3], y2);
+        GG[(I + 2) & 3] = fma2(C2, kb2, GG[(I + 2) & 3]);
+      }
+      // stage C on row i-3: Y1 = A^T kbar2
+      {
+        const f2 y1 = stage_t2(CT[(I + 1) & 3], CC, KB2[(I + 1) & 3], KB2[I & 3], KB2[(I + 2) & 3]);
+        const f2 kb1 = fma2(H2, y1, mul2(H6, Q[(I + 1) & 3]));
+        KB1[(I + 1) & 3] = kb1;
+        LN[(I + 1) & 3] = add2(LN[(I + 1) & 3], y1);
+        GG[(I + 1) & 3] = fma2(C1, kb1, GG[(I + 1) & 3]);
+      }
+      // stage D on row i-4: lambda_new = Ln + A^T kbar1 (+ source)
+      {
+        const f2 y0 = stage_t2(CT[I & 3], CC, KB1[I & 3], KB1[(I + 3) & 3], KB1[(I + 1) & 3]);
+        f2 lam = add2(LN[I & 3], y0);
+        if (add_src) lam = fma2(SRC, sv, lam);
+        if (i0 >= 8) {  // output row i - 8 of the segment
+          const int yd = tk.Y0 + i - 8;
+          if (out_col) {
+            if (INNER) {
+              *reinterpret_cast<f2*>(orow) = lam;
+            } else {
+              put_point(qo, p.Wp, p.nx, p.ny, xd, yd, lo_of(lam));
+              put_point(qo, p.Wp, p.nx, p.ny, xd + 1, yd, hi_of(lam));
+            }
+          }
+          if (own_col && yd >= tk.own_y0) {
+            const f2 g = GG[I & 3];
+            *reinterpret_cast<double2*>(grow) =
+                make_double2(gold.x + (double)lo_of(g), gold.y + (double)hi_of(g));
+          }
+          orow += p.Wp;
+          grow += p.nx;
+        }
+      }
+      CT[I & 3].e = te;  // row i (slot of row i-4, used above for the last time)
+      CT[I & 3].w = tw;
+      CT[I & 3].n = tn;
+      CT[I & 3].s = ts;
+    }
+  }
+  if (!ok) {
+    if (t == 0) set_status(status, PXA_ERR_TIMEOUT);
+    for (int s = 0; s < NB && s < nblocks; ++s) {
+      const int last = s + NB * ((nblocks - 1 - s) / NB);
+      (void)bar_wait(&bars[s], (uint32_t)((last / NB) & 1));
+    }
+  }
+}
+
 }  // namespace
 
 // s(t) at the three stage times of steps s0 .. s0+count-1: sc[3j + {0,1,2}] (FP64 sin,
@@ -306,6 +471,52 @@ __global__ void __launch_bounds__(32 * RWARPS, 2) ad2_rk4_roll_kernel(
     roll_task<false>(&qmap, &cmap, p, tk, qo, ring, wb, Hs, c1, c2, c4, status);
 }
 
+// One reverse step for lanes lane0 .. lane0 + count - 1 of `lanes`: lane l reads buffer
+// buf_in and writes the other; it is at absolute step zsrc0 + l * z_stride (its source row
+// in the trajectory, and its forcing factors sc[3 (zsrc0 + l * z_stride) + {0, 1, 2}]).
+__global__ void __launch_bounds__(32 * TWARPS, 3) ad2_rk4T_roll_kernel(
+    const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap tmap,
+    const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap gmap, Ad2Params p,
+    float* __restrict__ states, double* __restrict__ G, int lanes, int lane0, int count, int buf_in,
+    int nstrips, int nsegs, int Hs, const float* __restrict__ sc, int zsrc0, int z_stride, float src_scale,
+    int add_src, int* status) {
+  extern __shared__ __align__(1024) float rsm[];
+  __shared__ __align__(8) uint64_t bars[TWARPS * NB];
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int task = blockIdx.x * TWARPS + warp;
+  if (task >= count * nstrips * nsegs) return;  // whole warps only: no block barrier below
+  uint64_t* wb = bars + warp * NB;
+  if (t == 0) {
+    for (int j = 0; j < NB; ++j)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wb[j])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  RollTTask tk;
+  tk.l = lane0 + task % count;
+  const int rest = task / count;
+  const int sx = rest % nstrips, sy = rest / nstrips;
+  tk.X0 = min(sx * RS, p.nx - RS);
+  tk.Y0 = min(sy * Hs, p.ny - Hs);
+  tk.own_x0 = sx * RS;  // the last strip and segment overlap the previous ones: the points
+  tk.own_y0 = sy * Hs;  // before these are that task's to update in G
+  tk.buf_in = buf_in;
+  tk.lanes = lanes;
+  tk.zsrc = zsrc0 + tk.l * z_stride;
+  const size_t plane = (size_t)p.Hp * p.Wp;
+  float* qo = states + ((size_t)(1 - buf_in) * lanes + tk.l) * plane;
+  const float* scl = sc + 3 * (size_t)tk.zsrc;
+  const float c1 = scl[0], c2 = scl[1], c4 = scl[2];
+  float* ring = rsm + (size_t)warp * TRING_FLOATS;
+  const bool inner = tk.X0 >= G2 && tk.X0 + RS <= p.nx - G2 && tk.Y0 >= G2 && tk.Y0 + Hs <= p.ny - G2;
+  if (inner)
+    rollT_task<true>(&qmap, &tmap, &smap, &gmap, p, tk, qo, G, ring, wb, Hs, c1, c2, c4, src_scale,
+                     add_src != 0, status);
+  else
+    rollT_task<false>(&qmap, &tmap, &smap, &gmap, p, tk, qo, G, ring, wb, Hs, c1, c2, c4, src_scale,
+                      add_src != 0, status);
+}
+
 int ad2_roll_rows(int ny) {
   int hs = 128;
   while (hs > 8 && hs > ny) hs /= 2;
@@ -337,6 +548,25 @@ cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const 
   if (e != cudaSuccess) return e;
   ad2_rk4_roll_kernel<<<blocks, 32 * RWARPS, sh, st>>>(qmap, cmap, p, states, lanes, buf_in, nstrips, nsegs,
                                                        Hs, sc, sc_stride, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& tmap,
+                                 const CUtensorMap& smap, const CUtensorMap& gmap, const Ad2Params& p,
+                                 float* states, double* G, int lanes, int lane0, int count, int buf_in,
+                                 const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
+                                 int* status) {
+  if (count <= 0 || lane0 < 0 || lane0 + count > lanes) return cudaErrorInvalidValue;
+  const int Hs = ad2_roll_rows(p.ny);
+  const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
+  const long long tasks = (long long)count * nstrips * nsegs;
+  const unsigned blocks = (unsigned)((tasks + TWARPS - 1) / TWARPS);
+  const size_t sh = sizeof(float) * (size_t)TWARPS * TRING_FLOATS;
+  cudaError_t e = cudaFuncSetAttribute(ad2_rk4T_roll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  ad2_rk4T_roll_kernel<<<blocks, 32 * TWARPS, sh, st>>>(qmap, tmap, smap, gmap, p, states, G, lanes, lane0,
+                                                         count, buf_in, nstrips, nsegs, Hs, sc, zsrc0, z_stride,
+                                                         src_scale, add_src, status);
   return cudaGetLastError();
 }
 

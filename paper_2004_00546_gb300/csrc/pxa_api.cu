@@ -443,6 +443,11 @@ struct pxa_ctx {
   double* G2buf = nullptr;  // [P][ny*nx] FP64 lane gradients
   double* GC = nullptr;     // [ny*nx] FP64 chain gradient
   CUtensorMap mapD, mapA, mapC, mapCoef;
+  // adjoint lanes as a register wavefront (P > 1, grids the wavefront covers)
+  bool roll2 = false;
+  float* tcoef2 = nullptr;  // [4][Hp][Wp] coefficients of A^T
+  float* sc2 = nullptr;     // [K][3] s(t) at the stage times of every step
+  CUtensorMap mapA4, mapT4, mapS4, mapG4;
   float* stL = nullptr;     // pxa_rk4_lanes_2d states [2][lanesL][Hp][Wp]
   int lanesL = 0;
   float* scL = nullptr;     // pxa_rk4_lanes_2d forcing factors [lanes * steps][3]
@@ -506,7 +511,8 @@ void release_workspace(pxa_ctx* c) {
   c->lanes1d = 0;
   c->V = c->traj = c->scratch = c->Jdev = c->errmax = c->ctl_buf = c->grad_buf = nullptr;
   c->status = nullptr;
-  c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = nullptr;
+  c->coef2 = c->stD = c->stA = c->stC = c->traj2 = c->stL = c->tcoef2 = c->sc2 = nullptr;
+  c->roll2 = false;
   c->lanesL = 0;
   c->rpT = nullptr;
   c->colT = nullptr;
@@ -664,6 +670,16 @@ int prepare(pxa_ctx* c) {
     if (!ad2_make_map(&c->mapD, c->stD, a, 2, 1) || !ad2_make_map(&c->mapA, c->stA, a, 2 * P, 1) ||
         !ad2_make_map(&c->mapC, c->stC, a, 2, 1) || !ad2_make_map(&c->mapCoef, c->coef2, a, 3, 3))
       return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D state arrays");
+    c->roll2 = P > 1 && ad2_roll_ok(a);
+    if (c->roll2) {
+      if ((rc = alloc(c, &c->tcoef2, 4 * plane))) return rc;
+      if ((rc = alloc(c, &c->sc2, (size_t)3 * c->K))) return rc;
+      if (!ad2_make_map_box(&c->mapA4, c->stA, a, 2 * P, 64, AD2_ROLL_BR, 1) ||
+          !ad2_make_map_box(&c->mapT4, c->tcoef2, a, 4, 64, AD2_ROLL_BR, 4) ||
+          !ad2_make_map_plain(&c->mapS4, c->traj2, 4, a.nx, a.ny, (int)c->K + 1, 64, AD2_ROLL_BR) ||
+          !ad2_make_map_plain(&c->mapG4, c->G2buf, 8, a.nx, a.ny, P, 64, AD2_ROLL_BR))
+        return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D adjoint lanes");
+    }
   } else if (c->op.kind == PXA_ADVDIFF_1D) {
     double dt = c->T / (double)c->K;
     cn_band_taps(n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r);
@@ -1527,10 +1543,23 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   // Eq. hybadjinhom: lane l starts from the objective's source at its top row (l+1) k
   PXA_CUDA(c, launch_ad2_fill(st, a, c->stA, P, c->traj2, k, k, src), "lane init");
   const int lpc = P >= 16 ? 16 : P;
+  // the lanes as a register wavefront where the grid allows it, else on halo tiles
+  const bool roll = c->roll2 && P > 1;
+  if (roll) {
+    PXA_CUDA(c, launch_ad2_pack_coefT(st, a, c->op.u_dev, c->op.v_dev, c->tcoef2), "A^T coefficients");
+    PXA_CUDA(c, launch_ad2_forcing_table(st, 0, K, a.dtd, a.omega, c->sc2), "forcing table");
+  }
   for (int64_t j = 0; j < k; ++j) {
-    PXA_CUDA(c, launch_ad2_rk4T(st, c->mapA, c->mapCoef, a, c->stA, P, P, lpc, (int)(j & 1), k, 0,
-                                k - 1 - j, 1, c->traj2, src, c->G2buf, c->status),
-             "2d adjoint lanes");
+    const int64_t s_local = k - 1 - j;  // lane l at step l k + s_local
+    if (roll)
+      PXA_CUDA(c, launch_ad2_rk4T_roll(st, c->mapA4, c->mapT4, c->mapS4, c->mapG4, a, c->stA, c->G2buf, P, 0, P,
+                                       (int)(j & 1), c->sc2, (int)s_local, (int)k, (float)src, s_local > 0 ? 1 : 0,
+                                       c->status),
+               "2d adjoint lanes");
+    else
+      PXA_CUDA(c, launch_ad2_rk4T(st, c->mapA, c->mapCoef, a, c->stA, P, P, lpc, (int)(j & 1), k, 0, s_local, 1,
+                                  c->traj2, src, c->G2buf, c->status),
+               "2d adjoint lanes");
   }
   ev_record(c, 3);
   if (P > 1) {

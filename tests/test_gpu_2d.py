@@ -68,8 +68,12 @@ def test_rk4_lanes_match_oracle_steps(env, n):
         assert rel(got[l], q) < 1e-5
 
 
-@pytest.mark.parametrize("n,K,P", [(64, 48, 6), (72, 40, 4), (8, 30, 3)])
+@pytest.mark.parametrize("n,K,P", [(64, 48, 6), (72, 40, 4), (8, 30, 3), (120, 24, 4)])
 def test_gradient_serial_and_paraexp_match_oracle(env, n, K, P):
+    """Serial and Paraexp gradients against the oracle. The adjoint lanes run as a
+    register wavefront on 56-column strips and row segments from 64 points on: at 64,
+    72 and 120 the last strip (and at 72 and 120 the last segment) overlaps the one
+    before it, and only its own points add to the lane gradients."""
     torch, X = env
     nu, T = 0.02, 0.3
     u, v, f, ft = problem(n)
