@@ -499,6 +499,7 @@ def run_bu2(args, w, rank, world):
         times, phases, g = time_mode(X, torch, ctx, X.PARAEXP, args.steps, args.warmup, flush, timing=True)
     total_ms = reduce_max(float(sum(times)))
     ph = {k: float(np.mean([p[k] for p in phases])) for k in ("ms_direct_inhom", "ms_adjoint_hom", "ms_total")}
+    graph_kernels = ctx.stats()["graph_kernels"]  # kernels of the timed graph replays
     # end to end through the host-buffer entry point
     ctx.set_timing(False)
     n2 = 2 * w["n"] * w["n"]
@@ -552,7 +553,8 @@ def run_bu2(args, w, rank, world):
             "cpu_baseline": cpu,
             "e2e": {"value": world / float(np.mean(te)), "unit": "gradient evals/s", "h2d_bytes_per_step": 8 * n2,
                     "d2h_bytes_per_step": 8 * n2 + 8},
-            "clocks": clk.summary(), "gpu_launches": (2 * w["K"] + 6) * args.steps}
+            "clocks": clk.summary(),
+            "gpu_launches": (graph_kernels * args.steps) if graph_kernels > 0 else (2 * w["K"] + 6) * args.steps}
     ctx.close()
     return line
 
@@ -830,10 +832,9 @@ def run_ours(args, w, rank, world):
         roof.update({"issue_floor_ms": floors[dom], "frac_of_issue_floor": floors[dom] / ms_dom})
     roof["kernels_ms"] = {kk: v[0] for kk, v in kernels.items()}
 
-    if w["kind"] == "burgers1d":
-        launches_per_step = (6 if st["adjoint_band"] else 4) + (1 if w.get("omega", 0.0) else 0)
-    else:
-        launches_per_step = 7
+    # kernels one graph replay (one timed gradient) launches: the kernel nodes of the
+    # captured graph, as the library counted them
+    launches_per_step = st["graph_kernels"] if st["graph_kernels"] > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "gradient evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -843,7 +844,8 @@ def run_ours(args, w, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "variants": variants, "phases_ms": ph, "phases_source": phases_source, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "paraexp_vs_serial": comparison,
-        "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "gpu_launches": None if launches_per_step is None else launches_per_step * args.steps,
     }
     ctx.close()
     return line
@@ -1246,7 +1248,7 @@ def run_2d(args, w, rank, world):
             "vs_baseline": None, "dtype": "f32 stepping, f64 accumulation", "data": "synthetic",
             "config": {"workload": w["label"].replace("512x512", f"{n}x{n}"), "l2": "flushed between steps"},
             "variants": variants, "phases_ms": ph, "cpu_baseline": cpu, "clocks": clk.summary(),
-            "gpu_launches": None}
+            "gpu_launches": (ctx.stats()["graph_kernels"] * args.steps) or None}
 
 
 def run_batch(args, w, rank, world):
@@ -1326,8 +1328,8 @@ def run_batch(args, w, rank, world):
         # per direction one chain launch for each kind of homogeneous propagation in use
         kinds = sum(1 for c in (st["krylov_problems"], st["power_problems"],
                                 cnt - st["krylov_problems"] - st["power_problems"]) if c > 0)
-        variants[name]["kernels_per_step"] = (4 if mode == X.SERIAL else 1 if st["one_launch"]
-                                              else 5 + 2 * kinds)
+        variants[name]["kernels_per_step"] = (st["graph_kernels"] if st["graph_kernels"] > 0 else
+                                              4 if mode == X.SERIAL else 1 if st["one_launch"] else 5 + 2 * kinds)
         bats[name] = b
     head = "paraexp"
     ms = variants[head]["ms_per_step"]

@@ -218,6 +218,8 @@ typedef struct {
   float ms_side_pair;
   float ms_side_quad;
   float ms_side_lanes;
+  int graph_kernels;        /* kernel nodes of the gradient's captured CUDA graph (the
+                               kernels one graph replay launches; 0: no graph captured) */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -534,6 +536,7 @@ typedef struct {
   int lane_steps;           /* q: the lanes apply the band of M^q, q CN steps at a time */
   int one_launch;           /* 1 when the last gradient ran as one persistent launch */
   int flow_grid;            /* thread blocks of that launch */
+  int graph_kernels;        /* kernel nodes of the gradient's captured CUDA graph (0: none) */
 } pxa_batch_stats;
 /* Create / destroy a batch context on `device`; `cuda_stream` is borrowed (NULL = the
  * default stream). */

@@ -8,6 +8,9 @@
 
 namespace pxa {
 
+// Kernel nodes of a captured CUDA graph (-1 if the graph cannot be read).
+int graph_kernel_nodes(cudaGraph_t g);
+
 constexpr int kMaxM = 48;           // largest Krylov dimension
 constexpr int kDMax = kMaxM + 2;    // dense scratch: (m+1) plus the phi_1 augmentation
 constexpr int kLD = kDMax;          // leading dimension of dense scratch matrices

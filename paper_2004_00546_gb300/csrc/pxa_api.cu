@@ -20,6 +20,25 @@ using namespace pxa;
 
 namespace pxa {
 
+int graph_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
 template <typename Real>
 static void cn_band_taps_t(int n, double am, double a0, double ap, double dt, int cut_exp,
                            std::vector<double>& taps, int& r) {
@@ -2118,6 +2137,7 @@ int pxa_gradient_async(pxa_ctx* c, int mode, double* J_dev, double* grad_dev) {
         return erc;
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      c->stats.graph_kernels = graph_kernel_nodes(graph);
       // kernel nodes keep their own priorities (the direct above the overlapped side work)
       e = cudaGraphInstantiateWithFlags(&c->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(graph);

@@ -65,6 +65,7 @@ struct pxa_batch {
   int schedule = 1;          // requested: 1 = one launch when no problem uses Krylov, 0 = phases
   int4* items_flow = nullptr;
   int n_flow = 0, flow_grid = 0;
+  int graph_kernels = 0;  // kernel nodes of the captured gradient graph
   int* flow_state = nullptr;  // [1 + 4 count]: queue counter, per-problem counters
   bool flow_last = false;     // the last gradient ran as one launch
   double *src = nullptr, *E = nullptr, *EA = nullptr, *h = nullptr, *hA = nullptr, *qT = nullptr,
@@ -598,6 +599,7 @@ int pxa_batch_gradient(pxa_batch* b, int mode, const double* q0_dev, double* J_d
       return erc;
     }
     BCUDA(b, e, "end capture");
+    b->graph_kernels = graph_kernel_nodes(g);
     const cudaError_t ei = cudaGraphInstantiate(&b->gexec, g, 0);
     cudaGraphDestroy(g);
     BCUDA(b, ei, "graph instantiate");
@@ -717,6 +719,7 @@ int pxa_batch_get_stats(const pxa_batch* b, pxa_batch_stats* out) {
   s.lanes_grid = b->lanes_grid;
   s.one_launch = b->flow_last ? 1 : 0;
   s.flow_grid = b->flow_grid;
+  s.graph_kernels = b->graph_kernels;
   s.krylov_err_max = b->err_last;
   s.workspace_bytes = b->bytes;
   s.krylov_problems = b->n_kry;

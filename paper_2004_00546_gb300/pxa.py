@@ -80,7 +80,8 @@ class Stats(ctypes.Structure):
                 ("lane_steps", ctypes.c_int), ("lane_band_taps", ctypes.c_int),
                 ("prop_band_taps", ctypes.c_int), ("side_chunks", ctypes.c_int),
                 ("ms_side_prepass", ctypes.c_float), ("ms_side_pair", ctypes.c_float),
-                ("ms_side_quad", ctypes.c_float), ("ms_side_lanes", ctypes.c_float)]
+                ("ms_side_quad", ctypes.c_float), ("ms_side_lanes", ctypes.c_float),
+                ("graph_kernels", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):
@@ -93,7 +94,7 @@ class BatchStats(ctypes.Structure):
                 ("ms_adjoint_lanes", ctypes.c_float), ("ms_adjoint_chains", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("power_problems", ctypes.c_int),
                 ("band_power_max", ctypes.c_int), ("lane_steps", ctypes.c_int), ("one_launch", ctypes.c_int),
-                ("flow_grid", ctypes.c_int)]
+                ("flow_grid", ctypes.c_int), ("graph_kernels", ctypes.c_int)]
 
 
 _lib = None

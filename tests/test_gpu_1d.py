@@ -187,6 +187,9 @@ def test_c1_graph_replay_and_host_entry(X, torch, c1_oracle):
     J3 = ctx.gradient(X.PARAEXP, g2)  # replay of the captured graph
     assert J1 == J2 == J3
     assert torch.equal(g1, g2)
+    # the captured graph's kernel nodes: at least the lanes, the chain and a superposition
+    # in each direction
+    assert ctx.stats()["graph_kernels"] >= 6
     gh = np.empty(C1["n"])
     Jh = ctx.gradient_host(X.PARAEXP, np.ascontiguousarray(p["q0"]), gh)
     assert Jh == J1

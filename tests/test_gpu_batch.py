@@ -278,7 +278,7 @@ def test_batch_one_launch_equals_the_phases(X, torch, small, K, P):
     oracle's gradients within the FP32 tolerance."""
     q0 = dev(torch, small["q0"])
     nprob = len(small["n"])
-    res = {}
+    res, kernels = {}, {}
     for sched, graph in ((0, True), (1, True), (1, False)):
         b = X.Batch()
         b.set(small["n"], small["nu"], c=small["c"], T=small["T"], K=K, P=P)
@@ -291,11 +291,14 @@ def test_batch_one_launch_equals_the_phases(X, torch, small, K, P):
             b.gradient(X.PARAEXP, q0, J, g)
         b.sync()
         assert b.stats()["one_launch"] == sched
+        kernels[(sched, graph)] = b.stats()["graph_kernels"]
         res[(sched, graph)] = (J.cpu().numpy(), g.cpu().numpy())
         off = b.offsets()
         b.close()
     for key in ((1, True), (1, False)):
         assert np.array_equal(res[key][0], res[(0, True)][0]) and np.array_equal(res[key][1], res[(0, True)][1])
+    # the captured graphs' kernel nodes: one persistent launch against the phases' launches
+    assert 1 <= kernels[(1, True)] < kernels[(0, True)]
     tol = 1e-4 if K <= 512 else 2 * K * 2.0 ** -24
     J, g = res[(1, True)]
     for i in range(nprob):
