@@ -74,6 +74,11 @@ def lib():
                 "pxo_ad2_rk4_step": [_i, _i, _d, _d, _p, _p, _d, _d, _d, _p, _p, _p],
                 "pxo_ad2_gradient_serial": [_i, _i, _d, _d, _p, _p, _d, _i64, _d, _p, _p, _p, _p],
                 "pxo_csr_transpose": [_i64, _p, _p, _p, _p, _p, _p],
+                "pxo_rk4_power_coeffs": [_i, _p],
+                "pxo_rk4_forcing_coeffs": [_i, _d, _d, _d, _p],
+                "pxo_ad2_poly_apply": [_i, _i, _d, _d, _p, _p, _d, _i, _i, _p, _p, _p],
+                "pxo_ad2_gradient_hybrid_poly": [_i, _i, _d, _d, _p, _p, _d, _i64, _d, _p, _p, _i, _i, _p,
+                                                 _p],
                 "pxo_bu2_rhs": [_i, _d, _d, _p, _p, _p, _p],
                 "pxo_bu2_jac": [_i, _d, _d, _p, _p, _p, _p, _p, _p],
                 "pxo_bu2_jac_T": [_i, _d, _d, _p, _p, _p, _p, _p, _p],
@@ -312,6 +317,44 @@ def ad2_gradient_serial(f, f_true, u, v, nu, T, K, omega=1.0, L=TWO_PI):
     g = np.empty_like(f)
     _check(lib().pxo_ad2_gradient_serial(nx, ny, L, nu, _ptr(u), _ptr(v), T, int(K), omega, _ptr(f),
                                          _ptr(ft), ctypes.byref(J), _ptr(g)), "ad2_serial")
+    return J.value, g
+
+
+# ---- polynomial propagator of the homogeneous parts (RK4 stepper's power series) ----
+def rk4_power_coeffs(k):
+    """Coefficients a[0..4k] of R(z)^k, R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24."""
+    a = np.empty(4 * k + 1)
+    _check(lib().pxo_rk4_power_coeffs(int(k), _ptr(a)), "rk4_power_coeffs")
+    return a
+
+
+def rk4_forcing_coeffs(k, dt, t0, omega):
+    """Coefficients b[0..4k-1] of the forcing-gradient polynomial of k RK4 steps from t0."""
+    b = np.empty(4 * k)
+    _check(lib().pxo_rk4_forcing_coeffs(int(k), dt, t0, omega, _ptr(b)), "rk4_forcing_coeffs")
+    return b
+
+
+def ad2_poly_apply(x, u, v, nu, dt, coeffs, transpose=False, L=TWO_PI):
+    """sum_j coeffs[j] (dt A)^j x (A^T with transpose) for the 2D operator."""
+    x, u, v, c = _in(x), _in(u), _in(v), _in(coeffs)
+    ny, nx = x.shape
+    out = np.empty_like(x)
+    _check(lib().pxo_ad2_poly_apply(nx, ny, L, nu, _ptr(u), _ptr(v), dt, int(bool(transpose)), len(c) - 1,
+                                    _ptr(c), _ptr(x), _ptr(out)), "ad2_poly_apply")
+    return out
+
+
+def ad2_gradient_hybrid_poly(f, f_true, u, v, nu, T, K, P, m, omega=1.0, L=TWO_PI):
+    """Hybrid loop with the homogeneous adjoint by the power series cut after degree m
+    (m <= 0: the whole polynomials, i.e. serial stepping reorganised)."""
+    f, ft, u, v = _in(f), _in(f_true), _in(u), _in(v)
+    ny, nx = f.shape
+    J = ctypes.c_double()
+    g = np.empty_like(f)
+    _check(lib().pxo_ad2_gradient_hybrid_poly(nx, ny, L, nu, _ptr(u), _ptr(v), T, int(K), omega, _ptr(f),
+                                              _ptr(ft), int(P), int(m), ctypes.byref(J), _ptr(g)),
+           "ad2_hybrid_poly")
     return J.value, g
 
 

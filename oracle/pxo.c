@@ -1211,6 +1211,187 @@ int pxo_ad2_gradient_serial(int nx, int ny, double L, double nu, const double* u
 }
 
 /* ------------------------------------------------------------------------- */
+/* Homogeneous parts by a polynomial propagator (Eq. hom / Eq. adjHomNormal  */
+/* with a propagator that needs only operator applications, as the paper's  */
+/* ReLPM of Sec. 4.1 does). The stepper's own propagator over a subinterval  */
+/* of k classical RK4 steps is the polynomial R(dt A)^k,                     */
+/*   R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24,                                  */
+/* of degree 4k; its power series is cut after degree m. The forcing         */
+/* gradient that the homogeneous adjoint contributes over the subinterval    */
+/* (Eq. paramupdate summed over its steps) is a second polynomial in the     */
+/* same operator:                                                            */
+/*   b(z) = sum_{j=0}^{k-1} g_j(z) R(z)^{k-1-j},                             */
+/*   g_j(z) = dt [ (s1 + 4 s2 + s4)/6 + z (s1/6 + s2/3) + z^2 (s1 + s2)/12    */
+/*               + z^3 s1/24 ],                                              */
+/* where g_j(dt A) = d u_{j+1} / d f is the derivative of RK4 step j of      */
+/* du/dt = A u + s(t) f with respect to f (s1, s2, s4 = s(t) at the step's   */
+/* stage times t_j, t_j + dt/2, t_j + dt), and b(dt A^T) h is the sum of     */
+/* g_j(dt A)^T lambda_{j+1} along the homogeneous adjoint                    */
+/* lambda_j = R(dt A)^T lambda_{j+1} started from h at the subinterval's end.*/
+/* ------------------------------------------------------------------------- */
+
+/* c (degree da + db) = a (degree da) * b (degree db), long double. */
+static void poly_mul_ld(const long double* a, int da, const long double* b, int db, long double* c) {
+  for (int i = 0; i <= da + db; ++i) c[i] = 0.0L;
+  for (int i = 0; i <= da; ++i)
+    for (int j = 0; j <= db; ++j) c[i + j] += a[i] * b[j];
+}
+
+/* pw[j][0..4j] = coefficients of R(z)^j for j = 0..k (pw: (k+1) x (4k+1), zero padded). */
+static void rk4_powers_ld(int k, long double* pw) {
+  const long double R[5] = {1.0L, 1.0L, 0.5L, 1.0L / 6.0L, 1.0L / 24.0L};
+  const int w = 4 * k + 1;
+  for (int i = 0; i < (k + 1) * w; ++i) pw[i] = 0.0L;
+  pw[0] = 1.0L;
+  for (int j = 1; j <= k; ++j) poly_mul_ld(pw + (size_t)(j - 1) * w, 4 * (j - 1), R, 4, pw + (size_t)j * w);
+}
+
+int pxo_rk4_power_coeffs(int k, double* a) {
+  if (k < 1 || !a) return -1;
+  const int w = 4 * k + 1;
+  long double* pw = malloc(sizeof(long double) * (size_t)(k + 1) * w);
+  if (!pw) return -1;
+  rk4_powers_ld(k, pw);
+  for (int i = 0; i < w; ++i) a[i] = (double)pw[(size_t)k * w + i];
+  free(pw);
+  return 0;
+}
+
+int pxo_rk4_forcing_coeffs(int k, double dt, double t0, double omega, double* b) {
+  if (k < 1 || !b || !(dt > 0.0)) return -1;
+  const int w = 4 * k + 1;
+  long double* pw = malloc(sizeof(long double) * (size_t)(k + 1) * w);
+  long double* acc = malloc(sizeof(long double) * (size_t)w);
+  long double* term = malloc(sizeof(long double) * (size_t)(w + 3));
+  if (!pw || !acc || !term) {
+    free(pw); free(acc); free(term);
+    return -1;
+  }
+  rk4_powers_ld(k, pw);
+  for (int i = 0; i < w; ++i) acc[i] = 0.0L;
+  for (int j = 0; j < k; ++j) {
+    double t = t0 + j * dt;
+    long double s1 = forcing_s(omega, t), s2 = forcing_s(omega, t + 0.5 * dt), s4 = forcing_s(omega, t + dt);
+    long double g[4] = {(long double)dt * (s1 + 4.0L * s2 + s4) / 6.0L, (long double)dt * (s1 / 6.0L + s2 / 3.0L),
+                        (long double)dt * (s1 + s2) / 12.0L, (long double)dt * s1 / 24.0L};
+    const int e = k - 1 - j; /* g_j(z) R(z)^e, degree 3 + 4e <= 4k - 1 */
+    poly_mul_ld(g, 3, pw + (size_t)e * w, 4 * e, term);
+    for (int i = 0; i <= 3 + 4 * e; ++i) acc[i] += term[i];
+  }
+  for (int i = 0; i < 4 * k; ++i) b[i] = (double)acc[i];
+  free(pw); free(acc); free(term);
+  return 0;
+}
+
+int pxo_ad2_poly_apply(int nx, int ny, double L, double nu, const double* u, const double* v, double dt,
+                       int transpose, int m, const double* c, const double* x, double* out) {
+  if (bad_grid2(nx, ny, L) || !u || !v || m < 0 || !c || !x || !out) return -1;
+  size_t N = (size_t)nx * ny, nb = sizeof(double) * N;
+  double *p = malloc(nb), *q = malloc(nb);
+  if (!p || !q) {
+    free(p); free(q);
+    return -1;
+  }
+  memcpy(p, x, nb);                                   /* p = (dt A)^0 x */
+  for (size_t i = 0; i < N; ++i) out[i] = c[0] * p[i];
+  for (int j = 1; j <= m; ++j) {                      /* p = (dt A)^j x */
+    if (transpose) pxo_ad2_apply_T(nx, ny, L, nu, u, v, p, q);
+    else pxo_ad2_apply(nx, ny, L, nu, u, v, p, q);
+    for (size_t i = 0; i < N; ++i) p[i] = dt * q[i];
+    for (size_t i = 0; i < N; ++i) out[i] += c[j] * p[i];
+  }
+  free(p); free(q);
+  return 0;
+}
+
+/* One reverse step of the exact discrete adjoint of the RK4 map (as in the serial loop
+ * above): lam <- R(dt A)^T lam, grad += g_s(dt A)^T lam (the stage terms at the
+ * incoming lam), no objective source. */
+static void ad2_adjoint_step(int nx, int ny, double L, double nu, const double* u, const double* v,
+                             double dt, double t, double omega, double* lam, double* grad,
+                             double* mu, double* nv, double* acc) {
+  size_t N = (size_t)nx * ny;
+  double s1 = forcing_s(omega, t), s2 = forcing_s(omega, t + 0.5 * dt), s4 = forcing_s(omega, t + dt);
+  for (size_t i = 0; i < N; ++i) acc[i] = lam[i];
+  for (size_t i = 0; i < N; ++i) mu[i] = dt / 6.0 * lam[i];            /* kbar4 */
+  for (size_t i = 0; i < N; ++i) grad[i] += s4 * mu[i];
+  pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);
+  for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 3.0 * lam[i] + dt * nv[i]; }
+  for (size_t i = 0; i < N; ++i) grad[i] += s2 * mu[i];              /* kbar3 */
+  pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);
+  for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 3.0 * lam[i] + 0.5 * dt * nv[i]; }
+  for (size_t i = 0; i < N; ++i) grad[i] += s2 * mu[i];              /* kbar2 */
+  pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);
+  for (size_t i = 0; i < N; ++i) { acc[i] += nv[i]; mu[i] = dt / 6.0 * lam[i] + 0.5 * dt * nv[i]; }
+  for (size_t i = 0; i < N; ++i) grad[i] += s1 * mu[i];              /* kbar1 */
+  pxo_ad2_apply_T(nx, ny, L, nu, u, v, mu, nv);
+  for (size_t i = 0; i < N; ++i) lam[i] = acc[i] + nv[i];
+}
+
+int pxo_ad2_gradient_hybrid_poly(int nx, int ny, double L, double nu, const double* u, const double* v,
+                                 double T, int64_t K, double omega, const double* f, const double* f_true,
+                                 int P, int m, double* J, double* grad) {
+  if (bad_grid2(nx, ny, L) || K < 1 || P < 1 || K % P != 0 || !u || !v || !f || !f_true || !J || !grad)
+    return -1;
+  const int64_t k = K / P;
+  const int deg = 4 * (int)k;
+  if (m <= 0 || m > deg) m = deg;
+  size_t N = (size_t)nx * ny, nb = sizeof(double) * N;
+  double dt = T / (double)K, src = 2.0 * dt / T;
+  double *d = malloc(nb), *traj = malloc(nb * (size_t)(K + 1));
+  double *lam = malloc(nb), *mu = malloc(nb), *nv = malloc(nb), *acc = malloc(nb);
+  double *W = malloc(nb * (size_t)P), *h = malloc(nb), *hp = malloc(nb), *pw = malloc(nb), *q = malloc(nb);
+  double *a = malloc(sizeof(double) * (size_t)(deg + 1)), *b = malloc(sizeof(double) * (size_t)deg);
+  if (!d || !traj || !lam || !mu || !nv || !acc || !W || !h || !hp || !pw || !q || !a || !b) return -1;
+  /* Eq. seriesDirect: serial RK4 of the response to f - f_true, every state kept */
+  for (size_t i = 0; i < N; ++i) d[i] = f[i] - f_true[i];
+  memset(traj, 0, nb);
+  double Jacc = 0.0;
+  for (int64_t s = 0; s < K; ++s) {
+    pxo_ad2_rk4_step(nx, ny, L, nu, u, v, dt, s * dt, omega, d, traj + (size_t)s * N,
+                     traj + (size_t)(s + 1) * N);
+    double sq = 0.0;
+    for (size_t i = 0; i < N; ++i) sq += traj[(size_t)(s + 1) * N + i] * traj[(size_t)(s + 1) * N + i];
+    Jacc += dt / T * sq;
+  }
+  *J = Jacc;
+  memset(grad, 0, nb);
+  /* Eq. hybadjinhom: lane p from zero at its top row (p+1)k, where it takes the
+   * objective's source, down to row pk, adding the source of rows pk+1 .. (p+1)k-1 */
+  for (int p = 0; p < P; ++p) {
+    int64_t top = (int64_t)(p + 1) * k;
+    for (size_t i = 0; i < N; ++i) lam[i] = src * traj[(size_t)top * N + i];
+    for (int64_t s = top - 1; s >= (int64_t)p * k; --s) {
+      ad2_adjoint_step(nx, ny, L, nu, u, v, dt, s * dt, omega, lam, grad, mu, nv, acc);
+      if (s > (int64_t)p * k)
+        for (size_t i = 0; i < N; ++i) lam[i] += src * traj[(size_t)s * N + i];
+    }
+    memcpy(W + (size_t)p * N, lam, nb); /* w_p = lambda_{I,p} at row pk */
+  }
+  /* Eq. adjHomNormal, local form: h carries the summed homogeneous problems from
+   * subinterval P-2 down to 0, h <- a(dt A^T)(h + w_{p+1}); their forcing gradient over
+   * subinterval p is b_p(dt A^T)(h + w_{p+1}) (a, b cut after degree m) */
+  memset(h, 0, nb);
+  pxo_rk4_power_coeffs((int)k, a);
+  for (int p = P - 2; p >= 0; --p) {
+    pxo_rk4_forcing_coeffs((int)k, dt, (double)p * k * dt, omega, b);
+    for (size_t i = 0; i < N; ++i) hp[i] = h[i] + W[(size_t)(p + 1) * N + i];
+    memcpy(pw, hp, nb);
+    for (size_t i = 0; i < N; ++i) { h[i] = a[0] * pw[i]; grad[i] += b[0] * pw[i]; }
+    for (int j = 1; j <= m; ++j) {
+      pxo_ad2_apply_T(nx, ny, L, nu, u, v, pw, q);
+      for (size_t i = 0; i < N; ++i) pw[i] = dt * q[i];
+      for (size_t i = 0; i < N; ++i) h[i] += a[j] * pw[i];
+      if (j < deg)
+        for (size_t i = 0; i < N; ++i) grad[i] += b[j] * pw[i];
+    }
+  }
+  free(d); free(traj); free(lam); free(mu); free(nv); free(acc);
+  free(W); free(h); free(hp); free(pw); free(q); free(a); free(b);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Linear problem with a general sparse operator in CSR form (Sec. 2: the    */
 /* state equation dq/dt = A q with a constant discretised operator A; the    */
 /* paper's Sec. 4 operators are such matrices). Classical RK4, control =     */

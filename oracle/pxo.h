@@ -131,6 +131,30 @@ int pxo_ad2_gradient_serial(int nx, int ny, double L, double nu, const double* u
                             const double* v, double T, int64_t K, double omega,
                             const double* f, const double* f_true, double* J, double* grad);
 
+/* ---- polynomial propagator of the homogeneous parts (Eq. hom / adjHomNormal with
+ * operator applications only, as the ReLPM of Sec. 4.1): the RK4 stepper's propagator
+ * over k steps is R(dt A)^k, R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24.
+ * a[0..4k]: coefficients of R(z)^k (long double products, rounded once).          */
+int pxo_rk4_power_coeffs(int k, double* a);
+/* b[0..4k-1]: coefficients of b(z) = sum_{j<k} g_j(z) R(z)^{k-1-j}, g_j(dt A) =
+ * d u_{j+1}/d f for RK4 step j (times t0 + j dt) of du/dt = A u + s(t) f, s(t) =
+ * sin(omega t) (1 if omega == 0). b(dt A^T) h is the forcing gradient that the
+ * homogeneous adjoint started from h at the end of the k steps contributes.        */
+int pxo_rk4_forcing_coeffs(int k, double dt, double t0, double omega, double* b);
+/* out = sum_{j=0}^{m} c[j] (dt B)^j x, B = A (transpose == 0) or A^T, the 2D
+ * advection-diffusion operator; the powers formed one after another.             */
+int pxo_ad2_poly_apply(int nx, int ny, double L, double nu, const double* u, const double* v, double dt,
+                       int transpose, int m, const double* c, const double* x, double* out);
+/* The hybrid loop (Sec. 3.3) of pxo_ad2_gradient_serial's problem on P equal parts:
+ * serial direct; adjoint lanes by the exact discrete RK4 adjoint from zero; the
+ * summed homogeneous adjoint problems carried down subinterval by subinterval with
+ * the power series of R(dt A^T)^(K/P) and of the forcing-gradient polynomial, both
+ * cut after degree m (m <= 0 or m >= 4K/P: the whole polynomials, which reproduces
+ * serial stepping).                                                               */
+int pxo_ad2_gradient_hybrid_poly(int nx, int ny, double L, double nu, const double* u, const double* v,
+                                 double T, int64_t K, double omega, const double* f, const double* f_true,
+                                 int P, int m, double* J, double* grad);
+
 /* ---- small dense and Krylov building blocks ------------------------------- */
 /* Dense matrix exponential (row-major d x d), scaling and squaring of a Taylor
  * series evaluated in long double.                                              */
