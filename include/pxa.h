@@ -109,8 +109,10 @@ typedef enum { PXA_PHI_EXP = 0, PXA_PHI_STEPPER = 1 } pxa_phi;
 /* How the homogeneous propagations of ADVDIFF_1D are computed: Arnoldi/Krylov (default)
  * or the real Leja points method (Sec. 4.1: Newton interpolation of phi(z) = (e^z - 1)/z
  * at Leja points of the focal interval of the spectrum; exp(B) v = v + B phi(B) v; three
- * vectors of workspace instead of a Krylov basis; PXA_PHI_EXP only). */
-typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1, PXA_PROP_BAND = 2 } pxa_propagator;
+ * vectors of workspace instead of a Krylov basis; PXA_PHI_EXP only). PXA_PROP_POLY
+ * (ADVDIFF_2D): the RK4 stepper's own propagator R(dt A^T)^kk as its power series in
+ * tau A^T (tau = kk dt), operator applications only, like ReLPM (see pxa_set_propagator). */
+typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1, PXA_PROP_BAND = 2, PXA_PROP_POLY = 3 } pxa_propagator;
 /* SERIAL: one lane over [0, T] (plain serial stepping, same kernels).
  * PARAEXP: P lanes + homogeneous propagation + superposition. */
 typedef enum { PXA_SERIAL = 0, PXA_PARAEXP = 1 } pxa_mode;
@@ -220,6 +222,10 @@ typedef struct {
   float ms_side_lanes;
   int graph_kernels;        /* kernel nodes of the gradient's captured CUDA graph (the
                                kernels one graph replay launches; 0: no graph captured) */
+  int prop_degree;          /* ADVDIFF_2D with PXA_PROP_POLY: degree m of the series in use
+                               (0: the stepper chain) */
+  int prop_substeps;        /* chain segments per subinterval of that series */
+  double prop_tail;         /* its tail bound sum_{i>m} a_i ||tau A^T||_inf^i (relative) */
 } pxa_stats;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -265,7 +271,16 @@ int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
  * power M^(K/P) (PXA_PHI_STEPPER), is applied once per link as a circulant band: A is
  * circulant (periodic grid, constant coefficients), so the propagator's taps are the
  * inverse DFT of its eigenvalues, built on the host (FP64, kept to 2^-50 of the largest
- * tap; max_degree is not used). Invalidates the workspace. */
+ * tap; max_degree is not used). With PXA_PROP_POLY (ADVDIFF_2D, Paraexp; other operators
+ * return PXA_ERR_INVALID at the first solve) the summed homogeneous adjoint problems (Eq. adjHomNormal) are carried by the
+ * stepper's own propagator over chain segments of kk RK4 steps, R(dt A^T)^kk = sum_i a_i
+ * (tau A^T)^i with R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24 and tau = kk dt, and each segment's
+ * forcing gradient (Eq. paramupdate over its steps) by a second series in the same powers;
+ * both are cut after the smallest degree m (a multiple of 4) whose tail bound
+ * sum_{i>m} a_i ||tau A^T||_inf^i is below max(tolerance of pxa_set_krylov, 1e-7); kk is
+ * the largest divisor of K/P with kk ||dt A^T||_inf <= 4. m above max_degree returns
+ * PXA_ERR_NOT_CONVERGED at the first solve. The series needs only operator applications:
+ * m per segment against 4 kk for stepping. Invalidates the workspace. */
 int pxa_set_propagator(pxa_ctx* ctx, int method, int max_degree);
 /* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
 int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);

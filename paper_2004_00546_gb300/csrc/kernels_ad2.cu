@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels_ad2.cuh"
 
@@ -454,6 +456,168 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
   }
 }
 
+// ---- the chain's polynomial propagator (PXA_PROP_POLY) ---------------------------------
+// The summed homogeneous adjoint problems of one chain segment of kk RK4 steps are carried
+// by the power series of the stepper's own propagator, h <- sum_{i<=m} a_i Z^i h' with
+// Z = tau A^T, tau = kk dt (Eq. adjHomNormal with R(dt A^T)^kk, R the RK4 amplification
+// polynomial), and the segment's forcing gradient is sum_{i<=m} b_i Z^i h' (Eq. paramupdate
+// summed over the segment's steps). One launch forms four powers on one tile: from the halo-4 tile of
+// v_{i0} (TMA) the powers v_{i0+1}, .., v_{i0+4} on the halo-3, 2, 1 regions and the
+// interior, in the register layout of ad2_rk4_kernel (thread (tx, ty): tile column tx + 1
+// and RG2 rows; tau times the coefficients of A^T at its points in registers). Interior
+// points add their terms: H = (i0 == 0 ? a_0 v_0 : H) + sum_j a_{i0+j} v_{i0+j} (FP32,
+// padded with ghosts; skipped when want_h == 0) and G += (i0 == 0 ? b_0 v_0 : 0) + sum_j
+// b_{i0+j} v_{i0+j} (FP32 within the launch, FP64 across launches); v_{i0+4} goes to the
+// other plane of V (padded with ghosts). ca / cb hold at least i0 + 5 coefficients.
+__global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant__ CUtensorMap vmap,
+                                                          const __grid_constant__ CUtensorMap cmap,
+                                                          Ad2Params p, float tau, float* __restrict__ V,
+                                                          int buf_in, int i0, const float* __restrict__ ca,
+                                                          const double* __restrict__ cb,
+                                                          float* __restrict__ H, int want_h,
+                                                          double* __restrict__ G, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem t = carve(smem_raw);
+  const int tile = blockIdx.x;
+  const int tbx = tile % p.tiles_x, tby = tile / p.tiles_x;
+  const int x0 = tbx * TX2, y0 = tby * TY2;  // padded coordinates of the halo corner
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int col = tx + 1;                     // tile column
+  const bool colact = col <= BX2 - 2;         // inside the halo-3 region [1, BX2-1)
+  const int row0 = 1 + ty * RG2;              // first owned row
+  if (threadIdx.x == 0) {
+    mbar_init(&t.bar[0], 1);
+    mbar_init(&t.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
+    tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &vmap, x0, y0, buf_in, &t.bar[1]);
+  }
+  // this launch's series coefficients (the same for every thread), read while the copies fly
+  float ka[5], kb[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    ka[j] = __ldg(ca + i0 + j);
+    kb[j] = (float)__ldg(cb + i0 + j);
+  }
+  const bool ok0 = mbar_wait(&t.bar[0], 0);
+  const bool ok1 = mbar_wait(&t.bar[1], 0);
+  if (!(ok0 && ok1)) {
+    if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    // let both copies land (bounded again) before the block can leave
+    (void)mbar_wait(&t.bar[0], 0);
+    (void)mbar_wait(&t.bar[1], 0);
+    return;
+  }
+  const float* u = t.coef;
+  const float* v = t.coef + TILE2;
+  // tau (A^T x)_c = tw x_w + te x_e + ts x_s + tn x_n + tc x_c: the west neighbour's row of
+  // A holds c as its east entry (-u_w/(2h) + nu/h^2), and so on
+  const float d = p.nu * p.invh2, dt = tau, tc = -4.0f * d * dt;
+  float tw[RG2], te[RG2], ts[RG2], tn[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int c = (row0 + i) * BX2 + col;
+    tw[i] = dt * (-u[c - 1] * p.inv2h + d);
+    te[i] = dt * (u[c + 1] * p.inv2h + d);
+    ts[i] = dt * (-v[c - BX2] * p.inv2h + d);
+    tn[i] = dt * (v[c + BX2] * p.inv2h + d);
+  }
+  const float* Xp = t.q[0];
+  float xv[RG2], hacc[RG2], gacc[RG2];
+  const bool first = i0 == 0;
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    xv[i] = Xp[(row0 + i) * BX2 + col];
+    hacc[i] = first ? ka[0] * xv[i] : 0.0f;
+    gacc[i] = first ? kb[0] * xv[i] : 0.0f;
+  }
+  // powers 1, 2, 3 on every owned point (the valid region shrinks by one ring per power;
+  // ring values that read not-yet-valid neighbours never reach the interior); vertical
+  // neighbours from registers, horizontal ones and the strip ends from the previous power
+  float* Yn = t.ya;
+#pragma unroll
+  for (int j = 1; j <= 3; ++j) {
+    float yv[RG2];
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) {
+      const int c = (row0 + i) * BX2 + col;
+      const float xs = i > 0 ? xv[i - 1] : Xp[c - BX2];
+      const float xn = i + 1 < RG2 ? xv[i + 1] : Xp[c + BX2];
+      const float y = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * xv[i];
+      yv[i] = y;
+      if (colact) Yn[c] = y;
+      hacc[i] = fmaf(ka[j], y, hacc[i]);
+      gacc[i] = fmaf(kb[j], y, gacc[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) xv[i] = yv[i];
+    Xp = Yn;
+    Yn = Yn == t.ya ? t.yb : t.ya;
+  }
+  // power 4 on the interior; the interior's terms leave the tile
+  float* Vout = V + (size_t)(1 - buf_in) * p.Hp * p.Wp;
+  const bool cin = col >= G2 && col < G2 + TX2;
+  const int x = x0 + col - G2;  // domain column
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int row = row0 + i;
+    const int c = row * BX2 + col;
+    const int y = y0 + row - G2;
+    if (!(cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny)) continue;
+    const float xs = i > 0 ? xv[i - 1] : Xp[c - BX2];
+    const float xn = i + 1 < RG2 ? xv[i + 1] : Xp[c + BX2];
+    const float y4 = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * xv[i];
+    store_with_ghosts(Vout, p, x, y, y4);
+    if (want_h) {
+      float hv = fmaf(ka[4], y4, hacc[i]);
+      if (!first) hv += H[(size_t)(y + G2) * p.Wp + (x + G2)];
+      store_with_ghosts(H, p, x, y, hv);
+    }
+    const size_t gi = (size_t)y * p.nx + x;
+    G[gi] += (double)fmaf(kb[4], y4, gacc[i]);
+  }
+}
+
+// b[s][i], i = 0..m, of chain segment s (steps s kk .. s kk + kk - 1):
+// sum_j s(t_j) Q[0][j][i] + s(t_j + dt/2) Q[1][j][i] + s(t_j + dt) Q[2][j][i], t_j =
+// (s kk + j) dt, Q = [3][kk][m+1] (FP64; s(t) = sin(omega t), 1 when omega == 0). One block
+// per segment, one thread per coefficient (m < blockDim.x).
+__global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, const double* __restrict__ Q,
+                                        double* __restrict__ b) {
+  __shared__ double sv[3][128];
+  const int s = blockIdx.x, i = threadIdx.x;
+  double acc = 0.0;
+  for (int j0 = 0; j0 < kk; j0 += 128) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * 128; e += blockDim.x) {
+      const int jj = e / 3, w = e % 3, j = j0 + jj;
+      const double tj = ((double)s * kk + j) * dt + (w == 0 ? 0.0 : (w == 1 ? 0.5 * dt : dt));
+      sv[w][jj] = j < kk ? forcing_s(omega, tj) : 0.0;
+    }
+    __syncthreads();
+    if (i <= m)
+      for (int jj = 0; jj < 128 && j0 + jj < kk; ++jj) {
+        const size_t j = (size_t)(j0 + jj);
+        acc += sv[0][jj] * Q[(0 * (size_t)kk + j) * (m + 1) + i] + sv[1][jj] * Q[(1 * (size_t)kk + j) * (m + 1) + i] +
+               sv[2][jj] * Q[(2 * (size_t)kk + j) * (m + 1) + i];
+      }
+  }
+  if (i <= m) b[(size_t)s * (m + 1) + i] = acc;
+}
+
+// dst = a + b over `count` elements (b may be NULL: a copy).
+__global__ void ad2_sum2_kernel(size_t count, float* __restrict__ dst, const float* __restrict__ a,
+                                const float* __restrict__ b) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = b ? a[e] + b[e] : a[e];
+}
+
 // Pack u, v (FP64, [ny][nx]) and the forcing f - f_true into the padded FP32
 // coefficient array [3][Hp][Wp] with periodic ghosts.
 __global__ void ad2_pack_coef_kernel(Ad2Params p, const double* __restrict__ u,
@@ -627,6 +791,30 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
   ad2_rk4T_kernel<<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
                                                        lanes_per_cta, buf_in, lane_k, lane_off, s_local,
                                                        with_source, traj, src_scale, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
+                            float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
+                            int want_h, double* G, int* status) {
+  cudaError_t e = set_smem((const void*)ad2_poly_kernel);
+  if (e != cudaSuccess) return e;
+  ad2_poly_kernel<<<p.tiles_x * p.tiles_y, 256, ad2_smem_bytes(), st>>>(vmap, cmap, p, tau, V, buf_in, i0, ca, cb,
+                                                                        H, want_h, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
+                                    const double* Q, double* b) {
+  if (segments < 1) return cudaSuccess;
+  if (m < 0 || m >= 256) return cudaErrorInvalidValue;
+  ad2_poly_forcing_kernel<<<segments, 256, 0, st>>>(kk, m, dt, omega, Q, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b) {
+  const unsigned blocks = (unsigned)std::min<size_t>((count + 255) / 256, 4096);
+  ad2_sum2_kernel<<<blocks, 256, 0, st>>>(count, dst, a, b);
   return cudaGetLastError();
 }
 

@@ -73,6 +73,20 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
                                  float* states, double* G, int lanes, int lane0, int count, int buf_in,
                                  const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
                                  int* status);
+// The chain's polynomial propagator (PXA_PROP_POLY): one launch forms the powers
+// v_{i0+j} = (tau A^T)^j v_{i0}, j = 1..4, on every tile from plane buf_in of V (vmap: ad2_make_map
+// over V with depth 2), writes v_{i0+4} to the other plane, and adds the interior's terms
+// a_i v_i to H (padded plane; H = a_0 v_0 + ... when i0 == 0; skipped when want_h == 0) and
+// b_i v_i to G (FP64 [ny][nx]). ca (FP32) and cb (FP64) hold the coefficients 0 .. i0 + 4.
+cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
+                            float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
+                            int want_h, double* G, int* status);
+// The forcing-gradient coefficients b[s][0..m] of `segments` chain segments of kk steps
+// from the omega-free families Q = [3][kk][m+1] (m < 256).
+cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
+                                    const double* Q, double* b);
+// dst = a + b (b may be NULL) over count floats.
+cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b);
 cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
                                 const double* extra, double* grad, int* status);
 

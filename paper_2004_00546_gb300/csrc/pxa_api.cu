@@ -297,6 +297,50 @@ void relpm_setup_host(double t, double am, double a0, double ap, int mmax, int& 
   for (int i = 0; i < d; ++i) D[i] = F[(size_t)i * d];
 }
 
+
+// The RK4 stepper's propagator over a chain segment of kk steps as a power series
+// (PXA_PROP_POLY). With z = dt A and w = kk z = tau A (tau = kk dt, the segment's length),
+// R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24 and R(z)^kk = sum_i a_i w^i (degree 4kk; every
+// a_i > 0 and a_i <= 1/i!, since R's coefficients do not exceed exp's). The forcing
+// gradient that the homogeneous adjoint adds over the segment is sum_j g_j(dt A^T)
+// lambda_{j+1} with g_j(z) = dt [s1 (1/6 + z/6 + z^2/12 + z^3/24) + s2 (2/3 + z/3 +
+// z^2/12) + s4/6], the derivative of step j's map with respect to the forcing (s1, s2, s4:
+// s(t) at its stage times), and lambda_{j+1} = R(dt A^T)^(kk-1-j) h: a polynomial in
+// tau A^T applied to h, split into three omega-free families Q_w[j] = dt c_w(z)
+// R(z)^(kk-1-j) (w = s1, s2, s4), whose s(t)-weighted sum the device forms per segment.
+// Long double throughout; a_full is the whole series, Q is cut after degree m (products
+// cut at degree m are exact below it).
+void rk4_series_host(int kk, int m, double dt, std::vector<long double>& a_full, std::vector<double>& Q) {
+  const long double s = 1.0L / (long double)kk;
+  const long double R[5] = {1.0L, s, 0.5L * s * s, s * s * s / 6.0L, s * s * s * s / 24.0L};
+  auto times_R = [&](const std::vector<long double>& x, int deg) {
+    std::vector<long double> y((size_t)deg + 1, 0.0L);
+    for (int i = 0; i < (int)x.size() && i <= deg; ++i)
+      for (int r = 0; r < 5 && i + r <= deg; ++r) y[(size_t)i + r] += x[(size_t)i] * R[r];
+    return y;
+  };
+  a_full.assign(1, 1.0L);
+  for (int j = 1; j <= kk; ++j) a_full = times_R(a_full, 4 * j);
+  // c_w(z) in powers of w = kk z
+  const long double c1[4] = {1.0L / 6.0L, s / 6.0L, s * s / 12.0L, s * s * s / 24.0L};
+  const long double c2[4] = {2.0L / 3.0L, s / 3.0L, s * s / 12.0L, 0.0L};
+  const long double c4[4] = {1.0L / 6.0L, 0.0L, 0.0L, 0.0L};
+  const long double* cw[3] = {c1, c2, c4};
+  Q.assign((size_t)3 * kk * (m + 1), 0.0);
+  std::vector<long double> pw(1, 1.0L);  // R^e cut at degree m, e = 0 first
+  for (int e = 0; e < kk; ++e) {
+    const int j = kk - 1 - e;
+    for (int w = 0; w < 3; ++w)
+      for (int i = 0; i <= m; ++i) {
+        long double acc = 0.0L;
+        for (int r = 0; r < 4 && r <= i; ++r)
+          if (i - r < (int)pw.size()) acc += cw[w][r] * pw[(size_t)(i - r)];
+        Q[((size_t)w * kk + j) * (m + 1) + i] = (double)((long double)dt * acc);
+      }
+    pw = times_R(pw, std::min(4 * (e + 1), m));
+  }
+}
+
 }  // namespace pxa
 
 struct pxa_ctx {
@@ -467,6 +511,13 @@ struct pxa_ctx {
   float* tcoef2 = nullptr;  // [4][Hp][Wp] coefficients of A^T
   float* sc2 = nullptr;     // [K][3] s(t) at the stage times of every step
   CUtensorMap mapA4, mapT4, mapS4, mapG4;
+  // chain by the power series of the stepper's propagator (PXA_PROP_POLY)
+  float* polyA = nullptr;    // [m+1] coefficients of R(z)^kk cut at degree m (m % 4 == 0)
+  double* polyQ = nullptr;   // [3][kk][m+1] omega-free forcing families
+  double* polyB = nullptr;   // [segments][m+1] forcing-gradient coefficients of each segment
+  float* hC = nullptr;       // [Hp][Wp] the chain's carried value
+  int poly_m = 0, poly_sub = 1, poly_kk = 0;
+  double poly_tail = 0.0;
   float* stL = nullptr;     // pxa_rk4_lanes_2d states [2][lanesL][Hp][Wp]
   int lanesL = 0;
   float* scL = nullptr;     // pxa_rk4_lanes_2d forcing factors [lanes * steps][3]
@@ -633,6 +684,8 @@ int prepare(pxa_ctx* c) {
   if (!c->have_op || !c->have_time) return fail(c, PXA_ERR_STATE, "set_operator and set_time first");
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   release_workspace(c);
+  if (c->prop == PXA_PROP_POLY && c->op.kind != PXA_ADVDIFF_2D)
+    return fail(c, PXA_ERR_INVALID, "PXA_PROP_POLY is implemented for ADVDIFF_2D");
   const int n = c->op.n, P = c->P;
   int rc;
   if ((rc = alloc(c, &c->Jdev, 1))) return rc;
@@ -699,6 +752,71 @@ int prepare(pxa_ctx* c) {
           !ad2_make_map_plain(&c->mapG4, c->G2buf, 8, a.nx, a.ny, P, 64, AD2_ROLL_BR))
         return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D adjoint lanes");
     }
+    c->poly_m = 0;
+    if (c->prop == PXA_PROP_POLY && P > 1) {
+      // max-norm of dt A^T (largest absolute row sum of the transposed stencil), from the
+      // velocity copied to the host once (set-up, not the solve path)
+      std::vector<double> hu(N), hv(N);
+      PXA_CUDA(c, cudaMemcpy(hu.data(), c->op.u_dev, sizeof(double) * N, cudaMemcpyDeviceToHost), "copy u");
+      PXA_CUDA(c, cudaMemcpy(hv.data(), c->op.v_dev, sizeof(double) * N, cudaMemcpyDeviceToHost), "copy v");
+      const double dd = c->op.nu / (h * h), ih = 1.0 / (2.0 * h);
+      double rowmax = 0.0;
+      for (int y = 0; y < a.ny; ++y)
+        for (int x = 0; x < a.nx; ++x) {
+          const size_t w = (size_t)y * a.nx + (x + a.nx - 1) % a.nx, e = (size_t)y * a.nx + (x + 1) % a.nx;
+          const size_t sth = (size_t)((y + a.ny - 1) % a.ny) * a.nx + x, nth = (size_t)((y + 1) % a.ny) * a.nx + x;
+          const double r = std::fabs(-hu[w] * ih + dd) + std::fabs(hu[e] * ih + dd) + std::fabs(-hv[sth] * ih + dd) +
+                           std::fabs(hv[nth] * ih + dd) + 4.0 * dd;
+          rowmax = std::max(rowmax, r);
+        }
+      const double rho = a.dtd * rowmax;
+      // segments of kk steps: the smallest divisor of K/P with kk rho <= 4 (the partial
+      // sums of the series stay within e^4 of the result's scale in FP32)
+      const int64_t k = c->K / P;
+      int sub = 1;
+      while (sub < k && (k % sub != 0 || (double)(k / sub) * rho > 4.0)) ++sub;
+      const int kk = (int)(k / sub);
+      const long double rs = (long double)kk * rho;  // max-norm of tau A^T
+      const double tol = std::max(c->kry_tol, 1e-7);
+      std::vector<long double> afull;
+      std::vector<double> Q;
+      rk4_series_host(kk, 0, a.dtd, afull, Q);
+      // degree: the smallest multiple of 4 whose tail sum_{i>m} a_i rs^i is <= tol
+      int m = 4 * kk;
+      double tail = 0.0;
+      for (int mm = 4; mm <= 4 * kk; mm += 4) {
+        long double t = 0.0L, pr = 1.0L;
+        for (int i = 0; i <= 4 * kk; ++i) {
+          if (i > mm) t += afull[(size_t)i] * pr;
+          pr *= rs;
+        }
+        if (t <= (long double)tol) {
+          m = mm;
+          tail = (double)t;
+          break;
+        }
+      }
+      if (m > c->relpm_mmax || m > 252)
+        return fail(c, PXA_ERR_NOT_CONVERGED, "PXA_PROP_POLY: the series needs degree " + std::to_string(m) +
+                                                  " for the tolerance, above the maximum degree");
+      rk4_series_host(kk, m, a.dtd, afull, Q);
+      std::vector<float> ah((size_t)m + 1);
+      for (int i = 0; i <= m; ++i) ah[(size_t)i] = (float)afull[(size_t)i];
+      const int segments = (P - 1) * sub;
+      if ((rc = alloc(c, &c->polyA, (size_t)m + 1))) return rc;
+      if ((rc = alloc(c, &c->polyQ, Q.size()))) return rc;
+      if ((rc = alloc(c, &c->polyB, (size_t)segments * (m + 1)))) return rc;
+      if ((rc = alloc(c, &c->hC, plane))) return rc;
+      PXA_CUDA(c, cudaMemcpy(c->polyA, ah.data(), sizeof(float) * ah.size(), cudaMemcpyHostToDevice), "copy");
+      PXA_CUDA(c, cudaMemcpy(c->polyQ, Q.data(), sizeof(double) * Q.size(), cudaMemcpyHostToDevice), "copy");
+      c->poly_m = m;
+      c->poly_sub = sub;
+      c->poly_kk = kk;
+      c->poly_tail = tail;
+    }
+    c->stats.prop_degree = c->poly_m;
+    c->stats.prop_substeps = c->poly_m ? c->poly_sub : 0;
+    c->stats.prop_tail = c->poly_m ? c->poly_tail : 0.0;
   } else if (c->op.kind == PXA_ADVDIFF_1D) {
     double dt = c->T / (double)c->K;
     cn_band_taps(n, c->am, c->a0, c->ap, dt, c->band_host, c->band_r);
@@ -1581,7 +1699,30 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                "2d adjoint lanes");
   }
   ev_record(c, 3);
-  if (P > 1) {
+  if (P > 1 && c->poly_m > 0) {
+    // Eq. adjHomNormal with the stepper's own propagator as its power series: the summed
+    // homogeneous problems are carried down segment by segment (kk steps each, `sub` per
+    // subinterval), h <- a(tau A^T)(h + w), and each segment's forcing gradient
+    // b_s(tau A^T)(h + w) goes to GC; w is the lane value at the subinterval's top, added
+    // at the first segment of each subinterval (a, b cut after degree m)
+    const float* Wbuf = c->stA + (size_t)(k & 1) * P * plane;
+    const int m = c->poly_m, sub = c->poly_sub, kk = c->poly_kk;
+    const int segments = (P - 1) * sub;
+    const float tau = (float)((double)kk * a.dtd);
+    PXA_CUDA(c, launch_ad2_poly_forcing(st, segments, kk, m, a.dtd, a.omega, c->polyQ, c->polyB), "poly forcing");
+    PXA_CUDA(c, cudaMemsetAsync(c->hC, 0, sizeof(float) * plane, st), "zero chain");
+    for (int sg = segments - 1; sg >= 0; --sg) {
+      const bool top = (sg + 1) % sub == 0;  // the segment ends at a subinterval's top
+      const int lane_above = (sg + 1) / sub;  // its lane value when it does
+      PXA_CUDA(c, launch_ad2_sum2(st, plane, c->stC, c->hC, top ? Wbuf + (size_t)lane_above * plane : nullptr),
+               "chain add");
+      const double* cb = c->polyB + (size_t)sg * (m + 1);
+      for (int i0 = 0, buf = 0; i0 < m; i0 += 4, buf ^= 1)
+        PXA_CUDA(c, launch_ad2_poly(st, c->mapC, c->mapCoef, a, tau, c->stC, buf, i0, c->polyA, cb, c->hC,
+                                    sg > 0 ? 1 : 0, c->GC, c->status),
+                 "2d chain series");
+    }
+  } else if (P > 1) {
     // Eq. adjHomNormal with the stepper's own propagator: h = sum of the lane values
     // W_{l+1} carried down subinterval by subinterval, no source
     const float* Wbuf = c->stA + (size_t)(k & 1) * P * plane;
@@ -2010,7 +2151,8 @@ int pxa_partition_bounds(int64_t K, int P, double r, int max_chunks, int64_t* bo
 }
 
 int pxa_set_propagator(pxa_ctx* c, int method, int max_degree) {
-  if (!c || (method != PXA_PROP_KRYLOV && method != PXA_PROP_RELPM && method != PXA_PROP_BAND) ||
+  if (!c || (method != PXA_PROP_KRYLOV && method != PXA_PROP_RELPM && method != PXA_PROP_BAND &&
+             method != PXA_PROP_POLY) ||
       max_degree < 2 || max_degree > 200)
     return PXA_ERR_INVALID;
   c->prop = method;

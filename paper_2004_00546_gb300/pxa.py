@@ -22,7 +22,7 @@ OBJ_TERMINAL_L2, OBJ_INTEGRAL_TRACKING = 1, 2
 F64, F32 = 0, 1
 CN, RK4 = 1, 2
 PHI_EXP, PHI_STEPPER = 0, 1
-PROP_KRYLOV, PROP_RELPM, PROP_BAND = 0, 1, 2
+PROP_KRYLOV, PROP_RELPM, PROP_BAND, PROP_POLY = 0, 1, 2, 3
 SERIAL, PARAEXP = 0, 1
 STORE_FULL, STORE_CHECKPOINTS = 0, 1
 ADJ_BANDED, ADJ_RESTEP, ADJ_BANDED_SINGLE, ADJ_BANDED_PAIR = 0, 1, 2, 3
@@ -81,7 +81,8 @@ class Stats(ctypes.Structure):
                 ("prop_band_taps", ctypes.c_int), ("side_chunks", ctypes.c_int),
                 ("ms_side_prepass", ctypes.c_float), ("ms_side_pair", ctypes.c_float),
                 ("ms_side_quad", ctypes.c_float), ("ms_side_lanes", ctypes.c_float),
-                ("graph_kernels", ctypes.c_int)]
+                ("graph_kernels", ctypes.c_int), ("prop_degree", ctypes.c_int),
+                ("prop_substeps", ctypes.c_int), ("prop_tail", ctypes.c_double)]
 
 
 class BatchStats(ctypes.Structure):

@@ -132,3 +132,87 @@ def test_full_size_c3_central_fd_16_directions(env):
         fd = (Jp - Jm) / 2.0
         dd = float(np.sum(g * d.reshape(-1)))
         assert abs(fd - dd) < 1e-3 * abs(dd), (fd, dd)
+
+
+@pytest.mark.parametrize("n,T,K,P,tol,rough", [(64, 0.35, 24, 2, 100.0, True), (64, 0.35, 24, 2, 1.0, True),
+                                                (64, 0.35, 24, 2, 1e-10, True), (64, 0.3, 48, 6, 1e-10, False),
+                                                (72, 0.3, 40, 4, 1e-10, False), (120, 0.3, 48, 8, 1e-10, False),
+                                                (8, 0.3, 30, 3, 1e-10, False)])
+def test_poly_chain_matches_oracle_at_its_degree(env, n, T, K, P, tol, rough):
+    """The chain by the stepper's propagator as a power series (PXA_PROP_POLY) against the
+    oracle's hybrid loop cut at the same degree m, point by point. With white-noise
+    forcings and a subinterval near the series' reach (k ||dt A^T|| = 3.96), a loose
+    tolerance makes the series short (m = 4) and its cut moves the gradient by ~2e-3, far
+    above the FP32 tolerance: the GPU must evaluate the same truncated polynomials, not
+    merely land near serial stepping. At the default tolerance it matches serial
+    stepping as well."""
+    torch, X = env
+    nu = 0.02
+    u, v, f, ft = problem(n)
+    if rough:
+        rng = np.random.default_rng(5)
+        f, ft = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    ctx = ctx2d(torch, X, n, nu, T, K, P, u, v, f, ft)
+    ctx.set_krylov(20, tol, X.PHI_STEPPER, 1)
+    ctx.set_propagator(X.PROP_POLY, 200)
+    grad = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    J = ctx.gradient(X.PARAEXP, grad)
+    st = ctx.stats()
+    m = st["prop_degree"]
+    assert m > 0 and m % 4 == 0 and st["prop_substeps"] == 1, st
+    J_ref, g_ref = O.ad2_gradient_hybrid_poly(f, ft, u, v, nu, T, K, P, m, omega=1.0)
+    assert abs(J - J_ref) / J_ref < TOL32
+    g = grad.cpu().numpy().reshape(n, n)
+    assert rel(g, g_ref) < TOL32, (m, rel(g, g_ref))
+    _, g_ser = O.ad2_gradient_serial(f, ft, u, v, nu, T, K, omega=1.0)
+    if tol >= 100.0:
+        assert m == 4 and rel(g_ref, g_ser) > 1e-3
+    if tol <= 1e-7:
+        assert rel(g, g_ser) < TOL32
+
+
+def test_poly_chain_segments_within_a_subinterval(env):
+    """A long subinterval (K/P = 64 steps, kk * ||dt A^T|| > 4) is split into several
+    series segments; the gradient still matches serial stepping (the oracle)."""
+    torch, X = env
+    n, nu, T, K, P = 64, 0.02, 1.6, 256, 4
+    u, v, f, ft = problem(n, seed=91)
+    ctx = ctx2d(torch, X, n, nu, T, K, P, u, v, f, ft)
+    ctx.set_propagator(X.PROP_POLY, 200)
+    grad = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    ctx.gradient(X.PARAEXP, grad)
+    st = ctx.stats()
+    assert st["prop_substeps"] > 1 and st["prop_tail"] <= 1e-7, st
+    _, g_ser = O.ad2_gradient_serial(f, ft, u, v, nu, T, K, omega=1.0)
+    assert rel(grad.cpu().numpy().reshape(n, n), g_ser) < TOL32
+
+
+def test_poly_chain_full_size_against_the_stepper_chain(env):
+    """C3's size (512^2, K = 1024, P = 64): the series chain against the stepper chain on
+    the GPU, point by point, and serial stepping; both are FP32 reorganisations of the same
+    discrete adjoint, the series cut with tail bound <= 1e-7."""
+    torch, X = env
+    n, nu, T, K, P = 512, 1e-3, 1.0, 1024, 64
+    u, v = I.streamfunction_velocity(n, n, 8, 2006)
+    x = I.grid1d(n)
+    Xg, Yg = np.meshgrid(x, x)
+    ft = np.sin(Xg) * np.sin(Yg)
+    f = np.ones((n, n))
+    grads = {}
+    for name, prop in (("stepper", None), ("poly", X.PROP_POLY)):
+        ctx = ctx2d(torch, X, n, nu, T, K, P, u, v, f, ft)
+        if prop is not None:
+            ctx.set_propagator(prop, 200)
+        g = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        ctx.gradient(X.PARAEXP, g)
+        grads[name] = g.cpu().numpy()
+        if prop is not None:
+            st = ctx.stats()
+            assert st["prop_degree"] > 0 and st["prop_tail"] <= 1e-7, st
+        ctx.close()
+    ctx = ctx2d(torch, X, n, nu, T, K, 1, u, v, f, ft)
+    g = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    ctx.gradient(X.SERIAL, g)
+    grads["serial"] = g.cpu().numpy()
+    assert rel(grads["poly"], grads["stepper"]) < TOL32
+    assert rel(grads["poly"], grads["serial"]) < TOL32
