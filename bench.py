@@ -109,7 +109,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="grid size override for the 2D workloads")
     ap.add_argument("--once", action="store_true",
                     help="profiling run: W warm-up gradients then one more of the headline "
-                         "configuration (1D workloads), default cluster sizes, no autotuning")
+                         "configuration (1D, batched and 2D advection-diffusion workloads), default "
+                         "cluster sizes, no autotuning")
     ap.add_argument("--K", type=int, default=0,
                     help="with --once on the 1D workloads: this many time steps at the workload's dt (a "
                          "shorter window for profiling captures)")
@@ -933,6 +934,30 @@ def run_once(args, w):
             "clusters": [st["cluster_direct"], st["cluster_lanes"], st["cluster_chain"]]}
 
 
+def run_once_2d(args, w):
+    """2D advection-diffusion for ncu: W warm-up gradients and one more (Paraexp, the chain by
+    the stepper propagator's power series), no graph, so every kernel is its own launch."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    X.load()
+    n = args.n or w["n"]
+    ctx, keep = ctx_2d(X, torch, w, n, w["P"], w["K"])
+    ctx.set_propagator(X.PROP_POLY, 200)
+    ctx.set_timing(True)
+    grad = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.gradient(X.PARAEXP, grad)
+    J = ctx.gradient(X.PARAEXP, grad)
+    st = ctx.stats()
+    ctx.close()
+    del keep
+    return {"once": w["label"], "J": J, "warmup": args.warmup, "degree": st["prop_degree"],
+            "phases_ms": {k: st[k] for k in ("ms_direct_inhom", "ms_adjoint_inhom", "ms_adjoint_hom", "ms_total")}}
+
+
 def run_reference_batch(args, w, world):
     """The reference arm of the batched workload: the serial FP64 oracle of a bounded
     sample of the problems per step, scaled to the whole batch."""
@@ -1462,6 +1487,8 @@ def main():
         if args.K:
             w = dict(w, K=args.K, T=w["T"] * args.K / w["K"])
         line = run_once(args, w)
+    elif args.once and w["kind"] == "advdiff2d":
+        line = run_once_2d(args, w)
     elif args.once and w["kind"] == "batched1d":
         line = run_batch_once(args, w)
     elif w["kind"] == "lanes2d":

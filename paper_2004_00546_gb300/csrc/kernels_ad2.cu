@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
                                                          Ad2Params p, float* __restrict__ states,
                                                          int lanes, int map_lanes, int lanes_per_cta,
                                                          int buf_in, int64_t lane_k, int64_t s_local,
+                                                         const float* __restrict__ sc,
                                                          float* __restrict__ traj, int64_t traj_row,
                                                          double* __restrict__ Jpart, int64_t jrow,
                                                          double dt_over_T, int* status) {
@@ -206,15 +207,8 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
   const float dt = p.dt, hdt = 0.5f * p.dt, sdt = p.dt / 6.0f;
   float* Y0 = t.ya;
   float* Y1 = t.yb;
-  // s(t) at the three stage times, evaluated once per lane by one thread (FP64 sin is
-  // 64x slower than FP32 arithmetic) into a double-buffered slot of 4 floats per lane
-  if (threadIdx.x == 0) {
-    const double tabs = (double)((int64_t)l_begin * lane_k + s_local) * p.dtd;
-    t.sc[0] = (float)forcing_s(p.omega, tabs);
-    t.sc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
-    t.sc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
-  }
-  __syncthreads();
+  // s(t) at the three stage times of lane l's step come from the precomputed table
+  // sc[3 step + {0, 1, 2}] (FP64 sin costs thousands of cycles of one warp's FP64 pipe)
   for (int l = l_begin; l < l_end; ++l) {
     const int li = l - l_begin;
     if (threadIdx.x == 0 && l + 1 < l_end) {  // prefetch the next lane's tile
@@ -233,7 +227,8 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
       return;
     }
     const float* Q = t.q[0] + (li & 1) * TILE2;
-    const float c1 = t.sc[4 * (li & 1) + 0], c2 = t.sc[4 * (li & 1) + 1], c4 = t.sc[4 * (li & 1) + 2];
+    const float* scl = sc + 3 * ((int64_t)l * lane_k + s_local);
+    const float c1 = __ldg(scl), c2 = __ldg(scl + 1), c4 = __ldg(scl + 2);
     float qv[RG2], acc[RG2], yv[RG2];
 #pragma unroll
     for (int i = 0; i < RG2; ++i) qv[i] = Q[(row0 + i) * BX2 + col];
@@ -304,13 +299,6 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
       double s = block_sum(jl, t.red);
       if (threadIdx.x == 0) Jpart[(size_t)jrow * gridDim.x + tile] = dt_over_T * s;
     }
-    if (threadIdx.x == 0 && l + 1 < l_end) {
-      const double tabs = (double)((int64_t)(l + 1) * lane_k + s_local) * p.dtd;
-      float* nsc = t.sc + 4 * ((li + 1) & 1);
-      nsc[0] = (float)forcing_s(p.omega, tabs);
-      nsc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
-      nsc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
-    }
     __syncthreads();  // all reads of q[li & 1] and the stage buffers done before reuse
   }
 }
@@ -327,7 +315,7 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
                                                        int64_t s_local, int with_source,
                                                        const float* __restrict__ traj,
                                                        double src_scale, double* __restrict__ G,
-                                                       int* status) {
+                                                       const float* __restrict__ sc, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem t = carve(smem_raw);
   const int tile = blockIdx.x;
@@ -390,14 +378,10 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
       srcv[q] = (in && add_src) ? __ldg(es + gi) : 0.0f;
       gold[q] = in ? Gl[gi] : 0.0;
     }
-    if (threadIdx.x == 0) {
-      const double tabs = (double)s_abs * p.dtd;
-      t.sc[0] = (float)forcing_s(p.omega, tabs);
-      t.sc[1] = (float)forcing_s(p.omega, tabs + 0.5 * p.dtd);
-      t.sc[2] = (float)forcing_s(p.omega, tabs + p.dtd);
-    }
+    // s(t) at the step's stage times from the precomputed table
+    const float* scl = sc + 3 * s_abs;
+    const float c1 = __ldg(scl), c2 = __ldg(scl + 1), c4 = __ldg(scl + 2);
     __syncthreads();
-    const float c1 = t.sc[0], c2 = t.sc[1], c4 = t.sc[2];
     // kbar4 = dt/6 lambda on the whole halo-4 tile
     for (int e = threadIdx.x; e < TILE2; e += blockDim.x) ma[e] = dt / 6.0f * L[e];
     __syncthreads();
@@ -527,9 +511,22 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     ts[i] = dt * (-v[c - BX2] * p.inv2h + d);
     tn[i] = dt * (v[c + BX2] * p.inv2h + d);
   }
+  // this thread's interior points: their H and G values are loaded now, so that the
+  // global-memory latency passes during the first three powers
+  const bool cin = col >= G2 && col < G2 + TX2;
+  const int x = x0 + col - G2;  // domain column
+  const bool first = i0 == 0;
+  float hold[RG2];
+  double gold[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int row = row0 + i, y = y0 + row - G2;
+    const bool in = cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny;
+    hold[i] = (in && want_h && !first) ? H[(size_t)(y + G2) * p.Wp + (x + G2)] : 0.0f;
+    gold[i] = in ? G[(size_t)y * p.nx + x] : 0.0;
+  }
   const float* Xp = t.q[0];
   float xv[RG2], hacc[RG2], gacc[RG2];
-  const bool first = i0 == 0;
 #pragma unroll
   for (int i = 0; i < RG2; ++i) {
     xv[i] = Xp[(row0 + i) * BX2 + col];
@@ -562,8 +559,6 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
   }
   // power 4 on the interior; the interior's terms leave the tile
   float* Vout = V + (size_t)(1 - buf_in) * p.Hp * p.Wp;
-  const bool cin = col >= G2 && col < G2 + TX2;
-  const int x = x0 + col - G2;  // domain column
 #pragma unroll
   for (int i = 0; i < RG2; ++i) {
     const int row = row0 + i;
@@ -574,13 +569,8 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     const float xn = i + 1 < RG2 ? xv[i + 1] : Xp[c + BX2];
     const float y4 = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * xv[i];
     store_with_ghosts(Vout, p, x, y, y4);
-    if (want_h) {
-      float hv = fmaf(ka[4], y4, hacc[i]);
-      if (!first) hv += H[(size_t)(y + G2) * p.Wp + (x + G2)];
-      store_with_ghosts(H, p, x, y, hv);
-    }
-    const size_t gi = (size_t)y * p.nx + x;
-    G[gi] += (double)fmaf(kb[4], y4, gacc[i]);
+    if (want_h) store_with_ghosts(H, p, x, y, fmaf(ka[4], y4, hacc[i]) + hold[i]);
+    G[(size_t)y * p.nx + x] = gold[i] + (double)fmaf(kb[4], y4, gacc[i]);
   }
 }
 
@@ -758,8 +748,8 @@ static cudaError_t set_smem(const void* fn) {
 
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
-                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, float* traj,
-                           int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
+                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
+                           float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
                            int* status) {
   dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
   if (Jpart) {
@@ -767,14 +757,14 @@ cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUten
     if (e != cudaSuccess) return e;
     ad2_rk4_kernel<true><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
                                                               lanes_per_cta, buf_in, lane_k, s_local,
-                                                              traj, traj_row, Jpart, jrow, dt_over_T,
+                                                              sc, traj, traj_row, Jpart, jrow, dt_over_T,
                                                               status);
   } else {
     cudaError_t e = set_smem((const void*)ad2_rk4_kernel<false>);
     if (e != cudaSuccess) return e;
     ad2_rk4_kernel<false><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
                                                                lanes_per_cta, buf_in, lane_k, s_local,
-                                                               traj, traj_row, Jpart, jrow, dt_over_T,
+                                                               sc, traj, traj_row, Jpart, jrow, dt_over_T,
                                                                status);
   }
   return cudaGetLastError();
@@ -784,13 +774,13 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
                             int with_source, const float* traj, double src_scale, double* G,
-                            int* status) {
+                            const float* sc, int* status) {
   cudaError_t e = set_smem((const void*)ad2_rk4T_kernel);
   if (e != cudaSuccess) return e;
   dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
   ad2_rk4T_kernel<<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
                                                        lanes_per_cta, buf_in, lane_k, lane_off, s_local,
-                                                       with_source, traj, src_scale, G, status);
+                                                       with_source, traj, src_scale, G, sc, status);
   return cudaGetLastError();
 }
 

@@ -27,16 +27,19 @@ bool ad2_make_map(CUtensorMap* map, float* base, const Ad2Params& p, int depth, 
 // 3D map over [depth][Hp][Wp] FP32 with a box of box_x x box_y x box_depth elements.
 bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int depth, int box_x,
                       int box_y, int box_depth);
+// Tile-kernel RK4 steps of a group of lanes; lane l is at absolute step l * lane_k + s_local
+// (+ lane_off for the transposed step) and takes s(t) at its stage times from the table
+// sc[3 step + {0, 1, 2}] (launch_ad2_forcing_table over every step used).
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
-                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, float* traj,
-                           int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
+                           int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
+                           float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
                            int* status);
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
                             int with_source, const float* traj, double src_scale, double* G,
-                            int* status);
+                            const float* sc, int* status);
 cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const double* u,
                                  const double* v, const double* f, const double* ft, float* coef);
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,

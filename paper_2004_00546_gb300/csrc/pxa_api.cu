@@ -742,10 +742,10 @@ int prepare(pxa_ctx* c) {
     if (!ad2_make_map(&c->mapD, c->stD, a, 2, 1) || !ad2_make_map(&c->mapA, c->stA, a, 2 * P, 1) ||
         !ad2_make_map(&c->mapC, c->stC, a, 2, 1) || !ad2_make_map(&c->mapCoef, c->coef2, a, 3, 3))
       return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D state arrays");
+    if ((rc = alloc(c, &c->sc2, (size_t)3 * c->K))) return rc;
     c->roll2 = P > 1 && ad2_roll_ok(a);
     if (c->roll2) {
       if ((rc = alloc(c, &c->tcoef2, 4 * plane))) return rc;
-      if ((rc = alloc(c, &c->sc2, (size_t)3 * c->K))) return rc;
       if (!ad2_make_map_box(&c->mapA4, c->stA, a, 2 * P, 64, AD2_ROLL_BR, 1) ||
           !ad2_make_map_box(&c->mapT4, c->tcoef2, a, 4, 64, AD2_ROLL_BR, 4) ||
           !ad2_make_map_plain(&c->mapS4, c->traj2, 4, a.nx, a.ny, (int)c->K + 1, 64, AD2_ROLL_BR) ||
@@ -1660,13 +1660,14 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     return fail(c, PXA_ERR_INVALID, "ADVDIFF_2D Paraexp uses the stepper propagator (PXA_PHI_STEPPER)");
   PXA_CUDA(c, launch_ad2_pack_coef(st, a, c->op.u_dev, c->op.v_dev, c->control, c->target, c->coef2),
            "pack coefficients");
+  PXA_CUDA(c, launch_ad2_forcing_table(st, 0, K, a.dtd, a.omega, c->sc2), "forcing table");
   if (do_d) {
     ev_record(c, 0);
     // Eq. seriesDirect: serial FP32 RK4 of the response to f - f_true, storing every state
     PXA_CUDA(c, cudaMemsetAsync(c->stD, 0, sizeof(float) * plane, st), "zero state");
     PXA_CUDA(c, cudaMemsetAsync(c->traj2, 0, sizeof(float) * N, st), "zero row 0");
     for (int64_t s = 0; s < K; ++s) {
-      PXA_CUDA(c, launch_ad2_rk4(st, c->mapD, c->mapCoef, a, c->stD, 1, 1, 1, (int)(s & 1), 0, s,
+      PXA_CUDA(c, launch_ad2_rk4(st, c->mapD, c->mapCoef, a, c->stD, 1, 1, 1, (int)(s & 1), 0, s, c->sc2,
                                  c->traj2, s + 1, c->Jpart, s, a.dtd / c->T, c->status),
                "2d direct step");
     }
@@ -1684,7 +1685,6 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   const bool roll = c->roll2 && P > 1;
   if (roll) {
     PXA_CUDA(c, launch_ad2_pack_coefT(st, a, c->op.u_dev, c->op.v_dev, c->tcoef2), "A^T coefficients");
-    PXA_CUDA(c, launch_ad2_forcing_table(st, 0, K, a.dtd, a.omega, c->sc2), "forcing table");
   }
   for (int64_t j = 0; j < k; ++j) {
     const int64_t s_local = k - 1 - j;  // lane l at step l k + s_local
@@ -1695,7 +1695,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                "2d adjoint lanes");
     else
       PXA_CUDA(c, launch_ad2_rk4T(st, c->mapA, c->mapCoef, a, c->stA, P, P, lpc, (int)(j & 1), k, 0, s_local, 1,
-                                  c->traj2, src, c->G2buf, c->status),
+                                  c->traj2, src, c->G2buf, c->sc2, c->status),
                "2d adjoint lanes");
   }
   ev_record(c, 3);
@@ -1733,7 +1733,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                         Wbuf + (size_t)(lane + 1) * plane), "chain add");
       for (int64_t j = 0; j < k; ++j) {
         PXA_CUDA(c, launch_ad2_rk4T(st, c->mapC, c->mapCoef, a, c->stC, 1, 1, 1, bufc, 0,
-                                    (int64_t)lane * k, k - 1 - j, 0, nullptr, 0.0, c->GC, c->status),
+                                    (int64_t)lane * k, k - 1 - j, 0, nullptr, 0.0, c->GC, c->sc2, c->status),
                  "2d chain step");
         bufc ^= 1;
       }
@@ -2913,12 +2913,11 @@ int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, doub
   const int lpc = lanes >= 16 ? 16 : lanes;
   // lane l takes steps l*steps .. l*steps+steps-1 of one time axis
   const bool roll = ad2_roll_ok(a);
-  if (roll && c->scL_count < (int64_t)lanes * steps) {
+  if (c->scL_count < (int64_t)lanes * steps) {
     if ((rc = alloc(c, &c->scL, 3 * (size_t)lanes * steps))) return rc;
     c->scL_count = (int64_t)lanes * steps;
   }
-  if (roll)
-    PXA_CUDA(c, launch_ad2_forcing_table(st, 0, (int64_t)lanes * steps, a.dtd, a.omega, c->scL), "table");
+  PXA_CUDA(c, launch_ad2_forcing_table(st, 0, (int64_t)lanes * steps, a.dtd, a.omega, c->scL), "table");
   PXA_CUDA(c, cudaEventRecord(e0, st), "record");
   for (int64_t s = 0; s < steps; ++s) {
     if (roll) {
@@ -2926,7 +2925,7 @@ int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, doub
                                       c->scL + 3 * s, (int)steps, c->status), "lanes step");
     } else {
       PXA_CUDA(c, launch_ad2_rk4(st, c->mapL, c->mapCoef, a, c->stL, lanes, lanes, lpc, (int)(s & 1),
-                                 steps, s, nullptr, 0, nullptr, 0, 0.0, c->status), "lanes step");
+                                 steps, s, c->scL, nullptr, 0, nullptr, 0, 0.0, c->status), "lanes step");
     }
   }
   PXA_CUDA(c, cudaEventRecord(e1, st), "record");
