@@ -440,6 +440,143 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
   }
 }
 
+// One reverse step of the exact discrete adjoint of the RK4 map for one lane (the serial
+// adjoint and the stepper chain), in the register layout of ad2_rk4_kernel: thread
+// (tx, ty) owns tile column tx + 1 and RG2 rows of the halo-3 region, keeps dt times the
+// coefficients of A^T at its points in registers, takes vertical neighbours from its own
+// registers and horizontal ones (and the strip ends) from the previous stage's tile in
+// shared memory. With Z = A^T and lambda the incoming value (step s + 1):
+//   kbar4 = dt/6 lambda, kbar3 = dt/3 lambda + dt Z kbar4, kbar2 = dt/3 lambda + dt/2 Z kbar3,
+//   kbar1 = dt/6 lambda + dt/2 Z kbar2,
+//   lambda_s = lambda + Z (kbar4 + kbar3 + kbar2 + kbar1) (+ src_scale e_s when add_src),
+//   G += c4 kbar4 + c2 (kbar3 + kbar2) + c1 kbar1 (c1, c2, c4 = s(t) at the stage times of
+// step s, from the table sc). Z kbar4 = dt/6 Z lambda is formed from the lambda tile itself.
+__global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant__ CUtensorMap qmap,
+                                                           const __grid_constant__ CUtensorMap cmap,
+                                                           Ad2Params p, float* __restrict__ states, int buf_in,
+                                                           int64_t s_abs, int add_src,
+                                                           const float* __restrict__ traj, float src_scale,
+                                                           double* __restrict__ G, const float* __restrict__ sc,
+                                                           int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem t = carve(smem_raw);
+  const int tile = blockIdx.x;
+  const int tbx = tile % p.tiles_x, tby = tile / p.tiles_x;
+  const int x0 = tbx * TX2, y0 = tby * TY2;  // padded coordinates of the halo corner
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int col = tx + 1;
+  const bool colact = col <= BX2 - 2;
+  const int row0 = 1 + ty * RG2;
+  if (threadIdx.x == 0) {
+    mbar_init(&t.bar[0], 1);
+    mbar_init(&t.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
+    tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in, &t.bar[1]);
+  }
+  // the interior points' source and gradient values and the step's forcing factors, loaded
+  // while the copies fly
+  const bool cin = col >= G2 && col < G2 + TX2;
+  const int x = x0 + col - G2;  // domain column
+  const size_t N = (size_t)p.nx * p.ny;
+  const float* es = (add_src && traj) ? traj + (size_t)s_abs * N : nullptr;
+  float srcv[RG2];
+  double gold[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int row = row0 + i, y = y0 + row - G2;
+    const bool in = cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny;
+    const size_t gi = in ? (size_t)y * p.nx + x : 0;
+    srcv[i] = (in && es) ? __ldg(es + gi) : 0.0f;
+    gold[i] = in ? G[gi] : 0.0;
+  }
+  const float c1 = __ldg(sc + 3 * s_abs), c2 = __ldg(sc + 3 * s_abs + 1), c4 = __ldg(sc + 3 * s_abs + 2);
+  const bool ok0 = mbar_wait(&t.bar[0], 0);
+  const bool ok1 = mbar_wait(&t.bar[1], 0);
+  if (!(ok0 && ok1)) {
+    if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    (void)mbar_wait(&t.bar[0], 0);
+    (void)mbar_wait(&t.bar[1], 0);
+    return;
+  }
+  const float* u = t.coef;
+  const float* v = t.coef + TILE2;
+  const float d = p.nu * p.invh2, dt = p.dt, tc = -4.0f * d;
+  float tw[RG2], te[RG2], ts[RG2], tn[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int c = (row0 + i) * BX2 + col;
+    tw[i] = -u[c - 1] * p.inv2h + d;
+    te[i] = u[c + 1] * p.inv2h + d;
+    ts[i] = -v[c - BX2] * p.inv2h + d;
+    tn[i] = v[c + BX2] * p.inv2h + d;
+  }
+  const float* L = t.q[0];
+  float lam[RG2], ln[RG2], kb[RG2], g[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) lam[i] = L[(row0 + i) * BX2 + col];
+  // stage 1 (halo 3): Z kbar4 = dt/6 Z lambda
+  {
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) {
+      const int c = (row0 + i) * BX2 + col;
+      const float xs = i > 0 ? lam[i - 1] : L[c - BX2];
+      const float xn = i + 1 < RG2 ? lam[i + 1] : L[c + BX2];
+      const float z = tw[i] * L[c - 1] + te[i] * L[c + 1] + ts[i] * xs + tn[i] * xn + tc * lam[i];
+      const float nv = (dt / 6.0f) * z;
+      kb[i] = (dt / 3.0f) * lam[i] + dt * nv;  // kbar3
+      ln[i] = lam[i] + nv;
+      g[i] = c4 * ((dt / 6.0f) * lam[i]) + c2 * kb[i];
+      if (colact) t.ya[c] = kb[i];
+    }
+    __syncthreads();
+  }
+  // stages 2 and 3: Z kbar3 -> kbar2 (halo 2), Z kbar2 -> kbar1 (halo 1)
+#pragma unroll
+  for (int stg = 2; stg <= 3; ++stg) {
+    const float* Xp = stg == 2 ? t.ya : t.yb;
+    float* Xn = stg == 2 ? t.yb : t.ya;
+    const float wl = stg == 2 ? dt / 3.0f : dt / 6.0f;
+    const float cg = stg == 2 ? c2 : c1;
+    float nk[RG2];
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) {
+      const int c = (row0 + i) * BX2 + col;
+      const float xs = i > 0 ? kb[i - 1] : Xp[c - BX2];
+      const float xn = i + 1 < RG2 ? kb[i + 1] : Xp[c + BX2];
+      const float nv = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * kb[i];
+      ln[i] += nv;
+      nk[i] = wl * lam[i] + (0.5f * dt) * nv;
+      g[i] += cg * nk[i];
+      if (colact) Xn[c] = nk[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RG2; ++i) kb[i] = nk[i];
+  }
+  // stage 4 on the interior: lambda_s = ln + Z kbar1 (+ source); the gradient terms leave
+  float* out = states + (size_t)(1 - buf_in) * p.Hp * p.Wp;
+  const float* Xp = t.ya;
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int row = row0 + i;
+    const int c = row * BX2 + col;
+    const int y = y0 + row - G2;
+    if (!(cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny)) continue;
+    const float xs = i > 0 ? kb[i - 1] : Xp[c - BX2];
+    const float xn = i + 1 < RG2 ? kb[i + 1] : Xp[c + BX2];
+    const float nv = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * kb[i];
+    const float lnew = ln[i] + nv + src_scale * srcv[i];
+    store_with_ghosts(out, p, x, y, lnew);
+    G[(size_t)y * p.nx + x] = gold[i] + (double)g[i];
+  }
+}
+
 // ---- the chain's polynomial propagator (PXA_PROP_POLY) ---------------------------------
 // The summed homogeneous adjoint problems of one chain segment of kk RK4 steps are carried
 // by the power series of the stepper's own propagator, h <- sum_{i<=m} a_i Z^i h' with
@@ -775,6 +912,16 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
                             int with_source, const float* traj, double src_scale, double* G,
                             const float* sc, int* status) {
+  if (lanes == 1 && map_lanes == 1) {
+    // one lane: the register-layout step
+    cudaError_t e = set_smem((const void*)ad2_rk4T1_kernel);
+    if (e != cudaSuccess) return e;
+    const int64_t s_abs = lane_off + s_local;
+    ad2_rk4T1_kernel<<<p.tiles_x * p.tiles_y, 256, ad2_smem_bytes(), st>>>(
+        qmap, cmap, p, states, buf_in, s_abs, (with_source && s_local > 0 && traj) ? 1 : 0, traj,
+        (float)src_scale, G, sc, status);
+    return cudaGetLastError();
+  }
   cudaError_t e = set_smem((const void*)ad2_rk4T_kernel);
   if (e != cudaSuccess) return e;
   dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
