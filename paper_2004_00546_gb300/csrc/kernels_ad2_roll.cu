@@ -529,6 +529,42 @@ bool ad2_roll_ok(const Ad2Params& p) {
          ad2_roll_rows(p.ny) % 8 == 0;
 }
 
+// Rows per segment for a launch of `lanes` lanes: among 128, 64, 32, 16 and 8 rows (at most
+// ny), the one with the least estimated time, counted as whole waves of tasks (co-resident
+// blocks x warps per block, one task per warp) times the rows one task steps (its segment
+// and the 8 rows of overlap). A grid a little above one wave otherwise runs a second,
+// mostly empty wave. `per_sm` caches the blocks per SM of the kernel (0: not known yet).
+static int roll_rows_for(int nx, int ny, long long lanes, const void* fn, int warps, size_t smem, int& per_sm) {
+  int dev = 0, sms = 0;
+  if (per_sm == 0) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * warps, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return ad2_roll_rows(ny);
+    }
+    per_sm = per;
+  }
+  if (per_sm <= 0 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ad2_roll_rows(ny);
+  }
+  const long long cap = (long long)per_sm * sms * warps;
+  const long long nstrips = (nx + RS - 1) / RS;
+  int best = ad2_roll_rows(ny);
+  long long best_cost = -1;
+  for (int hs = 128; hs >= 8; hs /= 2) {
+    if (hs > ny) continue;
+    const long long tasks = lanes * nstrips * ((ny + hs - 1) / hs);
+    const long long cost = ((tasks + cap - 1) / cap) * (hs + 8);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = hs;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_ad2_forcing_table(cudaStream_t st, int64_t s0, int64_t count, double dt,
                                      double omega, float* sc) {
   if (count <= 0) return cudaSuccess;
@@ -539,13 +575,14 @@ cudaError_t launch_ad2_forcing_table(cudaStream_t st, int64_t s0, int64_t count,
 cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                                 const Ad2Params& p, float* states, int lanes, int buf_in,
                                 const float* sc, int sc_stride, int* status) {
-  const int Hs = ad2_roll_rows(p.ny);
-  const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
-  const long long tasks = (long long)lanes * nstrips * nsegs;
-  const unsigned blocks = (unsigned)((tasks + RWARPS - 1) / RWARPS);
   const size_t sh = sizeof(float) * (size_t)RWARPS * RING_FLOATS;
   cudaError_t e = cudaFuncSetAttribute(ad2_rk4_roll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
+  static int per_sm = 0;
+  const int Hs = roll_rows_for(p.nx, p.ny, lanes, (const void*)ad2_rk4_roll_kernel, RWARPS, sh, per_sm);
+  const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
+  const long long tasks = (long long)lanes * nstrips * nsegs;
+  const unsigned blocks = (unsigned)((tasks + RWARPS - 1) / RWARPS);
   ad2_rk4_roll_kernel<<<blocks, 32 * RWARPS, sh, st>>>(qmap, cmap, p, states, lanes, buf_in, nstrips, nsegs,
                                                        Hs, sc, sc_stride, status);
   return cudaGetLastError();
@@ -557,13 +594,14 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
                                  const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
                                  int* status) {
   if (count <= 0 || lane0 < 0 || lane0 + count > lanes) return cudaErrorInvalidValue;
-  const int Hs = ad2_roll_rows(p.ny);
-  const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
-  const long long tasks = (long long)count * nstrips * nsegs;
-  const unsigned blocks = (unsigned)((tasks + TWARPS - 1) / TWARPS);
   const size_t sh = sizeof(float) * (size_t)TWARPS * TRING_FLOATS;
   cudaError_t e = cudaFuncSetAttribute(ad2_rk4T_roll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
+  static int per_sm = 0;
+  const int Hs = roll_rows_for(p.nx, p.ny, count, (const void*)ad2_rk4T_roll_kernel, TWARPS, sh, per_sm);
+  const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
+  const long long tasks = (long long)count * nstrips * nsegs;
+  const unsigned blocks = (unsigned)((tasks + TWARPS - 1) / TWARPS);
   ad2_rk4T_roll_kernel<<<blocks, 32 * TWARPS, sh, st>>>(qmap, tmap, smap, gmap, p, states, G, lanes, lane0,
                                                          count, buf_in, nstrips, nsegs, Hs, sc, zsrc0, z_stride,
                                                          src_scale, add_src, status);
