@@ -48,6 +48,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization
+// attribute may start while the kernel before it in the stream still runs. It must wait
+// here before it touches anything that kernel writes (or reads what it overwrites);
+// before the wait it may only read data written by kernels that finished earlier. Without
+// the attribute the wait returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel in the stream (if launched with the attribute) start its blocks
+// once every block of this grid has passed this point.
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- small dense matrices in shared memory, row-major, leading dimension kLD ----
 __device__ __forceinline__ void dense_identity(double* A, int d) {
   for (int e = threadIdx.x; e < d * d; e += blockDim.x) {

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels_ad2.cuh"
@@ -70,6 +71,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ double forcing_s(double omega, double t) {
   return omega == 0.0 ? 1.0 : sin(omega * t);
+}
+
+// acc (hi, lo) += g in FP32 arithmetic: Knuth's two-sum gives the rounding error of hi + g
+// exactly, and it is carried in lo (about 2^-44 relative overall, without the FP64 pipe,
+// which issues one warp instruction per 64 cycles on GB300). Rounded adds, never fused.
+__device__ __forceinline__ float2 df_add(float2 acc, float g) {
+  const float s = __fadd_rn(acc.x, g);
+  const float bp = __fsub_rn(s, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bp)), __fsub_rn(g, bp));
+  return make_float2(s, __fadd_rn(acc.y, err));
 }
 
 // (A x)_c on a tile (row pitch BX2): advective central differences + 5-point Laplacian.
@@ -176,19 +187,19 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // the coefficient tile (written before the sweep) is loaded before the wait for the
+  // previous step; the state tile after it
   if (threadIdx.x == 0) {
     mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
     tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
-    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
-    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in * map_lanes + l_begin, &t.bar[1]);
   }
+  grid_dep_trigger();
   float* outbase = states + (size_t)(1 - buf_in) * map_lanes * p.Hp * p.Wp;
   bool ok = mbar_wait(&t.bar[0], 0);
   if (!ok) {
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
-    // let the two copies issued above land (bounded again) before the block can leave
+    // let the copy issued above land (bounded again) before the block can leave
     (void)mbar_wait(&t.bar[0], 0);
-    (void)mbar_wait(&t.bar[1], 0);
     return;
   }
   // per-point stencil coefficients: (A x)_c = cE x_e + cW x_w + cN x_n + cS x_s + cC x_c
@@ -203,6 +214,11 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
     cN[i] = -vv * p.inv2h + d;
     cS[i] = vv * p.inv2h + d;
     fr[i] = t.coef[2 * TILE2 + c];
+  }
+  grid_dep_wait();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in * map_lanes + l_begin, &t.bar[1]);
   }
   const float dt = p.dt, hdt = 0.5f * p.dt, sdt = p.dt / 6.0f;
   float* Y0 = t.ya;
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
     }
     // stage 4 on the interior: q_new = q + dt/6 (k1 + 2 k2 + 2 k3 + k4)
     float* out = outbase + (size_t)l * p.Hp * p.Wp;
-    double jl = 0.0;
+    float jl = 0.0f;  // FP32 within the thread and warp, FP64 across warps and steps
     {
       const float* Xp = Y0;
       const bool cin = col >= G2 && col < G2 + TX2;
@@ -291,13 +307,23 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
           float qn = qv[i] + sdt * (acc[i] + k);
           store_with_ghosts(out, p, x, y, qn);
           if (traj && l == 0) traj[(size_t)traj_row * p.nx * p.ny + (size_t)y * p.nx + x] = qn;
-          if (WITH_J) jl += (double)(qn * qn);
+          if (WITH_J) jl = fmaf(qn, qn, jl);
         }
       }
     }
     if (WITH_J) {
-      double s = block_sum(jl, t.red);
-      if (threadIdx.x == 0) Jpart[(size_t)jrow * gridDim.x + tile] = dt_over_T * s;
+      // the few FP64 instructions this takes matter on GB300 (one FP64 warp instruction per
+      // 64 cycles): the squares of a thread's points and a warp's partials are summed in
+      // FP32, the eight warp sums in FP64
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, o);
+      if ((threadIdx.x & 31) == 0) t.red[threadIdx.x >> 5] = (double)jl;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sj = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sj += t.red[w];
+        Jpart[(size_t)jrow * gridDim.x + tile] = dt_over_T * sj;
+      }
     }
     __syncthreads();  // all reads of q[li & 1] and the stage buffers done before reuse
   }
@@ -450,13 +476,14 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
 //   kbar1 = dt/6 lambda + dt/2 Z kbar2,
 //   lambda_s = lambda + Z (kbar4 + kbar3 + kbar2 + kbar1) (+ src_scale e_s when add_src),
 //   G += c4 kbar4 + c2 (kbar3 + kbar2) + c1 kbar1 (c1, c2, c4 = s(t) at the stage times of
-// step s, from the table sc). Z kbar4 = dt/6 Z lambda is formed from the lambda tile itself.
+// step s, from the table sc), G a double-float (hi, lo) FP32 pair per point (df_add).
+// Z kbar4 = dt/6 Z lambda is formed from the lambda tile itself.
 __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant__ CUtensorMap qmap,
                                                            const __grid_constant__ CUtensorMap cmap,
                                                            Ad2Params p, float* __restrict__ states, int buf_in,
                                                            int64_t s_abs, int add_src,
                                                            const float* __restrict__ traj, float src_scale,
-                                                           double* __restrict__ G, const float* __restrict__ sc,
+                                                           float2* __restrict__ G, const float* __restrict__ sc,
                                                            int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem t = carve(smem_raw);
@@ -473,35 +500,28 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // before the wait for the previous step: the coefficient tile, the source rows of the
+  // direct trajectory and the step's forcing factors (all written before the sweep)
   if (threadIdx.x == 0) {
     mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
     tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
-    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
-    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in, &t.bar[1]);
   }
-  // the interior points' source and gradient values and the step's forcing factors, loaded
-  // while the copies fly
+  grid_dep_trigger();
   const bool cin = col >= G2 && col < G2 + TX2;
   const int x = x0 + col - G2;  // domain column
   const size_t N = (size_t)p.nx * p.ny;
   const float* es = (add_src && traj) ? traj + (size_t)s_abs * N : nullptr;
   float srcv[RG2];
-  double gold[RG2];
 #pragma unroll
   for (int i = 0; i < RG2; ++i) {
     const int row = row0 + i, y = y0 + row - G2;
     const bool in = cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny;
-    const size_t gi = in ? (size_t)y * p.nx + x : 0;
-    srcv[i] = (in && es) ? __ldg(es + gi) : 0.0f;
-    gold[i] = in ? G[gi] : 0.0;
+    srcv[i] = (in && es) ? __ldg(es + (size_t)y * p.nx + x) : 0.0f;
   }
   const float c1 = __ldg(sc + 3 * s_abs), c2 = __ldg(sc + 3 * s_abs + 1), c4 = __ldg(sc + 3 * s_abs + 2);
-  const bool ok0 = mbar_wait(&t.bar[0], 0);
-  const bool ok1 = mbar_wait(&t.bar[1], 0);
-  if (!(ok0 && ok1)) {
+  if (!mbar_wait(&t.bar[0], 0)) {
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
     (void)mbar_wait(&t.bar[0], 0);
-    (void)mbar_wait(&t.bar[1], 0);
     return;
   }
   const float* u = t.coef;
@@ -515,6 +535,24 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
     te[i] = u[c + 1] * p.inv2h + d;
     ts[i] = -v[c - BX2] * p.inv2h + d;
     tn[i] = v[c + BX2] * p.inv2h + d;
+  }
+  // after it: the lambda tile and the gradient values the previous step wrote
+  grid_dep_wait();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &qmap, x0, y0, buf_in, &t.bar[1]);
+  }
+  float2 gold[RG2];
+#pragma unroll
+  for (int i = 0; i < RG2; ++i) {
+    const int row = row0 + i, y = y0 + row - G2;
+    const bool in = cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny;
+    gold[i] = in ? G[(size_t)y * p.nx + x] : make_float2(0.0f, 0.0f);
+  }
+  if (!mbar_wait(&t.bar[1], 0)) {
+    if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    (void)mbar_wait(&t.bar[1], 0);
+    return;
   }
   const float* L = t.q[0];
   float lam[RG2], ln[RG2], kb[RG2], g[RG2];
@@ -573,7 +611,7 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
     const float nv = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * kb[i];
     const float lnew = ln[i] + nv + src_scale * srcv[i];
     store_with_ghosts(out, p, x, y, lnew);
-    G[(size_t)y * p.nx + x] = gold[i] + (double)g[i];
+    G[(size_t)y * p.nx + x] = df_add(gold[i], g[i]);
   }
 }
 
@@ -588,15 +626,16 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
 // and RG2 rows; tau times the coefficients of A^T at its points in registers). Interior
 // points add their terms: H = (i0 == 0 ? a_0 v_0 : H) + sum_j a_{i0+j} v_{i0+j} (FP32,
 // padded with ghosts; skipped when want_h == 0) and G += (i0 == 0 ? b_0 v_0 : 0) + sum_j
-// b_{i0+j} v_{i0+j} (FP32 within the launch, FP64 across launches); v_{i0+4} goes to the
-// other plane of V (padded with ghosts). ca / cb hold at least i0 + 5 coefficients.
+// b_{i0+j} v_{i0+j} (FP32 within the launch, a double-float pair across launches, df_add);
+// v_{i0+4} goes to the other plane of V (padded with ghosts). ca / cb hold at least i0 + 5
+// coefficients.
 __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant__ CUtensorMap vmap,
                                                           const __grid_constant__ CUtensorMap cmap,
                                                           Ad2Params p, float tau, float* __restrict__ V,
                                                           int buf_in, int i0, const float* __restrict__ ca,
                                                           const double* __restrict__ cb,
                                                           float* __restrict__ H, int want_h,
-                                                          double* __restrict__ G, int* status) {
+                                                          float2* __restrict__ G, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem t = carve(smem_raw);
   const int tile = blockIdx.x;
@@ -612,26 +651,22 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // before the wait for the previous launch: the coefficient tile and this launch's series
+  // coefficients (the same for every thread; all written before the chain)
   if (threadIdx.x == 0) {
     mbar_expect_tx(&t.bar[0], 3 * TILE2 * sizeof(float));
     tma_load_3d(t.coef, &cmap, x0, y0, 0, &t.bar[0]);
-    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
-    tma_load_3d(t.q[0], &vmap, x0, y0, buf_in, &t.bar[1]);
   }
-  // this launch's series coefficients (the same for every thread), read while the copies fly
+  grid_dep_trigger();
   float ka[5], kb[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
     ka[j] = __ldg(ca + i0 + j);
     kb[j] = (float)__ldg(cb + i0 + j);
   }
-  const bool ok0 = mbar_wait(&t.bar[0], 0);
-  const bool ok1 = mbar_wait(&t.bar[1], 0);
-  if (!(ok0 && ok1)) {
+  if (!mbar_wait(&t.bar[0], 0)) {
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
-    // let both copies land (bounded again) before the block can leave
     (void)mbar_wait(&t.bar[0], 0);
-    (void)mbar_wait(&t.bar[1], 0);
     return;
   }
   const float* u = t.coef;
@@ -648,19 +683,29 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     ts[i] = dt * (-v[c - BX2] * p.inv2h + d);
     tn[i] = dt * (v[c + BX2] * p.inv2h + d);
   }
-  // this thread's interior points: their H and G values are loaded now, so that the
-  // global-memory latency passes during the first three powers
+  // after the wait: the power tile, and this thread's interior H and G values (loaded now,
+  // so that their latency passes during the first three powers)
+  grid_dep_wait();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
+    tma_load_3d(t.q[0], &vmap, x0, y0, buf_in, &t.bar[1]);
+  }
   const bool cin = col >= G2 && col < G2 + TX2;
   const int x = x0 + col - G2;  // domain column
   const bool first = i0 == 0;
   float hold[RG2];
-  double gold[RG2];
+  float2 gold[RG2];
 #pragma unroll
   for (int i = 0; i < RG2; ++i) {
     const int row = row0 + i, y = y0 + row - G2;
     const bool in = cin && row >= G2 && row < G2 + TY2 && x < p.nx && y < p.ny;
     hold[i] = (in && want_h && !first) ? H[(size_t)(y + G2) * p.Wp + (x + G2)] : 0.0f;
-    gold[i] = in ? G[(size_t)y * p.nx + x] : 0.0;
+    gold[i] = in ? G[(size_t)y * p.nx + x] : make_float2(0.0f, 0.0f);
+  }
+  if (!mbar_wait(&t.bar[1], 0)) {
+    if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
+    (void)mbar_wait(&t.bar[1], 0);
+    return;
   }
   const float* Xp = t.q[0];
   float xv[RG2], hacc[RG2], gacc[RG2];
@@ -707,7 +752,7 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     const float y4 = tw[i] * Xp[c - 1] + te[i] * Xp[c + 1] + ts[i] * xs + tn[i] * xn + tc * xv[i];
     store_with_ghosts(Vout, p, x, y, y4);
     if (want_h) store_with_ghosts(H, p, x, y, fmaf(ka[4], y4, hacc[i]) + hold[i]);
-    G[(size_t)y * p.nx + x] = gold[i] + (double)fmaf(kb[4], y4, gacc[i]);
+    G[(size_t)y * p.nx + x] = df_add(gold[i], fmaf(kb[4], y4, gacc[i]));
   }
 }
 
@@ -736,6 +781,14 @@ __global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, 
       }
   }
   if (i <= m) b[(size_t)s * (m + 1) + i] = acc;
+}
+
+// G[i] += hi + lo of the double-float accumulator D[i] (FP64), i < count.
+__global__ void ad2_df_flush_kernel(size_t count, double* __restrict__ G, const float2* __restrict__ D) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = D[e];
+    G[e] += (double)v.x + (double)v.y;
+  }
 }
 
 // dst = a + b over `count` elements (b may be NULL: a copy).
@@ -879,6 +932,24 @@ bool ad2_make_map_plain(CUtensorMap* map, void* base, int elem_bytes, int nx, in
   return r == CUDA_SUCCESS;
 }
 
+// Launch with or without the programmatic-serialization attribute (the kernel may then
+// start while the previous kernel in the stream finishes; see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_ex(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
 static cudaError_t set_smem(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ad2_smem_bytes());
 }
@@ -887,40 +958,35 @@ cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUten
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
                            float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
-                           int* status) {
+                           int* status, int pdl) {
   dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
   if (Jpart) {
     cudaError_t e = set_smem((const void*)ad2_rk4_kernel<true>);
     if (e != cudaSuccess) return e;
-    ad2_rk4_kernel<true><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
-                                                              lanes_per_cta, buf_in, lane_k, s_local,
-                                                              sc, traj, traj_row, Jpart, jrow, dt_over_T,
-                                                              status);
-  } else {
-    cudaError_t e = set_smem((const void*)ad2_rk4_kernel<false>);
-    if (e != cudaSuccess) return e;
-    ad2_rk4_kernel<false><<<grid, 256, ad2_smem_bytes(), st>>>(qmap, cmap, p, states, lanes, map_lanes,
-                                                               lanes_per_cta, buf_in, lane_k, s_local,
-                                                               sc, traj, traj_row, Jpart, jrow, dt_over_T,
-                                                               status);
+    return launch_ex(ad2_rk4_kernel<true>, grid, dim3(256), ad2_smem_bytes(), st, pdl != 0, qmap, cmap, p, states,
+                     lanes, map_lanes, lanes_per_cta, buf_in, lane_k, s_local, sc, traj, traj_row, Jpart, jrow,
+                     dt_over_T, status);
   }
-  return cudaGetLastError();
+  cudaError_t e = set_smem((const void*)ad2_rk4_kernel<false>);
+  if (e != cudaSuccess) return e;
+  return launch_ex(ad2_rk4_kernel<false>, grid, dim3(256), ad2_smem_bytes(), st, pdl != 0, qmap, cmap, p, states,
+                   lanes, map_lanes, lanes_per_cta, buf_in, lane_k, s_local, sc, traj, traj_row, Jpart, jrow,
+                   dt_over_T, status);
 }
 
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
                             int with_source, const float* traj, double src_scale, double* G,
-                            const float* sc, int* status) {
-  if (lanes == 1 && map_lanes == 1) {
-    // one lane: the register-layout step
+                            const float* sc, int* status, int pdl, float2* Gdf) {
+  if (lanes == 1 && map_lanes == 1 && Gdf) {
+    // one lane: the register-layout step, gradient into the double-float accumulator
     cudaError_t e = set_smem((const void*)ad2_rk4T1_kernel);
     if (e != cudaSuccess) return e;
     const int64_t s_abs = lane_off + s_local;
-    ad2_rk4T1_kernel<<<p.tiles_x * p.tiles_y, 256, ad2_smem_bytes(), st>>>(
-        qmap, cmap, p, states, buf_in, s_abs, (with_source && s_local > 0 && traj) ? 1 : 0, traj,
-        (float)src_scale, G, sc, status);
-    return cudaGetLastError();
+    return launch_ex(ad2_rk4T1_kernel, dim3(p.tiles_x * p.tiles_y), dim3(256), ad2_smem_bytes(), st, pdl != 0,
+                     qmap, cmap, p, states, buf_in, s_abs, (with_source && s_local > 0 && traj) ? 1 : 0, traj,
+                     (float)src_scale, Gdf, sc, status);
   }
   cudaError_t e = set_smem((const void*)ad2_rk4T_kernel);
   if (e != cudaSuccess) return e;
@@ -933,12 +999,11 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
 
 cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
                             float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
-                            int want_h, double* G, int* status) {
+                            int want_h, float2* G, int* status, int pdl) {
   cudaError_t e = set_smem((const void*)ad2_poly_kernel);
   if (e != cudaSuccess) return e;
-  ad2_poly_kernel<<<p.tiles_x * p.tiles_y, 256, ad2_smem_bytes(), st>>>(vmap, cmap, p, tau, V, buf_in, i0, ca, cb,
-                                                                        H, want_h, G, status);
-  return cudaGetLastError();
+  return launch_ex(ad2_poly_kernel, dim3(p.tiles_x * p.tiles_y), dim3(256), ad2_smem_bytes(), st, pdl != 0, vmap,
+                   cmap, p, tau, V, buf_in, i0, ca, cb, H, want_h, G, status);
 }
 
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
@@ -946,6 +1011,12 @@ cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m
   if (segments < 1) return cudaSuccess;
   if (m < 0 || m >= 256) return cudaErrorInvalidValue;
   ad2_poly_forcing_kernel<<<segments, 256, 0, st>>>(kk, m, dt, omega, Q, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ad2_df_flush(cudaStream_t st, size_t count, double* G, const float2* D) {
+  const unsigned blocks = (unsigned)std::min<size_t>((count + 255) / 256, 4096);
+  ad2_df_flush_kernel<<<blocks, 256, 0, st>>>(count, G, D);
   return cudaGetLastError();
 }
 

@@ -29,17 +29,23 @@ bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int dep
                       int box_y, int box_depth);
 // Tile-kernel RK4 steps of a group of lanes; lane l is at absolute step l * lane_k + s_local
 // (+ lane_off for the transposed step) and takes s(t) at its stage times from the table
-// sc[3 step + {0, 1, 2}] (launch_ad2_forcing_table over every step used).
+// sc[3 step + {0, 1, 2}] (launch_ad2_forcing_table over every step used). pdl != 0 (the
+// single-lane kernels): launched with programmatic dependent launch, so the coefficient
+// tile and the table are read while the previous kernel in the stream finishes; allowed
+// only when that kernel wrote neither of them (e.g. the previous step). The transposed step
+// of one lane (lanes == map_lanes == 1) with Gdf != NULL runs the register-layout kernel and
+// adds its forcing-gradient terms to the double-float accumulator Gdf ([ny][nx] (hi, lo)
+// FP32 pairs; launch_ad2_df_flush moves it into an FP64 gradient); otherwise to G (FP64).
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
                            float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
-                           int* status);
+                           int* status, int pdl);
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
                             int with_source, const float* traj, double src_scale, double* G,
-                            const float* sc, int* status);
+                            const float* sc, int* status, int pdl, float2* Gdf);
 cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const double* u,
                                  const double* v, const double* f, const double* ft, float* coef);
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
@@ -80,10 +86,14 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
 // v_{i0+j} = (tau A^T)^j v_{i0}, j = 1..4, on every tile from plane buf_in of V (vmap: ad2_make_map
 // over V with depth 2), writes v_{i0+4} to the other plane, and adds the interior's terms
 // a_i v_i to H (padded plane; H = a_0 v_0 + ... when i0 == 0; skipped when want_h == 0) and
-// b_i v_i to G (FP64 [ny][nx]). ca (FP32) and cb (FP64) hold the coefficients 0 .. i0 + 4.
+// b_i v_i to G (a double-float accumulator, [ny][nx] (hi, lo) FP32 pairs). ca (FP32) and cb (FP64) hold the coefficients 0 .. i0 + 4.
+// pdl != 0: programmatic dependent launch (the coefficient tile and ca, cb are read before
+// the wait for the previous kernel, which must not have written them).
 cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
                             float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
-                            int want_h, double* G, int* status);
+                            int want_h, float2* G, int* status, int pdl);
+// G[i] += hi + lo of the double-float accumulator D (count points, FP64 G).
+cudaError_t launch_ad2_df_flush(cudaStream_t st, size_t count, double* G, const float2* D);
 // The forcing-gradient coefficients b[s][0..m] of `segments` chain segments of kk steps
 // from the omega-free families Q = [3][kk][m+1] (m < 256).
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
