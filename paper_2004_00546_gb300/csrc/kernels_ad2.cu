@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
 
 // One reverse step of the exact discrete adjoint of the RK4 map for a group of lanes:
 // lambda_s = M^T lambda_{s+1} (+ (2dt/T) e_s when with_source and s_local > 0), and
-// G += sum of the stage terms s_i kbar_i (the forcing gradient, FP64 accumulator).
+// G += sum of the stage terms s_i kbar_i (the forcing gradient, a double-float accumulator).
 // Lane l is at absolute step l * lane_k + s_local (its time lane_base + ...).
 __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ CUtensorMap qmap,
                                                        const __grid_constant__ CUtensorMap cmap,
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
                                                        int buf_in, int64_t lane_k, int64_t lane_off,
                                                        int64_t s_local, int with_source,
                                                        const float* __restrict__ traj,
-                                                       double src_scale, double* __restrict__ G,
+                                                       double src_scale, float2* __restrict__ G,
                                                        const float* __restrict__ sc, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem t = carve(smem_raw);
@@ -390,11 +390,11 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
     // the source and gradient values of this thread's interior points, loaded now so
     // that their global-memory latency passes during the four stencil phases below
     constexpr int NQ = (TX2 * TY2 + 255) / 256;
-    double* Gl = G + (size_t)l * p.nx * p.ny;
+    float2* Gl = G + (size_t)l * p.nx * p.ny;
     const float* es = traj ? traj + (size_t)s_abs * p.nx * p.ny : nullptr;
     const bool add_src = with_source && s_local > 0 && es;
     float srcv[NQ];
-    double gold[NQ];
+    float2 gold[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int e = threadIdx.x + q * 256;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
       const bool in = e < TX2 * TY2 && x < p.nx && y < p.ny;
       const size_t gi = in ? (size_t)y * p.nx + x : 0;
       srcv[q] = (in && add_src) ? __ldg(es + gi) : 0.0f;
-      gold[q] = in ? Gl[gi] : 0.0;
+      gold[q] = in ? Gl[gi] : make_float2(0.0f, 0.0f);
     }
     // s(t) at the step's stage times from the precomputed table
     const float* scl = sc + 3 * s_abs;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) ad2_rk4T_kernel(const __grid_constant__ C
       if (add_src) lam += (float)src_scale * srcv[q];
       store_with_ghosts(out, p, x, y, lam);
       float gstep = g4[q] + c2 * ma[c] + c1 * mb[c];
-      Gl[gi] = gold[q] + (double)gstep;
+      Gl[gi] = df_add(gold[q], gstep);
     }
     __syncthreads();
   }
@@ -783,14 +783,6 @@ __global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, 
   if (i <= m) b[(size_t)s * (m + 1) + i] = acc;
 }
 
-// G[i] += hi + lo of the double-float accumulator D[i] (FP64), i < count.
-__global__ void ad2_df_flush_kernel(size_t count, double* __restrict__ G, const float2* __restrict__ D) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
-    const float2 v = D[e];
-    G[e] += (double)v.x + (double)v.y;
-  }
-}
-
 // dst = a + b over `count` elements (b may be NULL: a copy).
 __global__ void ad2_sum2_kernel(size_t count, float* __restrict__ dst, const float* __restrict__ a,
                                 const float* __restrict__ b) {
@@ -868,13 +860,17 @@ __global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t coun
   }
 }
 
-// grad = sum over lanes of G[l] (+ extra), FP64.
-__global__ void ad2_sum_grad_kernel(size_t N, int lanes, const double* __restrict__ G,
-                                    const double* __restrict__ extra, double* __restrict__ grad,
+// grad = sum over lanes of G[l] (+ extra), FP64 from the double-float accumulators.
+__global__ void ad2_sum_grad_kernel(size_t N, int lanes, const float2* __restrict__ G,
+                                    const float2* __restrict__ extra, double* __restrict__ grad,
                                     int* status) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    double acc = extra ? extra[i] : 0.0;
-    for (int l = 0; l < lanes; ++l) acc += G[(size_t)l * N + i];
+    double acc = 0.0;
+    if (extra) acc = (double)extra[i].x + (double)extra[i].y;
+    for (int l = 0; l < lanes; ++l) {
+      const float2 v = G[(size_t)l * N + i];
+      acc += (double)v.x + (double)v.y;
+    }
     grad[i] = acc;
     if (!isfinite(acc)) set_status(status, PXA_ERR_NONFINITE);
   }
@@ -977,16 +973,16 @@ cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUten
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
-                            int with_source, const float* traj, double src_scale, double* G,
-                            const float* sc, int* status, int pdl, float2* Gdf) {
-  if (lanes == 1 && map_lanes == 1 && Gdf) {
-    // one lane: the register-layout step, gradient into the double-float accumulator
+                            int with_source, const float* traj, double src_scale, float2* G,
+                            const float* sc, int* status, int pdl) {
+  if (lanes == 1 && map_lanes == 1) {
+    // one lane: the register-layout step
     cudaError_t e = set_smem((const void*)ad2_rk4T1_kernel);
     if (e != cudaSuccess) return e;
     const int64_t s_abs = lane_off + s_local;
     return launch_ex(ad2_rk4T1_kernel, dim3(p.tiles_x * p.tiles_y), dim3(256), ad2_smem_bytes(), st, pdl != 0,
                      qmap, cmap, p, states, buf_in, s_abs, (with_source && s_local > 0 && traj) ? 1 : 0, traj,
-                     (float)src_scale, Gdf, sc, status);
+                     (float)src_scale, G, sc, status);
   }
   cudaError_t e = set_smem((const void*)ad2_rk4T_kernel);
   if (e != cudaSuccess) return e;
@@ -1011,12 +1007,6 @@ cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m
   if (segments < 1) return cudaSuccess;
   if (m < 0 || m >= 256) return cudaErrorInvalidValue;
   ad2_poly_forcing_kernel<<<segments, 256, 0, st>>>(kk, m, dt, omega, Q, b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ad2_df_flush(cudaStream_t st, size_t count, double* G, const float2* D) {
-  const unsigned blocks = (unsigned)std::min<size_t>((count + 255) / 256, 4096);
-  ad2_df_flush_kernel<<<blocks, 256, 0, st>>>(count, G, D);
   return cudaGetLastError();
 }
 
@@ -1063,8 +1053,8 @@ cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t coun
   return cudaGetLastError();
 }
 
-cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
-                                const double* extra, double* grad, int* status) {
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G,
+                                const float2* extra, double* grad, int* status) {
   int threads = 256;
   int blocks = (int)((N + threads - 1) / threads);
   ad2_sum_grad_kernel<<<blocks, threads, 0, st>>>(N, lanes, G, extra, grad, status);

@@ -33,9 +33,10 @@ bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int dep
 // single-lane kernels): launched with programmatic dependent launch, so the coefficient
 // tile and the table are read while the previous kernel in the stream finishes; allowed
 // only when that kernel wrote neither of them (e.g. the previous step). The transposed step
-// of one lane (lanes == map_lanes == 1) with Gdf != NULL runs the register-layout kernel and
-// adds its forcing-gradient terms to the double-float accumulator Gdf ([ny][nx] (hi, lo)
-// FP32 pairs; launch_ad2_df_flush moves it into an FP64 gradient); otherwise to G (FP64).
+// of one lane (lanes == map_lanes == 1) runs the register-layout kernel. The forcing-gradient
+// accumulators G are double-float: [lanes][ny][nx] (hi, lo) FP32 pairs, summed in FP32
+// arithmetic (two-sum; GB300's FP64 pipe issues one warp instruction per 64 cycles) and
+// read out in FP64 by launch_ad2_sum_grad.
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
@@ -44,8 +45,8 @@ cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUten
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
-                            int with_source, const float* traj, double src_scale, double* G,
-                            const float* sc, int* status, int pdl, float2* Gdf);
+                            int with_source, const float* traj, double src_scale, float2* G,
+                            const float* sc, int* status, int pdl);
 cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const double* u,
                                  const double* v, const double* f, const double* ft, float* coef);
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
@@ -73,13 +74,13 @@ cudaError_t launch_ad2_pack_coefT(cudaStream_t st, const Ad2Params& p, const dou
 // One reverse step of the adjoint lanes as a register wavefront (kernels_ad2_roll.cu; needs
 // ad2_roll_ok): qmap over the lane states (depth 2*lanes, box {64, AD2_ROLL_BR, 1}), tmap
 // over tc (box {64, AD2_ROLL_BR, 4}), smap over the FP32 trajectory [K+1][ny][nx] and gmap
-// over the FP64 lane gradients G [lanes][ny][nx] (both ad2_make_map_plain, box
+// over the double-float lane gradients G [lanes][ny][nx] (8-byte elements; both ad2_make_map_plain, box
 // {64, AD2_ROLL_BR}). Steps lanes lane0 .. lane0 + count - 1 of `lanes`; lane l is at step
 // zsrc0 + l z_stride: its source row and its forcing factors sc[3 step + {0, 1, 2}]; the
 // source is added when add_src is set.
 cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& tmap,
                                  const CUtensorMap& smap, const CUtensorMap& gmap, const Ad2Params& p,
-                                 float* states, double* G, int lanes, int lane0, int count, int buf_in,
+                                 float* states, float2* G, int lanes, int lane0, int count, int buf_in,
                                  const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
                                  int* status);
 // The chain's polynomial propagator (PXA_PROP_POLY): one launch forms the powers
@@ -92,15 +93,14 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
 cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
                             float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
                             int want_h, float2* G, int* status, int pdl);
-// G[i] += hi + lo of the double-float accumulator D (count points, FP64 G).
-cudaError_t launch_ad2_df_flush(cudaStream_t st, size_t count, double* G, const float2* D);
 // The forcing-gradient coefficients b[s][0..m] of `segments` chain segments of kk steps
 // from the omega-free families Q = [3][kk][m+1] (m < 256).
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
                                     const double* Q, double* b);
 // dst = a + b (b may be NULL) over count floats.
 cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b);
-cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const double* G,
-                                const double* extra, double* grad, int* status);
+// grad (FP64) = sum over lanes of the double-float accumulators G[l] (+ extra, may be NULL).
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G,
+                                const float2* extra, double* grad, int* status);
 
 }  // namespace pxa

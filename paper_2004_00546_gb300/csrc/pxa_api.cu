@@ -503,9 +503,8 @@ struct pxa_ctx {
   float* stC = nullptr;     // homogeneous chain ping-pong [2][1][Hp][Wp]
   float* traj2 = nullptr;   // [(K+1)][ny*nx] FP32 direct trajectory
   double* Jpart = nullptr;  // [K][tiles]
-  double* G2buf = nullptr;  // [P][ny*nx] FP64 lane gradients
-  double* GC = nullptr;     // [ny*nx] FP64 chain gradient
-  float2* Gdf = nullptr;    // [ny*nx] double-float gradient of the single-lane kernels (serial adjoint, chain)
+  float2* G2buf = nullptr;  // [P][ny*nx] lane gradients, double-float (hi, lo) FP32 pairs
+  float2* GC = nullptr;     // [ny*nx] chain gradient, double-float
   CUtensorMap mapD, mapA, mapC, mapCoef;
   // adjoint lanes as a register wavefront (P > 1, grids the wavefront covers)
   bool roll2 = false;
@@ -597,7 +596,8 @@ void release_workspace(pxa_ctx* c) {
   }
   c->scL = nullptr;
   c->scL_count = 0;
-  c->Jpart = c->G2buf = c->GC = nullptr;
+  c->Jpart = nullptr;
+  c->G2buf = c->GC = nullptr;
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = c->rq = nullptr;
   c->Jrow = nullptr;
   for (auto& row : c->plans)
@@ -736,7 +736,6 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y))) return rc;
     if ((rc = alloc(c, &c->G2buf, (size_t)P * N))) return rc;
     if ((rc = alloc(c, &c->GC, N))) return rc;
-    if ((rc = alloc(c, &c->Gdf, N))) return rc;
     PXA_CUDA(c, cudaMemset(c->coef2, 0, sizeof(float) * 3 * plane), "memset coef");
     PXA_CUDA(c, cudaMemset(c->stD, 0, sizeof(float) * 2 * plane), "memset");
     PXA_CUDA(c, cudaMemset(c->stA, 0, sizeof(float) * 2 * (size_t)P * plane), "memset");
@@ -1678,9 +1677,8 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   }
   if (!do_a) return PXA_OK;
   ev_record(c, 2);
-  PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(double) * (size_t)P * N, st), "zero G");
-  PXA_CUDA(c, cudaMemsetAsync(c->GC, 0, sizeof(double) * N, st), "zero GC");
-  PXA_CUDA(c, cudaMemsetAsync(c->Gdf, 0, sizeof(float2) * N, st), "zero Gdf");
+  PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(float2) * (size_t)P * N, st), "zero G");
+  PXA_CUDA(c, cudaMemsetAsync(c->GC, 0, sizeof(float2) * N, st), "zero GC");
   // Eq. hybadjinhom: lane l starts from the objective's source at its top row (l+1) k
   PXA_CUDA(c, launch_ad2_fill(st, a, c->stA, P, c->traj2, k, k, src), "lane init");
   const int lpc = P >= 16 ? 16 : P;
@@ -1698,7 +1696,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                "2d adjoint lanes");
     else
       PXA_CUDA(c, launch_ad2_rk4T(st, c->mapA, c->mapCoef, a, c->stA, P, P, lpc, (int)(j & 1), k, 0, s_local, 1,
-                                  c->traj2, src, c->G2buf, c->sc2, c->status, P == 1 && j > 0, c->Gdf),
+                                  c->traj2, src, c->G2buf, c->sc2, c->status, P == 1 && j > 0),
                "2d adjoint lanes");
   }
   ev_record(c, 3);
@@ -1722,7 +1720,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       const double* cb = c->polyB + (size_t)sg * (m + 1);
       for (int i0 = 0, buf = 0; i0 < m; i0 += 4, buf ^= 1)
         PXA_CUDA(c, launch_ad2_poly(st, c->mapC, c->mapCoef, a, tau, c->stC, buf, i0, c->polyA, cb, c->hC,
-                                    sg > 0 ? 1 : 0, c->Gdf, c->status, i0 > 0),
+                                    sg > 0 ? 1 : 0, c->GC, c->status, i0 > 0),
                  "2d chain series");
     }
   } else if (P > 1) {
@@ -1737,14 +1735,12 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       for (int64_t j = 0; j < k; ++j) {
         PXA_CUDA(c, launch_ad2_rk4T(st, c->mapC, c->mapCoef, a, c->stC, 1, 1, 1, bufc, 0,
                                     (int64_t)lane * k, k - 1 - j, 0, nullptr, 0.0, c->GC, c->sc2, c->status,
-                                    j > 0, c->Gdf),
+                                    j > 0),
                  "2d chain step");
         bufc ^= 1;
       }
     }
   }
-  // the single-lane kernels' double-float gradient: the serial lane's, or the chain's
-  PXA_CUDA(c, launch_ad2_df_flush(st, N, P > 1 ? c->GC : c->G2buf, c->Gdf), "flush gradient");
   ev_record(c, 4);
   PXA_CUDA(c, launch_ad2_sum_grad(st, N, P, c->G2buf, P > 1 ? c->GC : nullptr, grad, c->status), "sum grad");
   ev_record(c, 5);
