@@ -109,11 +109,11 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="grid size override for the 2D workloads")
     ap.add_argument("--once", action="store_true",
                     help="profiling run: W warm-up gradients then one more of the headline "
-                         "configuration (1D, batched and 2D advection-diffusion workloads), default "
-                         "cluster sizes, no autotuning")
+                         "configuration (1D, batched and 2D workloads), default cluster sizes, no "
+                         "autotuning")
     ap.add_argument("--K", type=int, default=0,
-                    help="with --once on the 1D workloads: this many time steps at the workload's dt (a "
-                         "shorter window for profiling captures)")
+                    help="with --once on the 1D and 2D Burgers workloads: this many time steps at the "
+                         "workload's dt (a shorter window for profiling captures)")
     ap.add_argument("--no-compare", dest="no_compare", action="store_true",
                     help="skip the Paraexp-against-serial comparison of the other workloads")
     ap.add_argument("--checkpoints", type=int, default=0,
@@ -958,6 +958,28 @@ def run_once_2d(args, w):
             "phases_ms": {k: st[k] for k in ("ms_direct_inhom", "ms_adjoint_inhom", "ms_adjoint_hom", "ms_total")}}
 
 
+def run_once_bu2(args, w):
+    """2D Burgers for ncu: W warm-up gradients and one more (K from --K to shorten the
+    window), no graph, so every kernel is its own launch."""
+    import torch
+
+    from paper_2004_00546_gb300 import build, pxa as X
+
+    build.build()
+    X.load()
+    ctx, keep = bu2_setup(X, torch, w)
+    ctx.set_timing(True)
+    grad = torch.empty(2 * w["n"] * w["n"], dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.gradient(X.PARAEXP, grad)
+    J = ctx.gradient(X.PARAEXP, grad)
+    st = ctx.stats()
+    ctx.close()
+    del keep
+    return {"once": w["label"], "K": w["K"], "J": J, "warmup": args.warmup,
+            "phases_ms": {k: st[k] for k in ("ms_direct_inhom", "ms_adjoint_hom", "ms_total")}}
+
+
 def run_reference_batch(args, w, world):
     """The reference arm of the batched workload: the serial FP64 oracle of a bounded
     sample of the problems per step, scaled to the whole batch."""
@@ -1489,6 +1511,10 @@ def main():
         line = run_once(args, w)
     elif args.once and w["kind"] == "advdiff2d":
         line = run_once_2d(args, w)
+    elif args.once and w["kind"] == "burgers2d":
+        if args.K:
+            w = dict(w, K=args.K, T=w["T"] * args.K / w["K"], P=min(w["P"], args.K))
+        line = run_once_bu2(args, w)
     elif args.once and w["kind"] == "batched1d":
         line = run_batch_once(args, w)
     elif w["kind"] == "lanes2d":
