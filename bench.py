@@ -276,6 +276,56 @@ def time_pair(X, torch, make, steps, warmup, flush):
     return out
 
 
+def mode_phase_means(X, torch, make, flush, steps=3):
+    """Phase times (ms, CUDA events on the streams each phase runs on) of each mode,
+    averaged over a few graph replays after the timed pair."""
+    out = {}
+    for name, mode in (("paraexp", X.PARAEXP), ("serial", X.SERIAL)):
+        ctx = make(mode)
+        _, phs, _ = time_mode(X, torch, ctx, mode, steps, 1, flush, timing=True)
+        out[name] = {k: float(np.mean([p[k] for p in phs])) for k in
+                     ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_prep", "ms_adjoint_inhom", "ms_adjoint_hom",
+                      "ms_total")}
+        ctx.close()
+    return out
+
+
+def speedup_model(scheme, ph, T, P, T_H=None):
+    """The paper's speedup formulas with the rates measured on this GPU (time per unit of
+    simulated time, from the phase times of each mode).
+
+    linear (Alg. 1, Eq. LinSpeedup): s^-1 = 1/P + (P-1)/P (tau_H + tau_H')/(tau_I + tau_I'),
+    tau_I, tau_I' from serial stepping (its direct and adjoint sweeps over [0, T]), tau_H,
+    tau_H' from the Paraexp chains (spanning T (P-1)/P). The formula assumes P lanes each
+    as fast as one serial sweep; `lanes_efficiency` is that ideal (T/P)(tau_I + tau_I')
+    over the measured lane time.
+    hybrid (Sec. 3.3, Eq. hybridSpeedup): s^-1 = (T tau_I + (T/P) tau_I' + T_H tau_H') /
+    (T (tau_I + tau_I')), with the serial direct's tau_I, the serial adjoint's tau_I' and
+    the Paraexp chain's tau_H' over its span T_H; its limit for many subintervals is
+    (tau_I + tau_I')/(tau_I + tau_H')."""
+    par, ser = ph["paraexp"], ph["serial"]
+    out = {"scheme": scheme, "measured": ser["ms_total"] / par["ms_total"] if par["ms_total"] > 0 else None}
+    if scheme == "linear":
+        tI, tIa = ser["ms_direct_inhom"] / T, ser["ms_adjoint_inhom"] / T
+        span = T * (P - 1) / P
+        tH, tHa = par["ms_direct_hom"] / span, par["ms_adjoint_hom"] / span
+        inv = 1.0 / P + (P - 1) / P * (tH + tHa) / (tI + tIa)
+        lanes = par["ms_direct_inhom"] + par["ms_adjoint_inhom"]
+        out.update({"tau_I": tI, "tau_I_adj": tIa, "tau_H": tH, "tau_H_adj": tHa, "predicted": 1.0 / inv,
+                    "limit": (tI + tIa) / (tH + tHa) if tH + tHa > 0 else None,
+                    "lanes_efficiency": (T / P) * (tI + tIa) / lanes if lanes > 0 else None})
+    else:
+        tI = ser["ms_direct_inhom"] / T
+        tIa = (ser["ms_total"] - ser["ms_direct_inhom"]) / T
+        T_H = T if T_H is None else T_H
+        tHa = par["ms_adjoint_hom"] / T_H
+        inv = (T * tI + (T / P) * tIa + T_H * tHa) / (T * (tI + tIa))
+        out.update({"tau_I": tI, "tau_I_adj": tIa, "tau_H_adj": tHa, "T_H": T_H, "predicted": 1.0 / inv,
+                    "limit": (tI + tIa) / (tI + tHa)})
+    out["units"] = "tau: ms of GPU time per unit of simulated time"
+    return out
+
+
 def pair_entry(label, res, g_ref, tol, note):
     """One workload of the Paraexp-against-serial comparison."""
     pe, se = rel_err(res["paraexp"][1], g_ref), rel_err(res["serial"][1], g_ref)
@@ -304,6 +354,8 @@ def compare_advdiff1d(args, X, torch, flush):
     e = pair_entry(w["label"].replace(" (Krylov m autotuned)", ""), res, g_ref, GATE,
                    "homogeneous parts: the stepper's subinterval propagator M^(K/P) as one circulant band "
                    "per link (exact for this periodic constant-coefficient operator)")
+    e["phases_ms"] = mode_phase_means(X, torch, make, flush)
+    e["speedup_model"] = speedup_model("linear", e["phases_ms"], w["T"], w["P"])
     # the benchmark spec's Krylov propagator, autotuned (m, substeps), timed the same way
     ctx = make(X.PARAEXP, X.PROP_KRYLOV)
     ctx.autotune(X.PARAEXP, torch.empty(w["n"], dtype=torch.float64, device="cuda"))
@@ -453,6 +505,15 @@ def compare_advdiff2d(args, X, torch, flush):
     d = {k: rel_err(res[k][1], res["serial"][1]) for k in ("paraexp_stepper", "paraexp_poly")}
     ok = [k for k in d if d[k] <= 1e-4]
     head = min(ok, key=lambda k: res[k][0]) if ok else "paraexp_stepper"
+
+    def make(mode):
+        c2, kp = ctx_2d(X, torch, w, w["n"], w["P"], w["K"])
+        if mode == X.PARAEXP and head == "paraexp_poly":
+            c2.set_propagator(X.PROP_POLY, 200)
+        c2._keep = kp
+        return c2
+
+    phases = mode_phase_means(X, torch, make, flush)
     return {"workload": w["label"], "paraexp_ms": res[head][0], "serial_ms": res["serial"][0],
             "speedup": res["serial"][0] / res[head][0], "homogeneous": head, "rel_err_paraexp": None,
             "rel_err_serial": None, "rel_diff_paraexp_vs_serial": d[head], "tolerance": 1e-4,
@@ -462,6 +523,9 @@ def compare_advdiff2d(args, X, torch, flush):
             "paraexp_poly_chain": dict(info["paraexp_poly"], ms=res["paraexp_poly"][0],
                                        rel_diff_vs_serial=d["paraexp_poly"],
                                        speedup=res["serial"][0] / res["paraexp_poly"][0]),
+            "phases_ms": phases,
+            # the chain spans the P-1 lower subintervals (the top one is a lane)
+            "speedup_model": speedup_model("hybrid", phases, w["T"], w["P"], T_H=w["T"] * (w["P"] - 1) / w["P"]),
             "note": "FP32 stepping, FP64 accumulation; the FP64 oracle at full size is not run here"}
 
 
@@ -755,6 +819,8 @@ def run_ours(args, w, rank, world):
                 "carried by the stepper's own transposed step maps, so its chain sweeps all K steps like the "
                 "serial adjoint")
             comparison["C2"]["phases_ms"] = mode_phases
+            # the banded chain covers the top subinterval too (with its source): T_H = T
+            comparison["C2"]["speedup_model"] = speedup_model("hybrid", mode_phases, w["T"], w["P"], T_H=w["T"])
             comparison["C2"]["serial_one_step_ms"] = one_step[0]
             comparison["C2"]["rel_err_serial_one_step"] = rel_err(one_step[1], g_ref)
             comparison["C2"]["speedup_vs_one_step"] = one_step[0] / res["paraexp"][0]
