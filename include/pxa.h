@@ -12,9 +12,10 @@
  * (Eq. hom, Eq. adjHomNormal) are carried, by linearity, as their sum over the
  * problems active on one subinterval, by one of the propagators pxa_set_propagator
  * selects: Krylov matrix-exponential actions (Sec. 4.1, Saad 1992; the default), the
- * real Leja points method (Sec. 4.1), or, for periodic constant-coefficient 1D
- * operators, the subinterval propagator itself as a circulant band (the fastest and the
- * one the benchmarks use); the time-varying Burgers adjoint uses the stepper's own
+ * real Leja points method (Sec. 4.1), for periodic constant-coefficient 1D operators the
+ * subinterval propagator itself as a circulant band (the fastest and the one the 1D
+ * benchmarks use), and for the 2D operator the RK4 stepper's subinterval propagator as
+ * its power series (operator applications only); the time-varying Burgers adjoint uses the stepper's own
  * transposed step maps (or 4th-order Magnus steps with Krylov exponentials). The full
  * solution is the superposition of Eq. fullsol0 / Eq. fulladjsol, and the gradient
  * follows from Eq. initupdate (initial-condition control) or Eq. paramupdate (forcing
@@ -30,9 +31,11 @@
  *                   velocity (u, v); q(0) = 0; control = f; the target is the
  *                   trajectory driven by f_true (pxa_set_target), J = (1/T) sum_{j=1..K}
  *                   dt ||q_j(f) - q_j(f_true)||^2 (Eq. cost). RK4 stepping in FP32 on
- *                   TMA-staged halo tiles; J and the gradient accumulate in FP64.
- *                   Serial direct + Paraexp adjoint (hybrid scheme, Sec. 3.3) with the
- *                   stepper's own propagator for the homogeneous parts.
+ *                   TMA-staged halo tiles; J sums FP32 tile partials in FP64, the
+ *                   gradient accumulates as double-float (hi, lo) FP32 pairs and is
+ *                   returned in FP64. Serial direct + Paraexp adjoint (hybrid scheme,
+ *                   Sec. 3.3) with the stepper's own propagator for the homogeneous
+ *                   parts: its exact steps, or its power series (PXA_PROP_POLY).
  *   PXA_BURGERS_1D: du/dt = -u du/dx + nu d2u/dx2 + s(t) f(x), u(0) = 0, central
  *                   differences, periodic; classical RK4; control = f;
  *                   s(t) = sin(omega t) (omega != 0) or 1; objective
