@@ -1377,6 +1377,34 @@ def run_2d(args, w, rank, world):
     total_ms = float(sum(times))
     ph = {k: float(np.mean([p[k] for p in phases])) for k in
           ("ms_direct_inhom", "ms_direct_hom", "ms_adjoint_inhom", "ms_adjoint_hom", "ms_side_lanes")}
+    # end to end through the host-buffer entry point: H2D of the forcing, D2H of the gradient
+    u0, v0, f0, ft0 = inputs_2d(n)
+    fh = np.ascontiguousarray(f0.reshape(-1))
+    gh = np.empty(n * n)
+    ctx.gradient_host(X.PARAEXP, fh, gh)
+    te = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.gradient_host(X.PARAEXP, fh, gh)
+        te.append(time.perf_counter() - t0)
+    e2e = {"value": world / float(np.mean(te)), "unit": "gradient evals/s", "h2d_bytes_per_step": 8 * n * n,
+           "d2h_bytes_per_step": 8 * n * n + 8}
+    # roofline of the dominant kernel, the serial direct's tile step (one launch per step):
+    # algorithmic bytes per point and step = the state read and written and the stored
+    # trajectory row (12 B); the state (1 MB at 512^2) is L2-resident, so this is latency-
+    # bound work reported against HBM for reference
+    K = w["K"]
+    bytes_launch = 12.0 * n * n
+    ms_launch = ph["ms_direct_inhom"] / K
+    ach = bytes_launch / (ms_launch * 1e-3) / 1e9 if ms_launch > 0 else None
+    peak = measured_hbm_peak()
+    roof = {"bound": "hbm", "kernel": "ad2_rk4_kernel (serial direct, one RK4 step per launch)",
+            "unit": "GB/s", "achieved": ach, "peak": peak, "frac": (ach / peak) if ach else None,
+            "traffic": None, "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+            "peak_kind": "measured copy bandwidth",
+            "note": "L2-resident state: latency-bound (one 8-warp block per SM, 160 tiles); see the profiles"}
     cpu = {}
     if rank == 0:
         import oracle as O
@@ -1394,7 +1422,8 @@ def run_2d(args, w, rank, world):
             "vs_baseline": None, "dtype": "f32 stepping, f64 accumulation", "data": "synthetic",
             "config": {"workload": w["label"].replace("512x512", f"{n}x{n}"), "homogeneous": head,
                        "l2": "flushed between steps"},
-            "variants": variants, "phases_ms": ph, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "variants": variants, "phases_ms": ph, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk.summary(),
             "gpu_launches": (ctx.stats()["graph_kernels"] * args.steps) or None}
 
 
