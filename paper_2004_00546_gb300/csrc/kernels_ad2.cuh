@@ -8,11 +8,14 @@
 namespace pxa {
 
 constexpr int G2 = 4;                // ghost layers of the padded 2D arrays
-constexpr int TX2 = 56, TY2 = 34;    // tile interior (TX2 % 4 == 0 for 16-byte TMA x offsets)
+// tile interior (TX2 % 4 == 0 for 16-byte TMA x offsets). 18 rows: a 512 x 512 grid has
+// 290 tiles, about two 8-warp blocks per SM, six rows per thread; measured on the C3
+// gradient against 34, 26, 22, 14 and 10 rows (and 3 blocks per SM): the fastest
+constexpr int TX2 = 56, TY2 = 18;
 constexpr int BX2 = TX2 + 2 * G2;    // 64 floats = 256 bytes (a multiple of 16 for TMA)
-constexpr int BY2 = TY2 + 2 * G2;    // 42 rows
-constexpr int TILE2 = BX2 * BY2;     // 2688 floats = 10752 bytes (a multiple of 128)
-constexpr int RG2 = (BY2 - 2) / 4;   // rows of the halo-3 region owned by one thread (10)
+constexpr int BY2 = TY2 + 2 * G2;    // 26 rows
+constexpr int TILE2 = BX2 * BY2;     // 1664 floats = 6656 bytes (a multiple of 128)
+constexpr int RG2 = (BY2 - 2) / 4;   // rows of the halo-3 region owned by one thread (6)
 static_assert((BY2 - 2) % 4 == 0, "the halo-3 rows split evenly over the 4 row groups");
 static_assert(BX2 - 2 <= 64, "one thread per halo-3 column");
 
