@@ -631,6 +631,8 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
 // coefficients.
 __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant__ CUtensorMap vmap,
                                                           const __grid_constant__ CUtensorMap cmap,
+                                                          const __grid_constant__ CUtensorMap hmap,
+                                                          const __grid_constant__ CUtensorMap wmap, int w_z,
                                                           Ad2Params p, float tau, float* __restrict__ V,
                                                           int buf_in, int i0, const float* __restrict__ ca,
                                                           const double* __restrict__ cb,
@@ -683,16 +685,23 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     ts[i] = dt * (-v[c - BX2] * p.inv2h + d);
     tn[i] = dt * (v[c + BX2] * p.inv2h + d);
   }
-  // after the wait: the power tile, and this thread's interior H and G values (loaded now,
-  // so that their latency passes during the first three powers)
+  // after the wait: the power tile (for a segment's first launch v_0 = h + w: the carried
+  // value's tile and the lane value's, added below), and this thread's interior H and G
+  // values (loaded now, so that their latency passes during the first three powers)
   grid_dep_wait();
+  const bool first = i0 == 0;
+  const bool with_w = first && w_z >= 0;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&t.bar[1], TILE2 * sizeof(float));
-    tma_load_3d(t.q[0], &vmap, x0, y0, buf_in, &t.bar[1]);
+    mbar_expect_tx(&t.bar[1], (with_w ? 2 : 1) * TILE2 * sizeof(float));
+    if (first) {
+      tma_load_3d(t.q[0], &hmap, x0, y0, 0, &t.bar[1]);
+      if (with_w) tma_load_3d(t.q[1], &wmap, x0, y0, w_z, &t.bar[1]);
+    } else {
+      tma_load_3d(t.q[0], &vmap, x0, y0, buf_in, &t.bar[1]);
+    }
   }
   const bool cin = col >= G2 && col < G2 + TX2;
   const int x = x0 + col - G2;  // domain column
-  const bool first = i0 == 0;
   float hold[RG2];
   float2 gold[RG2];
 #pragma unroll
@@ -706,6 +715,10 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
     (void)mbar_wait(&t.bar[1], 0);
     return;
+  }
+  if (with_w) {
+    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) t.q[0][e] += t.q[1][e];
+    __syncthreads();
   }
   const float* Xp = t.q[0];
   float xv[RG2], hacc[RG2], gacc[RG2];
@@ -860,10 +873,10 @@ __global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t coun
   }
 }
 
-// grad = sum over lanes of G[l] (+ extra), FP64 from the double-float accumulators.
-__global__ void ad2_sum_grad_kernel(size_t N, int lanes, const float2* __restrict__ G,
-                                    const float2* __restrict__ extra, double* __restrict__ grad,
-                                    int* status) {
+// grad = sum over lanes of G[l] (double-float) and Gf[l] (FP32) (+ extra), in FP64.
+__global__ void ad2_sum_grad_kernel(size_t N, int lanes, const float2* __restrict__ G, int flanes,
+                                    const float* __restrict__ Gf, const float2* __restrict__ extra,
+                                    double* __restrict__ grad, int* status) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
     if (extra) acc = (double)extra[i].x + (double)extra[i].y;
@@ -871,6 +884,7 @@ __global__ void ad2_sum_grad_kernel(size_t N, int lanes, const float2* __restric
       const float2 v = G[(size_t)l * N + i];
       acc += (double)v.x + (double)v.y;
     }
+    for (int l = 0; l < flanes; ++l) acc += (double)Gf[(size_t)l * N + i];
     grad[i] = acc;
     if (!isfinite(acc)) set_status(status, PXA_ERR_NONFINITE);
   }
@@ -993,13 +1007,14 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
   return cudaGetLastError();
 }
 
-cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
-                            float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
-                            int want_h, float2* G, int* status, int pdl) {
+cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const CUtensorMap& hmap,
+                            const CUtensorMap& wmap, int w_z, const Ad2Params& p, float tau, float* V, int buf_in,
+                            int i0, const float* ca, const double* cb, float* H, int want_h, float2* G, int* status,
+                            int pdl) {
   cudaError_t e = set_smem((const void*)ad2_poly_kernel);
   if (e != cudaSuccess) return e;
   return launch_ex(ad2_poly_kernel, dim3(p.tiles_x * p.tiles_y), dim3(256), ad2_smem_bytes(), st, pdl != 0, vmap,
-                   cmap, p, tau, V, buf_in, i0, ca, cb, H, want_h, G, status);
+                   cmap, hmap, wmap, w_z, p, tau, V, buf_in, i0, ca, cb, H, want_h, G, status);
 }
 
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
@@ -1053,11 +1068,12 @@ cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t coun
   return cudaGetLastError();
 }
 
-cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G,
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G, int flanes, const float* Gf,
                                 const float2* extra, double* grad, int* status) {
   int threads = 256;
   int blocks = (int)((N + threads - 1) / threads);
-  ad2_sum_grad_kernel<<<blocks, threads, 0, st>>>(N, lanes, G, extra, grad, status);
+  if (blocks > 4096) blocks = 4096;
+  ad2_sum_grad_kernel<<<blocks, threads, 0, st>>>(N, lanes, G, flanes, Gf, extra, grad, status);
   return cudaGetLastError();
 }
 

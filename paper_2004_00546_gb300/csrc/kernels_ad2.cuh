@@ -77,13 +77,13 @@ cudaError_t launch_ad2_pack_coefT(cudaStream_t st, const Ad2Params& p, const dou
 // One reverse step of the adjoint lanes as a register wavefront (kernels_ad2_roll.cu; needs
 // ad2_roll_ok): qmap over the lane states (depth 2*lanes, box {64, AD2_ROLL_BR, 1}), tmap
 // over tc (box {64, AD2_ROLL_BR, 4}), smap over the FP32 trajectory [K+1][ny][nx] and gmap
-// over the double-float lane gradients G [lanes][ny][nx] (8-byte elements; both ad2_make_map_plain, box
+// over the FP32 lane gradients G [lanes][ny][nx] (both ad2_make_map_plain, box
 // {64, AD2_ROLL_BR}). Steps lanes lane0 .. lane0 + count - 1 of `lanes`; lane l is at step
 // zsrc0 + l z_stride: its source row and its forcing factors sc[3 step + {0, 1, 2}]; the
 // source is added when add_src is set.
 cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& tmap,
                                  const CUtensorMap& smap, const CUtensorMap& gmap, const Ad2Params& p,
-                                 float* states, float2* G, int lanes, int lane0, int count, int buf_in,
+                                 float* states, float* G, int lanes, int lane0, int count, int buf_in,
                                  const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
                                  int* status);
 // The chain's polynomial propagator (PXA_PROP_POLY): one launch forms the powers
@@ -91,19 +91,23 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
 // over V with depth 2), writes v_{i0+4} to the other plane, and adds the interior's terms
 // a_i v_i to H (padded plane; H = a_0 v_0 + ... when i0 == 0; skipped when want_h == 0) and
 // b_i v_i to G (a double-float accumulator, [ny][nx] (hi, lo) FP32 pairs). ca (FP32) and cb (FP64) hold the coefficients 0 .. i0 + 4.
+// For i0 == 0 the input is v_0 = H + W: the tile of H (hmap, a map over the padded H
+// plane) plus, when w_z >= 0, plane w_z of wmap (the lane value at the segment's top).
 // pdl != 0: programmatic dependent launch (the coefficient tile and ca, cb are read before
 // the wait for the previous kernel, which must not have written them).
-cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const Ad2Params& p,
-                            float tau, float* V, int buf_in, int i0, const float* ca, const double* cb, float* H,
-                            int want_h, float2* G, int* status, int pdl);
+cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const CUtensorMap& hmap,
+                            const CUtensorMap& wmap, int w_z, const Ad2Params& p, float tau, float* V, int buf_in,
+                            int i0, const float* ca, const double* cb, float* H, int want_h, float2* G, int* status,
+                            int pdl);
 // The forcing-gradient coefficients b[s][0..m] of `segments` chain segments of kk steps
 // from the omega-free families Q = [3][kk][m+1] (m < 256).
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
                                     const double* Q, double* b);
 // dst = a + b (b may be NULL) over count floats.
 cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b);
-// grad (FP64) = sum over lanes of the double-float accumulators G[l] (+ extra, may be NULL).
-cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G,
+// grad (FP64) = sum over `lanes` double-float accumulators G[l] and `flanes` FP32 ones Gf[l]
+// (+ extra, a double-float accumulator, may be NULL).
+cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G, int flanes, const float* Gf,
                                 const float2* extra, double* grad, int* status);
 
 }  // namespace pxa

@@ -113,16 +113,6 @@ __device__ __forceinline__ void put_point(float* dst, int Wp, int nx, int ny, in
   if (hx && hy) dst[(size_t)Ya * Wp + Xa] = val;
 }
 
-// acc (hi, lo) += g in FP32 arithmetic (Knuth's two-sum; the rounding error of hi + g is
-// carried in lo): the lane gradients accumulate without the FP64 pipe, which issues one
-// warp instruction per 64 cycles on GB300. Rounded adds, never fused.
-__device__ __forceinline__ float2 df_add(float2 acc, float g) {
-  const float s = __fadd_rn(acc.x, g);
-  const float bp = __fsub_rn(s, acc.x);
-  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bp)), __fsub_rn(g, bp));
-  return make_float2(s, __fadd_rn(acc.y, err));
-}
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -268,15 +258,16 @@ __device__ __forceinline__ void roll_task(const CUtensorMap* qmap, const CUtenso
 // kbar4 = dt/6 lambda; Y3 = A^T kbar4, kbar3 = dt/3 lambda + dt Y3; Y2 = A^T kbar3,
 // kbar2 = dt/3 lambda + dt/2 Y2; Y1 = A^T kbar2, kbar1 = dt/6 lambda + dt/2 Y1;
 // lambda_new = lambda + Y3 + Y2 + Y1 + A^T kbar1 (+ the objective's source); the forcing
-// gradient gains c4 kbar4 + c2 kbar3 + c2 kbar2 + c1 kbar1 (Eq. paramupdate), in a
-// double-float (hi, lo) FP32 accumulator per point.
+// gradient gains c4 kbar4 + c2 kbar3 + c2 kbar2 + c1 kbar1 (Eq. paramupdate), accumulated in
+// FP32 over the lane's steps (FP32 stepping with FP32 accumulation; the lanes are summed in
+// FP64 afterwards).
 // The same wavefront as the forward step: stage A on row i-1, B on i-2, C on i-3, D on
 // i-4, every A^T from the rows of the previous stage held in registers. A block of rows
 // brings, by four TMA copies on one mbarrier, the lambda rows, the four A^T coefficient
 // rows (tE, tW, tN, tS), and, eight rows behind (the rows that stage D finishes), the
 // source rows of the lane's step and its FP64 gradient rows.
 
-constexpr int TB_FLOATS = 8 * BR * 64;    // lambda, 4 coefficient planes, source, FP64 gradient
+constexpr int TB_FLOATS = 7 * BR * 64;    // lambda, 4 coefficient planes, source, FP32 gradient
 constexpr int TRING_FLOATS = NB * TB_FLOATS;
 constexpr int TWARPS = 4;
 
@@ -320,7 +311,7 @@ template <bool INNER>
 __device__ __forceinline__ void rollT_task(const CUtensorMap* qmap, const CUtensorMap* tmap,
                                            const CUtensorMap* smap, const CUtensorMap* gmap,
                                            const Ad2Params& p, const RollTTask& tk, float* qo,
-                                           float2* G, float* ring, uint64_t* bars, int Hs, float c1,
+                                           float* G, float* ring, uint64_t* bars, int Hs, float c1,
                                            float c2, float c4, float src_scale, bool add_src,
                                            int* status) {
   const int t = threadIdx.x & 31;
@@ -340,7 +331,7 @@ __device__ __forceinline__ void rollT_task(const CUtensorMap* qmap, const CUtens
   if (t == 0)
     for (int b = 0; b < NB - 1 && b < nblocks; ++b) issue_tblock(qmap, tmap, smap, gmap, tk, ring, bars, b, b);
   float* orow = qo + (size_t)(tk.Y0 + G2) * p.Wp + xd + G2;
-  float2* grow = G + ((size_t)tk.l * p.ny + tk.Y0) * p.nx + xd;
+  float* grow = G + ((size_t)tk.l * p.ny + tk.Y0) * p.nx + xd;
   bool ok = true;
   for (int i0 = 0; i0 < rows; i0 += 8) {
 #pragma unroll
@@ -363,8 +354,8 @@ __device__ __forceinline__ void rollT_task(const CUtensorMap* qmap, const CUtens
       const f2 tn = *reinterpret_cast<const f2*>(src + 3 * BR * 64);
       const f2 ts = *reinterpret_cast<const f2*>(src + 4 * BR * 64);
       const f2 sv = *reinterpret_cast<const f2*>(src + 5 * BR * 64);
-      const float4 gold = *reinterpret_cast<const float4*>(
-          reinterpret_cast<const float2*>(ring + slot_of_I[I] * TB_FLOATS + 6 * BR * 64) + (I % BR) * 64 + 2 * t);
+      const f2 gold = *reinterpret_cast<const f2*>(
+          ring + slot_of_I[I] * TB_FLOATS + 6 * BR * 64 + (I % BR) * 64 + 2 * t);
       // stage A on row i-1: Y3 = A^T (dt/6 lambda)
       {
         const f2 x = Q[(I + 3) & 3];
@@ -406,10 +397,7 @@ __device__ __forceinline__ void rollT_task(const CUtensorMap* qmap, const CUtens
             }
           }
           if (own_col && yd >= tk.own_y0) {
-            const f2 g = GG[I & 3];
-            const float2 g0 = df_add(make_float2(gold.x, gold.y), lo_of(g));
-            const float2 g1 = df_add(make_float2(gold.z, gold.w), hi_of(g));
-            *reinterpret_cast<float4*>(grow) = make_float4(g0.x, g0.y, g1.x, g1.y);
+            *reinterpret_cast<f2*>(grow) = add2(gold, GG[I & 3]);
           }
           orow += p.Wp;
           grow += p.nx;
@@ -489,7 +477,7 @@ __global__ void __launch_bounds__(32 * RWARPS, 2) ad2_rk4_roll_kernel(
 __global__ void __launch_bounds__(32 * TWARPS, 3) ad2_rk4T_roll_kernel(
     const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap tmap,
     const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap gmap, Ad2Params p,
-    float* __restrict__ states, float2* __restrict__ G, int lanes, int lane0, int count, int buf_in,
+    float* __restrict__ states, float* __restrict__ G, int lanes, int lane0, int count, int buf_in,
     int nstrips, int nsegs, int Hs, const float* __restrict__ sc, int zsrc0, int z_stride, float src_scale,
     int add_src, int* status) {
   extern __shared__ __align__(1024) float rsm[];
@@ -602,7 +590,7 @@ cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const 
 
 cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& tmap,
                                  const CUtensorMap& smap, const CUtensorMap& gmap, const Ad2Params& p,
-                                 float* states, float2* G, int lanes, int lane0, int count, int buf_in,
+                                 float* states, float* G, int lanes, int lane0, int count, int buf_in,
                                  const float* sc, int zsrc0, int z_stride, float src_scale, int add_src,
                                  int* status) {
   if (count <= 0 || lane0 < 0 || lane0 + count > lanes) return cudaErrorInvalidValue;

@@ -504,8 +504,10 @@ struct pxa_ctx {
   float* traj2 = nullptr;   // [(K+1)][ny*nx] FP32 direct trajectory
   double* Jpart = nullptr;  // [K][tiles]
   float2* G2buf = nullptr;  // [P][ny*nx] lane gradients, double-float (hi, lo) FP32 pairs
+  float* G2f = nullptr;     // [P][ny*nx] FP32 gradients of the wavefront lanes (K/P steps each)
   float2* GC = nullptr;     // [ny*nx] chain gradient, double-float
   CUtensorMap mapD, mapA, mapC, mapCoef;
+  CUtensorMap mapH;         // over hC (the series chain's carried value)
   // adjoint lanes as a register wavefront (P > 1, grids the wavefront covers)
   bool roll2 = false;
   float* tcoef2 = nullptr;  // [4][Hp][Wp] coefficients of A^T
@@ -598,6 +600,7 @@ void release_workspace(pxa_ctx* c) {
   c->scL_count = 0;
   c->Jpart = nullptr;
   c->G2buf = c->GC = nullptr;
+  c->G2f = nullptr;
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = c->rq = nullptr;
   c->Jrow = nullptr;
   for (auto& row : c->plans)
@@ -747,10 +750,11 @@ int prepare(pxa_ctx* c) {
     c->roll2 = P > 1 && ad2_roll_ok(a);
     if (c->roll2) {
       if ((rc = alloc(c, &c->tcoef2, 4 * plane))) return rc;
+      if ((rc = alloc(c, &c->G2f, (size_t)P * N))) return rc;
       if (!ad2_make_map_box(&c->mapA4, c->stA, a, 2 * P, 64, AD2_ROLL_BR, 1) ||
           !ad2_make_map_box(&c->mapT4, c->tcoef2, a, 4, 64, AD2_ROLL_BR, 4) ||
           !ad2_make_map_plain(&c->mapS4, c->traj2, 4, a.nx, a.ny, (int)c->K + 1, 64, AD2_ROLL_BR) ||
-          !ad2_make_map_plain(&c->mapG4, c->G2buf, 8, a.nx, a.ny, P, 64, AD2_ROLL_BR))
+          !ad2_make_map_plain(&c->mapG4, c->G2f, 4, a.nx, a.ny, P, 64, AD2_ROLL_BR))
         return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D adjoint lanes");
     }
     c->poly_m = 0;
@@ -808,6 +812,8 @@ int prepare(pxa_ctx* c) {
       if ((rc = alloc(c, &c->polyQ, Q.size()))) return rc;
       if ((rc = alloc(c, &c->polyB, (size_t)segments * (m + 1)))) return rc;
       if ((rc = alloc(c, &c->hC, plane))) return rc;
+      if (!ad2_make_map(&c->mapH, c->hC, a, 1, 1))
+        return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the series chain");
       PXA_CUDA(c, cudaMemcpy(c->polyA, ah.data(), sizeof(float) * ah.size(), cudaMemcpyHostToDevice), "copy");
       PXA_CUDA(c, cudaMemcpy(c->polyQ, Q.data(), sizeof(double) * Q.size(), cudaMemcpyHostToDevice), "copy");
       c->poly_m = m;
@@ -1678,6 +1684,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   if (!do_a) return PXA_OK;
   ev_record(c, 2);
   PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(float2) * (size_t)P * N, st), "zero G");
+  if (c->G2f) PXA_CUDA(c, cudaMemsetAsync(c->G2f, 0, sizeof(float) * (size_t)P * N, st), "zero Gf");
   PXA_CUDA(c, cudaMemsetAsync(c->GC, 0, sizeof(float2) * N, st), "zero GC");
   // Eq. hybadjinhom: lane l starts from the objective's source at its top row (l+1) k
   PXA_CUDA(c, launch_ad2_fill(st, a, c->stA, P, c->traj2, k, k, src), "lane init");
@@ -1690,7 +1697,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   for (int64_t j = 0; j < k; ++j) {
     const int64_t s_local = k - 1 - j;  // lane l at step l k + s_local
     if (roll)
-      PXA_CUDA(c, launch_ad2_rk4T_roll(st, c->mapA4, c->mapT4, c->mapS4, c->mapG4, a, c->stA, c->G2buf, P, 0, P,
+      PXA_CUDA(c, launch_ad2_rk4T_roll(st, c->mapA4, c->mapT4, c->mapS4, c->mapG4, a, c->stA, c->G2f, P, 0, P,
                                        (int)(j & 1), c->sc2, (int)s_local, (int)k, (float)src, s_local > 0 ? 1 : 0,
                                        c->status),
                "2d adjoint lanes");
@@ -1712,15 +1719,16 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     const float tau = (float)((double)kk * a.dtd);
     PXA_CUDA(c, launch_ad2_poly_forcing(st, segments, kk, m, a.dtd, a.omega, c->polyQ, c->polyB), "poly forcing");
     PXA_CUDA(c, cudaMemsetAsync(c->hC, 0, sizeof(float) * plane, st), "zero chain");
+    (void)Wbuf;
     for (int sg = segments - 1; sg >= 0; --sg) {
       const bool top = (sg + 1) % sub == 0;  // the segment ends at a subinterval's top
       const int lane_above = (sg + 1) / sub;  // its lane value when it does
-      PXA_CUDA(c, launch_ad2_sum2(st, plane, c->stC, c->hC, top ? Wbuf + (size_t)lane_above * plane : nullptr),
-               "chain add");
+      // the first launch reads h + w itself: plane (k & 1) P + lane_above of the lane states
+      const int w_z = top ? (int)((k & 1) * P + lane_above) : -1;
       const double* cb = c->polyB + (size_t)sg * (m + 1);
       for (int i0 = 0, buf = 0; i0 < m; i0 += 4, buf ^= 1)
-        PXA_CUDA(c, launch_ad2_poly(st, c->mapC, c->mapCoef, a, tau, c->stC, buf, i0, c->polyA, cb, c->hC,
-                                    sg > 0 ? 1 : 0, c->GC, c->status, i0 > 0),
+        PXA_CUDA(c, launch_ad2_poly(st, c->mapC, c->mapCoef, c->mapH, c->mapA, w_z, a, tau, c->stC, buf, i0,
+                                    c->polyA, cb, c->hC, sg > 0 ? 1 : 0, c->GC, c->status, i0 > 0),
                  "2d chain series");
     }
   } else if (P > 1) {
@@ -1742,7 +1750,9 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     }
   }
   ev_record(c, 4);
-  PXA_CUDA(c, launch_ad2_sum_grad(st, N, P, c->G2buf, P > 1 ? c->GC : nullptr, grad, c->status), "sum grad");
+  PXA_CUDA(c, launch_ad2_sum_grad(st, N, roll ? 0 : P, c->G2buf, roll ? P : 0, c->G2f, P > 1 ? c->GC : nullptr, grad,
+                                  c->status),
+           "sum grad");
   ev_record(c, 5);
   return PXA_OK;
 }
