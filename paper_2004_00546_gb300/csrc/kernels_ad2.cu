@@ -796,13 +796,6 @@ __global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, 
   if (i <= m) b[(size_t)s * (m + 1) + i] = acc;
 }
 
-// dst = a + b over `count` elements (b may be NULL: a copy).
-__global__ void ad2_sum2_kernel(size_t count, float* __restrict__ dst, const float* __restrict__ a,
-                                const float* __restrict__ b) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
-    dst[e] = b ? a[e] + b[e] : a[e];
-}
-
 // Pack u, v (FP64, [ny][nx]) and the forcing f - f_true into the padded FP32
 // coefficient array [3][Hp][Wp] with periodic ghosts.
 __global__ void ad2_pack_coef_kernel(Ad2Params p, const double* __restrict__ u,
@@ -1022,12 +1015,6 @@ cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m
   if (segments < 1) return cudaSuccess;
   if (m < 0 || m >= 256) return cudaErrorInvalidValue;
   ad2_poly_forcing_kernel<<<segments, 256, 0, st>>>(kk, m, dt, omega, Q, b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b) {
-  const unsigned blocks = (unsigned)std::min<size_t>((count + 255) / 256, 4096);
-  ad2_sum2_kernel<<<blocks, 256, 0, st>>>(count, dst, a, b);
   return cudaGetLastError();
 }
 

@@ -103,8 +103,6 @@ cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUte
 // from the omega-free families Q = [3][kk][m+1] (m < 256).
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
                                     const double* Q, double* b);
-// dst = a + b (b may be NULL) over count floats.
-cudaError_t launch_ad2_sum2(cudaStream_t st, size_t count, float* dst, const float* a, const float* b);
 // grad (FP64) = sum over `lanes` double-float accumulators G[l] and `flanes` FP32 ones Gf[l]
 // (+ extra, a double-float accumulator, may be NULL).
 cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G, int flanes, const float* Gf,
