@@ -61,7 +61,8 @@
  *                   pxa_set_target, 0 when none is set). Alg. 1 with Krylov
  *                   propagators: exp(tau A) (PXA_PHI_EXP) or the RK4 stepper's own
  *                   R(dt A)^(K/P), R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24
- *                   (PXA_PHI_STEPPER), evaluated on the Hessenberg matrix.
+ *                   (PXA_PHI_STEPPER), evaluated on the Hessenberg matrix; or that
+ *                   stepper propagator as its power series (PXA_PROP_POLY).
  *
  * Conventions:
  *   - Every call returns a pxa_status (0 = PXA_OK). No call aborts, traps or
@@ -113,8 +114,9 @@ typedef enum { PXA_PHI_EXP = 0, PXA_PHI_STEPPER = 1 } pxa_phi;
  * or the real Leja points method (Sec. 4.1: Newton interpolation of phi(z) = (e^z - 1)/z
  * at Leja points of the focal interval of the spectrum; exp(B) v = v + B phi(B) v; three
  * vectors of workspace instead of a Krylov basis; PXA_PHI_EXP only). PXA_PROP_POLY
- * (ADVDIFF_2D): the RK4 stepper's own propagator R(dt A^T)^kk as its power series in
- * tau A^T (tau = kk dt), operator applications only, like ReLPM (see pxa_set_propagator). */
+ * (ADVDIFF_2D, CSR): the RK4 stepper's own propagator R(dt B)^kk (B = A or A^T) as its
+ * power series in tau B (tau = kk dt), operator applications only, like ReLPM (see
+ * pxa_set_propagator). */
 typedef enum { PXA_PROP_KRYLOV = 0, PXA_PROP_RELPM = 1, PXA_PROP_BAND = 2, PXA_PROP_POLY = 3 } pxa_propagator;
 /* SERIAL: one lane over [0, T] (plain serial stepping, same kernels).
  * PARAEXP: P lanes + homogeneous propagation + superposition. */
@@ -274,16 +276,19 @@ int pxa_set_krylov(pxa_ctx* ctx, int m, double tol, int phi, int substeps);
  * power M^(K/P) (PXA_PHI_STEPPER), is applied once per link as a circulant band: A is
  * circulant (periodic grid, constant coefficients), so the propagator's taps are the
  * inverse DFT of its eigenvalues, built on the host (FP64, kept to 2^-50 of the largest
- * tap; max_degree is not used). With PXA_PROP_POLY (ADVDIFF_2D, Paraexp; other operators
- * return PXA_ERR_INVALID at the first solve) the summed homogeneous adjoint problems (Eq. adjHomNormal) are carried by the
- * stepper's own propagator over chain segments of kk RK4 steps, R(dt A^T)^kk = sum_i a_i
- * (tau A^T)^i with R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24 and tau = kk dt, and each segment's
- * forcing gradient (Eq. paramupdate over its steps) by a second series in the same powers;
- * both are cut after the smallest degree m (a multiple of 4) whose tail bound
- * sum_{i>m} a_i ||tau A^T||_inf^i is below max(tolerance of pxa_set_krylov, 1e-7); kk is
- * the largest divisor of K/P with kk ||dt A^T||_inf <= 4. m above max_degree returns
- * PXA_ERR_NOT_CONVERGED at the first solve. The series needs only operator applications:
- * m per segment against 4 kk for stepping. Invalidates the workspace. */
+ * tap; max_degree is not used). With PXA_PROP_POLY (ADVDIFF_2D and CSR, Paraexp; other
+ * operators return PXA_ERR_INVALID at the first solve) the summed homogeneous problems are
+ * carried by the RK4 stepper's own propagator over chain segments of kk steps,
+ * R(dt B)^kk = sum_i a_i (tau B)^i with R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, tau = kk dt
+ * and B = A^T (ADVDIFF_2D: the adjoint chain, Eq. adjHomNormal, whose forcing gradient over
+ * each segment, Eq. paramupdate, is a second series in the same powers) or B = A and A^T
+ * (CSR: the direct chain of Eq. hom and the adjoint chain). The series is cut after the
+ * smallest degree m (a multiple of 4) whose tail bound sum_{i>m} a_i ||tau B||_inf^i is
+ * below the tolerance of pxa_set_krylov (ADVDIFF_2D, FP32 stepping: at least 1e-7); kk is
+ * the largest divisor of K/P with kk ||dt B||_inf <= 4. m above max_degree returns
+ * PXA_ERR_NOT_CONVERGED at the first solve. The series needs only operator applications
+ * (m per segment against 4 kk for stepping) and no inner products. Invalidates the
+ * workspace. */
 int pxa_set_propagator(pxa_ctx* ctx, int method, int max_degree);
 /* Burgers: RK4 steps per Magnus step of the homogeneous adjoint (divides K/P). */
 int pxa_set_magnus(pxa_ctx* ctx, int steps_per_magnus);

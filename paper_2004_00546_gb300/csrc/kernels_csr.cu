@@ -124,6 +124,52 @@ __global__ void csr_chain_kernel(int n, const int64_t* __restrict__ rp, const in
   for (int p = threadIdx.x; p < n; p += blockDim.x) hout[p] = hvec[p];
 }
 
+// h = 0; for i < count: h += E[first + i stride]; then `sub` times h <- sum_{j<=m} a_j
+// (tau A)^j h (the RK4 stepper's propagator over a segment as its power series, cut after
+// degree m; the powers formed one after another). Vectors h, the power and its successor in
+// shared memory when they fit (3 n doubles), else in `work` (3 n doubles).
+__global__ void csr_series_chain_kernel(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                        const double* __restrict__ val, const double* __restrict__ E, int first,
+                                        int stride, int count, double* __restrict__ hout,
+                                        const double* __restrict__ a, int m, int sub, double tau,
+                                        double* __restrict__ work, int in_smem) {
+  extern __shared__ double sm[];
+  double* h = in_smem ? sm : work;
+  double* pw = h + n;
+  double* nx = pw + n;
+  const CsrRows A{n, rp, col, val};
+  for (int p = threadIdx.x; p < n; p += blockDim.x) h[p] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < count; ++i) {
+    const double* e = E + (size_t)(first + i * stride) * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      h[p] += e[p];
+      pw[p] = h[p];
+      h[p] *= a[0];
+    }
+    __syncthreads();
+    for (int s = 0; s < sub; ++s) {
+      if (s > 0) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          pw[p] = h[p];
+          h[p] *= a[0];
+        }
+        __syncthreads();
+      }
+      for (int j = 1; j <= m; ++j) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) nx[p] = tau * A.row(p, pw);
+        __syncthreads();
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+          pw[p] = nx[p];
+          h[p] = fma(a[j], nx[p], h[p]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) hout[p] = h[p];
+}
+
 // q(T) = q0 + elast + hsum (each may be NULL), lamT = q(T) - g (g may be NULL),
 // J = 0.5 ||lamT||^2.
 __global__ void csr_superpose_kernel(int n, const double* __restrict__ q0, const double* __restrict__ elast,
@@ -171,6 +217,21 @@ cudaError_t launch_csr_chain(cudaStream_t st, int n, const int64_t* rp, const in
   const int threads = n >= 512 ? 512 : 256;
   csr_chain_kernel<<<1, threads, sh, st>>>(n, rp, col, val, E, first, stride, count, hout, Vglob, m, phi_mode,
                                            hscale, steps_per_sub, nsub, tol, v_in_smem, status, errmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_series_chain(cudaStream_t st, int n, const int64_t* rp, const int32_t* col,
+                                    const double* val, const double* E, int first, int stride, int count,
+                                    double* hout, const double* a, int m, int sub, double tau, double* work) {
+  const size_t sh = sizeof(double) * 3 * (size_t)n;
+  const bool in_smem = sh <= 200 * 1024;
+  if (in_smem) {
+    cudaError_t e = cudaFuncSetAttribute(csr_series_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+  }
+  const int threads = n >= 512 ? 512 : 256;
+  csr_series_chain_kernel<<<1, threads, in_smem ? sh : 0, st>>>(n, rp, col, val, E, first, stride, count, hout, a,
+                                                                m, sub, tau, work, in_smem ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,12 @@ cudaError_t launch_csr_chain(cudaStream_t st, int n, const int64_t* rp, const in
                              const double* E, int first, int stride, int count, double* hout, double* Vglob,
                              int m, int phi_mode, double hscale, int64_t steps_per_sub, int nsub, double tol,
                              int v_in_smem, int* status, double* errmax);
+// One block: h = 0; for i < count: h += E[first + i stride]; h <- (sum_{j<=m} a_j (tau A)^j)^sub h
+// (PXA_PROP_POLY: the RK4 stepper's segment propagator as its power series); hout = h.
+// work: 3 n doubles, used when they do not fit in shared memory.
+cudaError_t launch_csr_series_chain(cudaStream_t st, int n, const int64_t* rp, const int32_t* col,
+                                    const double* val, const double* E, int first, int stride, int count,
+                                    double* hout, const double* a, int m, int sub, double tau, double* work);
 // q(T) = q0 + elast + hsum, lamT = q(T) - g, J = 0.5 ||lamT||^2 (each input may be NULL).
 cudaError_t launch_csr_superpose(cudaStream_t st, int n, const double* q0, const double* elast,
                                  const double* hsum, const double* g, double* lamT, double* Jdev, int* status);

@@ -341,6 +341,41 @@ void rk4_series_host(int kk, int m, double dt, std::vector<long double>& a_full,
   }
 }
 
+// The plan of a PXA_PROP_POLY chain for k = K/P steps per subinterval: rho = ||dt B||_inf
+// for the operator(s) B the chain applies. Segments of kk steps, kk the largest divisor of
+// k with kk rho <= 4 (the series' partial sums then stay within e^4 of the result's scale);
+// the degree m is the smallest multiple of 4 whose tail bound sum_{i>m} a_i (kk rho)^i is
+// <= tol (m <= 4 kk, where the series is the whole polynomial). a_full: the whole series
+// in powers of kk dt B.
+struct PolyPlan {
+  int sub = 1, kk = 1, m = 0;
+  double tail = 0.0;
+  std::vector<long double> a_full;
+};
+
+PolyPlan poly_plan(double rho, int64_t k, double dt, double tol) {
+  PolyPlan pl;
+  while (pl.sub < k && (k % pl.sub != 0 || (double)(k / pl.sub) * rho > 4.0)) ++pl.sub;
+  pl.kk = (int)(k / pl.sub);
+  const long double rs = (long double)pl.kk * rho;
+  std::vector<double> Q;
+  rk4_series_host(pl.kk, 0, dt, pl.a_full, Q);
+  pl.m = 4 * pl.kk;
+  for (int mm = 4; mm <= 4 * pl.kk; mm += 4) {
+    long double t = 0.0L, pr = 1.0L;
+    for (int i = 0; i <= 4 * pl.kk; ++i) {
+      if (i > mm) t += pl.a_full[(size_t)i] * pr;
+      pr *= rs;
+    }
+    if (t <= (long double)tol) {
+      pl.m = mm;
+      pl.tail = (double)t;
+      break;
+    }
+  }
+  return pl;
+}
+
 }  // namespace pxa
 
 struct pxa_ctx {
@@ -515,6 +550,7 @@ struct pxa_ctx {
   CUtensorMap mapA4, mapT4, mapS4, mapG4;
   // chain by the power series of the stepper's propagator (PXA_PROP_POLY)
   float* polyA = nullptr;    // [m+1] coefficients of R(z)^kk cut at degree m (m % 4 == 0)
+  double* polyAd = nullptr;  // the same in FP64 (CSR chains)
   double* polyQ = nullptr;   // [3][kk][m+1] omega-free forcing families
   double* polyB = nullptr;   // [segments][m+1] forcing-gradient coefficients of each segment
   float* hC = nullptr;       // [Hp][Wp] the chain's carried value
@@ -688,8 +724,8 @@ int prepare(pxa_ctx* c) {
   if (!c->have_op || !c->have_time) return fail(c, PXA_ERR_STATE, "set_operator and set_time first");
   PXA_CUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   release_workspace(c);
-  if (c->prop == PXA_PROP_POLY && c->op.kind != PXA_ADVDIFF_2D)
-    return fail(c, PXA_ERR_INVALID, "PXA_PROP_POLY is implemented for ADVDIFF_2D");
+  if (c->prop == PXA_PROP_POLY && c->op.kind != PXA_ADVDIFF_2D && c->op.kind != PXA_CSR)
+    return fail(c, PXA_ERR_INVALID, "PXA_PROP_POLY is implemented for ADVDIFF_2D and CSR");
   const int n = c->op.n, P = c->P;
   int rc;
   if ((rc = alloc(c, &c->Jdev, 1))) return rc;
@@ -774,33 +810,12 @@ int prepare(pxa_ctx* c) {
                            std::fabs(hv[nth] * ih + dd) + 4.0 * dd;
           rowmax = std::max(rowmax, r);
         }
-      const double rho = a.dtd * rowmax;
-      // segments of kk steps: the smallest divisor of K/P with kk rho <= 4 (the partial
-      // sums of the series stay within e^4 of the result's scale in FP32)
       const int64_t k = c->K / P;
-      int sub = 1;
-      while (sub < k && (k % sub != 0 || (double)(k / sub) * rho > 4.0)) ++sub;
-      const int kk = (int)(k / sub);
-      const long double rs = (long double)kk * rho;  // max-norm of tau A^T
-      const double tol = std::max(c->kry_tol, 1e-7);
-      std::vector<long double> afull;
+      PolyPlan pl = poly_plan(a.dtd * rowmax, k, a.dtd, std::max(c->kry_tol, 1e-7));
+      const int sub = pl.sub, kk = pl.kk, m = pl.m;
+      const double tail = pl.tail;
+      std::vector<long double>& afull = pl.a_full;
       std::vector<double> Q;
-      rk4_series_host(kk, 0, a.dtd, afull, Q);
-      // degree: the smallest multiple of 4 whose tail sum_{i>m} a_i rs^i is <= tol
-      int m = 4 * kk;
-      double tail = 0.0;
-      for (int mm = 4; mm <= 4 * kk; mm += 4) {
-        long double t = 0.0L, pr = 1.0L;
-        for (int i = 0; i <= 4 * kk; ++i) {
-          if (i > mm) t += afull[(size_t)i] * pr;
-          pr *= rs;
-        }
-        if (t <= (long double)tol) {
-          m = mm;
-          tail = (double)t;
-          break;
-        }
-      }
       if (m > c->relpm_mmax || m > 252)
         return fail(c, PXA_ERR_NOT_CONVERGED, "PXA_PROP_POLY: the series needs degree " + std::to_string(m) +
                                                   " for the tolerance, above the maximum degree");
@@ -916,6 +931,34 @@ int prepare(pxa_ctx* c) {
     PXA_CUDA(c, cudaMemcpy(c->colT, tcol.data(), sizeof(int32_t) * tcol.size(), cudaMemcpyHostToDevice), "copy A^T");
     PXA_CUDA(c, cudaMemcpy(c->valT, tval.data(), sizeof(double) * tval.size(), cudaMemcpyHostToDevice), "copy A^T");
     if (!csr_lanes_fit_smem(n) && (rc = alloc(c, &c->csr_work, (size_t)4 * n * P))) return rc;
+    c->poly_m = 0;
+    if (c->prop == PXA_PROP_POLY && P > 1) {
+      // the chains apply A (direct) and A^T (adjoint): rho = dt max(||A||_inf, ||A||_1)
+      std::vector<double> rowsum((size_t)n, 0.0), colsum((size_t)n, 0.0);
+      for (int i = 0; i < n; ++i)
+        for (int64_t e = hrp[i]; e < hrp[i + 1]; ++e) {
+          rowsum[(size_t)i] += std::fabs(hval[e]);
+          colsum[(size_t)hcol[e]] += std::fabs(hval[e]);
+        }
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) nrm = std::max(nrm, std::max(rowsum[(size_t)i], colsum[(size_t)i]));
+      const double dt = c->T / (double)c->K;
+      PolyPlan pl = poly_plan(dt * nrm, c->K / P, dt, c->kry_tol);
+      if (pl.m > c->relpm_mmax)
+        return fail(c, PXA_ERR_NOT_CONVERGED, "PXA_PROP_POLY: the series needs degree " + std::to_string(pl.m) +
+                                                  " for the tolerance, above the maximum degree");
+      std::vector<double> ad((size_t)pl.m + 1);
+      for (int i = 0; i <= pl.m; ++i) ad[(size_t)i] = (double)pl.a_full[(size_t)i];
+      if ((rc = alloc(c, &c->polyAd, ad.size()))) return rc;
+      PXA_CUDA(c, cudaMemcpy(c->polyAd, ad.data(), sizeof(double) * ad.size(), cudaMemcpyHostToDevice), "copy");
+      c->poly_m = pl.m;
+      c->poly_sub = pl.sub;
+      c->poly_kk = pl.kk;
+      c->poly_tail = pl.tail;
+    }
+    c->stats.prop_degree = c->poly_m;
+    c->stats.prop_substeps = c->poly_m ? c->poly_sub : 0;
+    c->stats.prop_tail = c->poly_m ? c->poly_tail : 0.0;
   } else {
     int64_t k = c->K / P;
     // the side streams, events and priorities of the banded adjoint
@@ -1805,7 +1848,11 @@ int enqueue_csr(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     PXA_CUDA(c, launch_csr_rk4_lanes(st, P, n, rp, col, val, c->src, dt, k, nullptr, c->E, c->csr_work), "lanes");
     ev_record(c, 1);
     // Eq. hom: the summed homogeneous problems, h <- Phi (h + e_j), j = 0 .. P-2
-    if (P > 1)
+    if (P > 1 && c->poly_m > 0)  // the stepper's propagator as its power series in kk dt A
+      PXA_CUDA(c, launch_csr_series_chain(st, n, rp, col, val, c->E, 0, 1, P - 1, c->hsum, c->polyAd, c->poly_m,
+                                          c->poly_sub, (double)c->poly_kk * dt, c->V),
+               "chain");
+    else if (P > 1)
       PXA_CUDA(c, launch_csr_chain(st, n, rp, col, val, c->E, 0, 1, P - 1, c->hsum, c->V, c->kry_m, phi_mode,
                                    hscale, steps_sub, nsub, c->kry_tol, c->v_in_smem, c->status, c->errmax),
                "chain");
@@ -1823,7 +1870,11 @@ int enqueue_csr(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                    c->csr_work), "adjoint lanes");
   ev_record(c, 3);
   // Eq. adjHomNormal: carried down from the top with Phi^T
-  if (P > 1)
+  if (P > 1 && c->poly_m > 0)
+    PXA_CUDA(c, launch_csr_series_chain(st, n, c->rpT, c->colT, c->valT, c->EA, P - 1, -1, P - 1, c->hsumA,
+                                        c->polyAd, c->poly_m, c->poly_sub, (double)c->poly_kk * dt, c->V),
+             "adjoint chain");
+  else if (P > 1)
     PXA_CUDA(c, launch_csr_chain(st, n, c->rpT, c->colT, c->valT, c->EA, P - 1, -1, P - 1, c->hsumA, c->V,
                                  c->kry_m, phi_mode, hscale, steps_sub, nsub, c->kry_tol, c->v_in_smem, c->status,
                                  c->errmax), "adjoint chain");

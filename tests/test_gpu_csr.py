@@ -94,6 +94,52 @@ def test_csr_gradient_matches_oracle(X, torch, case, target):
         ctx.close()
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("target", [False, True])
+def test_csr_series_chain_matches_serial_stepping(X, torch, case, target):
+    """PXA_PROP_POLY: both chains carry the summed homogeneous problems with the RK4 stepper's
+    segment propagator as its power series in kk dt A (A^T for the adjoint), cut where the
+    max-norm tail bound falls below 1e-12: Paraexp equals the oracle's serial stepping to
+    1e-10 point by point, with operator products only (no inner products)."""
+    (rp, col, val), T, K, P = CASES[case]()
+    n = rp.size - 1
+    q0 = I.grf_k2(max(n, 16), 33)[:n]
+    g = I.grf_k2(max(n, 16), 34)[:n] if target else None
+    Js, gs, _ = O.csr_gradient_serial(rp, col, val, q0, T, K, g)
+    ctx, keep = csr_ctx(X, torch, rp, col, val, T, K, P, X.PHI_STEPPER)
+    ctx.set_propagator(X.PROP_POLY, 200)
+    qd = dev(torch, q0, torch.float64)
+    ctx.set_control(qd)
+    if target:
+        ctx.set_objective(X.OBJ_TERMINAL_L2, dev(torch, g, torch.float64))
+    out = torch.empty_like(qd)
+    J = ctx.gradient(X.PARAEXP, out)
+    st = ctx.stats()
+    assert st["prop_degree"] > 0 and st["prop_tail"] <= 1e-12, st
+    assert abs(J - Js) / Js < 1e-10, (case, J, Js)
+    assert rel(out.cpu().numpy(), gs) < 1e-10, case
+    ctx.close()
+
+
+def test_csr_series_chain_segments_and_global_workspace(X, torch):
+    """n = 8000 (the chain's three vectors exceed a block's shared memory) and subintervals
+    long enough that the series runs in several segments per subinterval."""
+    rp, col, val = I.sparse_operator(8000, 4, 903)
+    T, K, P = 1.6, 512, 4
+    q0 = np.sin(np.arange(8000) * 0.01)
+    Js, gs, _ = O.csr_gradient_serial(rp, col, val, q0, T, K)
+    ctx, keep = csr_ctx(X, torch, rp, col, val, T, K, P, X.PHI_STEPPER, m=24)
+    ctx.set_propagator(X.PROP_POLY, 200)
+    qd = dev(torch, q0, torch.float64)
+    ctx.set_control(qd)
+    out = torch.empty_like(qd)
+    J = ctx.gradient(X.PARAEXP, out)
+    st = ctx.stats()
+    assert st["prop_substeps"] > 1, st
+    assert abs(J - Js) / Js < 1e-10 and rel(out.cpu().numpy(), gs) < 1e-10
+    ctx.close()
+
+
 def test_csr_lanes_in_global_memory_and_graph_replay(X, torch):
     """n = 8000: a lane's four vectors exceed a block's shared memory, so the lanes step
     in a global workspace; Paraexp with the stepper propagator against serial stepping of
