@@ -773,7 +773,10 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->stC, 2 * plane))) return rc;
     if ((rc = alloc(c, &c->traj2, (size_t)(c->K + 1) * N))) return rc;
     if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y))) return rc;
-    if ((rc = alloc(c, &c->G2buf, (size_t)P * N))) return rc;
+    c->roll2 = P > 1 && ad2_roll_ok(a);
+    // the halo-tile lanes' gradients: every lane's when they step the Paraexp lanes, else
+    // only the serial adjoint's (the wavefront lanes have FP32 planes of their own)
+    if ((rc = alloc(c, &c->G2buf, (size_t)(c->roll2 ? 1 : P) * N))) return rc;
     if ((rc = alloc(c, &c->GC, N))) return rc;
     PXA_CUDA(c, cudaMemset(c->coef2, 0, sizeof(float) * 3 * plane), "memset coef");
     PXA_CUDA(c, cudaMemset(c->stD, 0, sizeof(float) * 2 * plane), "memset");
@@ -783,7 +786,6 @@ int prepare(pxa_ctx* c) {
         !ad2_make_map(&c->mapC, c->stC, a, 2, 1) || !ad2_make_map(&c->mapCoef, c->coef2, a, 3, 3))
       return fail(c, PXA_ERR_CUDA, "cuTensorMapEncodeTiled failed for the 2D state arrays");
     if ((rc = alloc(c, &c->sc2, (size_t)3 * c->K))) return rc;
-    c->roll2 = P > 1 && ad2_roll_ok(a);
     if (c->roll2) {
       if ((rc = alloc(c, &c->tcoef2, 4 * plane))) return rc;
       if ((rc = alloc(c, &c->G2f, (size_t)P * N))) return rc;
@@ -1726,14 +1728,17 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
   }
   if (!do_a) return PXA_OK;
   ev_record(c, 2);
-  PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(float2) * (size_t)P * N, st), "zero G");
-  if (c->G2f) PXA_CUDA(c, cudaMemsetAsync(c->G2f, 0, sizeof(float) * (size_t)P * N, st), "zero Gf");
+  // the lanes as a register wavefront where the grid allows it (FP32 gradients G2f), else on
+  // halo tiles (double-float gradients G2buf): zero the one in use
+  const bool roll = c->roll2 && P > 1;
+  if (roll)
+    PXA_CUDA(c, cudaMemsetAsync(c->G2f, 0, sizeof(float) * (size_t)P * N, st), "zero Gf");
+  else
+    PXA_CUDA(c, cudaMemsetAsync(c->G2buf, 0, sizeof(float2) * (size_t)P * N, st), "zero G");
   PXA_CUDA(c, cudaMemsetAsync(c->GC, 0, sizeof(float2) * N, st), "zero GC");
   // Eq. hybadjinhom: lane l starts from the objective's source at its top row (l+1) k
   PXA_CUDA(c, launch_ad2_fill(st, a, c->stA, P, c->traj2, k, k, src), "lane init");
   const int lpc = P >= 16 ? 16 : P;
-  // the lanes as a register wavefront where the grid allows it, else on halo tiles
-  const bool roll = c->roll2 && P > 1;
   if (roll) {
     PXA_CUDA(c, launch_ad2_pack_coefT(st, a, c->op.u_dev, c->op.v_dev, c->tcoef2), "A^T coefficients");
   }
