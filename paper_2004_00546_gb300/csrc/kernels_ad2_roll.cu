@@ -29,7 +29,11 @@ namespace pxa {
 namespace {
 
 constexpr int RS = 56;      // output columns per strip (64 input columns, 4 lost per side)
-constexpr int RWARPS = 8;   // warps (independent tasks) per CTA
+// one warp (one task) per block, 16 blocks per SM (124 registers, rings 144 KB): a block's
+// resources free as soon as its task ends. Measured at 64 lanes x 2048^2: 3670 GB/s against
+// 3083 (8 warps x 2 blocks), 3159 (2 x 8), 3307 (1 x 20, 96 registers) and 1987 (1 x 24)
+constexpr int RWARPS = 1;   // warps (independent tasks) per CTA
+constexpr int RBLOCKS_PER_SM = 16;
 constexpr int BR = AD2_ROLL_BR;
 constexpr int NB = 2;       // ring blocks per warp (one in flight while the other is read)
 constexpr int BLOCK_FLOATS = 4 * BR * 64;  // state + u, v, f rows of one block
@@ -269,7 +273,12 @@ __device__ __forceinline__ void roll_task(const CUtensorMap* qmap, const CUtenso
 
 constexpr int TB_FLOATS = 7 * BR * 64;    // lambda, 4 coefficient planes, source, FP32 gradient
 constexpr int TRING_FLOATS = NB * TB_FLOATS;
-constexpr int TWARPS = 4;
+// one warp (one task) per block, 14 blocks per SM (their rings fill 215 KB of shared
+// memory; 123 registers): 14 warps per SM where 4-warp blocks fit 3 (12 warps, 164
+// registers), and a block's resources free as soon as its one task ends. Measured on C3's
+// 64 lanes: 1.38 ms against 1.49 (4 x 3), 1.55 (2 x 8) and 1.63 ms (4 x 4)
+constexpr int TWARPS = 1;
+constexpr int TBLOCKS_PER_SM = 14;
 
 struct CoefT2 {  // A^T coefficients of the thread's two points on one row
   f2 e, w, n, s;
@@ -435,7 +444,7 @@ __global__ void ad2_forcing_table_kernel(int64_t s0, int64_t count, double dt, d
 // One RK4 step for `lanes` lanes: lane l reads buffer buf_in and writes the other; its
 // forcing factors are sc[3*l*sc_stride + {0,1,2}]. Hs: output rows per segment (a
 // multiple of 8).
-__global__ void __launch_bounds__(32 * RWARPS, 2) ad2_rk4_roll_kernel(
+__global__ void __launch_bounds__(32 * RWARPS, RBLOCKS_PER_SM) ad2_rk4_roll_kernel(
     const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap cmap, Ad2Params p,
     float* __restrict__ states, int lanes, int buf_in, int nstrips, int nsegs, int Hs,
     const float* __restrict__ sc, int sc_stride, int* status) {
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(32 * RWARPS, 2) ad2_rk4_roll_kernel(
 // One reverse step for lanes lane0 .. lane0 + count - 1 of `lanes`: lane l reads buffer
 // buf_in and writes the other; it is at absolute step zsrc0 + l * z_stride (its source row
 // in the trajectory, and its forcing factors sc[3 (zsrc0 + l * z_stride) + {0, 1, 2}]).
-__global__ void __launch_bounds__(32 * TWARPS, 3) ad2_rk4T_roll_kernel(
+__global__ void __launch_bounds__(32 * TWARPS, TBLOCKS_PER_SM) ad2_rk4T_roll_kernel(
     const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap tmap,
     const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap gmap, Ad2Params p,
     float* __restrict__ states, float* __restrict__ G, int lanes, int lane0, int count, int buf_in,
@@ -578,6 +587,9 @@ cudaError_t launch_ad2_rk4_roll(cudaStream_t st, const CUtensorMap& qmap, const 
   const size_t sh = sizeof(float) * (size_t)RWARPS * RING_FLOATS;
   cudaError_t e = cudaFuncSetAttribute(ad2_rk4_roll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ad2_rk4_roll_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   static int per_sm = 0;
   const int Hs = roll_rows_for(p.nx, p.ny, lanes, (const void*)ad2_rk4_roll_kernel, RWARPS, sh, per_sm);
   const int nstrips = (p.nx + RS - 1) / RS, nsegs = (p.ny + Hs - 1) / Hs;
@@ -596,6 +608,10 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
   if (count <= 0 || lane0 < 0 || lane0 + count > lanes) return cudaErrorInvalidValue;
   const size_t sh = sizeof(float) * (size_t)TWARPS * TRING_FLOATS;
   cudaError_t e = cudaFuncSetAttribute(ad2_rk4T_roll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (e != cudaSuccess) return e;
+  // the rings of all resident blocks: the largest shared-memory carveout
+  e = cudaFuncSetAttribute(ad2_rk4T_roll_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   static int per_sm = 0;
   const int Hs = roll_rows_for(p.nx, p.ny, count, (const void*)ad2_rk4T_roll_kernel, TWARPS, sh, per_sm);
