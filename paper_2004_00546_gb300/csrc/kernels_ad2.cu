@@ -855,6 +855,21 @@ __global__ void ad2_add_padded_kernel(size_t count, float* __restrict__ dst, con
 }
 
 // J = sum of the per-(step, tile) partials, in a fixed order (one block).
+// First pass of the objective's sum: block b adds part[b chunk, (b + 1) chunk) in FP64 into
+// out[b]. Spread over the SMs because one SM completes only about one FP64 warp
+// instruction per 19 cycles on GB300: 1024 steps x 290 tile partials summed by one block
+// took ~0.1 ms on the path between the direct and the adjoint.
+__global__ void ad2_reduce_J_part_kernel(const double* __restrict__ part, size_t count, size_t chunk,
+                                         double* __restrict__ out) {
+  extern __shared__ double red[];
+  const size_t b0 = (size_t)blockIdx.x * chunk, b1 = min(count, b0 + chunk);
+  double s = 0.0;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// Second pass (or the whole sum when count is small): one block.
 __global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t count, double* J, int* status) {
   extern __shared__ double red[];
   double s = 0.0;
@@ -866,20 +881,25 @@ __global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t coun
   }
 }
 
-// grad = sum over lanes of G[l] (double-float) and Gf[l] (FP32) (+ extra), in FP64.
+// grad = sum over lanes of G[l] (double-float) and Gf[l] (FP32) (+ extra), read out in
+// FP64. The terms are added as a double-float (hi, lo) pair by FP32 two-sums, which keeps
+// the sum within about 2^-40 of its terms' magnitude (far below the FP32 rounding of the
+// terms themselves) without one FP64 add per term and point: 17 M of them at C3's size
+// cost ~30 us of the FP64 pipes.
 __global__ void ad2_sum_grad_kernel(size_t N, int lanes, const float2* __restrict__ G, int flanes,
                                     const float* __restrict__ Gf, const float2* __restrict__ extra,
                                     double* __restrict__ grad, int* status) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    if (extra) acc = (double)extra[i].x + (double)extra[i].y;
+    float2 acc = make_float2(0.0f, 0.0f);
     for (int l = 0; l < lanes; ++l) {
       const float2 v = G[(size_t)l * N + i];
-      acc += (double)v.x + (double)v.y;
+      acc = df_add(df_add(acc, v.x), v.y);
     }
-    for (int l = 0; l < flanes; ++l) acc += (double)Gf[(size_t)l * N + i];
-    grad[i] = acc;
-    if (!isfinite(acc)) set_status(status, PXA_ERR_NONFINITE);
+    for (int l = 0; l < flanes; ++l) acc = df_add(acc, Gf[(size_t)l * N + i]);
+    double r = (double)acc.x + (double)acc.y;
+    if (extra) r += (double)extra[i].x + (double)extra[i].y;
+    grad[i] = r;
+    if (!isfinite(r)) set_status(status, PXA_ERR_NONFINITE);
   }
 }
 
@@ -1050,8 +1070,18 @@ cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* J, int* status) {
-  ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(part, count, J, status);
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* scratch, double* J,
+                                int* status) {
+  size_t chunk = 2048;
+  if ((count + chunk - 1) / chunk > (size_t)AD2_REDUCE_J_BLOCKS)
+    chunk = (count + AD2_REDUCE_J_BLOCKS - 1) / AD2_REDUCE_J_BLOCKS;
+  const size_t nb = (count + chunk - 1) / chunk;
+  if (nb <= 1) {
+    ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(part, count, J, status);
+    return cudaGetLastError();
+  }
+  ad2_reduce_J_part_kernel<<<(unsigned)nb, 256, 40 * sizeof(double), st>>>(part, count, chunk, scratch);
+  ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(scratch, nb, J, status);
   return cudaGetLastError();
 }
 

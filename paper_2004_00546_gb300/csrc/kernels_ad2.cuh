@@ -55,7 +55,11 @@ cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const doub
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
                             const float* traj, int64_t row0, int64_t row_step, double scale);
 cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, const float* src);
-cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* J, int* status);
+// J = the sum of part[0 .. count) (FP64), in two passes over at most AD2_REDUCE_J_BLOCKS
+// blocks whose partial sums go to scratch (that many doubles).
+constexpr int AD2_REDUCE_J_BLOCKS = 1024;
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* scratch, double* J,
+                                int* status);
 // Register-wavefront RK4 step for many lanes (kernels_ad2_roll.cu); needs ad2_roll_ok.
 bool ad2_roll_ok(const Ad2Params& p);
 cudaError_t launch_ad2_forcing_table(cudaStream_t st, int64_t s0, int64_t count, double dt,

@@ -537,7 +537,7 @@ struct pxa_ctx {
   float* stA = nullptr;     // adjoint lanes ping-pong [2][P][Hp][Wp]
   float* stC = nullptr;     // homogeneous chain ping-pong [2][1][Hp][Wp]
   float* traj2 = nullptr;   // [(K+1)][ny*nx] FP32 direct trajectory
-  double* Jpart = nullptr;  // [K][tiles]
+  double* Jpart = nullptr;  // [K][tiles] + AD2_REDUCE_J_BLOCKS block sums
   float2* G2buf = nullptr;  // [P][ny*nx] lane gradients, double-float (hi, lo) FP32 pairs
   float* G2f = nullptr;     // [P][ny*nx] FP32 gradients of the wavefront lanes (K/P steps each)
   float2* GC = nullptr;     // [ny*nx] chain gradient, double-float
@@ -772,7 +772,8 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->stA, 2 * (size_t)P * plane))) return rc;
     if ((rc = alloc(c, &c->stC, 2 * plane))) return rc;
     if ((rc = alloc(c, &c->traj2, (size_t)(c->K + 1) * N))) return rc;
-    if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y))) return rc;
+    // the tile partials of every step, then room for the block sums of their reduction
+    if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y + AD2_REDUCE_J_BLOCKS))) return rc;
     c->roll2 = P > 1 && ad2_roll_ok(a);
     // the halo-tile lanes' gradients: every lane's when they step the Paraexp lanes, else
     // only the serial adjoint's (the wavefront lanes have FP32 planes of their own)
@@ -1723,7 +1724,8 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
                                  c->traj2, s + 1, c->Jpart, s, a.dtd / c->T, c->status, s > 0),
                "2d direct step");
     }
-    PXA_CUDA(c, launch_ad2_reduce_J(st, c->Jpart, (size_t)K * tiles, Jdev, c->status), "reduce J");
+    PXA_CUDA(c, launch_ad2_reduce_J(st, c->Jpart, (size_t)K * tiles, c->Jpart + (size_t)K * tiles, Jdev, c->status),
+             "reduce J");
     ev_record(c, 1);
   }
   if (!do_a) return PXA_OK;
