@@ -628,14 +628,15 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4T1_kernel(const __grid_constant
 // padded with ghosts; skipped when want_h == 0) and G += (i0 == 0 ? b_0 v_0 : 0) + sum_j
 // b_{i0+j} v_{i0+j} (FP32 within the launch, a double-float pair across launches, df_add);
 // v_{i0+4} goes to the other plane of V (padded with ghosts). ca / cb hold at least i0 + 5
-// coefficients.
+// coefficients, both FP32 (converting FP64 ones in every thread of every launch kept the
+// FP64 pipes 12 % busy in this latency-bound kernel).
 __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant__ CUtensorMap vmap,
                                                           const __grid_constant__ CUtensorMap cmap,
                                                           const __grid_constant__ CUtensorMap hmap,
                                                           const __grid_constant__ CUtensorMap wmap, int w_z,
                                                           Ad2Params p, float tau, float* __restrict__ V,
                                                           int buf_in, int i0, const float* __restrict__ ca,
-                                                          const double* __restrict__ cb,
+                                                          const float* __restrict__ cb,
                                                           float* __restrict__ H, int want_h,
                                                           float2* __restrict__ G, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
     ka[j] = __ldg(ca + i0 + j);
-    kb[j] = (float)__ldg(cb + i0 + j);
+    kb[j] = __ldg(cb + i0 + j);
   }
   if (!mbar_wait(&t.bar[0], 0)) {
     if (threadIdx.x == 0) set_status(status, PXA_ERR_TIMEOUT);
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(256, 2) ad2_poly_kernel(const __grid_constant_
 // (s kk + j) dt, Q = [3][kk][m+1] (FP64; s(t) = sin(omega t), 1 when omega == 0). One block
 // per segment, one thread per coefficient (m < blockDim.x).
 __global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, const double* __restrict__ Q,
-                                        double* __restrict__ b) {
+                                        float* __restrict__ b) {
   __shared__ double sv[3][128];
   const int s = blockIdx.x, i = threadIdx.x;
   double acc = 0.0;
@@ -793,7 +794,7 @@ __global__ void ad2_poly_forcing_kernel(int kk, int m, double dt, double omega, 
                sv[2][jj] * Q[(2 * (size_t)kk + j) * (m + 1) + i];
       }
   }
-  if (i <= m) b[(size_t)s * (m + 1) + i] = acc;
+  if (i <= m) b[(size_t)s * (m + 1) + i] = (float)acc;
 }
 
 // Pack u, v (FP64, [ny][nx]) and the forcing f - f_true into the padded FP32
@@ -833,18 +834,22 @@ __global__ void ad2_pack_coefT_kernel(Ad2Params p, const double* __restrict__ u,
 // Fill lanes' padded states: zero (src == nullptr), or scale * row(row0 + l*row_step)
 // of the FP32 trajectory (the adjoint's terminal source of each lane), or, when `add`
 // is set, state += padded vector `addv` (FP32 padded, per call one lane).
+// Lane l (blockIdx.y, strided) gets scale * traj row (row0 + l row_step), ghosts included,
+// or zero. FP32 product and 32-bit indices: an FP64 product with its two conversions per
+// point (three FP64-pipe instructions) and 64-bit divisions made this 16.8 M-point fill
+// take ~0.1 ms at C3's size.
 __global__ void ad2_fill_kernel(Ad2Params p, float* __restrict__ states, int lanes,
                                 const float* __restrict__ traj, int64_t row0, int64_t row_step,
-                                double scale) {
+                                float scale) {
   const size_t plane = (size_t)p.Hp * p.Wp;
-  const size_t N = (size_t)p.nx * p.ny;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N * lanes;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int l = (int)(i / N);
-    size_t r = i % N;
-    int x = (int)(r % p.nx), y = (int)(r / p.nx);
-    float val = traj ? (float)(scale * traj[(size_t)(row0 + (int64_t)l * row_step) * N + r]) : 0.0f;
-    store_with_ghosts(states + (size_t)l * plane, p, x, y, val);
+  const int N = p.nx * p.ny;
+  for (int l = blockIdx.y; l < lanes; l += gridDim.y) {
+    float* st = states + (size_t)l * plane;
+    const float* src = traj ? traj + (size_t)(row0 + (int64_t)l * row_step) * N : nullptr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+      const int y = r / p.nx, x = r - y * p.nx;
+      store_with_ghosts(st, p, x, y, src ? scale * src[r] : 0.0f);
+    }
   }
 }
 
@@ -854,7 +859,6 @@ __global__ void ad2_add_padded_kernel(size_t count, float* __restrict__ dst, con
     dst[i] += src[i];
 }
 
-// J = sum of the per-(step, tile) partials, in a fixed order (one block).
 // First pass of the objective's sum: block b adds part[b chunk, (b + 1) chunk) in FP64 into
 // out[b]. Spread over the SMs because one SM completes only about one FP64 warp
 // instruction per 19 cycles on GB300: 1024 steps x 290 tile partials summed by one block
@@ -1022,7 +1026,7 @@ cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUte
 
 cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const CUtensorMap& hmap,
                             const CUtensorMap& wmap, int w_z, const Ad2Params& p, float tau, float* V, int buf_in,
-                            int i0, const float* ca, const double* cb, float* H, int want_h, float2* G, int* status,
+                            int i0, const float* ca, const float* cb, float* H, int want_h, float2* G, int* status,
                             int pdl) {
   cudaError_t e = set_smem((const void*)ad2_poly_kernel);
   if (e != cudaSuccess) return e;
@@ -1031,7 +1035,7 @@ cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUte
 }
 
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
-                                    const double* Q, double* b) {
+                                    const double* Q, float* b) {
   if (segments < 1) return cudaSuccess;
   if (m < 0 || m >= 256) return cudaErrorInvalidValue;
   ad2_poly_forcing_kernel<<<segments, 256, 0, st>>>(kk, m, dt, omega, Q, b);
@@ -1054,11 +1058,10 @@ cudaError_t launch_ad2_pack_coefT(cudaStream_t st, const Ad2Params& p, const dou
 
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
                             const float* traj, int64_t row0, int64_t row_step, double scale) {
-  size_t total = (size_t)p.nx * p.ny * lanes;
-  int threads = 256;
-  int blocks = (int)((total + threads - 1) / threads);
-  if (blocks > 65535 * 8) blocks = 65535 * 8;
-  ad2_fill_kernel<<<blocks, threads, 0, st>>>(p, states, lanes, traj, row0, row_step, scale);
+  if (lanes <= 0) return cudaSuccess;
+  const int N = p.nx * p.ny, threads = 256;
+  const dim3 grid((unsigned)std::min((N + threads - 1) / threads, 1024), (unsigned)std::min(lanes, 65535));
+  ad2_fill_kernel<<<grid, threads, 0, st>>>(p, states, lanes, traj, row0, row_step, (float)scale);
   return cudaGetLastError();
 }
 

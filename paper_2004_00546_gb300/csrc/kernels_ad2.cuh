@@ -94,19 +94,19 @@ cudaError_t launch_ad2_rk4T_roll(cudaStream_t st, const CUtensorMap& qmap, const
 // v_{i0+j} = (tau A^T)^j v_{i0}, j = 1..4, on every tile from plane buf_in of V (vmap: ad2_make_map
 // over V with depth 2), writes v_{i0+4} to the other plane, and adds the interior's terms
 // a_i v_i to H (padded plane; H = a_0 v_0 + ... when i0 == 0; skipped when want_h == 0) and
-// b_i v_i to G (a double-float accumulator, [ny][nx] (hi, lo) FP32 pairs). ca (FP32) and cb (FP64) hold the coefficients 0 .. i0 + 4.
+// b_i v_i to G (a double-float accumulator, [ny][nx] (hi, lo) FP32 pairs). ca and cb (FP32) hold the coefficients 0 .. i0 + 4.
 // For i0 == 0 the input is v_0 = H + W: the tile of H (hmap, a map over the padded H
 // plane) plus, when w_z >= 0, plane w_z of wmap (the lane value at the segment's top).
 // pdl != 0: programmatic dependent launch (the coefficient tile and ca, cb are read before
 // the wait for the previous kernel, which must not have written them).
 cudaError_t launch_ad2_poly(cudaStream_t st, const CUtensorMap& vmap, const CUtensorMap& cmap, const CUtensorMap& hmap,
                             const CUtensorMap& wmap, int w_z, const Ad2Params& p, float tau, float* V, int buf_in,
-                            int i0, const float* ca, const double* cb, float* H, int want_h, float2* G, int* status,
+                            int i0, const float* ca, const float* cb, float* H, int want_h, float2* G, int* status,
                             int pdl);
 // The forcing-gradient coefficients b[s][0..m] of `segments` chain segments of kk steps
-// from the omega-free families Q = [3][kk][m+1] (m < 256).
+// from the omega-free families Q = [3][kk][m+1] (m < 256), summed in FP64, stored in FP32.
 cudaError_t launch_ad2_poly_forcing(cudaStream_t st, int segments, int kk, int m, double dt, double omega,
-                                    const double* Q, double* b);
+                                    const double* Q, float* b);
 // grad (FP64) = sum over `lanes` double-float accumulators G[l] and `flanes` FP32 ones Gf[l]
 // (+ extra, a double-float accumulator, may be NULL).
 cudaError_t launch_ad2_sum_grad(cudaStream_t st, size_t N, int lanes, const float2* G, int flanes, const float* Gf,

@@ -552,7 +552,7 @@ struct pxa_ctx {
   float* polyA = nullptr;    // [m+1] coefficients of R(z)^kk cut at degree m (m % 4 == 0)
   double* polyAd = nullptr;  // the same in FP64 (CSR chains)
   double* polyQ = nullptr;   // [3][kk][m+1] omega-free forcing families
-  double* polyB = nullptr;   // [segments][m+1] forcing-gradient coefficients of each segment
+  float* polyB = nullptr;    // [segments][m+1] forcing-gradient coefficients of each segment (FP32)
   float* hC = nullptr;       // [Hp][Wp] the chain's carried value
   int poly_m = 0, poly_sub = 1, poly_kk = 0;
   double poly_tail = 0.0;
@@ -1775,7 +1775,7 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
       const int lane_above = (sg + 1) / sub;  // its lane value when it does
       // the first launch reads h + w itself: plane (k & 1) P + lane_above of the lane states
       const int w_z = top ? (int)((k & 1) * P + lane_above) : -1;
-      const double* cb = c->polyB + (size_t)sg * (m + 1);
+      const float* cb = c->polyB + (size_t)sg * (m + 1);
       for (int i0 = 0, buf = 0; i0 < m; i0 += 4, buf ^= 1)
         PXA_CUDA(c, launch_ad2_poly(st, c->mapC, c->mapCoef, c->mapH, c->mapA, w_z, a, tau, c->stC, buf, i0,
                                     c->polyA, cb, c->hC, sg > 0 ? 1 : 0, c->GC, c->status, i0 > 0),
