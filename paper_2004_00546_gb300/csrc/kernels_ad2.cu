@@ -159,8 +159,9 @@ size_t ad2_smem_bytes() {
 // shared memory (stage values ping-pong between two tile buffers, one barrier per
 // stage). Lane l (global index) is at absolute step l * lane_k + s_local.
 // in/out: padded state arrays of the ping-pong pair, tensor-map z = buf * map_lanes + l.
-// traj (optional): interior of lane 0's new state as row traj_row. Jpart (WITH_J):
-// tile partial of (dt/T) ||q_new||^2 at Jpart[jrow * tiles + tile].
+// traj (optional): interior of lane 0's new state as row traj_row. Jpart (WITH_J): the
+// eight warps' partials of ||q_new||^2 over the tile (FP32) at
+// Jpart[(jrow * tiles + tile) * AD2_J_WARPS + warp]; launch_ad2_reduce_J sums them.
 template <bool WITH_J>
 __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__ CUtensorMap qmap,
                                                          const __grid_constant__ CUtensorMap cmap,
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
                                                          int buf_in, int64_t lane_k, int64_t s_local,
                                                          const float* __restrict__ sc,
                                                          float* __restrict__ traj, int64_t traj_row,
-                                                         double* __restrict__ Jpart, int64_t jrow,
-                                                         double dt_over_T, int* status) {
+                                                         float* __restrict__ Jpart, int64_t jrow,
+                                                         int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem t = carve(smem_raw);
   const int tile = blockIdx.x;
@@ -312,18 +313,14 @@ __global__ void __launch_bounds__(256, 2) ad2_rk4_kernel(const __grid_constant__
       }
     }
     if (WITH_J) {
-      // the few FP64 instructions this takes matter on GB300 (one FP64 warp instruction per
-      // 64 cycles): the squares of a thread's points and a warp's partials are summed in
-      // FP32, the eight warp sums in FP64
+      // no FP64 here (GB300 completes about one FP64 warp instruction per 19 cycles per SM,
+      // and a block's serial FP64 sum sat at the end of every step): each warp stores its
+      // FP32 partial; the reduction after the sweep adds them in double-float and FP64
+      static_assert(AD2_J_WARPS * 32 == 256, "one partial per warp of the 256-thread block");
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, o);
-      if ((threadIdx.x & 31) == 0) t.red[threadIdx.x >> 5] = (double)jl;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double sj = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sj += t.red[w];
-        Jpart[(size_t)jrow * gridDim.x + tile] = dt_over_T * sj;
-      }
+      if ((threadIdx.x & 31) == 0)
+        Jpart[((size_t)jrow * gridDim.x + tile) * AD2_J_WARPS + (threadIdx.x >> 5)] = jl;
     }
     __syncthreads();  // all reads of q[li & 1] and the stage buffers done before reuse
   }
@@ -859,29 +856,30 @@ __global__ void ad2_add_padded_kernel(size_t count, float* __restrict__ dst, con
     dst[i] += src[i];
 }
 
-// First pass of the objective's sum: block b adds part[b chunk, (b + 1) chunk) in FP64 into
-// out[b]. Spread over the SMs because one SM completes only about one FP64 warp
-// instruction per 19 cycles on GB300: 1024 steps x 290 tile partials summed by one block
-// took ~0.1 ms on the path between the direct and the adjoint.
-__global__ void ad2_reduce_J_part_kernel(const double* __restrict__ part, size_t count, size_t chunk,
+// First pass of the objective's sum: block b adds the FP32 partials part[b chunk,
+// (b + 1) chunk) as a double-float pair (FP32 two-sums, exact to about 2^-44 of the terms)
+// and then across the block in FP64 into out[b]. Spread over the SMs because one SM
+// completes only about one FP64 warp instruction per 19 cycles on GB300.
+__global__ void ad2_reduce_J_part_kernel(const float* __restrict__ part, size_t count, size_t chunk,
                                          double* __restrict__ out) {
   extern __shared__ double red[];
   const size_t b0 = (size_t)blockIdx.x * chunk, b1 = min(count, b0 + chunk);
-  double s = 0.0;
-  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += part[i];
-  s = block_sum(s, red);
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc = df_add(acc, part[i]);
+  const double s = block_sum((double)acc.x + (double)acc.y, red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// Second pass (or the whole sum when count is small): one block.
-__global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t count, double* J, int* status) {
+// Second pass: J = scale * the sum of the block sums (one block).
+__global__ void ad2_reduce_J_kernel(const double* __restrict__ part, size_t count, double scale, double* J,
+                                    int* status) {
   extern __shared__ double red[];
   double s = 0.0;
   for (size_t i = threadIdx.x; i < count; i += blockDim.x) s += part[i];
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
-    *J = s;
-    if (!isfinite(s)) set_status(status, PXA_ERR_NONFINITE);
+    *J = scale * s;
+    if (!isfinite(*J)) set_status(status, PXA_ERR_NONFINITE);
   }
 }
 
@@ -984,21 +982,20 @@ static cudaError_t set_smem(const void* fn) {
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
-                           float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
-                           int* status, int pdl) {
+                           float* traj, int64_t traj_row, float* Jpart, int64_t jrow, int* status, int pdl) {
   dim3 grid(p.tiles_x * p.tiles_y, (lanes + lanes_per_cta - 1) / lanes_per_cta);
   if (Jpart) {
     cudaError_t e = set_smem((const void*)ad2_rk4_kernel<true>);
     if (e != cudaSuccess) return e;
     return launch_ex(ad2_rk4_kernel<true>, grid, dim3(256), ad2_smem_bytes(), st, pdl != 0, qmap, cmap, p, states,
                      lanes, map_lanes, lanes_per_cta, buf_in, lane_k, s_local, sc, traj, traj_row, Jpart, jrow,
-                     dt_over_T, status);
+                     status);
   }
   cudaError_t e = set_smem((const void*)ad2_rk4_kernel<false>);
   if (e != cudaSuccess) return e;
   return launch_ex(ad2_rk4_kernel<false>, grid, dim3(256), ad2_smem_bytes(), st, pdl != 0, qmap, cmap, p, states,
                    lanes, map_lanes, lanes_per_cta, buf_in, lane_k, s_local, sc, traj, traj_row, Jpart, jrow,
-                   dt_over_T, status);
+                   status);
 }
 
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
@@ -1073,18 +1070,14 @@ cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* scratch, double* J,
-                                int* status) {
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const float* part, size_t count, double scale, double* scratch,
+                                double* J, int* status) {
   size_t chunk = 2048;
   if ((count + chunk - 1) / chunk > (size_t)AD2_REDUCE_J_BLOCKS)
     chunk = (count + AD2_REDUCE_J_BLOCKS - 1) / AD2_REDUCE_J_BLOCKS;
-  const size_t nb = (count + chunk - 1) / chunk;
-  if (nb <= 1) {
-    ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(part, count, J, status);
-    return cudaGetLastError();
-  }
+  const size_t nb = count ? (count + chunk - 1) / chunk : 1;
   ad2_reduce_J_part_kernel<<<(unsigned)nb, 256, 40 * sizeof(double), st>>>(part, count, chunk, scratch);
-  ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(scratch, nb, J, status);
+  ad2_reduce_J_kernel<<<1, 1024, 40 * sizeof(double), st>>>(scratch, nb, scale, J, status);
   return cudaGetLastError();
 }
 

@@ -43,8 +43,7 @@ bool ad2_make_map_box(CUtensorMap* map, float* base, const Ad2Params& p, int dep
 cudaError_t launch_ad2_rk4(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                            const Ad2Params& p, float* states, int lanes, int map_lanes,
                            int lanes_per_cta, int buf_in, int64_t lane_k, int64_t s_local, const float* sc,
-                           float* traj, int64_t traj_row, double* Jpart, int64_t jrow, double dt_over_T,
-                           int* status, int pdl);
+                           float* traj, int64_t traj_row, float* Jpart, int64_t jrow, int* status, int pdl);
 cudaError_t launch_ad2_rk4T(cudaStream_t st, const CUtensorMap& qmap, const CUtensorMap& cmap,
                             const Ad2Params& p, float* states, int lanes, int map_lanes,
                             int lanes_per_cta, int buf_in, int64_t lane_k, int64_t lane_off, int64_t s_local,
@@ -55,11 +54,13 @@ cudaError_t launch_ad2_pack_coef(cudaStream_t st, const Ad2Params& p, const doub
 cudaError_t launch_ad2_fill(cudaStream_t st, const Ad2Params& p, float* states, int lanes,
                             const float* traj, int64_t row0, int64_t row_step, double scale);
 cudaError_t launch_ad2_add_padded(cudaStream_t st, size_t count, float* dst, const float* src);
-// J = the sum of part[0 .. count) (FP64), in two passes over at most AD2_REDUCE_J_BLOCKS
-// blocks whose partial sums go to scratch (that many doubles).
+// J = scale * the sum of the FP32 partials part[0 .. count) (double-float within blocks,
+// FP64 across them), in two passes over at most AD2_REDUCE_J_BLOCKS blocks whose sums go
+// to scratch (that many doubles).
 constexpr int AD2_REDUCE_J_BLOCKS = 1024;
-cudaError_t launch_ad2_reduce_J(cudaStream_t st, const double* part, size_t count, double* scratch, double* J,
-                                int* status);
+constexpr int AD2_J_WARPS = 8;  // objective partials per tile and step (one per warp)
+cudaError_t launch_ad2_reduce_J(cudaStream_t st, const float* part, size_t count, double scale, double* scratch,
+                                double* J, int* status);
 // Register-wavefront RK4 step for many lanes (kernels_ad2_roll.cu); needs ad2_roll_ok.
 bool ad2_roll_ok(const Ad2Params& p);
 cudaError_t launch_ad2_forcing_table(cudaStream_t st, int64_t s0, int64_t count, double dt,

@@ -537,7 +537,8 @@ struct pxa_ctx {
   float* stA = nullptr;     // adjoint lanes ping-pong [2][P][Hp][Wp]
   float* stC = nullptr;     // homogeneous chain ping-pong [2][1][Hp][Wp]
   float* traj2 = nullptr;   // [(K+1)][ny*nx] FP32 direct trajectory
-  double* Jpart = nullptr;  // [K][tiles] + AD2_REDUCE_J_BLOCKS block sums
+  float* Jpart = nullptr;   // [K][tiles][AD2_J_WARPS] warp partials of the objective
+  double* Jred = nullptr;   // [AD2_REDUCE_J_BLOCKS] block sums of their reduction
   float2* G2buf = nullptr;  // [P][ny*nx] lane gradients, double-float (hi, lo) FP32 pairs
   float* G2f = nullptr;     // [P][ny*nx] FP32 gradients of the wavefront lanes (K/P steps each)
   float2* GC = nullptr;     // [ny*nx] chain gradient, double-float
@@ -635,6 +636,7 @@ void release_workspace(pxa_ctx* c) {
   c->scL = nullptr;
   c->scL_count = 0;
   c->Jpart = nullptr;
+  c->Jred = nullptr;
   c->G2buf = c->GC = nullptr;
   c->G2f = nullptr;
   c->rec = c->jt = c->LI = c->Hrows = c->gpart = c->sc = c->Jparts = c->rp = c->rq = nullptr;
@@ -772,8 +774,8 @@ int prepare(pxa_ctx* c) {
     if ((rc = alloc(c, &c->stA, 2 * (size_t)P * plane))) return rc;
     if ((rc = alloc(c, &c->stC, 2 * plane))) return rc;
     if ((rc = alloc(c, &c->traj2, (size_t)(c->K + 1) * N))) return rc;
-    // the tile partials of every step, then room for the block sums of their reduction
-    if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y + AD2_REDUCE_J_BLOCKS))) return rc;
+    if ((rc = alloc(c, &c->Jpart, (size_t)c->K * a.tiles_x * a.tiles_y * AD2_J_WARPS))) return rc;
+    if ((rc = alloc(c, &c->Jred, (size_t)AD2_REDUCE_J_BLOCKS))) return rc;
     c->roll2 = P > 1 && ad2_roll_ok(a);
     // the halo-tile lanes' gradients: every lane's when they step the Paraexp lanes, else
     // only the serial adjoint's (the wavefront lanes have FP32 planes of their own)
@@ -1721,10 +1723,11 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     PXA_CUDA(c, cudaMemsetAsync(c->traj2, 0, sizeof(float) * N, st), "zero row 0");
     for (int64_t s = 0; s < K; ++s) {
       PXA_CUDA(c, launch_ad2_rk4(st, c->mapD, c->mapCoef, a, c->stD, 1, 1, 1, (int)(s & 1), 0, s, c->sc2,
-                                 c->traj2, s + 1, c->Jpart, s, a.dtd / c->T, c->status, s > 0),
+                                 c->traj2, s + 1, c->Jpart, s, c->status, s > 0),
                "2d direct step");
     }
-    PXA_CUDA(c, launch_ad2_reduce_J(st, c->Jpart, (size_t)K * tiles, c->Jpart + (size_t)K * tiles, Jdev, c->status),
+    PXA_CUDA(c, launch_ad2_reduce_J(st, c->Jpart, (size_t)K * tiles * AD2_J_WARPS, a.dtd / c->T, c->Jred, Jdev,
+                                    c->status),
              "reduce J");
     ev_record(c, 1);
   }
@@ -2995,7 +2998,7 @@ int pxa_rk4_lanes_2d(pxa_ctx* c, int lanes, int64_t steps, double* out_dev, doub
                                       c->scL + 3 * s, (int)steps, c->status), "lanes step");
     } else {
       PXA_CUDA(c, launch_ad2_rk4(st, c->mapL, c->mapCoef, a, c->stL, lanes, lanes, lpc, (int)(s & 1),
-                                 steps, s, c->scL, nullptr, 0, nullptr, 0, 0.0, c->status, 0), "lanes step");
+                                 steps, s, c->scL, nullptr, 0, nullptr, 0, c->status, 0), "lanes step");
     }
   }
   PXA_CUDA(c, cudaEventRecord(e1, st), "record");
