@@ -31,7 +31,8 @@
  *                   velocity (u, v); q(0) = 0; control = f; the target is the
  *                   trajectory driven by f_true (pxa_set_target), J = (1/T) sum_{j=1..K}
  *                   dt ||q_j(f) - q_j(f_true)||^2 (Eq. cost). RK4 stepping in FP32 on
- *                   TMA-staged halo tiles; J sums FP32 tile partials in FP64, the
+ *                   TMA-staged halo tiles; J sums FP32 warp partials (double-float
+ *                   within blocks, FP64 across them), the
  *                   gradient accumulates as double-float (hi, lo) FP32 pairs and is
  *                   returned in FP64. Serial direct + Paraexp adjoint (hybrid scheme,
  *                   Sec. 3.3) with the stepper's own propagator for the homogeneous
