@@ -1,4 +1,6 @@
 """Pins of the 2D oracle (advection-diffusion with a frozen velocity field, Sec. 4.2)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -71,3 +73,40 @@ def test_gradient_vanishes_at_the_true_forcing():
     ft = I.fourier2d(n, n, 3, 22)
     J, g = O.ad2_gradient_serial(ft, ft, u, v, nu, T, K)
     assert J == 0.0 and np.abs(g).max() == 0.0
+
+
+@pytest.mark.parametrize("omega,t,dt", [(0.0, 0.0, 0.1), (1.0, 0.3, 0.05), (2.5, 1.1, 0.02)])
+def test_rk4_forcing_stage_times_simpson(omega, t, dt):
+    """With no velocity and no viscosity A = 0, and one RK4 step of dq/dt = s(t) f adds
+    Simpson's rule of s over [t, t + dt] times f: the forcing is sampled at t, at t + dt/2
+    (stages 2 and 3) and at t + dt (s = 1 when omega = 0)."""
+    n = 8
+    z = np.zeros((n, n))
+    f, q = I.fourier2d(n, n, 3, 5), I.fourier2d(n, n, 3, 6)
+    s = (lambda x: 1.0) if omega == 0.0 else (lambda x: math.sin(omega * x))
+    got = O.ad2_rk4_step(q, z, z, 0.0, dt, f, t=t, omega=omega)
+    ref = q + dt / 6.0 * (s(t) + 4.0 * s(t + dt / 2) + s(t + dt)) * f
+    assert np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("omega", [0.0, 1.3])
+def test_gradient_closed_form_without_transport(omega):
+    """A = 0 (no velocity, no viscosity): q_k = c_k (f - f_true), c_k the Simpson weights of
+    s summed over the first k steps, so J = (dt/T) sum_k c_k^2 ||f - f_true||^2 and
+    grad J = 2 (dt/T) sum_k c_k^2 (f - f_true). This fixes the objective's normalisation
+    and the adjoint's forcing quadrature without the oracle's adjoint code."""
+    n, T, K = 6, 0.7, 14
+    dt = T / K
+    z = np.zeros((n, n))
+    f, ft = I.fourier2d(n, n, 3, 7), I.fourier2d(n, n, 3, 8)
+    s = (lambda x: 1.0) if omega == 0.0 else (lambda x: math.sin(omega * x))
+    c = S = 0.0
+    for k in range(K):
+        t = k * dt
+        c += dt / 6.0 * (s(t) + 4.0 * s(t + dt / 2) + s(t + dt))
+        S += c * c
+    d = f - ft
+    J, g = O.ad2_gradient_serial(f, ft, z, z, 0.0, T, K, omega=omega)
+    assert J == pytest.approx(dt / T * S * float(np.sum(d * d)), rel=1e-13)
+    gref = 2.0 * dt / T * S * d
+    assert np.abs(g - gref).max() <= 1e-13 * np.abs(gref).max()
