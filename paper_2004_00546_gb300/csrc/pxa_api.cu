@@ -1766,13 +1766,11 @@ int enqueue_ad2(pxa_ctx* c, int mode, int parts, double* Jdev, double* grad) {
     // subinterval), h <- a(tau A^T)(h + w), and each segment's forcing gradient
     // b_s(tau A^T)(h + w) goes to GC; w is the lane value at the subinterval's top, added
     // at the first segment of each subinterval (a, b cut after degree m)
-    const float* Wbuf = c->stA + (size_t)(k & 1) * P * plane;
     const int m = c->poly_m, sub = c->poly_sub, kk = c->poly_kk;
     const int segments = (P - 1) * sub;
     const float tau = (float)((double)kk * a.dtd);
     PXA_CUDA(c, launch_ad2_poly_forcing(st, segments, kk, m, a.dtd, a.omega, c->polyQ, c->polyB), "poly forcing");
     PXA_CUDA(c, cudaMemsetAsync(c->hC, 0, sizeof(float) * plane, st), "zero chain");
-    (void)Wbuf;
     for (int sg = segments - 1; sg >= 0; --sg) {
       const bool top = (sg + 1) % sub == 0;  // the segment ends at a subinterval's top
       const int lane_above = (sg + 1) / sub;  // its lane value when it does
